@@ -1,0 +1,56 @@
+"""Plant plausible mistakes in copies of the oracle source (on the CPU) and
+check that some pin catches each one."""
+import pytest
+
+import oracle
+import oracle_pins
+
+# (name, text in qwlsh_oracle.c, replacement, pins expected to catch it)
+MUTANTS = [
+    ("hash_drops_offset", "double u = (t[i] + (double)b[i]) / (double)w;",
+     "double u = (t[i]) / (double)w;", ["pin_hash_exact_sum"]),
+    ("hash_truncates", "double u = (t[i] + (double)b[i]) / (double)w;\n            double f = floor(u);",
+     "double u = (t[i] + (double)b[i]) / (double)w;\n            double f = trunc(u);",
+     ["pin_hash_exact_sum"]),
+    ("level_floor_division_truncates", "if ((a % R != 0) && (a < 0)) q -= 1;", "",
+     ["pin_collision_counts", "pin_t3_fixpoint", "pin_workload_semantics"]),
+    ("threshold_strict", "for (int64_t j = 0; j < n; ++j) if (col[j] >= l) ncand += 1;",
+     "for (int64_t j = 0; j < n; ++j) if (col[j] > l) ncand += 1;",
+     ["pin_workload_semantics", "pin_v_ge_n_exact"]),
+    ("truncation_fewest_collisions_first", "if (a->col != b->col) return a->col > b->col ? -1 : 1;",
+     "if (a->col != b->col) return a->col < b->col ? -1 : 1;", ["pin_workload_semantics"]),
+    ("truncation_ignores_previous_level", "cs[nc].prev = prev[j];", "cs[nc].prev = 0;",
+     ["pin_workload_semantics"]),
+    ("radius_grows_additively", "R *= c;", "R += 1;",
+     ["pin_workload_semantics"]),
+    ("distance_not_squared", "s = s + diff * diff;", "s = s + fabs(diff);",
+     ["pin_bruteforce", "pin_v_ge_n_exact"]),
+    ("ties_by_larger_id",
+     "if (a->dist != b->dist) return a->dist < b->dist ? -1 : 1;\n    if (a->id != b->id) return a->id < b->id ? -1 : 1;",
+     "if (a->dist != b->dist) return a->dist < b->dist ? -1 : 1;\n    if (a->id != b->id) return a->id > b->id ? -1 : 1;",
+     ["pin_duplicates_tie_by_id"]),
+    ("index_not_anchored", "p[j].bid = H[(size_t)j * m + i] - o[i];", "p[j].bid = H[(size_t)j * m + i];",
+     ["pin_index_sorted_arrays"]),
+    ("eq1_tail_sign", "return 1.0 - two_phi_neg - tail;", "return 1.0 - two_phi_neg + tail;",
+     ["pin_collision_prob_quadrature"]),
+    ("alpha_swaps_p1_p2", "return (z * p1 + p2) / (1.0 + z);", "return (z * p2 + p1) / (1.0 + z);",
+     ["pin_threshold_balance"]),
+    ("query_not_anchored", "int64_t g = (int64_t)hq[i] - (int64_t)o[i];\n        int64_t beta",
+     "int64_t g = (int64_t)hq[i];\n        int64_t beta", ["pin_collision_counts", "pin_single_projection_is_e2lsh"]),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, name, old, new, pins):
+    src = open(oracle.SOURCE).read()
+    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    mutated = tmp_path / "mutant.c"
+    mutated.write_text(src.replace(old, new))
+    lib = oracle.compile_oracle(str(mutated), out=str(tmp_path / "libmutant.so"))
+    orc = oracle.Oracle(lib)
+    caught = []
+    for pname in pins:
+        fails = getattr(oracle_pins, pname)(orc)
+        if fails:
+            caught.append(pname)
+    assert caught, f"mutant {name} survived pins {pins}"
