@@ -1,0 +1,202 @@
+/*
+ * qwlsh.h -- C ABI of the GB300 LSH query-workload library (libqwlsh.so).
+ *
+ * The library builds an LSH index over n float32 vectors and answers a whole
+ * workload of k-nearest-neighbour queries against it, following the method of
+ * arXiv 1907.11803 and the LSH variants it builds on:
+ *   - hash family (Section 3): h_i(v) = floor((a_i . v + b_i) / w),
+ *     a_i ~ N(0, I_d), b_i ~ U[0, w);
+ *   - collision counting over m hash functions with a threshold l and at most
+ *     k + v candidates read per query (Section 3.1);
+ *   - virtual rehashing: the lookup range of every projection grows by the
+ *     factor c per level, served by range searches over one sorted structure
+ *     per hash function (Section 2);
+ *   - exact Euclidean top-k over the candidates (Section 3, c-k-ANN; Section 4
+ *     workload of |Q| queries).
+ *
+ * Conventions shared by every entry point:
+ *   - Arrays are row-major and contiguous.  float32 inputs, int32/int64 ids.
+ *   - Ownership: every buffer passed in or out belongs to the caller and is
+ *     only read / written during the call (or, for device-memory calls, by the
+ *     work the call enqueues on `stream`).  The library owns the index handle
+ *     and the device workspace inside it.
+ *   - `mem` says where the caller's buffers live: QW_MEM_DEVICE (device
+ *     pointers; the call enqueues work on `stream` and returns; outputs are
+ *     valid once the stream reaches that point) or QW_MEM_HOST (host pointers;
+ *     the call copies in, computes, copies out, and returns with the outputs
+ *     written).
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.
+ *   - Errors: every function returns a qw_status; nothing throws across the
+ *     ABI.  On failure qw_last_error() gives a message for the calling thread.
+ *     Invalid arguments are rejected before any work is enqueued.
+ *   - One index handle must not be used by two calls at the same time.
+ */
+#ifndef QWLSH_H
+#define QWLSH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t qw_status;
+#define QW_OK 0
+#define QW_ERR_ARG 1      /* invalid argument (null pointer, bad size, unsupported field) */
+#define QW_ERR_OOM 2      /* device or host allocation failed */
+#define QW_ERR_CUDA 3     /* a CUDA runtime call or kernel launch failed */
+#define QW_ERR_TIMEOUT 4  /* a bounded device loop ran out of iterations */
+#define QW_ERR_RANGE 5    /* a bucket id or bucket span does not fit in int32 */
+
+#define QW_MEM_DEVICE 0
+#define QW_MEM_HOST 1
+
+/* Number of int64 statistics written per query by qw_run_workload. */
+#define QW_NSTAT 8
+/* Statistic slots (per query):
+ *  0 levels run (1 = stopped at radius R = 1)
+ *  1 radius R of the last level
+ *  2 |C_R|, candidates (collision count >= l) at the last level
+ *  3 candidates kept after the k + v bound
+ *  4 termination: 2 = |C_R| >= k + v; 3 = R exceeds every bucket id of the
+ *    data and of the query, so no further level can change C_R
+ *  5 sorted index entries inside the last level's bucket ranges, summed over
+ *    projections (the entries an incremental scan reads in total)
+ *  6 sum over levels of the entries inside that level's ranges
+ *  7 |C_{R/c}|, candidates at the level before the last */
+
+/* Largest supported values. */
+#define QW_MAX_M 127          /* projections per index (collision counts are 7-bit) */
+#define QW_MAX_CAND 4096      /* k + v */
+
+typedef struct qw_index qw_index;
+
+/* Index parameters (Sections 3, 3.1, 6). */
+typedef struct {
+    int32_t m;     /* number of hash functions / projections, 1..QW_MAX_M */
+    float w;       /* bucket width w > 0 */
+    int32_t c;     /* approximation ratio, also the per-level radius factor; integer >= 2 */
+    int32_t v;     /* allowed false positives (Section 3.1 uses 100); >= 0 */
+    int32_t l;     /* collision threshold 1..m; 0 = derive from Eq. 1 (see
+                      qw_collision_threshold) with beta = v / n */
+    float delta;   /* error probability used when deriving l; <= 0 means 1/e (Section 6) */
+} qw_index_params;
+
+/* Per-workload options.  Zero-initialise; unknown non-zero fields are rejected. */
+typedef struct {
+    int32_t batch;        /* queries per pass over the index; 0 = library choice */
+    int32_t reserved[7];  /* must be zero */
+} qw_query_params;
+
+typedef struct {
+    int64_t n;             /* data vectors */
+    int32_t d;             /* dimension */
+    int32_t m;             /* projections */
+    float w;
+    int32_t c;
+    int32_t v;
+    int32_t l;             /* collision threshold in use */
+    int32_t tile;          /* ids per index tile (entries are grouped by id / tile) */
+    int32_t n_tiles;
+    int32_t span_max;      /* largest anchored bucket id over all projections */
+    int64_t n_fixups;      /* data projections recomputed in FP64 at build time */
+    int64_t device_bytes;  /* device memory held by the index (excluding workspace) */
+} qw_index_info;
+
+/* Library version string. */
+const char *qw_version(void);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *qw_last_error(void);
+
+/* Eq. 1: collision probability P(r) of the hash family for two points at
+ * distance r and bucket width w, in closed form
+ *   1 - 2 Phi(-w/r) - (2 r / (sqrt(2 pi) w)) (1 - exp(-w^2 / (2 r^2))).
+ * Returns NaN for r <= 0 or w <= 0. */
+double qw_collision_probability(double r, double w);
+
+/* Collision threshold l for m projections (Section 3.1; the paper gives no
+ * value, so the collision-counting rule is used): with p1 = P(1), p2 = P(c),
+ * beta = v / n and z = sqrt(ln(2 / beta) / ln(1 / delta)),
+ *   alpha = (z p1 + p2) / (1 + z),  l = ceil(alpha m)  clamped to [1, m].
+ * delta <= 0 means 1/e.  Returns -1 on invalid arguments. */
+int32_t qw_collision_threshold(int32_t m, float w, int32_t c, int64_t n, int32_t v, float delta);
+
+/* Hash vectors (Section 3): H[r * m + i] = floor((a_i . V_r + b_i) / w).
+ * V: nv x d float32, A: m x d float32, b: m float32, H: nv x m int32; all
+ * DEVICE pointers.  The projection runs in FP32; every result whose FP32 value
+ * lies within a proven error bound (and at least 1e-5 w) of a bucket boundary
+ * is recomputed in FP64 with the dot product summed in index order, so H
+ * equals the FP64 result.  *n_fixups (optional, host) receives how many were
+ * recomputed; passing it makes the call wait for the stream.
+ * Errors: QW_ERR_ARG (null pointer, nv < 0, d < 1, m < 1, w <= 0),
+ * QW_ERR_RANGE (a bucket id outside int32; H is then unspecified),
+ * QW_ERR_CUDA. */
+qw_status qw_hash(const float *V, int64_t nv, int32_t d, const float *A, const float *b,
+                  int32_t m, float w, int32_t *H, int64_t *n_fixups, void *stream);
+
+/* Build an index over data (n x d float32) with projections A (m x d float32)
+ * and offsets b (m float32), all in `mem` space.  The index keeps its own
+ * device copies of data, A and b; the caller's buffers may be freed after the
+ * call returns (device mode: after the stream has passed the call).
+ * Layout built (Section 2: one sorted structure per hash function):
+ *   anchor o_i = min over data of h_i, bucket id bid = h_i - o_i >= 0,
+ *   and, for every projection, the (bid, id) pairs sorted by bid then id,
+ *   grouped by id tile, with a directory of the distinct bids of each tile.
+ * The call waits for the stream.  *out receives the handle (free with
+ * qw_index_free).
+ * Errors: QW_ERR_ARG (null pointer, n < 1, n >= 2^31, d < 1, bad params),
+ * QW_ERR_RANGE (bucket id or span outside int32), QW_ERR_OOM, QW_ERR_CUDA. */
+qw_status qw_build_index(const float *data, int64_t n, int32_t d, const float *A,
+                         const float *b, const qw_index_params *params, int32_t mem,
+                         void *stream, qw_index **out);
+
+/* Answer a workload of nq queries (nq x d float32) for the k nearest
+ * neighbours each (Sections 3.1, 4).  Per query: levels R = 1, c, c^2, ...;
+ * C_R = { o : o collides with q on >= l projections at radius R }; stop at the
+ * first level with |C_R| >= k + v, or when R exceeds every bucket id of the
+ * data and the query; keep at most k + v candidates (those of the previous
+ * level first, then more collisions, then smaller id); return the k nearest
+ * by exact distance (ties by smaller id).
+ * Outputs: ids (nq x k int64, -1 where fewer than k candidates), dists
+ * (nq x k float32, Euclidean distance, +inf where id is -1), stats (optional,
+ * nq x QW_NSTAT int64, slots above).  All in `mem` space.
+ * Ids equal those of the FP64 definition: distances are computed in FP32 and
+ * every candidate whose order against a neighbour is not certain under the
+ * FP32 error bound is recomputed in FP64.
+ * Errors: QW_ERR_ARG (null pointer, nq < 0, k < 1, k > n, k + v > QW_MAX_CAND,
+ * non-zero reserved fields), QW_ERR_RANGE (query bucket id outside int32),
+ * QW_ERR_OOM, QW_ERR_CUDA. */
+qw_status qw_run_workload(qw_index *index, const float *queries, int64_t nq, int32_t k,
+                          const qw_query_params *qparams, int64_t *ids, float *dists,
+                          int64_t *stats, int32_t mem, void *stream);
+
+/* The candidate sets of a workload, for inspection: runs the steps of
+ * qw_run_workload up to and including the k + v bound and writes, per query,
+ * the kept candidates in ascending id order with their collision counts at the
+ * last level.  cand_ids: nq x (k + v) int64 padded with -1; cand_col:
+ * nq x (k + v) int32 padded with 0 (optional); stats as in qw_run_workload
+ * (optional).  All in `mem` space.  Errors as qw_run_workload. */
+qw_status qw_workload_candidates(qw_index *index, const float *queries, int64_t nq, int32_t k,
+                                 const qw_query_params *qparams, int64_t *cand_ids,
+                                 int32_t *cand_col, int64_t *stats, int32_t mem, void *stream);
+
+/* Copy index metadata into *info (host). */
+qw_status qw_index_get_info(const qw_index *index, qw_index_info *info);
+
+/* Export the index for inspection, into HOST buffers: o and span (m int32),
+ * and, per projection, every entry's bucket id and data id (m x n int32 each)
+ * in the index's own order: by id tile (id / tile), then bucket id, then id.
+ * Any output pointer may be NULL.  Waits for the stream. */
+qw_status qw_index_export(const qw_index *index, int32_t *o, int32_t *span,
+                          int32_t *entry_bid, int32_t *entry_id, void *stream);
+
+/* Free an index and its device memory (synchronises the device first). */
+void qw_index_free(qw_index *index);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QWLSH_H */

@@ -1,0 +1,541 @@
+// qw_api.cu -- the C ABI (include/qwlsh.h): argument checks, device memory
+// of the index and its workspace, and the order of kernel launches.  No step
+// of the method's arithmetic runs on the host.
+#include "qw_internal.cuh"
+
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace qw {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+void clear_error() { g_last_error.clear(); }
+
+qw_status cuda_status(cudaError_t e, const char *what)
+{
+    std::string msg = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+    set_error(msg);
+    return e == cudaErrorMemoryAllocation ? QW_ERR_OOM : QW_ERR_CUDA;
+}
+
+qw_status DevBuf::ensure(size_t want)
+{
+    if (want <= bytes) return QW_OK;
+    release();
+    if (want == 0) return QW_OK;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        bytes = 0;
+        (void)cudaGetLastError();
+        set_error("device allocation of " + std::to_string(want) + " bytes failed");
+        return QW_ERR_OOM;
+    }
+    bytes = want;
+    return QW_OK;
+}
+
+void DevBuf::release()
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+static qw_status arg_error(const std::string &msg)
+{
+    set_error(msg);
+    return QW_ERR_ARG;
+}
+
+}  // namespace qw
+
+using namespace qw;
+
+struct qw_index {
+    int64_t n = 0;
+    int d = 0, m = 0, c = 2, v = 0, l = 1;
+    float w = 1.0f;
+    int nT = 0;
+    int32_t span_max = 0;
+    int64_t n_fixups = 0;
+    DevBuf X, A, b, o, span, lid, dir_bid, dir_off, dir_start, dir_cnt;
+    // workspace for queries (grow-only)
+    DevBuf w_q, w_hq, w_state, w_counters, w_cand, w_out, w_err;
+    int64_t device_bytes = 0;
+
+    IndexView view() const
+    {
+        IndexView v;
+        v.X = X.as<float>();
+        v.n = n;
+        v.d = d;
+        v.m = m;
+        v.nT = nT;
+        v.o = o.as<int32_t>();
+        v.span = span.as<int32_t>();
+        v.lid = lid.as<uint16_t>();
+        v.dir_bid = dir_bid.as<int32_t>();
+        v.dir_off = dir_off.as<int32_t>();
+        v.dir_start = dir_start.as<int64_t>();
+        v.dir_cnt = dir_cnt.as<int32_t>();
+        return v;
+    }
+};
+
+extern "C" {
+
+const char *qw_version(void) { return "qwlsh-gb300 0.1 (sm_103a)"; }
+
+const char *qw_last_error(void) { return g_last_error.c_str(); }
+
+double qw_collision_probability(double r, double w)
+{
+    if (!(r > 0.0) || !(w > 0.0)) return NAN;
+    const double x = w / r;
+    // 1 - 2 Phi(-x) - (2 / (sqrt(2 pi) x)) (1 - exp(-x^2 / 2)),  2 Phi(-x) = erfc(x / sqrt 2)
+    return 1.0 - erfc(x * 0.70710678118654752440) -
+           (0.79788456080286535588 / x) * (1.0 - exp(-0.5 * x * x));
+}
+
+int32_t qw_collision_threshold(int32_t m, float w, int32_t c, int64_t n, int32_t v, float delta)
+{
+    if (m < 1 || !(w > 0.0f) || c < 2 || n < 1 || v < 0) return -1;
+    const double dl = delta > 0.0f ? (double)delta : exp(-1.0);
+    if (!(dl < 1.0)) return -1;
+    const double p1 = qw_collision_probability(1.0, w);
+    const double p2 = qw_collision_probability((double)c, w);
+    double beta = (double)v / (double)n;
+    if (beta > 1.0) beta = 1.0;
+    if (!(beta > 0.0)) return m;  // no false positive allowed: demand every projection
+    const double z = sqrt(log(2.0 / beta) / log(1.0 / dl));
+    const double alpha = (z * p1 + p2) / (1.0 + z);
+    int32_t l = (int32_t)ceil(alpha * (double)m);
+    return std::min(m, std::max(1, l));
+}
+
+qw_status qw_hash(const float *V, int64_t nv, int32_t d, const float *A, const float *b,
+                  int32_t m, float w, int32_t *H, int64_t *n_fixups, void *stream)
+{
+    clear_error();
+    if (!V || !A || !b || !H) return arg_error("qw_hash: null pointer");
+    if (nv < 0 || d < 1 || m < 1 || !(w > 0.0f)) return arg_error("qw_hash: bad size or width");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevBuf scratch;  // err word + fixup counter
+    QW_TRY(scratch.ensure(16));
+    int *err = scratch.as<int>();
+    unsigned long long *fix = reinterpret_cast<unsigned long long *>(scratch.as<char>() + 8);
+    QW_CUDA_TRY(cudaMemsetAsync(scratch.p, 0, 16, s));
+    qw_status st = launch_hash(V, nv, d, A, b, m, w, H, m, 1, err, fix, s);
+    if (st != QW_OK) { scratch.release(); return st; }
+    int h_err = 0;
+    unsigned long long h_fix = 0;
+    cudaError_t e1 = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t e2 = cudaMemcpyAsync(&h_fix, fix, sizeof(h_fix), cudaMemcpyDeviceToHost, s);
+    cudaError_t e3 = cudaStreamSynchronize(s);
+    scratch.release();
+    if (e1 != cudaSuccess) return cuda_status(e1, "qw_hash copy");
+    if (e2 != cudaSuccess) return cuda_status(e2, "qw_hash copy");
+    if (e3 != cudaSuccess) return cuda_status(e3, "qw_hash sync");
+    if (n_fixups) *n_fixups = (int64_t)h_fix;
+    if (h_err & 2) {
+        set_error("qw_hash: a bucket id falls outside int32");
+        return QW_ERR_RANGE;
+    }
+    return QW_OK;
+}
+
+static qw_status build_impl(qw_index *ix, const float *data, const float *A, const float *b,
+                            int32_t mem, cudaStream_t s)
+{
+    const int64_t n = ix->n;
+    const int d = ix->d, m = ix->m;
+    const cudaMemcpyKind kind = mem == QW_MEM_HOST ? cudaMemcpyHostToDevice
+                                                   : cudaMemcpyDeviceToDevice;
+    QW_TRY(ix->X.ensure((size_t)n * d * sizeof(float)));
+    QW_TRY(ix->A.ensure((size_t)m * d * sizeof(float)));
+    QW_TRY(ix->b.ensure((size_t)m * sizeof(float)));
+    QW_CUDA_TRY(cudaMemcpyAsync(ix->X.p, data, (size_t)n * d * sizeof(float), kind, s));
+    QW_CUDA_TRY(cudaMemcpyAsync(ix->A.p, A, (size_t)m * d * sizeof(float), kind, s));
+    QW_CUDA_TRY(cudaMemcpyAsync(ix->b.p, b, (size_t)m * sizeof(float), kind, s));
+
+    // 1. bucket ids of the data, projection-major (m x n)
+    DevBuf Ht, scratch;
+    QW_TRY(Ht.ensure((size_t)n * m * sizeof(int32_t)));
+    QW_TRY(scratch.ensure(64));
+    int *err = scratch.as<int>();
+    unsigned long long *fix = reinterpret_cast<unsigned long long *>(scratch.as<char>() + 8);
+    QW_CUDA_TRY(cudaMemsetAsync(scratch.p, 0, 16, s));
+    QW_TRY(launch_hash(ix->X.as<float>(), n, d, ix->A.as<float>(), ix->b.as<float>(), m, ix->w,
+                       Ht.as<int32_t>(), 1, n, err, fix, s));
+
+    // 2. anchors and spans
+    QW_TRY(ix->o.ensure((size_t)m * sizeof(int32_t)));
+    QW_TRY(ix->span.ensure((size_t)m * sizeof(int32_t)));
+    DevBuf hmax;
+    QW_TRY(hmax.ensure((size_t)m * sizeof(int32_t)));
+    {
+        std::vector<int32_t> init_lo(m, INT32_MAX), init_hi(m, INT32_MIN);
+        QW_CUDA_TRY(cudaMemcpyAsync(ix->o.p, init_lo.data(), m * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, s));
+        QW_CUDA_TRY(cudaMemcpyAsync(hmax.p, init_hi.data(), m * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, s));
+        QW_TRY(launch_minmax(Ht.as<int32_t>(), n, m, ix->o.as<int32_t>(), hmax.as<int32_t>(), s));
+    }
+    std::vector<int32_t> h_o(m), h_hi(m);
+    int h_err = 0;
+    unsigned long long h_fix = 0;
+    QW_CUDA_TRY(cudaMemcpyAsync(h_o.data(), ix->o.p, m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    QW_CUDA_TRY(cudaMemcpyAsync(h_hi.data(), hmax.p, m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    QW_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    QW_CUDA_TRY(cudaMemcpyAsync(&h_fix, fix, sizeof(h_fix), cudaMemcpyDeviceToHost, s));
+    QW_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h_err & 2) {
+        set_error("qw_build_index: a data bucket id falls outside int32");
+        return QW_ERR_RANGE;
+    }
+    ix->n_fixups = (int64_t)h_fix;
+    std::vector<int32_t> h_span(m);
+    ix->span_max = 0;
+    for (int i = 0; i < m; ++i) {
+        int64_t sp = (int64_t)h_hi[i] - (int64_t)h_o[i];
+        if (sp > 2147483646LL) {
+            set_error("qw_build_index: bucket span of a projection exceeds int32");
+            return QW_ERR_RANGE;
+        }
+        h_span[i] = (int32_t)sp;
+        ix->span_max = std::max(ix->span_max, h_span[i]);
+    }
+    QW_CUDA_TRY(cudaMemcpyAsync(ix->span.p, h_span.data(), m * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, s));
+
+    // 3. directory capacity per (projection, tile): min(tile length, span + 1)
+    const int nT = ix->nT;
+    std::vector<int64_t> h_start((size_t)m * nT);
+    int64_t total = 0;
+    for (int i = 0; i < m; ++i) {
+        for (int t = 0; t < nT; ++t) {
+            int64_t len = std::min<int64_t>(kTile, n - (int64_t)t * kTile);
+            h_start[(size_t)i * nT + t] = total;
+            total += std::min<int64_t>(len, (int64_t)h_span[i] + 1);
+        }
+    }
+    QW_TRY(ix->lid.ensure((size_t)m * n * sizeof(uint16_t)));
+    QW_TRY(ix->dir_bid.ensure((size_t)total * sizeof(int32_t)));
+    QW_TRY(ix->dir_off.ensure((size_t)total * sizeof(int32_t)));
+    QW_TRY(ix->dir_start.ensure((size_t)m * nT * sizeof(int64_t)));
+    QW_TRY(ix->dir_cnt.ensure((size_t)m * nT * sizeof(int32_t)));
+    QW_CUDA_TRY(cudaMemcpyAsync(ix->dir_start.p, h_start.data(), h_start.size() * sizeof(int64_t),
+                                cudaMemcpyHostToDevice, s));
+    QW_TRY(launch_tile_sort(Ht.as<int32_t>(), n, m, nT, ix->o.as<int32_t>(), ix->lid.as<uint16_t>(),
+                            ix->dir_bid.as<int32_t>(), ix->dir_off.as<int32_t>(),
+                            ix->dir_start.as<int64_t>(), ix->dir_cnt.as<int32_t>(), s));
+    QW_CUDA_TRY(cudaStreamSynchronize(s));
+    ix->device_bytes = (int64_t)(ix->X.bytes + ix->A.bytes + ix->b.bytes + ix->o.bytes +
+                                 ix->span.bytes + ix->lid.bytes + ix->dir_bid.bytes +
+                                 ix->dir_off.bytes + ix->dir_start.bytes + ix->dir_cnt.bytes);
+    return QW_OK;
+}
+
+qw_status qw_build_index(const float *data, int64_t n, int32_t d, const float *A, const float *b,
+                         const qw_index_params *p, int32_t mem, void *stream, qw_index **out)
+{
+    clear_error();
+    if (!out) return arg_error("qw_build_index: out is null");
+    *out = nullptr;
+    if (!data || !A || !b || !p) return arg_error("qw_build_index: null pointer");
+    if (mem != QW_MEM_DEVICE && mem != QW_MEM_HOST) return arg_error("qw_build_index: bad mem flag");
+    if (n < 1 || n > 2147483647LL) return arg_error("qw_build_index: n must be in [1, 2^31)");
+    if (d < 1) return arg_error("qw_build_index: d must be >= 1");
+    if (p->m < 1 || p->m > QW_MAX_M) return arg_error("qw_build_index: m must be in [1, 127]");
+    if (!(p->w > 0.0f) || !isfinite(p->w)) return arg_error("qw_build_index: w must be > 0");
+    if (p->c < 2) return arg_error("qw_build_index: c must be an integer >= 2");
+    if (p->v < 0) return arg_error("qw_build_index: v must be >= 0");
+    if (p->l < 0 || p->l > p->m) return arg_error("qw_build_index: l must be in [0, m]");
+    qw_index *ix = new (std::nothrow) qw_index();
+    if (!ix) {
+        set_error("qw_build_index: host allocation failed");
+        return QW_ERR_OOM;
+    }
+    ix->n = n;
+    ix->d = d;
+    ix->m = p->m;
+    ix->w = p->w;
+    ix->c = p->c;
+    ix->v = p->v;
+    ix->l = p->l > 0 ? p->l : qw_collision_threshold(p->m, p->w, p->c, n, p->v, p->delta);
+    if (ix->l < 1) {
+        delete ix;
+        return arg_error("qw_build_index: cannot derive the collision threshold (bad delta?)");
+    }
+    ix->nT = (int)((n + kTile - 1) / kTile);
+    qw_status st = build_impl(ix, data, A, b, mem, (cudaStream_t)stream);
+    if (st != QW_OK) {
+        qw_index_free(ix);
+        return st;
+    }
+    *out = ix;
+    return QW_OK;
+}
+
+static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
+                          const qw_query_params *qp, int64_t *ids, float *dists,
+                          int64_t *stats, int64_t *cand_ids, int32_t *cand_col, int32_t mem,
+                          cudaStream_t s)
+{
+    const bool want_cand = cand_ids != nullptr;
+    const int m = ix->m, d = ix->d;
+    const int cap = k + ix->v;
+    const int64_t wpq_bytes = (int64_t)ix->nT * kTile;  // counter bytes per query
+    int64_t B = qp && qp->batch > 0 ? qp->batch : 0;
+    if (B == 0) {
+        const int64_t budget = (int64_t)2 << 30;  // counters of one batch
+        B = std::max<int64_t>(1, budget / wpq_bytes);
+    }
+    B = std::min<int64_t>(B, std::max<int64_t>(nq, 1));
+    B = std::min<int64_t>(B, 65535);
+    const bool host = mem == QW_MEM_HOST;
+
+    // workspace
+    QW_TRY(ix->w_hq.ensure((size_t)B * m * sizeof(int32_t)));
+    QW_TRY(ix->w_counters.ensure((size_t)B * wpq_bytes));
+    QW_TRY(ix->w_cand.ensure((size_t)B * cap * 2 * sizeof(int32_t)));
+    QW_TRY(ix->w_err.ensure(64));
+    const size_t st_bytes = (size_t)B * m * 8 + (size_t)B * 8 * 16 + 64;
+    QW_TRY(ix->w_state.ensure(st_bytes));
+    // per-batch output staging for host mode: ids, dists, stats, candidates
+    const size_t out_ids = (size_t)B * k * sizeof(int64_t);
+    const size_t out_dists = (size_t)B * k * sizeof(float);
+    const size_t out_stats = (size_t)B * QW_NSTAT * sizeof(int64_t);
+    const size_t out_cids = want_cand ? (size_t)B * cap * sizeof(int64_t) : 0;
+    const size_t out_ccol = want_cand ? (size_t)B * cap * sizeof(int32_t) : 0;
+    auto up16 = [](size_t x) { return (x + 15) / 16 * 16; };
+    if (host) {
+        QW_TRY(ix->w_q.ensure((size_t)B * d * sizeof(float)));
+        QW_TRY(ix->w_out.ensure(up16(out_ids) + up16(out_dists) + up16(out_stats) +
+                                up16(out_cids) + up16(out_ccol)));
+    }
+    QueryState st;
+    {
+        char *p = ix->w_state.as<char>();
+        auto take = [&](size_t bytes) { char *r = p; p += (bytes + 15) / 16 * 16; return r; };
+        st.g = reinterpret_cast<int64_t *>(take((size_t)B * m * 8));
+        st.top = reinterpret_cast<int64_t *>(take((size_t)B * 8));
+        st.finalR = reinterpret_cast<int64_t *>(take((size_t)B * 8));
+        st.scan_level = reinterpret_cast<int64_t *>(take((size_t)B * 8));
+        st.scan_last = reinterpret_cast<int64_t *>(take((size_t)B * 8));
+        st.scan_full = reinterpret_cast<int64_t *>(take((size_t)B * 8));
+        st.active = reinterpret_cast<int32_t *>(take((size_t)B * 4));
+        st.ncand = reinterpret_cast<int32_t *>(take((size_t)B * 4));
+        st.nprev = reinterpret_cast<int32_t *>(take((size_t)B * 4));
+        st.cross = reinterpret_cast<int32_t *>(take((size_t)B * 4));
+        st.term = reinterpret_cast<int32_t *>(take((size_t)B * 4));
+        st.levels = reinterpret_cast<int32_t *>(take((size_t)B * 4));
+        st.nkeep = reinterpret_cast<int32_t *>(take((size_t)B * 4));
+        st.max_top = reinterpret_cast<unsigned long long *>(take(8));
+        if ((size_t)(p - ix->w_state.as<char>()) > ix->w_state.bytes) {
+            set_error("internal: query state workspace too small");
+            return QW_ERR_CUDA;
+        }
+    }
+    st.counters = ix->w_counters.as<uint32_t>();
+    st.cand = ix->w_cand.as<int32_t>();
+    st.cand_col = st.cand + (size_t)B * cap;
+    int *err = ix->w_err.as<int>();
+    const IndexView view = ix->view();
+
+    for (int64_t b0 = 0; b0 < nq; b0 += B) {
+        const int nb = (int)std::min<int64_t>(B, nq - b0);
+        const float *Qb;
+        int64_t *ids_b = nullptr, *stats_b = nullptr, *cids_b = nullptr;
+        float *dists_b = nullptr;
+        int32_t *ccol_b = nullptr;
+        if (host) {
+            QW_CUDA_TRY(cudaMemcpyAsync(ix->w_q.p, queries + b0 * d, (size_t)nb * d * sizeof(float),
+                                        cudaMemcpyHostToDevice, s));
+            Qb = ix->w_q.as<float>();
+            char *o = ix->w_out.as<char>();
+            ids_b = reinterpret_cast<int64_t *>(o);
+            dists_b = reinterpret_cast<float *>(o + up16(out_ids));
+            char *o2 = o + up16(out_ids) + up16(out_dists);
+            if (stats) stats_b = reinterpret_cast<int64_t *>(o2);
+            o2 += up16(out_stats);
+            if (want_cand) cids_b = reinterpret_cast<int64_t *>(o2);
+            o2 += up16(out_cids);
+            if (want_cand && cand_col) ccol_b = reinterpret_cast<int32_t *>(o2);
+        } else {
+            Qb = queries + b0 * d;
+            if (ids) ids_b = ids + b0 * k;
+            if (dists) dists_b = dists + b0 * k;
+            stats_b = stats ? stats + b0 * QW_NSTAT : nullptr;
+            if (want_cand) cids_b = cand_ids + b0 * cap;
+            if (want_cand && cand_col) ccol_b = cand_col + b0 * cap;
+        }
+        QW_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+        QW_TRY(launch_hash(Qb, nb, d, ix->A.as<float>(), ix->b.as<float>(), m, ix->w,
+                           ix->w_hq.as<int32_t>(), m, 1, err, nullptr, s));
+        QW_TRY(launch_query_setup(view, ix->w_hq.as<int32_t>(), nb, st, s));
+        unsigned long long max_top = 0;
+        int h_err = 0;
+        QW_CUDA_TRY(cudaMemcpyAsync(&max_top, st.max_top, sizeof(max_top), cudaMemcpyDeviceToHost, s));
+        QW_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        QW_CUDA_TRY(cudaStreamSynchronize(s));
+        if (h_err & 2) {
+            set_error("qw_run_workload: a query bucket id falls outside int32");
+            return QW_ERR_RANGE;
+        }
+        // levels 0..L where c^L > max_top: afterwards every query has stopped
+        int64_t R = 1, Rp = 1;
+        for (int level = 0;; ++level) {
+            QW_TRY(launch_level(view, nb, level, R, Rp, ix->l, st, s));
+            QW_TRY(launch_decide(nb, level, R, cap, st, s));
+            if ((unsigned long long)R > max_top) break;
+            if (level > 62) {
+                set_error("qw_run_workload: level limit reached");
+                return QW_ERR_TIMEOUT;
+            }
+            Rp = R;
+            R *= ix->c;
+        }
+        QW_TRY(launch_collect(view, nb, ix->l, cap, st, stats_b, s));
+        if (want_cand) QW_TRY(launch_candidates_out(st, nb, cap, cids_b, ccol_b, s));
+        if (ids) QW_TRY(launch_rerank(view, Qb, nb, k, cap, st, ids_b, dists_b, s));
+        if (host) {
+            if (ids) {
+                QW_CUDA_TRY(cudaMemcpyAsync(ids + b0 * k, ids_b, (size_t)nb * k * sizeof(int64_t),
+                                            cudaMemcpyDeviceToHost, s));
+                QW_CUDA_TRY(cudaMemcpyAsync(dists + b0 * k, dists_b, (size_t)nb * k * sizeof(float),
+                                            cudaMemcpyDeviceToHost, s));
+            }
+            if (stats)
+                QW_CUDA_TRY(cudaMemcpyAsync(stats + b0 * QW_NSTAT, stats_b,
+                                            (size_t)nb * QW_NSTAT * sizeof(int64_t),
+                                            cudaMemcpyDeviceToHost, s));
+            if (want_cand) {
+                QW_CUDA_TRY(cudaMemcpyAsync(cand_ids + b0 * cap, cids_b,
+                                            (size_t)nb * cap * sizeof(int64_t),
+                                            cudaMemcpyDeviceToHost, s));
+                if (cand_col)
+                    QW_CUDA_TRY(cudaMemcpyAsync(cand_col + b0 * cap, ccol_b,
+                                                (size_t)nb * cap * sizeof(int32_t),
+                                                cudaMemcpyDeviceToHost, s));
+            }
+        }
+    }
+    if (host) QW_CUDA_TRY(cudaStreamSynchronize(s));
+    return QW_OK;
+}
+
+static qw_status check_workload_args(const qw_index *ix, const float *queries, int64_t nq,
+                                     int32_t k, const qw_query_params *qp, int32_t mem)
+{
+    if (!ix) return arg_error("qw_run_workload: index is null");
+    if (nq < 0) return arg_error("qw_run_workload: nq < 0");
+    if (nq > 0 && !queries) return arg_error("qw_run_workload: null pointer");
+    if (mem != QW_MEM_DEVICE && mem != QW_MEM_HOST) return arg_error("qw_run_workload: bad mem flag");
+    if (k < 1 || (int64_t)k > ix->n) return arg_error("qw_run_workload: k must be in [1, n]");
+    if ((int64_t)k + ix->v > QW_MAX_CAND) return arg_error("qw_run_workload: k + v exceeds 4096");
+    if (qp) {
+        if (qp->batch < 0) return arg_error("qw_run_workload: batch < 0");
+        for (int r = 0; r < 7; ++r)
+            if (qp->reserved[r] != 0) return arg_error("qw_run_workload: reserved field set");
+    }
+    return QW_OK;
+}
+
+qw_status qw_run_workload(qw_index *ix, const float *queries, int64_t nq, int32_t k,
+                          const qw_query_params *qp, int64_t *ids, float *dists, int64_t *stats,
+                          int32_t mem, void *stream)
+{
+    clear_error();
+    QW_TRY(check_workload_args(ix, queries, nq, k, qp, mem));
+    if (nq > 0 && (!ids || !dists)) return arg_error("qw_run_workload: null output pointer");
+    if (nq == 0) return QW_OK;
+    return run_impl(ix, queries, nq, k, qp, ids, dists, stats, nullptr, nullptr, mem,
+                    (cudaStream_t)stream);
+}
+
+qw_status qw_workload_candidates(qw_index *ix, const float *queries, int64_t nq, int32_t k,
+                                 const qw_query_params *qp, int64_t *cand_ids, int32_t *cand_col,
+                                 int64_t *stats, int32_t mem, void *stream)
+{
+    clear_error();
+    QW_TRY(check_workload_args(ix, queries, nq, k, qp, mem));
+    if (nq > 0 && !cand_ids) return arg_error("qw_workload_candidates: cand_ids is null");
+    if (nq == 0) return QW_OK;
+    return run_impl(ix, queries, nq, k, qp, nullptr, nullptr, stats, cand_ids, cand_col, mem,
+                    (cudaStream_t)stream);
+}
+
+qw_status qw_index_get_info(const qw_index *ix, qw_index_info *info)
+{
+    clear_error();
+    if (!ix || !info) return arg_error("qw_index_get_info: null pointer");
+    info->n = ix->n;
+    info->d = ix->d;
+    info->m = ix->m;
+    info->w = ix->w;
+    info->c = ix->c;
+    info->v = ix->v;
+    info->l = ix->l;
+    info->tile = kTile;
+    info->n_tiles = ix->nT;
+    info->span_max = ix->span_max;
+    info->n_fixups = ix->n_fixups;
+    info->device_bytes = ix->device_bytes;
+    return QW_OK;
+}
+
+qw_status qw_index_export(const qw_index *ix, int32_t *o, int32_t *span, int32_t *entry_bid,
+                          int32_t *entry_id, void *stream)
+{
+    clear_error();
+    if (!ix) return arg_error("qw_index_export: index is null");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int m = ix->m;
+    const int64_t n = ix->n;
+    if (o) QW_CUDA_TRY(cudaMemcpyAsync(o, ix->o.p, m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (span)
+        QW_CUDA_TRY(cudaMemcpyAsync(span, ix->span.p, m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (entry_bid || entry_id) {
+        DevBuf eb, ei;
+        if (entry_bid) QW_TRY(eb.ensure((size_t)m * n * sizeof(int32_t)));
+        if (entry_id) QW_TRY(ei.ensure((size_t)m * n * sizeof(int32_t)));
+        QW_TRY(launch_export(ix->lid.as<uint16_t>(), ix->dir_bid.as<int32_t>(),
+                             ix->dir_off.as<int32_t>(), ix->dir_start.as<int64_t>(),
+                             ix->dir_cnt.as<int32_t>(), n, m, ix->nT, eb.as<int32_t>(),
+                             ei.as<int32_t>(), s));
+        if (entry_bid)
+            QW_CUDA_TRY(cudaMemcpyAsync(entry_bid, eb.p, (size_t)m * n * sizeof(int32_t),
+                                        cudaMemcpyDeviceToHost, s));
+        if (entry_id)
+            QW_CUDA_TRY(cudaMemcpyAsync(entry_id, ei.p, (size_t)m * n * sizeof(int32_t),
+                                        cudaMemcpyDeviceToHost, s));
+        QW_CUDA_TRY(cudaStreamSynchronize(s));
+        eb.release();
+        ei.release();
+    }
+    QW_CUDA_TRY(cudaStreamSynchronize(s));
+    return QW_OK;
+}
+
+void qw_index_free(qw_index *ix)
+{
+    if (!ix) return;
+    cudaDeviceSynchronize();
+    DevBuf *bufs[] = {&ix->X, &ix->A, &ix->b, &ix->o, &ix->span, &ix->lid, &ix->dir_bid,
+                      &ix->dir_off, &ix->dir_start, &ix->dir_cnt, &ix->w_q, &ix->w_hq,
+                      &ix->w_state, &ix->w_counters, &ix->w_cand, &ix->w_out, &ix->w_err};
+    for (DevBuf *bb : bufs) bb->release();
+    delete ix;
+}
+
+}  // extern "C"

@@ -1,0 +1,127 @@
+// qw_internal.cuh -- declarations shared by the library's translation units.
+//
+// Nothing here is shared with the CPU oracle; the oracle is a separate C file
+// with its own arithmetic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qwlsh.h"
+
+namespace qw {
+
+// Ids per index tile.  Entries of one projection are grouped by tile
+// (id / kTile), so a tile's collision counters fit in shared memory and its
+// ids fit in 16 bits.
+constexpr int kTile = 32768;
+constexpr int kTileShift = 15;
+
+// Bucket id written by the FP32 projection when the value is too close to a
+// bucket boundary to trust; the FP64 pass replaces every such entry.
+constexpr int32_t kNeedsFp64 = INT32_MIN;
+
+// Thread-local error text behind qw_last_error().
+void set_error(const std::string &msg);
+void clear_error();
+
+qw_status cuda_status(cudaError_t e, const char *what);
+
+#define QW_CUDA_TRY(call)                                           \
+    do {                                                            \
+        cudaError_t qw_e_ = (call);                                 \
+        if (qw_e_ != cudaSuccess) return qw::cuda_status(qw_e_, #call); \
+    } while (0)
+
+#define QW_TRY(call)                        \
+    do {                                    \
+        qw_status qw_s_ = (call);           \
+        if (qw_s_ != QW_OK) return qw_s_;   \
+    } while (0)
+
+// Grow-only device buffer.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    qw_status ensure(size_t want);
+    void release();
+    template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// ---------------------------------------------------------------- projection
+// H[r * ld_row + i * ld_col] = floor((a_i . V_r + b_i) / w), FP32 with an
+// FP64 recomputation of every entry near a bucket boundary.  err (device int)
+// gets bit 1 set when a bucket id falls outside int32.  fixups (device
+// unsigned long long, may be null) counts FP64 recomputations.
+qw_status launch_hash(const float *V, int64_t nv, int d, const float *A, const float *b, int m,
+                      float w, int32_t *H, int64_t ld_row, int64_t ld_col, int *err,
+                      unsigned long long *fixups, cudaStream_t s);
+
+// ---------------------------------------------------------------- index build
+qw_status launch_minmax(const int32_t *Ht, int64_t n, int m, int32_t *hmin, int32_t *hmax,
+                        cudaStream_t s);
+qw_status launch_tile_sort(const int32_t *Ht, int64_t n, int m, int nT, const int32_t *o,
+                           uint16_t *lid, int32_t *dir_bid, int32_t *dir_off,
+                           const int64_t *dir_start, int32_t *dir_cnt, cudaStream_t s);
+qw_status launch_export(const uint16_t *lid, const int32_t *dir_bid, const int32_t *dir_off,
+                        const int64_t *dir_start, const int32_t *dir_cnt, int64_t n, int m,
+                        int nT, int32_t *entry_bid, int32_t *entry_id, cudaStream_t s);
+
+// ---------------------------------------------------------------- queries
+struct IndexView {
+    const float *X;
+    int64_t n;
+    int d;
+    int m;
+    int nT;
+    const int32_t *o;
+    const int32_t *span;
+    const uint16_t *lid;
+    const int32_t *dir_bid;
+    const int32_t *dir_off;
+    const int64_t *dir_start;
+    const int32_t *dir_cnt;
+};
+
+// Per-batch query state, all device arrays of length nb (or nb x m).
+struct QueryState {
+    int64_t *g;             // nb x m: h_i(q) - o_i
+    int64_t *top;           // nb: max_i max(span_i, g_i)
+    int32_t *active;        // nb
+    int32_t *ncand;         // nb: |C_R| after the last finished level
+    int32_t *nprev;         // nb
+    int32_t *cross;         // nb: candidates gained in the running level
+    int32_t *term;          // nb
+    int32_t *levels;        // nb
+    int64_t *finalR;        // nb
+    int64_t *scan_level;    // nb
+    int64_t *scan_last;     // nb
+    int64_t *scan_full;     // nb
+    int32_t *nkeep;         // nb
+    unsigned long long *max_top;  // 1
+    uint32_t *counters;     // nb x (nT * kTile / 4)
+    int32_t *cand;          // nb x cap
+    int32_t *cand_col;      // nb x cap
+};
+
+qw_status launch_query_setup(const IndexView &ix, const int32_t *HQ, int nb, QueryState &st,
+                             cudaStream_t s);
+qw_status launch_level(const IndexView &ix, int nb, int level, int64_t R, int64_t Rp, int l,
+                       QueryState &st, cudaStream_t s);
+qw_status launch_decide(int nb, int level, int64_t R, int cap, QueryState &st, cudaStream_t s);
+qw_status launch_collect(const IndexView &ix, int nb, int l, int cap, QueryState &st,
+                         int64_t *stats_out, cudaStream_t s);
+qw_status launch_candidates_out(const QueryState &st, int nb, int cap, int64_t *cand_ids,
+                                int32_t *cand_col, cudaStream_t s);
+qw_status launch_rerank(const IndexView &ix, const float *Qb, int nb, int k, int cap,
+                        const QueryState &st, int64_t *ids_out, float *dists_out,
+                        cudaStream_t s);
+
+}  // namespace qw

@@ -1,0 +1,210 @@
+// qw_rerank.cu -- exact distances on the kept candidates and the top-k
+// (Section 3: c-k-ANN returns the k objects nearest to q among those found;
+// Section 1.2: the candidates are read from storage to remove false
+// positives).
+//
+// One CTA per query.  Each warp streams whole candidate rows with 16-byte
+// loads and forms the FP32 squared distance (per-lane fused multiply-add
+// chains, then a butterfly sum).  For that summation order the FP32 result
+// differs from the exact value by at most rho times the value, with
+//   rho = (ceil(d / 32) + 12) * 2^-24 * 1.02,
+// (at most ceil(d / 32) + 3 chained additions per lane, 5 butterfly levels, 2
+// roundings of the difference and square) -- and the FP64 reference differs
+// from the exact value by far less than the slack in that constant.
+// After sorting by (FP32 distance, id), two neighbours whose FP32 gap is not
+// larger than the sum of their bounds may be out of order.  Every maximal run
+// of such neighbours that reaches into the first k positions is recomputed in
+// FP64 with the reference summation order (index order, no fused
+// multiply-add), and the array is re-sorted on (FP64 value if recomputed,
+// FP32 value otherwise, id).  The runs are separated from everything else by
+// certain gaps, so the first k ids are exactly those of the FP64 order, ties
+// broken by the smaller id.
+#include "qw_internal.cuh"
+#include "qw_scan.cuh"
+
+#include <math_constants.h>
+
+namespace qw {
+namespace {
+
+constexpr int RR_THREADS = 256;
+constexpr int RR_WARPS = RR_THREADS / 32;
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+__global__ void __launch_bounds__(RR_THREADS) rerank_kernel(
+    const float *__restrict__ X, int d, const float *__restrict__ Qb, int k, int cap, int P2,
+    const int32_t *__restrict__ cand, const int32_t *__restrict__ nkeep,
+    int64_t *__restrict__ ids_out, float *__restrict__ dists_out, bool vec)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    double *key = reinterpret_cast<double *>(sm);
+    float *d32 = reinterpret_cast<float *>(key + P2);
+    float *outd = d32 + P2;
+    int32_t *sid = reinterpret_cast<int32_t *>(outd + P2);
+    uint8_t *mark = reinterpret_cast<uint8_t *>(sid + P2);
+    __shared__ int scan_tmp[RR_WARPS];
+    __shared__ int any_mark;
+
+    const int q = blockIdx.x;
+    const int nc = nkeep[q];
+    const float *qv = Qb + (int64_t)q * d;
+    const int32_t *cl = cand + (int64_t)q * cap;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) any_mark = 0;
+
+    // 1. FP32 squared distances, one warp per candidate row
+    for (int j = warp; j < P2; j += RR_WARPS) {
+        if (j >= nc) {
+            if (lane == 0) {
+                d32[j] = CUDART_INF_F;
+                sid[j] = INT32_MAX;
+            }
+            continue;
+        }
+        const int32_t id = cl[j];
+        const float *x = X + (int64_t)id * d;
+        float acc = 0.0f;
+        if (vec) {
+            const float4 *x4 = reinterpret_cast<const float4 *>(x);
+            const float4 *q4 = reinterpret_cast<const float4 *>(qv);
+            for (int c = lane; c < (d >> 2); c += 32) {
+                float4 a = __ldg(x4 + c), b = __ldg(q4 + c);
+                float t0 = a.x - b.x, t1 = a.y - b.y, t2 = a.z - b.z, t3 = a.w - b.w;
+                acc = fmaf(t0, t0, acc);
+                acc = fmaf(t1, t1, acc);
+                acc = fmaf(t2, t2, acc);
+                acc = fmaf(t3, t3, acc);
+            }
+        } else {
+            for (int c = lane; c < d; c += 32) {
+                float t0 = __ldg(x + c) - __ldg(qv + c);
+                acc = fmaf(t0, t0, acc);
+            }
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            d32[j] = acc;
+            sid[j] = id;
+        }
+    }
+    __syncthreads();
+
+    // 2. sort by (FP32 distance, id)
+    for (int kk = 2; kk <= P2; kk <<= 1) {
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int x = threadIdx.x; x < (P2 >> 1); x += RR_THREADS) {
+                int a = 2 * x - (x & (jj - 1));
+                int c = a + jj;
+                bool up = (a & kk) == 0;
+                float ka = d32[a], kc = d32[c];
+                int32_t ia = sid[a], ic = sid[c];
+                bool gt = (ka > kc) || (ka == kc && ia > ic);
+                if (gt == up) {
+                    d32[a] = kc; d32[c] = ka;
+                    sid[a] = ic; sid[c] = ia;
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    // 3. runs of neighbours whose order FP32 cannot certify
+    const double rho = (double)((d + 31) / 32 + 12) * 5.9604644775390625e-08 * 1.02;
+    const int per = (P2 + RR_THREADS - 1) / RR_THREADS;
+    const int j0 = threadIdx.x * per;
+    const int j1 = min(P2, j0 + per);
+    auto gap_uncertain = [&](int j) -> bool {  // between j and j + 1
+        if (j < 0 || j + 1 >= nc) return false;
+        double a = (double)d32[j], b = (double)d32[j + 1];
+        return (b - a) <= rho * (a + b) * 1.0000001;
+    };
+    int last_start = -1;
+    for (int j = j0; j < j1; ++j)
+        if (j == 0 || !gap_uncertain(j - 1)) last_start = j;
+    int run_start = block_exclusive_max<RR_THREADS>(last_start, -1, scan_tmp);
+    int nmark = 0;
+    for (int j = j0; j < j1; ++j) {
+        if (j == 0 || !gap_uncertain(j - 1)) run_start = j;
+        bool mk = (j < nc) && (run_start < k) && (gap_uncertain(j - 1) || gap_uncertain(j));
+        mark[j] = mk ? 1 : 0;
+        nmark += mk ? 1 : 0;
+    }
+    if (nmark) atomicAdd(&any_mark, nmark);
+    __syncthreads();
+
+    // 4. FP64 recomputation of the marked runs, in the reference order
+    for (int j = threadIdx.x; j < P2; j += RR_THREADS) {
+        if (j < nc && mark[j]) {
+            const float *x = X + (int64_t)sid[j] * d;
+            double s = 0.0;
+            for (int c = 0; c < d; ++c) {
+                double t = __dsub_rn((double)x[c], (double)qv[c]);
+                s = __dadd_rn(s, __dmul_rn(t, t));
+            }
+            key[j] = s;
+            outd[j] = (float)sqrt(s);
+        } else {
+            key[j] = (j < nc) ? (double)d32[j] : CUDART_INF;
+            outd[j] = (j < nc) ? sqrtf(d32[j]) : CUDART_INF_F;
+        }
+    }
+    __syncthreads();
+
+    // 5. re-sort on the certified keys when anything was recomputed
+    if (any_mark) {
+        for (int kk = 2; kk <= P2; kk <<= 1) {
+            for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                for (int x = threadIdx.x; x < (P2 >> 1); x += RR_THREADS) {
+                    int a = 2 * x - (x & (jj - 1));
+                    int c = a + jj;
+                    bool up = (a & kk) == 0;
+                    double ka = key[a], kc = key[c];
+                    int32_t ia = sid[a], ic = sid[c];
+                    bool gt = (ka > kc) || (ka == kc && ia > ic);
+                    if (gt == up) {
+                        key[a] = kc; key[c] = ka;
+                        sid[a] = ic; sid[c] = ia;
+                        float oa = outd[a];
+                        outd[a] = outd[c];
+                        outd[c] = oa;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+
+    // 6. the k nearest
+    for (int j = threadIdx.x; j < k; j += RR_THREADS) {
+        const bool have = j < nc;
+        ids_out[(int64_t)q * k + j] = have ? (int64_t)sid[j] : -1;
+        dists_out[(int64_t)q * k + j] = have ? outd[j] : CUDART_INF_F;
+    }
+}
+
+}  // namespace
+
+qw_status launch_rerank(const IndexView &ix, const float *Qb, int nb, int k, int cap,
+                        const QueryState &st, int64_t *ids_out, float *dists_out,
+                        cudaStream_t s)
+{
+    int P2 = 2;
+    while (P2 < cap) P2 <<= 1;
+    const size_t smem = (size_t)P2 * (sizeof(double) + 2 * sizeof(float) + sizeof(int32_t) + 1);
+    QW_CUDA_TRY(cudaFuncSetAttribute(rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    // 16-byte row loads need d % 4 == 0 and 16-byte aligned bases
+    const bool vec = (ix.d % 4 == 0) && ((uintptr_t)Qb % 16 == 0) && ((uintptr_t)ix.X % 16 == 0);
+    rerank_kernel<<<nb, RR_THREADS, smem, s>>>(ix.X, ix.d, Qb, k, cap, P2, st.cand, st.nkeep,
+                                               ids_out, dists_out, vec);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
+
+}  // namespace qw

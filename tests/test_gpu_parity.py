@@ -1,0 +1,268 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Bar: bucket ids, anchors, spans, sorted arrays, levels, candidate sets with
+their collision counts, statistics and result ids bit-exact; distances within
+1e-5 relative (the tolerance the path is specified to).
+"""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+DIST_RTOL = 1e-5
+TILE = 32768
+
+
+def _t(x, dev):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+
+
+def _oracle_run(orc, X, Q, A, b, w, k, v, l, c=2):
+    H = orc.hash(X, A, b, w)
+    HQ = orc.hash(Q, A, b, w)
+    idx = orc.build_index(H)
+    ref = orc.query(X, idx, Q, HQ, k=k, v=v, l=l, c=c)
+    return H, HQ, idx, ref
+
+
+def _check_results(ids, dists, ref_ids, ref_dists):
+    assert ids.shape == ref_ids.shape
+    bad = np.nonzero((ids != ref_ids).any(axis=1))[0]
+    assert bad.size == 0, f"ids differ on queries {bad[:10]}: gpu {ids[bad[0]]} oracle {ref_ids[bad[0]]}"
+    fin = np.isfinite(ref_dists)
+    assert np.array_equal(fin, np.isfinite(dists))
+    rel = np.abs(dists[fin].astype(np.float64) - ref_dists[fin]) / np.maximum(ref_dists[fin], 1e-300)
+    assert rel.size == 0 or rel.max() <= DIST_RTOL, f"max rel dist err {rel.max():.3g}"
+
+
+def _check_candidates(cid, ccol, ref_cid, ref_ccol):
+    nq = ref_cid.shape[0]
+    for q in range(nq):
+        keep = ref_cid[q] >= 0
+        order = np.argsort(ref_cid[q][keep], kind="stable")
+        want_ids = ref_cid[q][keep][order]
+        want_col = ref_ccol[q][keep][order]
+        got = cid[q][cid[q] >= 0]
+        assert np.array_equal(got, want_ids), f"candidate set differs on query {q}"
+        assert np.array_equal(ccol[q][: got.size], want_col), f"counts differ on query {q}"
+
+
+def _gpu_workload(qw, dev, X, Q, A, b, *, w, k, v, l, c=2, batch=0, host=False):
+    import torch
+    if host:
+        Xd, Ad, bd = (torch.from_numpy(np.ascontiguousarray(a)) for a in (X, A, b))
+        Qd = torch.from_numpy(np.ascontiguousarray(Q))
+    else:
+        Xd, Qd, Ad, bd = _t(X, dev), _t(Q, dev), _t(A, dev), _t(b, dev)
+    index = qw.Index(Xd, Ad, bd, w=w, c=c, v=v, l=l)
+    ids, dists, st = index.query(Qd, k, batch=batch, stats=True)
+    cid, ccol, st2 = index.candidates(Qd, k, batch=batch)
+    torch.cuda.synchronize()
+    out = dict(ids=ids.cpu().numpy(), dists=dists.cpu().numpy(), stats=st.cpu().numpy(),
+               cid=cid.cpu().numpy(), ccol=ccol.cpu().numpy(), stats2=st2.cpu().numpy(),
+               index=index)
+    return out
+
+
+def _full_parity(orc, qw, dev, X, Q, A, b, *, w, k, v, l=None, c=2, batch=0, host=False):
+    n = X.shape[0]
+    if l is None:
+        l = orc.threshold(A.shape[0], w, c, n, v)
+    H, HQ, oidx, ref = _oracle_run(orc, X, Q, A, b, w, k, v, l, c)
+    g = _gpu_workload(qw, dev, X, Q, A, b, w=w, k=k, v=v, l=l, c=c, batch=batch, host=host)
+    _check_results(g["ids"], g["dists"], ref["ids"], ref["dists"])
+    assert np.array_equal(g["stats"], ref["stats"]), "per-query statistics differ"
+    assert np.array_equal(g["stats2"], ref["stats"])
+    _check_candidates(g["cid"], g["ccol"], ref["cand_ids"], ref["cand_col"])
+    g["index"].free()
+    return ref, g
+
+
+# ---------------------------------------------------------------- a1 + a2: hashing
+@pytest.mark.parametrize("n,d,m,scale", [(10_000, 32, 16, 1.0), (1_007, 33, 5, 3.0),
+                                         (20_000, 128, 64, 1.0), (4_099, 512, 7, 0.5)])
+def test_hash_bit_exact(orc, qwlib, cuda, n, d, m, scale):
+    wl = workloads.make_workload("mix10k_d32", seed=n, n=n, nq=1, d=d, m=m)
+    X = (wl.X * scale).astype(np.float32)
+    want = orc.hash(X, wl.A, wl.b, 4.0)
+    H, fix = qwlib.hash(_t(X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), 4.0)
+    got = H.cpu().numpy()
+    assert np.array_equal(got, want), f"{int((got != want).sum())} bucket ids differ"
+    assert fix >= 0
+
+
+def test_hash_boundary_points_take_fp64(orc, qwlib, cuda):
+    """Points placed within ~1e-6 w of a bucket edge of projection 0 must be
+    re-evaluated in FP64 and still match the FP64 definition."""
+    rng = np.random.default_rng(7)
+    d, m, w = 128, 8, 4.0
+    A = rng.standard_normal((m, d), dtype=np.float32)
+    b = (rng.random(m) * w).astype(np.float32)
+    X0 = rng.standard_normal((4096, d)).astype(np.float64) * 5.0
+    a0 = A[0].astype(np.float64)
+    t0 = X0 @ a0 + float(b[0])
+    target = np.round(t0 / w) * w + rng.uniform(-1e-6, 1e-6, size=t0.shape) * w
+    X = (X0 + np.outer(target - t0, a0) / (a0 @ a0)).astype(np.float32)
+    want = orc.hash(X, A, b, w)
+    H, fix = qwlib.hash(_t(X, cuda), _t(A, cuda), _t(b, cuda), w)
+    assert np.array_equal(H.cpu().numpy(), want)
+    assert fix >= 2000, f"only {fix} entries were recomputed in FP64"
+
+
+# ---------------------------------------------------------------- a3: index build
+@pytest.mark.parametrize("n,d,m", [(10_000, 32, 16), (2 * TILE + 1234, 16, 8), (TILE, 8, 3),
+                                   (1, 4, 2), (TILE + 1, 12, 5)])
+def test_build_matches_oracle(orc, qwlib, cuda, n, d, m):
+    wl = workloads.make_workload("mix10k_d32", seed=3, n=n, nq=1, d=d, m=m,
+                                 n_clusters=min(50, n))
+    H = orc.hash(wl.X, wl.A, wl.b, 4.0)
+    oidx = orc.build_index(H)
+    index = qwlib.Index(_t(wl.X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=4.0, v=100)
+    o, span, eb, ei = index.export()
+    index.free()
+    assert np.array_equal(o, oidx.o)
+    assert np.array_equal(span, oidx.span)
+    for i in range(m):
+        tile = ei[i] // TILE
+        assert np.all(np.diff(tile) >= 0), "entries not grouped by tile"
+        for t in np.unique(tile):
+            sel = tile == t
+            bb, ii = eb[i][sel].astype(np.int64), ei[i][sel].astype(np.int64)
+            comp = bb * (1 << 32) + ii
+            assert np.all(np.diff(comp) > 0), "entries of a tile not sorted by (bid, id)"
+        order = np.lexsort((ei[i], eb[i]))
+        assert np.array_equal(eb[i][order], oidx.sbid[i])
+        assert np.array_equal(ei[i][order], oidx.sid[i])
+
+
+# ---------------------------------------------------------------- a4..a9: workloads
+def test_workload_small_config(orc, qwlib, cuda):
+    wl = workloads.make_workload("mix10k_d32", seed=0)
+    s = wl.spec
+    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=s.w, k=s.k, v=s.v)
+
+
+def test_workload_ragged_tiles_and_batches(orc, qwlib, cuda):
+    """Three index tiles (the last one ragged), small k + v so the truncation
+    and its tie rule run, several query batches with a ragged last batch."""
+    wl = workloads.make_workload("mix10k_d32", seed=11, n=2 * TILE + 777, nq=61, d=24, m=12,
+                                 n_clusters=40)
+    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=7, v=20, batch=13)
+
+
+def test_workload_host_memory(orc, qwlib, cuda):
+    wl = workloads.make_workload("mix10k_d32", seed=5, n=5000, nq=40)
+    s = wl.spec
+    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=s.w, k=s.k, v=s.v, host=True,
+                 batch=16)
+
+
+def test_workload_v_ge_n_is_exact_knn(orc, qwlib, cuda):
+    """v >= n: the k + v bound never stops a query, the last level holds every
+    point, and the answer is the exact k-NN (queries are data rows)."""
+    wl = workloads.make_workload("mix10k_d32", seed=2, n=600, nq=25, n_clusters=6)
+    Q = wl.X[:25].copy()
+    ref, g = _full_parity(orc, qwlib, cuda, wl.X, Q, wl.A, wl.b, w=4.0, k=10, v=600, l=10)
+    bf_ids, bf_d = orc.bruteforce(wl.X, Q, 10)
+    assert np.array_equal(g["ids"], bf_ids)
+    assert np.all(g["stats"][:, 4] == 3)
+
+
+def test_workload_single_projection(orc, qwlib, cuda):
+    """m = 1, l = 1: plain E2LSH bucket lookup with growing radius."""
+    wl = workloads.make_workload("mix10k_d32", seed=4, n=3000, nq=30, m=1)
+    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=5, v=10, l=1)
+
+
+def test_workload_far_queries_and_padding(orc, qwlib, cuda):
+    """Queries far outside the data: many levels, bucket ids below the anchor,
+    fewer than k candidates (padded with -1 / inf)."""
+    wl = workloads.make_workload("mix10k_d32", seed=9, n=2000, nq=12)
+    Q = wl.Q.copy()
+    Q[:6] += 400.0
+    Q[6:] -= 400.0
+    _full_parity(orc, qwlib, cuda, wl.X, Q, wl.A, wl.b, w=4.0, k=10, v=100)
+
+
+def test_workload_duplicates_tie_by_id(orc, qwlib, cuda):
+    """Exact duplicate rows: equal distances are ordered by id."""
+    wl = workloads.make_workload("mix10k_d32", seed=6, n=1500, nq=20)
+    X = np.repeat(wl.X[:300], 5, axis=0)
+    _full_parity(orc, qwlib, cuda, X, wl.Q, wl.A, wl.b, w=4.0, k=12, v=30)
+
+
+def test_workload_tiny_index(orc, qwlib, cuda):
+    X = np.array([[0.5, -1.0, 2.0]], np.float32)
+    A = np.array([[1.0, 0.0, 0.0], [0.3, 0.2, -0.7]], np.float32)
+    b = np.array([0.25, 1.5], np.float32)
+    Q = np.array([[0.4, -1.1, 2.0], [30.0, 30.0, 30.0]], np.float32)
+    _full_parity(orc, qwlib, cuda, X, Q, A, b, w=2.0, k=1, v=3, l=1)
+
+
+def test_workload_k_equals_n(orc, qwlib, cuda):
+    wl = workloads.make_workload("mix10k_d32", seed=8, n=64, nq=5, n_clusters=3)
+    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=64, v=0, l=4)
+
+
+def test_empty_workload(qwlib, cuda):
+    import torch
+    wl = workloads.make_workload("mix10k_d32", seed=1, n=500, nq=1)
+    index = qwlib.Index(_t(wl.X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=4.0)
+    ids, dists = index.query(torch.empty((0, wl.X.shape[1]), dtype=torch.float32, device=cuda), 5)
+    assert ids.shape == (0, 5)
+    index.free()
+
+
+def test_argument_errors(qwlib, cuda):
+    wl = workloads.make_workload("mix10k_d32", seed=1, n=500, nq=4)
+    index = qwlib.Index(_t(wl.X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=4.0)
+    Q = _t(wl.Q, cuda)
+    with pytest.raises(qwlib.QwError) as e:
+        index.query(Q, 0)
+    assert e.value.status == qwlib.QW_ERR_ARG
+    with pytest.raises(qwlib.QwError):
+        index.query(Q, 501)
+    with pytest.raises(qwlib.QwError):
+        index.query(Q, 4000)  # k + v > 4096
+    index.free()
+    with pytest.raises(qwlib.QwError) as e:
+        qwlib.Index(_t(wl.X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=0.0)
+    assert e.value.status == qwlib.QW_ERR_ARG
+    with pytest.raises(qwlib.QwError) as e:
+        qwlib.Index(_t(wl.X * 1e12, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=1e-6)
+    assert e.value.status == qwlib.QW_ERR_RANGE
+
+
+# ---------------------------------------------------------------- full size, sampled
+@pytest.mark.slow
+def test_full_size_sampled(orc, qwlib, cuda):
+    """The benchmarked workload (1M x 128, 64 projections, 10,000 queries,
+    k = 100) run whole on the GPU in the benchmark's launch configuration;
+    the oracle recomputes a seeded sample of queries one by one."""
+    import torch
+    wl = workloads.make_workload("mix1m_d128", seed=0)
+    s = wl.spec
+    l = orc.threshold(s.m, s.w, s.c, s.n, s.v)
+    index = qwlib.Index(_t(wl.X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=s.w, c=s.c, v=s.v, l=l)
+    Qd = _t(wl.Q, cuda)
+    ids, dists, st = index.query(Qd, s.k, stats=True)
+    torch.cuda.synchronize()
+    ids, dists, st = ids.cpu().numpy(), dists.cpu().numpy(), st.cpu().numpy()
+    H = orc.hash(wl.X, wl.A, wl.b, s.w)
+    oidx = orc.build_index(H, sorted_arrays=True)
+    info = index.info
+    assert info.l == l
+    sample = np.random.default_rng(123).choice(s.nq, size=12, replace=False)
+    sample.sort()
+    HQ = orc.hash(wl.Q[sample], wl.A, wl.b, s.w)
+    ref = orc.query(wl.X, oidx, wl.Q[sample], HQ, k=s.k, v=s.v, l=l, c=s.c)
+    _check_results(ids[sample], dists[sample], ref["ids"], ref["dists"])
+    assert np.array_equal(st[sample], ref["stats"])
+    # properties that hold for every query
+    assert np.all((st[:, 4] == 2) | (st[:, 4] == 3))
+    assert np.all(st[:, 3] <= s.k + s.v)
+    assert np.all(np.diff(dists, axis=1)[np.isfinite(dists[:, 1:])] >= 0)
+    index.free()
