@@ -1,0 +1,436 @@
+#!/usr/bin/env python
+"""Benchmark of the LSH query-workload path (qwLSH's method) on GB300.
+
+One step = one call answering the whole synthetic query workload (project the
+queries, collision counting over all levels, candidate selection, distances,
+top-k) against an index already resident in HBM.  The default workload is
+1,000,000 x 128 float32 points (Gaussian mixture of 1,000 clusters), 64
+projections, w = 4, 10,000 queries from 100 clusters, k = 100, v = 100.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle on a bounded
+sample of the same workload instead.  Under torchrun (``--gpus N``) every rank
+answers its own copy of the workload against its own replica of the index
+(the path has no exchange step); the timed region is bracketed by barriers and
+the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "workload queries/sec at recall>=0.9, ratio<=1.05 (plain vs chosen); HBM roofline %"
+UNIT = "queries/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="mix1m_d128")
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--quality-sample", type=int, default=200,
+                   help="queries checked against exact k-NN for recall / ratio")
+    p.add_argument("--cpu-sample", type=int, default=6,
+                   help="queries the CPU oracle answers for the cpu_baseline entry")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--queries", type=int, default=0,
+                   help="override the workload's query count (smaller cases for profiling)")
+    p.add_argument("--batch", type=int, default=0, help="queries per pass (0 = library choice)")
+    p.add_argument("--path", choices=["auto", "cluster", "levels"], default="auto",
+                   help="execution path of the query loop (identical results)")
+    return p.parse_args(argv)
+
+
+# ---------------------------------------------------------------- ranks
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    """Largest value over all ranks (the slowest rank's time)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" \
+        else torch.device("cpu")
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        return parse_clock_csv(out)
+
+
+def parse_clock_csv(text: str):
+    """Summary of nvidia-smi samples: median SM clock, max clock, and every
+    throttle reason seen active."""
+    rows = [r for r in csv.reader(io.StringIO(text)) if len(r) >= 9]
+    if not rows:
+        return None
+
+    def num(x):
+        try:
+            return float(x)
+        except ValueError:
+            return None
+
+    sm = [v for v in (num(r[1]) for r in rows) if v is not None]
+    mx = [v for v in (num(r[2]) for r in rows) if v is not None]
+    names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+    reasons = sorted({nm for r in rows for nm, v in zip(names, r[5:9])
+                      if v.strip().lower() == "active"})
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_uuid(torch):
+    try:
+        u = torch.cuda.get_device_properties(torch.cuda.current_device()).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
+    the current kernel source (the summary records the source's sha256)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_1907_11803_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(src)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(src, f), "rb") as fh:
+                h.update(fh.read())
+    sha = h.hexdigest()[:16]
+    try:
+        with open(path) as fh:
+            for line in fh:
+                parts = line.split()
+                if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel \
+                        and parts[1] == workload and parts[2] == sha:
+                    return float(parts[3])
+    except OSError:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------- quality
+def exact_knn_gpu(X, Qs, k):
+    """Exact k-NN of a query sample in float64 on the GPU (measurement only)."""
+    import torch
+    Xd = X.double()
+    xn = (Xd * Xd).sum(1)
+    ids, dists = [], []
+    for s in range(0, Qs.shape[0], 32):
+        q = Qs[s:s + 32].double()
+        d2 = xn[None, :] - 2.0 * (q @ Xd.T) + (q * q).sum(1)[:, None]
+        d2.clamp_(min=0)
+        v, i = torch.topk(d2, k, dim=1, largest=False, sorted=True)
+        ids.append(i)
+        dists.append(v.sqrt())
+    del Xd
+    return torch.cat(ids), torch.cat(dists)
+
+
+def recall_ratio(ids, dists, tids, tdists):
+    import torch
+    k = ids.shape[1]
+    hit = torch.zeros(ids.shape[0], dtype=torch.float64, device=ids.device)
+    for j in range(k):
+        hit += (tids == ids[:, j:j + 1]).any(dim=1).double()
+    recall = float((hit / k).mean())
+    ok = (ids >= 0) & (tdists > 0)
+    ratio = float((dists.double()[ok] / tdists[ok]).mean()) if bool(ok.any()) else float("nan")
+    return recall, ratio
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+def oracle_sample(wl, l, n_queries, seed=1):
+    """Time the oracle's query procedure on a seeded sample of the workload's
+    queries (the index build is excluded, as on the GPU).  Returns
+    (queries/s, seconds, sample size)."""
+    import numpy as np
+    import oracle
+    orc = oracle.get()
+    s = wl.spec
+    H = orc.hash(wl.X, wl.A, wl.b, s.w)
+    idx = orc.build_index(H, sorted_arrays=False)
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(s.nq, size=min(n_queries, s.nq), replace=False))
+    Qs = wl.Q[pick]
+    HQ = orc.hash(Qs, wl.A, wl.b, s.w)
+    t0 = time.perf_counter()
+    orc.query(wl.X, idx, Qs, HQ, k=s.k, v=s.v, l=l, c=s.c, want_candidates=False,
+              want_stats=False)
+    dt = time.perf_counter() - t0
+    return len(pick) / dt, dt, len(pick), (orc, idx)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1907_11803_gb300 as qw
+    import workloads
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    nq = args.queries or None
+    wl = workloads.make_workload(args.workload, seed=args.seed, nq=nq)
+    if world > 1 and rank > 0:
+        # each rank answers its own seeded query workload against the same data
+        other = workloads.make_workload(args.workload, seed=args.seed + 1000 * rank, nq=nq)
+        wl.Q = other.Q
+    s = wl.spec
+    X = torch.from_numpy(wl.X).to(dev)
+    A = torch.from_numpy(wl.A).to(dev)
+    b = torch.from_numpy(wl.b).to(dev)
+    Q = torch.from_numpy(wl.Q).to(dev)
+    index = qw.Index(X, A, b, w=s.w, c=s.c, v=s.v)
+    ids = torch.empty((s.nq, s.k), dtype=torch.int64, device=dev)
+    dists = torch.empty((s.nq, s.k), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        index.query(Q, s.k, out=(ids, dists), batch=args.batch, path=args.path)
+    torch.cuda.synchronize()
+    _, _, st = index.query(Q, s.k, stats=True, batch=args.batch, path=args.path)
+    st = st.cpu().numpy()
+    index.profile(reset=True)
+
+    clocks = ClockSampler(gpu_uuid(torch))
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        index.query(Q, s.k, out=(ids, dists), profile=True, batch=args.batch, path=args.path)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = index.profile(reset=True)
+    ms_max = max_over_ranks(ms, world)
+    value = world * s.nq * args.steps / (ms_max / 1e3)
+
+    # end to end through the public API: pinned host queries in, host results out
+    Qh = torch.from_numpy(wl.Q).pin_memory()
+    ids_h = torch.empty((s.nq, s.k), dtype=torch.int64).pin_memory()
+    dists_h = torch.empty((s.nq, s.k), dtype=torch.float32).pin_memory()
+    index.query(Qh, s.k, out=(ids_h, dists_h), batch=args.batch, path=args.path)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        index.query(Qh, s.k, out=(ids_h, dists_h), batch=args.batch, path=args.path)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": world * s.nq * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(Qh.numel() * 4),
+           "d2h_bytes_per_step": int(ids_h.numel() * 8 + dists_h.numel() * 4)}
+
+    # quality on a seeded query sample (exact k-NN in float64)
+    rng = np.random.default_rng(12345)
+    pick = torch.from_numpy(np.sort(rng.choice(s.nq, size=min(args.quality_sample, s.nq),
+                                               replace=False))).to(dev)
+    tids, tdists = exact_knn_gpu(X, Q[pick], s.k)
+    recall, ratio = recall_ratio(ids[pick], dists[pick], tids, tdists)
+
+    # roofline of the dominant kernel and of the candidate-distance kernel
+    peaks, peak_kind = measured_peaks()
+    steps = args.steps
+    hbm = float(peaks["hbm_gbs"])
+    entries = float(st[:, 5].sum())      # index entries scanned per step (incremental flanks)
+    count_bytes = entries * 2.0          # 16-bit ids
+    dom = "cluster" if prof["ms"]["cluster"] >= prof["ms"]["level"] else "level"
+    dom_name = {"cluster": "cluster_query_kernel (all levels of collision counting, persistent)",
+                "level": "level_kernel (bucket-range search + collision counting)"}[dom]
+    dom_launches = prof["timed_launches"][dom] / steps
+    dom_ms = prof["ms"][dom] / steps
+    per_launch_bytes = count_bytes / max(dom_launches, 1)
+    per_launch_s = (dom_ms / 1e3) / max(dom_launches, 1)
+    achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
+    kept = float(st[:, 3].sum())
+    rr_bytes = kept * s.d * 4 + s.nq * s.d * 4 + s.nq * s.k * 12
+    rr_launches = prof["timed_launches"]["rerank"] / steps
+    rr_ms = prof["ms"]["rerank"] / steps
+    rr_achieved = (rr_bytes / max(rr_launches, 1)) / ((rr_ms / 1e3) / max(rr_launches, 1)) / 1e9 \
+        if rr_ms > 0 else 0.0
+    kname = "cluster_query_kernel" if dom == "cluster" else "level_kernel"
+    roofline = {"kernel": dom_name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+                "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": ncu_traffic(kname, args.workload), "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": per_launch_bytes,
+                "avg_launch_ms": per_launch_s * 1e3, "launches_per_step": dom_launches,
+                "share_of_step": round(dom_ms / (ms / steps), 4)}
+    roofline_gather = {"kernel": "rerank_kernel (candidate gather + L2 + top-k)", "bound": "hbm",
+                       "achieved": round(rr_achieved, 1), "peak": hbm,
+                       "frac": round(rr_achieved / hbm, 4), "unit": "GB/s",
+                       "traffic": ncu_traffic("rerank_kernel", args.workload),
+                       "algorithmic_bytes_per_launch": rr_bytes / max(rr_launches, 1),
+                       "avg_launch_ms": rr_ms / max(rr_launches, 1)}
+    launches = int(sum(prof["launches"].values()))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        qps, dt, nsamp, _ = oracle_sample(wl, index.l, args.cpu_sample)
+        cpu = {"value": qps, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nsamp} seeded queries of the same workload, query procedure only "
+                         f"({dt:.1f} s, single thread, FP64)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n": s.n, "d": s.d, "m": s.m, "w": s.w, "c": s.c,
+                   "k": s.k, "v": s.v, "l": index.l, "queries_per_gpu": s.nq,
+                   "query_clusters": s.query_clusters, "seed": args.seed,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "path": args.path,
+                   "l2": "inputs larger than L2 (index %.2f GB + data %.2f GB + counters)"
+                         % (index.info.device_bytes / 1e9 - s.n * s.d * 4 / 1e9,
+                            s.n * s.d * 4 / 1e9)},
+        "quality": {"recall": round(recall, 4), "ratio": round(ratio, 5),
+                    "sample": int(pick.numel()), "meets_target": recall >= 0.9 and ratio <= 1.05},
+        "roofline": roofline, "roofline_gather": roofline_gather,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk,
+        "stats": {"levels_median": float(np.median(st[:, 0])),
+                  "entries_scanned_per_query": float(np.mean(st[:, 5])),
+                  "kernel_ms_per_step": {k2: round(v2 / steps, 3) for k2, v2 in prof["ms"].items()}},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    index.free()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    import workloads
+    wl = workloads.make_workload(args.workload, seed=args.seed, nq=args.queries or None)
+    s = wl.spec
+    l = oracle.get().threshold(s.m, s.w, s.c, s.n, s.v)
+    per_step = max(1, args.cpu_sample // 2)
+    qps0, _, _, (orc, idx) = oracle_sample(wl, l, per_step, seed=0)
+    rng = np.random.default_rng(99)
+    times = []
+    for step in range(args.warmup + args.steps):
+        pick = np.sort(rng.choice(s.nq, size=per_step, replace=False))
+        Qs = wl.Q[pick]
+        HQ = orc.hash(Qs, wl.A, wl.b, s.w)
+        t0 = time.perf_counter()
+        orc.query(wl.X, idx, Qs, HQ, k=s.k, v=s.v, l=l, c=s.c, want_candidates=False,
+                  want_stats=False)
+        if step >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = per_step * len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total / len(times) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": s.n, "d": s.d, "m": s.m, "k": s.k,
+                       "v": s.v, "l": l},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} seeded queries per step, query procedure "
+                                       "only, single thread, FP64"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.steps < 1 or args.warmup < 0:
+        raise SystemExit("--steps must be >= 1 and --warmup >= 0")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -68,6 +68,7 @@ typedef int32_t qw_status;
 
 /* Largest supported values. */
 #define QW_MAX_M 127          /* projections per index (collision counts are 7-bit) */
+#define QW_MAX_CLUSTER_TILES 96  /* index tiles the cluster path can hold */
 #define QW_MAX_CAND 4096      /* k + v */
 
 typedef struct qw_index qw_index;
@@ -86,8 +87,45 @@ typedef struct {
 /* Per-workload options.  Zero-initialise; unknown non-zero fields are rejected. */
 typedef struct {
     int32_t batch;        /* queries per pass over the index; 0 = library choice */
-    int32_t reserved[7];  /* must be zero */
+    int32_t profile;      /* non-zero: time every kernel launch with CUDA events on the call's
+                             stream and add the times to the index's profile (see
+                             qw_index_profile); the call then waits for the stream */
+    int32_t path;         /* QW_PATH_AUTO, QW_PATH_CLUSTER or QW_PATH_LEVELS (below) */
+    int32_t clusters;     /* cluster path: most clusters resident at once; 0 = all that fit */
+    int32_t reserved[4];  /* must be zero */
 } qw_query_params;
+
+/* Execution paths of the query loop (identical results):
+ * QW_PATH_LEVELS: one launch per level over (index tile, query) pairs, collision
+ *   counters in device memory between levels; any index size.
+ * QW_PATH_CLUSTER: one persistent launch of thread-block clusters; a cluster
+ *   answers one query at a time with its counters in shared memory for all
+ *   levels and pulls the next query from a work queue; indexes of up to
+ *   96 tiles (3,145,728 points).
+ * QW_PATH_AUTO: the cluster path when the index fits, else the level path. */
+#define QW_PATH_AUTO 0
+#define QW_PATH_CLUSTER 1
+#define QW_PATH_LEVELS 2
+
+/* Kernel classes of the query path, for qw_profile. */
+#define QW_K_PROJECT 0   /* query projection + FP64 boundary pass */
+#define QW_K_SETUP 1     /* per-query state */
+#define QW_K_LEVEL 2     /* bucket-range search + collision counting, one launch per level */
+#define QW_K_DECIDE 3    /* per-level termination test */
+#define QW_K_SELECT 4    /* candidate selection under the k + v bound */
+#define QW_K_RERANK 5    /* candidate distances + top-k */
+#define QW_K_CLUSTER 6   /* cluster path: every level, the stop test and the selection of a
+                            query in one persistent launch */
+#define QW_K_COUNT 7
+
+/* Launch counts and (profile mode) summed kernel times of qw_run_workload /
+ * qw_workload_candidates calls on one index since the last reset. */
+typedef struct {
+    int64_t launches[QW_K_COUNT];  /* kernels launched, per class (always counted) */
+    double ms[QW_K_COUNT];         /* summed CUDA-event durations, per class (profile mode) */
+    int64_t timed_launches[QW_K_COUNT];  /* launches included in ms[] */
+    int64_t queries;               /* queries answered */
+} qw_profile;
 
 typedef struct {
     int64_t n;             /* data vectors */
@@ -181,6 +219,10 @@ qw_status qw_run_workload(qw_index *index, const float *queries, int64_t nq, int
 qw_status qw_workload_candidates(qw_index *index, const float *queries, int64_t nq, int32_t k,
                                  const qw_query_params *qparams, int64_t *cand_ids,
                                  int32_t *cand_col, int64_t *stats, int32_t mem, void *stream);
+
+/* Copy the index's profile counters into *out (host); reset them afterwards
+ * when `reset` is non-zero. */
+qw_status qw_index_profile(qw_index *index, qw_profile *out, int32_t reset);
 
 /* Copy index metadata into *info (host). */
 qw_status qw_index_get_info(const qw_index *index, qw_index_info *info);

@@ -32,7 +32,7 @@ STAT_FIELDS = ("levels", "final_R", "n_cand_raw", "n_cand", "term", "scanned_las
 # Every symbol include/qwlsh.h declares.
 EXPORTED = ("qw_version", "qw_last_error", "qw_collision_probability",
             "qw_collision_threshold", "qw_hash", "qw_build_index", "qw_run_workload",
-            "qw_workload_candidates", "qw_index_get_info", "qw_index_export", "qw_index_free")
+            "qw_workload_candidates", "qw_index_profile", "qw_index_get_info", "qw_index_export", "qw_index_free")
 
 
 class qw_index_params(C.Structure):
@@ -41,7 +41,20 @@ class qw_index_params(C.Structure):
 
 
 class qw_query_params(C.Structure):
-    _fields_ = [("batch", C.c_int32), ("reserved", C.c_int32 * 7)]
+    _fields_ = [("batch", C.c_int32), ("profile", C.c_int32), ("path", C.c_int32),
+                ("clusters", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+
+QW_PATH_AUTO, QW_PATH_CLUSTER, QW_PATH_LEVELS = 0, 1, 2
+PATHS = {"auto": QW_PATH_AUTO, "cluster": QW_PATH_CLUSTER, "levels": QW_PATH_LEVELS}
+QW_K_PROJECT, QW_K_SETUP, QW_K_LEVEL, QW_K_DECIDE, QW_K_SELECT, QW_K_RERANK, QW_K_CLUSTER = range(7)
+QW_K_COUNT = 7
+KERNEL_CLASSES = ("project", "setup", "level", "decide", "select", "rerank", "cluster")
+
+
+class qw_profile(C.Structure):
+    _fields_ = [("launches", C.c_int64 * QW_K_COUNT), ("ms", C.c_double * QW_K_COUNT),
+                ("timed_launches", C.c_int64 * QW_K_COUNT), ("queries", C.c_int64)]
 
 
 class qw_index_info(C.Structure):
@@ -92,6 +105,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.qw_workload_candidates.restype = C.c_int32
     L.qw_workload_candidates.argtypes = [vp, vp, C.c_int64, C.c_int32, C.POINTER(qw_query_params),
                                          vp, vp, vp, C.c_int32, vp]
+    L.qw_index_profile.restype = C.c_int32
+    L.qw_index_profile.argtypes = [vp, C.POINTER(qw_profile), C.c_int32]
     L.qw_index_get_info.restype = C.c_int32
     L.qw_index_get_info.argtypes = [vp, C.POINTER(qw_index_info)]
     L.qw_index_export.restype = C.c_int32
@@ -147,6 +162,12 @@ def qw_workload_candidates(index: int, queries: int, nq: int, k: int, qparams: q
                            cand_ids: int, cand_col: int, stats: int, mem: int, stream: int = 0):
     _check(load().qw_workload_candidates(index, queries, nq, k, C.byref(qparams), cand_ids,
                                          cand_col or None, stats or None, mem, stream or None))
+
+
+def qw_index_profile(index: int, reset: bool = False) -> qw_profile:
+    prof = qw_profile()
+    _check(load().qw_index_profile(index, C.byref(prof), 1 if reset else 0))
+    return prof
 
 
 def qw_index_get_info(index: int) -> qw_index_info:
@@ -243,7 +264,17 @@ class Index:
     def v(self) -> int:
         return int(self.info.v)
 
-    def query(self, Q, k: int, *, batch: int = 0, stats: bool = False, out=None):
+    def profile(self, reset: bool = False) -> dict:
+        """Launch counts and (profile mode) summed kernel milliseconds per kernel
+        class since the last reset."""
+        p = qw_index_profile(self._h, reset)
+        return {"launches": dict(zip(KERNEL_CLASSES, list(p.launches))),
+                "ms": dict(zip(KERNEL_CLASSES, list(p.ms))),
+                "timed_launches": dict(zip(KERNEL_CLASSES, list(p.timed_launches))),
+                "queries": int(p.queries)}
+
+    def query(self, Q, k: int, *, batch: int = 0, stats: bool = False, out=None,
+              profile: bool = False, path: str = "auto", clusters: int = 0):
         """Top-k of every query row.  Returns (ids int64 nq x k, dists float32
         nq x k[, stats int64 nq x QW_NSTAT]) on Q's device (host tensors in,
         host tensors out).  ``out`` may give preallocated (ids, dists[, stats])."""
@@ -262,12 +293,13 @@ class Index:
             st = (torch.empty((nq, QW_NSTAT), dtype=torch.int64, device=Q.device, pin_memory=pin)
                   if stats else None)
         mem = _mem_of(Q, ids, dists, st)
-        qp = qw_query_params(batch=int(batch))
+        qp = qw_query_params(batch=int(batch), profile=1 if profile else 0, path=PATHS[path],
+                             clusters=int(clusters))
         qw_run_workload(self._h, Q.data_ptr(), nq, int(k), qp, ids.data_ptr(), dists.data_ptr(),
                         st.data_ptr() if st is not None else 0, mem, _stream_of(Q))
         return (ids, dists, st) if stats else (ids, dists)
 
-    def candidates(self, Q, k: int, *, batch: int = 0):
+    def candidates(self, Q, k: int, *, batch: int = 0, path: str = "auto"):
         """Kept candidates per query (ascending ids, -1 padded) with their
         collision counts, and the per-query statistics, on Q's device."""
         torch = _torch()
@@ -278,7 +310,7 @@ class Index:
         ccol = torch.empty((nq, cap), dtype=torch.int32, device=Q.device)
         st = torch.empty((nq, QW_NSTAT), dtype=torch.int64, device=Q.device)
         mem = _mem_of(Q, cid, ccol, st)
-        qp = qw_query_params(batch=int(batch))
+        qp = qw_query_params(batch=int(batch), path=PATHS[path])
         qw_workload_candidates(self._h, Q.data_ptr(), nq, int(k), qp, cid.data_ptr(),
                                ccol.data_ptr(), st.data_ptr(), mem, _stream_of(Q))
         return cid, ccol, st

@@ -71,6 +71,8 @@ struct qw_index {
     // workspace for queries (grow-only)
     DevBuf w_q, w_hq, w_state, w_counters, w_cand, w_out, w_err;
     int64_t device_bytes = 0;
+    qw_profile prof{};
+    std::vector<cudaEvent_t> event_pool;
 
     IndexView view() const
     {
@@ -88,6 +90,61 @@ struct qw_index {
         v.dir_start = dir_start.as<int64_t>();
         v.dir_cnt = dir_cnt.as<int32_t>();
         return v;
+    }
+};
+
+// Launch accounting and, in profile mode, CUDA-event timing of every launch
+// on the call's stream.
+struct LaunchTimer {
+    qw_index *ix;
+    cudaStream_t s;
+    bool on;
+    size_t next = 0;
+    struct Rec {
+        int cls, n;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+
+    qw_status event(cudaEvent_t *e)
+    {
+        if (next == ix->event_pool.size()) {
+            cudaEvent_t ne;
+            QW_CUDA_TRY(cudaEventCreate(&ne));
+            ix->event_pool.push_back(ne);
+        }
+        *e = ix->event_pool[next++];
+        return QW_OK;
+    }
+
+    template <class F> qw_status run(int cls, int nlaunch, F &&f)
+    {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (on) {
+            QW_TRY(event(&a));
+            QW_TRY(event(&b));
+            QW_CUDA_TRY(cudaEventRecord(a, s));
+        }
+        QW_TRY(f());
+        ix->prof.launches[cls] += nlaunch;
+        if (on) {
+            QW_CUDA_TRY(cudaEventRecord(b, s));
+            recs.push_back({cls, nlaunch, a, b});
+        }
+        return QW_OK;
+    }
+
+    qw_status finish()
+    {
+        if (!on) return QW_OK;
+        QW_CUDA_TRY(cudaStreamSynchronize(s));
+        for (const Rec &r : recs) {
+            float ms = 0.0f;
+            QW_CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
+            ix->prof.ms[r.cls] += ms;
+            ix->prof.timed_launches[r.cls] += r.n;
+        }
+        return QW_OK;
     }
 };
 
@@ -228,7 +285,8 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
             total += std::min<int64_t>(len, (int64_t)h_span[i] + 1);
         }
     }
-    QW_TRY(ix->lid.ensure((size_t)m * n * sizeof(uint16_t)));
+    QW_TRY(ix->lid.ensure((size_t)m * nT * kTile * sizeof(uint16_t)));
+    QW_CUDA_TRY(cudaMemsetAsync(ix->lid.p, 0, ix->lid.bytes, s));
     QW_TRY(ix->dir_bid.ensure((size_t)total * sizeof(int32_t)));
     QW_TRY(ix->dir_off.ensure((size_t)total * sizeof(int32_t)));
     QW_TRY(ix->dir_start.ensure((size_t)m * nT * sizeof(int64_t)));
@@ -295,10 +353,18 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     const int m = ix->m, d = ix->d;
     const int cap = k + ix->v;
     const int64_t wpq_bytes = (int64_t)ix->nT * kTile;  // counter bytes per query
+    const int path = qp ? qp->path : QW_PATH_AUTO;
+    int csize = 0, tpc = 0;
+    const bool fits = cluster_path_fits(ix->view(), &csize, &tpc);
+    if (path == QW_PATH_CLUSTER && !fits) {
+        set_error("qw_run_workload: the index has more tiles than the cluster path can hold");
+        return QW_ERR_ARG;
+    }
+    const bool use_cluster = fits && path != QW_PATH_LEVELS;
     int64_t B = qp && qp->batch > 0 ? qp->batch : 0;
     if (B == 0) {
         const int64_t budget = (int64_t)2 << 30;  // counters of one batch
-        B = std::max<int64_t>(1, budget / wpq_bytes);
+        B = use_cluster ? (int64_t)65535 : std::max<int64_t>(1, budget / wpq_bytes);
     }
     B = std::min<int64_t>(B, std::max<int64_t>(nq, 1));
     B = std::min<int64_t>(B, 65535);
@@ -306,10 +372,11 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
 
     // workspace
     QW_TRY(ix->w_hq.ensure((size_t)B * m * sizeof(int32_t)));
-    QW_TRY(ix->w_counters.ensure((size_t)B * wpq_bytes));
+    if (!use_cluster) QW_TRY(ix->w_counters.ensure((size_t)B * wpq_bytes));
     QW_TRY(ix->w_cand.ensure((size_t)B * cap * 2 * sizeof(int32_t)));
     QW_TRY(ix->w_err.ensure(64));
-    const size_t st_bytes = (size_t)B * m * 8 + (size_t)B * 8 * 16 + 64;
+    const size_t plan_ints = (size_t)B * ix->nT * (kHistBins + 2) + (size_t)B * 2;
+    const size_t st_bytes = (size_t)B * m * 8 + (size_t)B * 8 * 16 + plan_ints * 4 + 256;
     QW_TRY(ix->w_state.ensure(st_bytes));
     // per-batch output staging for host mode: ids, dists, stats, candidates
     const size_t out_ids = (size_t)B * k * sizeof(int64_t);
@@ -341,6 +408,9 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         st.levels = reinterpret_cast<int32_t *>(take((size_t)B * 4));
         st.nkeep = reinterpret_cast<int32_t *>(take((size_t)B * 4));
         st.max_top = reinterpret_cast<unsigned long long *>(take(8));
+        st.tile_hist = reinterpret_cast<int32_t *>(take((size_t)B * ix->nT * kHistBins * 4));
+        st.tile_plan = reinterpret_cast<int32_t *>(take((size_t)B * ix->nT * 2 * 4));
+        st.qplan = reinterpret_cast<int32_t *>(take((size_t)B * 2 * 4));
         if ((size_t)(p - ix->w_state.as<char>()) > ix->w_state.bytes) {
             set_error("internal: query state workspace too small");
             return QW_ERR_CUDA;
@@ -351,6 +421,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     st.cand_col = st.cand + (size_t)B * cap;
     int *err = ix->w_err.as<int>();
     const IndexView view = ix->view();
+    LaunchTimer tm{ix, s, qp && qp->profile != 0};
 
     for (int64_t b0 = 0; b0 < nq; b0 += B) {
         const int nb = (int)std::min<int64_t>(B, nq - b0);
@@ -380,9 +451,32 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             if (want_cand && cand_col) ccol_b = cand_col + b0 * cap;
         }
         QW_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-        QW_TRY(launch_hash(Qb, nb, d, ix->A.as<float>(), ix->b.as<float>(), m, ix->w,
-                           ix->w_hq.as<int32_t>(), m, 1, err, nullptr, s));
-        QW_TRY(launch_query_setup(view, ix->w_hq.as<int32_t>(), nb, st, s));
+        QW_TRY(tm.run(QW_K_PROJECT, 2, [&] {
+            return launch_hash(Qb, nb, d, ix->A.as<float>(), ix->b.as<float>(), m, ix->w,
+                               ix->w_hq.as<int32_t>(), m, 1, err, nullptr, s);
+        }));
+        if (use_cluster) {
+            int used = 0;
+            QW_CUDA_TRY(cudaMemsetAsync(st.nkeep, 0, (size_t)nb * sizeof(int32_t), s));
+            QW_TRY(tm.run(QW_K_CLUSTER, 1, [&] {
+                return launch_cluster_query(view, ix->w_hq.as<int32_t>(), nb, ix->l, ix->c, cap,
+                                            csize, tpc, qp ? qp->clusters : 0, st,
+                                            reinterpret_cast<int *>(ix->w_err.as<char>() + 32),
+                                            stats_b, err, s, &used);
+            }));
+            int h_err = 0;
+            QW_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            QW_CUDA_TRY(cudaStreamSynchronize(s));
+            if (h_err & 2) {
+                set_error("qw_run_workload: a query bucket id falls outside int32");
+                return QW_ERR_RANGE;
+            }
+            if (h_err & 4) {
+                set_error("qw_run_workload: a staged-copy wait in the cluster kernel gave up");
+                return QW_ERR_TIMEOUT;
+            }
+        } else {
+        QW_TRY(tm.run(QW_K_SETUP, 1, [&] { return launch_query_setup(view, ix->w_hq.as<int32_t>(), nb, st, s); }));
         unsigned long long max_top = 0;
         int h_err = 0;
         QW_CUDA_TRY(cudaMemcpyAsync(&max_top, st.max_top, sizeof(max_top), cudaMemcpyDeviceToHost, s));
@@ -395,8 +489,8 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         // levels 0..L where c^L > max_top: afterwards every query has stopped
         int64_t R = 1, Rp = 1;
         for (int level = 0;; ++level) {
-            QW_TRY(launch_level(view, nb, level, R, Rp, ix->l, st, s));
-            QW_TRY(launch_decide(nb, level, R, cap, st, s));
+            QW_TRY(tm.run(QW_K_LEVEL, 1, [&] { return launch_level(view, nb, level, R, Rp, ix->l, st, s); }));
+            QW_TRY(tm.run(QW_K_DECIDE, 1, [&] { return launch_decide(nb, level, R, cap, st, s); }));
             if ((unsigned long long)R > max_top) break;
             if (level > 62) {
                 set_error("qw_run_workload: level limit reached");
@@ -405,9 +499,12 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             Rp = R;
             R *= ix->c;
         }
-        QW_TRY(launch_collect(view, nb, ix->l, cap, st, stats_b, s));
-        if (want_cand) QW_TRY(launch_candidates_out(st, nb, cap, cids_b, ccol_b, s));
-        if (ids) QW_TRY(launch_rerank(view, Qb, nb, k, cap, st, ids_b, dists_b, s));
+        QW_TRY(tm.run(QW_K_SELECT, 2, [&] { return launch_collect(view, nb, ix->l, cap, st, stats_b, s); }));
+        }
+        if (want_cand)
+            QW_TRY(tm.run(QW_K_SELECT, 1, [&] { return launch_candidates_out(st, nb, cap, cids_b, ccol_b, s); }));
+        if (ids)
+            QW_TRY(tm.run(QW_K_RERANK, 1, [&] { return launch_rerank(view, Qb, nb, k, cap, st, ids_b, dists_b, s); }));
         if (host) {
             if (ids) {
                 QW_CUDA_TRY(cudaMemcpyAsync(ids + b0 * k, ids_b, (size_t)nb * k * sizeof(int64_t),
@@ -431,6 +528,8 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         }
     }
     if (host) QW_CUDA_TRY(cudaStreamSynchronize(s));
+    QW_TRY(tm.finish());
+    ix->prof.queries += nq;
     return QW_OK;
 }
 
@@ -445,7 +544,10 @@ static qw_status check_workload_args(const qw_index *ix, const float *queries, i
     if ((int64_t)k + ix->v > QW_MAX_CAND) return arg_error("qw_run_workload: k + v exceeds 4096");
     if (qp) {
         if (qp->batch < 0) return arg_error("qw_run_workload: batch < 0");
-        for (int r = 0; r < 7; ++r)
+        if (qp->path < QW_PATH_AUTO || qp->path > QW_PATH_LEVELS)
+            return arg_error("qw_run_workload: unknown path");
+        if (qp->clusters < 0) return arg_error("qw_run_workload: clusters < 0");
+        for (int r = 0; r < 4; ++r)
             if (qp->reserved[r] != 0) return arg_error("qw_run_workload: reserved field set");
     }
     return QW_OK;
@@ -473,6 +575,15 @@ qw_status qw_workload_candidates(qw_index *ix, const float *queries, int64_t nq,
     if (nq == 0) return QW_OK;
     return run_impl(ix, queries, nq, k, qp, nullptr, nullptr, stats, cand_ids, cand_col, mem,
                     (cudaStream_t)stream);
+}
+
+qw_status qw_index_profile(qw_index *ix, qw_profile *out, int32_t reset)
+{
+    clear_error();
+    if (!ix || !out) return arg_error("qw_index_profile: null pointer");
+    *out = ix->prof;
+    if (reset) ix->prof = qw_profile{};
+    return QW_OK;
 }
 
 qw_status qw_index_get_info(const qw_index *ix, qw_index_info *info)
@@ -535,6 +646,7 @@ void qw_index_free(qw_index *ix)
                       &ix->dir_off, &ix->dir_start, &ix->dir_cnt, &ix->w_q, &ix->w_hq,
                       &ix->w_state, &ix->w_counters, &ix->w_cand, &ix->w_out, &ix->w_err};
     for (DevBuf *bb : bufs) bb->release();
+    for (cudaEvent_t e : ix->event_pool) cudaEventDestroy(e);
     delete ix;
 }
 

@@ -3,8 +3,10 @@
 // structure is a flat sorted array with a directory instead of a B-tree).
 //
 // Layout, per projection i (all device memory):
-//   lid[i * n + p]   16-bit id within its tile (id = tile * kTile + lid),
-//                    entries grouped by tile, sorted by (bid, id) inside a tile;
+//   lid[i * nT * kTile + t * kTile + p]
+//                    16-bit id within its tile (id = t * kTile + lid); every
+//                    tile owns kTile slots (the last one is padded), entries
+//                    of a tile sorted by (bid, id);
 //   dir_bid / dir_off at dir_start[i * nT + t]: the distinct bucket ids of
 //                    tile t and the offset of the first entry of each, so a
 //                    bucket-id range maps to an entry range by two searches.
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(SORT_THREADS) tile_sort_kernel(
             __syncthreads();
         }
     }
-    uint16_t *lo = lid_out + (int64_t)i * n + base;
+    uint16_t *lo = lid_out + (int64_t)i * nT * kTile + base;
     for (int j = threadIdx.x; j < len; j += SORT_THREADS) lo[j] = sl[j];
 
     // Directory: each thread owns a contiguous run of entries; a block scan
@@ -146,6 +148,7 @@ __global__ void export_kernel(const uint16_t *__restrict__ lid, const int32_t *_
     const int32_t *ub = dir_bid + dir_start[(int64_t)i * nT + t];
     const int32_t *uo = dir_off + dir_start[(int64_t)i * nT + t];
     const int cnt = dir_cnt[(int64_t)i * nT + t];
+    const uint16_t *tl = lid + (int64_t)i * nT * kTile + base;
     for (int p = threadIdx.x; p < len; p += blockDim.x) {
         // last directory slot whose offset is <= p
         int lo = 0, hi = cnt - 1;
@@ -155,7 +158,7 @@ __global__ void export_kernel(const uint16_t *__restrict__ lid, const int32_t *_
         }
         int64_t e = (int64_t)i * n + base + p;
         if (entry_bid) entry_bid[e] = ub[lo];
-        if (entry_id) entry_id[e] = (int32_t)(base + lid[e]);
+        if (entry_id) entry_id[e] = (int32_t)(base + tl[p]);
     }
 }
 

@@ -24,6 +24,10 @@ constexpr int kTileShift = 15;
 // bucket boundary to trust; the FP64 pass replaces every such entry.
 constexpr int32_t kNeedsFp64 = INT32_MIN;
 
+// Per-(query, tile) candidate profile: [0] previous-level candidates,
+// [1 + c] other candidates with collision count c (c <= QW_MAX_M).
+constexpr int kHistBins = QW_MAX_M + 2;
+
 // Thread-local error text behind qw_last_error().
 void set_error(const std::string &msg);
 void clear_error();
@@ -97,7 +101,7 @@ struct QueryState {
     int32_t *active;        // nb
     int32_t *ncand;         // nb: |C_R| after the last finished level
     int32_t *nprev;         // nb
-    int32_t *cross;         // nb: candidates gained in the running level
+    int32_t *cross;         // nb: candidates of the running level, summed over tiles
     int32_t *term;          // nb
     int32_t *levels;        // nb
     int64_t *finalR;        // nb
@@ -109,6 +113,9 @@ struct QueryState {
     uint32_t *counters;     // nb x (nT * kTile / 4)
     int32_t *cand;          // nb x cap
     int32_t *cand_col;      // nb x cap
+    int32_t *tile_hist;     // nb x nT x kHistBins
+    int32_t *tile_plan;     // nb x nT x 2: first output slot, count-c* ids before the tile
+    int32_t *qplan;         // nb x 2: c*, how many count-c* ids are kept
 };
 
 qw_status launch_query_setup(const IndexView &ix, const int32_t *HQ, int nb, QueryState &st,
@@ -118,6 +125,11 @@ qw_status launch_level(const IndexView &ix, int nb, int level, int64_t R, int64_
 qw_status launch_decide(int nb, int level, int64_t R, int cap, QueryState &st, cudaStream_t s);
 qw_status launch_collect(const IndexView &ix, int nb, int l, int cap, QueryState &st,
                          int64_t *stats_out, cudaStream_t s);
+bool cluster_path_fits(const IndexView &ix, int *cluster_size, int *tiles_per_cta);
+qw_status launch_cluster_query(const IndexView &ix, const int32_t *HQ, int nq, int l, int c,
+                               int cap, int cluster_size, int tpc, int max_clusters,
+                               QueryState &st, int *queue, int64_t *stats_out, int *err,
+                               cudaStream_t s, int *clusters_used);
 qw_status launch_candidates_out(const QueryState &st, int nb, int cap, int64_t *cand_ids,
                                 int32_t *cand_col, cudaStream_t s);
 qw_status launch_rerank(const IndexView &ix, const float *Qb, int nb, int k, int cap,

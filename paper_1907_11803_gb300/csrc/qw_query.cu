@@ -19,6 +19,7 @@
 // boundaries of all m projections, increments the counters of every id in the
 // flanks, counts the ids whose count reaches l, and writes the counters back.
 #include "qw_internal.cuh"
+#include "qw_count.cuh"
 #include "qw_scan.cuh"
 
 #include <algorithm>
@@ -28,6 +29,7 @@ namespace {
 
 constexpr int LV_THREADS = 256;
 constexpr int kWordsPerTile = kTile / 4;
+constexpr int kUnroll = 4;
 
 __device__ __forceinline__ int64_t floordiv64(int64_t a, int64_t R)
 {
@@ -94,10 +96,14 @@ __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int lev
                                                            int64_t words_per_query)
 {
     __shared__ __align__(16) uint32_t cnt_s[kWordsPerTile];
-    __shared__ int64_t seg_base[2 * QW_MAX_M];
-    __shared__ int32_t seg_pref[2 * QW_MAX_M + 1];
-    __shared__ int32_t red_cross;
+    __shared__ int64_t f_gc0[2 * QW_MAX_M];
+    __shared__ int32_t f_cpref[2 * QW_MAX_M + 1];
+    __shared__ uint8_t f_head[2 * QW_MAX_M], f_tail[2 * QW_MAX_M], f_tile[2 * QW_MAX_M];
+    __shared__ int32_t wsum[LV_THREADS / 32];
+    __shared__ int hist[kHistBins];
+    __shared__ int32_t red_count;
     __shared__ unsigned long long red_scan;
+    FlankSet fl{f_gc0, f_cpref, f_head, f_tail, f_tile};
 
     const int t = blockIdx.x;
     const int q = blockIdx.y;
@@ -107,13 +113,14 @@ __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int lev
     const int64_t tbase = (int64_t)t * kTile;
     const int len = (int)min((int64_t)kTile, n - tbase);
     if (threadIdx.x == 0) {
-        red_cross = 0;
+        red_count = 0;
         red_scan = 0;
     }
+    for (int c = threadIdx.x; c < kHistBins; c += LV_THREADS) hist[c] = 0;
 
     // 1. flank boundaries of every projection (one thread per projection)
     unsigned long long my_scan = 0;
-    int my_len0 = 0, my_len1 = 0;
+    int my_c0 = 0, my_c1 = 0;
     if (threadIdx.x < m) {
         const int i = threadIdx.x;
         const int64_t gi = st.g[(int64_t)q * m + i];
@@ -136,33 +143,20 @@ __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int lev
                 e1 = pB;
             }
         }
-        my_len0 = e0 - s0;
-        my_len1 = e1 - s1;
-        const int64_t ebase = (int64_t)i * n + tbase;
-        seg_base[2 * i] = ebase + s0;
-        seg_base[2 * i + 1] = ebase + s1;
+        // the tile's slots start 16-byte aligned, so chunks are tile offsets / 8
+        const int64_t ebase = (int64_t)i * ix.nT * kTile + tbase;
+        flank_set(fl, 2 * i, ebase + s0, ebase + e0, 0, &my_c0);
+        flank_set(fl, 2 * i + 1, ebase + s1, ebase + e1, 0, &my_c1);
         my_scan = (unsigned long long)(pB - pA);
     }
-    // prefix over the 2m segment lengths (m <= 127 fits in the first 4 warps)
     {
-        __shared__ int32_t wsum[LV_THREADS / 32];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        int v = my_len0 + my_len1;
-        int incl = v;
-        for (int off = 1; off < 32; off <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += y;
-        }
-        if (lane == 31) wsum[warp] = incl;
-        __syncthreads();
-        int wbase = 0;
-        for (int w2 = 0; w2 < warp; ++w2) wbase += wsum[w2];
-        const int excl = wbase + incl - v;
+        int total;
+        const int excl = block_exclusive_scan<LV_THREADS>(my_c0 + my_c1, wsum, &total);
         if (threadIdx.x < m) {
-            seg_pref[2 * threadIdx.x] = excl;
-            seg_pref[2 * threadIdx.x + 1] = excl + my_len0;
+            f_cpref[2 * threadIdx.x] = excl;
+            f_cpref[2 * threadIdx.x + 1] = excl + my_c0;
         }
-        if (threadIdx.x == m - 1) seg_pref[2 * m] = excl + v;
+        if (threadIdx.x == 0) f_cpref[2 * m] = total;
     }
     if (my_scan) atomicAdd(&red_scan, my_scan);
 
@@ -177,35 +171,71 @@ __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int lev
     } else {
         for (int w4 = threadIdx.x; w4 < kWordsPerTile / 4; w4 += LV_THREADS) {
             uint4 x = cg[w4];
-            x.x |= __vcmpgeu4(x.x & 0x7f7f7f7fu, lrep) & 0x80808080u;
-            x.y |= __vcmpgeu4(x.y & 0x7f7f7f7fu, lrep) & 0x80808080u;
-            x.z |= __vcmpgeu4(x.z & 0x7f7f7f7fu, lrep) & 0x80808080u;
-            x.w |= __vcmpgeu4(x.w & 0x7f7f7f7fu, lrep) & 0x80808080u;
+            x.x = flag_ge(x.x, lrep);
+            x.y = flag_ge(x.y, lrep);
+            x.z = flag_ge(x.z, lrep);
+            x.w = flag_ge(x.w, lrep);
             cs[w4] = x;
         }
     }
     __syncthreads();
 
-    // 3. count every id in the flanks
-    const int total = seg_pref[2 * m];
-    int my_cross = 0;
+    // 3. count every id in the flanks: 8 ids per 16-byte load, kUnroll loads
+    //    in flight per thread
+    const int total = f_cpref[2 * m];
+    const uint4 *lid4 = reinterpret_cast<const uint4 *>(ix.lid);
     int s = 0;
-    const uint32_t lm1 = (uint32_t)(l - 1);
-    for (int e = threadIdx.x; e < total; e += LV_THREADS) {
-        while (e >= seg_pref[s + 1]) ++s;
-        const uint32_t id = ix.lid[seg_base[s] + (e - seg_pref[s])];
-        const uint32_t sh = (id & 3u) << 3;
-        const uint32_t old = atomicAdd(&cnt_s[id >> 2], 1u << sh);
-        my_cross += (((old >> sh) & 0x7fu) == lm1) ? 1 : 0;
+    for (int e0 = threadIdx.x; e0 < total; e0 += LV_THREADS * kUnroll) {
+        uint4 v[kUnroll];
+        uint32_t mask[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int e = e0 + u * LV_THREADS;
+            mask[u] = 0;
+            if (e < total) {
+                while (e >= f_cpref[s + 1]) ++s;
+                v[u] = __ldg(lid4 + f_gc0[s] + (e - f_cpref[s]));
+                mask[u] = flank_mask(fl, s, e);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (mask[u]) count_chunk(cnt_s, v[u], mask[u]);
     }
-    my_cross = __reduce_add_sync(0xffffffffu, my_cross);
-    if ((threadIdx.x & 31) == 0 && my_cross) atomicAdd(&red_cross, my_cross);
     __syncthreads();
 
-    // 4. counters back to global memory
-    for (int w4 = threadIdx.x; w4 < kWordsPerTile / 4; w4 += LV_THREADS) cg[w4] = cs[w4];
+    // 4. counters back to global memory, and this tile's candidate profile:
+    //    previous-level candidates, and the other candidates by count
+    int my_prev = 0, my_count = 0;
+    for (int w4 = threadIdx.x; w4 < kWordsPerTile / 4; w4 += LV_THREADS) {
+        const uint4 x = cs[w4];
+        cg[w4] = x;
+        const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int c4 = count_ge(wv[h], lrep);
+            if (!c4) continue;
+            my_count += c4;
+#pragma unroll
+            for (int by = 0; by < 4; ++by) {
+                const uint32_t b8 = (wv[h] >> (8 * by)) & 0xffu;
+                if ((b8 & 0x7fu) < (uint32_t)l) continue;
+                if (b8 & 0x80u) ++my_prev;
+                else atomicAdd(&hist[1 + (b8 & 0x7fu)], 1);
+            }
+        }
+    }
+    my_prev = __reduce_add_sync(0xffffffffu, my_prev);
+    my_count = __reduce_add_sync(0xffffffffu, my_count);
+    if ((threadIdx.x & 31) == 0) {
+        if (my_prev) atomicAdd(&hist[0], my_prev);
+        if (my_count) atomicAdd(&red_count, my_count);
+    }
+    __syncthreads();
+    int *th = st.tile_hist + ((int64_t)q * ix.nT + t) * kHistBins;
+    for (int c = threadIdx.x; c < kHistBins; c += LV_THREADS) th[c] = hist[c];
     if (threadIdx.x == 0) {
-        if (red_cross) atomicAdd(st.cross + q, red_cross);
+        if (red_count) atomicAdd(st.cross + q, red_count);
         if (red_scan) atomicAdd(reinterpret_cast<unsigned long long *>(st.scan_level + q), red_scan);
     }
 }
@@ -214,8 +244,8 @@ __global__ void decide_kernel(int nb, int level, int64_t R, int cap, QueryState 
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nb || !st.active[q]) return;
-    const int32_t before = st.ncand[q];
-    const int32_t nc = before + st.cross[q];
+    const int32_t before = st.ncand[q];  // |C_R| of the previous level
+    const int32_t nc = st.cross[q];      // |C_R| of this level, summed over tiles
     st.cross[q] = 0;
     const int64_t sl = st.scan_level[q];
     st.scan_level[q] = 0;
@@ -236,106 +266,78 @@ __global__ void decide_kernel(int nb, int level, int64_t R, int cap, QueryState 
 constexpr int CL_THREADS = 256;
 constexpr int CL_PER = 16;  // ids per thread per chunk (one 16-byte load)
 
-// Select the kept candidates of one query: all ids with count >= l when there
-// are at most k + v of them; otherwise the previous level's candidates, then
-// by count descending, then by id ascending, up to k + v.  Emits ids in
-// ascending order with their counts, and the query's statistics.
-__global__ void __launch_bounds__(CL_THREADS) collect_kernel(
-    int64_t n, int m, int l, int cap, QueryState st, int64_t words_per_query,
-    int64_t *__restrict__ stats_out)
+// Plan the kept candidates of one query from the per-tile profiles of its
+// last level: all ids with count >= l when there are at most k + v of them;
+// otherwise the previous level's candidates, then by count descending, then by
+// id ascending, up to k + v.  The boundary count c* splits the ids with count
+// above it (all kept) from those equal to it (the first take_eq by id kept).
+// Writes, per tile, where its kept ids start in the query's list and how many
+// count-c* ids precede it; and the query's statistics.
+__global__ void __launch_bounds__(CL_THREADS) select_plan_kernel(
+    int nT, int m, int l, int cap, QueryState st, int64_t *__restrict__ stats_out)
 {
-    __shared__ int hist[128];
+    __shared__ int tot[kHistBins];
     __shared__ int s_cstar, s_take_eq;
     __shared__ int scan_tmp[CL_THREADS / 32];
     const int q = blockIdx.x;
     const int nc = st.ncand[q];
     const int np = st.nprev[q];
-    const uint8_t *cb = reinterpret_cast<const uint8_t *>(st.counters + (int64_t)q * words_per_query);
-    const int64_t n16 = (n + 15) / 16 * 16;  // counters are padded to whole tiles
-
-    if (threadIdx.x < 128) hist[threadIdx.x] = 0;
+    const int *qh = st.tile_hist + (int64_t)q * nT * kHistBins;
     if (threadIdx.x == 0) {
         s_cstar = l - 1;
         s_take_eq = 0;
     }
-    __syncthreads();
     if (nc > cap) {
-        for (int64_t base = (int64_t)threadIdx.x * CL_PER; base < n16;
-             base += (int64_t)CL_THREADS * CL_PER) {
-            uint4 v4 = *reinterpret_cast<const uint4 *>(cb + base);
-            const uint8_t *bytes = reinterpret_cast<const uint8_t *>(&v4);
-#pragma unroll
-            for (int u = 0; u < CL_PER; ++u) {
-                int c = bytes[u] & 0x7f;
-                if (c >= l && !(bytes[u] & 0x80)) atomicAdd(&hist[c], 1);
-            }
+        for (int c = threadIdx.x; c < kHistBins; c += CL_THREADS) {
+            int sum = 0;
+            for (int t = 0; t < nT; ++t) sum += qh[(int64_t)t * kHistBins + c];
+            tot[c] = sum;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             const int need = cap - np;
             int acc = 0;
             for (int c = m; c >= l; --c) {
-                if (acc + hist[c] >= need) {
+                const int hc = tot[1 + c];
+                if (acc + hc >= need) {
                     s_cstar = c;
                     s_take_eq = need - acc;
                     break;
                 }
-                acc += hist[c];
+                acc += hc;
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
     const int cstar = s_cstar, take_eq = s_take_eq;
+    // per tile: kept ids above c*, and ids at c*, then prefixes over tiles
     int eq_base = 0, out_base = 0;
-    for (int64_t chunk = 0; chunk < n16; chunk += (int64_t)CL_THREADS * CL_PER) {
-        const int64_t base = chunk + (int64_t)threadIdx.x * CL_PER;
-        uint4 v4 = make_uint4(0, 0, 0, 0);
-        if (base < n16) v4 = *reinterpret_cast<const uint4 *>(cb + base);
-        const uint8_t *bytes = reinterpret_cast<const uint8_t *>(&v4);
-        int n_eq = 0;
-#pragma unroll
-        for (int u = 0; u < CL_PER; ++u) {
-            int c = bytes[u] & 0x7f;
-            n_eq += (c == cstar && !(bytes[u] & 0x80) && c >= l) ? 1 : 0;
+    for (int t0 = 0; t0 < nT; t0 += CL_THREADS) {
+        const int t = t0 + threadIdx.x;
+        int above = 0, eq = 0;
+        if (t < nT) {
+            const int *th = qh + (int64_t)t * kHistBins;
+            above = th[0];
+            for (int c = max(cstar + 1, l); c <= m; ++c) above += th[1 + c];
+            eq = (cstar >= l) ? th[1 + cstar] : 0;
         }
-        int eq_total;
-        int eq_excl = block_exclusive_scan<CL_THREADS>(n_eq, scan_tmp, &eq_total);
-        int rank = eq_base + eq_excl;
-        uint16_t selmask = 0;
-        int n_sel = 0;
-#pragma unroll
-        for (int u = 0; u < CL_PER; ++u) {
-            int c = bytes[u] & 0x7f;
-            bool prev = bytes[u] & 0x80;
-            bool sel = false;
-            if (c >= l) {
-                if (prev || c > cstar) sel = true;
-                else if (c == cstar) { sel = rank < take_eq; ++rank; }
-            }
-            if (sel) { selmask |= (uint16_t)(1u << u); ++n_sel; }
+        int eq_tot;
+        const int eq_ex = eq_base + block_exclusive_scan<CL_THREADS>(eq, scan_tmp, &eq_tot);
+        const int kept = above + min(max(take_eq - eq_ex, 0), eq);
+        int kept_tot;
+        const int out_ex = out_base + block_exclusive_scan<CL_THREADS>(kept, scan_tmp, &kept_tot);
+        if (t < nT) {
+            st.tile_plan[((int64_t)q * nT + t) * 2 + 0] = out_ex;
+            st.tile_plan[((int64_t)q * nT + t) * 2 + 1] = eq_ex;
         }
-        int sel_total;
-        int pos = out_base + block_exclusive_scan<CL_THREADS>(n_sel, scan_tmp, &sel_total);
-#pragma unroll
-        for (int u = 0; u < CL_PER; ++u) {
-            if (selmask & (1u << u)) {
-                if (pos < cap) {
-                    st.cand[(int64_t)q * cap + pos] = (int32_t)(base + u);
-                    st.cand_col[(int64_t)q * cap + pos] = bytes[u] & 0x7f;
-                }
-                ++pos;
-            }
-        }
-        eq_base += eq_total;
-        out_base += sel_total;
+        eq_base += eq_tot;
+        out_base += kept_tot;
     }
     if (threadIdx.x == 0) {
         const int keep = min(out_base, cap);
         st.nkeep[q] = keep;
-        for (int p = keep; p < cap; ++p) {
-            st.cand[(int64_t)q * cap + p] = -1;
-            st.cand_col[(int64_t)q * cap + p] = 0;
-        }
+        st.qplan[q * 2 + 0] = cstar;
+        st.qplan[q * 2 + 1] = take_eq;
         if (stats_out) {
             int64_t *so = stats_out + (int64_t)q * QW_NSTAT;
             so[0] = st.levels[q];
@@ -347,6 +349,74 @@ __global__ void __launch_bounds__(CL_THREADS) collect_kernel(
             so[6] = st.scan_full[q];
             so[7] = np;
         }
+    }
+    // pad the list (the emit kernel fills [0, keep))
+    const int keep = min(out_base, cap);
+    for (int p = keep + threadIdx.x; p < cap; p += CL_THREADS) {
+        st.cand[(int64_t)q * cap + p] = -1;
+        st.cand_col[(int64_t)q * cap + p] = 0;
+    }
+}
+
+// Emit the kept ids of one (tile, query) in ascending order at the tile's
+// planned position.
+__global__ void __launch_bounds__(CL_THREADS) select_emit_kernel(
+    int64_t n, int nT, int l, int cap, QueryState st, int64_t words_per_query)
+{
+    __shared__ int scan_tmp[CL_THREADS / 32];
+    const int t = blockIdx.x;
+    const int q = blockIdx.y;
+    const int *th = st.tile_hist + ((int64_t)q * nT + t) * kHistBins;
+    const int cstar = st.qplan[q * 2 + 0], take_eq = st.qplan[q * 2 + 1];
+    // nothing kept in this tile: skip reading its counters
+    int any = th[0];
+    for (int c = max(cstar, l); c < kHistBins - 1 && !any; ++c) any = th[1 + c];
+    if (!any) return;
+    const int out0 = st.tile_plan[((int64_t)q * nT + t) * 2 + 0];
+    int rank = st.tile_plan[((int64_t)q * nT + t) * 2 + 1];
+    const int64_t tbase = (int64_t)t * kTile;
+    const int len = (int)min((int64_t)kTile, n - tbase);
+    const uint8_t *cb = reinterpret_cast<const uint8_t *>(st.counters + (int64_t)q * words_per_query) + tbase;
+    int out_base = out0;
+    for (int chunk = 0; chunk < len; chunk += CL_THREADS * CL_PER) {
+        const int base = chunk + threadIdx.x * CL_PER;
+        uint4 v4 = make_uint4(0, 0, 0, 0);
+        if (base < len) v4 = *reinterpret_cast<const uint4 *>(cb + base);
+        const uint8_t *bytes = reinterpret_cast<const uint8_t *>(&v4);
+        int n_eq = 0;
+#pragma unroll
+        for (int u = 0; u < CL_PER; ++u) {
+            const int c = bytes[u] & 0x7f;
+            n_eq += (c == cstar && c >= l && !(bytes[u] & 0x80)) ? 1 : 0;
+        }
+        int eq_total;
+        int r = rank + block_exclusive_scan<CL_THREADS>(n_eq, scan_tmp, &eq_total);
+        uint16_t selmask = 0;
+        int n_sel = 0;
+#pragma unroll
+        for (int u = 0; u < CL_PER; ++u) {
+            const int c = bytes[u] & 0x7f;
+            bool sel = false;
+            if (c >= l) {
+                if ((bytes[u] & 0x80) || c > cstar) sel = true;
+                else if (c == cstar) { sel = r < take_eq; ++r; }
+            }
+            if (sel) { selmask |= (uint16_t)(1u << u); ++n_sel; }
+        }
+        int sel_total;
+        int pos = out_base + block_exclusive_scan<CL_THREADS>(n_sel, scan_tmp, &sel_total);
+#pragma unroll
+        for (int u = 0; u < CL_PER; ++u) {
+            if (selmask & (1u << u)) {
+                if (pos < cap) {
+                    st.cand[(int64_t)q * cap + pos] = (int32_t)(tbase + base + u);
+                    st.cand_col[(int64_t)q * cap + pos] = bytes[u] & 0x7f;
+                }
+                ++pos;
+            }
+        }
+        rank += eq_total;
+        out_base += sel_total;
     }
 }
 
@@ -404,7 +474,10 @@ qw_status launch_collect(const IndexView &ix, int nb, int l, int cap, QueryState
                          int64_t *stats_out, cudaStream_t s)
 {
     const int64_t wpq = (int64_t)ix.nT * kWordsPerTile;
-    collect_kernel<<<nb, CL_THREADS, 0, s>>>(ix.n, ix.m, l, cap, st, wpq, stats_out);
+    select_plan_kernel<<<nb, CL_THREADS, 0, s>>>(ix.nT, ix.m, l, cap, st, stats_out);
+    QW_CUDA_TRY(cudaGetLastError());
+    select_emit_kernel<<<dim3((unsigned)ix.nT, (unsigned)nb), CL_THREADS, 0, s>>>(ix.n, ix.nT, l, cap,
+                                                                                st, wpq);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }

@@ -13,6 +13,7 @@ pytestmark = pytest.mark.gpu
 
 DIST_RTOL = 1e-5
 TILE = 32768
+PATHS = pytest.mark.parametrize("path", ["levels", "cluster"])
 
 
 def _t(x, dev):
@@ -50,7 +51,7 @@ def _check_candidates(cid, ccol, ref_cid, ref_ccol):
         assert np.array_equal(ccol[q][: got.size], want_col), f"counts differ on query {q}"
 
 
-def _gpu_workload(qw, dev, X, Q, A, b, *, w, k, v, l, c=2, batch=0, host=False):
+def _gpu_workload(qw, dev, X, Q, A, b, *, w, k, v, l, c=2, batch=0, host=False, path="auto"):
     import torch
     if host:
         Xd, Ad, bd = (torch.from_numpy(np.ascontiguousarray(a)) for a in (X, A, b))
@@ -58,8 +59,8 @@ def _gpu_workload(qw, dev, X, Q, A, b, *, w, k, v, l, c=2, batch=0, host=False):
     else:
         Xd, Qd, Ad, bd = _t(X, dev), _t(Q, dev), _t(A, dev), _t(b, dev)
     index = qw.Index(Xd, Ad, bd, w=w, c=c, v=v, l=l)
-    ids, dists, st = index.query(Qd, k, batch=batch, stats=True)
-    cid, ccol, st2 = index.candidates(Qd, k, batch=batch)
+    ids, dists, st = index.query(Qd, k, batch=batch, stats=True, path=path)
+    cid, ccol, st2 = index.candidates(Qd, k, batch=batch, path=path)
     torch.cuda.synchronize()
     out = dict(ids=ids.cpu().numpy(), dists=dists.cpu().numpy(), stats=st.cpu().numpy(),
                cid=cid.cpu().numpy(), ccol=ccol.cpu().numpy(), stats2=st2.cpu().numpy(),
@@ -67,12 +68,14 @@ def _gpu_workload(qw, dev, X, Q, A, b, *, w, k, v, l, c=2, batch=0, host=False):
     return out
 
 
-def _full_parity(orc, qw, dev, X, Q, A, b, *, w, k, v, l=None, c=2, batch=0, host=False):
+def _full_parity(orc, qw, dev, X, Q, A, b, *, w, k, v, l=None, c=2, batch=0, host=False,
+                 path="auto"):
     n = X.shape[0]
     if l is None:
         l = orc.threshold(A.shape[0], w, c, n, v)
     H, HQ, oidx, ref = _oracle_run(orc, X, Q, A, b, w, k, v, l, c)
-    g = _gpu_workload(qw, dev, X, Q, A, b, w=w, k=k, v=v, l=l, c=c, batch=batch, host=host)
+    g = _gpu_workload(qw, dev, X, Q, A, b, w=w, k=k, v=v, l=l, c=c, batch=batch, host=host,
+                      path=path)
     _check_results(g["ids"], g["dists"], ref["ids"], ref["dists"])
     assert np.array_equal(g["stats"], ref["stats"]), "per-query statistics differ"
     assert np.array_equal(g["stats2"], ref["stats"])
@@ -139,72 +142,81 @@ def test_build_matches_oracle(orc, qwlib, cuda, n, d, m):
 
 
 # ---------------------------------------------------------------- a4..a9: workloads
-def test_workload_small_config(orc, qwlib, cuda):
+@PATHS
+def test_workload_small_config(orc, qwlib, cuda, path):
     wl = workloads.make_workload("mix10k_d32", seed=0)
     s = wl.spec
-    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=s.w, k=s.k, v=s.v)
+    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=s.w, k=s.k, v=s.v, path=path)
 
 
-def test_workload_ragged_tiles_and_batches(orc, qwlib, cuda):
+@PATHS
+def test_workload_ragged_tiles_and_batches(orc, qwlib, cuda, path):
     """Three index tiles (the last one ragged), small k + v so the truncation
     and its tie rule run, several query batches with a ragged last batch."""
     wl = workloads.make_workload("mix10k_d32", seed=11, n=2 * TILE + 777, nq=61, d=24, m=12,
                                  n_clusters=40)
-    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=7, v=20, batch=13)
+    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=7, v=20, batch=13, path=path)
 
 
-def test_workload_host_memory(orc, qwlib, cuda):
+@PATHS
+def test_workload_host_memory(orc, qwlib, cuda, path):
     wl = workloads.make_workload("mix10k_d32", seed=5, n=5000, nq=40)
     s = wl.spec
     _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=s.w, k=s.k, v=s.v, host=True,
-                 batch=16)
+                 batch=16, path=path)
 
 
-def test_workload_v_ge_n_is_exact_knn(orc, qwlib, cuda):
+@PATHS
+def test_workload_v_ge_n_is_exact_knn(orc, qwlib, cuda, path):
     """v >= n: the k + v bound never stops a query, the last level holds every
     point, and the answer is the exact k-NN (queries are data rows)."""
     wl = workloads.make_workload("mix10k_d32", seed=2, n=600, nq=25, n_clusters=6)
     Q = wl.X[:25].copy()
-    ref, g = _full_parity(orc, qwlib, cuda, wl.X, Q, wl.A, wl.b, w=4.0, k=10, v=600, l=10)
+    ref, g = _full_parity(orc, qwlib, cuda, wl.X, Q, wl.A, wl.b, w=4.0, k=10, v=600, l=10, path=path)
     bf_ids, bf_d = orc.bruteforce(wl.X, Q, 10)
     assert np.array_equal(g["ids"], bf_ids)
     assert np.all(g["stats"][:, 4] == 3)
 
 
-def test_workload_single_projection(orc, qwlib, cuda):
+@PATHS
+def test_workload_single_projection(orc, qwlib, cuda, path):
     """m = 1, l = 1: plain E2LSH bucket lookup with growing radius."""
     wl = workloads.make_workload("mix10k_d32", seed=4, n=3000, nq=30, m=1)
-    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=5, v=10, l=1)
+    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=5, v=10, l=1, path=path)
 
 
-def test_workload_far_queries_and_padding(orc, qwlib, cuda):
+@PATHS
+def test_workload_far_queries_and_padding(orc, qwlib, cuda, path):
     """Queries far outside the data: many levels, bucket ids below the anchor,
     fewer than k candidates (padded with -1 / inf)."""
     wl = workloads.make_workload("mix10k_d32", seed=9, n=2000, nq=12)
     Q = wl.Q.copy()
     Q[:6] += 400.0
     Q[6:] -= 400.0
-    _full_parity(orc, qwlib, cuda, wl.X, Q, wl.A, wl.b, w=4.0, k=10, v=100)
+    _full_parity(orc, qwlib, cuda, wl.X, Q, wl.A, wl.b, w=4.0, k=10, v=100, path=path)
 
 
-def test_workload_duplicates_tie_by_id(orc, qwlib, cuda):
+@PATHS
+def test_workload_duplicates_tie_by_id(orc, qwlib, cuda, path):
     """Exact duplicate rows: equal distances are ordered by id."""
     wl = workloads.make_workload("mix10k_d32", seed=6, n=1500, nq=20)
     X = np.repeat(wl.X[:300], 5, axis=0)
-    _full_parity(orc, qwlib, cuda, X, wl.Q, wl.A, wl.b, w=4.0, k=12, v=30)
+    _full_parity(orc, qwlib, cuda, X, wl.Q, wl.A, wl.b, w=4.0, k=12, v=30, path=path)
 
 
-def test_workload_tiny_index(orc, qwlib, cuda):
+@PATHS
+def test_workload_tiny_index(orc, qwlib, cuda, path):
     X = np.array([[0.5, -1.0, 2.0]], np.float32)
     A = np.array([[1.0, 0.0, 0.0], [0.3, 0.2, -0.7]], np.float32)
     b = np.array([0.25, 1.5], np.float32)
     Q = np.array([[0.4, -1.1, 2.0], [30.0, 30.0, 30.0]], np.float32)
-    _full_parity(orc, qwlib, cuda, X, Q, A, b, w=2.0, k=1, v=3, l=1)
+    _full_parity(orc, qwlib, cuda, X, Q, A, b, w=2.0, k=1, v=3, l=1, path=path)
 
 
-def test_workload_k_equals_n(orc, qwlib, cuda):
+@PATHS
+def test_workload_k_equals_n(orc, qwlib, cuda, path):
     wl = workloads.make_workload("mix10k_d32", seed=8, n=64, nq=5, n_clusters=3)
-    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=64, v=0, l=4)
+    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=64, v=0, l=4, path=path)
 
 
 def test_empty_workload(qwlib, cuda):
@@ -213,6 +225,25 @@ def test_empty_workload(qwlib, cuda):
     index = qwlib.Index(_t(wl.X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=4.0)
     ids, dists = index.query(torch.empty((0, wl.X.shape[1]), dtype=torch.float32, device=cuda), 5)
     assert ids.shape == (0, 5)
+    index.free()
+
+
+def test_cluster_path_refuses_oversized_index(qwlib, cuda):
+    """More than 96 tiles do not fit the cluster path: forcing it is an argument
+    error, and the automatic choice runs the level path instead."""
+    import torch
+    n = 96 * TILE + 5
+    rng = np.random.default_rng(0)
+    X = torch.from_numpy(rng.standard_normal((n, 4), dtype=np.float32)).to(cuda)
+    A = torch.from_numpy(rng.standard_normal((2, 4), dtype=np.float32)).to(cuda)
+    b = torch.from_numpy(np.array([0.5, 1.0], np.float32)).to(cuda)
+    index = qwlib.Index(X, A, b, w=4.0, v=10, l=1)
+    Q = X[:3].clone()
+    with pytest.raises(qwlib.QwError) as e:
+        index.query(Q, 2, path="cluster")
+    assert e.value.status == qwlib.QW_ERR_ARG
+    ids, _ = index.query(Q, 2)
+    assert ids.shape == (3, 2)
     index.free()
 
 
@@ -249,8 +280,13 @@ def test_full_size_sampled(orc, qwlib, cuda):
     index = qwlib.Index(_t(wl.X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=s.w, c=s.c, v=s.v, l=l)
     Qd = _t(wl.Q, cuda)
     ids, dists, st = index.query(Qd, s.k, stats=True)
+    ids2, dists2, st2 = index.query(Qd, s.k, stats=True, path="levels")
     torch.cuda.synchronize()
     ids, dists, st = ids.cpu().numpy(), dists.cpu().numpy(), st.cpu().numpy()
+    # the two execution paths agree on every query
+    assert np.array_equal(ids, ids2.cpu().numpy())
+    assert np.array_equal(st, st2.cpu().numpy())
+    assert np.array_equal(dists, dists2.cpu().numpy())
     H = orc.hash(wl.X, wl.A, wl.b, s.w)
     oidx = orc.build_index(H, sorted_arrays=True)
     info = index.info
