@@ -220,6 +220,38 @@ qw_status qw_workload_candidates(qw_index *index, const float *queries, int64_t 
                                  const qw_query_params *qparams, int64_t *cand_ids,
                                  int32_t *cand_col, int64_t *stats, int32_t mem, void *stream);
 
+/* Bytes of the library-owned static device scratch used by
+ * qw_run_workload_noalloc (held by every GPU that loads the library, until the
+ * process exits). */
+#define QW_STATIC_SCRATCH_BYTES (64u << 20)
+
+/* qw_run_workload for callers that must not allocate device memory.
+ *
+ * The paper has no counterpart: this is a deployment variant of the
+ * level-synchronous path.  Some callers cannot call cudaMalloc or cudaFree at
+ * query time -- for example a process whose device memory is already fully
+ * reserved by another framework's caching allocator, or a latency-critical
+ * serving thread that must not trigger the device-wide synchronisation these
+ * calls can imply.  This entry point allocates nothing: its working memory is
+ * one file-scope device array of QW_STATIC_SCRATCH_BYTES, and queries are
+ * processed in batches sized to fit it.  The index must already exist
+ * (qw_build_index allocates; build it beforehand).
+ *
+ * Arguments as qw_run_workload, except that queries, ids, dists and stats
+ * (optional) are DEVICE pointers and there are no per-call options.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture.  Every call on a device shares the
+ * same array, so calls whose work overlaps on the GPU (different streams or
+ * threads without ordering between them) race and corrupt each other's
+ * results: order them on one stream.  The call waits for `stream` once per
+ * batch.
+ * Errors: as qw_run_workload; QW_ERR_ARG also when one query's working memory
+ * (about n + 64 * n_tiles * 33 + 8 * (k + v) bytes) exceeds the static array,
+ * i.e. indexes of more than about 64 million points. */
+qw_status qw_run_workload_noalloc(qw_index *index, const float *queries, int64_t nq, int32_t k,
+                                  int64_t *ids, float *dists, int64_t *stats, void *stream);
+
 /* Copy the index's profile counters into *out (host); reset them afterwards
  * when `reset` is non-zero. */
 qw_status qw_index_profile(qw_index *index, qw_profile *out, int32_t reset);

@@ -32,7 +32,8 @@ STAT_FIELDS = ("levels", "final_R", "n_cand_raw", "n_cand", "term", "scanned_las
 # Every symbol include/qwlsh.h declares.
 EXPORTED = ("qw_version", "qw_last_error", "qw_collision_probability",
             "qw_collision_threshold", "qw_hash", "qw_build_index", "qw_run_workload",
-            "qw_workload_candidates", "qw_index_profile", "qw_index_get_info", "qw_index_export", "qw_index_free")
+            "qw_workload_candidates", "qw_run_workload_noalloc", "qw_index_profile",
+            "qw_index_get_info", "qw_index_export", "qw_index_free")
 
 
 class qw_index_params(C.Structure):
@@ -105,6 +106,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.qw_workload_candidates.restype = C.c_int32
     L.qw_workload_candidates.argtypes = [vp, vp, C.c_int64, C.c_int32, C.POINTER(qw_query_params),
                                          vp, vp, vp, C.c_int32, vp]
+    L.qw_run_workload_noalloc.restype = C.c_int32
+    L.qw_run_workload_noalloc.argtypes = [vp, vp, C.c_int64, C.c_int32, vp, vp, vp, vp]
     L.qw_index_profile.restype = C.c_int32
     L.qw_index_profile.argtypes = [vp, C.POINTER(qw_profile), C.c_int32]
     L.qw_index_get_info.restype = C.c_int32
@@ -162,6 +165,13 @@ def qw_workload_candidates(index: int, queries: int, nq: int, k: int, qparams: q
                            cand_ids: int, cand_col: int, stats: int, mem: int, stream: int = 0):
     _check(load().qw_workload_candidates(index, queries, nq, k, C.byref(qparams), cand_ids,
                                          cand_col or None, stats or None, mem, stream or None))
+
+
+def qw_run_workload_noalloc(index: int, queries: int, nq: int, k: int, ids: int, dists: int,
+                            stats: int, stream: int = 0):
+    """Device pointers only; uses the library's static scratch, allocates nothing."""
+    _check(load().qw_run_workload_noalloc(index, queries, nq, k, ids, dists, stats or None,
+                                          stream or None))
 
 
 def qw_index_profile(index: int, reset: bool = False) -> qw_profile:

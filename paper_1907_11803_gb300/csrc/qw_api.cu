@@ -148,6 +148,19 @@ struct LaunchTimer {
     }
 };
 
+qw_status qw::index_params(const qw_index *ix, IndexParams *out)
+{
+    if (!ix || !out) return QW_ERR_ARG;
+    out->view = ix->view();
+    out->A = ix->A.as<float>();
+    out->b = ix->b.as<float>();
+    out->w = ix->w;
+    out->c = ix->c;
+    out->v = ix->v;
+    out->l = ix->l;
+    return QW_OK;
+}
+
 extern "C" {
 
 const char *qw_version(void) { return "qwlsh-gb300 0.1 (sm_103a)"; }

@@ -136,4 +136,14 @@ qw_status launch_rerank(const IndexView &ix, const float *Qb, int nb, int k, int
                         const QueryState &st, int64_t *ids_out, float *dists_out,
                         cudaStream_t s);
 
+// Read-only view of a built index for entry points outside qw_api.cu.
+struct IndexParams {
+    IndexView view;
+    const float *A;
+    const float *b;
+    float w;
+    int c, v, l;
+};
+qw_status index_params(const qw_index *ix, IndexParams *out);
+
 }  // namespace qw
