@@ -30,6 +30,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# Operating points (v, l) meeting recall >= 0.9 and ratio <= 1.05, from sweeps
+# of v and l on the GPU; the paper's v = 100 gives recall 0.35 on mix1m_d128.
+OPERATING_POINTS = {"mix1m_d128": (700, 43)}
+
 METRIC = "workload queries/sec at recall>=0.9, ratio<=1.05 (plain vs chosen); HBM roofline %"
 UNIT = "queries/s"
 L2_BYTES = 129 * 1024 * 1024
@@ -53,7 +57,22 @@ def parse_args(argv=None):
     p.add_argument("--batch", type=int, default=0, help="queries per pass (0 = library choice)")
     p.add_argument("--path", choices=["auto", "cluster", "levels"], default="auto",
                    help="execution path of the query loop (identical results)")
+    p.add_argument("--order", choices=["auto", "signature", "given"], default="auto",
+                   help="workload order: grouped by bucket signature, or as given")
+    p.add_argument("--v", type=int, default=-1,
+                   help="allowed false positives (-1 = the workload's operating point)")
+    p.add_argument("--l", type=int, default=-1,
+                   help="collision threshold (0 = derived from Eq. 1, -1 = operating point)")
     return p.parse_args(argv)
+
+
+def operating_point(args, spec):
+    """(v, l) for this run: explicit flags, else the workload's operating
+    point, else the spec's v with l derived from Eq. 1 (l = 0)."""
+    dv, dl = OPERATING_POINTS.get(args.workload, (spec.v, 0))
+    v = args.v if args.v >= 0 else dv
+    l = args.l if args.l >= 0 else dl
+    return v, l
 
 
 # ---------------------------------------------------------------- ranks
@@ -159,17 +178,29 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def ncu_traffic(kernel: str, workload: str):
-    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
-    the current kernel source (the summary records the source's sha256)."""
-    path = os.path.join(ROOT, "profiles", "traffic.txt")
+KERNEL_SOURCES = {
+    "level_kernel": ("qw_query.cu", "qw_count.cuh", "qw_internal.cuh"),
+    "cluster_query_kernel": ("qw_cluster.cu", "qw_count.cuh", "qw_internal.cuh"),
+    "rerank_kernel": ("qw_rerank.cu", "qw_internal.cuh"),
+}
+
+
+def kernel_source_sha(kernel: str) -> str:
+    """sha256 (16 hex digits) of the source files a kernel is built from."""
     src = os.path.join(ROOT, "paper_1907_11803_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(src, f), "rb") as fh:
-                h.update(fh.read())
-    sha = h.hexdigest()[:16]
+    for f in KERNEL_SOURCES.get(kernel, ()):
+        with open(os.path.join(src, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes (read + write) of a kernel from the committed ncu
+    summary profiles/traffic.txt, if that was taken on the current source of
+    the kernel (lines: kernel workload source-sha bytes-per-launch)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    sha = kernel_source_sha(kernel)
     try:
         with open(path) as fh:
             for line in fh:
@@ -213,7 +244,7 @@ def recall_ratio(ids, dists, tids, tdists):
 
 
 # ---------------------------------------------------------------- CPU oracle leg
-def oracle_sample(wl, l, n_queries, seed=1):
+def oracle_sample(wl, l, n_queries, seed=1, v=None):
     """Time the oracle's query procedure on a seeded sample of the workload's
     queries (the index build is excluded, as on the GPU).  Returns
     (queries/s, seconds, sample size)."""
@@ -228,8 +259,8 @@ def oracle_sample(wl, l, n_queries, seed=1):
     Qs = wl.Q[pick]
     HQ = orc.hash(Qs, wl.A, wl.b, s.w)
     t0 = time.perf_counter()
-    orc.query(wl.X, idx, Qs, HQ, k=s.k, v=s.v, l=l, c=s.c, want_candidates=False,
-              want_stats=False)
+    orc.query(wl.X, idx, Qs, HQ, k=s.k, v=s.v if v is None else v, l=l, c=s.c,
+              want_candidates=False, want_stats=False)
     dt = time.perf_counter() - t0
     return len(pick) / dt, dt, len(pick), (orc, idx)
 
@@ -259,15 +290,16 @@ def run_ours(args):
     A = torch.from_numpy(wl.A).to(dev)
     b = torch.from_numpy(wl.b).to(dev)
     Q = torch.from_numpy(wl.Q).to(dev)
-    index = qw.Index(X, A, b, w=s.w, c=s.c, v=s.v)
+    v_used, l_arg = operating_point(args, s)
+    index = qw.Index(X, A, b, w=s.w, c=s.c, v=v_used, l=l_arg)
     ids = torch.empty((s.nq, s.k), dtype=torch.int64, device=dev)
     dists = torch.empty((s.nq, s.k), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     for _ in range(args.warmup):
-        index.query(Q, s.k, out=(ids, dists), batch=args.batch, path=args.path)
+        index.query(Q, s.k, out=(ids, dists), batch=args.batch, path=args.path, order=args.order)
     torch.cuda.synchronize()
-    _, _, st = index.query(Q, s.k, stats=True, batch=args.batch, path=args.path)
+    _, _, st = index.query(Q, s.k, stats=True, batch=args.batch, path=args.path, order=args.order)
     st = st.cpu().numpy()
     index.profile(reset=True)
 
@@ -279,7 +311,7 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        index.query(Q, s.k, out=(ids, dists), profile=True, batch=args.batch, path=args.path)
+        index.query(Q, s.k, out=(ids, dists), profile=True, batch=args.batch, path=args.path, order=args.order)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -293,11 +325,11 @@ def run_ours(args):
     Qh = torch.from_numpy(wl.Q).pin_memory()
     ids_h = torch.empty((s.nq, s.k), dtype=torch.int64).pin_memory()
     dists_h = torch.empty((s.nq, s.k), dtype=torch.float32).pin_memory()
-    index.query(Qh, s.k, out=(ids_h, dists_h), batch=args.batch, path=args.path)
+    index.query(Qh, s.k, out=(ids_h, dists_h), batch=args.batch, path=args.path, order=args.order)
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        index.query(Qh, s.k, out=(ids_h, dists_h), batch=args.batch, path=args.path)
+        index.query(Qh, s.k, out=(ids_h, dists_h), batch=args.batch, path=args.path, order=args.order)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     e2e = {"value": world * s.nq * args.steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(Qh.numel() * 4),
@@ -347,7 +379,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        qps, dt, nsamp, _ = oracle_sample(wl, index.l, args.cpu_sample)
+        qps, dt, nsamp, _ = oracle_sample(wl, index.l, args.cpu_sample, v=v_used)
         cpu = {"value": qps, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{nsamp} seeded queries of the same workload, query procedure only "
                          f"({dt:.1f} s, single thread, FP64)"}
@@ -357,10 +389,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "n": s.n, "d": s.d, "m": s.m, "w": s.w, "c": s.c,
-                   "k": s.k, "v": s.v, "l": index.l, "queries_per_gpu": s.nq,
+                   "k": s.k, "v": v_used, "l": index.l, "queries_per_gpu": s.nq,
                    "query_clusters": s.query_clusters, "seed": args.seed,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "path": args.path,
+                   "path": args.path, "order": args.order,
                    "l2": "inputs larger than L2 (index %.2f GB + data %.2f GB + counters)"
                          % (index.info.device_bytes / 1e9 - s.n * s.d * 4 / 1e9,
                             s.n * s.d * 4 / 1e9)},
@@ -392,9 +424,10 @@ def run_reference(args):
     import workloads
     wl = workloads.make_workload(args.workload, seed=args.seed, nq=args.queries or None)
     s = wl.spec
-    l = oracle.get().threshold(s.m, s.w, s.c, s.n, s.v)
+    v_used, l_arg = operating_point(args, s)
+    l = l_arg if l_arg > 0 else oracle.get().threshold(s.m, s.w, s.c, s.n, v_used)
     per_step = max(1, args.cpu_sample // 2)
-    qps0, _, _, (orc, idx) = oracle_sample(wl, l, per_step, seed=0)
+    qps0, _, _, (orc, idx) = oracle_sample(wl, l, per_step, seed=0, v=v_used)
     rng = np.random.default_rng(99)
     times = []
     for step in range(args.warmup + args.steps):
@@ -402,7 +435,7 @@ def run_reference(args):
         Qs = wl.Q[pick]
         HQ = orc.hash(Qs, wl.A, wl.b, s.w)
         t0 = time.perf_counter()
-        orc.query(wl.X, idx, Qs, HQ, k=s.k, v=s.v, l=l, c=s.c, want_candidates=False,
+        orc.query(wl.X, idx, Qs, HQ, k=s.k, v=v_used, l=l, c=s.c, want_candidates=False,
                   want_stats=False)
         if step >= args.warmup:
             times.append(time.perf_counter() - t0)
@@ -413,7 +446,7 @@ def run_reference(args):
             "ms_per_step": total / len(times) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "n": s.n, "d": s.d, "m": s.m, "k": s.k,
-                       "v": s.v, "l": l},
+                       "v": v_used, "l": l},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{per_step} seeded queries per step, query procedure "
                                        "only, single thread, FP64"},

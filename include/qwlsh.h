@@ -92,8 +92,16 @@ typedef struct {
                              qw_index_profile); the call then waits for the stream */
     int32_t path;         /* QW_PATH_AUTO, QW_PATH_CLUSTER or QW_PATH_LEVELS (below) */
     int32_t clusters;     /* cluster path: most clusters resident at once; 0 = all that fit */
-    int32_t reserved[4];  /* must be zero */
+    int32_t order;        /* QW_ORDER_AUTO / QW_ORDER_SIGNATURE: answer queries grouped by a
+                             coarse bucket signature (queries of one region share index
+                             entries in L2); QW_ORDER_GIVEN: in the caller's order.  Results are
+                             returned in the caller's order either way and do not depend on it */
+    int32_t reserved[3];  /* must be zero */
 } qw_query_params;
+
+#define QW_ORDER_AUTO 0
+#define QW_ORDER_SIGNATURE 1
+#define QW_ORDER_GIVEN 2
 
 /* Execution paths of the query loop (identical results):
  * QW_PATH_LEVELS: one launch per level over (index tile, query) pairs, collision
@@ -116,7 +124,8 @@ typedef struct {
 #define QW_K_RERANK 5    /* candidate distances + top-k */
 #define QW_K_CLUSTER 6   /* cluster path: every level, the stop test and the selection of a
                             query in one persistent launch */
-#define QW_K_COUNT 7
+#define QW_K_ORDER 7     /* workload ordering: signature sort, gather, scatter of results */
+#define QW_K_COUNT 8
 
 /* Launch counts and (profile mode) summed kernel times of qw_run_workload /
  * qw_workload_candidates calls on one index since the last reset. */

@@ -43,14 +43,17 @@ class qw_index_params(C.Structure):
 
 class qw_query_params(C.Structure):
     _fields_ = [("batch", C.c_int32), ("profile", C.c_int32), ("path", C.c_int32),
-                ("clusters", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("clusters", C.c_int32), ("order", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 QW_PATH_AUTO, QW_PATH_CLUSTER, QW_PATH_LEVELS = 0, 1, 2
 PATHS = {"auto": QW_PATH_AUTO, "cluster": QW_PATH_CLUSTER, "levels": QW_PATH_LEVELS}
-QW_K_PROJECT, QW_K_SETUP, QW_K_LEVEL, QW_K_DECIDE, QW_K_SELECT, QW_K_RERANK, QW_K_CLUSTER = range(7)
-QW_K_COUNT = 7
-KERNEL_CLASSES = ("project", "setup", "level", "decide", "select", "rerank", "cluster")
+QW_ORDER_AUTO, QW_ORDER_SIGNATURE, QW_ORDER_GIVEN = 0, 1, 2
+ORDERS = {"auto": QW_ORDER_AUTO, "signature": QW_ORDER_SIGNATURE, "given": QW_ORDER_GIVEN}
+(QW_K_PROJECT, QW_K_SETUP, QW_K_LEVEL, QW_K_DECIDE, QW_K_SELECT, QW_K_RERANK, QW_K_CLUSTER,
+ QW_K_ORDER) = range(8)
+QW_K_COUNT = 8
+KERNEL_CLASSES = ("project", "setup", "level", "decide", "select", "rerank", "cluster", "order")
 
 
 class qw_profile(C.Structure):
@@ -284,7 +287,8 @@ class Index:
                 "queries": int(p.queries)}
 
     def query(self, Q, k: int, *, batch: int = 0, stats: bool = False, out=None,
-              profile: bool = False, path: str = "auto", clusters: int = 0):
+              profile: bool = False, path: str = "auto", clusters: int = 0,
+              order: str = "auto"):
         """Top-k of every query row.  Returns (ids int64 nq x k, dists float32
         nq x k[, stats int64 nq x QW_NSTAT]) on Q's device (host tensors in,
         host tensors out).  ``out`` may give preallocated (ids, dists[, stats])."""
@@ -304,12 +308,12 @@ class Index:
                   if stats else None)
         mem = _mem_of(Q, ids, dists, st)
         qp = qw_query_params(batch=int(batch), profile=1 if profile else 0, path=PATHS[path],
-                             clusters=int(clusters))
+                             clusters=int(clusters), order=ORDERS[order])
         qw_run_workload(self._h, Q.data_ptr(), nq, int(k), qp, ids.data_ptr(), dists.data_ptr(),
                         st.data_ptr() if st is not None else 0, mem, _stream_of(Q))
         return (ids, dists, st) if stats else (ids, dists)
 
-    def candidates(self, Q, k: int, *, batch: int = 0, path: str = "auto"):
+    def candidates(self, Q, k: int, *, batch: int = 0, path: str = "auto", order: str = "auto"):
         """Kept candidates per query (ascending ids, -1 padded) with their
         collision counts, and the per-query statistics, on Q's device."""
         torch = _torch()
@@ -320,7 +324,7 @@ class Index:
         ccol = torch.empty((nq, cap), dtype=torch.int32, device=Q.device)
         st = torch.empty((nq, QW_NSTAT), dtype=torch.int64, device=Q.device)
         mem = _mem_of(Q, cid, ccol, st)
-        qp = qw_query_params(batch=int(batch), path=PATHS[path])
+        qp = qw_query_params(batch=int(batch), path=PATHS[path], order=ORDERS[order])
         qw_workload_candidates(self._h, Q.data_ptr(), nq, int(k), qp, cid.data_ptr(),
                                ccol.data_ptr(), st.data_ptr(), mem, _stream_of(Q))
         return cid, ccol, st

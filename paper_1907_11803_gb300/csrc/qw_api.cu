@@ -69,7 +69,7 @@ struct qw_index {
     int64_t n_fixups = 0;
     DevBuf X, A, b, o, span, lid, dir_bid, dir_off, dir_start, dir_cnt;
     // workspace for queries (grow-only)
-    DevBuf w_q, w_hq, w_state, w_counters, w_cand, w_out, w_err;
+    DevBuf w_q, w_hq, w_state, w_counters, w_cand, w_out, w_err, w_order, w_qb, w_ob;
     int64_t device_bytes = 0;
     qw_profile prof{};
     std::vector<cudaEvent_t> event_pool;
@@ -363,10 +363,13 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                           cudaStream_t s)
 {
     const bool want_cand = cand_ids != nullptr;
+    const bool want_ids = ids != nullptr;
     const int m = ix->m, d = ix->d;
     const int cap = k + ix->v;
     const int64_t wpq_bytes = (int64_t)ix->nT * kTile;  // counter bytes per query
     const int path = qp ? qp->path : QW_PATH_AUTO;
+    const bool order = !qp || qp->order != QW_ORDER_GIVEN;
+    const bool host = mem == QW_MEM_HOST;
     int csize = 0, tpc = 0;
     const bool fits = cluster_path_fits(ix->view(), &csize, &tpc);
     if (path == QW_PATH_CLUSTER && !fits) {
@@ -381,27 +384,54 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     }
     B = std::min<int64_t>(B, std::max<int64_t>(nq, 1));
     B = std::min<int64_t>(B, 65535);
-    const bool host = mem == QW_MEM_HOST;
+    auto up16 = [](size_t x) { return (x + 15) / 16 * 16; };
 
-    // workspace
-    QW_TRY(ix->w_hq.ensure((size_t)B * m * sizeof(int32_t)));
+    // ---- workspace
+    QW_TRY(ix->w_err.ensure(64));
+    QW_TRY(ix->w_hq.ensure((size_t)nq * m * sizeof(int32_t)));       // bucket ids of all queries
     if (!use_cluster) QW_TRY(ix->w_counters.ensure((size_t)B * wpq_bytes));
     QW_TRY(ix->w_cand.ensure((size_t)B * cap * 2 * sizeof(int32_t)));
-    QW_TRY(ix->w_err.ensure(64));
-    const size_t plan_ints = (size_t)B * ix->nT * (kHistBins + 2) + (size_t)B * 2;
+    const size_t plan_ints = (size_t)B * ix->nT * (kHistBins + 3) + (size_t)B * 2;
     const size_t st_bytes = (size_t)B * m * 8 + (size_t)B * 8 * 16 + plan_ints * 4 + 256;
     QW_TRY(ix->w_state.ensure(st_bytes));
-    // per-batch output staging for host mode: ids, dists, stats, candidates
-    const size_t out_ids = (size_t)B * k * sizeof(int64_t);
-    const size_t out_dists = (size_t)B * k * sizeof(float);
-    const size_t out_stats = (size_t)B * QW_NSTAT * sizeof(int64_t);
-    const size_t out_cids = want_cand ? (size_t)B * cap * sizeof(int64_t) : 0;
-    const size_t out_ccol = want_cand ? (size_t)B * cap * sizeof(int32_t) : 0;
-    auto up16 = [](size_t x) { return (x + 15) / 16 * 16; };
+    // outputs of the whole workload in device memory (the caller's in device mode)
+    const size_t o_ids = want_ids ? (size_t)nq * k * sizeof(int64_t) : 0;
+    const size_t o_dists = want_ids ? (size_t)nq * k * sizeof(float) : 0;
+    const size_t o_stats = stats ? (size_t)nq * QW_NSTAT * sizeof(int64_t) : 0;
+    const size_t o_cids = want_cand ? (size_t)nq * cap * sizeof(int64_t) : 0;
+    const size_t o_ccol = (want_cand && cand_col) ? (size_t)nq * cap * sizeof(int32_t) : 0;
+    const float *Qall = queries;
+    int64_t *f_ids = ids, *f_stats = stats, *f_cids = cand_ids;
+    float *f_dists = dists;
+    int32_t *f_ccol = cand_col;
     if (host) {
-        QW_TRY(ix->w_q.ensure((size_t)B * d * sizeof(float)));
-        QW_TRY(ix->w_out.ensure(up16(out_ids) + up16(out_dists) + up16(out_stats) +
-                                up16(out_cids) + up16(out_ccol)));
+        QW_TRY(ix->w_q.ensure((size_t)nq * d * sizeof(float)));
+        QW_TRY(ix->w_out.ensure(up16(o_ids) + up16(o_dists) + up16(o_stats) + up16(o_cids) +
+                                up16(o_ccol)));
+        char *o = ix->w_out.as<char>();
+        f_ids = want_ids ? reinterpret_cast<int64_t *>(o) : nullptr;
+        o += up16(o_ids);
+        f_dists = want_ids ? reinterpret_cast<float *>(o) : nullptr;
+        o += up16(o_dists);
+        f_stats = stats ? reinterpret_cast<int64_t *>(o) : nullptr;
+        o += up16(o_stats);
+        f_cids = want_cand ? reinterpret_cast<int64_t *>(o) : nullptr;
+        o += up16(o_cids);
+        f_ccol = (want_cand && cand_col) ? reinterpret_cast<int32_t *>(o) : nullptr;
+        Qall = ix->w_q.as<float>();
+    }
+    // per-batch staging when the workload is reordered
+    const size_t b_ids = want_ids ? (size_t)B * k * sizeof(int64_t) : 0;
+    const size_t b_dists = want_ids ? (size_t)B * k * sizeof(float) : 0;
+    const size_t b_stats = stats ? (size_t)B * QW_NSTAT * sizeof(int64_t) : 0;
+    const size_t b_cids = want_cand ? (size_t)B * cap * sizeof(int64_t) : 0;
+    const size_t b_ccol = (want_cand && cand_col) ? (size_t)B * cap * sizeof(int32_t) : 0;
+    if (order) {
+        QW_TRY(ix->w_order.ensure(up16((size_t)nq * 4) * 2 + order_hist_ints() * 4));
+        QW_TRY(ix->w_qb.ensure(up16((size_t)B * d * sizeof(float)) +
+                               up16((size_t)B * m * sizeof(int32_t))));
+        QW_TRY(ix->w_ob.ensure(up16(b_ids) + up16(b_dists) + up16(b_stats) + up16(b_cids) +
+                               up16(b_ccol) + 16));
     }
     QueryState st;
     {
@@ -422,7 +452,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         st.nkeep = reinterpret_cast<int32_t *>(take((size_t)B * 4));
         st.max_top = reinterpret_cast<unsigned long long *>(take(8));
         st.tile_hist = reinterpret_cast<int32_t *>(take((size_t)B * ix->nT * kHistBins * 4));
-        st.tile_plan = reinterpret_cast<int32_t *>(take((size_t)B * ix->nT * 2 * 4));
+        st.tile_plan = reinterpret_cast<int32_t *>(take((size_t)B * ix->nT * 3 * 4));
         st.qplan = reinterpret_cast<int32_t *>(take((size_t)B * 2 * 4));
         if ((size_t)(p - ix->w_state.as<char>()) > ix->w_state.bytes) {
             set_error("internal: query state workspace too small");
@@ -433,114 +463,135 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     st.cand = ix->w_cand.as<int32_t>();
     st.cand_col = st.cand + (size_t)B * cap;
     int *err = ix->w_err.as<int>();
+    int *queue = reinterpret_cast<int *>(ix->w_err.as<char>() + 32);
     const IndexView view = ix->view();
     LaunchTimer tm{ix, s, qp && qp->profile != 0};
 
-    for (int64_t b0 = 0; b0 < nq; b0 += B) {
-        const int nb = (int)std::min<int64_t>(B, nq - b0);
-        const float *Qb;
-        int64_t *ids_b = nullptr, *stats_b = nullptr, *cids_b = nullptr;
-        float *dists_b = nullptr;
-        int32_t *ccol_b = nullptr;
-        if (host) {
-            QW_CUDA_TRY(cudaMemcpyAsync(ix->w_q.p, queries + b0 * d, (size_t)nb * d * sizeof(float),
-                                        cudaMemcpyHostToDevice, s));
-            Qb = ix->w_q.as<float>();
-            char *o = ix->w_out.as<char>();
-            ids_b = reinterpret_cast<int64_t *>(o);
-            dists_b = reinterpret_cast<float *>(o + up16(out_ids));
-            char *o2 = o + up16(out_ids) + up16(out_dists);
-            if (stats) stats_b = reinterpret_cast<int64_t *>(o2);
-            o2 += up16(out_stats);
-            if (want_cand) cids_b = reinterpret_cast<int64_t *>(o2);
-            o2 += up16(out_cids);
-            if (want_cand && cand_col) ccol_b = reinterpret_cast<int32_t *>(o2);
-        } else {
-            Qb = queries + b0 * d;
-            if (ids) ids_b = ids + b0 * k;
-            if (dists) dists_b = dists + b0 * k;
-            stats_b = stats ? stats + b0 * QW_NSTAT : nullptr;
-            if (want_cand) cids_b = cand_ids + b0 * cap;
-            if (want_cand && cand_col) ccol_b = cand_col + b0 * cap;
-        }
-        QW_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-        QW_TRY(tm.run(QW_K_PROJECT, 2, [&] {
-            return launch_hash(Qb, nb, d, ix->A.as<float>(), ix->b.as<float>(), m, ix->w,
-                               ix->w_hq.as<int32_t>(), m, 1, err, nullptr, s);
-        }));
-        if (use_cluster) {
-            int used = 0;
-            QW_CUDA_TRY(cudaMemsetAsync(st.nkeep, 0, (size_t)nb * sizeof(int32_t), s));
-            QW_TRY(tm.run(QW_K_CLUSTER, 1, [&] {
-                return launch_cluster_query(view, ix->w_hq.as<int32_t>(), nb, ix->l, ix->c, cap,
-                                            csize, tpc, qp ? qp->clusters : 0, st,
-                                            reinterpret_cast<int *>(ix->w_err.as<char>() + 32),
-                                            stats_b, err, s, &used);
-            }));
-            int h_err = 0;
-            QW_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-            QW_CUDA_TRY(cudaStreamSynchronize(s));
-            if (h_err & 2) {
-                set_error("qw_run_workload: a query bucket id falls outside int32");
-                return QW_ERR_RANGE;
-            }
-            if (h_err & 4) {
-                set_error("qw_run_workload: a staged-copy wait in the cluster kernel gave up");
-                return QW_ERR_TIMEOUT;
-            }
-        } else {
-        QW_TRY(tm.run(QW_K_SETUP, 1, [&] { return launch_query_setup(view, ix->w_hq.as<int32_t>(), nb, st, s); }));
-        unsigned long long max_top = 0;
+    // ---- the whole workload: copy in (host mode), hash, order
+    if (host)
+        QW_CUDA_TRY(cudaMemcpyAsync(ix->w_q.p, queries, (size_t)nq * d * sizeof(float),
+                                    cudaMemcpyHostToDevice, s));
+    int32_t *HQall = ix->w_hq.as<int32_t>();
+    QW_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+    QW_TRY(tm.run(QW_K_PROJECT, 2, [&] {
+        return launch_hash(Qall, nq, d, ix->A.as<float>(), ix->b.as<float>(), m, ix->w, HQall, m, 1,
+                           err, nullptr, s);
+    }));
+    int32_t *perm = nullptr;
+    if (order) {
+        char *o = ix->w_order.as<char>();
+        perm = reinterpret_cast<int32_t *>(o);
+        uint32_t *keys = reinterpret_cast<uint32_t *>(o + up16((size_t)nq * 4));
+        int32_t *hist = reinterpret_cast<int32_t *>(o + 2 * up16((size_t)nq * 4));
+        QW_TRY(tm.run(QW_K_ORDER, 3, [&] { return launch_order(HQall, nq, view, keys, hist, perm, s); }));
+    }
+    {
         int h_err = 0;
-        QW_CUDA_TRY(cudaMemcpyAsync(&max_top, st.max_top, sizeof(max_top), cudaMemcpyDeviceToHost, s));
         QW_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
         QW_CUDA_TRY(cudaStreamSynchronize(s));
         if (h_err & 2) {
             set_error("qw_run_workload: a query bucket id falls outside int32");
             return QW_ERR_RANGE;
         }
-        // levels 0..L where c^L > max_top: afterwards every query has stopped
-        int64_t R = 1, Rp = 1;
-        for (int level = 0;; ++level) {
-            QW_TRY(tm.run(QW_K_LEVEL, 1, [&] { return launch_level(view, nb, level, R, Rp, ix->l, st, s); }));
-            QW_TRY(tm.run(QW_K_DECIDE, 1, [&] { return launch_decide(nb, level, R, cap, st, s); }));
-            if ((unsigned long long)R > max_top) break;
-            if (level > 62) {
-                set_error("qw_run_workload: level limit reached");
+    }
+
+    for (int64_t b0 = 0; b0 < nq; b0 += B) {
+        const int nb = (int)std::min<int64_t>(B, nq - b0);
+        const float *Qb;
+        const int32_t *HQb;
+        int64_t *ids_b = nullptr, *stats_b = nullptr, *cids_b = nullptr;
+        float *dists_b = nullptr;
+        int32_t *ccol_b = nullptr;
+        if (order) {
+            float *qb = ix->w_qb.as<float>();
+            int32_t *hqb = reinterpret_cast<int32_t *>(ix->w_qb.as<char>() +
+                                                       up16((size_t)B * d * sizeof(float)));
+            QW_TRY(tm.run(QW_K_ORDER, 1, [&] {
+                return launch_gather(Qall, HQall, perm, b0, nb, d, m, qb, hqb, s);
+            }));
+            Qb = qb;
+            HQb = hqb;
+            char *o = ix->w_ob.as<char>();
+            if (want_ids) ids_b = reinterpret_cast<int64_t *>(o);
+            o += up16(b_ids);
+            if (want_ids) dists_b = reinterpret_cast<float *>(o);
+            o += up16(b_dists);
+            if (stats) stats_b = reinterpret_cast<int64_t *>(o);
+            o += up16(b_stats);
+            if (want_cand) cids_b = reinterpret_cast<int64_t *>(o);
+            o += up16(b_cids);
+            if (want_cand && cand_col) ccol_b = reinterpret_cast<int32_t *>(o);
+        } else {
+            Qb = Qall + b0 * d;
+            HQb = HQall + b0 * m;
+            if (want_ids) {
+                ids_b = f_ids + b0 * k;
+                dists_b = f_dists + b0 * k;
+            }
+            if (stats) stats_b = f_stats + b0 * QW_NSTAT;
+            if (want_cand) cids_b = f_cids + b0 * cap;
+            if (want_cand && cand_col) ccol_b = f_ccol + b0 * cap;
+        }
+        if (use_cluster) {
+            int used = 0;
+            QW_CUDA_TRY(cudaMemsetAsync(st.nkeep, 0, (size_t)nb * sizeof(int32_t), s));
+            QW_TRY(tm.run(QW_K_CLUSTER, 1, [&] {
+                return launch_cluster_query(view, HQb, nb, ix->l, ix->c, cap, csize, tpc,
+                                            qp ? qp->clusters : 0, st, queue, stats_b, err, s,
+                                            &used);
+            }));
+            int h_err = 0;
+            QW_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            QW_CUDA_TRY(cudaStreamSynchronize(s));
+            if (h_err & 4) {
+                set_error("qw_run_workload: a staged-copy wait in the cluster kernel gave up");
                 return QW_ERR_TIMEOUT;
             }
-            Rp = R;
-            R *= ix->c;
-        }
-        QW_TRY(tm.run(QW_K_SELECT, 2, [&] { return launch_collect(view, nb, ix->l, cap, st, stats_b, s); }));
+        } else {
+            QW_TRY(tm.run(QW_K_SETUP, 1, [&] { return launch_query_setup(view, HQb, nb, st, s); }));
+            unsigned long long max_top = 0;
+            QW_CUDA_TRY(cudaMemcpyAsync(&max_top, st.max_top, sizeof(max_top),
+                                        cudaMemcpyDeviceToHost, s));
+            QW_CUDA_TRY(cudaStreamSynchronize(s));
+            // levels 0..L where c^L > max_top: afterwards every query has stopped
+            int64_t R = 1, Rp = 1;
+            for (int level = 0;; ++level) {
+                QW_TRY(tm.run(QW_K_LEVEL, 1, [&] { return launch_level(view, nb, level, R, Rp, ix->l, st, s); }));
+                QW_TRY(tm.run(QW_K_DECIDE, 1, [&] { return launch_decide(nb, level, R, cap, st, s); }));
+                if ((unsigned long long)R > max_top) break;
+                if (level > 62) {
+                    set_error("qw_run_workload: level limit reached");
+                    return QW_ERR_TIMEOUT;
+                }
+                Rp = R;
+                R *= ix->c;
+            }
+            QW_TRY(tm.run(QW_K_SELECT, 2, [&] { return launch_collect(view, nb, ix->l, cap, st, stats_b, s); }));
         }
         if (want_cand)
             QW_TRY(tm.run(QW_K_SELECT, 1, [&] { return launch_candidates_out(st, nb, cap, cids_b, ccol_b, s); }));
-        if (ids)
+        if (want_ids)
             QW_TRY(tm.run(QW_K_RERANK, 1, [&] { return launch_rerank(view, Qb, nb, k, cap, st, ids_b, dists_b, s); }));
-        if (host) {
-            if (ids) {
-                QW_CUDA_TRY(cudaMemcpyAsync(ids + b0 * k, ids_b, (size_t)nb * k * sizeof(int64_t),
-                                            cudaMemcpyDeviceToHost, s));
-                QW_CUDA_TRY(cudaMemcpyAsync(dists + b0 * k, dists_b, (size_t)nb * k * sizeof(float),
-                                            cudaMemcpyDeviceToHost, s));
-            }
-            if (stats)
-                QW_CUDA_TRY(cudaMemcpyAsync(stats + b0 * QW_NSTAT, stats_b,
-                                            (size_t)nb * QW_NSTAT * sizeof(int64_t),
-                                            cudaMemcpyDeviceToHost, s));
-            if (want_cand) {
-                QW_CUDA_TRY(cudaMemcpyAsync(cand_ids + b0 * cap, cids_b,
-                                            (size_t)nb * cap * sizeof(int64_t),
-                                            cudaMemcpyDeviceToHost, s));
-                if (cand_col)
-                    QW_CUDA_TRY(cudaMemcpyAsync(cand_col + b0 * cap, ccol_b,
-                                                (size_t)nb * cap * sizeof(int32_t),
-                                                cudaMemcpyDeviceToHost, s));
-            }
+        if (order) {
+            QW_TRY(tm.run(QW_K_ORDER, 1, [&] {
+                return launch_scatter(perm, b0, nb, k, cap, ids_b, dists_b, stats_b, cids_b, ccol_b,
+                                      f_ids, f_dists, f_stats, f_cids, f_ccol, s);
+            }));
         }
     }
-    if (host) QW_CUDA_TRY(cudaStreamSynchronize(s));
+    if (host) {
+        if (want_ids) {
+            QW_CUDA_TRY(cudaMemcpyAsync(ids, f_ids, o_ids, cudaMemcpyDeviceToHost, s));
+            QW_CUDA_TRY(cudaMemcpyAsync(dists, f_dists, o_dists, cudaMemcpyDeviceToHost, s));
+        }
+        if (stats) QW_CUDA_TRY(cudaMemcpyAsync(stats, f_stats, o_stats, cudaMemcpyDeviceToHost, s));
+        if (want_cand) {
+            QW_CUDA_TRY(cudaMemcpyAsync(cand_ids, f_cids, o_cids, cudaMemcpyDeviceToHost, s));
+            if (cand_col)
+                QW_CUDA_TRY(cudaMemcpyAsync(cand_col, f_ccol, o_ccol, cudaMemcpyDeviceToHost, s));
+        }
+        QW_CUDA_TRY(cudaStreamSynchronize(s));
+    }
     QW_TRY(tm.finish());
     ix->prof.queries += nq;
     return QW_OK;
@@ -560,7 +611,9 @@ static qw_status check_workload_args(const qw_index *ix, const float *queries, i
         if (qp->path < QW_PATH_AUTO || qp->path > QW_PATH_LEVELS)
             return arg_error("qw_run_workload: unknown path");
         if (qp->clusters < 0) return arg_error("qw_run_workload: clusters < 0");
-        for (int r = 0; r < 4; ++r)
+        if (qp->order < QW_ORDER_AUTO || qp->order > QW_ORDER_GIVEN)
+            return arg_error("qw_run_workload: unknown order");
+        for (int r = 0; r < 3; ++r)
             if (qp->reserved[r] != 0) return arg_error("qw_run_workload: reserved field set");
     }
     return QW_OK;
@@ -657,7 +710,8 @@ void qw_index_free(qw_index *ix)
     cudaDeviceSynchronize();
     DevBuf *bufs[] = {&ix->X, &ix->A, &ix->b, &ix->o, &ix->span, &ix->lid, &ix->dir_bid,
                       &ix->dir_off, &ix->dir_start, &ix->dir_cnt, &ix->w_q, &ix->w_hq,
-                      &ix->w_state, &ix->w_counters, &ix->w_cand, &ix->w_out, &ix->w_err};
+                      &ix->w_state, &ix->w_counters, &ix->w_cand, &ix->w_out, &ix->w_err,
+                      &ix->w_order, &ix->w_qb, &ix->w_ob};
     for (DevBuf *bb : bufs) bb->release();
     for (cudaEvent_t e : ix->event_pool) cudaEventDestroy(e);
     delete ix;

@@ -114,7 +114,8 @@ struct QueryState {
     int32_t *cand;          // nb x cap
     int32_t *cand_col;      // nb x cap
     int32_t *tile_hist;     // nb x nT x kHistBins
-    int32_t *tile_plan;     // nb x nT x 2: first output slot, count-c* ids before the tile
+    int32_t *tile_plan;     // nb x nT x 3: first output slot, count-c* ids before the tile,
+                            //   ids kept in the tile
     int32_t *qplan;         // nb x 2: c*, how many count-c* ids are kept
 };
 
@@ -130,6 +131,15 @@ qw_status launch_cluster_query(const IndexView &ix, const int32_t *HQ, int nq, i
                                int cap, int cluster_size, int tpc, int max_clusters,
                                QueryState &st, int *queue, int64_t *stats_out, int *err,
                                cudaStream_t s, int *clusters_used);
+size_t order_hist_ints();
+qw_status launch_order(const int32_t *HQ, int64_t nq, const IndexView &ix, uint32_t *keys,
+                       int32_t *hist, int32_t *perm, cudaStream_t s);
+qw_status launch_gather(const float *Q, const int32_t *HQ, const int32_t *perm, int64_t b0, int nb,
+                        int d, int m, float *Qb, int32_t *HQb, cudaStream_t s);
+qw_status launch_scatter(const int32_t *perm, int64_t b0, int nb, int k, int cap,
+                         const int64_t *ids_b, const float *dists_b, const int64_t *stats_b,
+                         const int64_t *cids_b, const int32_t *ccol_b, int64_t *ids, float *dists,
+                         int64_t *stats, int64_t *cids, int32_t *ccol, cudaStream_t s);
 qw_status launch_candidates_out(const QueryState &st, int nb, int cap, int64_t *cand_ids,
                                 int32_t *cand_col, cudaStream_t s);
 qw_status launch_rerank(const IndexView &ix, const float *Qb, int nb, int k, int cap,

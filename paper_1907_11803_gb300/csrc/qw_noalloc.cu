@@ -62,7 +62,7 @@ size_t batch_bytes(size_t B, int m, int nT, int cap)
     total += 7 * up(B * sizeof(int32_t));            // active, ncand, nprev, cross, term, levels, nkeep
     total += up(B * (size_t)nT * kTile);             // collision counters
     total += up(B * (size_t)nT * kHistBins * 4);     // per-tile candidate profiles
-    total += up(B * (size_t)nT * 2 * 4);             // per-tile emit plan
+    total += up(B * (size_t)nT * 3 * 4);             // per-tile emit plan
     total += up(B * 2 * 4);                          // per-query plan
     total += 2 * up(B * (size_t)cap * 4);            // candidate ids and counts
     return total;
@@ -139,7 +139,7 @@ extern "C" qw_status qw_run_workload_noalloc(qw_index *index, const float *queri
     st.nkeep = reinterpret_cast<int32_t *>(take(B * 4));
     st.counters = reinterpret_cast<uint32_t *>(take(B * (size_t)nT * kTile));
     st.tile_hist = reinterpret_cast<int32_t *>(take(B * (size_t)nT * kHistBins * 4));
-    st.tile_plan = reinterpret_cast<int32_t *>(take(B * (size_t)nT * 2 * 4));
+    st.tile_plan = reinterpret_cast<int32_t *>(take(B * (size_t)nT * 3 * 4));
     st.qplan = reinterpret_cast<int32_t *>(take(B * 2 * 4));
     st.cand = reinterpret_cast<int32_t *>(take(B * (size_t)cap * 4));
     st.cand_col = reinterpret_cast<int32_t *>(take(B * (size_t)cap * 4));

@@ -327,8 +327,9 @@ __global__ void __launch_bounds__(CL_THREADS) select_plan_kernel(
         int kept_tot;
         const int out_ex = out_base + block_exclusive_scan<CL_THREADS>(kept, scan_tmp, &kept_tot);
         if (t < nT) {
-            st.tile_plan[((int64_t)q * nT + t) * 2 + 0] = out_ex;
-            st.tile_plan[((int64_t)q * nT + t) * 2 + 1] = eq_ex;
+            st.tile_plan[((int64_t)q * nT + t) * 3 + 0] = out_ex;
+            st.tile_plan[((int64_t)q * nT + t) * 3 + 1] = eq_ex;
+            st.tile_plan[((int64_t)q * nT + t) * 3 + 2] = kept;
         }
         eq_base += eq_tot;
         out_base += kept_tot;
@@ -359,65 +360,86 @@ __global__ void __launch_bounds__(CL_THREADS) select_plan_kernel(
 }
 
 // Emit the kept ids of one (tile, query) in ascending order at the tile's
-// planned position.
+// planned position.  Each thread owns 128 consecutive ids of the tile, so one
+// pair of block scans orders the whole tile.
+constexpr int EM_PER = kTile / CL_THREADS;  // ids per thread
+
 __global__ void __launch_bounds__(CL_THREADS) select_emit_kernel(
     int64_t n, int nT, int l, int cap, QueryState st, int64_t words_per_query)
 {
     __shared__ int scan_tmp[CL_THREADS / 32];
     const int t = blockIdx.x;
     const int q = blockIdx.y;
-    const int *th = st.tile_hist + ((int64_t)q * nT + t) * kHistBins;
     const int cstar = st.qplan[q * 2 + 0], take_eq = st.qplan[q * 2 + 1];
-    // nothing kept in this tile: skip reading its counters
-    int any = th[0];
-    for (int c = max(cstar, l); c < kHistBins - 1 && !any; ++c) any = th[1 + c];
-    if (!any) return;
-    const int out0 = st.tile_plan[((int64_t)q * nT + t) * 2 + 0];
-    int rank = st.tile_plan[((int64_t)q * nT + t) * 2 + 1];
+    const int *plan = st.tile_plan + ((int64_t)q * nT + t) * 3;
+    if (plan[2] == 0) return;  // nothing kept in this tile: skip its counters
+    const int out0 = plan[0];
+    const int eq0 = plan[1];
     const int64_t tbase = (int64_t)t * kTile;
-    const int len = (int)min((int64_t)kTile, n - tbase);
-    const uint8_t *cb = reinterpret_cast<const uint8_t *>(st.counters + (int64_t)q * words_per_query) + tbase;
-    int out_base = out0;
-    for (int chunk = 0; chunk < len; chunk += CL_THREADS * CL_PER) {
-        const int base = chunk + threadIdx.x * CL_PER;
-        uint4 v4 = make_uint4(0, 0, 0, 0);
-        if (base < len) v4 = *reinterpret_cast<const uint4 *>(cb + base);
-        const uint8_t *bytes = reinterpret_cast<const uint8_t *>(&v4);
-        int n_eq = 0;
+    // counters are allocated for whole tiles; ids past n hold zero
+    const uint4 *cb = reinterpret_cast<const uint4 *>(
+        reinterpret_cast<const uint8_t *>(st.counters + (int64_t)q * words_per_query) + tbase +
+        (int64_t)threadIdx.x * EM_PER);
+    const uint32_t lrep = (uint32_t)l * 0x01010101u;
+    uint4 v[EM_PER / 16];
+    bool mine = false;
 #pragma unroll
-        for (int u = 0; u < CL_PER; ++u) {
-            const int c = bytes[u] & 0x7f;
-            n_eq += (c == cstar && c >= l && !(bytes[u] & 0x80)) ? 1 : 0;
-        }
-        int eq_total;
-        int r = rank + block_exclusive_scan<CL_THREADS>(n_eq, scan_tmp, &eq_total);
-        uint16_t selmask = 0;
-        int n_sel = 0;
-#pragma unroll
-        for (int u = 0; u < CL_PER; ++u) {
-            const int c = bytes[u] & 0x7f;
-            bool sel = false;
-            if (c >= l) {
-                if ((bytes[u] & 0x80) || c > cstar) sel = true;
-                else if (c == cstar) { sel = r < take_eq; ++r; }
-            }
-            if (sel) { selmask |= (uint16_t)(1u << u); ++n_sel; }
-        }
-        int sel_total;
-        int pos = out_base + block_exclusive_scan<CL_THREADS>(n_sel, scan_tmp, &sel_total);
-#pragma unroll
-        for (int u = 0; u < CL_PER; ++u) {
-            if (selmask & (1u << u)) {
-                if (pos < cap) {
-                    st.cand[(int64_t)q * cap + pos] = (int32_t)(tbase + base + u);
-                    st.cand_col[(int64_t)q * cap + pos] = bytes[u] & 0x7f;
-                }
-                ++pos;
-            }
-        }
-        rank += eq_total;
-        out_base += sel_total;
+    for (int u = 0; u < EM_PER / 16; ++u) {
+        v[u] = cb[u];
+        mine |= (count_ge(v[u].x, lrep) | count_ge(v[u].y, lrep) | count_ge(v[u].z, lrep) |
+                 count_ge(v[u].w, lrep)) != 0;
     }
+    int n_eq = 0;
+    if (mine && cstar >= l) {
+#pragma unroll
+        for (int u = 0; u < EM_PER / 16; ++u) {
+            const uint8_t *bytes = reinterpret_cast<const uint8_t *>(&v[u]);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                n_eq += ((bytes[j] & 0x7f) == cstar && !(bytes[j] & 0x80)) ? 1 : 0;
+        }
+    }
+    int eq_total;
+    int r = eq0 + block_exclusive_scan<CL_THREADS>(n_eq, scan_tmp, &eq_total);
+    int n_sel = 0;
+    if (mine) {
+        int rr = r;
+#pragma unroll
+        for (int u = 0; u < EM_PER / 16; ++u) {
+            const uint8_t *bytes = reinterpret_cast<const uint8_t *>(&v[u]);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int c = bytes[j] & 0x7f;
+                if (c < l) continue;
+                if ((bytes[j] & 0x80) || c > cstar) ++n_sel;
+                else if (c == cstar) { n_sel += (rr < take_eq) ? 1 : 0; ++rr; }
+            }
+        }
+    }
+    int sel_total;
+    int pos = out0 + block_exclusive_scan<CL_THREADS>(n_sel, scan_tmp, &sel_total);
+    if (!mine) return;
+    const int64_t id0 = tbase + (int64_t)threadIdx.x * EM_PER;
+#pragma unroll
+    for (int u = 0; u < EM_PER / 16; ++u) {
+        const uint8_t *bytes = reinterpret_cast<const uint8_t *>(&v[u]);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int c = bytes[j] & 0x7f;
+            if (c < l) continue;
+            bool sel;
+            if ((bytes[j] & 0x80) || c > cstar) sel = true;
+            else if (c == cstar) { sel = r < take_eq; ++r; }
+            else sel = false;
+            if (!sel) continue;
+            if (pos < cap) {
+                st.cand[(int64_t)q * cap + pos] = (int32_t)(id0 + u * 16 + j);
+                st.cand_col[(int64_t)q * cap + pos] = c;
+            }
+            ++pos;
+        }
+    }
+    (void)n;
 }
 
 __global__ void candidates_out_kernel(const int32_t *__restrict__ cand,

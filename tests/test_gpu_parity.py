@@ -51,7 +51,8 @@ def _check_candidates(cid, ccol, ref_cid, ref_ccol):
         assert np.array_equal(ccol[q][: got.size], want_col), f"counts differ on query {q}"
 
 
-def _gpu_workload(qw, dev, X, Q, A, b, *, w, k, v, l, c=2, batch=0, host=False, path="auto"):
+def _gpu_workload(qw, dev, X, Q, A, b, *, w, k, v, l, c=2, batch=0, host=False, path="auto",
+                  order="auto"):
     import torch
     if host:
         Xd, Ad, bd = (torch.from_numpy(np.ascontiguousarray(a)) for a in (X, A, b))
@@ -59,8 +60,8 @@ def _gpu_workload(qw, dev, X, Q, A, b, *, w, k, v, l, c=2, batch=0, host=False, 
     else:
         Xd, Qd, Ad, bd = _t(X, dev), _t(Q, dev), _t(A, dev), _t(b, dev)
     index = qw.Index(Xd, Ad, bd, w=w, c=c, v=v, l=l)
-    ids, dists, st = index.query(Qd, k, batch=batch, stats=True, path=path)
-    cid, ccol, st2 = index.candidates(Qd, k, batch=batch, path=path)
+    ids, dists, st = index.query(Qd, k, batch=batch, stats=True, path=path, order=order)
+    cid, ccol, st2 = index.candidates(Qd, k, batch=batch, path=path, order=order)
     torch.cuda.synchronize()
     out = dict(ids=ids.cpu().numpy(), dists=dists.cpu().numpy(), stats=st.cpu().numpy(),
                cid=cid.cpu().numpy(), ccol=ccol.cpu().numpy(), stats2=st2.cpu().numpy(),
@@ -69,13 +70,13 @@ def _gpu_workload(qw, dev, X, Q, A, b, *, w, k, v, l, c=2, batch=0, host=False, 
 
 
 def _full_parity(orc, qw, dev, X, Q, A, b, *, w, k, v, l=None, c=2, batch=0, host=False,
-                 path="auto"):
+                 path="auto", order="auto"):
     n = X.shape[0]
     if l is None:
         l = orc.threshold(A.shape[0], w, c, n, v)
     H, HQ, oidx, ref = _oracle_run(orc, X, Q, A, b, w, k, v, l, c)
     g = _gpu_workload(qw, dev, X, Q, A, b, w=w, k=k, v=v, l=l, c=c, batch=batch, host=host,
-                      path=path)
+                      path=path, order=order)
     _check_results(g["ids"], g["dists"], ref["ids"], ref["dists"])
     assert np.array_equal(g["stats"], ref["stats"]), "per-query statistics differ"
     assert np.array_equal(g["stats2"], ref["stats"])
@@ -150,12 +151,15 @@ def test_workload_small_config(orc, qwlib, cuda, path):
 
 
 @PATHS
-def test_workload_ragged_tiles_and_batches(orc, qwlib, cuda, path):
+@pytest.mark.parametrize("order", ["given", "signature"])
+def test_workload_ragged_tiles_and_batches(orc, qwlib, cuda, path, order):
     """Three index tiles (the last one ragged), small k + v so the truncation
-    and its tie rule run, several query batches with a ragged last batch."""
+    and its tie rule run, several query batches with a ragged last batch, in
+    the caller's order and in signature order."""
     wl = workloads.make_workload("mix10k_d32", seed=11, n=2 * TILE + 777, nq=61, d=24, m=12,
                                  n_clusters=40)
-    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=7, v=20, batch=13, path=path)
+    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=7, v=20, batch=13, path=path,
+                 order=order)
 
 
 @PATHS
@@ -280,10 +284,10 @@ def test_full_size_sampled(orc, qwlib, cuda):
     index = qwlib.Index(_t(wl.X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=s.w, c=s.c, v=s.v, l=l)
     Qd = _t(wl.Q, cuda)
     ids, dists, st = index.query(Qd, s.k, stats=True)
-    ids2, dists2, st2 = index.query(Qd, s.k, stats=True, path="levels")
+    ids2, dists2, st2 = index.query(Qd, s.k, stats=True, path="levels", order="given")
     torch.cuda.synchronize()
     ids, dists, st = ids.cpu().numpy(), dists.cpu().numpy(), st.cpu().numpy()
-    # the two execution paths agree on every query
+    # the two execution paths and the two query orders agree on every query
     assert np.array_equal(ids, ids2.cpu().numpy())
     assert np.array_equal(st, st2.cpu().numpy())
     assert np.array_equal(dists, dists2.cpu().numpy())
