@@ -82,6 +82,8 @@ typedef struct {
     int32_t l;     /* collision threshold 1..m; 0 = derive from Eq. 1 (see
                       qw_collision_threshold) with beta = v / n */
     float delta;   /* error probability used when deriving l; <= 0 means 1/e (Section 6) */
+    int32_t shadow_bf16;  /* non-zero: also keep a BF16 copy of the data and row-norm bounds,
+                             for the QW_RERANK_BF16 pre-filter (2 * n * d + 4 * n bytes) */
 } qw_index_params;
 
 /* Per-workload options.  Zero-initialise; unknown non-zero fields are rejected. */
@@ -96,8 +98,29 @@ typedef struct {
                              coarse bucket signature (queries of one region share index
                              entries in L2); QW_ORDER_GIVEN: in the caller's order.  Results are
                              returned in the caller's order either way and do not depend on it */
-    int32_t reserved[3];  /* must be zero */
+    int32_t rerank;       /* QW_RERANK_FP32 (default) or QW_RERANK_BF16 (needs shadow_bf16) */
+    int32_t start;        /* QW_START_PLAIN (default) or QW_START_LEARNED (level path; needs a
+                             start model, see qw_index_set_start_model) */
+    int32_t reserved[1];  /* must be zero */
 } qw_query_params;
+
+/* First level of the collision-counting loop.  QW_START_PLAIN: every query
+ * starts at radius R = 1.  QW_START_LEARNED: the index's start model predicts,
+ * per query, the level at which it stops; the query begins at the largest
+ * level s whose predicted probability of stopping at or before s is at most
+ * eps, counting its whole bucket range there.  A query that nevertheless stops
+ * at its first level is answered again from R = 1, so the results (ids,
+ * distances, statistics) equal the plain ones. */
+#define QW_START_PLAIN 0
+#define QW_START_LEARNED 1
+
+/* Candidate distance stage.  QW_RERANK_FP32: FP32 distances of every kept
+ * candidate, FP64 for neighbours FP32 cannot order.  QW_RERANK_BF16: distances
+ * from the BF16 copy first, with a proven error bound; only candidates that
+ * could still be among the k nearest go through the FP32/FP64 stage.  Both
+ * return the same ids and distances. */
+#define QW_RERANK_FP32 0
+#define QW_RERANK_BF16 1
 
 #define QW_ORDER_AUTO 0
 #define QW_ORDER_SIGNATURE 1
@@ -125,7 +148,8 @@ typedef struct {
 #define QW_K_CLUSTER 6   /* cluster path: every level, the stop test and the selection of a
                             query in one persistent launch */
 #define QW_K_ORDER 7     /* workload ordering: signature sort, gather, scatter of results */
-#define QW_K_COUNT 8
+#define QW_K_START 8     /* learned start levels: features + network forward */
+#define QW_K_COUNT 9
 
 /* Launch counts and (profile mode) summed kernel times of qw_run_workload /
  * qw_workload_candidates calls on one index since the last reset. */
@@ -134,6 +158,10 @@ typedef struct {
     double ms[QW_K_COUNT];         /* summed CUDA-event durations, per class (profile mode) */
     int64_t timed_launches[QW_K_COUNT];  /* launches included in ms[] */
     int64_t queries;               /* queries answered */
+    int64_t rerank_candidates;     /* kept candidates reranked (profile mode) */
+    int64_t rerank_fp32_rows;      /* of those, read in FP32 (profile mode; BF16 pre-filter) */
+    int64_t start_levels_skipped;  /* levels skipped by learned starts (always counted) */
+    int64_t start_fallbacks;       /* queries recomputed from R = 1 (always counted) */
 } qw_profile;
 
 typedef struct {
@@ -264,6 +292,44 @@ qw_status qw_run_workload_noalloc(qw_index *index, const float *queries, int64_t
 /* Copy the index's profile counters into *out (host); reset them afterwards
  * when `reset` is non-zero. */
 qw_status qw_index_profile(qw_index *index, qw_profile *out, int32_t reset);
+
+/* ---- The learned start model (a13 of the path; the paper trains an offline
+ * model for its cache split in Section 5.2 but prints no network).
+ * A multilayer perceptron n_in -> hidden -> hidden -> classes with ReLU,
+ * softmax cross-entropy, FP16 weight copies of FP32 master weights and FP32
+ * accumulation; trained with Adam by the library's kernels.  Parameters are a
+ * flat float array: W1 (hidden x n_in, row-major), b1, W2 (hidden x hidden),
+ * b2, W3 (classes x hidden), b3.  The caller provides the initial values (the
+ * random draws of the method are inputs). */
+typedef struct qw_mlp qw_mlp;
+
+qw_status qw_mlp_create(int32_t n_in, int32_t hidden, int32_t classes, qw_mlp **out);
+int64_t qw_mlp_param_count(const qw_mlp *mlp);
+/* Host arrays of qw_mlp_param_count floats; set_params also resets Adam. */
+qw_status qw_mlp_set_params(qw_mlp *mlp, const float *params, int64_t count);
+qw_status qw_mlp_get_params(const qw_mlp *mlp, float *params, int64_t count);
+/* Mean loss (host *loss) and its gradient (host grad, optional) over n rows:
+ * X DEVICE n x n_in float32, y DEVICE n int32 class labels. */
+qw_status qw_mlp_loss_grad(qw_mlp *mlp, const float *X, const int32_t *y, int64_t n, float *loss,
+                           float *grad, void *stream);
+/* Adam (beta 0.9 / 0.999) over the rows in order, `batch` rows per step;
+ * *final_loss (host, optional) = mean loss of the last epoch. */
+qw_status qw_mlp_train(qw_mlp *mlp, const float *X, const int32_t *y, int64_t n, int32_t epochs,
+                       int32_t batch, float lr, float *final_loss, void *stream);
+/* Class probabilities (DEVICE n x classes) of DEVICE rows X. */
+qw_status qw_mlp_predict(qw_mlp *mlp, const float *X, int64_t n, float *prob, void *stream);
+void qw_mlp_free(qw_mlp *mlp);
+
+/* Features of queries for the start model (DEVICE pointers): per query its
+ * d coordinates divided by the data's RMS coordinate, then for each of the m
+ * projections its position in the data's bucket-id range, (g + 0.5) /
+ * (span + 1) - 0.5 clamped to [-1.5, 1.5]; F is nq x (d + m). */
+qw_status qw_query_features(qw_index *index, const float *queries, int64_t nq, float *F,
+                            void *stream);
+/* Attach a start model (not owned; it must outlive its use) with classes =
+ * level index 0, 1, ...; eps in (0, 1) bounds the predicted probability of
+ * starting too late.  NULL detaches. */
+qw_status qw_index_set_start_model(qw_index *index, qw_mlp *mlp, float eps);
 
 /* Copy index metadata into *info (host). */
 qw_status qw_index_get_info(const qw_index *index, qw_index_info *info);

@@ -33,32 +33,42 @@ STAT_FIELDS = ("levels", "final_R", "n_cand_raw", "n_cand", "term", "scanned_las
 EXPORTED = ("qw_version", "qw_last_error", "qw_collision_probability",
             "qw_collision_threshold", "qw_hash", "qw_build_index", "qw_run_workload",
             "qw_workload_candidates", "qw_run_workload_noalloc", "qw_index_profile",
-            "qw_index_get_info", "qw_index_export", "qw_index_free")
+            "qw_index_get_info", "qw_mlp_create", "qw_mlp_param_count", "qw_mlp_set_params",
+            "qw_mlp_get_params", "qw_mlp_loss_grad", "qw_mlp_train", "qw_mlp_predict",
+            "qw_mlp_free", "qw_query_features", "qw_index_set_start_model", "qw_index_export", "qw_index_free")
 
 
 class qw_index_params(C.Structure):
     _fields_ = [("m", C.c_int32), ("w", C.c_float), ("c", C.c_int32), ("v", C.c_int32),
-                ("l", C.c_int32), ("delta", C.c_float)]
+                ("l", C.c_int32), ("delta", C.c_float), ("shadow_bf16", C.c_int32)]
 
 
 class qw_query_params(C.Structure):
     _fields_ = [("batch", C.c_int32), ("profile", C.c_int32), ("path", C.c_int32),
-                ("clusters", C.c_int32), ("order", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("clusters", C.c_int32), ("order", C.c_int32), ("rerank", C.c_int32),
+                ("start", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 QW_PATH_AUTO, QW_PATH_CLUSTER, QW_PATH_LEVELS = 0, 1, 2
 PATHS = {"auto": QW_PATH_AUTO, "cluster": QW_PATH_CLUSTER, "levels": QW_PATH_LEVELS}
 QW_ORDER_AUTO, QW_ORDER_SIGNATURE, QW_ORDER_GIVEN = 0, 1, 2
+QW_RERANK_FP32, QW_RERANK_BF16 = 0, 1
+RERANKS = {"fp32": QW_RERANK_FP32, "bf16": QW_RERANK_BF16}
 ORDERS = {"auto": QW_ORDER_AUTO, "signature": QW_ORDER_SIGNATURE, "given": QW_ORDER_GIVEN}
+QW_START_PLAIN, QW_START_LEARNED = 0, 1
+STARTS = {"plain": QW_START_PLAIN, "learned": QW_START_LEARNED}
 (QW_K_PROJECT, QW_K_SETUP, QW_K_LEVEL, QW_K_DECIDE, QW_K_SELECT, QW_K_RERANK, QW_K_CLUSTER,
- QW_K_ORDER) = range(8)
-QW_K_COUNT = 8
-KERNEL_CLASSES = ("project", "setup", "level", "decide", "select", "rerank", "cluster", "order")
+ QW_K_ORDER, QW_K_START) = range(9)
+QW_K_COUNT = 9
+KERNEL_CLASSES = ("project", "setup", "level", "decide", "select", "rerank", "cluster", "order",
+                  "start")
 
 
 class qw_profile(C.Structure):
     _fields_ = [("launches", C.c_int64 * QW_K_COUNT), ("ms", C.c_double * QW_K_COUNT),
-                ("timed_launches", C.c_int64 * QW_K_COUNT), ("queries", C.c_int64)]
+                ("timed_launches", C.c_int64 * QW_K_COUNT), ("queries", C.c_int64),
+                ("rerank_candidates", C.c_int64), ("rerank_fp32_rows", C.c_int64),
+                ("start_levels_skipped", C.c_int64), ("start_fallbacks", C.c_int64)]
 
 
 class qw_index_info(C.Structure):
@@ -111,6 +121,27 @@ def load(path: Optional[str] = None) -> C.CDLL:
                                          vp, vp, vp, C.c_int32, vp]
     L.qw_run_workload_noalloc.restype = C.c_int32
     L.qw_run_workload_noalloc.argtypes = [vp, vp, C.c_int64, C.c_int32, vp, vp, vp, vp]
+    L.qw_mlp_create.restype = C.c_int32
+    L.qw_mlp_create.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.POINTER(vp)]
+    L.qw_mlp_param_count.restype = C.c_int64
+    L.qw_mlp_param_count.argtypes = [vp]
+    L.qw_mlp_set_params.restype = C.c_int32
+    L.qw_mlp_set_params.argtypes = [vp, vp, C.c_int64]
+    L.qw_mlp_get_params.restype = C.c_int32
+    L.qw_mlp_get_params.argtypes = [vp, vp, C.c_int64]
+    L.qw_mlp_loss_grad.restype = C.c_int32
+    L.qw_mlp_loss_grad.argtypes = [vp, vp, vp, C.c_int64, C.POINTER(C.c_float), vp, vp]
+    L.qw_mlp_train.restype = C.c_int32
+    L.qw_mlp_train.argtypes = [vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_float,
+                               C.POINTER(C.c_float), vp]
+    L.qw_mlp_predict.restype = C.c_int32
+    L.qw_mlp_predict.argtypes = [vp, vp, C.c_int64, vp, vp]
+    L.qw_mlp_free.restype = None
+    L.qw_mlp_free.argtypes = [vp]
+    L.qw_query_features.restype = C.c_int32
+    L.qw_query_features.argtypes = [vp, vp, C.c_int64, vp, vp]
+    L.qw_index_set_start_model.restype = C.c_int32
+    L.qw_index_set_start_model.argtypes = [vp, vp, C.c_float]
     L.qw_index_profile.restype = C.c_int32
     L.qw_index_profile.argtypes = [vp, C.POINTER(qw_profile), C.c_int32]
     L.qw_index_get_info.restype = C.c_int32
@@ -251,14 +282,15 @@ class Index:
     threshold from Eq. 1 (see ``qw_collision_threshold``)."""
 
     def __init__(self, data, A, b, *, w: float, c: int = 2, v: int = 100, l: int = 0,
-                 delta: float = 0.0):
+                 delta: float = 0.0, shadow_bf16: bool = False):
         _f32(data, "data"), _f32(A, "A"), _f32(b, "b")
         mem = _mem_of(data, A, b)
         n, d = data.shape
         m, d2 = A.shape
         if d2 != d or b.shape != (m,):
             raise ValueError("shape mismatch between data, A and b")
-        p = qw_index_params(m=m, w=float(w), c=int(c), v=int(v), l=int(l), delta=float(delta))
+        p = qw_index_params(m=m, w=float(w), c=int(c), v=int(v), l=int(l), delta=float(delta),
+                            shadow_bf16=1 if shadow_bf16 else 0)
         self._h = 0
         self._h = qw_build_index(data.data_ptr(), n, d, A.data_ptr(), b.data_ptr(), p, mem,
                                  _stream_of(data))
@@ -284,11 +316,14 @@ class Index:
         return {"launches": dict(zip(KERNEL_CLASSES, list(p.launches))),
                 "ms": dict(zip(KERNEL_CLASSES, list(p.ms))),
                 "timed_launches": dict(zip(KERNEL_CLASSES, list(p.timed_launches))),
-                "queries": int(p.queries)}
+                "queries": int(p.queries), "rerank_candidates": int(p.rerank_candidates),
+                "rerank_fp32_rows": int(p.rerank_fp32_rows),
+                "start_levels_skipped": int(p.start_levels_skipped),
+                "start_fallbacks": int(p.start_fallbacks)}
 
     def query(self, Q, k: int, *, batch: int = 0, stats: bool = False, out=None,
               profile: bool = False, path: str = "auto", clusters: int = 0,
-              order: str = "auto"):
+              order: str = "auto", rerank: str = "fp32", start: str = "plain"):
         """Top-k of every query row.  Returns (ids int64 nq x k, dists float32
         nq x k[, stats int64 nq x QW_NSTAT]) on Q's device (host tensors in,
         host tensors out).  ``out`` may give preallocated (ids, dists[, stats])."""
@@ -308,7 +343,8 @@ class Index:
                   if stats else None)
         mem = _mem_of(Q, ids, dists, st)
         qp = qw_query_params(batch=int(batch), profile=1 if profile else 0, path=PATHS[path],
-                             clusters=int(clusters), order=ORDERS[order])
+                             clusters=int(clusters), order=ORDERS[order], rerank=RERANKS[rerank],
+                             start=STARTS[start])
         qw_run_workload(self._h, Q.data_ptr(), nq, int(k), qp, ids.data_ptr(), dists.data_ptr(),
                         st.data_ptr() if st is not None else 0, mem, _stream_of(Q))
         return (ids, dists, st) if stats else (ids, dists)
@@ -328,6 +364,20 @@ class Index:
         qw_workload_candidates(self._h, Q.data_ptr(), nq, int(k), qp, cid.data_ptr(),
                                ccol.data_ptr(), st.data_ptr(), mem, _stream_of(Q))
         return cid, ccol, st
+
+    def features(self, Q):
+        """Start-model features of CUDA float32 queries (nq x (d + m))."""
+        torch = _torch()
+        _f32(Q, "Q")
+        F = torch.empty((Q.shape[0], self.d + self.m), dtype=torch.float32, device=Q.device)
+        _check(load().qw_query_features(self._h, Q.data_ptr(), Q.shape[0], F.data_ptr(),
+                                        _stream_of(Q) or None))
+        return F
+
+    def set_start_model(self, mlp, eps: float = 0.02):
+        """Attach a trained Mlp (kept alive by this index) for start='learned'."""
+        _check(load().qw_index_set_start_model(self._h, mlp.handle if mlp else None, float(eps)))
+        self._start_model = mlp
 
     def export(self):
         """Host numpy copies: o (m), span (m), entry_bid and entry_id (m x n),
@@ -352,6 +402,80 @@ class Index:
             pass
 
 
+class Mlp:
+    """The learned start model: n_in -> hidden -> hidden -> classes (ReLU),
+    softmax cross-entropy, FP16 weights over FP32 masters, Adam; every kernel
+    is the library's."""
+
+    def __init__(self, n_in: int, hidden: int, classes: int):
+        h = C.c_void_p()
+        _check(load().qw_mlp_create(n_in, hidden, classes, C.byref(h)))
+        self._h = int(h.value)
+        self.n_in, self.hidden, self.classes = n_in, hidden, classes
+        self.count = int(load().qw_mlp_param_count(self._h))
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def set_params(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.count:
+            raise ValueError("parameter count mismatch")
+        _check(load().qw_mlp_set_params(self._h, p.ctypes.data, p.size))
+
+    def get_params(self):
+        import numpy as np
+        p = np.empty(self.count, np.float32)
+        _check(load().qw_mlp_get_params(self._h, p.ctypes.data, p.size))
+        return p
+
+    def loss_grad(self, X, y):
+        """Mean loss and flat gradient (numpy) for CUDA X (float32) and y (int32)."""
+        import numpy as np
+        g = np.empty(self.count, np.float32)
+        loss = C.c_float(0.0)
+        _check(load().qw_mlp_loss_grad(self._h, X.data_ptr(), y.data_ptr(), X.shape[0],
+                                       C.byref(loss), g.ctypes.data, _stream_of(X) or None))
+        return float(loss.value), g
+
+    def train(self, X, y, *, epochs: int, batch: int = 1024, lr: float = 1e-3) -> float:
+        loss = C.c_float(0.0)
+        _check(load().qw_mlp_train(self._h, X.data_ptr(), y.data_ptr(), X.shape[0], epochs, batch,
+                                   lr, C.byref(loss), _stream_of(X) or None))
+        return float(loss.value)
+
+    def predict(self, X):
+        torch = _torch()
+        P = torch.empty((X.shape[0], self.classes), dtype=torch.float32, device=X.device)
+        _check(load().qw_mlp_predict(self._h, X.data_ptr(), X.shape[0], P.data_ptr(),
+                                     _stream_of(X) or None))
+        return P
+
+    def free(self):
+        if self._h:
+            load().qw_mlp_free(self._h)
+            self._h = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def mlp_init(n_in: int, hidden: int, classes: int, seed: int = 0):
+    """He-normal initial weights, zero biases (seeded numpy draws, flat)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in in ((hidden, n_in), (hidden, hidden), (classes, hidden)):
+        parts.append((rng.standard_normal((fan_out, fan_in)) * np.sqrt(2.0 / fan_in)).ravel())
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
+
+
 def collision_probability(r: float, w: float) -> float:
     """Eq. 1 in closed form (library implementation)."""
     return qw_collision_probability(r, w)
@@ -361,5 +485,5 @@ def collision_threshold(m: int, w: float, c: int, n: int, v: int, delta: float =
     return qw_collision_threshold(m, w, c, n, v, delta)
 
 
-__all__ = ["Index", "hash", "load", "QwError", "collision_probability", "collision_threshold",
+__all__ = ["Index", "Mlp", "mlp_init", "hash", "load", "QwError", "collision_probability", "collision_threshold",
            "STAT_FIELDS", "EXPORTED"] + [n for n in EXPORTED]

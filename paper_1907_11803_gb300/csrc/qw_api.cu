@@ -67,7 +67,12 @@ struct qw_index {
     int nT = 0;
     int32_t span_max = 0;
     int64_t n_fixups = 0;
-    DevBuf X, A, b, o, span, lid, dir_bid, dir_off, dir_start, dir_cnt;
+    DevBuf X, A, b, o, span, lid, dir_bid, dir_off, dir_start, dir_cnt, Xb, xnorm;
+    bool shadow = false;
+    float xs = 1.0f;                 // 1 / RMS coordinate of the data (start-model features)
+    qw_mlp *start_model = nullptr;   // not owned
+    float start_eps = 0.02f;
+    DevBuf w_feat;
     // workspace for queries (grow-only)
     DevBuf w_q, w_hq, w_state, w_counters, w_cand, w_out, w_err, w_order, w_qb, w_ob;
     int64_t device_bytes = 0;
@@ -309,8 +314,20 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
     QW_TRY(launch_tile_sort(Ht.as<int32_t>(), n, m, nT, ix->o.as<int32_t>(), ix->lid.as<uint16_t>(),
                             ix->dir_bid.as<int32_t>(), ix->dir_off.as<int32_t>(),
                             ix->dir_start.as<int64_t>(), ix->dir_cnt.as<int32_t>(), s));
+    {
+        DevBuf acc;
+        QW_TRY(acc.ensure(16));
+        double rms = 1.0;
+        QW_TRY(data_rms(ix->X.as<float>(), n * (int64_t)d, acc.as<double>(), &rms, s));
+        ix->xs = rms > 0.0 ? (float)(1.0 / rms) : 1.0f;
+    }
+    if (ix->shadow) {
+        QW_TRY(ix->Xb.ensure((size_t)n * d * 2));
+        QW_TRY(ix->xnorm.ensure((size_t)n * sizeof(float)));
+        QW_TRY(launch_shadow_bf16(ix->X.as<float>(), n, d, ix->Xb.p, ix->xnorm.as<float>(), s));
+    }
     QW_CUDA_TRY(cudaStreamSynchronize(s));
-    ix->device_bytes = (int64_t)(ix->X.bytes + ix->A.bytes + ix->b.bytes + ix->o.bytes +
+    ix->device_bytes = (int64_t)(ix->Xb.bytes + ix->xnorm.bytes + ix->X.bytes + ix->A.bytes + ix->b.bytes + ix->o.bytes +
                                  ix->span.bytes + ix->lid.bytes + ix->dir_bid.bytes +
                                  ix->dir_off.bytes + ix->dir_start.bytes + ix->dir_cnt.bytes);
     return QW_OK;
@@ -348,6 +365,7 @@ qw_status qw_build_index(const float *data, int64_t n, int32_t d, const float *A
         return arg_error("qw_build_index: cannot derive the collision threshold (bad delta?)");
     }
     ix->nT = (int)((n + kTile - 1) / kTile);
+    ix->shadow = p->shadow_bf16 != 0;
     qw_status st = build_impl(ix, data, A, b, mem, (cudaStream_t)stream);
     if (st != QW_OK) {
         qw_index_free(ix);
@@ -370,13 +388,27 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     const int path = qp ? qp->path : QW_PATH_AUTO;
     const bool order = !qp || qp->order != QW_ORDER_GIVEN;
     const bool host = mem == QW_MEM_HOST;
+    const bool bf16 = qp && qp->rerank == QW_RERANK_BF16;
+    if (bf16 && !ix->shadow) {
+        set_error("qw_run_workload: QW_RERANK_BF16 needs an index built with shadow_bf16");
+        return QW_ERR_ARG;
+    }
     int csize = 0, tpc = 0;
     const bool fits = cluster_path_fits(ix->view(), &csize, &tpc);
     if (path == QW_PATH_CLUSTER && !fits) {
         set_error("qw_run_workload: the index has more tiles than the cluster path can hold");
         return QW_ERR_ARG;
     }
-    const bool use_cluster = fits && path != QW_PATH_LEVELS;
+    const bool learned = qp && qp->start == QW_START_LEARNED;
+    if (learned && !ix->start_model) {
+        set_error("qw_run_workload: QW_START_LEARNED needs a start model (qw_index_set_start_model)");
+        return QW_ERR_ARG;
+    }
+    if (learned && path == QW_PATH_CLUSTER) {
+        set_error("qw_run_workload: learned start levels run on the level path");
+        return QW_ERR_ARG;
+    }
+    const bool use_cluster = fits && path != QW_PATH_LEVELS && !learned;
     int64_t B = qp && qp->batch > 0 ? qp->batch : 0;
     if (B == 0) {
         const int64_t budget = (int64_t)2 << 30;  // counters of one batch
@@ -392,8 +424,18 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     if (!use_cluster) QW_TRY(ix->w_counters.ensure((size_t)B * wpq_bytes));
     QW_TRY(ix->w_cand.ensure((size_t)B * cap * 2 * sizeof(int32_t)));
     const size_t plan_ints = (size_t)B * ix->nT * (kHistBins + 3) + (size_t)B * 2;
-    const size_t st_bytes = (size_t)B * m * 8 + (size_t)B * 8 * 16 + plan_ints * 4 + 256;
+    const size_t st_bytes = (size_t)B * m * 8 + (size_t)B * 8 * 16 + plan_ints * 4 + 256 +
+                            (size_t)B * 4 * 2 + 64;
     QW_TRY(ix->w_state.ensure(st_bytes));
+    int nclass = 0;
+    if (learned) {
+        nclass = mlp_classes(ix->start_model);
+        if (mlp_inputs(ix->start_model) != d + m) {
+            set_error("qw_run_workload: the start model's input size is not d + m");
+            return QW_ERR_ARG;
+        }
+        QW_TRY(ix->w_feat.ensure((size_t)B * (d + m + nclass) * sizeof(float)));
+    }
     // outputs of the whole workload in device memory (the caller's in device mode)
     const size_t o_ids = want_ids ? (size_t)nq * k * sizeof(int64_t) : 0;
     const size_t o_dists = want_ids ? (size_t)nq * k * sizeof(float) : 0;
@@ -454,6 +496,9 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         st.tile_hist = reinterpret_cast<int32_t *>(take((size_t)B * ix->nT * kHistBins * 4));
         st.tile_plan = reinterpret_cast<int32_t *>(take((size_t)B * ix->nT * 3 * 4));
         st.qplan = reinterpret_cast<int32_t *>(take((size_t)B * 2 * 4));
+        st.start = reinterpret_cast<int32_t *>(take((size_t)B * 4));
+        st.fb = reinterpret_cast<int32_t *>(take((size_t)B * 4));
+        st.fb_count = reinterpret_cast<unsigned long long *>(take(16));
         if ((size_t)(p - ix->w_state.as<char>()) > ix->w_state.bytes) {
             set_error("internal: query state workspace too small");
             return QW_ERR_CUDA;
@@ -464,8 +509,11 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     st.cand_col = st.cand + (size_t)B * cap;
     int *err = ix->w_err.as<int>();
     int *queue = reinterpret_cast<int *>(ix->w_err.as<char>() + 32);
+    unsigned long long *rows_ctr = reinterpret_cast<unsigned long long *>(ix->w_err.as<char>() + 40);
+    unsigned long long *cand_ctr = reinterpret_cast<unsigned long long *>(ix->w_err.as<char>() + 48);
     const IndexView view = ix->view();
     LaunchTimer tm{ix, s, qp && qp->profile != 0};
+    if (tm.on) QW_CUDA_TRY(cudaMemsetAsync(ix->w_err.as<char>() + 40, 0, 16, s));
 
     // ---- the whole workload: copy in (host mode), hash, order
     if (host)
@@ -549,29 +597,60 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             }
         } else {
             QW_TRY(tm.run(QW_K_SETUP, 1, [&] { return launch_query_setup(view, HQb, nb, st, s); }));
+            if (learned) {
+                float *F = ix->w_feat.as<float>();
+                float *prob = F + (size_t)B * (d + m);
+                QW_TRY(tm.run(QW_K_START, 5, [&] {
+                    QW_TRY(launch_features(Qb, HQb, nb, view, ix->xs, F, s));
+                    QW_TRY(mlp_predict_dev(ix->start_model, F, nb, prob, s));
+                    return launch_start_levels(prob, nb, nclass, ix->start_eps, st.start, s);
+                }));
+                QW_CUDA_TRY(cudaMemsetAsync(st.fb_count, 0, 16, s));
+            }
             unsigned long long max_top = 0;
             QW_CUDA_TRY(cudaMemcpyAsync(&max_top, st.max_top, sizeof(max_top),
                                         cudaMemcpyDeviceToHost, s));
             QW_CUDA_TRY(cudaStreamSynchronize(s));
             // levels 0..L where c^L > max_top: afterwards every query has stopped
-            int64_t R = 1, Rp = 1;
-            for (int level = 0;; ++level) {
-                QW_TRY(tm.run(QW_K_LEVEL, 1, [&] { return launch_level(view, nb, level, R, Rp, ix->l, st, s); }));
-                QW_TRY(tm.run(QW_K_DECIDE, 1, [&] { return launch_decide(nb, level, R, cap, st, s); }));
-                if ((unsigned long long)R > max_top) break;
-                if (level > 62) {
-                    set_error("qw_run_workload: level limit reached");
-                    return QW_ERR_TIMEOUT;
+            for (int pass = 0; pass < 2; ++pass) {
+                int64_t R = 1, Rp = 1;
+                for (int level = 0;; ++level) {
+                    QW_TRY(tm.run(QW_K_LEVEL, 1, [&] { return launch_level(view, nb, level, R, Rp, ix->l, ix->c, st, s); }));
+                    QW_TRY(tm.run(QW_K_DECIDE, 1, [&] { return launch_decide(nb, level, R, cap, st, s); }));
+                    if ((unsigned long long)R > max_top) break;
+                    if (level > 62) {
+                        set_error("qw_run_workload: level limit reached");
+                        return QW_ERR_TIMEOUT;
+                    }
+                    Rp = R;
+                    R *= ix->c;
                 }
-                Rp = R;
-                R *= ix->c;
+                if (!learned) break;
+                // queries that stopped at a learned first level run again from level 0
+                unsigned long long fbc[2] = {0, 0};
+                QW_TRY(launch_fallback(nb, st, s));
+                QW_CUDA_TRY(cudaMemcpyAsync(fbc, st.fb_count, sizeof(fbc), cudaMemcpyDeviceToHost, s));
+                QW_CUDA_TRY(cudaStreamSynchronize(s));
+                if (pass == 0) {
+                    ix->prof.start_fallbacks += (int64_t)fbc[0];
+                    ix->prof.start_levels_skipped += (int64_t)fbc[1];
+                }
+                if (fbc[0] == 0) break;
+                QW_CUDA_TRY(cudaMemsetAsync(st.fb_count, 0, 16, s));
             }
             QW_TRY(tm.run(QW_K_SELECT, 2, [&] { return launch_collect(view, nb, ix->l, cap, st, stats_b, s); }));
         }
         if (want_cand)
             QW_TRY(tm.run(QW_K_SELECT, 1, [&] { return launch_candidates_out(st, nb, cap, cids_b, ccol_b, s); }));
-        if (want_ids)
+        if (want_ids && bf16)
+            QW_TRY(tm.run(QW_K_RERANK, 1, [&] {
+                return launch_rerank_bf16(view, ix->Xb.p, ix->xnorm.as<float>(), Qb, nb, k, cap, st,
+                                          ids_b, dists_b, tm.on ? rows_ctr : nullptr, s);
+            }));
+        else if (want_ids)
             QW_TRY(tm.run(QW_K_RERANK, 1, [&] { return launch_rerank(view, Qb, nb, k, cap, st, ids_b, dists_b, s); }));
+        if (want_ids && tm.on)
+            QW_TRY(launch_sum_i32(st.nkeep, nb, cand_ctr, s));
         if (order) {
             QW_TRY(tm.run(QW_K_ORDER, 1, [&] {
                 return launch_scatter(perm, b0, nb, k, cap, ids_b, dists_b, stats_b, cids_b, ccol_b,
@@ -593,6 +672,12 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         QW_CUDA_TRY(cudaStreamSynchronize(s));
     }
     QW_TRY(tm.finish());
+    if (tm.on) {
+        unsigned long long ctr[2] = {0, 0};
+        QW_CUDA_TRY(cudaMemcpy(ctr, ix->w_err.as<char>() + 40, sizeof(ctr), cudaMemcpyDeviceToHost));
+        ix->prof.rerank_fp32_rows += (int64_t)(bf16 ? ctr[0] : ctr[1]);
+        ix->prof.rerank_candidates += (int64_t)ctr[1];
+    }
     ix->prof.queries += nq;
     return QW_OK;
 }
@@ -613,7 +698,11 @@ static qw_status check_workload_args(const qw_index *ix, const float *queries, i
         if (qp->clusters < 0) return arg_error("qw_run_workload: clusters < 0");
         if (qp->order < QW_ORDER_AUTO || qp->order > QW_ORDER_GIVEN)
             return arg_error("qw_run_workload: unknown order");
-        for (int r = 0; r < 3; ++r)
+        if (qp->rerank < QW_RERANK_FP32 || qp->rerank > QW_RERANK_BF16)
+            return arg_error("qw_run_workload: unknown rerank");
+        if (qp->start < QW_START_PLAIN || qp->start > QW_START_LEARNED)
+            return arg_error("qw_run_workload: unknown start");
+        for (int r = 0; r < 1; ++r)
             if (qp->reserved[r] != 0) return arg_error("qw_run_workload: reserved field set");
     }
     return QW_OK;
@@ -641,6 +730,44 @@ qw_status qw_workload_candidates(qw_index *ix, const float *queries, int64_t nq,
     if (nq == 0) return QW_OK;
     return run_impl(ix, queries, nq, k, qp, nullptr, nullptr, stats, cand_ids, cand_col, mem,
                     (cudaStream_t)stream);
+}
+
+qw_status qw_query_features(qw_index *ix, const float *queries, int64_t nq, float *F, void *stream)
+{
+    clear_error();
+    if (!ix || (nq > 0 && (!queries || !F))) return arg_error("qw_query_features: null pointer");
+    if (nq < 0) return arg_error("qw_query_features: nq < 0");
+    if (nq == 0) return QW_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    QW_TRY(ix->w_hq.ensure((size_t)nq * ix->m * sizeof(int32_t)));
+    QW_TRY(ix->w_err.ensure(64));
+    int *err = ix->w_err.as<int>();
+    QW_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+    QW_TRY(launch_hash(queries, nq, ix->d, ix->A.as<float>(), ix->b.as<float>(), ix->m, ix->w,
+                       ix->w_hq.as<int32_t>(), ix->m, 1, err, nullptr, s));
+    QW_TRY(launch_features(queries, ix->w_hq.as<int32_t>(), nq, ix->view(), ix->xs, F, s));
+    int h_err = 0;
+    QW_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    QW_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h_err & 2) {
+        set_error("qw_query_features: a query bucket id falls outside int32");
+        return QW_ERR_RANGE;
+    }
+    return QW_OK;
+}
+
+qw_status qw_index_set_start_model(qw_index *ix, qw_mlp *mlp, float eps)
+{
+    clear_error();
+    if (!ix) return arg_error("qw_index_set_start_model: index is null");
+    if (mlp) {
+        if (!(eps > 0.0f && eps < 1.0f)) return arg_error("qw_index_set_start_model: eps not in (0, 1)");
+        if (mlp_inputs(mlp) != ix->d + ix->m)
+            return arg_error("qw_index_set_start_model: the model's input size is not d + m");
+    }
+    ix->start_model = mlp;
+    ix->start_eps = eps;
+    return QW_OK;
 }
 
 qw_status qw_index_profile(qw_index *ix, qw_profile *out, int32_t reset)
@@ -708,10 +835,11 @@ void qw_index_free(qw_index *ix)
 {
     if (!ix) return;
     cudaDeviceSynchronize();
-    DevBuf *bufs[] = {&ix->X, &ix->A, &ix->b, &ix->o, &ix->span, &ix->lid, &ix->dir_bid,
+    DevBuf *bufs[] = {&ix->X, &ix->Xb, &ix->xnorm, &ix->A, &ix->b, &ix->o, &ix->span, &ix->lid,
+                      &ix->dir_bid,
                       &ix->dir_off, &ix->dir_start, &ix->dir_cnt, &ix->w_q, &ix->w_hq,
                       &ix->w_state, &ix->w_counters, &ix->w_cand, &ix->w_out, &ix->w_err,
-                      &ix->w_order, &ix->w_qb, &ix->w_ob};
+                      &ix->w_order, &ix->w_qb, &ix->w_ob, &ix->w_feat};
     for (DevBuf *bb : bufs) bb->release();
     for (cudaEvent_t e : ix->event_pool) cudaEventDestroy(e);
     delete ix;

@@ -6,12 +6,22 @@
 //   lid[i * nT * kTile + t * kTile + p]
 //                    16-bit id within its tile (id = t * kTile + lid); every
 //                    tile owns kTile slots (the last one is padded), entries
-//                    of a tile sorted by (bid, id);
+//                    of a tile grouped by bid in ascending order;
 //   dir_bid / dir_off at dir_start[i * nT + t]: the distinct bucket ids of
 //                    tile t and the offset of the first entry of each, so a
 //                    bucket-id range maps to an entry range by two searches.
 // bid = h - o_i with o_i = min over the data of h_i, so bid >= 0.
+//
+// Inside one bucket the ids form a set; their order is free.  It is chosen
+// for the counting kernels, which add one to a shared-memory byte counter per
+// id (4 counters per 32-bit word, word w in bank w mod 32): the ids of a
+// bucket are laid out in groups of up to 8 ids of the same bank, the groups
+// cycling through the banks.  A warp then reads 32 consecutive 8-id chunks
+// whose ids fall in (mostly) different banks, instead of 32 random banks.
 #include "qw_internal.cuh"
+#include "qw_scan.cuh"
+
+#include <cuda_bf16.h>
 
 namespace qw {
 namespace {
@@ -40,22 +50,43 @@ __global__ void minmax_kernel(const int32_t *__restrict__ Ht, int64_t n, int32_t
 
 constexpr int SORT_THREADS = 1024;
 
-__device__ __forceinline__ bool pair_greater(int32_t b0, uint16_t l0, int32_t b1, uint16_t l1)
+__device__ __forceinline__ uint32_t lid_bank(uint16_t lid) { return ((uint32_t)lid >> 2) & 31u; }
+
+// In-place bitonic sort of P (a power of two) entries of (sb, sl, sg) in
+// shared memory, ascending by the strict total order `greater`.
+template <class Greater>
+__device__ __forceinline__ void bitonic_sort(int P, int32_t *sb, uint16_t *sl, uint8_t *sg,
+                                             Greater greater)
 {
-    return (b0 > b1) || (b0 == b1 && l0 > l1);
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int x = threadIdx.x; x < (P >> 1); x += SORT_THREADS) {
+                const int a = 2 * x - (x & (jj - 1));
+                const int c = a + jj;
+                const bool up = (a & k) == 0;
+                if (greater(a, c) == up) {
+                    const int32_t tb = sb[a]; sb[a] = sb[c]; sb[c] = tb;
+                    const uint16_t tl = sl[a]; sl[a] = sl[c]; sl[c] = tl;
+                    const uint8_t tg = sg[a]; sg[a] = sg[c]; sg[c] = tg;
+                }
+            }
+            __syncthreads();
+        }
+    }
 }
 
-// One CTA sorts one (tile, projection) pair of up to kTile entries in shared
-// memory with a bitonic network on the unique key (bid, lid), then writes the
-// 16-bit ids and the tile's bucket directory.
+// One CTA orders one (tile, projection) pair of up to kTile entries in shared
+// memory: by bucket id, and inside a bucket in bank-interleaved groups (see
+// the file comment); then writes the 16-bit ids and the tile's directory.
 __global__ void __launch_bounds__(SORT_THREADS) tile_sort_kernel(
     const int32_t *__restrict__ Ht, int64_t n, const int32_t *__restrict__ o,
     uint16_t *__restrict__ lid_out, int32_t *__restrict__ dir_bid, int32_t *__restrict__ dir_off,
     const int64_t *__restrict__ dir_start, int32_t *__restrict__ dir_cnt, int nT)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    int32_t *sb = reinterpret_cast<int32_t *>(smem);               // kTile
-    uint16_t *sl = reinterpret_cast<uint16_t *>(sb + kTile);       // kTile
+    int32_t *sb = reinterpret_cast<int32_t *>(smem);               // kTile bucket ids
+    uint16_t *sl = reinterpret_cast<uint16_t *>(sb + kTile);       // kTile in-tile ids
+    uint8_t *sg = reinterpret_cast<uint8_t *>(sl + kTile);         // kTile group numbers
     __shared__ int32_t warp_sums[SORT_THREADS / 32];
     __shared__ int32_t carry;
 
@@ -72,27 +103,44 @@ __global__ void __launch_bounds__(SORT_THREADS) tile_sort_kernel(
             sb[j] = col[j] - oi;
             sl[j] = (uint16_t)j;
         } else {
-            sb[j] = INT32_MAX;
+            sb[j] = INT32_MAX;  // sorts after every bucket id
             sl[j] = 0xffff;
         }
+        sg[j] = 0;
     }
     __syncthreads();
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int jj = k >> 1; jj > 0; jj >>= 1) {
-            for (int x = threadIdx.x; x < (P >> 1); x += SORT_THREADS) {
-                int a = 2 * x - (x & (jj - 1));
-                int c = a + jj;
-                bool up = (a & k) == 0;
-                int32_t ba = sb[a], bc = sb[c];
-                uint16_t la = sl[a], lc = sl[c];
-                if (pair_greater(ba, la, bc, lc) == up) {
-                    sb[a] = bc; sb[c] = ba;
-                    sl[a] = lc; sl[c] = la;
-                }
-            }
-            __syncthreads();
+    // 1. by (bid, bank, id): the ids of one bank inside a bucket become a run
+    bitonic_sort(P, sb, sl, sg, [&](int a, int c) {
+        if (sb[a] != sb[c]) return sb[a] > sb[c];
+        const uint32_t ka = lid_bank(sl[a]), kc = lid_bank(sl[c]);
+        if (ka != kc) return ka > kc;
+        return sl[a] > sl[c];
+    });
+    // 2. group number = rank inside the (bid, bank) run / 8
+    {
+        const int per = P / SORT_THREADS > 0 ? P / SORT_THREADS : 1;
+        const int j0 = min(P, (int)threadIdx.x * per), j1 = min(P, j0 + per);
+        auto run_start = [&](int j) {
+            return j == 0 || sb[j] != sb[j - 1] || lid_bank(sl[j]) != lid_bank(sl[j - 1]);
+        };
+        int last = -1;
+        for (int j = j0; j < j1; ++j)
+            if (run_start(j)) last = j;
+        int start = block_exclusive_max<SORT_THREADS>(last, -1, warp_sums);
+        for (int j = j0; j < j1; ++j) {
+            if (run_start(j)) start = j;
+            sg[j] = (uint8_t)((j - start) >> 3);  // a bank holds <= 1024 ids of a tile
         }
+        __syncthreads();
     }
+    // 3. by (bid, group, bank, id): groups of one bank, cycling the banks
+    bitonic_sort(P, sb, sl, sg, [&](int a, int c) {
+        if (sb[a] != sb[c]) return sb[a] > sb[c];
+        if (sg[a] != sg[c]) return sg[a] > sg[c];
+        const uint32_t ka = lid_bank(sl[a]), kc = lid_bank(sl[c]);
+        if (ka != kc) return ka > kc;
+        return sl[a] > sl[c];
+    });
     uint16_t *lo = lid_out + (int64_t)i * nT * kTile + base;
     for (int j = threadIdx.x; j < len; j += SORT_THREADS) lo[j] = sl[j];
 
@@ -162,7 +210,36 @@ __global__ void export_kernel(const uint16_t *__restrict__ lid, const int32_t *_
     }
 }
 
+// BF16 copy of the data (round to nearest even) and an upper bound of each
+// row's Euclidean norm (FP64 sum, rounded up to float).
+__global__ void shadow_bf16_kernel(const float *__restrict__ X, int64_t n, int d,
+                                   __nv_bfloat16 *__restrict__ Xb, float *__restrict__ xnorm)
+{
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const float *x = X + r * d;
+    double s = 0.0;
+    for (int j = lane; j < d; j += 32) {
+        const float v = x[j];
+        Xb[r * d + j] = __float2bfloat16_rn(v);
+        s += (double)v * (double)v;
+    }
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) xnorm[r] = __double2float_ru(sqrt(s) * (1.0 + 1e-12));
+}
+
 }  // namespace
+
+qw_status launch_shadow_bf16(const float *X, int64_t n, int d, void *Xb, float *xnorm,
+                             cudaStream_t s)
+{
+    const int64_t blocks = (n + 7) / 8;
+    shadow_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(
+        X, n, d, reinterpret_cast<__nv_bfloat16 *>(Xb), xnorm);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
 
 qw_status launch_minmax(const int32_t *Ht, int64_t n, int m, int32_t *hmin, int32_t *hmax,
                         cudaStream_t s)
@@ -178,7 +255,7 @@ qw_status launch_tile_sort(const int32_t *Ht, int64_t n, int m, int nT, const in
                            uint16_t *lid, int32_t *dir_bid, int32_t *dir_off,
                            const int64_t *dir_start, int32_t *dir_cnt, cudaStream_t s)
 {
-    const size_t smem = (size_t)kTile * (sizeof(int32_t) + sizeof(uint16_t));
+    const size_t smem = (size_t)kTile * (sizeof(int32_t) + sizeof(uint16_t) + sizeof(uint8_t));
     QW_CUDA_TRY(cudaFuncSetAttribute(tile_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     tile_sort_kernel<<<dim3((unsigned)nT, (unsigned)m), SORT_THREADS, smem, s>>>(

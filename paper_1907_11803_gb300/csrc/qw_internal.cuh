@@ -117,12 +117,16 @@ struct QueryState {
     int32_t *tile_plan;     // nb x nT x 3: first output slot, count-c* ids before the tile,
                             //   ids kept in the tile
     int32_t *qplan;         // nb x 2: c*, how many count-c* ids are kept
+    int32_t *start;         // nb: first level of the query (0 unless learned)
+    int32_t *fb;            // nb: query stopped at a learned first level > 0
+    unsigned long long *fb_count;  // 2: queries to recompute, levels skipped
 };
 
 qw_status launch_query_setup(const IndexView &ix, const int32_t *HQ, int nb, QueryState &st,
                              cudaStream_t s);
 qw_status launch_level(const IndexView &ix, int nb, int level, int64_t R, int64_t Rp, int l,
-                       QueryState &st, cudaStream_t s);
+                       int cgrow, QueryState &st, cudaStream_t s);
+qw_status launch_fallback(int nb, QueryState &st, cudaStream_t s);
 qw_status launch_decide(int nb, int level, int64_t R, int cap, QueryState &st, cudaStream_t s);
 qw_status launch_collect(const IndexView &ix, int nb, int l, int cap, QueryState &st,
                          int64_t *stats_out, cudaStream_t s);
@@ -140,11 +144,28 @@ qw_status launch_scatter(const int32_t *perm, int64_t b0, int nb, int k, int cap
                          const int64_t *ids_b, const float *dists_b, const int64_t *stats_b,
                          const int64_t *cids_b, const int32_t *ccol_b, int64_t *ids, float *dists,
                          int64_t *stats, int64_t *cids, int32_t *ccol, cudaStream_t s);
+qw_status launch_sum_i32(const int32_t *v, int n, unsigned long long *out, cudaStream_t s);
 qw_status launch_candidates_out(const QueryState &st, int nb, int cap, int64_t *cand_ids,
                                 int32_t *cand_col, cudaStream_t s);
+qw_status launch_rerank_bf16(const IndexView &ix, const void *Xb, const float *xnorm,
+                             const float *Qb, int nb, int k, int cap, const QueryState &st,
+                             int64_t *ids_out, float *dists_out,
+                             unsigned long long *rows_fp32, cudaStream_t s);
+qw_status launch_shadow_bf16(const float *X, int64_t n, int d, void *Xb, float *xnorm,
+                             cudaStream_t s);
 qw_status launch_rerank(const IndexView &ix, const float *Qb, int nb, int k, int cap,
                         const QueryState &st, int64_t *ids_out, float *dists_out,
                         cudaStream_t s);
+
+// The learned start model (qw_mlp.cu).
+int mlp_inputs(const qw_mlp *mp);
+int mlp_classes(const qw_mlp *mp);
+qw_status mlp_predict_dev(qw_mlp *mp, const float *X, int64_t n, float *prob, cudaStream_t s);
+qw_status launch_features(const float *Q, const int32_t *HQ, int64_t nq, const IndexView &ix,
+                          float xs, float *F, cudaStream_t s);
+qw_status launch_start_levels(const float *prob, int n, int C, float eps, int32_t *start,
+                              cudaStream_t s);
+qw_status data_rms(const float *X, int64_t count, double *dev_acc, double *out, cudaStream_t s);
 
 // Read-only view of a built index for entry points outside qw_api.cu.
 struct IndexParams {

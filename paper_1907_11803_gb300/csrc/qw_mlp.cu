@@ -1,0 +1,501 @@
+// qw_mlp.cu -- the learned part: a small multilayer perceptron that predicts,
+// from a query's features, the level at which the collision-counting loop
+// stops, so the level path can begin at a later level (a query that then
+// stops at its first level is recomputed from level 0: the prediction changes
+// only the speed, never the result).
+//
+// The paper trains an offline model to pick its cache split (Section 5.2); it
+// gives no network.  This one is x (n_in) -> ReLU(W1 x + b1) -> ReLU(W2 . + b2)
+// -> W3 . + b3 (C logits), trained with mean softmax cross-entropy and Adam.
+// Weights are used as FP16 copies of FP32 master weights; every product is
+// accumulated in FP32.  Forward, backward and the optimizer step are the
+// kernels below (tiled SIMT GEMMs: the layers are a few hundred wide, far too
+// small for the tensor cores to matter next to the counting kernels).
+#include "qw_internal.cuh"
+
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+namespace qw {
+namespace {
+
+constexpr int GM = 64, GN = 64, GK = 16, GT = 256;
+
+template <typename TB>
+__device__ __forceinline__ float to_f(TB v);
+template <>
+__device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
+
+// C[m][n] = sum_k A(m, k) B(k, n) (+ bias[n]) with arbitrary strides.
+// EPI 0: store; 1: add bias; 2: add bias, store pre-activation to C and
+// ReLU(.) to Aout.
+template <typename TB, int EPI>
+__global__ void __launch_bounds__(GT) mlp_gemm_kernel(int M, int N, int K,
+                                                      const float *__restrict__ A, int64_t sam,
+                                                      int64_t sak, const TB *__restrict__ B,
+                                                      int64_t sbk, int64_t sbn,
+                                                      float *__restrict__ C, int64_t ldc,
+                                                      const float *__restrict__ bias,
+                                                      float *__restrict__ Aout)
+{
+    __shared__ float As[GK][GM + 1];
+    __shared__ float Bs[GK][GN + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += GK) {
+        for (int e = threadIdx.x; e < GM * GK; e += GT) {
+            const int mm = e / GK, kk = e % GK;
+            const int gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < M && gk < K) ? A[gm * sam + gk * sak] : 0.0f;
+        }
+        for (int e = threadIdx.x; e < GN * GK; e += GT) {
+            const int nn = e / GK, kk = e % GK;
+            const int gn = n0 + nn, gk = k0 + kk;
+            Bs[kk][nn] = (gn < N && gk < K) ? to_f<TB>(B[gk * sbk + gn * sbn]) : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gm = m0 + ty + 16 * i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gn = n0 + tx + 16 * j;
+            if (gn >= N) continue;
+            float v = acc[i][j];
+            if (EPI >= 1) v += bias[gn];
+            C[gm * ldc + gn] = v;
+            if (EPI == 2) Aout[gm * ldc + gn] = v > 0.0f ? v : 0.0f;
+        }
+    }
+}
+
+// Softmax cross-entropy of one row per warp: adds -log p[y] to *loss_sum and
+// writes d logits = (p - onehot(y)) * inv_n; or, without labels, p.
+__global__ void softmax_rows_kernel(const float *__restrict__ Z, int n, int C,
+                                    const int32_t *__restrict__ y, float inv_n,
+                                    float *__restrict__ dZ, float *__restrict__ loss_sum,
+                                    float *__restrict__ prob)
+{
+    const int r = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const float *z = Z + (int64_t)r * C;
+    float mx = -INFINITY;
+    for (int c = lane; c < C; c += 32) mx = fmaxf(mx, z[c]);
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    float s = 0.0f;
+    for (int c = lane; c < C; c += 32) s += __expf(z[c] - mx);
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    const float inv_s = 1.0f / s;
+    for (int c = lane; c < C; c += 32) {
+        const float p = __expf(z[c] - mx) * inv_s;
+        if (prob) prob[(int64_t)r * C + c] = p;
+        if (dZ) dZ[(int64_t)r * C + c] = (p - ((y && c == y[r]) ? 1.0f : 0.0f)) * inv_n;
+    }
+    if (lane == 0 && y && loss_sum) {
+        const float logp = (z[y[r]] - mx) - __logf(s);
+        atomicAdd(loss_sum, -logp);
+    }
+}
+
+// out[c] = sum_r D[r][c]
+__global__ void colsum_kernel(const float *__restrict__ D, int n, int C, float *__restrict__ out)
+{
+    const int c = blockIdx.x;
+    float s = 0.0f;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) s += D[(int64_t)r * C + c];
+    __shared__ float red[32];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (int)(blockDim.x / 32) ? red[threadIdx.x] : 0.0f;
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (threadIdx.x == 0) out[c] = s;
+    }
+}
+
+__global__ void relu_back_kernel(float *__restrict__ dA, const float *__restrict__ Z, int64_t count)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (!(Z[i] > 0.0f)) dA[i] = 0.0f;
+}
+
+__global__ void to_half_kernel(const float *__restrict__ p, __half *__restrict__ h, int64_t count)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        h[i] = __float2half_rn(p[i]);
+}
+
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g,
+                            float *__restrict__ m1, float *__restrict__ m2,
+                            __half *__restrict__ h, int64_t count, float lr, float b1, float b2,
+                            float eps, float c1, float c2)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float a = b1 * m1[i] + (1.0f - b1) * gi;
+        const float b = b2 * m2[i] + (1.0f - b2) * gi * gi;
+        m1[i] = a;
+        m2[i] = b;
+        const float v = p[i] - lr * (a / c1) / (sqrtf(b / c2) + eps);
+        p[i] = v;
+        h[i] = __float2half_rn(v);
+    }
+}
+
+// Start level of every query: the largest s whose predicted probability of
+// stopping at a level <= s is at most eps (0 when none is).
+__global__ void start_level_kernel(const float *__restrict__ prob, int n, int C, float eps,
+                                   int32_t *__restrict__ start)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    float cdf = 0.0f;
+    int s = 0;
+    for (int c = 0; c < C - 1; ++c) {
+        cdf += prob[(int64_t)q * C + c];
+        if (cdf <= eps) s = c + 1; else break;
+    }
+    // s - 1 is the last level with cdf <= eps; a start beyond it risks a
+    // stop at the start level
+    start[q] = s > 0 ? s - 1 : 0;
+}
+
+// Features of a query: its coordinates scaled by 1 / (data RMS), then for
+// every projection its position in the data's bucket-id range.
+__global__ void features_kernel(const float *__restrict__ Q, const int32_t *__restrict__ HQ,
+                                int64_t nq, int d, int m, const int32_t *__restrict__ o,
+                                const int32_t *__restrict__ span, float xs,
+                                float *__restrict__ F)
+{
+    const int64_t q = blockIdx.x;
+    if (q >= nq) return;
+    const int nin = d + m;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) F[q * nin + j] = Q[q * d + j] * xs;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const double g = (double)HQ[q * m + i] - (double)o[i];
+        double pos = (g + 0.5) / ((double)span[i] + 1.0);
+        pos = pos < -1.0 ? -1.0 : (pos > 2.0 ? 2.0 : pos);
+        F[q * nin + d + i] = (float)(pos - 0.5);
+    }
+}
+
+__global__ void sumsq_kernel(const float *__restrict__ X, int64_t count, double *__restrict__ out)
+{
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        s += (double)X[i] * (double)X[i];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+template <typename TB, int EPI>
+qw_status gemm(int M, int N, int K, const float *A, int64_t sam, int64_t sak, const TB *B,
+               int64_t sbk, int64_t sbn, float *C, int64_t ldc, const float *bias, float *Aout,
+               cudaStream_t s)
+{
+    if (M <= 0 || N <= 0) return QW_OK;
+    dim3 grid((unsigned)((N + GN - 1) / GN), (unsigned)((M + GM - 1) / GM));
+    mlp_gemm_kernel<TB, EPI><<<grid, GT, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias,
+                                                 Aout);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
+
+}  // namespace
+}  // namespace qw
+
+using namespace qw;
+
+struct qw_mlp {
+    int n_in = 0, H = 0, C = 0;
+    int64_t np = 0;
+    int64_t oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0;
+    DevBuf p32, p16, grad, m1, m2, work, scalar;
+    int cap = 0;  // rows the work buffers hold
+    int64_t step = 0;
+
+    float *Z1, *A1, *Z2, *A2, *Z3, *D3, *DA, *DZ;
+
+    qw_status ensure_work(int rows)
+    {
+        if (rows <= cap) return QW_OK;
+        const size_t per = (size_t)rows;
+        const size_t bytes = per * (6 * (size_t)H + 2 * (size_t)C) * sizeof(float);
+        QW_TRY(work.ensure(bytes));
+        float *p = work.as<float>();
+        Z1 = p; p += per * H;
+        A1 = p; p += per * H;
+        Z2 = p; p += per * H;
+        A2 = p; p += per * H;
+        DA = p; p += per * H;
+        DZ = p; p += per * H;
+        Z3 = p; p += per * C;
+        D3 = p;
+        cap = rows;
+        return QW_OK;
+    }
+
+    // forward of rows [0, n) of X (n <= cap): logits in Z3
+    qw_status forward(const float *X, int n, cudaStream_t s)
+    {
+        const __half *h = p16.as<__half>();
+        const float *p = p32.as<float>();
+        QW_TRY((gemm<__half, 2>(n, H, n_in, X, n_in, 1, h + oW1, 1, n_in, Z1, H, p + ob1, A1, s)));
+        QW_TRY((gemm<__half, 2>(n, H, H, A1, H, 1, h + oW2, 1, H, Z2, H, p + ob2, A2, s)));
+        QW_TRY((gemm<__half, 1>(n, C, H, A2, H, 1, h + oW3, 1, H, Z3, C, p + ob3, nullptr, s)));
+        return QW_OK;
+    }
+
+    // loss sum into scalar[0] and gradient (mean over n rows) into grad
+    qw_status backward(const float *X, const int32_t *y, int n, cudaStream_t s)
+    {
+        const __half *h = p16.as<__half>();
+        float *g = grad.as<float>();
+        float *loss = scalar.as<float>();
+        softmax_rows_kernel<<<(n + 7) / 8, 256, 0, s>>>(Z3, n, C, y, 1.0f / (float)n, D3, loss,
+                                                        nullptr);
+        QW_CUDA_TRY(cudaGetLastError());
+        // layer 3
+        QW_TRY((gemm<float, 0>(C, H, n, D3, 1, C, A2, H, 1, g + oW3, H, nullptr, nullptr, s)));
+        colsum_kernel<<<C, 256, 0, s>>>(D3, n, C, g + ob3);
+        QW_CUDA_TRY(cudaGetLastError());
+        QW_TRY((gemm<__half, 0>(n, H, C, D3, C, 1, h + oW3, H, 1, DA, H, nullptr, nullptr, s)));
+        relu_back_kernel<<<152 * 4, 256, 0, s>>>(DA, Z2, (int64_t)n * H);
+        QW_CUDA_TRY(cudaGetLastError());
+        // layer 2 (DA now holds d Z2)
+        QW_TRY((gemm<float, 0>(H, H, n, DA, 1, H, A1, H, 1, g + oW2, H, nullptr, nullptr, s)));
+        colsum_kernel<<<H, 256, 0, s>>>(DA, n, H, g + ob2);
+        QW_CUDA_TRY(cudaGetLastError());
+        QW_TRY((gemm<__half, 0>(n, H, H, DA, H, 1, h + oW2, H, 1, DZ, H, nullptr, nullptr, s)));
+        relu_back_kernel<<<152 * 4, 256, 0, s>>>(DZ, Z1, (int64_t)n * H);
+        QW_CUDA_TRY(cudaGetLastError());
+        // layer 1 (DZ holds d Z1)
+        QW_TRY((gemm<float, 0>(H, n_in, n, DZ, 1, H, X, n_in, 1, g + oW1, n_in, nullptr, nullptr,
+                               s)));
+        colsum_kernel<<<H, 256, 0, s>>>(DZ, n, H, g + ob1);
+        QW_CUDA_TRY(cudaGetLastError());
+        return QW_OK;
+    }
+};
+
+static qw_status mlp_error(const char *msg)
+{
+    set_error(std::string("qw_mlp: ") + msg);
+    return QW_ERR_ARG;
+}
+
+extern "C" {
+
+qw_status qw_mlp_create(int32_t n_in, int32_t hidden, int32_t classes, qw_mlp **out)
+{
+    clear_error();
+    if (!out) return mlp_error("out is null");
+    *out = nullptr;
+    if (n_in < 1 || hidden < 1 || classes < 2 || n_in > 65536 || hidden > 65536 || classes > 1024)
+        return mlp_error("bad layer sizes");
+    qw_mlp *mp = new (std::nothrow) qw_mlp();
+    if (!mp) return QW_ERR_OOM;
+    mp->n_in = n_in;
+    mp->H = hidden;
+    mp->C = classes;
+    int64_t o = 0;
+    mp->oW1 = o; o += (int64_t)hidden * n_in;
+    mp->ob1 = o; o += hidden;
+    mp->oW2 = o; o += (int64_t)hidden * hidden;
+    mp->ob2 = o; o += hidden;
+    mp->oW3 = o; o += (int64_t)classes * hidden;
+    mp->ob3 = o; o += classes;
+    mp->np = o;
+    qw_status st = QW_OK;
+    if ((st = mp->p32.ensure(o * 4)) != QW_OK || (st = mp->p16.ensure(o * 2)) != QW_OK ||
+        (st = mp->grad.ensure(o * 4)) != QW_OK || (st = mp->m1.ensure(o * 4)) != QW_OK ||
+        (st = mp->m2.ensure(o * 4)) != QW_OK || (st = mp->scalar.ensure(64)) != QW_OK) {
+        delete mp;
+        return st;
+    }
+    cudaMemset(mp->p32.p, 0, o * 4);
+    cudaMemset(mp->p16.p, 0, o * 2);
+    cudaMemset(mp->m1.p, 0, o * 4);
+    cudaMemset(mp->m2.p, 0, o * 4);
+    *out = mp;
+    return QW_OK;
+}
+
+int64_t qw_mlp_param_count(const qw_mlp *mp) { return mp ? mp->np : -1; }
+
+qw_status qw_mlp_set_params(qw_mlp *mp, const float *params, int64_t count)
+{
+    clear_error();
+    if (!mp || !params) return mlp_error("null pointer");
+    if (count != mp->np) return mlp_error("parameter count mismatch");
+    QW_CUDA_TRY(cudaMemcpy(mp->p32.p, params, count * 4, cudaMemcpyHostToDevice));
+    to_half_kernel<<<152 * 4, 256>>>(mp->p32.as<float>(), mp->p16.as<__half>(), count);
+    QW_CUDA_TRY(cudaGetLastError());
+    QW_CUDA_TRY(cudaMemset(mp->m1.p, 0, count * 4));
+    QW_CUDA_TRY(cudaMemset(mp->m2.p, 0, count * 4));
+    mp->step = 0;
+    QW_CUDA_TRY(cudaDeviceSynchronize());
+    return QW_OK;
+}
+
+qw_status qw_mlp_get_params(const qw_mlp *mp, float *params, int64_t count)
+{
+    clear_error();
+    if (!mp || !params) return mlp_error("null pointer");
+    if (count != mp->np) return mlp_error("parameter count mismatch");
+    QW_CUDA_TRY(cudaDeviceSynchronize());
+    QW_CUDA_TRY(cudaMemcpy(params, mp->p32.p, count * 4, cudaMemcpyDeviceToHost));
+    return QW_OK;
+}
+
+qw_status qw_mlp_loss_grad(qw_mlp *mp, const float *X, const int32_t *y, int64_t n, float *loss,
+                           float *grad, void *stream)
+{
+    clear_error();
+    if (!mp || !X || !y) return mlp_error("null pointer");
+    if (n < 1 || n > (1 << 20)) return mlp_error("n out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    QW_TRY(mp->ensure_work((int)n));
+    QW_CUDA_TRY(cudaMemsetAsync(mp->scalar.p, 0, 64, s));
+    QW_TRY(mp->forward(X, (int)n, s));
+    QW_TRY(mp->backward(X, y, (int)n, s));
+    float ls = 0.0f;
+    QW_CUDA_TRY(cudaMemcpyAsync(&ls, mp->scalar.p, 4, cudaMemcpyDeviceToHost, s));
+    if (grad)
+        QW_CUDA_TRY(cudaMemcpyAsync(grad, mp->grad.p, mp->np * 4, cudaMemcpyDeviceToHost, s));
+    QW_CUDA_TRY(cudaStreamSynchronize(s));
+    if (loss) *loss = ls / (float)n;
+    return QW_OK;
+}
+
+qw_status qw_mlp_train(qw_mlp *mp, const float *X, const int32_t *y, int64_t n, int32_t epochs,
+                       int32_t batch, float lr, float *final_loss, void *stream)
+{
+    clear_error();
+    if (!mp || !X || !y) return mlp_error("null pointer");
+    if (n < 1 || epochs < 1 || batch < 1 || !(lr > 0.0f)) return mlp_error("bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int B = (int)std::min<int64_t>(batch, n);
+    QW_TRY(mp->ensure_work(B));
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    float last = 0.0f;
+    for (int ep = 0; ep < epochs; ++ep) {
+        QW_CUDA_TRY(cudaMemsetAsync(mp->scalar.p, 0, 64, s));
+        for (int64_t r0 = 0; r0 < n; r0 += B) {
+            const int nb = (int)std::min<int64_t>(B, n - r0);
+            const float *Xb = X + r0 * mp->n_in;
+            QW_TRY(mp->forward(Xb, nb, s));
+            QW_TRY(mp->backward(Xb, y + r0, nb, s));
+            mp->step += 1;
+            const float c1 = 1.0f - powf(b1, (float)mp->step);
+            const float c2 = 1.0f - powf(b2, (float)mp->step);
+            adam_kernel<<<152 * 4, 256, 0, s>>>(mp->p32.as<float>(), mp->grad.as<float>(),
+                                                mp->m1.as<float>(), mp->m2.as<float>(),
+                                                mp->p16.as<__half>(), mp->np, lr, b1, b2, eps, c1,
+                                                c2);
+            QW_CUDA_TRY(cudaGetLastError());
+        }
+        float ls = 0.0f;
+        QW_CUDA_TRY(cudaMemcpyAsync(&ls, mp->scalar.p, 4, cudaMemcpyDeviceToHost, s));
+        QW_CUDA_TRY(cudaStreamSynchronize(s));
+        last = ls / (float)n;
+    }
+    if (final_loss) *final_loss = last;
+    return QW_OK;
+}
+
+qw_status qw_mlp_predict(qw_mlp *mp, const float *X, int64_t n, float *prob, void *stream)
+{
+    clear_error();
+    if (!mp || !X || !prob) return mlp_error("null pointer");
+    if (n < 0) return mlp_error("n < 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int B = 1024;
+    QW_TRY(mp->ensure_work(B));
+    for (int64_t r0 = 0; r0 < n; r0 += B) {
+        const int nb = (int)std::min<int64_t>(B, n - r0);
+        QW_TRY(mp->forward(X + r0 * mp->n_in, nb, s));
+        softmax_rows_kernel<<<(nb + 7) / 8, 256, 0, s>>>(mp->Z3, nb, mp->C, nullptr, 1.0f, nullptr,
+                                                         nullptr, prob + r0 * mp->C);
+        QW_CUDA_TRY(cudaGetLastError());
+    }
+    return QW_OK;
+}
+
+void qw_mlp_free(qw_mlp *mp)
+{
+    if (!mp) return;
+    cudaDeviceSynchronize();
+    delete mp;
+}
+
+}  // extern "C"
+
+namespace qw {
+
+int mlp_inputs(const qw_mlp *mp) { return mp ? mp->n_in : 0; }
+int mlp_classes(const qw_mlp *mp) { return mp ? mp->C : 0; }
+
+qw_status mlp_predict_dev(qw_mlp *mp, const float *X, int64_t n, float *prob, cudaStream_t s)
+{
+    return qw_mlp_predict(mp, X, n, prob, s);
+}
+
+qw_status launch_features(const float *Q, const int32_t *HQ, int64_t nq, const IndexView &ix,
+                          float xs, float *F, cudaStream_t s)
+{
+    if (nq == 0) return QW_OK;
+    features_kernel<<<(unsigned)nq, 128, 0, s>>>(Q, HQ, nq, ix.d, ix.m, ix.o, ix.span, xs, F);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
+
+qw_status launch_start_levels(const float *prob, int n, int C, float eps, int32_t *start,
+                              cudaStream_t s)
+{
+    if (n == 0) return QW_OK;
+    start_level_kernel<<<(n + 127) / 128, 128, 0, s>>>(prob, n, C, eps, start);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
+
+qw_status data_rms(const float *X, int64_t count, double *dev_acc, double *out, cudaStream_t s)
+{
+    QW_CUDA_TRY(cudaMemsetAsync(dev_acc, 0, sizeof(double), s));
+    sumsq_kernel<<<152 * 4, 256, 0, s>>>(X, count, dev_acc);
+    QW_CUDA_TRY(cudaGetLastError());
+    double h = 0.0;
+    QW_CUDA_TRY(cudaMemcpyAsync(&h, dev_acc, sizeof(double), cudaMemcpyDeviceToHost, s));
+    QW_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = count > 0 ? sqrt(h / (double)count) : 1.0;
+    return QW_OK;
+}
+
+}  // namespace qw

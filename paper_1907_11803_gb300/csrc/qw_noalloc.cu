@@ -59,7 +59,8 @@ size_t batch_bytes(size_t B, int m, int nT, int cap)
     total += up(B * m * sizeof(int32_t));            // query bucket ids
     total += up(B * m * sizeof(int64_t));            // anchored query ids
     total += 5 * up(B * sizeof(int64_t));            // top, finalR, scan_level, scan_last, scan_full
-    total += 7 * up(B * sizeof(int32_t));            // active, ncand, nprev, cross, term, levels, nkeep
+    total += 9 * up(B * sizeof(int32_t));            // active, ncand, nprev, cross, term, levels,
+                                                     // nkeep, start, fb
     total += up(B * (size_t)nT * kTile);             // collision counters
     total += up(B * (size_t)nT * kHistBins * 4);     // per-tile candidate profiles
     total += up(B * (size_t)nT * 3 * 4);             // per-tile emit plan
@@ -123,6 +124,7 @@ extern "C" qw_status qw_run_workload_noalloc(qw_index *index, const float *queri
     int *err = reinterpret_cast<int *>(hdr);
     QueryState st;
     st.max_top = reinterpret_cast<unsigned long long *>(hdr + 8);
+    st.fb_count = reinterpret_cast<unsigned long long *>(hdr + 16);
     int32_t *hq = reinterpret_cast<int32_t *>(take(B * m * sizeof(int32_t)));
     st.g = reinterpret_cast<int64_t *>(take(B * m * sizeof(int64_t)));
     st.top = reinterpret_cast<int64_t *>(take(B * 8));
@@ -137,6 +139,8 @@ extern "C" qw_status qw_run_workload_noalloc(qw_index *index, const float *queri
     st.term = reinterpret_cast<int32_t *>(take(B * 4));
     st.levels = reinterpret_cast<int32_t *>(take(B * 4));
     st.nkeep = reinterpret_cast<int32_t *>(take(B * 4));
+    st.start = reinterpret_cast<int32_t *>(take(B * 4));
+    st.fb = reinterpret_cast<int32_t *>(take(B * 4));
     st.counters = reinterpret_cast<uint32_t *>(take(B * (size_t)nT * kTile));
     st.tile_hist = reinterpret_cast<int32_t *>(take(B * (size_t)nT * kHistBins * 4));
     st.tile_plan = reinterpret_cast<int32_t *>(take(B * (size_t)nT * 3 * 4));
@@ -167,7 +171,7 @@ extern "C" qw_status qw_run_workload_noalloc(qw_index *index, const float *queri
         }
         int64_t R = 1, Rp = 1;
         for (int level = 0;; ++level) {
-            QW_TRY(launch_level(ix, nb, level, R, Rp, P.l, st, s));
+            QW_TRY(launch_level(ix, nb, level, R, Rp, P.l, P.c, st, s));
             QW_TRY(launch_decide(nb, level, R, cap, st, s));
             if ((unsigned long long)R > max_top) break;
             if (level > 62) {

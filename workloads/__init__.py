@@ -97,6 +97,7 @@ class Workload:
     b: np.ndarray          # m float32, offsets in [0, w)
     seed: int = 0
     extra: dict = field(default_factory=dict)
+    Q_train: Optional[np.ndarray] = None  # n_train x d: earlier queries of the same workload
 
 
 def _streams(seed: int):
@@ -132,15 +133,18 @@ def make_data(n: int, d: int, n_clusters: int, rng: np.random.Generator, *,
 
 def make_queries(X: np.ndarray, labels: np.ndarray, nq: int, rng: np.random.Generator, *,
                  n_clusters: int, query_clusters: int = 0, zipf: float = 0.0,
-                 noise=(0.1,)):
+                 noise=(0.1,), pool=None, return_pool: bool = False):
     """Queries from dense regions: a data row of a chosen cluster + noise.
 
-    Returns (Q float32 nq x d, src int64 nq).
+    Returns (Q float32 nq x d, src int64 nq), plus the cluster pool the queries
+    were limited to (None when unlimited) if ``return_pool``.  Passing ``pool``
+    reuses an earlier draw's pool: more queries of the same workload.
     """
     n, d = X.shape
     present = np.unique(labels)
     if query_clusters and query_clusters < present.size:
-        pool = rng.choice(present, size=query_clusters, replace=False)
+        if pool is None:
+            pool = rng.choice(present, size=query_clusters, replace=False)
         qlab = pool[rng.integers(0, pool.size, size=nq)]
     elif zipf > 0.0:
         p = _zipf_weights(n_clusters, zipf)
@@ -160,7 +164,10 @@ def make_queries(X: np.ndarray, labels: np.ndarray, nq: int, rng: np.random.Gene
     sig = np.asarray(noise, dtype=np.float32)
     qsig = sig[np.arange(nq) % sig.size] if sig.size > 1 else np.full(nq, sig[0], np.float32)
     Q = X[src] + rng.standard_normal((nq, d), dtype=np.float32) * qsig[:, None]
-    return np.ascontiguousarray(Q, dtype=np.float32), src
+    Q = np.ascontiguousarray(Q, dtype=np.float32)
+    if return_pool:
+        return Q, src, pool
+    return Q, src
 
 
 def make_projections(m: int, d: int, w: float, rng: np.random.Generator):
@@ -172,11 +179,13 @@ def make_projections(m: int, d: int, w: float, rng: np.random.Generator):
 
 
 def make_workload(spec, seed: int = 0, *, n: Optional[int] = None, nq: Optional[int] = None,
-                  **overrides) -> Workload:
+                  n_train: int = 0, **overrides) -> Workload:
     """Build a whole workload from a spec name or a ``WorkloadSpec``.
 
     ``n``/``nq`` and any other field can be overridden to get a smaller case
-    with the same structure.
+    with the same structure.  ``n_train`` > 0 also draws that many training
+    queries (``Q_train``): the same data, cluster pool and noise mix as ``Q``,
+    from a separate random stream, so ``Q`` does not depend on ``n_train``.
     """
     if isinstance(spec, str):
         spec = SPECS[spec]
@@ -190,8 +199,14 @@ def make_workload(spec, seed: int = 0, *, n: Optional[int] = None, nq: Optional[
     r_data, r_query, r_proj, r_extra = _streams(seed)
     X, labels, _ = make_data(spec.n, spec.d, spec.n_clusters, r_data, zipf=spec.zipf,
                              sigma=spec.sigma, center_range=spec.center_range)
-    Q, src = make_queries(X, labels, spec.nq, r_query, n_clusters=spec.n_clusters,
-                          query_clusters=spec.query_clusters, zipf=spec.zipf,
-                          noise=spec.query_noise)
+    Q, src, pool = make_queries(X, labels, spec.nq, r_query, n_clusters=spec.n_clusters,
+                                query_clusters=spec.query_clusters, zipf=spec.zipf,
+                                noise=spec.query_noise, return_pool=True)
     A, b = make_projections(spec.m, spec.d, spec.w, r_proj)
-    return Workload(spec=spec, X=X, labels=labels, Q=Q, q_src=src, A=A, b=b, seed=seed)
+    Q_train = None
+    if n_train > 0:
+        Q_train, _ = make_queries(X, labels, n_train, r_extra, n_clusters=spec.n_clusters,
+                                  query_clusters=spec.query_clusters, zipf=spec.zipf,
+                                  noise=spec.query_noise, pool=pool)
+    return Workload(spec=spec, X=X, labels=labels, Q=Q, q_src=src, A=A, b=b, seed=seed,
+                    extra={"query_pool": pool}, Q_train=Q_train)
