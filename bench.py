@@ -5,7 +5,14 @@ One step = one call answering the whole synthetic query workload (project the
 queries, collision counting over all levels, candidate selection, distances,
 top-k) against an index already resident in HBM.  The default workload is
 1,000,000 x 128 float32 points (Gaussian mixture of 1,000 clusters), 64
-projections, w = 4, 10,000 queries from 100 clusters, k = 100, v = 100.
+projections, w = 4, 10,000 queries from 100 clusters, k = 100.
+
+Two configurations of the same call are timed, with identical results: the
+plain path (queries in the given order, collision counting from level 0, FP32
+distances) and the chosen path (queries grouped by bucket signature, learned
+first levels, BF16 distance pre-filter).  ``value`` is the chosen path's; the
+plain path's figures are reported beside it.  The start model is trained
+before the timed region on queries drawn from the same workload.
 
 Prints one JSON line.  ``--impl reference`` times the CPU oracle on a bounded
 sample of the same workload instead.  Under torchrun (``--gpus N``) every rank
@@ -59,6 +66,17 @@ def parse_args(argv=None):
                    help="execution path of the query loop (identical results)")
     p.add_argument("--order", choices=["auto", "signature", "given"], default="auto",
                    help="workload order: grouped by bucket signature, or as given")
+    p.add_argument("--rerank", choices=["fp32", "bf16"], default="bf16",
+                   help="distance arithmetic of the chosen path (identical results)")
+    p.add_argument("--start", choices=["plain", "learned"], default="learned",
+                   help="first level of the chosen path (identical results)")
+    p.add_argument("--train-queries", type=int, default=20_000,
+                   help="queries the start model is trained and the autotuner run on (untimed)")
+    p.add_argument("--no-tune", action="store_true",
+                   help="chosen path from --path/--order/--rerank/--start/--graph instead of "
+                        "the autotuner")
+    p.add_argument("--graph", action="store_true",
+                   help="with --no-tune: run the level loop as a CUDA graph")
     p.add_argument("--v", type=int, default=-1,
                    help="allowed false positives (-1 = the workload's operating point)")
     p.add_argument("--l", type=int, default=-1,
@@ -266,6 +284,23 @@ def oracle_sample(wl, l, n_queries, seed=1, v=None):
 
 
 # ---------------------------------------------------------------- our arm
+def train_start_model(qw, torch, index, Qt, k, args):
+    """Train the first-level model on earlier queries of the same workload
+    (labels: the level each one stops at on the plain path).  Untimed."""
+    t0 = time.perf_counter()
+    _, _, st = index.query(Qt, k, stats=True, start="plain")
+    labels = (st[:, 0] - 1).clamp(0, 15).to(torch.int32).contiguous()
+    F = index.features(Qt)
+    mlp = qw.Mlp(F.shape[1], 256, 16)
+    mlp.set_params(qw.mlp_init(F.shape[1], 256, 16, seed=args.seed + 5))
+    loss = mlp.train(F, labels, epochs=20, batch=512, lr=1e-3)
+    acc = float((mlp.predict(F).argmax(1) == labels).float().mean())
+    index.set_start_model(mlp, eps=0.02)
+    return mlp, {"train_queries": int(Qt.shape[0]), "epochs": 20, "final_loss": round(loss, 4),
+                 "train_accuracy": round(acc, 4), "eps": 0.02,
+                 "seconds": round(time.perf_counter() - t0, 2)}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -291,45 +326,77 @@ def run_ours(args):
     b = torch.from_numpy(wl.b).to(dev)
     Q = torch.from_numpy(wl.Q).to(dev)
     v_used, l_arg = operating_point(args, s)
-    index = qw.Index(X, A, b, w=s.w, c=s.c, v=v_used, l=l_arg)
+    index = qw.Index(X, A, b, w=s.w, c=s.c, v=v_used, l=l_arg,
+                     shadow_bf16=args.rerank == "bf16")
     ids = torch.empty((s.nq, s.k), dtype=torch.int64, device=dev)
     dists = torch.empty((s.nq, s.k), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    for _ in range(args.warmup):
-        index.query(Q, s.k, out=(ids, dists), batch=args.batch, path=args.path, order=args.order)
-    torch.cuda.synchronize()
-    _, _, st = index.query(Q, s.k, stats=True, batch=args.batch, path=args.path, order=args.order)
+    plain_kw = dict(batch=args.batch, path="levels", order="given", rerank="fp32",
+                    start="plain", graph=False)
+    chosen_kw = dict(batch=args.batch, path=args.path, order=args.order, rerank=args.rerank,
+                     start=args.start, graph=args.graph)
+    mlp = None
+    train_info = None
+    wt = workloads.make_workload(args.workload, seed=args.seed, nq=1, n_train=args.train_queries)
+    Qt = torch.from_numpy(wt.Q_train).to(dev)
+    if args.start == "learned":
+        mlp, train_info = train_start_model(qw, torch, index, Qt, s.k, args)
+        if args.no_tune:
+            chosen_kw["path"] = "levels"  # learned first levels run on the level path
+    tune = None
+    if not args.no_tune:
+        # settings from the autotuner, timed on earlier queries of the same workload
+        t0 = time.perf_counter()
+        chosen_kw, trials = index.autotune(Qt[:s.nq], s.k, reps=1)
+        tune = {"seconds": round(time.perf_counter() - t0, 2), "queries": int(min(s.nq, Qt.shape[0])),
+                "trials": [dict(t, ms=round(ms, 3)) for t, ms in trials]}
+
+    def timed(kw, steps):
+        for _ in range(args.warmup):
+            index.query(Q, s.k, out=(ids, dists), **kw)
+        torch.cuda.synchronize()
+        index.profile(reset=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            index.query(Q, s.k, out=(ids, dists), profile=True, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = e0.elapsed_time(e1)
+        return ms, max_over_ranks(ms, world), index.profile(reset=True)
+
+    # the plain path first: its results are the reference for the chosen one
+    _, _, st = index.query(Q, s.k, stats=True, **plain_kw)
     st = st.cpu().numpy()
-    index.profile(reset=True)
+    p_ms, p_ms_max, p_prof = timed(plain_kw, args.steps)
+    ids_plain, dists_plain = ids.clone(), dists.clone()
 
     clocks = ClockSampler(gpu_uuid(torch))
-    barrier(world)
-    torch.cuda.synchronize()
     clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        index.query(Q, s.k, out=(ids, dists), profile=True, batch=args.batch, path=args.path, order=args.order)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
+    ms, ms_max, prof = timed(chosen_kw, args.steps)
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    prof = index.profile(reset=True)
-    ms_max = max_over_ranks(ms, world)
     value = world * s.nq * args.steps / (ms_max / 1e3)
+    same = bool(torch.equal(ids, ids_plain) and torch.equal(dists, dists_plain))
+    plain = {"value": world * s.nq * args.steps / (p_ms_max / 1e3),
+             "ms_per_step": p_ms_max / args.steps, "settings": plain_kw,
+             "results_identical_to_chosen": same,
+             "kernel_ms_per_step": {k2: round(v2 / args.steps, 3)
+                                    for k2, v2 in p_prof["ms"].items()}}
 
     # end to end through the public API: pinned host queries in, host results out
     Qh = torch.from_numpy(wl.Q).pin_memory()
     ids_h = torch.empty((s.nq, s.k), dtype=torch.int64).pin_memory()
     dists_h = torch.empty((s.nq, s.k), dtype=torch.float32).pin_memory()
-    index.query(Qh, s.k, out=(ids_h, dists_h), batch=args.batch, path=args.path, order=args.order)
+    index.query(Qh, s.k, out=(ids_h, dists_h), **chosen_kw)
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        index.query(Qh, s.k, out=(ids_h, dists_h), batch=args.batch, path=args.path, order=args.order)
+        index.query(Qh, s.k, out=(ids_h, dists_h), **chosen_kw)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     e2e = {"value": world * s.nq * args.steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(Qh.numel() * 4),
@@ -351,7 +418,8 @@ def run_ours(args):
     dom = "cluster" if prof["ms"]["cluster"] >= prof["ms"]["level"] else "level"
     dom_name = {"cluster": "cluster_query_kernel (all levels of collision counting, persistent)",
                 "level": "level_kernel (bucket-range search + collision counting)"}[dom]
-    dom_launches = prof["timed_launches"][dom] / steps
+    # launches actually run (graph mode counts the device-driven level passes)
+    dom_launches = prof["launches"][dom] / steps
     dom_ms = prof["ms"][dom] / steps
     per_launch_bytes = count_bytes / max(dom_launches, 1)
     per_launch_s = (dom_ms / 1e3) / max(dom_launches, 1)
@@ -392,12 +460,13 @@ def run_ours(args):
                    "k": s.k, "v": v_used, "l": index.l, "queries_per_gpu": s.nq,
                    "query_clusters": s.query_clusters, "seed": args.seed,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "path": args.path, "order": args.order,
+                   "chosen": chosen_kw, "start_model": train_info, "autotune": tune,
                    "l2": "inputs larger than L2 (index %.2f GB + data %.2f GB + counters)"
                          % (index.info.device_bytes / 1e9 - s.n * s.d * 4 / 1e9,
                             s.n * s.d * 4 / 1e9)},
         "quality": {"recall": round(recall, 4), "ratio": round(ratio, 5),
                     "sample": int(pick.numel()), "meets_target": recall >= 0.9 and ratio <= 1.05},
+        "plain": plain,
         "roofline": roofline, "roofline_gather": roofline_gather,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk,
@@ -407,6 +476,8 @@ def run_ours(args):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if mlp is not None:
+        mlp.free()
     index.free()
     if world > 1:
         import torch.distributed as dist

@@ -101,6 +101,10 @@ typedef struct {
     int32_t rerank;       /* QW_RERANK_FP32 (default) or QW_RERANK_BF16 (needs shadow_bf16) */
     int32_t start;        /* QW_START_PLAIN (default) or QW_START_LEARNED (level path; needs a
                              start model, see qw_index_set_start_model) */
+    int32_t graph;        /* non-zero (level path): each batch's level loop runs as one CUDA
+                             graph whose conditional WHILE node advances the level on the
+                             device, so the host does not wait inside a batch; the call waits
+                             for the stream once at its end.  Same kernels, same results */
     int32_t reserved[1];  /* must be zero */
 } qw_query_params;
 
@@ -133,7 +137,7 @@ typedef struct {
  *   answers one query at a time with its counters in shared memory for all
  *   levels and pulls the next query from a work queue; indexes of up to
  *   96 tiles (3,145,728 points).
- * QW_PATH_AUTO: the cluster path when the index fits, else the level path. */
+ * QW_PATH_AUTO: the path qw_autotune chose for the index, else the level path. */
 #define QW_PATH_AUTO 0
 #define QW_PATH_CLUSTER 1
 #define QW_PATH_LEVELS 2
@@ -217,7 +221,8 @@ qw_status qw_hash(const float *V, int64_t nv, int32_t d, const float *A, const f
  * call returns (device mode: after the stream has passed the call).
  * Layout built (Section 2: one sorted structure per hash function):
  *   anchor o_i = min over data of h_i, bucket id bid = h_i - o_i >= 0,
- *   and, for every projection, the (bid, id) pairs sorted by bid then id,
+ *   and, for every projection, the (bid, id) pairs sorted by bid (ids within
+ *   a bucket in the bank-spread order described at qw_index_export),
  *   grouped by id tile, with a directory of the distinct bids of each tile.
  * The call waits for the stream.  *out receives the handle (free with
  * qw_index_free).
@@ -293,8 +298,37 @@ qw_status qw_run_workload_noalloc(qw_index *index, const float *queries, int64_t
  * when `reset` is non-zero. */
 qw_status qw_index_profile(qw_index *index, qw_profile *out, int32_t reset);
 
-/* ---- The learned start model (a13 of the path; the paper trains an offline
- * model for its cache split in Section 5.2 but prints no network).
+/* Settings qw_autotune tried, with their median times. */
+#define QW_TUNE_MAX 32
+typedef struct {
+    int32_t tried;                         /* entries filled below */
+    qw_query_params params[QW_TUNE_MAX];   /* each setting tried */
+    float ms[QW_TUNE_MAX];                 /* its median time over `reps` calls */
+    int32_t best;                          /* index of the chosen setting */
+} qw_tune_report;
+
+/* Autotuner of the workload path (the paper has no counterpart; its settings
+ * change speed only).  Times qw_run_workload on the given queries (a sample
+ * of the workload, `mem` space) under candidate settings, one coordinate at a
+ * time, keeping the fastest before moving on: start level (plain / learned,
+ * when a start model is attached), queries per batch on the level path (the
+ * default and 1/16, 1/4, 4x of it), graph mode, then the cluster path against
+ * that best level setting (when the index fits it and the start is plain),
+ * order (signature / given) and rerank (FP32 / BF16, when the index has the
+ * BF16 copy).  Every setting returns the same results, so the choice cannot change
+ * them.  Each setting runs once untimed, then `reps` (>= 1) times timed with
+ * CUDA events on `stream`; the median counts.  The chosen setting is written
+ * to *best (host) and stored in the index: later calls with QW_PATH_AUTO take
+ * its path and, with batch 0, its batch size.  report (host, optional)
+ * receives every setting tried.  base (optional) gives the fields not tuned
+ * (profile); NULL means zero.  Waits for the stream.
+ * Errors: as qw_run_workload; QW_ERR_ARG also for reps < 1 or best NULL. */
+qw_status qw_autotune(qw_index *index, const float *queries, int64_t nq, int32_t k, int32_t mem,
+                      int32_t reps, const qw_query_params *base, qw_query_params *best,
+                      qw_tune_report *report, void *stream);
+
+/* ---- The learned start model (the paper trains an offline model for its
+ * cache split in Section 5.2 but prints no network).
  * A multilayer perceptron n_in -> hidden -> hidden -> classes with ReLU,
  * softmax cross-entropy, FP16 weight copies of FP32 master weights and FP32
  * accumulation; trained with Adam by the library's kernels.  Parameters are a
@@ -336,7 +370,10 @@ qw_status qw_index_get_info(const qw_index *index, qw_index_info *info);
 
 /* Export the index for inspection, into HOST buffers: o and span (m int32),
  * and, per projection, every entry's bucket id and data id (m x n int32 each)
- * in the index's own order: by id tile (id / tile), then bucket id, then id.
+ * in the index's own order: by id tile (id / tile), then bucket id; within a
+ * bucket, ids are arranged so that consecutive entries fall into different
+ * shared-memory banks of the counting kernels (groups of 8 ids of one bank,
+ * the groups cycling through the banks).
  * Any output pointer may be NULL.  Waits for the stream. */
 qw_status qw_index_export(const qw_index *index, int32_t *o, int32_t *span,
                           int32_t *entry_bid, int32_t *entry_id, void *stream);

@@ -35,7 +35,8 @@ EXPORTED = ("qw_version", "qw_last_error", "qw_collision_probability",
             "qw_workload_candidates", "qw_run_workload_noalloc", "qw_index_profile",
             "qw_index_get_info", "qw_mlp_create", "qw_mlp_param_count", "qw_mlp_set_params",
             "qw_mlp_get_params", "qw_mlp_loss_grad", "qw_mlp_train", "qw_mlp_predict",
-            "qw_mlp_free", "qw_query_features", "qw_index_set_start_model", "qw_index_export", "qw_index_free")
+            "qw_mlp_free", "qw_query_features", "qw_index_set_start_model", "qw_autotune",
+            "qw_index_export", "qw_index_free")
 
 
 class qw_index_params(C.Structure):
@@ -46,7 +47,15 @@ class qw_index_params(C.Structure):
 class qw_query_params(C.Structure):
     _fields_ = [("batch", C.c_int32), ("profile", C.c_int32), ("path", C.c_int32),
                 ("clusters", C.c_int32), ("order", C.c_int32), ("rerank", C.c_int32),
-                ("start", C.c_int32), ("reserved", C.c_int32 * 1)]
+                ("start", C.c_int32), ("graph", C.c_int32), ("reserved", C.c_int32 * 1)]
+
+
+QW_TUNE_MAX = 32
+
+
+class qw_tune_report(C.Structure):
+    _fields_ = [("tried", C.c_int32), ("params", qw_query_params * QW_TUNE_MAX),
+                ("ms", C.c_float * QW_TUNE_MAX), ("best", C.c_int32)]
 
 
 QW_PATH_AUTO, QW_PATH_CLUSTER, QW_PATH_LEVELS = 0, 1, 2
@@ -138,6 +147,10 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.qw_mlp_predict.argtypes = [vp, vp, C.c_int64, vp, vp]
     L.qw_mlp_free.restype = None
     L.qw_mlp_free.argtypes = [vp]
+    L.qw_autotune.restype = C.c_int32
+    L.qw_autotune.argtypes = [vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_int32,
+                              C.POINTER(qw_query_params), C.POINTER(qw_query_params),
+                              C.POINTER(qw_tune_report), vp]
     L.qw_query_features.restype = C.c_int32
     L.qw_query_features.argtypes = [vp, vp, C.c_int64, vp, vp]
     L.qw_index_set_start_model.restype = C.c_int32
@@ -237,6 +250,14 @@ def _torch():
     return torch
 
 
+def _params_kwargs(p) -> dict:
+    """query() keyword arguments of a qw_query_params."""
+    inv = lambda d, v: next(k for k, x in d.items() if x == v)  # noqa: E731
+    return {"batch": int(p.batch), "path": inv(PATHS, p.path), "order": inv(ORDERS, p.order),
+            "rerank": inv(RERANKS, p.rerank), "start": inv(STARTS, p.start),
+            "graph": bool(p.graph)}
+
+
 def _stream_of(t) -> int:
     torch = _torch()
     if t.is_cuda:
@@ -323,7 +344,8 @@ class Index:
 
     def query(self, Q, k: int, *, batch: int = 0, stats: bool = False, out=None,
               profile: bool = False, path: str = "auto", clusters: int = 0,
-              order: str = "auto", rerank: str = "fp32", start: str = "plain"):
+              order: str = "auto", rerank: str = "fp32", start: str = "plain",
+              graph: bool = False):
         """Top-k of every query row.  Returns (ids int64 nq x k, dists float32
         nq x k[, stats int64 nq x QW_NSTAT]) on Q's device (host tensors in,
         host tensors out).  ``out`` may give preallocated (ids, dists[, stats])."""
@@ -344,12 +366,13 @@ class Index:
         mem = _mem_of(Q, ids, dists, st)
         qp = qw_query_params(batch=int(batch), profile=1 if profile else 0, path=PATHS[path],
                              clusters=int(clusters), order=ORDERS[order], rerank=RERANKS[rerank],
-                             start=STARTS[start])
+                             start=STARTS[start], graph=1 if graph else 0)
         qw_run_workload(self._h, Q.data_ptr(), nq, int(k), qp, ids.data_ptr(), dists.data_ptr(),
                         st.data_ptr() if st is not None else 0, mem, _stream_of(Q))
         return (ids, dists, st) if stats else (ids, dists)
 
-    def candidates(self, Q, k: int, *, batch: int = 0, path: str = "auto", order: str = "auto"):
+    def candidates(self, Q, k: int, *, batch: int = 0, path: str = "auto", order: str = "auto",
+                   graph: bool = False):
         """Kept candidates per query (ascending ids, -1 padded) with their
         collision counts, and the per-query statistics, on Q's device."""
         torch = _torch()
@@ -360,7 +383,8 @@ class Index:
         ccol = torch.empty((nq, cap), dtype=torch.int32, device=Q.device)
         st = torch.empty((nq, QW_NSTAT), dtype=torch.int64, device=Q.device)
         mem = _mem_of(Q, cid, ccol, st)
-        qp = qw_query_params(batch=int(batch), path=PATHS[path], order=ORDERS[order])
+        qp = qw_query_params(batch=int(batch), path=PATHS[path], order=ORDERS[order],
+                             graph=1 if graph else 0)
         qw_workload_candidates(self._h, Q.data_ptr(), nq, int(k), qp, cid.data_ptr(),
                                ccol.data_ptr(), st.data_ptr(), mem, _stream_of(Q))
         return cid, ccol, st
@@ -379,9 +403,22 @@ class Index:
         _check(load().qw_index_set_start_model(self._h, mlp.handle if mlp else None, float(eps)))
         self._start_model = mlp
 
+    def autotune(self, Q, k: int, *, reps: int = 3):
+        """Time the workload Q under the candidate settings (qw_autotune) and keep
+        the fastest for path='auto' / batch=0.  Returns (best settings as
+        query() keyword arguments, [(settings, median ms), ...] of every trial)."""
+        _f32(Q, "Q")
+        mem = _mem_of(Q)
+        best = qw_query_params()
+        rep = qw_tune_report()
+        _check(load().qw_autotune(self._h, Q.data_ptr(), Q.shape[0], int(k), mem, int(reps), None,
+                                  C.byref(best), C.byref(rep), _stream_of(Q) or None))
+        trials = [(_params_kwargs(rep.params[i]), float(rep.ms[i])) for i in range(rep.tried)]
+        return _params_kwargs(best), trials
+
     def export(self):
         """Host numpy copies: o (m), span (m), entry_bid and entry_id (m x n),
-        entries of each projection ordered by (id tile, bid, id)."""
+        entries of each projection ordered by (id tile, bid, bank-spread order)."""
         import numpy as np
         o = np.empty(self.m, np.int32)
         span = np.empty(self.m, np.int32)

@@ -72,6 +72,10 @@ struct qw_index {
     float xs = 1.0f;                 // 1 / RMS coordinate of the data (start-model features)
     qw_mlp *start_model = nullptr;   // not owned
     float start_eps = 0.02f;
+    LevelGraphCache *graphs = nullptr;  // graph mode of the level loop
+    bool tuned = false;                 // qw_autotune ran: QW_PATH_AUTO / batch 0 use these
+    int32_t tuned_path = QW_PATH_LEVELS;
+    int32_t tuned_batch = 0;
     DevBuf w_feat;
     // workspace for queries (grow-only)
     DevBuf w_q, w_hq, w_state, w_counters, w_cand, w_out, w_err, w_order, w_qb, w_ob;
@@ -375,6 +379,46 @@ qw_status qw_build_index(const float *data, int64_t n, int32_t d, const float *A
     return QW_OK;
 }
 
+// The level loop of one batch, driven by the host: levels 0..L where c^L
+// exceeds the batch's largest useful radius (afterwards every query has
+// stopped); with learned starts, a second pass from level 0 for the queries
+// that stopped at their learned first level.
+static qw_status host_level_loop(qw_index *ix, LaunchTimer &tm, const IndexView &view, int nb,
+                                 int cap, bool learned, QueryState &st, cudaStream_t s)
+{
+    unsigned long long max_top = 0;
+    QW_CUDA_TRY(cudaMemcpyAsync(&max_top, st.max_top, sizeof(max_top), cudaMemcpyDeviceToHost, s));
+    QW_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int pass = 0; pass < 2; ++pass) {
+        int64_t R = 1, Rp = 1;
+        for (int level = 0;; ++level) {
+            QW_TRY(tm.run(QW_K_LEVEL, 1, [&] {
+                return launch_level(view, nb, level, R, Rp, ix->l, ix->c, st, s);
+            }));
+            QW_TRY(tm.run(QW_K_DECIDE, 1, [&] { return launch_decide(nb, level, R, cap, st, s); }));
+            if ((unsigned long long)R > max_top) break;
+            if (level > 62) {
+                set_error("qw_run_workload: level limit reached");
+                return QW_ERR_TIMEOUT;
+            }
+            Rp = R;
+            R *= ix->c;
+        }
+        if (!learned) break;
+        unsigned long long fbc[2] = {0, 0};
+        QW_TRY(tm.run(QW_K_DECIDE, 1, [&] { return launch_fallback(nb, st, s); }));
+        QW_CUDA_TRY(cudaMemcpyAsync(fbc, st.fb_count, sizeof(fbc), cudaMemcpyDeviceToHost, s));
+        QW_CUDA_TRY(cudaStreamSynchronize(s));
+        if (pass == 0) {
+            ix->prof.start_fallbacks += (int64_t)fbc[0];
+            ix->prof.start_levels_skipped += (int64_t)fbc[1];
+        }
+        if (fbc[0] == 0) break;
+        QW_CUDA_TRY(cudaMemsetAsync(st.fb_count, 0, 16, s));
+    }
+    return QW_OK;
+}
+
 static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                           const qw_query_params *qp, int64_t *ids, float *dists,
                           int64_t *stats, int64_t *cand_ids, int32_t *cand_col, int32_t mem,
@@ -408,8 +452,18 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         set_error("qw_run_workload: learned start levels run on the level path");
         return QW_ERR_ARG;
     }
-    const bool use_cluster = fits && path != QW_PATH_LEVELS && !learned;
+    const bool graph = qp && qp->graph != 0;
+    if (graph && path == QW_PATH_CLUSTER) {
+        set_error("qw_run_workload: graph mode runs the level path");
+        return QW_ERR_ARG;
+    }
+    // QW_PATH_AUTO: the tuned path if the index was tuned, else the level path
+    int eff_path = path;
+    if (eff_path == QW_PATH_AUTO)
+        eff_path = (ix->tuned && !learned && !graph) ? ix->tuned_path : QW_PATH_LEVELS;
+    const bool use_cluster = eff_path == QW_PATH_CLUSTER && fits;
     int64_t B = qp && qp->batch > 0 ? qp->batch : 0;
+    if (B == 0 && ix->tuned && ix->tuned_batch > 0 && !use_cluster) B = ix->tuned_batch;
     if (B == 0) {
         const int64_t budget = (int64_t)2 << 30;  // counters of one batch
         B = use_cluster ? (int64_t)65535 : std::max<int64_t>(1, budget / wpq_bytes);
@@ -425,7 +479,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     QW_TRY(ix->w_cand.ensure((size_t)B * cap * 2 * sizeof(int32_t)));
     const size_t plan_ints = (size_t)B * ix->nT * (kHistBins + 3) + (size_t)B * 2;
     const size_t st_bytes = (size_t)B * m * 8 + (size_t)B * 8 * 16 + plan_ints * 4 + 256 +
-                            (size_t)B * 4 * 2 + 64;
+                            (size_t)B * 4 * 2 + 64 + 16 * ((sizeof(LoopCtl) + 15) / 16);
     QW_TRY(ix->w_state.ensure(st_bytes));
     int nclass = 0;
     if (learned) {
@@ -476,6 +530,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                                up16(b_ccol) + 16));
     }
     QueryState st;
+    LoopCtl *ctl = nullptr;
     {
         char *p = ix->w_state.as<char>();
         auto take = [&](size_t bytes) { char *r = p; p += (bytes + 15) / 16 * 16; return r; };
@@ -499,6 +554,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         st.start = reinterpret_cast<int32_t *>(take((size_t)B * 4));
         st.fb = reinterpret_cast<int32_t *>(take((size_t)B * 4));
         st.fb_count = reinterpret_cast<unsigned long long *>(take(16));
+        ctl = reinterpret_cast<LoopCtl *>(take(sizeof(LoopCtl)));
         if ((size_t)(p - ix->w_state.as<char>()) > ix->w_state.bytes) {
             set_error("internal: query state workspace too small");
             return QW_ERR_CUDA;
@@ -543,8 +599,17 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         }
     }
 
+    int64_t n_batches = 0;
+    if (graph && !use_cluster) {
+        if (!ix->graphs && !(ix->graphs = level_graph_cache_new())) {
+            set_error("qw_run_workload: out of host memory");
+            return QW_ERR_OOM;
+        }
+        QW_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(LoopCtl), s));
+    }
     for (int64_t b0 = 0; b0 < nq; b0 += B) {
         const int nb = (int)std::min<int64_t>(B, nq - b0);
+        ++n_batches;
         const float *Qb;
         const int32_t *HQb;
         int64_t *ids_b = nullptr, *stats_b = nullptr, *cids_b = nullptr;
@@ -607,36 +672,13 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                 }));
                 QW_CUDA_TRY(cudaMemsetAsync(st.fb_count, 0, 16, s));
             }
-            unsigned long long max_top = 0;
-            QW_CUDA_TRY(cudaMemcpyAsync(&max_top, st.max_top, sizeof(max_top),
-                                        cudaMemcpyDeviceToHost, s));
-            QW_CUDA_TRY(cudaStreamSynchronize(s));
-            // levels 0..L where c^L > max_top: afterwards every query has stopped
-            for (int pass = 0; pass < 2; ++pass) {
-                int64_t R = 1, Rp = 1;
-                for (int level = 0;; ++level) {
-                    QW_TRY(tm.run(QW_K_LEVEL, 1, [&] { return launch_level(view, nb, level, R, Rp, ix->l, ix->c, st, s); }));
-                    QW_TRY(tm.run(QW_K_DECIDE, 1, [&] { return launch_decide(nb, level, R, cap, st, s); }));
-                    if ((unsigned long long)R > max_top) break;
-                    if (level > 62) {
-                        set_error("qw_run_workload: level limit reached");
-                        return QW_ERR_TIMEOUT;
-                    }
-                    Rp = R;
-                    R *= ix->c;
-                }
-                if (!learned) break;
-                // queries that stopped at a learned first level run again from level 0
-                unsigned long long fbc[2] = {0, 0};
-                QW_TRY(launch_fallback(nb, st, s));
-                QW_CUDA_TRY(cudaMemcpyAsync(fbc, st.fb_count, sizeof(fbc), cudaMemcpyDeviceToHost, s));
-                QW_CUDA_TRY(cudaStreamSynchronize(s));
-                if (pass == 0) {
-                    ix->prof.start_fallbacks += (int64_t)fbc[0];
-                    ix->prof.start_levels_skipped += (int64_t)fbc[1];
-                }
-                if (fbc[0] == 0) break;
-                QW_CUDA_TRY(cudaMemsetAsync(st.fb_count, 0, 16, s));
+            if (graph) {
+                QW_TRY(tm.run(QW_K_LEVEL, 0, [&] {
+                    return run_level_graph(ix->graphs, view, nb, ix->l, ix->c, cap, learned, st,
+                                           ctl, err, s);
+                }));
+            } else {
+                QW_TRY(host_level_loop(ix, tm, view, nb, cap, learned, st, s));
             }
             QW_TRY(tm.run(QW_K_SELECT, 2, [&] { return launch_collect(view, nb, ix->l, cap, st, stats_b, s); }));
         }
@@ -656,6 +698,25 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                 return launch_scatter(perm, b0, nb, k, cap, ids_b, dists_b, stats_b, cids_b, ccol_b,
                                       f_ids, f_dists, f_stats, f_cids, f_ccol, s);
             }));
+        }
+    }
+    if (graph && !use_cluster) {
+        // the device-driven loops: their launch counts, the level-limit flag and
+        // the learned-start counters, once per call
+        LoopCtl h_ctl;
+        int h_err = 0;
+        QW_CUDA_TRY(cudaMemcpyAsync(&h_ctl, ctl, sizeof(h_ctl), cudaMemcpyDeviceToHost, s));
+        QW_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        QW_CUDA_TRY(cudaStreamSynchronize(s));
+        if (h_err & 8) {
+            set_error("qw_run_workload: level limit reached");
+            return QW_ERR_TIMEOUT;
+        }
+        ix->prof.launches[QW_K_LEVEL] += (int64_t)h_ctl.iters;
+        ix->prof.launches[QW_K_DECIDE] += 2 * (int64_t)h_ctl.iters + n_batches * (learned ? 3 : 1);
+        if (learned) {
+            ix->prof.start_fallbacks += (int64_t)h_ctl.fb_total;
+            ix->prof.start_levels_skipped += (int64_t)h_ctl.skipped_total;
         }
     }
     if (host) {
@@ -702,6 +763,7 @@ static qw_status check_workload_args(const qw_index *ix, const float *queries, i
             return arg_error("qw_run_workload: unknown rerank");
         if (qp->start < QW_START_PLAIN || qp->start > QW_START_LEARNED)
             return arg_error("qw_run_workload: unknown start");
+        if (qp->graph != 0 && qp->graph != 1) return arg_error("qw_run_workload: graph must be 0 or 1");
         for (int r = 0; r < 1; ++r)
             if (qp->reserved[r] != 0) return arg_error("qw_run_workload: reserved field set");
     }
@@ -718,6 +780,158 @@ qw_status qw_run_workload(qw_index *ix, const float *queries, int64_t nq, int32_
     if (nq == 0) return QW_OK;
     return run_impl(ix, queries, nq, k, qp, ids, dists, stats, nullptr, nullptr, mem,
                     (cudaStream_t)stream);
+}
+
+qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k, int32_t mem,
+                      int32_t reps, const qw_query_params *base, qw_query_params *best,
+                      qw_tune_report *report, void *stream)
+{
+    clear_error();
+    qw_query_params p0{};
+    if (base) p0 = *base;
+    p0.batch = 0;
+    p0.path = QW_PATH_LEVELS;
+    p0.order = QW_ORDER_SIGNATURE;
+    p0.rerank = QW_RERANK_FP32;
+    p0.start = QW_START_PLAIN;
+    p0.graph = 0;
+    p0.clusters = 0;
+    QW_TRY(check_workload_args(ix, queries, nq, k, &p0, mem));
+    if (!best) return arg_error("qw_autotune: best is null");
+    if (reps < 1) return arg_error("qw_autotune: reps < 1");
+    if (nq < 1) return arg_error("qw_autotune: no queries");
+    if (report) memset(report, 0, sizeof(*report));
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool host = mem == QW_MEM_HOST;
+    // results of every trial go to one device buffer (host mode: host buffer)
+    DevBuf out_dev;
+    std::vector<char> out_host;
+    const size_t ob = (size_t)nq * k * (sizeof(int64_t) + sizeof(float));
+    int64_t *ids;
+    float *dists;
+    if (host) {
+        try {
+            out_host.resize(ob);
+        } catch (const std::bad_alloc &) {
+            set_error("qw_autotune: out of host memory");
+            return QW_ERR_OOM;
+        }
+        ids = reinterpret_cast<int64_t *>(out_host.data());
+    } else {
+        QW_TRY(out_dev.ensure(ob));
+        ids = out_dev.as<int64_t>();
+    }
+    dists = reinterpret_cast<float *>(ids + (size_t)nq * k);
+    cudaEvent_t e0, e1;
+    QW_CUDA_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_status(cudaErrorUnknown, "cudaEventCreate");
+    }
+    // the library's own batch choice for the level path, as the base of the batch sweep
+    const int64_t wpq_bytes = (int64_t)ix->nT * kTile;
+    const int64_t b_default =
+        std::min<int64_t>(std::min<int64_t>(std::max<int64_t>(1, ((int64_t)2 << 30) / wpq_bytes), nq),
+                          65535);
+    const bool saved_tuned = ix->tuned;
+    ix->tuned = false;  // trials name their path and batch explicitly
+    int tried = 0;
+    qw_status status = QW_OK;
+    auto time_one = [&](const qw_query_params &p, float *ms_out) -> qw_status {
+        QW_TRY(run_impl(ix, queries, nq, k, &p, ids, dists, nullptr, nullptr, nullptr, mem, s));
+        std::vector<float> t;
+        for (int r = 0; r < reps; ++r) {
+            QW_CUDA_TRY(cudaEventRecord(e0, s));
+            QW_TRY(run_impl(ix, queries, nq, k, &p, ids, dists, nullptr, nullptr, nullptr, mem, s));
+            QW_CUDA_TRY(cudaEventRecord(e1, s));
+            QW_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            QW_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            t.push_back(ms);
+        }
+        std::sort(t.begin(), t.end());
+        *ms_out = t[t.size() / 2];
+        if (report && tried < QW_TUNE_MAX) {
+            report->params[tried] = p;
+            report->ms[tried] = *ms_out;
+        }
+        ++tried;
+        return QW_OK;
+    };
+    qw_query_params cur = p0;
+    float cur_ms = 0.0f;
+    int cur_slot = 0;
+    auto try_alt = [&](const qw_query_params &alt) -> qw_status {
+        float ms = 0.0f;
+        const int slot = tried;
+        QW_TRY(time_one(alt, &ms));
+        if (ms < cur_ms) {
+            cur = alt;
+            cur_ms = ms;
+            cur_slot = slot;
+        }
+        return QW_OK;
+    };
+    do {
+        if ((status = time_one(cur, &cur_ms)) != QW_OK) break;
+        int csize = 0, tpc = 0;
+        // 1. first level
+        if (ix->start_model && mlp_inputs(ix->start_model) == ix->d + ix->m) {
+            qw_query_params alt = cur;
+            alt.start = QW_START_LEARNED;
+            if ((status = try_alt(alt)) != QW_OK) break;
+        }
+        // 2. queries per batch and 3. graph mode, on the level path
+        {
+            const int64_t cands[3] = {b_default / 16, b_default / 4, b_default * 4};
+            const qw_query_params keep = cur;
+            for (int64_t bb : cands) {
+                bb = std::min<int64_t>(std::min<int64_t>(bb, nq), 65535);
+                if (bb < 1 || bb == b_default) continue;
+                qw_query_params alt = keep;
+                alt.batch = (int32_t)bb;
+                if ((status = try_alt(alt)) != QW_OK) break;
+            }
+            if (status != QW_OK) break;
+            qw_query_params alt = cur;
+            alt.graph = 1;
+            if ((status = try_alt(alt)) != QW_OK) break;
+        }
+        // 4. path: the cluster path (plain starts only) against the best level setting
+        if (cur.start == QW_START_PLAIN && cluster_path_fits(ix->view(), &csize, &tpc)) {
+            qw_query_params alt = cur;
+            alt.path = QW_PATH_CLUSTER;
+            alt.batch = 0;
+            alt.graph = 0;
+            if ((status = try_alt(alt)) != QW_OK) break;
+        }
+        // 5. order, 6. distance arithmetic
+        {
+            qw_query_params alt = cur;
+            alt.order = QW_ORDER_GIVEN;
+            if ((status = try_alt(alt)) != QW_OK) break;
+        }
+        if (ix->shadow) {
+            qw_query_params alt = cur;
+            alt.rerank = QW_RERANK_BF16;
+            if ((status = try_alt(alt)) != QW_OK) break;
+        }
+    } while (false);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status != QW_OK) {
+        ix->tuned = saved_tuned;
+        return status;
+    }
+    *best = cur;
+    ix->tuned = true;
+    ix->tuned_path = cur.path;
+    ix->tuned_batch = cur.batch;
+    if (report) {
+        report->tried = std::min(tried, QW_TUNE_MAX);
+        report->best = cur_slot < QW_TUNE_MAX ? cur_slot : -1;
+    }
+    return QW_OK;
 }
 
 qw_status qw_workload_candidates(qw_index *ix, const float *queries, int64_t nq, int32_t k,
@@ -842,6 +1056,7 @@ void qw_index_free(qw_index *ix)
                       &ix->w_order, &ix->w_qb, &ix->w_ob, &ix->w_feat};
     for (DevBuf *bb : bufs) bb->release();
     for (cudaEvent_t e : ix->event_pool) cudaEventDestroy(e);
+    level_graph_cache_free(ix->graphs);
     delete ix;
 }
 

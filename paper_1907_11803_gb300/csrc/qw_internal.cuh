@@ -122,12 +122,39 @@ struct QueryState {
     unsigned long long *fb_count;  // 2: queries to recompute, levels skipped
 };
 
+// Level of a loop that runs on the device (graph mode): the level kernels
+// read level, R and R/c from here, and the loop-control kernel advances it.
+struct LoopCtl {
+    int64_t R;
+    int64_t Rp;
+    int32_t level;
+    int32_t pass;                 // 0, then 1 for the recomputed queries (learned start)
+    unsigned long long iters;     // level passes run, summed over the call's batches
+    unsigned long long fb_total;  // learned start: queries recomputed, summed over batches
+    unsigned long long skipped_total;  // learned start: levels skipped, summed over batches
+};
+
 qw_status launch_query_setup(const IndexView &ix, const int32_t *HQ, int nb, QueryState &st,
                              cudaStream_t s);
 qw_status launch_level(const IndexView &ix, int nb, int level, int64_t R, int64_t Rp, int l,
-                       int cgrow, QueryState &st, cudaStream_t s);
+                       int cgrow, QueryState &st, cudaStream_t s, const LoopCtl *ctl = nullptr);
 qw_status launch_fallback(int nb, QueryState &st, cudaStream_t s);
-qw_status launch_decide(int nb, int level, int64_t R, int cap, QueryState &st, cudaStream_t s);
+qw_status launch_decide(int nb, int level, int64_t R, int cap, QueryState &st, cudaStream_t s,
+                        const LoopCtl *ctl = nullptr);
+// Device-driven loop control (qw_graph.cu builds the graphs that use them).
+qw_status launch_loop_init(LoopCtl *ctl, cudaStream_t s);
+qw_status launch_loop_ctl(LoopCtl *ctl, const unsigned long long *max_top, int cgrow,
+                          cudaGraphConditionalHandle h, int *err, cudaStream_t s);
+qw_status launch_fallback_graph(int nb, QueryState &st, LoopCtl *ctl,
+                                cudaGraphConditionalHandle h, cudaStream_t s);
+
+// Graph mode of the level loop: one CUDA graph per batch shape, cached.
+struct LevelGraphCache;
+LevelGraphCache *level_graph_cache_new();
+void level_graph_cache_free(LevelGraphCache *c);
+qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l, int cgrow,
+                          int cap, bool learned, QueryState &st, LoopCtl *ctl, int *err,
+                          cudaStream_t s);
 qw_status launch_collect(const IndexView &ix, int nb, int l, int cap, QueryState &st,
                          int64_t *stats_out, cudaStream_t s);
 bool cluster_path_fits(const IndexView &ix, int *cluster_size, int *tiles_per_cta);

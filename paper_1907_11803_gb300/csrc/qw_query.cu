@@ -120,7 +120,8 @@ __global__ void fallback_kernel(int nb, QueryState st)
 
 __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int level, int64_t R,
                                                            int64_t Rp, int l, int cgrow,
-                                                           QueryState st, int64_t words_per_query)
+                                                           QueryState st, int64_t words_per_query,
+                                                           const LoopCtl *ctl)
 {
     __shared__ __align__(16) uint32_t cnt_s[kWordsPerTile];
     __shared__ int64_t f_gc0[2 * QW_MAX_M];
@@ -135,6 +136,11 @@ __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int lev
     const int t = blockIdx.x;
     const int q = blockIdx.y;
     if (!st.active[q]) return;
+    if (ctl) {
+        level = ctl->level;
+        R = ctl->R;
+        Rp = ctl->Rp;
+    }
     const int qstart = st.start[q];
     if (level < qstart) return;
     // the query's first level counts its whole range from zeroed counters
@@ -297,10 +303,16 @@ __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int lev
     }
 }
 
-__global__ void decide_kernel(int nb, int level, int64_t R, int cap, QueryState st)
+__global__ void decide_kernel(int nb, int level, int64_t R, int cap, QueryState st,
+                              const LoopCtl *ctl)
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nb || !st.active[q] || level < st.start[q]) return;
+    if (q >= nb || !st.active[q]) return;
+    if (ctl) {
+        level = ctl->level;
+        R = ctl->R;
+    }
+    if (level < st.start[q]) return;
     const int32_t before = st.ncand[q];  // |C_R| of the previous level
     const int32_t nc = st.cross[q];      // |C_R| of this level, summed over tiles
     st.cross[q] = 0;
@@ -325,6 +337,52 @@ __global__ void decide_kernel(int nb, int level, int64_t R, int cap, QueryState 
         st.nprev[q] = before;
     }
     st.ncand[q] = nc;
+}
+
+// Graph mode: the level loop runs on the device.  The first pass starts at
+// level 0 with R = 1.
+__global__ void loop_init_kernel(LoopCtl *ctl)
+{
+    ctl->level = 0;
+    ctl->R = 1;
+    ctl->Rp = 1;
+    ctl->pass = 0;
+}
+
+// After a level's decision: stop once R exceeds every query's last useful
+// radius (after this level no query can still be active), else go to the
+// next level.  Mirrors the host loop; level 63 would overflow R and is an
+// error (flag 8).
+__global__ void loop_ctl_kernel(LoopCtl *ctl, const unsigned long long *max_top, int cgrow,
+                                cudaGraphConditionalHandle h, int *err)
+{
+    const int64_t R = ctl->R;
+    bool more = (unsigned long long)R <= *max_top;
+    ctl->iters += 1;
+    if (more && ctl->level > 62) {
+        atomicOr(err, 8);
+        more = false;
+    }
+    if (more) {
+        ctl->level += 1;
+        ctl->Rp = R;
+        ctl->R = R * cgrow;
+    }
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// Learned start, graph mode: after the fallback kernel marked the queries that
+// stopped at their learned first level, run the loop again from level 0 if
+// there are any.
+__global__ void second_pass_kernel(QueryState st, LoopCtl *ctl, cudaGraphConditionalHandle h)
+{
+    ctl->level = 0;
+    ctl->R = 1;
+    ctl->Rp = 1;
+    ctl->pass = 1;
+    ctl->fb_total += st.fb_count[0];
+    ctl->skipped_total += st.fb_count[1];
+    cudaGraphSetConditional(h, st.fb_count[0] > 0 ? 1u : 0u);
 }
 
 constexpr int CL_THREADS = 256;
@@ -571,11 +629,36 @@ qw_status launch_query_setup(const IndexView &ix, const int32_t *HQ, int nb, Que
 }
 
 qw_status launch_level(const IndexView &ix, int nb, int level, int64_t R, int64_t Rp, int l,
-                       int cgrow, QueryState &st, cudaStream_t s)
+                       int cgrow, QueryState &st, cudaStream_t s, const LoopCtl *ctl)
 {
     const int64_t wpq = (int64_t)ix.nT * kWordsPerTile;
     level_kernel<<<dim3((unsigned)ix.nT, (unsigned)nb), LV_THREADS, 0, s>>>(ix, level, R, Rp, l,
-                                                                           cgrow, st, wpq);
+                                                                           cgrow, st, wpq, ctl);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
+
+qw_status launch_loop_init(LoopCtl *ctl, cudaStream_t s)
+{
+    loop_init_kernel<<<1, 1, 0, s>>>(ctl);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
+
+qw_status launch_loop_ctl(LoopCtl *ctl, const unsigned long long *max_top, int cgrow,
+                          cudaGraphConditionalHandle h, int *err, cudaStream_t s)
+{
+    loop_ctl_kernel<<<1, 1, 0, s>>>(ctl, max_top, cgrow, h, err);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
+
+qw_status launch_fallback_graph(int nb, QueryState &st, LoopCtl *ctl, cudaGraphConditionalHandle h,
+                                cudaStream_t s)
+{
+    fallback_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, st);
+    QW_CUDA_TRY(cudaGetLastError());
+    second_pass_kernel<<<1, 1, 0, s>>>(st, ctl, h);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }
@@ -587,9 +670,10 @@ qw_status launch_fallback(int nb, QueryState &st, cudaStream_t s)
     return QW_OK;
 }
 
-qw_status launch_decide(int nb, int level, int64_t R, int cap, QueryState &st, cudaStream_t s)
+qw_status launch_decide(int nb, int level, int64_t R, int cap, QueryState &st, cudaStream_t s,
+                        const LoopCtl *ctl)
 {
-    decide_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, level, R, cap, st);
+    decide_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, level, R, cap, st, ctl);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }

@@ -75,6 +75,12 @@ def test_learned_start_same_results_fewer_levels(qwlib, cuda):
     assert torch.equal(d0, d1)
     assert torch.equal(st0, st1)
     assert prof["start_levels_skipped"] > 0
+    # graph mode: the same loop driven on the device, the same counters
+    ids3, d3, st3 = index.query(Q, 20, stats=True, start="learned", graph=True)
+    prof3 = index.profile(reset=True)
+    assert torch.equal(ids0, ids3) and torch.equal(d0, d3) and torch.equal(st0, st3)
+    assert prof3["start_levels_skipped"] == prof["start_levels_skipped"]
+    assert prof3["start_fallbacks"] == prof["start_fallbacks"]
     # an over-eager model (eps close to 1) starts too late for many queries:
     # they are recomputed from level 0 and the results still match
     index.set_start_model(mlp, eps=0.999)
@@ -82,5 +88,9 @@ def test_learned_start_same_results_fewer_levels(qwlib, cuda):
     prof2 = index.profile(reset=True)
     assert torch.equal(ids0, ids2) and torch.equal(st0, st2)
     assert prof2["start_fallbacks"] > 0
+    ids4, d4, st4 = index.query(Q, 20, stats=True, start="learned", graph=True)
+    prof4 = index.profile(reset=True)
+    assert torch.equal(ids0, ids4) and torch.equal(st0, st4)
+    assert prof4["start_fallbacks"] == prof2["start_fallbacks"]
     index.free()
     mlp.free()

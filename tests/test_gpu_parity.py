@@ -13,7 +13,8 @@ pytestmark = pytest.mark.gpu
 
 DIST_RTOL = 1e-5
 TILE = 32768
-PATHS = pytest.mark.parametrize("path", ["levels", "cluster"])
+# "graph": the level path with its level loop run as a CUDA graph
+PATHS = pytest.mark.parametrize("path", ["levels", "cluster", "graph"])
 
 
 def _t(x, dev):
@@ -60,9 +61,12 @@ def _gpu_workload(qw, dev, X, Q, A, b, *, w, k, v, l, c=2, batch=0, host=False, 
     else:
         Xd, Qd, Ad, bd = _t(X, dev), _t(Q, dev), _t(A, dev), _t(b, dev)
     index = qw.Index(Xd, Ad, bd, w=w, c=c, v=v, l=l, shadow_bf16=(rerank == "bf16"))
+    graph = path == "graph"
+    if graph:
+        path = "levels"
     ids, dists, st = index.query(Qd, k, batch=batch, stats=True, path=path, order=order,
-                                 rerank=rerank)
-    cid, ccol, st2 = index.candidates(Qd, k, batch=batch, path=path, order=order)
+                                 rerank=rerank, graph=graph)
+    cid, ccol, st2 = index.candidates(Qd, k, batch=batch, path=path, order=order, graph=graph)
     torch.cuda.synchronize()
     out = dict(ids=ids.cpu().numpy(), dists=dists.cpu().numpy(), stats=st.cpu().numpy(),
                cid=cid.cpu().numpy(), ccol=ccol.cpu().numpy(), stats2=st2.cpu().numpy(),
