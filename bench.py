@@ -62,7 +62,7 @@ def parse_args(argv=None):
     p.add_argument("--queries", type=int, default=0,
                    help="override the workload's query count (smaller cases for profiling)")
     p.add_argument("--batch", type=int, default=0, help="queries per pass (0 = library choice)")
-    p.add_argument("--path", choices=["auto", "cluster", "levels"], default="auto",
+    p.add_argument("--path", choices=["auto", "cluster", "levels", "bitmap"], default="auto",
                    help="execution path of the query loop (identical results)")
     p.add_argument("--order", choices=["auto", "signature", "given"], default="auto",
                    help="workload order: grouped by bucket signature, or as given")
@@ -75,6 +75,8 @@ def parse_args(argv=None):
     p.add_argument("--no-tune", action="store_true",
                    help="chosen path from --path/--order/--rerank/--start/--graph instead of "
                         "the autotuner")
+    p.add_argument("--no-bitmaps", action="store_true",
+                   help="build the index without the level bitmaps of the bitmap path")
     p.add_argument("--graph", action="store_true",
                    help="with --no-tune: run the level loop as a CUDA graph")
     p.add_argument("--v", type=int, default=-1,
@@ -197,7 +199,8 @@ def measured_peaks():
 
 
 KERNEL_SOURCES = {
-    "level_kernel": ("qw_query.cu", "qw_count.cuh", "qw_internal.cuh"),
+    "level_kernel": ("qw_query.cu", "qw_count.cuh", "qw_dir.cuh", "qw_internal.cuh"),
+    "bm_level_kernel": ("qw_bitmap.cu", "qw_dir.cuh", "qw_scan.cuh", "qw_internal.cuh"),
     "cluster_query_kernel": ("qw_cluster.cu", "qw_count.cuh", "qw_internal.cuh"),
     "rerank_kernel": ("qw_rerank.cu", "qw_internal.cuh"),
 }
@@ -327,7 +330,7 @@ def run_ours(args):
     Q = torch.from_numpy(wl.Q).to(dev)
     v_used, l_arg = operating_point(args, s)
     index = qw.Index(X, A, b, w=s.w, c=s.c, v=v_used, l=l_arg,
-                     shadow_bf16=args.rerank == "bf16")
+                     shadow_bf16=args.rerank == "bf16", bitmaps=not args.no_bitmaps)
     ids = torch.empty((s.nq, s.k), dtype=torch.int64, device=dev)
     dists = torch.empty((s.nq, s.k), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -416,8 +419,14 @@ def run_ours(args):
     entries = float(st[:, 5].sum())      # index entries scanned per step (incremental flanks)
     count_bytes = entries * 2.0          # 16-bit ids
     dom = "cluster" if prof["ms"]["cluster"] >= prof["ms"]["level"] else "level"
+    bitmap = chosen_kw.get("path") == "bitmap"
     dom_name = {"cluster": "cluster_query_kernel (all levels of collision counting, persistent)",
                 "level": "level_kernel (bucket-range search + collision counting)"}[dom]
+    if bitmap and dom == "level":
+        # per (query, level) pass and tile: the m bucket bitmaps, the previous
+        # level's candidate bitmap and the new one, 4 KiB each
+        dom_name = "bm_level_kernel (bit-sliced collision counts from level bitmaps)"
+        count_bytes = (prof["level_passes"] / steps) * index.info.n_tiles * (s.m + 2) * 4096.0
     # launches actually run (graph mode counts the device-driven level passes)
     dom_launches = prof["launches"][dom] / steps
     dom_ms = prof["ms"][dom] / steps
@@ -430,7 +439,8 @@ def run_ours(args):
     rr_ms = prof["ms"]["rerank"] / steps
     rr_achieved = (rr_bytes / max(rr_launches, 1)) / ((rr_ms / 1e3) / max(rr_launches, 1)) / 1e9 \
         if rr_ms > 0 else 0.0
-    kname = "cluster_query_kernel" if dom == "cluster" else "level_kernel"
+    kname = "cluster_query_kernel" if dom == "cluster" else (
+        "bm_level_kernel" if bitmap else "level_kernel")
     roofline = {"kernel": dom_name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "unit": "GB/s", "frac": round(achieved / hbm, 4),
                 "traffic": ncu_traffic(kname, args.workload), "peak_kind": peak_kind,
@@ -461,6 +471,7 @@ def run_ours(args):
                    "query_clusters": s.query_clusters, "seed": args.seed,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "chosen": chosen_kw, "start_model": train_info, "autotune": tune,
+                   "bitmap_bytes": int(index.info.bitmap_bytes),
                    "l2": "inputs larger than L2 (index %.2f GB + data %.2f GB + counters)"
                          % (index.info.device_bytes / 1e9 - s.n * s.d * 4 / 1e9,
                             s.n * s.d * 4 / 1e9)},

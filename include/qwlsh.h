@@ -84,6 +84,10 @@ typedef struct {
     float delta;   /* error probability used when deriving l; <= 0 means 1/e (Section 6) */
     int32_t shadow_bf16;  /* non-zero: also keep a BF16 copy of the data and row-norm bounds,
                              for the QW_RERANK_BF16 pre-filter (2 * n * d + 4 * n bytes) */
+    int32_t bitmaps;      /* non-zero: also build the level bitmaps of QW_PATH_BITMAP: per
+                             projection i, id tile and level L, one bitmap of the tile's ids
+                             per level-L bucket; about m * n_tiles * (c/(c-1)) * (span_i + 1)
+                             * 4 KiB (qw_index_info.bitmap_bytes) */
 } qw_index_params;
 
 /* Per-workload options.  Zero-initialise; unknown non-zero fields are rejected. */
@@ -137,10 +141,15 @@ typedef struct {
  *   answers one query at a time with its counters in shared memory for all
  *   levels and pulls the next query from a work queue; indexes of up to
  *   96 tiles (3,145,728 points).
+ * QW_PATH_BITMAP: the level loop of QW_PATH_LEVELS, but the collision counts
+ *   of a (tile, query) are recomputed at every level as the bit-sliced sum of
+ *   the m precomputed bitmaps of the query's level-L buckets (no per-entry
+ *   work, no counters kept between levels); needs an index built with bitmaps.
  * QW_PATH_AUTO: the path qw_autotune chose for the index, else the level path. */
 #define QW_PATH_AUTO 0
 #define QW_PATH_CLUSTER 1
 #define QW_PATH_LEVELS 2
+#define QW_PATH_BITMAP 3
 
 /* Kernel classes of the query path, for qw_profile. */
 #define QW_K_PROJECT 0   /* query projection + FP64 boundary pass */
@@ -166,6 +175,8 @@ typedef struct {
     int64_t rerank_fp32_rows;      /* of those, read in FP32 (profile mode; BF16 pre-filter) */
     int64_t start_levels_skipped;  /* levels skipped by learned starts (always counted) */
     int64_t start_fallbacks;       /* queries recomputed from R = 1 (always counted) */
+    int64_t level_passes;          /* (query, level) pairs counted by the level paths
+                                      (profile mode) */
 } qw_profile;
 
 typedef struct {
@@ -181,6 +192,7 @@ typedef struct {
     int32_t span_max;      /* largest anchored bucket id over all projections */
     int64_t n_fixups;      /* data projections recomputed in FP64 at build time */
     int64_t device_bytes;  /* device memory held by the index (excluding workspace) */
+    int64_t bitmap_bytes;  /* of which the level bitmaps (0 without them) */
 } qw_index_info;
 
 /* Library version string. */
@@ -312,10 +324,11 @@ typedef struct {
  * of the workload, `mem` space) under candidate settings, one coordinate at a
  * time, keeping the fastest before moving on: start level (plain / learned,
  * when a start model is attached), queries per batch on the level path (the
- * default and 1/16, 1/4, 4x of it), graph mode, then the cluster path against
- * that best level setting (when the index fits it and the start is plain),
- * order (signature / given) and rerank (FP32 / BF16, when the index has the
- * BF16 copy).  Every setting returns the same results, so the choice cannot change
+ * default and 1/16, 1/4, 4x of it) and graph mode; the bitmap path (when the
+ * index has bitmaps) with its default batch, 1/16 and 1/4 of it, and graph
+ * mode; then the cluster path against the best so far (when the index fits it
+ * and the start is plain); order (signature / given) and rerank (FP32 / BF16,
+ * when the index has the BF16 copy).  Every setting returns the same results, so the choice cannot change
  * them.  Each setting runs once untimed, then `reps` (>= 1) times timed with
  * CUDA events on `stream`; the median counts.  The chosen setting is written
  * to *best (host) and stored in the index: later calls with QW_PATH_AUTO take

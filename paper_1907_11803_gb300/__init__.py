@@ -41,7 +41,8 @@ EXPORTED = ("qw_version", "qw_last_error", "qw_collision_probability",
 
 class qw_index_params(C.Structure):
     _fields_ = [("m", C.c_int32), ("w", C.c_float), ("c", C.c_int32), ("v", C.c_int32),
-                ("l", C.c_int32), ("delta", C.c_float), ("shadow_bf16", C.c_int32)]
+                ("l", C.c_int32), ("delta", C.c_float), ("shadow_bf16", C.c_int32),
+                ("bitmaps", C.c_int32)]
 
 
 class qw_query_params(C.Structure):
@@ -58,8 +59,9 @@ class qw_tune_report(C.Structure):
                 ("ms", C.c_float * QW_TUNE_MAX), ("best", C.c_int32)]
 
 
-QW_PATH_AUTO, QW_PATH_CLUSTER, QW_PATH_LEVELS = 0, 1, 2
-PATHS = {"auto": QW_PATH_AUTO, "cluster": QW_PATH_CLUSTER, "levels": QW_PATH_LEVELS}
+QW_PATH_AUTO, QW_PATH_CLUSTER, QW_PATH_LEVELS, QW_PATH_BITMAP = 0, 1, 2, 3
+PATHS = {"auto": QW_PATH_AUTO, "cluster": QW_PATH_CLUSTER, "levels": QW_PATH_LEVELS,
+         "bitmap": QW_PATH_BITMAP}
 QW_ORDER_AUTO, QW_ORDER_SIGNATURE, QW_ORDER_GIVEN = 0, 1, 2
 QW_RERANK_FP32, QW_RERANK_BF16 = 0, 1
 RERANKS = {"fp32": QW_RERANK_FP32, "bf16": QW_RERANK_BF16}
@@ -77,14 +79,15 @@ class qw_profile(C.Structure):
     _fields_ = [("launches", C.c_int64 * QW_K_COUNT), ("ms", C.c_double * QW_K_COUNT),
                 ("timed_launches", C.c_int64 * QW_K_COUNT), ("queries", C.c_int64),
                 ("rerank_candidates", C.c_int64), ("rerank_fp32_rows", C.c_int64),
-                ("start_levels_skipped", C.c_int64), ("start_fallbacks", C.c_int64)]
+                ("start_levels_skipped", C.c_int64), ("start_fallbacks", C.c_int64),
+                ("level_passes", C.c_int64)]
 
 
 class qw_index_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("m", C.c_int32), ("w", C.c_float),
                 ("c", C.c_int32), ("v", C.c_int32), ("l", C.c_int32), ("tile", C.c_int32),
                 ("n_tiles", C.c_int32), ("span_max", C.c_int32), ("n_fixups", C.c_int64),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("bitmap_bytes", C.c_int64)]
 
 
 class QwError(RuntimeError):
@@ -303,7 +306,7 @@ class Index:
     threshold from Eq. 1 (see ``qw_collision_threshold``)."""
 
     def __init__(self, data, A, b, *, w: float, c: int = 2, v: int = 100, l: int = 0,
-                 delta: float = 0.0, shadow_bf16: bool = False):
+                 delta: float = 0.0, shadow_bf16: bool = False, bitmaps: bool = False):
         _f32(data, "data"), _f32(A, "A"), _f32(b, "b")
         mem = _mem_of(data, A, b)
         n, d = data.shape
@@ -311,7 +314,7 @@ class Index:
         if d2 != d or b.shape != (m,):
             raise ValueError("shape mismatch between data, A and b")
         p = qw_index_params(m=m, w=float(w), c=int(c), v=int(v), l=int(l), delta=float(delta),
-                            shadow_bf16=1 if shadow_bf16 else 0)
+                            shadow_bf16=1 if shadow_bf16 else 0, bitmaps=1 if bitmaps else 0)
         self._h = 0
         self._h = qw_build_index(data.data_ptr(), n, d, A.data_ptr(), b.data_ptr(), p, mem,
                                  _stream_of(data))
@@ -340,7 +343,8 @@ class Index:
                 "queries": int(p.queries), "rerank_candidates": int(p.rerank_candidates),
                 "rerank_fp32_rows": int(p.rerank_fp32_rows),
                 "start_levels_skipped": int(p.start_levels_skipped),
-                "start_fallbacks": int(p.start_fallbacks)}
+                "start_fallbacks": int(p.start_fallbacks),
+                "level_passes": int(p.level_passes)}
 
     def query(self, Q, k: int, *, batch: int = 0, stats: bool = False, out=None,
               profile: bool = False, path: str = "auto", clusters: int = 0,

@@ -69,6 +69,9 @@ struct qw_index {
     int64_t n_fixups = 0;
     DevBuf X, A, b, o, span, lid, dir_bid, dir_off, dir_start, dir_cnt, Xb, xnorm;
     bool shadow = false;
+    bool bitmaps = false;               // level bitmaps for QW_PATH_BITMAP
+    DevBuf bm, bm_base, bm_nb, bm_lvl, bm_J;
+    int bm_maxJ = 0;
     float xs = 1.0f;                 // 1 / RMS coordinate of the data (start-model features)
     qw_mlp *start_model = nullptr;   // not owned
     float start_eps = 0.02f;
@@ -78,7 +81,7 @@ struct qw_index {
     int32_t tuned_batch = 0;
     DevBuf w_feat;
     // workspace for queries (grow-only)
-    DevBuf w_q, w_hq, w_state, w_counters, w_cand, w_out, w_err, w_order, w_qb, w_ob;
+    DevBuf w_q, w_hq, w_state, w_counters, w_cand, w_out, w_err, w_order, w_qb, w_ob, w_cbits;
     int64_t device_bytes = 0;
     qw_profile prof{};
     std::vector<cudaEvent_t> event_pool;
@@ -98,6 +101,11 @@ struct qw_index {
         v.dir_off = dir_off.as<int32_t>();
         v.dir_start = dir_start.as<int64_t>();
         v.dir_cnt = dir_cnt.as<int32_t>();
+        v.bm = bm.as<uint4>();
+        v.bm_base = bm_base.as<int64_t>();
+        v.bm_nb = bm_nb.as<int32_t>();
+        v.bm_lvl = bm_lvl.as<int32_t>();
+        v.bm_J = bm_J.as<int32_t>();
         return v;
     }
 };
@@ -325,6 +333,26 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
         QW_TRY(data_rms(ix->X.as<float>(), n * (int64_t)d, acc.as<double>(), &rms, s));
         ix->xs = rms > 0.0 ? (float)(1.0 / rms) : 1.0f;
     }
+    if (ix->bitmaps) {
+        BitmapLayout lay;
+        QW_TRY(bitmap_layout(h_span, nT, ix->c, &lay));
+        QW_TRY(ix->bm.ensure((size_t)lay.total * kBmUint4 * sizeof(uint4)));
+        QW_TRY(ix->bm_base.ensure((size_t)m * sizeof(int64_t)));
+        QW_TRY(ix->bm_nb.ensure((size_t)m * sizeof(int32_t)));
+        QW_TRY(ix->bm_lvl.ensure((size_t)m * kBmLevels * sizeof(int32_t)));
+        QW_TRY(ix->bm_J.ensure((size_t)m * sizeof(int32_t)));
+        QW_CUDA_TRY(cudaMemsetAsync(ix->bm.p, 0, ix->bm.bytes, s));
+        QW_CUDA_TRY(cudaMemcpyAsync(ix->bm_base.p, lay.base.data(), m * sizeof(int64_t),
+                                    cudaMemcpyHostToDevice, s));
+        QW_CUDA_TRY(cudaMemcpyAsync(ix->bm_nb.p, lay.nb.data(), m * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, s));
+        QW_CUDA_TRY(cudaMemcpyAsync(ix->bm_lvl.p, lay.lvl.data(), lay.lvl.size() * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, s));
+        QW_CUDA_TRY(cudaMemcpyAsync(ix->bm_J.p, lay.J.data(), m * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, s));
+        ix->bm_maxJ = *std::max_element(lay.J.begin(), lay.J.end());
+        QW_TRY(launch_bitmap_build(ix->view(), ix->c, ix->bm_maxJ, ix->bm.as<uint4>(), s));
+    }
     if (ix->shadow) {
         QW_TRY(ix->Xb.ensure((size_t)n * d * 2));
         QW_TRY(ix->xnorm.ensure((size_t)n * sizeof(float)));
@@ -333,7 +361,9 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
     QW_CUDA_TRY(cudaStreamSynchronize(s));
     ix->device_bytes = (int64_t)(ix->Xb.bytes + ix->xnorm.bytes + ix->X.bytes + ix->A.bytes + ix->b.bytes + ix->o.bytes +
                                  ix->span.bytes + ix->lid.bytes + ix->dir_bid.bytes +
-                                 ix->dir_off.bytes + ix->dir_start.bytes + ix->dir_cnt.bytes);
+                                 ix->dir_off.bytes + ix->dir_start.bytes + ix->dir_cnt.bytes +
+                                 ix->bm.bytes + ix->bm_base.bytes + ix->bm_nb.bytes +
+                                 ix->bm_lvl.bytes + ix->bm_J.bytes);
     return QW_OK;
 }
 
@@ -370,6 +400,7 @@ qw_status qw_build_index(const float *data, int64_t n, int32_t d, const float *A
     }
     ix->nT = (int)((n + kTile - 1) / kTile);
     ix->shadow = p->shadow_bf16 != 0;
+    ix->bitmaps = p->bitmaps != 0;
     qw_status st = build_impl(ix, data, A, b, mem, (cudaStream_t)stream);
     if (st != QW_OK) {
         qw_index_free(ix);
@@ -384,7 +415,7 @@ qw_status qw_build_index(const float *data, int64_t n, int32_t d, const float *A
 // stopped); with learned starts, a second pass from level 0 for the queries
 // that stopped at their learned first level.
 static qw_status host_level_loop(qw_index *ix, LaunchTimer &tm, const IndexView &view, int nb,
-                                 int cap, bool learned, QueryState &st, cudaStream_t s)
+                                 int cap, bool learned, bool bitmap, QueryState &st, cudaStream_t s)
 {
     unsigned long long max_top = 0;
     QW_CUDA_TRY(cudaMemcpyAsync(&max_top, st.max_top, sizeof(max_top), cudaMemcpyDeviceToHost, s));
@@ -393,7 +424,8 @@ static qw_status host_level_loop(qw_index *ix, LaunchTimer &tm, const IndexView 
         int64_t R = 1, Rp = 1;
         for (int level = 0;; ++level) {
             QW_TRY(tm.run(QW_K_LEVEL, 1, [&] {
-                return launch_level(view, nb, level, R, Rp, ix->l, ix->c, st, s);
+                return bitmap ? launch_bm_level(view, nb, level, R, Rp, ix->l, ix->c, st, s)
+                              : launch_level(view, nb, level, R, Rp, ix->l, ix->c, st, s);
             }));
             QW_TRY(tm.run(QW_K_DECIDE, 1, [&] { return launch_decide(nb, level, R, cap, st, s); }));
             if ((unsigned long long)R > max_top) break;
@@ -461,12 +493,23 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     int eff_path = path;
     if (eff_path == QW_PATH_AUTO)
         eff_path = (ix->tuned && !learned && !graph) ? ix->tuned_path : QW_PATH_LEVELS;
+    if (path == QW_PATH_BITMAP && !ix->bitmaps) {
+        set_error("qw_run_workload: QW_PATH_BITMAP needs an index built with bitmaps");
+        return QW_ERR_ARG;
+    }
+    if (eff_path == QW_PATH_BITMAP && !ix->bitmaps) eff_path = QW_PATH_LEVELS;
     const bool use_cluster = eff_path == QW_PATH_CLUSTER && fits;
+    const bool use_bitmap = eff_path == QW_PATH_BITMAP;
+    // candidate bitmaps of the bitmap path: two levels of (query, tile) bitmaps
+    const int64_t cb_bytes = (int64_t)ix->nT * kBmUint4 * (int64_t)sizeof(uint4) * 2;
     int64_t B = qp && qp->batch > 0 ? qp->batch : 0;
-    if (B == 0 && ix->tuned && ix->tuned_batch > 0 && !use_cluster) B = ix->tuned_batch;
+    if (B == 0 && ix->tuned && ix->tuned_batch > 0 && !use_cluster &&
+        (path == QW_PATH_AUTO || path == ix->tuned_path))
+        B = ix->tuned_batch;
     if (B == 0) {
         const int64_t budget = (int64_t)2 << 30;  // counters of one batch
-        B = use_cluster ? (int64_t)65535 : std::max<int64_t>(1, budget / wpq_bytes);
+        B = use_cluster ? (int64_t)65535
+                        : std::max<int64_t>(1, budget / (use_bitmap ? cb_bytes : wpq_bytes));
     }
     B = std::min<int64_t>(B, std::max<int64_t>(nq, 1));
     B = std::min<int64_t>(B, 65535);
@@ -475,7 +518,8 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     // ---- workspace
     QW_TRY(ix->w_err.ensure(64));
     QW_TRY(ix->w_hq.ensure((size_t)nq * m * sizeof(int32_t)));       // bucket ids of all queries
-    if (!use_cluster) QW_TRY(ix->w_counters.ensure((size_t)B * wpq_bytes));
+    if (!use_cluster && !use_bitmap) QW_TRY(ix->w_counters.ensure((size_t)B * wpq_bytes));
+    if (use_bitmap) QW_TRY(ix->w_cbits.ensure((size_t)B * cb_bytes));
     QW_TRY(ix->w_cand.ensure((size_t)B * cap * 2 * sizeof(int32_t)));
     const size_t plan_ints = (size_t)B * ix->nT * (kHistBins + 3) + (size_t)B * 2;
     const size_t st_bytes = (size_t)B * m * 8 + (size_t)B * 8 * 16 + plan_ints * 4 + 256 +
@@ -561,6 +605,9 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         }
     }
     st.counters = ix->w_counters.as<uint32_t>();
+    st.cbits = ix->w_cbits.as<uint4>();
+    st.level_passes = nullptr;
+    st.cb_par = B * ix->nT * kBmUint4;
     st.cand = ix->w_cand.as<int32_t>();
     st.cand_col = st.cand + (size_t)B * cap;
     int *err = ix->w_err.as<int>();
@@ -569,7 +616,10 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     unsigned long long *cand_ctr = reinterpret_cast<unsigned long long *>(ix->w_err.as<char>() + 48);
     const IndexView view = ix->view();
     LaunchTimer tm{ix, s, qp && qp->profile != 0};
-    if (tm.on) QW_CUDA_TRY(cudaMemsetAsync(ix->w_err.as<char>() + 40, 0, 16, s));
+    if (tm.on) {
+        QW_CUDA_TRY(cudaMemsetAsync(ix->w_err.as<char>() + 40, 0, 24, s));
+        st.level_passes = reinterpret_cast<unsigned long long *>(ix->w_err.as<char>() + 56);
+    }
 
     // ---- the whole workload: copy in (host mode), hash, order
     if (host)
@@ -674,13 +724,16 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             }
             if (graph) {
                 QW_TRY(tm.run(QW_K_LEVEL, 0, [&] {
-                    return run_level_graph(ix->graphs, view, nb, ix->l, ix->c, cap, learned, st,
-                                           ctl, err, s);
+                    return run_level_graph(ix->graphs, view, nb, ix->l, ix->c, cap, learned,
+                                           use_bitmap, st, ctl, err, s);
                 }));
             } else {
-                QW_TRY(host_level_loop(ix, tm, view, nb, cap, learned, st, s));
+                QW_TRY(host_level_loop(ix, tm, view, nb, cap, learned, use_bitmap, st, s));
             }
-            QW_TRY(tm.run(QW_K_SELECT, 2, [&] { return launch_collect(view, nb, ix->l, cap, st, stats_b, s); }));
+            QW_TRY(tm.run(QW_K_SELECT, 2, [&] {
+                return use_bitmap ? launch_bm_collect(view, nb, ix->l, cap, st, stats_b, s)
+                                  : launch_collect(view, nb, ix->l, cap, st, stats_b, s);
+            }));
         }
         if (want_cand)
             QW_TRY(tm.run(QW_K_SELECT, 1, [&] { return launch_candidates_out(st, nb, cap, cids_b, ccol_b, s); }));
@@ -734,10 +787,11 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     }
     QW_TRY(tm.finish());
     if (tm.on) {
-        unsigned long long ctr[2] = {0, 0};
+        unsigned long long ctr[3] = {0, 0, 0};
         QW_CUDA_TRY(cudaMemcpy(ctr, ix->w_err.as<char>() + 40, sizeof(ctr), cudaMemcpyDeviceToHost));
         ix->prof.rerank_fp32_rows += (int64_t)(bf16 ? ctr[0] : ctr[1]);
         ix->prof.rerank_candidates += (int64_t)ctr[1];
+        ix->prof.level_passes += (int64_t)ctr[2];
     }
     ix->prof.queries += nq;
     return QW_OK;
@@ -754,7 +808,7 @@ static qw_status check_workload_args(const qw_index *ix, const float *queries, i
     if ((int64_t)k + ix->v > QW_MAX_CAND) return arg_error("qw_run_workload: k + v exceeds 4096");
     if (qp) {
         if (qp->batch < 0) return arg_error("qw_run_workload: batch < 0");
-        if (qp->path < QW_PATH_AUTO || qp->path > QW_PATH_LEVELS)
+        if (qp->path < QW_PATH_AUTO || qp->path > QW_PATH_BITMAP)
             return arg_error("qw_run_workload: unknown path");
         if (qp->clusters < 0) return arg_error("qw_run_workload: clusters < 0");
         if (qp->order < QW_ORDER_AUTO || qp->order > QW_ORDER_GIVEN)
@@ -897,7 +951,44 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
             alt.graph = 1;
             if ((status = try_alt(alt)) != QW_OK) break;
         }
-        // 4. path: the cluster path (plain starts only) against the best level setting
+        // 4. the bitmap path (when built): default batch, then its batch and graph
+        if (ix->bitmaps) {
+            const qw_query_params best_levels = cur;
+            const float best_levels_ms = cur_ms;
+            const int best_levels_slot = cur_slot;
+            qw_query_params bp0 = cur;
+            bp0.path = QW_PATH_BITMAP;
+            bp0.batch = 0;
+            bp0.graph = 0;
+            float bms = 0.0f;
+            const int bslot = tried;
+            if ((status = time_one(bp0, &bms)) != QW_OK) break;
+            cur = bp0;
+            cur_ms = bms;
+            cur_slot = bslot;
+            const int64_t cb_b = (int64_t)ix->nT * kBmUint4 * (int64_t)sizeof(uint4) * 2;
+            const int64_t bdef = std::min<int64_t>(
+                std::min<int64_t>(std::max<int64_t>(1, ((int64_t)2 << 30) / cb_b), nq), 65535);
+            const int64_t bc[2] = {bdef / 16, bdef / 4};
+            const qw_query_params keepb = cur;
+            for (int64_t bb : bc) {
+                bb = std::min<int64_t>(std::min<int64_t>(bb, nq), 65535);
+                if (bb < 1 || bb == bdef) continue;
+                qw_query_params alt = keepb;
+                alt.batch = (int32_t)bb;
+                if ((status = try_alt(alt)) != QW_OK) break;
+            }
+            if (status != QW_OK) break;
+            qw_query_params alt = cur;
+            alt.graph = 1;
+            if ((status = try_alt(alt)) != QW_OK) break;
+            if (best_levels_ms < cur_ms) {
+                cur = best_levels;
+                cur_ms = best_levels_ms;
+                cur_slot = best_levels_slot;
+            }
+        }
+        // 5. path: the cluster path (plain starts only) against the best so far
         if (cur.start == QW_START_PLAIN && cluster_path_fits(ix->view(), &csize, &tpc)) {
             qw_query_params alt = cur;
             alt.path = QW_PATH_CLUSTER;
@@ -905,7 +996,7 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
             alt.graph = 0;
             if ((status = try_alt(alt)) != QW_OK) break;
         }
-        // 5. order, 6. distance arithmetic
+        // 6. order, 7. distance arithmetic
         {
             qw_query_params alt = cur;
             alt.order = QW_ORDER_GIVEN;
@@ -1009,6 +1100,7 @@ qw_status qw_index_get_info(const qw_index *ix, qw_index_info *info)
     info->span_max = ix->span_max;
     info->n_fixups = ix->n_fixups;
     info->device_bytes = ix->device_bytes;
+    info->bitmap_bytes = (int64_t)ix->bm.bytes;
     return QW_OK;
 }
 
@@ -1055,6 +1147,8 @@ void qw_index_free(qw_index *ix)
                       &ix->w_state, &ix->w_counters, &ix->w_cand, &ix->w_out, &ix->w_err,
                       &ix->w_order, &ix->w_qb, &ix->w_ob, &ix->w_feat};
     for (DevBuf *bb : bufs) bb->release();
+    DevBuf *bmb[] = {&ix->bm, &ix->bm_base, &ix->bm_nb, &ix->bm_lvl, &ix->bm_J, &ix->w_cbits};
+    for (DevBuf *bb : bmb) bb->release();
     for (cudaEvent_t e : ix->event_pool) cudaEventDestroy(e);
     level_graph_cache_free(ix->graphs);
     delete ix;

@@ -19,6 +19,7 @@
 // c*, and per-tile prefixes so each CTA writes its kept ids in id order.
 #include "qw_internal.cuh"
 #include "qw_count.cuh"
+#include "qw_dir.cuh"
 #include "qw_scan.cuh"
 
 #include <cooperative_groups.h>
@@ -101,35 +102,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
-}
-
-__device__ __forceinline__ int64_t floordiv64(int64_t a, int64_t R)
-{
-    int64_t q = a / R;
-    if ((a % R != 0) && (a < 0)) --q;
-    return q;
-}
-
-__device__ __forceinline__ int64_t clamp64(int64_t x, int64_t lo, int64_t hi)
-{
-    return x < lo ? lo : (x > hi ? hi : x);
-}
-
-__device__ __forceinline__ int dir_lower(const int32_t *__restrict__ ub,
-                                         const int32_t *__restrict__ uo, int cnt, int len,
-                                         int64_t x)
-{
-    if (cnt == 0) return 0;
-    const int32_t b0 = ub[0];
-    if (x <= b0) return 0;
-    const int64_t p = x - b0;
-    if (p < cnt && ub[p] == x) return uo[p];
-    int lo = 0, hi = cnt;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if ((int64_t)ub[mid] < x) lo = mid + 1; else hi = mid;
-    }
-    return lo < cnt ? uo[lo] : len;
 }
 
 struct ClusterShared {

@@ -12,10 +12,13 @@
 // host synchronisation inside the batch; the kernels and their order are
 // those of the host loop, so the results are the same.
 //
-// Graphs are cached per batch shape (batch size, workspace pointers and the
-// index's parameters): a workload of full batches and one short batch
-// instantiates two graphs on its first call and none afterwards.
+// Graphs are cached per batch shape (batch size, every workspace pointer the
+// kernels take, and the index's parameters): a workload of full batches and
+// one short batch instantiates two graphs on its first call and none
+// afterwards.
 #include "qw_internal.cuh"
+
+#include <string.h>
 
 #include <vector>
 
@@ -23,17 +26,17 @@ namespace qw {
 
 struct GraphKey {
     int nb, l, cgrow, cap;
-    bool learned;
-    const void *state;     // st.g: the workspace the graph's kernels address
-    const void *counters;
+    bool learned, bitmap;
+    QueryState st;         // every workspace pointer the graph's kernels take by value
     const void *lid;       // the index
     const void *ctl;
     const void *err;
     bool operator==(const GraphKey &o) const
     {
         return nb == o.nb && l == o.l && cgrow == o.cgrow && cap == o.cap &&
-               learned == o.learned && state == o.state && counters == o.counters &&
-               lid == o.lid && ctl == o.ctl && err == o.err;
+               learned == o.learned && bitmap == o.bitmap &&
+               memcmp(&st, &o.st, sizeof(QueryState)) == 0 && lid == o.lid && ctl == o.ctl &&
+               err == o.err;
     }
 };
 
@@ -109,8 +112,8 @@ qw_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
 }
 
 qw_status build(LevelGraphCache *c, const GraphKey &key, const IndexView &ix, int nb, int l,
-                int cgrow, int cap, bool learned, QueryState &st, LoopCtl *ctl, int *err,
-                cudaGraph_t *graph_out)
+                int cgrow, int cap, bool learned, bool bitmap, QueryState &st, LoopCtl *ctl,
+                int *err, cudaGraph_t *graph_out)
 {
     cudaStream_t cs = c->cap_stream;
     cudaGraph_t g = nullptr;
@@ -131,7 +134,10 @@ qw_status build(LevelGraphCache *c, const GraphKey &key, const IndexView &ix, in
     if ((s = add_while(g, tail, h1, &body)) != QW_OK) return fail(s);
     auto level_body = [&](cudaGraphConditionalHandle h) {
         return [&, h] {
-            QW_TRY(launch_level(ix, nb, 0, 1, 1, l, cgrow, st, cs, ctl));
+            if (bitmap)
+                QW_TRY(launch_bm_level(ix, nb, 0, 1, 1, l, cgrow, st, cs, ctl));
+            else
+                QW_TRY(launch_level(ix, nb, 0, 1, 1, l, cgrow, st, cs, ctl));
             QW_TRY(launch_decide(nb, 0, 1, cap, st, cs, ctl));
             return launch_loop_ctl(ctl, st.max_top, cgrow, h, err, cs);
         };
@@ -158,14 +164,25 @@ qw_status build(LevelGraphCache *c, const GraphKey &key, const IndexView &ix, in
 }  // namespace
 
 qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l, int cgrow,
-                          int cap, bool learned, QueryState &st, LoopCtl *ctl, int *err,
-                          cudaStream_t s)
+                          int cap, bool learned, bool bitmap, QueryState &st, LoopCtl *ctl,
+                          int *err, cudaStream_t s)
 {
     if (!c) {
         set_error("internal: no graph cache");
         return QW_ERR_CUDA;
     }
-    const GraphKey key{nb, l, cgrow, cap, learned, st.g, st.counters, ix.lid, ctl, err};
+    GraphKey key;
+    memset(&key, 0, sizeof(key));  // padding too: the key is compared bytewise in part
+    key.nb = nb;
+    key.l = l;
+    key.cgrow = cgrow;
+    key.cap = cap;
+    key.learned = learned;
+    key.bitmap = bitmap;
+    key.st = st;
+    key.lid = ix.lid;
+    key.ctl = ctl;
+    key.err = err;
     for (auto &en : c->entries)
         if (en.key == key) {
             QW_CUDA_TRY(cudaGraphLaunch(en.exec, s));
@@ -178,7 +195,7 @@ qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l
         c->entries.erase(c->entries.begin());
     }
     cudaGraph_t g = nullptr;
-    QW_TRY(build(c, key, ix, nb, l, cgrow, cap, learned, st, ctl, err, &g));
+    QW_TRY(build(c, key, ix, nb, l, cgrow, cap, learned, bitmap, st, ctl, err, &g));
     cudaGraphExec_t ex = nullptr;
     const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
     if (e != cudaSuccess) {

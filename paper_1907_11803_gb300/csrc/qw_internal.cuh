@@ -92,34 +92,50 @@ struct IndexView {
     const int32_t *dir_off;
     const int64_t *dir_start;
     const int32_t *dir_cnt;
+    // level bitmaps (null when the index was built without them): for every
+    // projection i, tile t, level L <= bm_J[i] and level-L bucket beta, the
+    // tile's ids whose bid / c^L == beta, as kTile bits (kTile / 128 uint4):
+    // bitmap number bm_base[i] + t * bm_nb[i] + bm_lvl[i * kBmLevels + L] + beta
+    const uint4 *bm;
+    const int64_t *bm_base;
+    const int32_t *bm_nb;
+    const int32_t *bm_lvl;
+    const int32_t *bm_J;
 };
+
+// Most levels a bitmap table describes per projection (c >= 2, bids < 2^31).
+constexpr int kBmLevels = 32;
+constexpr int kBmUint4 = kTile / 128;  // uint4 per bitmap
 
 // Per-batch query state, all device arrays of length nb (or nb x m).
 struct QueryState {
-    int64_t *g;             // nb x m: h_i(q) - o_i
-    int64_t *top;           // nb: max_i max(span_i, g_i)
-    int32_t *active;        // nb
-    int32_t *ncand;         // nb: |C_R| after the last finished level
-    int32_t *nprev;         // nb
-    int32_t *cross;         // nb: candidates of the running level, summed over tiles
-    int32_t *term;          // nb
-    int32_t *levels;        // nb
-    int64_t *finalR;        // nb
-    int64_t *scan_level;    // nb
-    int64_t *scan_last;     // nb
-    int64_t *scan_full;     // nb
-    int32_t *nkeep;         // nb
-    unsigned long long *max_top;  // 1
-    uint32_t *counters;     // nb x (nT * kTile / 4)
-    int32_t *cand;          // nb x cap
-    int32_t *cand_col;      // nb x cap
-    int32_t *tile_hist;     // nb x nT x kHistBins
-    int32_t *tile_plan;     // nb x nT x 3: first output slot, count-c* ids before the tile,
+    int64_t *g = nullptr;             // nb x m: h_i(q) - o_i
+    int64_t *top = nullptr;           // nb: max_i max(span_i, g_i)
+    int32_t *active = nullptr;        // nb
+    int32_t *ncand = nullptr;         // nb: |C_R| after the last finished level
+    int32_t *nprev = nullptr;         // nb
+    int32_t *cross = nullptr;         // nb: candidates of the running level, summed over tiles
+    int32_t *term = nullptr;          // nb
+    int32_t *levels = nullptr;        // nb
+    int64_t *finalR = nullptr;        // nb
+    int64_t *scan_level = nullptr;    // nb
+    int64_t *scan_last = nullptr;     // nb
+    int64_t *scan_full = nullptr;     // nb
+    int32_t *nkeep = nullptr;         // nb
+    unsigned long long *max_top = nullptr;  // 1
+    uint32_t *counters = nullptr;     // nb x (nT * kTile / 4)
+    int32_t *cand = nullptr;          // nb x cap
+    int32_t *cand_col = nullptr;      // nb x cap
+    int32_t *tile_hist = nullptr;     // nb x nT x kHistBins
+    int32_t *tile_plan = nullptr;     // nb x nT x 3: first output slot, count-c* ids before the tile,
                             //   ids kept in the tile
-    int32_t *qplan;         // nb x 2: c*, how many count-c* ids are kept
-    int32_t *start;         // nb: first level of the query (0 unless learned)
-    int32_t *fb;            // nb: query stopped at a learned first level > 0
-    unsigned long long *fb_count;  // 2: queries to recompute, levels skipped
+    int32_t *qplan = nullptr;         // nb x 2: c*, how many count-c* ids are kept
+    int32_t *start = nullptr;         // nb: first level of the query (0 unless learned)
+    int32_t *fb = nullptr;            // nb: query stopped at a learned first level > 0
+    unsigned long long *fb_count = nullptr;  // 2: queries to recompute, levels skipped
+    unsigned long long *level_passes = nullptr;  // profile mode: (query, level) passes run, else null
+    uint4 *cbits = nullptr;           // bitmap path: 2 (level parity) x nb x nT candidate bitmaps
+    int64_t cb_par = 0;         // uint4 per parity (batch capacity x nT x kBmUint4)
 };
 
 // Level of a loop that runs on the device (graph mode): the level kernels
@@ -141,6 +157,23 @@ qw_status launch_level(const IndexView &ix, int nb, int level, int64_t R, int64_
 qw_status launch_fallback(int nb, QueryState &st, cudaStream_t s);
 qw_status launch_decide(int nb, int level, int64_t R, int cap, QueryState &st, cudaStream_t s,
                         const LoopCtl *ctl = nullptr);
+// Bitmap path (qw_bitmap.cu).
+struct BitmapLayout {
+    std::vector<int64_t> base;   // per projection, first bitmap
+    std::vector<int32_t> nb;     // per projection, bitmaps per tile
+    std::vector<int32_t> lvl;    // m x kBmLevels, first bitmap of each level in a tile's block
+    std::vector<int32_t> J;      // per projection, last level stored (c^J > span)
+    int64_t total = 0;           // bitmaps
+};
+qw_status bitmap_layout(const std::vector<int32_t> &span, int nT, int c, BitmapLayout *out);
+qw_status launch_bitmap_build(const IndexView &ix, int c, int maxJ, uint4 *bm, cudaStream_t s);
+qw_status launch_bm_level(const IndexView &ix, int nb, int level, int64_t R, int64_t Rp, int l,
+                          int cgrow, QueryState &st, cudaStream_t s, const LoopCtl *ctl = nullptr);
+qw_status launch_bm_collect(const IndexView &ix, int nb, int l, int cap, QueryState &st,
+                            int64_t *stats_out, cudaStream_t s);
+qw_status launch_select_plan(const IndexView &ix, int nb, int l, int cap, QueryState &st,
+                             int64_t *stats_out, cudaStream_t s);
+
 // Device-driven loop control (qw_graph.cu builds the graphs that use them).
 qw_status launch_loop_init(LoopCtl *ctl, cudaStream_t s);
 qw_status launch_loop_ctl(LoopCtl *ctl, const unsigned long long *max_top, int cgrow,
@@ -153,8 +186,8 @@ struct LevelGraphCache;
 LevelGraphCache *level_graph_cache_new();
 void level_graph_cache_free(LevelGraphCache *c);
 qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l, int cgrow,
-                          int cap, bool learned, QueryState &st, LoopCtl *ctl, int *err,
-                          cudaStream_t s);
+                          int cap, bool learned, bool bitmap, QueryState &st, LoopCtl *ctl,
+                          int *err, cudaStream_t s);
 qw_status launch_collect(const IndexView &ix, int nb, int l, int cap, QueryState &st,
                          int64_t *stats_out, cudaStream_t s);
 bool cluster_path_fits(const IndexView &ix, int *cluster_size, int *tiles_per_cta);

@@ -20,6 +20,7 @@
 // flanks, counts the ids whose count reaches l, and writes the counters back.
 #include "qw_internal.cuh"
 #include "qw_count.cuh"
+#include "qw_dir.cuh"
 #include "qw_scan.cuh"
 
 #include <algorithm>
@@ -30,39 +31,6 @@ namespace {
 constexpr int LV_THREADS = 256;
 constexpr int kWordsPerTile = kTile / 4;
 constexpr int kUnroll = 4;
-
-__device__ __forceinline__ int64_t floordiv64(int64_t a, int64_t R)
-{
-    int64_t q = a / R;
-    if ((a % R != 0) && (a < 0)) --q;
-    return q;
-}
-
-__device__ __forceinline__ int64_t clamp64(int64_t x, int64_t lo, int64_t hi)
-{
-    return x < lo ? lo : (x > hi ? hi : x);
-}
-
-// Offset (inside the tile's entry segment) of the first entry with bid >= x.
-// The directory of a tile holds its distinct bids ub[0..cnt) ascending and the
-// offset uo[] of each bid's first entry.  When every bid between ub[0] and x is
-// present the answer sits at slot x - ub[0]; otherwise binary search.
-__device__ __forceinline__ int dir_lower(const int32_t *__restrict__ ub,
-                                         const int32_t *__restrict__ uo, int cnt, int len,
-                                         int64_t x)
-{
-    if (cnt == 0) return 0;
-    const int32_t b0 = ub[0];
-    if (x <= b0) return 0;
-    const int64_t p = x - b0;
-    if (p < cnt && ub[p] == x) return uo[p];
-    int lo = 0, hi = cnt;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if ((int64_t)ub[mid] < x) lo = mid + 1; else hi = mid;
-    }
-    return lo < cnt ? uo[lo] : len;
-}
 
 __global__ void query_setup_kernel(const int32_t *__restrict__ HQ, int nb, int m,
                                    const int32_t *__restrict__ o,
@@ -313,6 +281,7 @@ __global__ void decide_kernel(int nb, int level, int64_t R, int cap, QueryState 
         R = ctl->R;
     }
     if (level < st.start[q]) return;
+    if (st.level_passes) atomicAdd(st.level_passes, 1ull);
     const int32_t before = st.ncand[q];  // |C_R| of the previous level
     const int32_t nc = st.cross[q];      // |C_R| of this level, summed over tiles
     st.cross[q] = 0;
@@ -678,12 +647,19 @@ qw_status launch_decide(int nb, int level, int64_t R, int cap, QueryState &st, c
     return QW_OK;
 }
 
+qw_status launch_select_plan(const IndexView &ix, int nb, int l, int cap, QueryState &st,
+                             int64_t *stats_out, cudaStream_t s)
+{
+    select_plan_kernel<<<nb, CL_THREADS, 0, s>>>(ix.nT, ix.m, l, cap, st, stats_out);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
+
 qw_status launch_collect(const IndexView &ix, int nb, int l, int cap, QueryState &st,
                          int64_t *stats_out, cudaStream_t s)
 {
     const int64_t wpq = (int64_t)ix.nT * kWordsPerTile;
-    select_plan_kernel<<<nb, CL_THREADS, 0, s>>>(ix.nT, ix.m, l, cap, st, stats_out);
-    QW_CUDA_TRY(cudaGetLastError());
+    QW_TRY(launch_select_plan(ix, nb, l, cap, st, stats_out, s));
     select_emit_kernel<<<dim3((unsigned)ix.nT, (unsigned)nb), CL_THREADS, 0, s>>>(ix.n, ix.nT, l, cap,
                                                                                 st, wpq);
     QW_CUDA_TRY(cudaGetLastError());

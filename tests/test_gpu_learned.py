@@ -63,7 +63,7 @@ def test_learned_start_same_results_fewer_levels(qwlib, cuda):
     spec = dict(n=60_000, d=48, m=32, n_clusters=120, query_clusters=30)
     wl = workloads.make_workload("mix1m_d128", seed=7, nq=600, n_train=3000, **spec)
     X, A, b = (torch.from_numpy(a).to(cuda) for a in (wl.X, wl.A, wl.b))
-    index = qwlib.Index(X, A, b, w=4.0, v=300)
+    index = qwlib.Index(X, A, b, w=4.0, v=300, bitmaps=True)
     mlp, labels = _train_start_model(qwlib, cuda, index, wl.Q_train, 20)
     index.set_start_model(mlp, eps=0.02)
     Q = torch.from_numpy(wl.Q).to(cuda)
@@ -81,6 +81,12 @@ def test_learned_start_same_results_fewer_levels(qwlib, cuda):
     assert torch.equal(ids0, ids3) and torch.equal(d0, d3) and torch.equal(st0, st3)
     assert prof3["start_levels_skipped"] == prof["start_levels_skipped"]
     assert prof3["start_fallbacks"] == prof["start_fallbacks"]
+    # bitmap path, host loop and graph mode
+    for graph in (False, True):
+        ids5, d5, st5 = index.query(Q, 20, stats=True, start="learned", path="bitmap", graph=graph)
+        prof5 = index.profile(reset=True)
+        assert torch.equal(ids0, ids5) and torch.equal(d0, d5) and torch.equal(st0, st5)
+        assert prof5["start_levels_skipped"] == prof["start_levels_skipped"]
     # an over-eager model (eps close to 1) starts too late for many queries:
     # they are recomputed from level 0 and the results still match
     index.set_start_model(mlp, eps=0.999)

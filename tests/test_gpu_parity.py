@@ -13,8 +13,9 @@ pytestmark = pytest.mark.gpu
 
 DIST_RTOL = 1e-5
 TILE = 32768
-# "graph": the level path with its level loop run as a CUDA graph
-PATHS = pytest.mark.parametrize("path", ["levels", "cluster", "graph"])
+# "graph": the level path with its level loop run as a CUDA graph; "bitmap":
+# counts from the index's level bitmaps ("bitmap_graph": the same in graph mode)
+PATHS = pytest.mark.parametrize("path", ["levels", "cluster", "graph", "bitmap", "bitmap_graph"])
 
 
 def _t(x, dev):
@@ -60,10 +61,10 @@ def _gpu_workload(qw, dev, X, Q, A, b, *, w, k, v, l, c=2, batch=0, host=False, 
         Qd = torch.from_numpy(np.ascontiguousarray(Q))
     else:
         Xd, Qd, Ad, bd = _t(X, dev), _t(Q, dev), _t(A, dev), _t(b, dev)
-    index = qw.Index(Xd, Ad, bd, w=w, c=c, v=v, l=l, shadow_bf16=(rerank == "bf16"))
-    graph = path == "graph"
-    if graph:
-        path = "levels"
+    index = qw.Index(Xd, Ad, bd, w=w, c=c, v=v, l=l, shadow_bf16=(rerank == "bf16"),
+                     bitmaps=path.startswith("bitmap"))
+    graph = path in ("graph", "bitmap_graph")
+    path = {"graph": "levels", "bitmap_graph": "bitmap"}.get(path, path)
     ids, dists, st = index.query(Qd, k, batch=batch, stats=True, path=path, order=order,
                                  rerank=rerank, graph=graph)
     cid, ccol, st2 = index.candidates(Qd, k, batch=batch, path=path, order=order, graph=graph)
