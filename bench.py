@@ -345,8 +345,8 @@ def run_ours(args):
     Qt = torch.from_numpy(wt.Q_train).to(dev)
     if args.start == "learned":
         mlp, train_info = train_start_model(qw, torch, index, Qt, s.k, args)
-        if args.no_tune:
-            chosen_kw["path"] = "levels"  # learned first levels run on the level path
+        if args.no_tune and chosen_kw["path"] in ("auto", "cluster"):
+            chosen_kw["path"] = "levels"  # learned first levels need a level loop
     tune = None
     if not args.no_tune:
         # settings from the autotuner, timed on earlier queries of the same workload

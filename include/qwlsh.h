@@ -109,8 +109,15 @@ typedef struct {
                              graph whose conditional WHILE node advances the level on the
                              device, so the host does not wait inside a batch; the call waits
                              for the stream once at its end.  Same kernels, same results */
+    int32_t bitmap_loads; /* QW_PATH_BITMAP: QW_LOADS_TMA (default) stages the bucket bitmaps
+                             in shared memory with TMA bulk copies in a persistent kernel;
+                             QW_LOADS_DIRECT loads them straight from global memory, one CTA
+                             per (tile, query).  Same results */
     int32_t reserved[1];  /* must be zero */
 } qw_query_params;
+
+#define QW_LOADS_TMA 0
+#define QW_LOADS_DIRECT 1
 
 /* First level of the collision-counting loop.  QW_START_PLAIN: every query
  * starts at radius R = 1.  QW_START_LEARNED: the index's start model predicts,
@@ -326,7 +333,7 @@ typedef struct {
  * when a start model is attached), queries per batch on the level path (the
  * default and 1/16, 1/4, 4x of it) and graph mode; the bitmap path (when the
  * index has bitmaps) with its default batch, 1/16 and 1/4 of it, and graph
- * mode; then the cluster path against the best so far (when the index fits it
+ * mode and direct loads; then the cluster path against the best so far (when the index fits it
  * and the start is plain); order (signature / given) and rerank (FP32 / BF16,
  * when the index has the BF16 copy).  Every setting returns the same results, so the choice cannot change
  * them.  Each setting runs once untimed, then `reps` (>= 1) times timed with

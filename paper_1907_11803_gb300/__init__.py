@@ -48,7 +48,8 @@ class qw_index_params(C.Structure):
 class qw_query_params(C.Structure):
     _fields_ = [("batch", C.c_int32), ("profile", C.c_int32), ("path", C.c_int32),
                 ("clusters", C.c_int32), ("order", C.c_int32), ("rerank", C.c_int32),
-                ("start", C.c_int32), ("graph", C.c_int32), ("reserved", C.c_int32 * 1)]
+                ("start", C.c_int32), ("graph", C.c_int32), ("bitmap_loads", C.c_int32),
+                ("reserved", C.c_int32 * 1)]
 
 
 QW_TUNE_MAX = 32
@@ -68,6 +69,8 @@ RERANKS = {"fp32": QW_RERANK_FP32, "bf16": QW_RERANK_BF16}
 ORDERS = {"auto": QW_ORDER_AUTO, "signature": QW_ORDER_SIGNATURE, "given": QW_ORDER_GIVEN}
 QW_START_PLAIN, QW_START_LEARNED = 0, 1
 STARTS = {"plain": QW_START_PLAIN, "learned": QW_START_LEARNED}
+QW_LOADS_TMA, QW_LOADS_DIRECT = 0, 1
+LOADS = {"tma": QW_LOADS_TMA, "direct": QW_LOADS_DIRECT}
 (QW_K_PROJECT, QW_K_SETUP, QW_K_LEVEL, QW_K_DECIDE, QW_K_SELECT, QW_K_RERANK, QW_K_CLUSTER,
  QW_K_ORDER, QW_K_START) = range(9)
 QW_K_COUNT = 9
@@ -258,7 +261,7 @@ def _params_kwargs(p) -> dict:
     inv = lambda d, v: next(k for k, x in d.items() if x == v)  # noqa: E731
     return {"batch": int(p.batch), "path": inv(PATHS, p.path), "order": inv(ORDERS, p.order),
             "rerank": inv(RERANKS, p.rerank), "start": inv(STARTS, p.start),
-            "graph": bool(p.graph)}
+            "graph": bool(p.graph), "loads": inv(LOADS, p.bitmap_loads)}
 
 
 def _stream_of(t) -> int:
@@ -349,7 +352,7 @@ class Index:
     def query(self, Q, k: int, *, batch: int = 0, stats: bool = False, out=None,
               profile: bool = False, path: str = "auto", clusters: int = 0,
               order: str = "auto", rerank: str = "fp32", start: str = "plain",
-              graph: bool = False):
+              graph: bool = False, loads: str = "tma"):
         """Top-k of every query row.  Returns (ids int64 nq x k, dists float32
         nq x k[, stats int64 nq x QW_NSTAT]) on Q's device (host tensors in,
         host tensors out).  ``out`` may give preallocated (ids, dists[, stats])."""
@@ -370,13 +373,14 @@ class Index:
         mem = _mem_of(Q, ids, dists, st)
         qp = qw_query_params(batch=int(batch), profile=1 if profile else 0, path=PATHS[path],
                              clusters=int(clusters), order=ORDERS[order], rerank=RERANKS[rerank],
-                             start=STARTS[start], graph=1 if graph else 0)
+                             start=STARTS[start], graph=1 if graph else 0,
+                             bitmap_loads=LOADS[loads])
         qw_run_workload(self._h, Q.data_ptr(), nq, int(k), qp, ids.data_ptr(), dists.data_ptr(),
                         st.data_ptr() if st is not None else 0, mem, _stream_of(Q))
         return (ids, dists, st) if stats else (ids, dists)
 
     def candidates(self, Q, k: int, *, batch: int = 0, path: str = "auto", order: str = "auto",
-                   graph: bool = False):
+                   graph: bool = False, loads: str = "tma"):
         """Kept candidates per query (ascending ids, -1 padded) with their
         collision counts, and the per-query statistics, on Q's device."""
         torch = _torch()
@@ -388,7 +392,7 @@ class Index:
         st = torch.empty((nq, QW_NSTAT), dtype=torch.int64, device=Q.device)
         mem = _mem_of(Q, cid, ccol, st)
         qp = qw_query_params(batch=int(batch), path=PATHS[path], order=ORDERS[order],
-                             graph=1 if graph else 0)
+                             graph=1 if graph else 0, bitmap_loads=LOADS[loads])
         qw_workload_candidates(self._h, Q.data_ptr(), nq, int(k), qp, cid.data_ptr(),
                                ccol.data_ptr(), st.data_ptr(), mem, _stream_of(Q))
         return cid, ccol, st

@@ -70,7 +70,7 @@ struct qw_index {
     DevBuf X, A, b, o, span, lid, dir_bid, dir_off, dir_start, dir_cnt, Xb, xnorm;
     bool shadow = false;
     bool bitmaps = false;               // level bitmaps for QW_PATH_BITMAP
-    DevBuf bm, bm_base, bm_nb, bm_lvl, bm_J;
+    DevBuf bm, bm_base, bm_nb, bm_lvl, bm_J, bid_prefix, prefix_off;
     int bm_maxJ = 0;
     float xs = 1.0f;                 // 1 / RMS coordinate of the data (start-model features)
     qw_mlp *start_model = nullptr;   // not owned
@@ -81,7 +81,8 @@ struct qw_index {
     int32_t tuned_batch = 0;
     DevBuf w_feat;
     // workspace for queries (grow-only)
-    DevBuf w_q, w_hq, w_state, w_counters, w_cand, w_out, w_err, w_order, w_qb, w_ob, w_cbits;
+    DevBuf w_q, w_hq, w_state, w_counters, w_cand, w_out, w_err, w_order, w_qb, w_ob, w_cbits,
+        w_clist;
     int64_t device_bytes = 0;
     qw_profile prof{};
     std::vector<cudaEvent_t> event_pool;
@@ -106,6 +107,8 @@ struct qw_index {
         v.bm_nb = bm_nb.as<int32_t>();
         v.bm_lvl = bm_lvl.as<int32_t>();
         v.bm_J = bm_J.as<int32_t>();
+        v.bid_prefix = bid_prefix.as<int64_t>();
+        v.prefix_off = prefix_off.as<int64_t>();
         return v;
     }
 };
@@ -351,7 +354,21 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
         QW_CUDA_TRY(cudaMemcpyAsync(ix->bm_J.p, lay.J.data(), m * sizeof(int32_t),
                                     cudaMemcpyHostToDevice, s));
         ix->bm_maxJ = *std::max_element(lay.J.begin(), lay.J.end());
+        // per projection, objects with bid < b for b = 0 .. span + 1
+        std::vector<int64_t> poff(m);
+        int64_t ptot = 0;
+        for (int i = 0; i < m; ++i) {
+            poff[i] = ptot;
+            ptot += (int64_t)h_span[i] + 2;
+        }
+        QW_TRY(ix->bid_prefix.ensure((size_t)ptot * sizeof(int64_t)));
+        QW_TRY(ix->prefix_off.ensure((size_t)m * sizeof(int64_t)));
+        QW_CUDA_TRY(cudaMemsetAsync(ix->bid_prefix.p, 0, ix->bid_prefix.bytes, s));
+        QW_CUDA_TRY(cudaMemcpyAsync(ix->prefix_off.p, poff.data(), m * sizeof(int64_t),
+                                    cudaMemcpyHostToDevice, s));
         QW_TRY(launch_bitmap_build(ix->view(), ix->c, ix->bm_maxJ, ix->bm.as<uint4>(), s));
+        QW_TRY(launch_bid_prefix(ix->view(), ix->bid_prefix.as<int64_t>(),
+                                 ix->prefix_off.as<int64_t>(), s));
     }
     if (ix->shadow) {
         QW_TRY(ix->Xb.ensure((size_t)n * d * 2));
@@ -363,7 +380,8 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
                                  ix->span.bytes + ix->lid.bytes + ix->dir_bid.bytes +
                                  ix->dir_off.bytes + ix->dir_start.bytes + ix->dir_cnt.bytes +
                                  ix->bm.bytes + ix->bm_base.bytes + ix->bm_nb.bytes +
-                                 ix->bm_lvl.bytes + ix->bm_J.bytes);
+                                 ix->bm_lvl.bytes + ix->bm_J.bytes + ix->bid_prefix.bytes +
+                                 ix->prefix_off.bytes);
     return QW_OK;
 }
 
@@ -415,7 +433,8 @@ qw_status qw_build_index(const float *data, int64_t n, int32_t d, const float *A
 // stopped); with learned starts, a second pass from level 0 for the queries
 // that stopped at their learned first level.
 static qw_status host_level_loop(qw_index *ix, LaunchTimer &tm, const IndexView &view, int nb,
-                                 int cap, bool learned, bool bitmap, QueryState &st, cudaStream_t s)
+                                 int cap, bool learned, bool bitmap, bool tma, int *err,
+                                 QueryState &st, cudaStream_t s)
 {
     unsigned long long max_top = 0;
     QW_CUDA_TRY(cudaMemcpyAsync(&max_top, st.max_top, sizeof(max_top), cudaMemcpyDeviceToHost, s));
@@ -424,10 +443,13 @@ static qw_status host_level_loop(qw_index *ix, LaunchTimer &tm, const IndexView 
         int64_t R = 1, Rp = 1;
         for (int level = 0;; ++level) {
             QW_TRY(tm.run(QW_K_LEVEL, 1, [&] {
-                return bitmap ? launch_bm_level(view, nb, level, R, Rp, ix->l, ix->c, st, s)
+                return bitmap ? launch_bm_level(view, nb, level, R, Rp, ix->l, ix->c, st, err, tma, s)
                               : launch_level(view, nb, level, R, Rp, ix->l, ix->c, st, s);
             }));
-            QW_TRY(tm.run(QW_K_DECIDE, 1, [&] { return launch_decide(nb, level, R, cap, st, s); }));
+            QW_TRY(tm.run(QW_K_DECIDE, 1, [&] {
+                return launch_decide(nb, level, R, cap, st, s, nullptr,
+                                     bitmap ? scan_stats_of(view, ix->c) : ScanStats());
+            }));
             if ((unsigned long long)R > max_top) break;
             if (level > 62) {
                 set_error("qw_run_workload: level limit reached");
@@ -500,8 +522,10 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     if (eff_path == QW_PATH_BITMAP && !ix->bitmaps) eff_path = QW_PATH_LEVELS;
     const bool use_cluster = eff_path == QW_PATH_CLUSTER && fits;
     const bool use_bitmap = eff_path == QW_PATH_BITMAP;
-    // candidate bitmaps of the bitmap path: two levels of (query, tile) bitmaps
+    const bool tma_loads = !qp || qp->bitmap_loads == QW_LOADS_TMA;
+    // bitmap path, per query: two levels of (tile) candidate bitmaps and lists
     const int64_t cb_bytes = (int64_t)ix->nT * kBmUint4 * (int64_t)sizeof(uint4) * 2;
+    const int64_t cl_bytes = (int64_t)ix->nT * (kListCap + 1) * (int64_t)sizeof(uint32_t) * 2;
     int64_t B = qp && qp->batch > 0 ? qp->batch : 0;
     if (B == 0 && ix->tuned && ix->tuned_batch > 0 && !use_cluster &&
         (path == QW_PATH_AUTO || path == ix->tuned_path))
@@ -509,7 +533,8 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     if (B == 0) {
         const int64_t budget = (int64_t)2 << 30;  // counters of one batch
         B = use_cluster ? (int64_t)65535
-                        : std::max<int64_t>(1, budget / (use_bitmap ? cb_bytes : wpq_bytes));
+                        : std::max<int64_t>(1, budget / (use_bitmap ? cb_bytes + cl_bytes
+                                                                    : wpq_bytes));
     }
     B = std::min<int64_t>(B, std::max<int64_t>(nq, 1));
     B = std::min<int64_t>(B, 65535);
@@ -519,7 +544,10 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     QW_TRY(ix->w_err.ensure(64));
     QW_TRY(ix->w_hq.ensure((size_t)nq * m * sizeof(int32_t)));       // bucket ids of all queries
     if (!use_cluster && !use_bitmap) QW_TRY(ix->w_counters.ensure((size_t)B * wpq_bytes));
-    if (use_bitmap) QW_TRY(ix->w_cbits.ensure((size_t)B * cb_bytes));
+    if (use_bitmap) {
+        QW_TRY(ix->w_cbits.ensure((size_t)B * cb_bytes));
+        QW_TRY(ix->w_clist.ensure((size_t)B * cl_bytes));
+    }
     QW_TRY(ix->w_cand.ensure((size_t)B * cap * 2 * sizeof(int32_t)));
     const size_t plan_ints = (size_t)B * ix->nT * (kHistBins + 3) + (size_t)B * 2;
     const size_t st_bytes = (size_t)B * m * 8 + (size_t)B * 8 * 16 + plan_ints * 4 + 256 +
@@ -608,6 +636,10 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     st.cbits = ix->w_cbits.as<uint4>();
     st.level_passes = nullptr;
     st.cb_par = B * ix->nT * kBmUint4;
+    st.cl_par = B * ix->nT * kListCap;
+    st.cln_par = B * ix->nT;
+    st.clist = ix->w_clist.as<uint32_t>();
+    st.clist_n = st.clist ? reinterpret_cast<int32_t *>(st.clist + 2 * st.cl_par) : nullptr;
     st.cand = ix->w_cand.as<int32_t>();
     st.cand_col = st.cand + (size_t)B * cap;
     int *err = ix->w_err.as<int>();
@@ -725,10 +757,11 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             if (graph) {
                 QW_TRY(tm.run(QW_K_LEVEL, 0, [&] {
                     return run_level_graph(ix->graphs, view, nb, ix->l, ix->c, cap, learned,
-                                           use_bitmap, st, ctl, err, s);
+                                           use_bitmap, tma_loads, st, ctl, err, s);
                 }));
             } else {
-                QW_TRY(host_level_loop(ix, tm, view, nb, cap, learned, use_bitmap, st, s));
+                QW_TRY(host_level_loop(ix, tm, view, nb, cap, learned, use_bitmap, tma_loads, err,
+                                       st, s));
             }
             QW_TRY(tm.run(QW_K_SELECT, 2, [&] {
                 return use_bitmap ? launch_bm_collect(view, nb, ix->l, cap, st, stats_b, s)
@@ -753,6 +786,16 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             }));
         }
     }
+    if (use_bitmap && !graph) {
+        // a staged-copy wait of the bitmap kernel that gave up (bounded waits)
+        int h_err = 0;
+        QW_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        QW_CUDA_TRY(cudaStreamSynchronize(s));
+        if (h_err & 4) {
+            set_error("qw_run_workload: a staged-copy wait in the bitmap kernel gave up");
+            return QW_ERR_TIMEOUT;
+        }
+    }
     if (graph && !use_cluster) {
         // the device-driven loops: their launch counts, the level-limit flag and
         // the learned-start counters, once per call
@@ -763,6 +806,10 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         QW_CUDA_TRY(cudaStreamSynchronize(s));
         if (h_err & 8) {
             set_error("qw_run_workload: level limit reached");
+            return QW_ERR_TIMEOUT;
+        }
+        if (h_err & 4) {
+            set_error("qw_run_workload: a staged-copy wait in the bitmap kernel gave up");
             return QW_ERR_TIMEOUT;
         }
         ix->prof.launches[QW_K_LEVEL] += (int64_t)h_ctl.iters;
@@ -818,6 +865,8 @@ static qw_status check_workload_args(const qw_index *ix, const float *queries, i
         if (qp->start < QW_START_PLAIN || qp->start > QW_START_LEARNED)
             return arg_error("qw_run_workload: unknown start");
         if (qp->graph != 0 && qp->graph != 1) return arg_error("qw_run_workload: graph must be 0 or 1");
+        if (qp->bitmap_loads != QW_LOADS_TMA && qp->bitmap_loads != QW_LOADS_DIRECT)
+            return arg_error("qw_run_workload: unknown bitmap_loads");
         for (int r = 0; r < 1; ++r)
             if (qp->reserved[r] != 0) return arg_error("qw_run_workload: reserved field set");
     }
@@ -966,7 +1015,8 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
             cur = bp0;
             cur_ms = bms;
             cur_slot = bslot;
-            const int64_t cb_b = (int64_t)ix->nT * kBmUint4 * (int64_t)sizeof(uint4) * 2;
+            const int64_t cb_b = (int64_t)ix->nT * kBmUint4 * (int64_t)sizeof(uint4) * 2 +
+                                 (int64_t)ix->nT * (kListCap + 1) * (int64_t)sizeof(uint32_t) * 2;
             const int64_t bdef = std::min<int64_t>(
                 std::min<int64_t>(std::max<int64_t>(1, ((int64_t)2 << 30) / cb_b), nq), 65535);
             const int64_t bc[2] = {bdef / 16, bdef / 4};
@@ -981,6 +1031,9 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
             if (status != QW_OK) break;
             qw_query_params alt = cur;
             alt.graph = 1;
+            if ((status = try_alt(alt)) != QW_OK) break;
+            alt = cur;
+            alt.bitmap_loads = QW_LOADS_DIRECT;
             if ((status = try_alt(alt)) != QW_OK) break;
             if (best_levels_ms < cur_ms) {
                 cur = best_levels;
@@ -1147,7 +1200,9 @@ void qw_index_free(qw_index *ix)
                       &ix->w_state, &ix->w_counters, &ix->w_cand, &ix->w_out, &ix->w_err,
                       &ix->w_order, &ix->w_qb, &ix->w_ob, &ix->w_feat};
     for (DevBuf *bb : bufs) bb->release();
-    DevBuf *bmb[] = {&ix->bm, &ix->bm_base, &ix->bm_nb, &ix->bm_lvl, &ix->bm_J, &ix->w_cbits};
+    DevBuf *bmb[] = {&ix->bm,  &ix->bm_base,    &ix->bm_nb,      &ix->bm_lvl,
+                     &ix->bm_J, &ix->bid_prefix, &ix->prefix_off, &ix->w_cbits,
+                     &ix->w_clist};
     for (DevBuf *bb : bmb) bb->release();
     for (cudaEvent_t e : ix->event_pool) cudaEventDestroy(e);
     level_graph_cache_free(ix->graphs);

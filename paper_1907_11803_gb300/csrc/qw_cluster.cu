@@ -20,6 +20,7 @@
 #include "qw_internal.cuh"
 #include "qw_count.cuh"
 #include "qw_dir.cuh"
+#include "qw_tma.cuh"
 #include "qw_scan.cuh"
 
 #include <cooperative_groups.h>
@@ -39,70 +40,6 @@ constexpr int kMaxTPC = 6;
 constexpr int kStages = 4;                     // ring of staged index entries
 constexpr int kStageBytes = 8192;
 constexpr int kCPS = kStageBytes / 16;         // 8-entry chunks per stage
-constexpr long long kWaitCycles = 4000000000LL;  // about 2 s: a stuck wait gives up
-
-// ---- TMA bulk copies and mbarriers (inline PTX, sm_90+)
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Wait for the phase of `bar` with the given parity; gives up after about two
-// seconds, records the failure in *err and in *stuck (later waits then return
-// at once), so the kernel always runs to its end.
-__device__ __forceinline__ void mbar_wait(uint64_t *bar, uint32_t parity, int *err, bool &stuck)
-{
-    if (stuck) return;
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > kWaitCycles) {
-            atomicOr(err, 4);
-            stuck = true;
-            return;
-        }
-    }
-}
-
-// One TMA bulk copy global -> this CTA's shared memory, completing on `bar`.
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
 
 struct ClusterShared {
     // used in every CTA

@@ -26,7 +26,7 @@ namespace qw {
 
 struct GraphKey {
     int nb, l, cgrow, cap;
-    bool learned, bitmap;
+    bool learned, bitmap, tma;
     QueryState st;         // every workspace pointer the graph's kernels take by value
     const void *lid;       // the index
     const void *ctl;
@@ -34,7 +34,7 @@ struct GraphKey {
     bool operator==(const GraphKey &o) const
     {
         return nb == o.nb && l == o.l && cgrow == o.cgrow && cap == o.cap &&
-               learned == o.learned && bitmap == o.bitmap &&
+               learned == o.learned && bitmap == o.bitmap && tma == o.tma &&
                memcmp(&st, &o.st, sizeof(QueryState)) == 0 && lid == o.lid && ctl == o.ctl &&
                err == o.err;
     }
@@ -112,8 +112,8 @@ qw_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
 }
 
 qw_status build(LevelGraphCache *c, const GraphKey &key, const IndexView &ix, int nb, int l,
-                int cgrow, int cap, bool learned, bool bitmap, QueryState &st, LoopCtl *ctl,
-                int *err, cudaGraph_t *graph_out)
+                int cgrow, int cap, bool learned, bool bitmap, bool tma, QueryState &st,
+                LoopCtl *ctl, int *err, cudaGraph_t *graph_out)
 {
     cudaStream_t cs = c->cap_stream;
     cudaGraph_t g = nullptr;
@@ -126,7 +126,8 @@ qw_status build(LevelGraphCache *c, const GraphKey &key, const IndexView &ix, in
     cudaGraphConditionalHandle h1, h2;
     cudaError_t e = cudaGraphConditionalHandleCreate(&h1, g, 1, cudaGraphCondAssignDefault);
     if (e != cudaSuccess) return fail(cuda_status(e, "cudaGraphConditionalHandleCreate"));
-    qw_status s = capture_into(cs, g, nullptr, 0, [&] { return launch_loop_init(ctl, cs); });
+    qw_status s =
+        capture_into(cs, g, nullptr, 0, [&] { return launch_loop_init(ctl, st, nb, cgrow, cs); });
     if (s != QW_OK) return fail(s);
     std::vector<cudaGraphNode_t> tail;
     if ((s = sinks(g, tail)) != QW_OK) return fail(s);
@@ -135,10 +136,11 @@ qw_status build(LevelGraphCache *c, const GraphKey &key, const IndexView &ix, in
     auto level_body = [&](cudaGraphConditionalHandle h) {
         return [&, h] {
             if (bitmap)
-                QW_TRY(launch_bm_level(ix, nb, 0, 1, 1, l, cgrow, st, cs, ctl));
+                QW_TRY(launch_bm_level(ix, nb, 0, 1, 1, l, cgrow, st, err, tma, cs, ctl));
             else
                 QW_TRY(launch_level(ix, nb, 0, 1, 1, l, cgrow, st, cs, ctl));
-            QW_TRY(launch_decide(nb, 0, 1, cap, st, cs, ctl));
+            QW_TRY(launch_decide(nb, 0, 1, cap, st, cs, ctl,
+                                 bitmap ? scan_stats_of(ix, cgrow) : ScanStats()));
             return launch_loop_ctl(ctl, st.max_top, cgrow, h, err, cs);
         };
     };
@@ -164,8 +166,8 @@ qw_status build(LevelGraphCache *c, const GraphKey &key, const IndexView &ix, in
 }  // namespace
 
 qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l, int cgrow,
-                          int cap, bool learned, bool bitmap, QueryState &st, LoopCtl *ctl,
-                          int *err, cudaStream_t s)
+                          int cap, bool learned, bool bitmap, bool tma, QueryState &st,
+                          LoopCtl *ctl, int *err, cudaStream_t s)
 {
     if (!c) {
         set_error("internal: no graph cache");
@@ -179,6 +181,7 @@ qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l
     key.cap = cap;
     key.learned = learned;
     key.bitmap = bitmap;
+    key.tma = tma;
     key.st = st;
     key.lid = ix.lid;
     key.ctl = ctl;
@@ -195,7 +198,7 @@ qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l
         c->entries.erase(c->entries.begin());
     }
     cudaGraph_t g = nullptr;
-    QW_TRY(build(c, key, ix, nb, l, cgrow, cap, learned, bitmap, st, ctl, err, &g));
+    QW_TRY(build(c, key, ix, nb, l, cgrow, cap, learned, bitmap, tma, st, ctl, err, &g));
     cudaGraphExec_t ex = nullptr;
     const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
     if (e != cudaSuccess) {

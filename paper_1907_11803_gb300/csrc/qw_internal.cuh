@@ -101,6 +101,20 @@ struct IndexView {
     const int32_t *bm_nb;
     const int32_t *bm_lvl;
     const int32_t *bm_J;
+    // per projection i, bid_prefix[prefix_off[i] + b] = data objects with bid < b,
+    // b = 0 .. span_i + 1 (built with the bitmaps; entries scanned per range)
+    const int64_t *bid_prefix;
+    const int64_t *prefix_off;
+};
+
+// Entries-scanned statistics from the bid prefix counts (bitmap path), for
+// the decision kernel; prefix == null: the level kernel accumulated them.
+struct ScanStats {
+    const int64_t *prefix = nullptr;
+    const int64_t *off = nullptr;
+    const int32_t *span = nullptr;
+    int m = 0;
+    int cgrow = 2;
 };
 
 // Most levels a bitmap table describes per projection (c >= 2, bids < 2^31).
@@ -136,7 +150,17 @@ struct QueryState {
     unsigned long long *level_passes = nullptr;  // profile mode: (query, level) passes run, else null
     uint4 *cbits = nullptr;           // bitmap path: 2 (level parity) x nb x nT candidate bitmaps
     int64_t cb_par = 0;         // uint4 per parity (batch capacity x nT x kBmUint4)
+    // bitmap path: per (level parity, query, tile) the candidates in ascending
+    // in-tile id, (count << 16) | id, up to kListCap of them, and their number
+    uint32_t *clist = nullptr;
+    int32_t *clist_n = nullptr;
+    int64_t cl_par = 0;         // entries of clist per parity (batch capacity x nT x kListCap)
+    int64_t cln_par = 0;        // entries of clist_n per parity (batch capacity x nT)
 };
+
+// Candidates of one (query, tile) kept in list form by the bitmap level
+// kernels; tiles with more fall back to recounting in the emit kernel.
+constexpr int kListCap = 512;
 
 // Level of a loop that runs on the device (graph mode): the level kernels
 // read level, R and R/c from here, and the loop-control kernel advances it.
@@ -148,6 +172,8 @@ struct LoopCtl {
     unsigned long long iters;     // level passes run, summed over the call's batches
     unsigned long long fb_total;  // learned start: queries recomputed, summed over batches
     unsigned long long skipped_total;  // learned start: levels skipped, summed over batches
+    int32_t min_start;            // smallest first level of the batch's queries
+    uint32_t active;              // queries still running or not yet started after a level
 };
 
 qw_status launch_query_setup(const IndexView &ix, const int32_t *HQ, int nb, QueryState &st,
@@ -156,7 +182,7 @@ qw_status launch_level(const IndexView &ix, int nb, int level, int64_t R, int64_
                        int cgrow, QueryState &st, cudaStream_t s, const LoopCtl *ctl = nullptr);
 qw_status launch_fallback(int nb, QueryState &st, cudaStream_t s);
 qw_status launch_decide(int nb, int level, int64_t R, int cap, QueryState &st, cudaStream_t s,
-                        const LoopCtl *ctl = nullptr);
+                        LoopCtl *ctl = nullptr, const ScanStats &ss = ScanStats());
 // Bitmap path (qw_bitmap.cu).
 struct BitmapLayout {
     std::vector<int64_t> base;   // per projection, first bitmap
@@ -167,15 +193,21 @@ struct BitmapLayout {
 };
 qw_status bitmap_layout(const std::vector<int32_t> &span, int nT, int c, BitmapLayout *out);
 qw_status launch_bitmap_build(const IndexView &ix, int c, int maxJ, uint4 *bm, cudaStream_t s);
+qw_status launch_bid_prefix(const IndexView &ix, int64_t *prefix, const int64_t *off,
+                            cudaStream_t s);
+ScanStats scan_stats_of(const IndexView &ix, int c);
+// tma: stage the bitmaps with TMA bulk copies in a persistent kernel (else
+// plain loads, one CTA per (tile, query)); err bit 4: a staged-copy wait gave up.
 qw_status launch_bm_level(const IndexView &ix, int nb, int level, int64_t R, int64_t Rp, int l,
-                          int cgrow, QueryState &st, cudaStream_t s, const LoopCtl *ctl = nullptr);
+                          int cgrow, QueryState &st, int *err, bool tma, cudaStream_t s,
+                          const LoopCtl *ctl = nullptr);
 qw_status launch_bm_collect(const IndexView &ix, int nb, int l, int cap, QueryState &st,
                             int64_t *stats_out, cudaStream_t s);
 qw_status launch_select_plan(const IndexView &ix, int nb, int l, int cap, QueryState &st,
                              int64_t *stats_out, cudaStream_t s);
 
 // Device-driven loop control (qw_graph.cu builds the graphs that use them).
-qw_status launch_loop_init(LoopCtl *ctl, cudaStream_t s);
+qw_status launch_loop_init(LoopCtl *ctl, const QueryState &st, int nb, int cgrow, cudaStream_t s);
 qw_status launch_loop_ctl(LoopCtl *ctl, const unsigned long long *max_top, int cgrow,
                           cudaGraphConditionalHandle h, int *err, cudaStream_t s);
 qw_status launch_fallback_graph(int nb, QueryState &st, LoopCtl *ctl,
@@ -186,8 +218,8 @@ struct LevelGraphCache;
 LevelGraphCache *level_graph_cache_new();
 void level_graph_cache_free(LevelGraphCache *c);
 qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l, int cgrow,
-                          int cap, bool learned, bool bitmap, QueryState &st, LoopCtl *ctl,
-                          int *err, cudaStream_t s);
+                          int cap, bool learned, bool bitmap, bool tma, QueryState &st,
+                          LoopCtl *ctl, int *err, cudaStream_t s);
 qw_status launch_collect(const IndexView &ix, int nb, int l, int cap, QueryState &st,
                          int64_t *stats_out, cudaStream_t s);
 bool cluster_path_fits(const IndexView &ix, int *cluster_size, int *tiles_per_cta);

@@ -24,6 +24,7 @@
 #include "qw_scan.cuh"
 
 #include <algorithm>
+#include <climits>
 
 namespace qw {
 namespace {
@@ -271,21 +272,63 @@ __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int lev
     }
 }
 
-__global__ void decide_kernel(int nb, int level, int64_t R, int cap, QueryState st,
-                              const LoopCtl *ctl)
+// Entries of projection i's data with bid in the level-R range of g.
+__device__ __forceinline__ int64_t range_entries(const ScanStats &ss, int i, int64_t g, int64_t R)
 {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t sp1 = (int64_t)ss.span[i] + 1;
+    const int64_t lo = floordiv64(g, R) * R;
+    const int64_t A = clamp64(lo, 0, sp1), B = clamp64(lo + R, 0, sp1);
+    const int64_t *P = ss.prefix + ss.off[i];
+    return P[B] - P[A];
+}
+
+// One warp per query: the lanes add the entries-scanned statistics over the
+// projections (bitmap path), lane 0 takes the decision.
+__global__ void decide_kernel(int nb, int level, int64_t R, int cap, QueryState st,
+                              LoopCtl *ctl, ScanStats ss)
+{
+    const int q = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (q >= nb || !st.active[q]) return;
     if (ctl) {
         level = ctl->level;
         R = ctl->R;
     }
-    if (level < st.start[q]) return;
+    if (level < st.start[q]) {
+        // not started yet: the device-driven loop must go on
+        if (ctl && lane == 0) atomicAdd(&ctl->active, 1u);
+        return;
+    }
+    const bool first = level == st.start[q];
+    int64_t sl = 0, skipped = 0;
+    if (ss.prefix) {
+        // the same sums as the level kernel's, from the bid prefix counts: this
+        // level's ranges, and at a learned first level > 0 the ranges of the
+        // levels it skipped
+        for (int i = lane; i < ss.m; i += 32) {
+            const int64_t g = st.g[(int64_t)q * ss.m + i];
+            sl += range_entries(ss, i, g, R);
+            if (first && level > 0) {
+                int64_t Rs = R;
+                for (int L2 = level - 1; L2 >= 0; --L2) {
+                    Rs /= ss.cgrow;
+                    skipped += range_entries(ss, i, g, Rs);
+                }
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sl += __shfl_down_sync(0xffffffffu, sl, off);
+            skipped += __shfl_down_sync(0xffffffffu, skipped, off);
+        }
+    }
+    if (lane != 0) return;
     if (st.level_passes) atomicAdd(st.level_passes, 1ull);
+    if (!ss.prefix) sl = st.scan_level[q];
     const int32_t before = st.ncand[q];  // |C_R| of the previous level
     const int32_t nc = st.cross[q];      // |C_R| of this level, summed over tiles
     st.cross[q] = 0;
-    const int64_t sl = st.scan_level[q];
+    st.scan_full[q] += skipped;
     st.scan_level[q] = 0;
     st.scan_last[q] = sl;
     st.scan_full[q] += sl;
@@ -293,7 +336,7 @@ __global__ void decide_kernel(int nb, int level, int64_t R, int cap, QueryState 
     st.finalR[q] = R;
     const bool enough = nc >= cap;        // the k + v bound (Section 3.1)
     const bool past = R > st.top[q];      // no further level can change C_R
-    if ((enough || past) && level == st.start[q] && level > 0) {
+    if ((enough || past) && first && level > 0) {
         // stopped at a learned first level: the previous level is unknown,
         // so the query is answered again from level 0
         st.fb[q] = 1;
@@ -304,18 +347,43 @@ __global__ void decide_kernel(int nb, int level, int64_t R, int cap, QueryState 
         st.term[q] = enough ? 2 : 3;
         st.active[q] = 0;
         st.nprev[q] = before;
+    } else if (ctl) {
+        atomicAdd(&ctl->active, 1u);
     }
     st.ncand[q] = nc;
 }
 
 // Graph mode: the level loop runs on the device.  The first pass starts at
-// level 0 with R = 1.
-__global__ void loop_init_kernel(LoopCtl *ctl)
+// the smallest first level of the batch (0 unless every query has a learned
+// start above it): levels below it would do no work.
+__global__ void loop_min_start_kernel(LoopCtl *ctl, QueryState st, int nb)
 {
-    ctl->level = 0;
-    ctl->R = 1;
-    ctl->Rp = 1;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    int s = q < nb ? st.start[q] : INT_MAX;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s = min(s, __shfl_down_sync(0xffffffffu, s, off));
+    if ((threadIdx.x & 31) == 0 && s != INT_MAX) atomicMin(&ctl->min_start, s);
+}
+
+__global__ void loop_reset_kernel(LoopCtl *ctl)
+{
+    ctl->min_start = INT_MAX;
+    ctl->active = 0;
+}
+
+__global__ void loop_init_kernel(LoopCtl *ctl, int cgrow)
+{
+    const int L = ctl->min_start == INT_MAX ? 0 : ctl->min_start;
+    int64_t R = 1, Rp = 1;
+    for (int j = 0; j < L; ++j) {
+        Rp = R;
+        R *= cgrow;
+    }
+    ctl->level = L;
+    ctl->R = R;
+    ctl->Rp = Rp;
     ctl->pass = 0;
+    ctl->active = 0;
 }
 
 // After a level's decision: stop once R exceeds every query's last useful
@@ -326,7 +394,9 @@ __global__ void loop_ctl_kernel(LoopCtl *ctl, const unsigned long long *max_top,
                                 cudaGraphConditionalHandle h, int *err)
 {
     const int64_t R = ctl->R;
-    bool more = (unsigned long long)R <= *max_top;
+    // stop once R exceeds every useful radius, or no query is left to run
+    bool more = (unsigned long long)R <= *max_top && ctl->active > 0;
+    ctl->active = 0;
     ctl->iters += 1;
     if (more && ctl->level > 62) {
         atomicOr(err, 8);
@@ -349,6 +419,7 @@ __global__ void second_pass_kernel(QueryState st, LoopCtl *ctl, cudaGraphConditi
     ctl->R = 1;
     ctl->Rp = 1;
     ctl->pass = 1;
+    ctl->active = 0;
     ctl->fb_total += st.fb_count[0];
     ctl->skipped_total += st.fb_count[1];
     cudaGraphSetConditional(h, st.fb_count[0] > 0 ? 1u : 0u);
@@ -607,9 +678,13 @@ qw_status launch_level(const IndexView &ix, int nb, int level, int64_t R, int64_
     return QW_OK;
 }
 
-qw_status launch_loop_init(LoopCtl *ctl, cudaStream_t s)
+qw_status launch_loop_init(LoopCtl *ctl, const QueryState &st, int nb, int cgrow, cudaStream_t s)
 {
-    loop_init_kernel<<<1, 1, 0, s>>>(ctl);
+    loop_reset_kernel<<<1, 1, 0, s>>>(ctl);
+    QW_CUDA_TRY(cudaGetLastError());
+    loop_min_start_kernel<<<(nb + 255) / 256, 256, 0, s>>>(ctl, st, nb);
+    QW_CUDA_TRY(cudaGetLastError());
+    loop_init_kernel<<<1, 1, 0, s>>>(ctl, cgrow);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }
@@ -640,9 +715,10 @@ qw_status launch_fallback(int nb, QueryState &st, cudaStream_t s)
 }
 
 qw_status launch_decide(int nb, int level, int64_t R, int cap, QueryState &st, cudaStream_t s,
-                        const LoopCtl *ctl)
+                        LoopCtl *ctl, const ScanStats &ss)
 {
-    decide_kernel<<<(nb + 127) / 128, 128, 0, s>>>(nb, level, R, cap, st, ctl);
+    decide_kernel<<<(unsigned)(((int64_t)nb * 32 + 127) / 128), 128, 0, s>>>(nb, level, R, cap, st,
+                                                                            ctl, ss);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }

@@ -82,8 +82,9 @@ def test_learned_start_same_results_fewer_levels(qwlib, cuda):
     assert prof3["start_levels_skipped"] == prof["start_levels_skipped"]
     assert prof3["start_fallbacks"] == prof["start_fallbacks"]
     # bitmap path, host loop and graph mode
-    for graph in (False, True):
-        ids5, d5, st5 = index.query(Q, 20, stats=True, start="learned", path="bitmap", graph=graph)
+    for graph, loads in ((False, "tma"), (True, "tma"), (False, "direct")):
+        ids5, d5, st5 = index.query(Q, 20, stats=True, start="learned", path="bitmap", graph=graph,
+                                    loads=loads)
         prof5 = index.profile(reset=True)
         assert torch.equal(ids0, ids5) and torch.equal(d0, d5) and torch.equal(st0, st5)
         assert prof5["start_levels_skipped"] == prof["start_levels_skipped"]

@@ -14,8 +14,10 @@ pytestmark = pytest.mark.gpu
 DIST_RTOL = 1e-5
 TILE = 32768
 # "graph": the level path with its level loop run as a CUDA graph; "bitmap":
-# counts from the index's level bitmaps ("bitmap_graph": the same in graph mode)
-PATHS = pytest.mark.parametrize("path", ["levels", "cluster", "graph", "bitmap", "bitmap_graph"])
+# counts from the index's level bitmaps staged by TMA ("bitmap_graph": the same
+# in graph mode; "bitmap_direct": plain loads, one CTA per tile and query)
+PATHS = pytest.mark.parametrize("path", ["levels", "cluster", "graph", "bitmap", "bitmap_graph",
+                                         "bitmap_direct"])
 
 
 def _t(x, dev):
@@ -64,10 +66,12 @@ def _gpu_workload(qw, dev, X, Q, A, b, *, w, k, v, l, c=2, batch=0, host=False, 
     index = qw.Index(Xd, Ad, bd, w=w, c=c, v=v, l=l, shadow_bf16=(rerank == "bf16"),
                      bitmaps=path.startswith("bitmap"))
     graph = path in ("graph", "bitmap_graph")
-    path = {"graph": "levels", "bitmap_graph": "bitmap"}.get(path, path)
+    loads = "direct" if path == "bitmap_direct" else "tma"
+    path = {"graph": "levels", "bitmap_graph": "bitmap", "bitmap_direct": "bitmap"}.get(path, path)
     ids, dists, st = index.query(Qd, k, batch=batch, stats=True, path=path, order=order,
-                                 rerank=rerank, graph=graph)
-    cid, ccol, st2 = index.candidates(Qd, k, batch=batch, path=path, order=order, graph=graph)
+                                 rerank=rerank, graph=graph, loads=loads)
+    cid, ccol, st2 = index.candidates(Qd, k, batch=batch, path=path, order=order, graph=graph,
+                                      loads=loads)
     torch.cuda.synchronize()
     out = dict(ids=ids.cpu().numpy(), dists=dists.cpu().numpy(), stats=st.cpu().numpy(),
                cid=cid.cpu().numpy(), ccol=ccol.cpu().numpy(), stats2=st2.cpu().numpy(),
@@ -310,34 +314,49 @@ def test_argument_errors(qwlib, cuda):
 @pytest.mark.slow
 def test_full_size_sampled(orc, qwlib, cuda):
     """The benchmarked workload (1M x 128, 64 projections, 10,000 queries,
-    k = 100) run whole on the GPU in the benchmark's launch configuration;
-    the oracle recomputes a seeded sample of queries one by one."""
+    k = 100, v = 700, l = 43) run whole on the GPU in the benchmark's launch
+    configuration (bitmap path, signature order, learned first levels, graph
+    mode) and in the plain one; the oracle recomputes a seeded sample of
+    queries one by one."""
     import torch
-    wl = workloads.make_workload("mix1m_d128", seed=0)
+    wl = workloads.make_workload("mix1m_d128", seed=0, n_train=8_000)
     s = wl.spec
-    l = orc.threshold(s.m, s.w, s.c, s.n, s.v)
-    index = qwlib.Index(_t(wl.X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=s.w, c=s.c, v=s.v, l=l)
+    v, l = 700, 43
+    index = qwlib.Index(_t(wl.X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=s.w, c=s.c, v=v, l=l,
+                        bitmaps=True)
     Qd = _t(wl.Q, cuda)
-    ids, dists, st = index.query(Qd, s.k, stats=True)
+    # start model trained on earlier queries of the workload, as the benchmark does
+    Qt = _t(wl.Q_train, cuda)
+    _, _, stt = index.query(Qt, s.k, stats=True, path="bitmap")
+    labels = (stt[:, 0] - 1).clamp(0, 15).to(torch.int32).contiguous()
+    F = index.features(Qt)
+    mlp = qwlib.Mlp(F.shape[1], 256, 16)
+    mlp.set_params(qwlib.mlp_init(F.shape[1], 256, 16, seed=5))
+    mlp.train(F, labels, epochs=10, batch=512, lr=1e-3)
+    index.set_start_model(mlp, eps=0.02)
+    ids, dists, st = index.query(Qd, s.k, stats=True, path="bitmap", order="signature",
+                                 start="learned", graph=True, loads="direct")
+    prof = index.profile(reset=True)
     ids2, dists2, st2 = index.query(Qd, s.k, stats=True, path="levels", order="given")
     torch.cuda.synchronize()
     ids, dists, st = ids.cpu().numpy(), dists.cpu().numpy(), st.cpu().numpy()
-    # the two execution paths and the two query orders agree on every query
+    # the two configurations agree on every query
     assert np.array_equal(ids, ids2.cpu().numpy())
     assert np.array_equal(st, st2.cpu().numpy())
     assert np.array_equal(dists, dists2.cpu().numpy())
+    assert prof["start_levels_skipped"] > 0
     H = orc.hash(wl.X, wl.A, wl.b, s.w)
     oidx = orc.build_index(H, sorted_arrays=True)
-    info = index.info
-    assert info.l == l
+    assert index.info.l == l
     sample = np.random.default_rng(123).choice(s.nq, size=12, replace=False)
     sample.sort()
     HQ = orc.hash(wl.Q[sample], wl.A, wl.b, s.w)
-    ref = orc.query(wl.X, oidx, wl.Q[sample], HQ, k=s.k, v=s.v, l=l, c=s.c)
+    ref = orc.query(wl.X, oidx, wl.Q[sample], HQ, k=s.k, v=v, l=l, c=s.c)
     _check_results(ids[sample], dists[sample], ref["ids"], ref["dists"])
     assert np.array_equal(st[sample], ref["stats"])
     # properties that hold for every query
     assert np.all((st[:, 4] == 2) | (st[:, 4] == 3))
-    assert np.all(st[:, 3] <= s.k + s.v)
+    assert np.all(st[:, 3] <= s.k + v)
     assert np.all(np.diff(dists, axis=1)[np.isfinite(dists[:, 1:])] >= 0)
     index.free()
+    mlp.free()
