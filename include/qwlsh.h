@@ -184,6 +184,9 @@ typedef struct {
     int64_t start_fallbacks;       /* queries recomputed from R = 1 (always counted) */
     int64_t level_passes;          /* (query, level) pairs counted by the level paths
                                       (profile mode) */
+    int64_t bitmap_fallbacks;      /* QW_PATH_BITMAP queries whose candidates overflowed its
+                                      fixed lists and were answered by the level path
+                                      (always counted; same results) */
 } qw_profile;
 
 typedef struct {

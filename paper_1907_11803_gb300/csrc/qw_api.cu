@@ -70,7 +70,7 @@ struct qw_index {
     DevBuf X, A, b, o, span, lid, dir_bid, dir_off, dir_start, dir_cnt, Xb, xnorm;
     bool shadow = false;
     bool bitmaps = false;               // level bitmaps for QW_PATH_BITMAP
-    DevBuf bm, bm_base, bm_nb, bm_lvl, bm_J, bid_prefix, prefix_off;
+    DevBuf bm, bm_base, bm_nb, bm_lvl, bm_J, bid_prefix, prefix_off, perm, bm_sum;
     int bm_maxJ = 0;
     float xs = 1.0f;                 // 1 / RMS coordinate of the data (start-model features)
     qw_mlp *start_model = nullptr;   // not owned
@@ -82,7 +82,7 @@ struct qw_index {
     DevBuf w_feat;
     // workspace for queries (grow-only)
     DevBuf w_q, w_hq, w_state, w_counters, w_cand, w_out, w_err, w_order, w_qb, w_ob, w_cbits,
-        w_clist;
+        w_clist, w_bmsel, w_ovf, w_bmwork;
     int64_t device_bytes = 0;
     qw_profile prof{};
     std::vector<cudaEvent_t> event_pool;
@@ -108,6 +108,8 @@ struct qw_index {
         v.bm_lvl = bm_lvl.as<int32_t>();
         v.bm_J = bm_J.as<int32_t>();
         v.bid_prefix = bid_prefix.as<int64_t>();
+        v.perm = perm.as<int32_t>();
+        v.bm_sum = bm_sum.as<uint32_t>();
         v.prefix_off = prefix_off.as<int64_t>();
         return v;
     }
@@ -366,7 +368,31 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
         QW_CUDA_TRY(cudaMemsetAsync(ix->bid_prefix.p, 0, ix->bid_prefix.bytes, s));
         QW_CUDA_TRY(cudaMemcpyAsync(ix->prefix_off.p, poff.data(), m * sizeof(int64_t),
                                     cudaMemcpyHostToDevice, s));
-        QW_TRY(launch_bitmap_build(ix->view(), ix->c, ix->bm_maxJ, ix->bm.as<uint4>(), s));
+        // internal (locality) order of the bitmaps
+        std::vector<int32_t> h_perm;
+        {
+            std::vector<float> hX, hA;
+            try {
+                hX.resize((size_t)n * d);
+                hA.resize((size_t)m * d);
+            } catch (const std::bad_alloc &) {
+                set_error("qw_build_index: out of host memory for the locality order");
+                return QW_ERR_OOM;
+            }
+            QW_CUDA_TRY(cudaMemcpyAsync(hX.data(), ix->X.p, hX.size() * sizeof(float),
+                                        cudaMemcpyDeviceToHost, s));
+            QW_CUDA_TRY(cudaMemcpyAsync(hA.data(), ix->A.p, hA.size() * sizeof(float),
+                                        cudaMemcpyDeviceToHost, s));
+            QW_CUDA_TRY(cudaStreamSynchronize(s));
+            QW_TRY(locality_order(hX.data(), n, d, hA.data(), m, h_perm));
+        }
+        QW_TRY(ix->perm.ensure((size_t)n * sizeof(int32_t)));
+        QW_CUDA_TRY(cudaMemcpyAsync(ix->perm.p, h_perm.data(), (size_t)n * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, s));
+        QW_TRY(ix->bm_sum.ensure((size_t)lay.total * (kBmUint4 / 32) * sizeof(uint32_t)));
+        QW_TRY(launch_bitmap_build(ix->view(), ix->c, ix->bm_maxJ, Ht.as<int32_t>(),
+                                   ix->bm.as<uint4>(), ix->bm_sum.as<uint32_t>(), lay.total, s));
+        QW_CUDA_TRY(cudaStreamSynchronize(s));  // the host order must outlive its upload
         QW_TRY(launch_bid_prefix(ix->view(), ix->bid_prefix.as<int64_t>(),
                                  ix->prefix_off.as<int64_t>(), s));
     }
@@ -381,7 +407,7 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
                                  ix->dir_off.bytes + ix->dir_start.bytes + ix->dir_cnt.bytes +
                                  ix->bm.bytes + ix->bm_base.bytes + ix->bm_nb.bytes +
                                  ix->bm_lvl.bytes + ix->bm_J.bytes + ix->bid_prefix.bytes +
-                                 ix->prefix_off.bytes);
+                                 ix->prefix_off.bytes + ix->perm.bytes + ix->bm_sum.bytes);
     return QW_OK;
 }
 
@@ -425,6 +451,46 @@ qw_status qw_build_index(const float *data, int64_t n, int32_t d, const float *A
         return st;
     }
     *out = ix;
+    return QW_OK;
+}
+
+static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
+                          const qw_query_params *qp, int64_t *ids, float *dists, int64_t *stats,
+                          int64_t *cand_ids, int32_t *cand_col, int32_t mem, cudaStream_t s);
+
+// Answer the workload queries listed in `list` (device, n of them) again on
+// the level path and write their rows of the outputs.  Used for the rare
+// queries whose candidates overflow the bitmap path's fixed buffers.
+static qw_status level_path_rerun(qw_index *ix, const float *Qall, const int32_t *HQall,
+                                  const int32_t *list, int n, int k, int cap, int64_t *f_ids,
+                                  float *f_dists, int64_t *f_stats, int64_t *f_cids,
+                                  int32_t *f_ccol, cudaStream_t s)
+{
+    const int d = ix->d, m = ix->m;
+    DevBuf q_in, hq_in, o_ids, o_dists, o_stats, o_cids, o_ccol;
+    QW_TRY(q_in.ensure((size_t)n * d * sizeof(float)));
+    QW_TRY(hq_in.ensure((size_t)n * m * sizeof(int32_t)));
+    QW_TRY(launch_gather(Qall, HQall, list, 0, n, d, m, q_in.as<float>(), hq_in.as<int32_t>(), s));
+    if (f_ids) {
+        QW_TRY(o_ids.ensure((size_t)n * k * sizeof(int64_t)));
+        QW_TRY(o_dists.ensure((size_t)n * k * sizeof(float)));
+    }
+    if (f_stats) QW_TRY(o_stats.ensure((size_t)n * QW_NSTAT * sizeof(int64_t)));
+    if (f_cids) QW_TRY(o_cids.ensure((size_t)n * cap * sizeof(int64_t)));
+    if (f_ccol) QW_TRY(o_ccol.ensure((size_t)n * cap * sizeof(int32_t)));
+    qw_query_params p{};
+    p.path = QW_PATH_LEVELS;
+    p.order = QW_ORDER_GIVEN;
+    const qw_profile saved = ix->prof;
+    QW_TRY(run_impl(ix, q_in.as<float>(), n, k, &p, o_ids.as<int64_t>(), o_dists.as<float>(),
+                    o_stats.as<int64_t>(), o_cids.as<int64_t>(), o_ccol.as<int32_t>(),
+                    QW_MEM_DEVICE, s));
+    ix->prof = saved;
+    ix->prof.bitmap_fallbacks += n;
+    QW_TRY(launch_scatter(list, 0, n, k, cap, o_ids.as<int64_t>(), o_dists.as<float>(),
+                          o_stats.as<int64_t>(), o_cids.as<int64_t>(), o_ccol.as<int32_t>(), f_ids,
+                          f_dists, f_stats, f_cids, f_ccol, s));
+    QW_CUDA_TRY(cudaStreamSynchronize(s));  // the temporaries are freed on return
     return QW_OK;
 }
 
@@ -525,7 +591,9 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     const bool tma_loads = !qp || qp->bitmap_loads == QW_LOADS_TMA;
     // bitmap path, per query: two levels of (tile) candidate bitmaps and lists
     const int64_t cb_bytes = (int64_t)ix->nT * kBmUint4 * (int64_t)sizeof(uint4) * 2;
-    const int64_t cl_bytes = (int64_t)ix->nT * (kListCap + 1) * (int64_t)sizeof(uint32_t) * 2;
+    // (per query: two levels of tile candidate counts and candidate lists)
+    const int64_t cl_bytes = (int64_t)ix->nT * (int64_t)sizeof(int32_t) * 2 +
+                             ((int64_t)kQCap * (int64_t)sizeof(uint64_t) + 4) * 2;
     int64_t B = qp && qp->batch > 0 ? qp->batch : 0;
     if (B == 0 && ix->tuned && ix->tuned_batch > 0 && !use_cluster &&
         (path == QW_PATH_AUTO || path == ix->tuned_path))
@@ -538,6 +606,8 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     }
     B = std::min<int64_t>(B, std::max<int64_t>(nq, 1));
     B = std::min<int64_t>(B, 65535);
+    // bitmap path: (query, tile) item slots are numbered in 23 bits
+    if (use_bitmap) B = std::max<int64_t>(1, std::min<int64_t>(B, ((int64_t)1 << 23) / ix->nT));
     auto up16 = [](size_t x) { return (x + 15) / 16 * 16; };
 
     // ---- workspace
@@ -546,7 +616,13 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     if (!use_cluster && !use_bitmap) QW_TRY(ix->w_counters.ensure((size_t)B * wpq_bytes));
     if (use_bitmap) {
         QW_TRY(ix->w_cbits.ensure((size_t)B * cb_bytes));
-        QW_TRY(ix->w_clist.ensure((size_t)B * cl_bytes));
+        QW_TRY(ix->w_clist.ensure((size_t)B * cl_bytes + 64));
+        QW_TRY(ix->w_bmsel.ensure((size_t)B * (1 + kEqCap) * sizeof(int32_t)));
+        // two-pass level: one slot per (query, tile), one work entry per group
+        const size_t items = (size_t)B * ix->nT;
+        QW_TRY(ix->w_bmwork.ensure(16 + items * (sizeof(int2) + (size_t)m * sizeof(int64_t)) +
+                                   items * kBmUint4 * sizeof(int32_t)));
+        QW_TRY(ix->w_ovf.ensure(((size_t)nq + 1) * sizeof(int32_t)));
     }
     QW_TRY(ix->w_cand.ensure((size_t)B * cap * 2 * sizeof(int32_t)));
     const size_t plan_ints = (size_t)B * ix->nT * (kHistBins + 3) + (size_t)B * 2;
@@ -636,10 +712,30 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     st.cbits = ix->w_cbits.as<uint4>();
     st.level_passes = nullptr;
     st.cb_par = B * ix->nT * kBmUint4;
-    st.cl_par = B * ix->nT * kListCap;
-    st.cln_par = B * ix->nT;
-    st.clist = ix->w_clist.as<uint32_t>();
-    st.clist_n = st.clist ? reinterpret_cast<int32_t *>(st.clist + 2 * st.cl_par) : nullptr;
+    if (use_bitmap) {
+        // w_clist: qbuf (2 x B x kQCap), then clist_n (2 x B x nT), then qbuf_n (2 x B)
+        st.qb_par = B * (int64_t)kQCap;
+        st.qbuf = ix->w_clist.as<uint64_t>();
+        st.cln_par = B * ix->nT;
+        st.clist_n = reinterpret_cast<int32_t *>(st.qbuf + 2 * st.qb_par);
+        st.qbn_par = B;
+        st.qbuf_n = st.clist_n + 2 * st.cln_par;
+        st.bm_ovf = ix->w_bmsel.as<int32_t>();
+        st.eqbuf = st.bm_ovf + B;
+        const int64_t items = B * (int64_t)ix->nT;
+        char *wp = ix->w_bmwork.as<char>();
+        st.bm_nitems = reinterpret_cast<int32_t *>(wp);
+        st.bm_nwork = st.bm_nitems + 1;
+        st.bm_item_qt = reinterpret_cast<int2 *>(wp + 16);
+        st.bm_item_bi = reinterpret_cast<int64_t *>(wp + 16 + items * sizeof(int2));
+        st.bm_work = reinterpret_cast<int32_t *>(wp + 16 + items * sizeof(int2) +
+                                                 items * m * sizeof(int64_t));
+        st.bm_item_cap = (int32_t)std::min<int64_t>(items, (int64_t)1 << 23);
+        st.bm_work_cap = (int32_t)std::min<int64_t>(items * kBmUint4, INT32_MAX);
+    }
+    int32_t *ovf_count = use_bitmap ? ix->w_ovf.as<int32_t>() : nullptr;
+    int32_t *ovf_list = use_bitmap ? ovf_count + 1 : nullptr;
+    if (use_bitmap) QW_CUDA_TRY(cudaMemsetAsync(ovf_count, 0, sizeof(int32_t), s));
     st.cand = ix->w_cand.as<int32_t>();
     st.cand_col = st.cand + (size_t)B * cap;
     int *err = ix->w_err.as<int>();
@@ -747,10 +843,11 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             if (learned) {
                 float *F = ix->w_feat.as<float>();
                 float *prob = F + (size_t)B * (d + m);
-                QW_TRY(tm.run(QW_K_START, 5, [&] {
-                    QW_TRY(launch_features(Qb, HQb, nb, view, ix->xs, F, s));
-                    QW_TRY(mlp_predict_dev(ix->start_model, F, nb, prob, s));
-                    return launch_start_levels(prob, nb, nclass, ix->start_eps, st.start, s);
+                (void)F;
+                (void)prob;
+                QW_TRY(tm.run(QW_K_START, 1, [&] {
+                    return launch_start_model(ix->start_model, Qb, HQb, nb, view, ix->xs,
+                                              ix->start_eps, st.start, s);
                 }));
                 QW_CUDA_TRY(cudaMemsetAsync(st.fb_count, 0, 16, s));
             }
@@ -763,10 +860,13 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                 QW_TRY(host_level_loop(ix, tm, view, nb, cap, learned, use_bitmap, tma_loads, err,
                                        st, s));
             }
-            QW_TRY(tm.run(QW_K_SELECT, 2, [&] {
+            QW_TRY(tm.run(QW_K_SELECT, use_bitmap ? 3 : 2, [&] {
                 return use_bitmap ? launch_bm_collect(view, nb, ix->l, cap, st, stats_b, s)
                                   : launch_collect(view, nb, ix->l, cap, st, stats_b, s);
             }));
+            if (use_bitmap)
+                QW_TRY(launch_bm_overflow_list(st, nb, order ? perm : nullptr, b0, ovf_list,
+                                               ovf_count, s));
         }
         if (want_cand)
             QW_TRY(tm.run(QW_K_SELECT, 1, [&] { return launch_candidates_out(st, nb, cap, cids_b, ccol_b, s); }));
@@ -818,6 +918,18 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             ix->prof.start_fallbacks += (int64_t)h_ctl.fb_total;
             ix->prof.start_levels_skipped += (int64_t)h_ctl.skipped_total;
         }
+    }
+    if (use_bitmap) {
+        // queries whose candidate lists overflowed the bitmap path's buffers:
+        // answered again by the level path (same results by construction);
+        // after every read of this call's flags and loop state, which the
+        // level path's call reuses
+        int32_t n_ovf = 0;
+        QW_CUDA_TRY(cudaMemcpyAsync(&n_ovf, ovf_count, sizeof(n_ovf), cudaMemcpyDeviceToHost, s));
+        QW_CUDA_TRY(cudaStreamSynchronize(s));
+        if (n_ovf > 0)
+            QW_TRY(level_path_rerun(ix, Qall, HQall, ovf_list, n_ovf, k, cap, f_ids, f_dists,
+                                    f_stats, f_cids, f_ccol, s));
     }
     if (host) {
         if (want_ids) {
@@ -1016,7 +1128,8 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
             cur_ms = bms;
             cur_slot = bslot;
             const int64_t cb_b = (int64_t)ix->nT * kBmUint4 * (int64_t)sizeof(uint4) * 2 +
-                                 (int64_t)ix->nT * (kListCap + 1) * (int64_t)sizeof(uint32_t) * 2;
+                                 (int64_t)ix->nT * (int64_t)sizeof(int32_t) * 2 +
+                                 ((int64_t)kQCap * (int64_t)sizeof(uint64_t) + 4) * 2;
             const int64_t bdef = std::min<int64_t>(
                 std::min<int64_t>(std::max<int64_t>(1, ((int64_t)2 << 30) / cb_b), nq), 65535);
             const int64_t bc[2] = {bdef / 16, bdef / 4};
@@ -1202,7 +1315,8 @@ void qw_index_free(qw_index *ix)
     for (DevBuf *bb : bufs) bb->release();
     DevBuf *bmb[] = {&ix->bm,  &ix->bm_base,    &ix->bm_nb,      &ix->bm_lvl,
                      &ix->bm_J, &ix->bid_prefix, &ix->prefix_off, &ix->w_cbits,
-                     &ix->w_clist};
+                     &ix->w_clist, &ix->perm, &ix->bm_sum, &ix->w_bmsel, &ix->w_ovf,
+                     &ix->w_bmwork};
     for (DevBuf *bb : bmb) bb->release();
     for (cudaEvent_t e : ix->event_pool) cudaEventDestroy(e);
     level_graph_cache_free(ix->graphs);

@@ -14,25 +14,37 @@
 // bits (4 KiB).  A query collides with an object on projection i at radius R
 // exactly when the object lies in the bucket beta_i = floor(g_i / R) of the
 // query, so at every level the collision count of each id is the number of
-// the m bitmaps B_i(beta_i) that contain it (Section 3.1).  The kernel loads
-// those m bitmaps of a tile -- coalesced 16-byte loads, no atomics -- and adds
-// them bit-sliced: a carry-save adder tree keeps, per group of 32 ids, the
-// seven bit planes of their counts in registers.  Counts are recomputed from
-// scratch at every level, so nothing is carried between levels except the
-// candidate bitmap (count >= l) of the previous level, which orders the
-// truncation to k + v candidates.  The results -- candidate sets, counts,
-// statistics -- are those of the level path.
+// the m bitmaps B_i(beta_i) that contain it (Section 3.1).  Counts are summed
+// bit-sliced (a carry-save adder tree keeps, per 32 ids, the seven bit planes
+// of their counts in registers) and recomputed from scratch at every level:
+// no atomics per entry and no counters kept between levels.
+//
+// Ids are numbered in a locality order (a two-means tree over the data, leaves
+// of 128 ids): a 128-id group holds nearby points.  Every bitmap carries a
+// 256-bit summary (which groups it touches).  A group touched by fewer than l
+// of the query's m buckets cannot hold a candidate, so a level runs in two
+// passes: a filter on the summaries finds the live groups of every (query,
+// tile), and only those are counted from the bitmaps.  Candidates go to a
+// per-query list with their counts; the k + v bound and the tie rule (smallest
+// original id) are applied per query at the end.  Results -- candidate sets,
+// counts, statistics -- are those of the level path; a query whose candidates
+// overflow the fixed lists is answered by the level path.
 //
 // Storage: per (projection, tile), sum over levels L of (span / c^L + 1)
-// bitmaps, i.e. about (c / (c - 1)) * (span + 1) * 4 KiB.  A level-L bitmap is
-// the OR of its c children at level L - 1; the finest level comes from the
-// tile's sorted entries.
+// bitmaps, i.e. about (c / (c - 1)) * (span + 1) * 4 KiB, plus 32 bytes of
+// summary each.  A level-L bitmap is the OR of its c children at level L - 1;
+// the finest level comes from the data's bucket ids.
 #include "qw_internal.cuh"
 #include "qw_dir.cuh"
 #include "qw_scan.cuh"
 #include "qw_tma.cuh"
 
 #include <algorithm>
+#include <thread>
+#include <cmath>
+#include <atomic>
+#include <new>
+#include <vector>
 
 namespace qw {
 
@@ -80,32 +92,39 @@ namespace {
 
 constexpr int BM_THREADS = kBmUint4;  // one thread per 16 bytes (128 ids) of a tile bitmap
 
-// Level 0: one bitmap per bid present in the tile, from the tile's sorted
-// entries.  Bitmaps of absent bids stay zero (the buffer is cleared first).
-__global__ void __launch_bounds__(BM_THREADS) bm_fill_level0_kernel(IndexView ix, uint4 *bm)
+// Level 0: bit j of bitmap (i, t, 0, bid) for every internal id j of tile t
+// whose object has anchored bucket id bid on projection i.  A warp covers one
+// 32-bit word (32 consecutive internal ids); lanes with equal bids share one
+// atomic OR.  The buffer is cleared first.
+__global__ void __launch_bounds__(BM_THREADS) bm_fill_level0_kernel(IndexView ix,
+                                                                    const int32_t *__restrict__ Ht,
+                                                                    uint4 *bm)
 {
-    __shared__ __align__(16) uint32_t sb[kTile / 32];
     const int t = blockIdx.x, i = blockIdx.y;
-    const int64_t dslot = (int64_t)i * ix.nT + t;
-    const int32_t *ub = ix.dir_bid + ix.dir_start[dslot];
-    const int32_t *uo = ix.dir_off + ix.dir_start[dslot];
-    const int cnt = ix.dir_cnt[dslot];
     const int len = (int)min((int64_t)kTile, ix.n - (int64_t)t * kTile);
-    const uint16_t *seg = ix.lid + dslot * kTile;
-    uint4 *sb4 = reinterpret_cast<uint4 *>(sb);
     const int64_t blk = ix.bm_base[i] + (int64_t)t * ix.bm_nb[i] + ix.bm_lvl[i * kBmLevels + 0];
-    sb4[threadIdx.x] = make_uint4(0, 0, 0, 0);
-    __syncthreads();
-    for (int u = 0; u < cnt; ++u) {
-        const int e0 = uo[u], e1 = (u + 1 < cnt) ? uo[u + 1] : len;
-        for (int e = e0 + threadIdx.x; e < e1; e += BM_THREADS) {
-            const uint32_t id = seg[e];
-            atomicOr(&sb[id >> 5], 1u << (id & 31));
-        }
-        __syncthreads();
-        bm[(blk + ub[u]) * kBmUint4 + threadIdx.x] = sb4[threadIdx.x];
-        sb4[threadIdx.x] = make_uint4(0, 0, 0, 0);
-        __syncthreads();
+    const int32_t oi = ix.o[i];
+    uint32_t *bw = reinterpret_cast<uint32_t *>(bm);
+    const int lane = threadIdx.x & 31;
+    for (int j = threadIdx.x; j < kTile; j += BM_THREADS) {
+        const bool valid = j < len;
+        const int32_t bid =
+            valid ? Ht[(int64_t)i * ix.n + ix.perm[(int64_t)t * kTile + j]] - oi : -1;
+        const uint32_t same = __match_any_sync(0xffffffffu, bid);
+        if (valid && lane == __ffs(same) - 1)
+            atomicOr(&bw[(blk + bid) * (kTile / 32) + (j >> 5)], same);
+    }
+}
+
+// Per bitmap, one bit per 128-id group: the group has at least one id.
+__global__ void __launch_bounds__(BM_THREADS) bm_summary_kernel(const uint4 *__restrict__ bm,
+                                                                int64_t total,
+                                                                uint32_t *__restrict__ sum)
+{
+    for (int64_t b = blockIdx.x; b < total; b += gridDim.x) {
+        const uint4 v = bm[b * kBmUint4 + threadIdx.x];
+        const uint32_t word = __ballot_sync(0xffffffffu, (v.x | v.y | v.z | v.w) != 0);
+        if ((threadIdx.x & 31) == 0) sum[b * (kBmUint4 / 32) + (threadIdx.x >> 5)] = word;
     }
 }
 
@@ -137,24 +156,6 @@ __global__ void __launch_bounds__(BM_THREADS) bm_or_level_kernel(IndexView ix, u
     }
 }
 
-// Bitmap of the level-`level` bucket beta of projection i in tile t, or null
-// when the bucket holds no data (beta below zero or past the span).  Past the
-// last stored level a single bucket (beta == 0) holds every id.
-__device__ __forceinline__ const uint4 *bm_ptr(const IndexView &ix, int i, int t, int level,
-                                               int64_t R, int64_t beta)
-{
-    const int J = ix.bm_J[i];
-    int L = level;
-    if (level > J) {
-        if (beta != 0) return nullptr;
-        L = J;
-    } else if (beta < 0 || beta > (int64_t)ix.span[i] / R) {
-        return nullptr;
-    }
-    const int64_t idx =
-        ix.bm_base[i] + (int64_t)t * ix.bm_nb[i] + ix.bm_lvl[i * kBmLevels + L] + beta;
-    return ix.bm + idx * kBmUint4;
-}
 
 // Full adder on 32 lanes of bits: lo = a ^ b ^ c, hi = majority(a, b, c).
 __device__ __forceinline__ void csa(uint32_t &hi, uint32_t &lo, uint32_t a, uint32_t b, uint32_t c)
@@ -196,25 +197,6 @@ __device__ __forceinline__ void add8(Planes &P, const uint4 (&x)[8])
     }
 }
 
-// Counts of the 128 ids of this thread: the sum of the m bucket bitmaps bp[]
-// (null = empty), padded with empty inputs to a multiple of 8.
-__device__ __forceinline__ void count_planes(Planes &P, const uint4 *const *bp, int m8)
-{
-#pragma unroll
-    for (int k = 0; k < 7; ++k)
-#pragma unroll
-        for (int w = 0; w < 4; ++w) P.s[k][w] = 0;
-#pragma unroll 1
-    for (int g = 0; g < m8; g += 8) {
-        uint4 x[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const uint4 *p = bp[g + u];
-            x[u] = p ? __ldg(p + threadIdx.x) : make_uint4(0, 0, 0, 0);
-        }
-        add8(P, x);
-    }
-}
 
 // Bits of word w whose count is >= l (l in 1..127).
 __device__ __forceinline__ uint32_t count_ge_planes(const Planes &P, int w, int l)
@@ -246,23 +228,8 @@ __device__ __forceinline__ uint32_t word_of(const uint4 &v, int w)
     return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
 }
 
-// Bucket bitmaps of the m projections for (query q, tile t) at one level
-// (threads 0 .. m8 - 1 fill bp; entries m .. m8 - 1 are empty).
-__device__ __forceinline__ void bucket_bitmaps(const IndexView &ix, const QueryState &st, int q,
-                                               int t, int level, int64_t R, const uint4 **bp,
-                                               int m8)
-{
-    const int m = ix.m;
-    if (threadIdx.x < m) {
-        const int i = threadIdx.x;
-        bp[i] = bm_ptr(ix, i, t, level, R, floordiv64(st.g[(int64_t)q * m + i], R));
-    } else if (threadIdx.x < m8) {
-        bp[threadIdx.x] = nullptr;
-    }
-}
 
-// Epilogue shared by both level kernels: the candidate bitmap of the thread's
-// 128 ids, the previous level's, and the tile profile's counts by bin.
+// The candidate bits (count >= l) of the thread's 4 x 32 ids.
 __device__ __forceinline__ uint4 candidates_of(const Planes &P, int l)
 {
     uint4 cand;
@@ -273,12 +240,11 @@ __device__ __forceinline__ uint4 candidates_of(const Planes &P, int l)
     return cand;
 }
 
-// The tile profile's bins (candidates that were not candidates at the
-// previous level, by count) and the candidate list entries of this thread's
-// 128 ids, written in ascending id order from list position pos.
-__device__ __forceinline__ void profile_and_list(const Planes &P, const uint4 &cand,
-                                                 const uint4 &prev, int *hist, uint32_t *list,
-                                                 int pos, int id_base)
+// Append this thread's candidates (128 ids, ascending) to the query's list
+// for the level from position pos: (internal id << 32) | (prev << 8) | count.
+__device__ __forceinline__ void append_candidates(const Planes &P, const uint4 &cand,
+                                                  const uint4 &prev, uint64_t *list, int pos,
+                                                  int64_t id_base)
 {
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
@@ -287,64 +253,186 @@ __device__ __forceinline__ void profile_and_list(const Planes &P, const uint4 &c
         while (x) {
             const int b = __ffs(x) - 1;
             x &= x - 1;
-            const int c = count_of(P, w, b);
-            if (!((pw >> b) & 1u)) atomicAdd(&hist[1 + c], 1);
-            if (pos < kListCap) list[pos] = ((uint32_t)c << 16) | (uint32_t)(id_base + w * 32 + b);
+            if (pos < kQCap)
+                list[pos] = ((uint64_t)(id_base + w * 32 + b) << 32) |
+                            ((uint64_t)((pw >> b) & 1u) << 8) | (uint64_t)count_of(P, w, b);
             ++pos;
         }
     }
 }
 
-// One level for one (tile, query), loads straight from global memory: counts
-// of every id of the tile, the candidate bitmap (count >= l), and the tile's
-// candidate profile (previous-level candidates; the others by count), as the
-// level path produces it.
-__global__ void __launch_bounds__(BM_THREADS, 3) bm_level_kernel(IndexView ix, int level,
-                                                                 int64_t R, int l,
-                                                                 QueryState st, const LoopCtl *ctl)
+// Bitmap number of the level-`level` bucket beta of projection i in tile t,
+// or -1 when the bucket holds no data (beta below zero or past the span).
+// Past the last stored level a single bucket (beta == 0) holds every id.
+__device__ __forceinline__ int64_t bm_index(const IndexView &ix, int i, int t, int level,
+                                            int64_t R, int64_t beta)
 {
-    __shared__ const uint4 *bp[QW_MAX_M + 8];
-    __shared__ int hist[kHistBins];
-    __shared__ int wsum[BM_THREADS / 32];
-    const int t = blockIdx.x;
-    const int q = blockIdx.y;
-    if (!st.active[q]) return;
+    const int J = ix.bm_J[i];
+    int L = level;
+    if (level > J) {
+        if (beta != 0) return -1;
+        L = J;
+    } else if (beta < 0 || beta > (int64_t)ix.span[i] / R) {
+        return -1;
+    }
+    return ix.bm_base[i] + (int64_t)t * ix.bm_nb[i] + ix.bm_lvl[i * kBmLevels + L] + beta;
+}
+
+// ---- the same level in two passes (the bitmap path's default)
+//
+// Pass 1, one warp per (query, tile): only the bucket summaries are read (8
+// words of 32 bits per projection, one bit per 128-id group), and a carry-save
+// sum over the m projections gives every group the number of the query's
+// buckets that touch it.  Groups below l cannot hold a candidate.  A tile
+// without live groups is done (its candidate count is 0); otherwise its dead
+// groups' candidate words are cleared, the item's m bitmap numbers are stored
+// in a slot, and its live groups go to a work list.
+// Pass 2, one thread per live group: the 128-id group's word of each of the
+// m bitmaps, summed into bit planes; the group's candidates (count >= l) are
+// written to the tile's candidate bitmap and the query's list.
+constexpr int FL_WARPS = 8;                   // warps per block in pass 1
+constexpr int kSumWords = kBmUint4 / 32;      // summary words per bitmap (8)
+
+__global__ void __launch_bounds__(FL_WARPS * 32) bm_filter_kernel(IndexView ix, int level,
+                                                                  int64_t R, int l, int nb,
+                                                                  QueryState st,
+                                                                  const LoopCtl *ctl)
+{
+    __shared__ int64_t wbi[FL_WARPS][QW_MAX_M + 1];
+    __shared__ uint32_t wsum[FL_WARPS][QW_MAX_M + 1][kSumWords];
+    __shared__ uint32_t walive[FL_WARPS][kSumWords];
     if (ctl) {
         level = ctl->level;
         R = ctl->R;
     }
-    const int qstart = st.start[q];
-    if (level < qstart) return;
-    const bool first = level == qstart;
-    const int m8 = (ix.m + 7) & ~7;
-    for (int c = threadIdx.x; c < kHistBins; c += BM_THREADS) hist[c] = 0;
-    bucket_bitmaps(ix, st, q, t, level, R, bp, m8);
-    __syncthreads();
-
-    const int64_t slot = ((int64_t)q * ix.nT + t) * kBmUint4 + threadIdx.x;
-    const uint4 prev = first ? make_uint4(0, 0, 0, 0)
-                             : st.cbits[(int64_t)((level - 1) & 1) * st.cb_par + slot];
-    Planes P;
-    count_planes(P, bp, m8);
-    const uint4 cand = candidates_of(P, l);
-    st.cbits[(int64_t)(level & 1) * st.cb_par + slot] = cand;
-    // prev-level candidates are candidates here too (ranges nest, counts grow)
-    const int my_count = __popc(cand.x) + __popc(cand.y) + __popc(cand.z) + __popc(cand.w);
-    const int my_prev = __popc(prev.x) + __popc(prev.y) + __popc(prev.z) + __popc(prev.w);
-    int tot_count, tot_prev;
-    const int pos = block_exclusive_scan<BM_THREADS>(my_count, wsum, &tot_count);
-    block_exclusive_scan<BM_THREADS>(my_prev, wsum, &tot_prev);
-    const int64_t qt = (int64_t)q * ix.nT + t;
-    profile_and_list(P, cand, prev, hist, st.clist + (int64_t)(level & 1) * st.cl_par + qt * kListCap,
-                     pos, threadIdx.x * 128);
-    if (threadIdx.x == 0) {
-        hist[0] += tot_prev;
-        st.clist_n[(int64_t)(level & 1) * st.cln_par + qt] = tot_count;
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int m = ix.m, nT = ix.nT;
+    const int64_t items = (int64_t)nb * nT;
+    for (int64_t k = (int64_t)blockIdx.x * FL_WARPS + wi; k < items;
+         k += (int64_t)gridDim.x * FL_WARPS) {
+        const int q = (int)(k / nT), t = (int)(k % nT);
+        if (!st.active[q] || level < st.start[q]) continue;
+        const int64_t qt = (int64_t)q * nT + t;
+        for (int i = lane; i < m; i += 32)
+            wbi[wi][i] = bm_index(ix, i, t, level, R, floordiv64(st.g[(int64_t)q * m + i], R));
+        __syncwarp();
+        for (int e = lane; e < m * kSumWords; e += 32) {
+            const int i = e / kSumWords, w = e % kSumWords;
+            const int64_t b = wbi[wi][i];
+            wsum[wi][i][w] = b >= 0 ? ix.bm_sum[b * kSumWords + w] : 0u;
+        }
+        __syncwarp();
+        if (lane < kSumWords) {
+            // bit planes of the number of touching buckets, 32 groups per lane
+            uint32_t p[7] = {0, 0, 0, 0, 0, 0, 0};
+            for (int i0 = 0; i0 < m; i0 += 8) {
+                uint32_t xs[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) xs[u] = i0 + u < m ? wsum[wi][i0 + u][lane] : 0u;
+                uint32_t t2a, t2b, t4a, t4b, t8;
+                csa(t2a, p[0], p[0], xs[0], xs[1]);
+                csa(t2b, p[0], p[0], xs[2], xs[3]);
+                csa(t4a, p[1], p[1], t2a, t2b);
+                csa(t2a, p[0], p[0], xs[4], xs[5]);
+                csa(t2b, p[0], p[0], xs[6], xs[7]);
+                csa(t4b, p[1], p[1], t2a, t2b);
+                csa(t8, p[2], p[2], t4a, t4b);
+                uint32_t cy = t8, nx;
+                nx = p[3] & cy; p[3] ^= cy; cy = nx;
+                nx = p[4] & cy; p[4] ^= cy; cy = nx;
+                nx = p[5] & cy; p[5] ^= cy; cy = nx;
+                p[6] ^= cy;
+            }
+            uint32_t gt = 0, eq = 0xffffffffu;
+#pragma unroll
+            for (int kk = 6; kk >= 0; --kk) {
+                if ((l >> kk) & 1) {
+                    eq &= p[kk];
+                } else {
+                    gt |= eq & p[kk];
+                    eq &= ~p[kk];
+                }
+            }
+            walive[wi][lane] = gt | eq;
+        }
+        __syncwarp();
+        const uint32_t aw = lane < kSumWords ? walive[wi][lane] : 0u;
+        const int n_alive = __reduce_add_sync(0xffffffffu, __popc(aw));
+        if (lane == 0) st.clist_n[(int64_t)(level & 1) * st.cln_par + qt] = 0;
+        if (n_alive > 0) {
+            // the dead groups' candidate words are 0 at this level
+            uint4 *cw = st.cbits + (int64_t)(level & 1) * st.cb_par + qt * kBmUint4;
+            for (int g = lane; g < kBmUint4; g += 32)
+                if (!((walive[wi][g >> 5] >> (g & 31)) & 1u)) cw[g] = make_uint4(0, 0, 0, 0);
+            int slot = 0, base = 0;
+            if (lane == 0) {
+                slot = atomicAdd(st.bm_nitems, 1);
+                base = atomicAdd(st.bm_nwork, n_alive);
+            }
+            slot = __shfl_sync(0xffffffffu, slot, 0);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (slot < st.bm_item_cap) {
+                for (int i = lane; i < m; i += 32) st.bm_item_bi[(int64_t)slot * m + i] = wbi[wi][i];
+                if (lane == 0) st.bm_item_qt[slot] = make_int2(q, t);
+                // live groups of the tile, in ascending order, after `base`
+                int pos = base;
+                for (int w = 0; w < kSumWords; ++w) {
+                    const uint32_t x = walive[wi][w];
+                    const int before = __popc(x & ((1u << lane) - 1u));
+                    if ((x >> lane) & 1u) {
+                        const int at = pos + before;
+                        if (at < st.bm_work_cap) st.bm_work[at] = (slot << 8) | (w * 32 + lane);
+                    }
+                    pos += __popc(x);
+                }
+            }
+        }
+        __syncwarp();
     }
-    __syncthreads();
-    int *th = st.tile_hist + qt * kHistBins;
-    for (int c = threadIdx.x; c < kHistBins; c += BM_THREADS) th[c] = hist[c];
-    if (threadIdx.x == 0 && tot_count) atomicAdd(st.cross + q, tot_count);
+}
+
+__global__ void __launch_bounds__(256) bm_count_kernel(IndexView ix, int level, int l,
+                                                       QueryState st, const LoopCtl *ctl)
+{
+    if (ctl) level = ctl->level;
+    const int m = ix.m, nT = ix.nT;
+    const int nwork = min(*st.bm_nwork, st.bm_work_cap);
+    for (int wk = blockIdx.x * blockDim.x + threadIdx.x; wk < nwork;
+         wk += gridDim.x * blockDim.x) {
+        const int e = st.bm_work[wk];
+        const int slot = e >> 8, g = e & 0xff;
+        const int2 qt2 = st.bm_item_qt[slot];
+        const int q = qt2.x, t = qt2.y;
+        const int64_t qt = (int64_t)q * nT + t;
+        const int64_t *bi = st.bm_item_bi + (int64_t)slot * m;
+        const bool first = level == st.start[q];
+        const bool has_prev = !first && st.clist_n[(int64_t)((level - 1) & 1) * st.cln_par + qt] > 0;
+        const uint4 prev = has_prev ? st.cbits[(int64_t)((level - 1) & 1) * st.cb_par + qt * kBmUint4 + g]
+                                    : make_uint4(0, 0, 0, 0);
+        Planes P;
+#pragma unroll
+        for (int kk = 0; kk < 7; ++kk)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) P.s[kk][w] = 0;
+        for (int i0 = 0; i0 < m; i0 += 8) {
+            uint4 x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t b = i0 + u < m ? bi[i0 + u] : -1;
+                x[u] = b >= 0 ? __ldg(ix.bm + b * kBmUint4 + g) : make_uint4(0, 0, 0, 0);
+            }
+            add8(P, x);
+        }
+        const uint4 cand = candidates_of(P, l);
+        st.cbits[(int64_t)(level & 1) * st.cb_par + qt * kBmUint4 + g] = cand;
+        const int nc = __popc(cand.x) + __popc(cand.y) + __popc(cand.z) + __popc(cand.w);
+        if (nc == 0) continue;
+        atomicAdd(st.clist_n + (int64_t)(level & 1) * st.cln_par + qt, nc);
+        atomicAdd(st.cross + q, nc);
+        const int pos = atomicAdd(st.qbuf_n + (int64_t)(level & 1) * st.qbn_par + q, nc);
+        append_candidates(P, cand, prev, st.qbuf + (int64_t)(level & 1) * st.qb_par + (int64_t)q * kQCap,
+                          pos, (int64_t)t * kTile + (int64_t)g * 128);
+    }
 }
 
 // ---- the same level with the bitmaps staged by TMA
@@ -383,7 +471,7 @@ struct TmaShared {
     int64_t lbase[QW_MAX_M];       // per projection: bm_base + bm_lvl[min(level, J)]
     int32_t nbk[QW_MAX_M];         // per projection: buckets at this level (0: past J)
     int32_t pnb[QW_MAX_M];         // per projection: bitmaps per tile
-    int hist[2][kHistBins];        // tile profile of the current item (alternating)
+    int base[2];                   // list position of the current item (alternating)
     int wsum[TMA_CONSUMERS / 32];
 };
 
@@ -449,7 +537,6 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) bm_level_tma_kernel(IndexView 
         mbar_init(&sh.group, TMA_CONSUMERS / 32);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int c = tid; c < 2 * kHistBins; c += TMA_THREADS) (&sh.hist[0][0])[c] = 0;
     for (int i = tid; i < m; i += TMA_THREADS) {
         const int J = ix.bm_J[i];
         const int L = level > J ? J : level;
@@ -584,166 +671,198 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) bm_level_tma_kernel(IndexView 
         if (lane == 0) mbar_arrive(&sh.empty[slot]);
         add8(P, x);
         if (!(h.flags & kLastStage)) continue;
-        // ---- the item's epilogue
+        // ---- the item's epilogue (consumers only: the producer does not take part)
         const uint4 cand = candidates_of(P, l);
         st.cbits[(int64_t)(level & 1) * st.cb_par + qt * kBmUint4 + tid] = cand;
         const int my_count = __popc(cand.x) + __popc(cand.y) + __popc(cand.z) + __popc(cand.w);
-        int my_prev = __popc(prev.x) + __popc(prev.y) + __popc(prev.z) + __popc(prev.w);
-        // consumers only (the producer does not take part)
         int tot_count;
         const int pos = consumer_scan(my_count, sh.wsum, &tot_count, &sh.group, gph, err, stuck);
-        profile_and_list(P, cand, prev, sh.hist[par],
-                         st.clist + (int64_t)(level & 1) * st.cl_par + qt * kListCap, pos, tid * 128);
-        my_prev = __reduce_add_sync(0xffffffffu, my_prev);
-        if (lane == 0 && my_prev) atomicAdd(&sh.hist[par][0], my_prev);
-        group_sync(&sh.group, gph, err, stuck);
-        if (stuck) break;
-        int *th = st.tile_hist + qt * kHistBins;
-        for (int c = tid; c < kHistBins; c += TMA_CONSUMERS) {
-            th[c] = sh.hist[par][c];
-            sh.hist[par][c] = 0;
-        }
         if (tid == 0) {
             st.clist_n[(int64_t)(level & 1) * st.cln_par + qt] = tot_count;
+            sh.base[par] = tot_count ? atomicAdd(st.qbuf_n + (int64_t)(level & 1) * st.qbn_par + h.q,
+                                                 tot_count)
+                                     : 0;
             if (tot_count) atomicAdd(st.cross + h.q, tot_count);
         }
+        group_sync(&sh.group, gph, err, stuck);
+        if (stuck) break;
+        append_candidates(P, cand, prev,
+                          st.qbuf + (int64_t)(level & 1) * st.qb_par + (int64_t)h.q * kQCap,
+                          sh.base[par] + pos, (int64_t)h.t * kTile + tid * 128);
         par ^= 1;
     }
 }
 
-// Emit the kept ids of one (tile, query) in ascending order at the tile's
-// planned position (the plan comes from the tile profiles, as on the level
-// path).  Ids and counts come from the final level's candidate list; a tile
-// with more candidates than the list holds recounts its candidate groups.
-__global__ void __launch_bounds__(BM_THREADS, 2) bm_emit_kernel(IndexView ix, int l, int cap,
-                                                                QueryState st)
+// Sort keys[0..n) ascending in shared memory (n padded to P2 with ~0).
+__device__ __forceinline__ void smem_bitonic(uint64_t *keys, int n, int P2)
 {
-    __shared__ const uint4 *bp[QW_MAX_M + 8];
-    __shared__ int scan_tmp[BM_THREADS / 32];
-    const int t = blockIdx.x;
-    const int q = blockIdx.y;
-    const int nT = ix.nT;
-    const int *plan = st.tile_plan + ((int64_t)q * nT + t) * 3;
-    if (plan[2] == 0) return;
-    const int out0 = plan[0];
-    const int eq0 = plan[1];
-    const int cstar = st.qplan[q * 2 + 0], take_eq = st.qplan[q * 2 + 1];
-    const int jf = st.levels[q] - 1;
-    const int64_t Rf = st.finalR[q];
-    const int m8 = (ix.m + 7) & ~7;
-    const int64_t qt = (int64_t)q * nT + t;
-    const int64_t slot = qt * kBmUint4 + threadIdx.x;
-    const bool has_prev = jf > st.start[q];
-    const int nlist = st.clist_n[(int64_t)(jf & 1) * st.cln_par + qt];
-    if (nlist <= kListCap) {
-        // the level kernel listed the tile's candidates with their counts
-        const uint32_t *L = st.clist + (int64_t)(jf & 1) * st.cl_par + qt * kListCap;
-        const uint32_t *pw = reinterpret_cast<const uint32_t *>(
-            st.cbits + (int64_t)((jf - 1) & 1) * st.cb_par + qt * kBmUint4);
-        const int per = (nlist + BM_THREADS - 1) / BM_THREADS;
-        const int j0 = min(nlist, (int)threadIdx.x * per), j1 = min(nlist, j0 + per);
-        int n_eq = 0;
-        if (cstar >= l)
-            for (int j = j0; j < j1; ++j) {
-                const uint32_t e = L[j], id = e & 0xffffu;
-                const bool pf = has_prev && ((pw[id >> 5] >> (id & 31)) & 1u);
-                n_eq += (!pf && (int)(e >> 16) == cstar) ? 1 : 0;
+    for (int i = n + (int)threadIdx.x; i < P2; i += blockDim.x) keys[i] = ~0ull;
+    __syncthreads();
+    for (int kk = 2; kk <= P2; kk <<= 1) {
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int x = threadIdx.x; x < (P2 >> 1); x += blockDim.x) {
+                const int a = 2 * x - (x & (jj - 1));
+                const int c = a + jj;
+                const bool up = (a & kk) == 0;
+                if ((keys[a] > keys[c]) == up) {
+                    const uint64_t tmp = keys[a];
+                    keys[a] = keys[c];
+                    keys[c] = tmp;
+                }
             }
-        int eq_total;
-        int r = eq0 + block_exclusive_scan<BM_THREADS>(n_eq, scan_tmp, &eq_total);
-        int n_sel = 0;
-        {
-            int rr = r;
-            for (int j = j0; j < j1; ++j) {
-                const uint32_t e = L[j], id = e & 0xffffu;
-                const int c = (int)(e >> 16);
-                const bool pf = has_prev && ((pw[id >> 5] >> (id & 31)) & 1u);
-                if (pf || c > cstar) ++n_sel;
-                else if (c == cstar) { n_sel += (rr < take_eq) ? 1 : 0; ++rr; }
+            __syncthreads();
+        }
+    }
+}
+
+// The k + v bound on the bitmap path, one block per query, from the list of
+// its last level's candidates: the boundary count c* and how many ids at c*
+// are kept follow from the counts exactly as on the level path (Section 3.1,
+// readings R4/R5); candidates of the previous level and those above c* are
+// kept, and of those at c* the ones with the smallest original ids.  The kept
+// list is written in ascending original id with its counts, plus the per-query
+// statistics.  A query whose list or tie class exceeds the fixed buffers is
+// marked for the level path and keeps nothing here.
+constexpr int SEL_THREADS = 512;
+
+__global__ void __launch_bounds__(SEL_THREADS) bm_select_kernel(IndexView ix, int l, int cap,
+                                                                QueryState st,
+                                                                int64_t *__restrict__ stats_out)
+{
+    extern __shared__ uint64_t keys[];
+    __shared__ int hist[kHistBins];
+    __shared__ int s_np, s_nd, s_ne, s_cstar, s_take, s_keep;
+    const int q = blockIdx.x;
+    const int m = ix.m;
+    const int jf = st.levels[q] - 1;
+    const int n = st.qbuf_n[(int64_t)(jf & 1) * st.qbn_par + q];
+    const int nc = st.ncand[q];
+    const uint64_t *E = st.qbuf + (int64_t)(jf & 1) * st.qb_par + (int64_t)q * kQCap;
+    int32_t *cand = st.cand + (int64_t)q * cap;
+    int32_t *col = st.cand_col + (int64_t)q * cap;
+    const bool ovf_list = n > kQCap || n != nc;
+    if (threadIdx.x == 0) {
+        s_np = 0;
+        s_nd = 0;
+        s_ne = 0;
+    }
+    for (int c = threadIdx.x; c < kHistBins; c += SEL_THREADS) hist[c] = 0;
+    __syncthreads();
+    if (!ovf_list) {
+        for (int j = threadIdx.x; j < n; j += SEL_THREADS) {
+            const uint64_t e = E[j];
+            if ((e >> 8) & 1u) atomicAdd(&s_np, 1);
+            else atomicAdd(&hist[1 + (int)(e & 0xffu)], 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int cstar = l - 1, take = 0;
+        const int np = s_np;
+        if (nc > cap) {
+            const int need = cap - np;
+            int acc = 0;
+            for (int c = m; c >= l; --c) {
+                const int hc = hist[1 + c];
+                if (acc + hc >= need) {
+                    cstar = c;
+                    take = need - acc;
+                    break;
+                }
+                acc += hc;
             }
         }
-        int sel_total;
-        int pos = out0 + block_exclusive_scan<BM_THREADS>(n_sel, scan_tmp, &sel_total);
-        for (int j = j0; j < j1; ++j) {
-            const uint32_t e = L[j], id = e & 0xffffu;
-            const int c = (int)(e >> 16);
-            const bool pf = has_prev && ((pw[id >> 5] >> (id & 31)) & 1u);
-            bool sel;
-            if (pf || c > cstar) sel = true;
-            else if (c == cstar) { sel = r < take_eq; ++r; }
-            else sel = false;
-            if (!sel) continue;
-            if (pos < cap) {
-                st.cand[(int64_t)q * cap + pos] = (int32_t)((int64_t)t * kTile + id);
-                st.cand_col[(int64_t)q * cap + pos] = c;
+        int kept = np + take;
+        for (int c = max(cstar + 1, l); c <= m; ++c) kept += hist[1 + c];
+        s_cstar = cstar;
+        s_take = take;
+        s_keep = min(kept, cap);
+    }
+    __syncthreads();
+    const int cstar = s_cstar, take = s_take, keep = s_keep;
+    // kept outright, and the tie class at c* (original ids)
+    if (!ovf_list) {
+        const int32_t *perm = ix.perm;
+        for (int j = threadIdx.x; j < n; j += SEL_THREADS) {
+            const uint64_t e = E[j];
+            const int c = (int)(e & 0xffu);
+            const bool pf = (e >> 8) & 1u;
+            const int32_t orig = perm[e >> 32];
+            if (pf || c > cstar) {
+                const int d = atomicAdd(&s_nd, 1);
+                if (d < cap) {
+                    cand[d] = orig;
+                    col[d] = c;
+                }
+            } else if (c == cstar && take > 0) {
+                const int e2 = atomicAdd(&s_ne, 1);
+                if (e2 < kEqCap) st.eqbuf[(int64_t)q * kEqCap + e2] = orig;
             }
-            ++pos;
+        }
+    }
+    __syncthreads();
+    const int nd = s_nd, ne = s_ne;
+    const bool ovf = ovf_list || ne > kEqCap || nd + take != keep || take > ne;
+    if (ovf) {
+        if (threadIdx.x == 0) {
+            atomicOr(st.bm_ovf + q, 1);
+            st.nkeep[q] = 0;
+        }
+        for (int p = threadIdx.x; p < cap; p += SEL_THREADS) {
+            cand[p] = -1;
+            col[p] = 0;
         }
         return;
     }
-    // more candidates than the list holds: recount the groups that have some
-    bucket_bitmaps(ix, st, q, t, jf, Rf, bp, m8);
-    __syncthreads();
-    const uint4 cand = st.cbits[(int64_t)(jf & 1) * st.cb_par + slot];
-    const uint4 prev = has_prev ? st.cbits[(int64_t)((jf - 1) & 1) * st.cb_par + slot]
-                                : make_uint4(0, 0, 0, 0);
-    const bool mine = (cand.x | cand.y | cand.z | cand.w) != 0;
-    Planes P;
-    if (mine) count_planes(P, bp, m8);
-    int n_eq = 0;
-    if (mine && cstar >= l) {
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            uint32_t x = word_of(cand, w) & ~word_of(prev, w);
-            while (x) {
-                const int b = __ffs(x) - 1;
-                x &= x - 1;
-                n_eq += count_of(P, w, b) == cstar ? 1 : 0;
-            }
+    if (take > 0) {
+        int P2 = 2;
+        while (P2 < ne) P2 <<= 1;
+        for (int i = threadIdx.x; i < ne; i += SEL_THREADS)
+            keys[i] = (uint64_t)(uint32_t)st.eqbuf[(int64_t)q * kEqCap + i];
+        smem_bitonic(keys, ne, P2);
+        for (int r = threadIdx.x; r < take; r += SEL_THREADS) {
+            cand[nd + r] = (int32_t)keys[r];
+            col[nd + r] = cstar;
+        }
+        __syncthreads();
+    }
+    int P2 = 2;
+    while (P2 < keep) P2 <<= 1;
+    for (int i = threadIdx.x; i < keep; i += SEL_THREADS)
+        keys[i] = ((uint64_t)(uint32_t)cand[i] << 32) | (uint32_t)col[i];
+    smem_bitonic(keys, keep, P2);
+    for (int i = threadIdx.x; i < keep; i += SEL_THREADS) {
+        cand[i] = (int32_t)(keys[i] >> 32);
+        col[i] = (int32_t)(keys[i] & 0xffffffffu);
+    }
+    for (int p = keep + threadIdx.x; p < cap; p += SEL_THREADS) {
+        cand[p] = -1;
+        col[p] = 0;
+    }
+    if (threadIdx.x == 0) {
+        st.nkeep[q] = keep;
+        if (stats_out) {
+            int64_t *so = stats_out + (int64_t)q * QW_NSTAT;
+            so[0] = st.levels[q];
+            so[1] = st.finalR[q];
+            so[2] = nc;
+            so[3] = keep;
+            so[4] = st.term[q];
+            so[5] = st.scan_last[q];
+            so[6] = st.scan_full[q];
+            so[7] = st.nprev[q];
         }
     }
-    int eq_total;
-    int r = eq0 + block_exclusive_scan<BM_THREADS>(n_eq, scan_tmp, &eq_total);
-    int n_sel = 0;
-    if (mine) {
-        int rr = r;
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            uint32_t x = word_of(cand, w);
-            const uint32_t pw = word_of(prev, w);
-            while (x) {
-                const int b = __ffs(x) - 1;
-                x &= x - 1;
-                const int c = count_of(P, w, b);
-                if (((pw >> b) & 1u) || c > cstar) ++n_sel;
-                else if (c == cstar) { n_sel += (rr < take_eq) ? 1 : 0; ++rr; }
-            }
-        }
-    }
-    int sel_total;
-    int pos = out0 + block_exclusive_scan<BM_THREADS>(n_sel, scan_tmp, &sel_total);
-    if (!mine) return;
-    const int64_t id0 = (int64_t)t * kTile + (int64_t)threadIdx.x * 128;
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-        uint32_t x = word_of(cand, w);
-        const uint32_t pw = word_of(prev, w);
-        while (x) {
-            const int b = __ffs(x) - 1;
-            x &= x - 1;
-            const int c = count_of(P, w, b);
-            bool sel;
-            if (((pw >> b) & 1u) || c > cstar) sel = true;
-            else if (c == cstar) { sel = r < take_eq; ++r; }
-            else sel = false;
-            if (!sel) continue;
-            if (pos < cap) {
-                st.cand[(int64_t)q * cap + pos] = (int32_t)(id0 + w * 32 + b);
-                st.cand_col[(int64_t)q * cap + pos] = c;
-            }
-            ++pos;
-        }
-    }
+}
+
+// Workload indices of the batch's queries marked for the level path.
+__global__ void bm_overflow_list_kernel(const QueryState st, int nb, const int32_t *order_perm,
+                                        int64_t b0, int32_t *list, int32_t *count)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nb || !st.bm_ovf[q]) return;
+    const int pos = atomicAdd(count, 1);
+    list[pos] = order_perm ? order_perm[b0 + q] : (int32_t)(b0 + q);
 }
 
 // Data objects per bid of every projection, then the exclusive prefix over
@@ -777,16 +896,195 @@ __global__ void bid_scan_kernel(IndexView ix, int64_t *prefix, const int64_t *of
 
 }  // namespace
 
-qw_status launch_bitmap_build(const IndexView &ix, int c, int maxJ, uint4 *bm, cudaStream_t s)
+qw_status launch_bitmap_build(const IndexView &ix, int c, int maxJ, const int32_t *Ht, uint4 *bm,
+                              uint32_t *bm_sum, int64_t total_bitmaps, cudaStream_t s)
 {
     const dim3 grid((unsigned)ix.nT, (unsigned)ix.m);
-    bm_fill_level0_kernel<<<grid, BM_THREADS, 0, s>>>(ix, bm);
+    bm_fill_level0_kernel<<<grid, BM_THREADS, 0, s>>>(ix, Ht, bm);
     QW_CUDA_TRY(cudaGetLastError());
     int64_t R = 1;
     for (int L = 1; L <= maxJ; ++L) {
         R *= c;
         bm_or_level_kernel<<<grid, BM_THREADS, 0, s>>>(ix, bm, L, R, c);
         QW_CUDA_TRY(cudaGetLastError());
+    }
+    const int64_t blocks = std::min<int64_t>(total_bitmaps, 152 * 64);
+    bm_summary_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), BM_THREADS, 0, s>>>(
+        bm, total_bitmaps, bm_sum);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
+
+namespace {
+
+// Run f(chunk, begin, end) over [0, n) in chunks of `chunk` on the host's
+// cores.  Chunk boundaries do not depend on the thread count, so results
+// combined per chunk in chunk order are deterministic.
+template <class F>
+void parallel_chunks(int64_t n, int64_t chunk, F &&f)
+{
+    const int64_t nc = (n + chunk - 1) / chunk;
+    int64_t nt = (int64_t)std::max(1u, std::thread::hardware_concurrency());
+    nt = std::min(nt, nc);
+    if (nt <= 1) {
+        for (int64_t c = 0; c < nc; ++c) f(c, c * chunk, std::min(n, (c + 1) * chunk));
+        return;
+    }
+    std::atomic<int64_t> next(0);
+    std::vector<std::thread> th;
+    for (int64_t t = 0; t < nt; ++t)
+        th.emplace_back([&] {
+            for (;;) {
+                const int64_t c = next.fetch_add(1);
+                if (c >= nc) break;
+                f(c, c * chunk, std::min(n, (c + 1) * chunk));
+            }
+        });
+    for (auto &x : th) x.join();
+}
+
+struct TreeNode {
+    int64_t lo, hi;
+    int depth;
+};
+
+// Split perm[lo, hi) in two: two centroids seeded by the extremes along LSH
+// projection depth mod m, refined by three rounds of two-means, then the
+// points ordered by their side of the bisecting hyperplane and cut where the
+// two-means boundary falls, rounded to a multiple of kGroupIds (so every
+// 128-id group of the internal order stays inside one leaf).
+void split_node(const float *X, int d, const float *A, int m, std::vector<int32_t> &perm,
+                const TreeNode &nd, bool par, TreeNode *kids)
+{
+    const int64_t lo = nd.lo, len = nd.hi - nd.lo;
+    const int64_t chunk = 4096;
+    const int64_t nc = (len + chunk - 1) / chunk;
+    auto each = [&](auto &&f) {
+        if (par) {
+            parallel_chunks(len, chunk, f);
+        } else {
+            for (int64_t c = 0; c < nc; ++c) f(c, c * chunk, std::min(len, (c + 1) * chunk));
+        }
+    };
+    auto row = [&](int64_t j) { return X + (size_t)perm[(size_t)(lo + j)] * (size_t)d; };
+    // seeds: smallest and largest projection on one LSH direction
+    const float *a = A + (size_t)(nd.depth % m) * (size_t)d;
+    std::vector<double> cmin(nc, HUGE_VAL), cmax(nc, -HUGE_VAL);
+    std::vector<int64_t> amin(nc, 0), amax(nc, 0);
+    each([&](int64_t c, int64_t b, int64_t e) {
+        for (int64_t j = b; j < e; ++j) {
+            const float *x = row(j);
+            double t = 0.0;
+            for (int k = 0; k < d; ++k) t += (double)a[k] * (double)x[k];
+            if (t < cmin[c]) { cmin[c] = t; amin[c] = j; }
+            if (t > cmax[c]) { cmax[c] = t; amax[c] = j; }
+        }
+    });
+    int64_t jmin = amin[0], jmax = amax[0];
+    double vmin = cmin[0], vmax = cmax[0];
+    for (int64_t c = 1; c < nc; ++c) {
+        if (cmin[c] < vmin) { vmin = cmin[c]; jmin = amin[c]; }
+        if (cmax[c] > vmax) { vmax = cmax[c]; jmax = amax[c]; }
+    }
+    std::vector<double> c1(d), c2(d), v(d);
+    for (int k = 0; k < d; ++k) {
+        c1[k] = row(jmin)[k];
+        c2[k] = row(jmax)[k];
+    }
+    double thr = 0.0;
+    std::vector<double> part((size_t)nc * (2 * (size_t)d + 2));
+    for (int it = 0; it < 4; ++it) {
+        double n1 = 0.0, n2 = 0.0;
+        double q1 = 0.0, q2 = 0.0;
+        for (int k = 0; k < d; ++k) {
+            v[k] = c2[k] - c1[k];
+            q1 += c1[k] * c1[k];
+            q2 += c2[k] * c2[k];
+        }
+        thr = 0.5 * (q2 - q1);
+        if (it == 3) break;  // the last round only fixes the hyperplane
+        std::fill(part.begin(), part.end(), 0.0);
+        each([&](int64_t c, int64_t b, int64_t e) {
+            double *ps = part.data() + (size_t)c * (2 * (size_t)d + 2);
+            for (int64_t j = b; j < e; ++j) {
+                const float *x = row(j);
+                double t = 0.0;
+                for (int k = 0; k < d; ++k) t += v[k] * (double)x[k];
+                double *acc = t < thr ? ps : ps + d;
+                for (int k = 0; k < d; ++k) acc[k] += (double)x[k];
+                ps[2 * d + (t < thr ? 0 : 1)] += 1.0;
+            }
+        });
+        std::vector<double> s1(d, 0.0), s2(d, 0.0);
+        for (int64_t c = 0; c < nc; ++c) {
+            const double *ps = part.data() + (size_t)c * (2 * (size_t)d + 2);
+            for (int k = 0; k < d; ++k) {
+                s1[k] += ps[k];
+                s2[k] += ps[d + k];
+            }
+            n1 += ps[2 * d];
+            n2 += ps[2 * d + 1];
+        }
+        if (n1 == 0.0 || n2 == 0.0) break;
+        for (int k = 0; k < d; ++k) {
+            c1[k] = s1[k] / n1;
+            c2[k] = s2[k] / n2;
+        }
+    }
+    // order by side of the hyperplane, cut at the boundary (aligned)
+    std::vector<std::pair<double, int32_t>> key((size_t)len);
+    std::vector<int64_t> below(nc, 0);
+    each([&](int64_t c, int64_t b, int64_t e) {
+        for (int64_t j = b; j < e; ++j) {
+            const float *x = row(j);
+            double t = -thr;
+            for (int k = 0; k < d; ++k) t += v[k] * (double)x[k];
+            key[(size_t)j] = {t, perm[(size_t)(lo + j)]};
+            below[c] += t < 0.0 ? 1 : 0;
+        }
+    });
+    int64_t k1 = 0;
+    for (int64_t c = 0; c < nc; ++c) k1 += below[c];
+    int64_t cut = (k1 + kGroupIds / 2) / kGroupIds * kGroupIds;
+    cut = std::max<int64_t>(kGroupIds, std::min<int64_t>(cut, (len - 1) / kGroupIds * kGroupIds));
+    std::nth_element(key.begin(), key.begin() + cut, key.end());
+    for (int64_t j = 0; j < len; ++j) perm[(size_t)(lo + j)] = key[(size_t)j].second;
+    kids[0] = {lo, lo + cut, nd.depth + 1};
+    kids[1] = {lo + cut, nd.hi, nd.depth + 1};
+}
+
+}  // namespace
+
+qw_status locality_order(const float *X, int64_t n, int d, const float *A, int m,
+                         std::vector<int32_t> &perm)
+{
+    try {
+        perm.resize((size_t)n);
+        for (int64_t j = 0; j < n; ++j) perm[(size_t)j] = (int32_t)j;
+        std::vector<TreeNode> cur;
+        if (n > kGroupIds) cur.push_back({0, n, 0});
+        const int64_t big = (int64_t)1 << 16;
+        while (!cur.empty()) {
+            std::vector<TreeNode> kids(2 * cur.size());
+            // large nodes one at a time, each split on all cores ...
+            std::vector<size_t> small;
+            for (size_t u = 0; u < cur.size(); ++u) {
+                if (cur[u].hi - cur[u].lo >= big) split_node(X, d, A, m, perm, cur[u], true, &kids[2 * u]);
+                else small.push_back(u);
+            }
+            // ... small ones side by side (they touch disjoint ranges of perm)
+            parallel_chunks((int64_t)small.size(), 1, [&](int64_t c, int64_t, int64_t) {
+                const size_t u = small[(size_t)c];
+                split_node(X, d, A, m, perm, cur[u], false, &kids[2 * u]);
+            });
+            std::vector<TreeNode> next;
+            for (const TreeNode &k : kids)
+                if (k.hi - k.lo > kGroupIds) next.push_back(k);
+            cur.swap(next);
+        }
+    } catch (const std::bad_alloc &) {
+        set_error("qw_build_index: out of host memory for the locality order");
+        return QW_ERR_OOM;
     }
     return QW_OK;
 }
@@ -819,8 +1117,14 @@ qw_status launch_bm_level(const IndexView &ix, int nb, int level, int64_t R, int
     (void)Rp;
     (void)cgrow;
     if (!tma) {
-        bm_level_kernel<<<dim3((unsigned)ix.nT, (unsigned)nb), BM_THREADS, 0, s>>>(ix, level, R, l,
-                                                                                  st, ctl);
+        // two passes: filter on the summaries, then count the live groups
+        QW_CUDA_TRY(cudaMemsetAsync(st.bm_nitems, 0, 2 * sizeof(int32_t), s));
+        const int64_t items = (int64_t)nb * ix.nT;
+        const int fl_blocks = (int)std::max<int64_t>(
+            1, std::min<int64_t>((items + FL_WARPS - 1) / FL_WARPS, 152 * 16));
+        bm_filter_kernel<<<fl_blocks, FL_WARPS * 32, 0, s>>>(ix, level, R, l, nb, st, ctl);
+        QW_CUDA_TRY(cudaGetLastError());
+        bm_count_kernel<<<152 * 8, 256, 0, s>>>(ix, level, l, st, ctl);
         QW_CUDA_TRY(cudaGetLastError());
         return QW_OK;
     }
@@ -840,8 +1144,21 @@ qw_status launch_bm_level(const IndexView &ix, int nb, int level, int64_t R, int
 qw_status launch_bm_collect(const IndexView &ix, int nb, int l, int cap, QueryState &st,
                             int64_t *stats_out, cudaStream_t s)
 {
-    QW_TRY(launch_select_plan(ix, nb, l, cap, st, stats_out, s));
-    bm_emit_kernel<<<dim3((unsigned)ix.nT, (unsigned)nb), BM_THREADS, 0, s>>>(ix, l, cap, st);
+    QW_CUDA_TRY(cudaMemsetAsync(st.bm_ovf, 0, (size_t)nb * sizeof(int32_t), s));
+    int P2 = 2;
+    while (P2 < std::max(cap, kEqCap)) P2 <<= 1;
+    const size_t smem = (size_t)P2 * sizeof(uint64_t);
+    QW_CUDA_TRY(cudaFuncSetAttribute(bm_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    bm_select_kernel<<<nb, SEL_THREADS, smem, s>>>(ix, l, cap, st, stats_out);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
+
+qw_status launch_bm_overflow_list(const QueryState &st, int nb, const int32_t *order_perm,
+                                  int64_t b0, int32_t *list, int32_t *count, cudaStream_t s)
+{
+    bm_overflow_list_kernel<<<(nb + 255) / 256, 256, 0, s>>>(st, nb, order_perm, b0, list, count);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }

@@ -95,8 +95,13 @@ struct IndexView {
     // level bitmaps (null when the index was built without them): for every
     // projection i, tile t, level L <= bm_J[i] and level-L bucket beta, the
     // tile's ids whose bid / c^L == beta, as kTile bits (kTile / 128 uint4):
-    // bitmap number bm_base[i] + t * bm_nb[i] + bm_lvl[i * kBmLevels + L] + beta
+    // bitmap number bm_base[i] + t * bm_nb[i] + bm_lvl[i * kBmLevels + L] + beta.
+    // Bitmaps number ids in locality order: internal id j is data object
+    // perm[j] (groups of 128 consecutive internal ids are spatially compact);
+    // bm_sum holds per bitmap 256 bits, bit g set when 128-id group g has an id.
     const uint4 *bm;
+    const int32_t *perm;
+    const uint32_t *bm_sum;
     const int64_t *bm_base;
     const int32_t *bm_nb;
     const int32_t *bm_lvl;
@@ -150,17 +155,39 @@ struct QueryState {
     unsigned long long *level_passes = nullptr;  // profile mode: (query, level) passes run, else null
     uint4 *cbits = nullptr;           // bitmap path: 2 (level parity) x nb x nT candidate bitmaps
     int64_t cb_par = 0;         // uint4 per parity (batch capacity x nT x kBmUint4)
-    // bitmap path: per (level parity, query, tile) the candidates in ascending
-    // in-tile id, (count << 16) | id, up to kListCap of them, and their number
-    uint32_t *clist = nullptr;
+    // bitmap path: per (level parity, query, tile) the number of candidates
+    // (0: the tile's candidate bitmap was not written at that level)
     int32_t *clist_n = nullptr;
-    int64_t cl_par = 0;         // entries of clist per parity (batch capacity x nT x kListCap)
     int64_t cln_par = 0;        // entries of clist_n per parity (batch capacity x nT)
+    // bitmap path: per (level parity, query) every candidate of the level as
+    // (internal id << 32) | (was a candidate at the previous level << 8) | count,
+    // up to kQCap of them (qbuf_n counts beyond: more means overflow)
+    uint64_t *qbuf = nullptr;
+    int32_t *qbuf_n = nullptr;
+    int64_t qb_par = 0;         // entries of qbuf per parity (batch capacity x kQCap)
+    int64_t qbn_par = 0;        // entries of qbuf_n per parity (batch capacity)
+    // bitmap path selection: per query "answer on the level path" flags, and
+    // tie lists of kEqCap original ids
+    int32_t *bm_ovf = nullptr;
+    int32_t *eqbuf = nullptr;
+    // bitmap path, two-pass level: item slots (query, tile) with their m bitmap
+    // numbers, and the work list of live (slot << 8 | group) entries
+    int32_t *bm_nitems = nullptr;   // 2 counters: items, work entries (per level)
+    int32_t *bm_nwork = nullptr;
+    int2 *bm_item_qt = nullptr;
+    int64_t *bm_item_bi = nullptr;
+    int32_t *bm_work = nullptr;
+    int32_t bm_item_cap = 0;
+    int32_t bm_work_cap = 0;
 };
 
-// Candidates of one (query, tile) kept in list form by the bitmap level
-// kernels; tiles with more fall back to recounting in the emit kernel.
-constexpr int kListCap = 512;
+// Candidates per query and level the bitmap path holds (more: the query is
+// answered by the level path).
+constexpr int kQCap = 16384;
+// Tie-list capacity per query on the bitmap path (larger tie classes are
+// answered by the level path).
+constexpr int kEqCap = 4096;
+
 
 // Level of a loop that runs on the device (graph mode): the level kernels
 // read level, R and R/c from here, and the loop-control kernel advances it.
@@ -192,7 +219,13 @@ struct BitmapLayout {
     int64_t total = 0;           // bitmaps
 };
 qw_status bitmap_layout(const std::vector<int32_t> &span, int nT, int c, BitmapLayout *out);
-qw_status launch_bitmap_build(const IndexView &ix, int c, int maxJ, uint4 *bm, cudaStream_t s);
+// Internal order of the bitmaps: a two-means tree over the data (host
+// copies X n x d, A m x d), leaves of at most kGroupIds ids aligned to groups.
+constexpr int kGroupIds = 128;
+qw_status locality_order(const float *X, int64_t n, int d, const float *A, int m,
+                         std::vector<int32_t> &perm);
+qw_status launch_bitmap_build(const IndexView &ix, int c, int maxJ, const int32_t *Ht, uint4 *bm,
+                              uint32_t *bm_sum, int64_t total_bitmaps, cudaStream_t s);
 qw_status launch_bid_prefix(const IndexView &ix, int64_t *prefix, const int64_t *off,
                             cudaStream_t s);
 ScanStats scan_stats_of(const IndexView &ix, int c);
@@ -205,6 +238,8 @@ qw_status launch_bm_collect(const IndexView &ix, int nb, int l, int cap, QuerySt
                             int64_t *stats_out, cudaStream_t s);
 qw_status launch_select_plan(const IndexView &ix, int nb, int l, int cap, QueryState &st,
                              int64_t *stats_out, cudaStream_t s);
+qw_status launch_bm_overflow_list(const QueryState &st, int nb, const int32_t *order_perm,
+                                  int64_t b0, int32_t *list, int32_t *count, cudaStream_t s);
 
 // Device-driven loop control (qw_graph.cu builds the graphs that use them).
 qw_status launch_loop_init(LoopCtl *ctl, const QueryState &st, int nb, int cgrow, cudaStream_t s);
@@ -257,6 +292,10 @@ qw_status launch_features(const float *Q, const int32_t *HQ, int64_t nq, const I
                           float xs, float *F, cudaStream_t s);
 qw_status launch_start_levels(const float *prob, int n, int C, float eps, int32_t *start,
                               cudaStream_t s);
+// Features, network, softmax and first-level rule in one launch (inference).
+qw_status launch_start_model(qw_mlp *mp, const float *Q, const int32_t *HQ, int nq,
+                             const IndexView &ix, float xs, float eps, int32_t *start,
+                             cudaStream_t s);
 qw_status data_rms(const float *X, int64_t count, double *dev_acc, double *out, cudaStream_t s);
 
 // Read-only view of a built index for entry points outside qw_api.cu.

@@ -238,8 +238,10 @@ struct qw_mlp {
     int64_t np = 0;
     int64_t oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0;
     DevBuf p32, p16, grad, m1, m2, work, scalar;
+    DevBuf p16t;  // k-major FP16 copies of W1, W2, W3 for the fused inference kernel
     int cap = 0;  // rows the work buffers hold
     int64_t step = 0;
+    int64_t version = 0, t_version = -1;  // weights changed / k-major copies made at
 
     float *Z1, *A1, *Z2, *A2, *Z3, *D3, *DA, *DZ;
 
@@ -357,6 +359,7 @@ qw_status qw_mlp_set_params(qw_mlp *mp, const float *params, int64_t count)
     if (count != mp->np) return mlp_error("parameter count mismatch");
     QW_CUDA_TRY(cudaMemcpy(mp->p32.p, params, count * 4, cudaMemcpyHostToDevice));
     to_half_kernel<<<152 * 4, 256>>>(mp->p32.as<float>(), mp->p16.as<__half>(), count);
+    mp->version += 1;
     QW_CUDA_TRY(cudaGetLastError());
     QW_CUDA_TRY(cudaMemset(mp->m1.p, 0, count * 4));
     QW_CUDA_TRY(cudaMemset(mp->m2.p, 0, count * 4));
@@ -414,6 +417,7 @@ qw_status qw_mlp_train(qw_mlp *mp, const float *X, const int32_t *y, int64_t n, 
             QW_TRY(mp->forward(Xb, nb, s));
             QW_TRY(mp->backward(Xb, y + r0, nb, s));
             mp->step += 1;
+            mp->version += 1;
             const float c1 = 1.0f - powf(b1, (float)mp->step);
             const float c2 = 1.0f - powf(b2, (float)mp->step);
             adam_kernel<<<152 * 4, 256, 0, s>>>(mp->p32.as<float>(), mp->grad.as<float>(),
@@ -462,6 +466,145 @@ namespace qw {
 
 int mlp_inputs(const qw_mlp *mp) { return mp ? mp->n_in : 0; }
 int mlp_classes(const qw_mlp *mp) { return mp ? mp->C : 0; }
+
+namespace {
+
+// out[k * rows + j] = in[j * cols + k] (a rows x cols matrix made k-major).
+__global__ void transpose_half_kernel(const __half *__restrict__ in, int rows, int cols,
+                                      __half *__restrict__ out)
+{
+    const int64_t total = (int64_t)rows * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / cols, k = e % cols;
+        out[k * rows + j] = in[e];
+    }
+}
+
+constexpr int SM_RB = 16;  // queries per block of the fused inference kernel
+constexpr int SM_THREADS = 256;
+
+// Out[k][r] = ReLU(b[j] + sum_k In[k][r] Wt[k][j]) for the block's SM_RB rows;
+// activations are k-major in shared memory so four rows load as one float4.
+__device__ __forceinline__ void dense_relu(const float *In, int K, const __half *__restrict__ Wt,
+                                           const float *__restrict__ b, int N, float *Out)
+{
+    for (int j = threadIdx.x; j < N; j += SM_THREADS) {
+        float acc[SM_RB];
+#pragma unroll
+        for (int r = 0; r < SM_RB; ++r) acc[r] = b[j];
+        for (int k = 0; k < K; ++k) {
+            const float w = __half2float(Wt[(int64_t)k * N + j]);
+            const float4 *x4 = reinterpret_cast<const float4 *>(In + k * SM_RB);
+#pragma unroll
+            for (int r4 = 0; r4 < SM_RB / 4; ++r4) {
+                const float4 x = x4[r4];
+                acc[4 * r4 + 0] = fmaf(x.x, w, acc[4 * r4 + 0]);
+                acc[4 * r4 + 1] = fmaf(x.y, w, acc[4 * r4 + 1]);
+                acc[4 * r4 + 2] = fmaf(x.z, w, acc[4 * r4 + 2]);
+                acc[4 * r4 + 3] = fmaf(x.w, w, acc[4 * r4 + 3]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < SM_RB; ++r) Out[j * SM_RB + r] = fmaxf(acc[r], 0.0f);
+    }
+}
+
+// The start model's inference for SM_RB queries per block, in one launch:
+// the features (as features_kernel), the three layers with FP16 weights and
+// FP32 accumulation, the softmax, and the first-level rule of
+// start_level_kernel.  The prediction only chooses where a query starts, so
+// its rounding cannot change any result.
+__global__ void __launch_bounds__(SM_THREADS) start_model_kernel(
+    const float *__restrict__ Q, const int32_t *__restrict__ HQ, int nq, int d, int m,
+    const int32_t *__restrict__ o, const int32_t *__restrict__ span, float xs,
+    const __half *__restrict__ W1t, const float *__restrict__ b1, const __half *__restrict__ W2t,
+    const float *__restrict__ b2, const __half *__restrict__ W3t, const float *__restrict__ b3,
+    int H, int C, float eps, int32_t *__restrict__ start)
+{
+    extern __shared__ __align__(16) float smf[];
+    const int nin = d + m;
+    float *X = smf;                   // nin x SM_RB (k-major)
+    float *A1 = X + nin * SM_RB;      // H x SM_RB
+    float *A2 = A1 + H * SM_RB;       // H x SM_RB
+    float *Z = A2 + H * SM_RB;        // SM_RB x C
+    const int r0 = blockIdx.x * SM_RB;
+    const int rows = min(SM_RB, nq - r0);
+    for (int e = threadIdx.x; e < SM_RB * nin; e += SM_THREADS) {
+        const int r = e / nin, j = e % nin;
+        float v = 0.0f;
+        if (r < rows) {
+            const int64_t q = r0 + r;
+            if (j < d) {
+                v = Q[q * d + j] * xs;
+            } else {
+                const int i = j - d;
+                const double g = (double)HQ[q * m + i] - (double)o[i];
+                double pos = (g + 0.5) / ((double)span[i] + 1.0);
+                pos = pos < -1.0 ? -1.0 : (pos > 2.0 ? 2.0 : pos);
+                v = (float)(pos - 0.5);
+            }
+        }
+        X[j * SM_RB + r] = v;
+    }
+    __syncthreads();
+    dense_relu(X, nin, W1t, b1, H, A1);
+    __syncthreads();
+    dense_relu(A1, H, W2t, b2, H, A2);
+    __syncthreads();
+    for (int e = threadIdx.x; e < SM_RB * C; e += SM_THREADS) {
+        const int r = e / C, c = e % C;
+        float z = b3[c];
+        for (int k = 0; k < H; ++k) z = fmaf(A2[k * SM_RB + r], __half2float(W3t[(int64_t)k * C + c]), z);
+        Z[r * C + c] = z;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < rows) {
+        const float *z = Z + threadIdx.x * C;
+        float mx = -INFINITY;
+        for (int c = 0; c < C; ++c) mx = fmaxf(mx, z[c]);
+        float sum = 0.0f;
+        for (int c = 0; c < C; ++c) sum += __expf(z[c] - mx);
+        const float inv = 1.0f / sum;
+        float cdf = 0.0f;
+        int s = 0;
+        for (int c = 0; c < C - 1; ++c) {
+            cdf += __expf(z[c] - mx) * inv;
+            if (cdf <= eps) s = c + 1; else break;
+        }
+        start[r0 + threadIdx.x] = s > 0 ? s - 1 : 0;
+    }
+}
+
+}  // namespace
+
+qw_status launch_start_model(qw_mlp *mp, const float *Q, const int32_t *HQ, int nq,
+                             const IndexView &ix, float xs, float eps, int32_t *start,
+                             cudaStream_t s)
+{
+    if (nq == 0) return QW_OK;
+    const int H = mp->H, C = mp->C, nin = mp->n_in;
+    if (mp->t_version != mp->version) {
+        QW_TRY(mp->p16t.ensure((size_t)(mp->oW3 + (int64_t)C * H) * sizeof(__half)));
+        const __half *h = mp->p16.as<__half>();
+        __half *t = mp->p16t.as<__half>();
+        transpose_half_kernel<<<152, 256, 0, s>>>(h + mp->oW1, H, nin, t + mp->oW1);
+        transpose_half_kernel<<<152, 256, 0, s>>>(h + mp->oW2, H, H, t + mp->oW2);
+        transpose_half_kernel<<<152, 256, 0, s>>>(h + mp->oW3, C, H, t + mp->oW3);
+        QW_CUDA_TRY(cudaGetLastError());
+        mp->t_version = mp->version;
+    }
+    const size_t smem = (size_t)SM_RB * ((size_t)nin + 2 * (size_t)H + (size_t)C) * sizeof(float);
+    QW_CUDA_TRY(cudaFuncSetAttribute(start_model_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const __half *t = mp->p16t.as<__half>();
+    const float *p = mp->p32.as<float>();
+    start_model_kernel<<<(nq + SM_RB - 1) / SM_RB, SM_THREADS, smem, s>>>(
+        Q, HQ, nq, ix.d, ix.m, ix.o, ix.span, xs, t + mp->oW1, p + mp->ob1, t + mp->oW2,
+        p + mp->ob2, t + mp->oW3, p + mp->ob3, H, C, eps, start);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
 
 qw_status mlp_predict_dev(qw_mlp *mp, const float *X, int64_t n, float *prob, cudaStream_t s)
 {

@@ -59,6 +59,10 @@ __global__ void query_setup_kernel(const int32_t *__restrict__ HQ, int nb, int m
     st.nkeep[q] = 0;
     st.start[q] = 0;
     st.fb[q] = 0;
+    if (st.qbuf_n) {
+        st.qbuf_n[q] = 0;
+        st.qbuf_n[st.qbn_par + q] = 0;
+    }
     atomicMax(st.max_top, (unsigned long long)top);
 }
 
@@ -84,6 +88,10 @@ __global__ void fallback_kernel(int nb, QueryState st)
     st.scan_level[q] = 0;
     st.scan_last[q] = 0;
     st.scan_full[q] = 0;
+    if (st.qbuf_n) {
+        st.qbuf_n[q] = 0;
+        st.qbuf_n[st.qbn_par + q] = 0;
+    }
     atomicAdd(st.fb_count, 1ull);
 }
 
@@ -347,8 +355,10 @@ __global__ void decide_kernel(int nb, int level, int64_t R, int cap, QueryState 
         st.term[q] = enough ? 2 : 3;
         st.active[q] = 0;
         st.nprev[q] = before;
-    } else if (ctl) {
-        atomicAdd(&ctl->active, 1u);
+    } else {
+        if (ctl) atomicAdd(&ctl->active, 1u);
+        // the next level's candidate list starts empty (bitmap path)
+        if (st.qbuf_n) st.qbuf_n[(int64_t)((level + 1) & 1) * st.qbn_par + q] = 0;
     }
     st.ncand[q] = nc;
 }

@@ -360,3 +360,25 @@ def test_full_size_sampled(orc, qwlib, cuda):
     assert np.all(np.diff(dists, axis=1)[np.isfinite(dists[:, 1:])] >= 0)
     index.free()
     mlp.free()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_bitmap_path_overflow_answered_by_level_path(orc, qwlib, cuda, graph):
+    """Ten distinct points, 7,000 copies each: whole tiles of candidates and
+    tie classes of thousands of ids with the same count.  The bitmap path's
+    fixed lists overflow; those queries are answered by the level path and
+    every output still equals the oracle's."""
+    import torch
+    rng = np.random.default_rng(31)
+    base = rng.uniform(-10, 10, size=(10, 16)).astype(np.float32)
+    X = np.repeat(base, 7_000, axis=0)
+    Q = (base[[0, 3, 7, 9]] + rng.normal(0, 0.05, size=(4, 16))).astype(np.float32)
+    wl = workloads.make_workload("mix10k_d32", seed=3, n=1000, nq=1, d=16, m=16)
+    _full_parity(orc, qwlib, cuda, X, Q, wl.A, wl.b, w=4.0, k=10, v=90, l=12,
+                 path="bitmap_graph" if graph else "bitmap")
+    index = qwlib.Index(_t(X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=4.0, v=90, l=12,
+                        bitmaps=True)
+    index.profile(reset=True)
+    index.query(_t(Q, cuda), 10, path="bitmap", graph=graph, loads="direct")
+    assert index.profile()["bitmap_fallbacks"] > 0
+    index.free()
