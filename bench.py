@@ -77,6 +77,8 @@ def parse_args(argv=None):
                         "the autotuner")
     p.add_argument("--no-bitmaps", action="store_true",
                    help="build the index without the level bitmaps of the bitmap path")
+    p.add_argument("--loads", choices=["tma", "direct"], default="direct",
+                   help="with --no-tune and --path bitmap: how the bitmap kernel reads bitmaps")
     p.add_argument("--graph", action="store_true",
                    help="with --no-tune: run the level loop as a CUDA graph")
     p.add_argument("--v", type=int, default=-1,
@@ -200,7 +202,8 @@ def measured_peaks():
 
 KERNEL_SOURCES = {
     "level_kernel": ("qw_query.cu", "qw_count.cuh", "qw_dir.cuh", "qw_internal.cuh"),
-    "bm_level_kernel": ("qw_bitmap.cu", "qw_dir.cuh", "qw_scan.cuh", "qw_internal.cuh"),
+    "bm_filter_count": ("qw_bitmap.cu", "qw_dir.cuh", "qw_scan.cuh", "qw_internal.cuh"),
+    "bm_level_tma_kernel": ("qw_bitmap.cu", "qw_tma.cuh", "qw_internal.cuh"),
     "cluster_query_kernel": ("qw_cluster.cu", "qw_count.cuh", "qw_internal.cuh"),
     "rerank_kernel": ("qw_rerank.cu", "qw_internal.cuh"),
 }
@@ -338,7 +341,7 @@ def run_ours(args):
     plain_kw = dict(batch=args.batch, path="levels", order="given", rerank="fp32",
                     start="plain", graph=False)
     chosen_kw = dict(batch=args.batch, path=args.path, order=args.order, rerank=args.rerank,
-                     start=args.start, graph=args.graph)
+                     start=args.start, graph=args.graph, loads=args.loads)
     mlp = None
     train_info = None
     wt = workloads.make_workload(args.workload, seed=args.seed, nq=1, n_train=args.train_queries)
@@ -423,10 +426,21 @@ def run_ours(args):
     dom_name = {"cluster": "cluster_query_kernel (all levels of collision counting, persistent)",
                 "level": "level_kernel (bucket-range search + collision counting)"}[dom]
     if bitmap and dom == "level":
-        # per (query, level) pass and tile: the m bucket bitmaps, the previous
-        # level's candidate bitmap and the new one, 4 KiB each
-        dom_name = "bm_level_kernel (bit-sliced collision counts from level bitmaps)"
-        count_bytes = (prof["level_passes"] / steps) * index.info.n_tiles * (s.m + 2) * 4096.0
+        if chosen_kw.get("loads", "tma") == "direct":
+            # two passes: per (query, tile, level) the m bucket summaries (32 B);
+            # per live item its m bitmap numbers and its candidate words (4 KiB);
+            # per live 128-id group m bitmap words, the previous and the new
+            # candidate word (16 B each)
+            dom_name = ("bm_filter_kernel + bm_count_kernel (summary filter, then bit-sliced "
+                        "collision counts of the live 128-id groups)")
+            count_bytes = ((prof["level_passes"] / steps) * index.info.n_tiles * s.m * 32.0
+                           + (prof["bitmap_live_items"] / steps) * (s.m * 8.0 + 4096.0)
+                           + (prof["bitmap_live_groups"] / steps) * (s.m + 2) * 16.0)
+        else:
+            # per (query, level) pass and tile: the m bucket bitmaps, the previous
+            # level's candidate bitmap and the new one, 4 KiB each
+            dom_name = "bm_level_tma_kernel (bit-sliced collision counts, TMA-staged bitmaps)"
+            count_bytes = (prof["level_passes"] / steps) * index.info.n_tiles * (s.m + 2) * 4096.0
     # launches actually run (graph mode counts the device-driven level passes)
     dom_launches = prof["launches"][dom] / steps
     dom_ms = prof["ms"][dom] / steps
@@ -440,7 +454,8 @@ def run_ours(args):
     rr_achieved = (rr_bytes / max(rr_launches, 1)) / ((rr_ms / 1e3) / max(rr_launches, 1)) / 1e9 \
         if rr_ms > 0 else 0.0
     kname = "cluster_query_kernel" if dom == "cluster" else (
-        "bm_level_kernel" if bitmap else "level_kernel")
+        ("bm_filter_count" if chosen_kw.get("loads", "tma") == "direct" else "bm_level_tma_kernel")
+        if bitmap else "level_kernel")
     roofline = {"kernel": dom_name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "unit": "GB/s", "frac": round(achieved / hbm, 4),
                 "traffic": ncu_traffic(kname, args.workload), "peak_kind": peak_kind,
@@ -482,6 +497,9 @@ def run_ours(args):
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk,
         "stats": {"levels_median": float(np.median(st[:, 0])),
+                  "bitmap_live_items_per_step": prof["bitmap_live_items"] / steps,
+                  "bitmap_live_groups_per_step": prof["bitmap_live_groups"] / steps,
+                  "level_passes_per_step": prof["level_passes"] / steps,
                   "entries_scanned_per_query": float(np.mean(st[:, 5])),
                   "kernel_ms_per_step": {k2: round(v2 / steps, 3) for k2, v2 in prof["ms"].items()}},
     }

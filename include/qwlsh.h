@@ -187,6 +187,9 @@ typedef struct {
     int64_t bitmap_fallbacks;      /* QW_PATH_BITMAP queries whose candidates overflowed its
                                       fixed lists and were answered by the level path
                                       (always counted; same results) */
+    int64_t bitmap_live_items;     /* QW_PATH_BITMAP, direct loads: (query, tile, level) items
+                                      with a live 128-id group (profile mode) */
+    int64_t bitmap_live_groups;    /* ... and live groups counted from the bitmaps */
 } qw_profile;
 
 typedef struct {

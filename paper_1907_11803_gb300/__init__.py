@@ -83,7 +83,8 @@ class qw_profile(C.Structure):
                 ("timed_launches", C.c_int64 * QW_K_COUNT), ("queries", C.c_int64),
                 ("rerank_candidates", C.c_int64), ("rerank_fp32_rows", C.c_int64),
                 ("start_levels_skipped", C.c_int64), ("start_fallbacks", C.c_int64),
-                ("level_passes", C.c_int64), ("bitmap_fallbacks", C.c_int64)]
+                ("level_passes", C.c_int64), ("bitmap_fallbacks", C.c_int64),
+                ("bitmap_live_items", C.c_int64), ("bitmap_live_groups", C.c_int64)]
 
 
 class qw_index_info(C.Structure):
@@ -348,7 +349,9 @@ class Index:
                 "start_levels_skipped": int(p.start_levels_skipped),
                 "start_fallbacks": int(p.start_fallbacks),
                 "level_passes": int(p.level_passes),
-                "bitmap_fallbacks": int(p.bitmap_fallbacks)}
+                "bitmap_fallbacks": int(p.bitmap_fallbacks),
+                "bitmap_live_items": int(p.bitmap_live_items),
+                "bitmap_live_groups": int(p.bitmap_live_groups)}
 
     def query(self, Q, k: int, *, batch: int = 0, stats: bool = False, out=None,
               profile: bool = False, path: str = "auto", clusters: int = 0,

@@ -611,7 +611,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     auto up16 = [](size_t x) { return (x + 15) / 16 * 16; };
 
     // ---- workspace
-    QW_TRY(ix->w_err.ensure(64));
+    QW_TRY(ix->w_err.ensure(128));
     QW_TRY(ix->w_hq.ensure((size_t)nq * m * sizeof(int32_t)));       // bucket ids of all queries
     if (!use_cluster && !use_bitmap) QW_TRY(ix->w_counters.ensure((size_t)B * wpq_bytes));
     if (use_bitmap) {
@@ -621,7 +621,8 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         // two-pass level: one slot per (query, tile), one work entry per group
         const size_t items = (size_t)B * ix->nT;
         QW_TRY(ix->w_bmwork.ensure(16 + items * (sizeof(int2) + (size_t)m * sizeof(int64_t)) +
-                                   items * kBmUint4 * sizeof(int32_t)));
+                                   items * kBmUint4 * sizeof(int32_t) +
+                                   2 * items * (kBmUint4 / 32) * sizeof(uint32_t)));
         QW_TRY(ix->w_ovf.ensure(((size_t)nq + 1) * sizeof(int32_t)));
     }
     QW_TRY(ix->w_cand.ensure((size_t)B * cap * 2 * sizeof(int32_t)));
@@ -730,6 +731,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         st.bm_item_bi = reinterpret_cast<int64_t *>(wp + 16 + items * sizeof(int2));
         st.bm_work = reinterpret_cast<int32_t *>(wp + 16 + items * sizeof(int2) +
                                                  items * m * sizeof(int64_t));
+        st.bm_amask = reinterpret_cast<uint32_t *>(st.bm_work + items * kBmUint4);
         st.bm_item_cap = (int32_t)std::min<int64_t>(items, (int64_t)1 << 23);
         st.bm_work_cap = (int32_t)std::min<int64_t>(items * kBmUint4, INT32_MAX);
     }
@@ -745,8 +747,10 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     const IndexView view = ix->view();
     LaunchTimer tm{ix, s, qp && qp->profile != 0};
     if (tm.on) {
-        QW_CUDA_TRY(cudaMemsetAsync(ix->w_err.as<char>() + 40, 0, 24, s));
+        QW_CUDA_TRY(cudaMemsetAsync(ix->w_err.as<char>() + 40, 0, 40, s));
         st.level_passes = reinterpret_cast<unsigned long long *>(ix->w_err.as<char>() + 56);
+        if (use_bitmap)
+            st.bm_prof = reinterpret_cast<unsigned long long *>(ix->w_err.as<char>() + 64);
     }
 
     // ---- the whole workload: copy in (host mode), hash, order
@@ -946,11 +950,13 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     }
     QW_TRY(tm.finish());
     if (tm.on) {
-        unsigned long long ctr[3] = {0, 0, 0};
+        unsigned long long ctr[5] = {0, 0, 0, 0, 0};
         QW_CUDA_TRY(cudaMemcpy(ctr, ix->w_err.as<char>() + 40, sizeof(ctr), cudaMemcpyDeviceToHost));
         ix->prof.rerank_fp32_rows += (int64_t)(bf16 ? ctr[0] : ctr[1]);
         ix->prof.rerank_candidates += (int64_t)ctr[1];
         ix->prof.level_passes += (int64_t)ctr[2];
+        ix->prof.bitmap_live_items += (int64_t)ctr[3];
+        ix->prof.bitmap_live_groups += (int64_t)ctr[4];
     }
     ix->prof.queries += nq;
     return QW_OK;
@@ -1211,7 +1217,7 @@ qw_status qw_query_features(qw_index *ix, const float *queries, int64_t nq, floa
     if (nq == 0) return QW_OK;
     cudaStream_t s = (cudaStream_t)stream;
     QW_TRY(ix->w_hq.ensure((size_t)nq * ix->m * sizeof(int32_t)));
-    QW_TRY(ix->w_err.ensure(64));
+    QW_TRY(ix->w_err.ensure(128));
     int *err = ix->w_err.as<int>();
     QW_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
     QW_TRY(launch_hash(queries, nq, ix->d, ix->A.as<float>(), ix->b.as<float>(), ix->m, ix->w,

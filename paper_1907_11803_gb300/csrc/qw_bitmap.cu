@@ -284,9 +284,10 @@ __device__ __forceinline__ int64_t bm_index(const IndexView &ix, int i, int t, i
 // words of 32 bits per projection, one bit per 128-id group), and a carry-save
 // sum over the m projections gives every group the number of the query's
 // buckets that touch it.  Groups below l cannot hold a candidate.  A tile
-// without live groups is done (its candidate count is 0); otherwise its dead
-// groups' candidate words are cleared, the item's m bitmap numbers are stored
-// in a slot, and its live groups go to a work list.
+// without live groups is done (its candidate count is 0); otherwise its live
+// groups are recorded (a 256-bit mask: only their candidate words are written
+// at this level), the item's m bitmap numbers are stored in a slot, and its
+// live groups go to a work list.
 // Pass 2, one thread per live group: the 128-id group's word of each of the
 // m bitmaps, summed into bit planes; the group's candidates (count >= l) are
 // written to the tile's candidate bitmap and the query's list.
@@ -360,10 +361,9 @@ __global__ void __launch_bounds__(FL_WARPS * 32) bm_filter_kernel(IndexView ix, 
         const int n_alive = __reduce_add_sync(0xffffffffu, __popc(aw));
         if (lane == 0) st.clist_n[(int64_t)(level & 1) * st.cln_par + qt] = 0;
         if (n_alive > 0) {
-            // the dead groups' candidate words are 0 at this level
-            uint4 *cw = st.cbits + (int64_t)(level & 1) * st.cb_par + qt * kBmUint4;
-            for (int g = lane; g < kBmUint4; g += 32)
-                if (!((walive[wi][g >> 5] >> (g & 31)) & 1u)) cw[g] = make_uint4(0, 0, 0, 0);
+            // which groups have a candidate word at this level
+            if (lane < kSumWords)
+                st.bm_amask[((int64_t)(level & 1) * st.cln_par + qt) * kSumWords + lane] = aw;
             int slot = 0, base = 0;
             if (lane == 0) {
                 slot = atomicAdd(st.bm_nitems, 1);
@@ -391,7 +391,14 @@ __global__ void __launch_bounds__(FL_WARPS * 32) bm_filter_kernel(IndexView ix, 
     }
 }
 
-__global__ void __launch_bounds__(256) bm_count_kernel(IndexView ix, int level, int l,
+// Profile mode: add this level's live items and live groups to the totals.
+__global__ void bm_prof_kernel(QueryState st)
+{
+    st.bm_prof[0] += (unsigned long long)min(*st.bm_nitems, st.bm_item_cap);
+    st.bm_prof[1] += (unsigned long long)min(*st.bm_nwork, st.bm_work_cap);
+}
+
+__global__ void __launch_bounds__(256, 3) bm_count_kernel(IndexView ix, int level, int l,
                                                        QueryState st, const LoopCtl *ctl)
 {
     if (ctl) level = ctl->level;
@@ -406,7 +413,11 @@ __global__ void __launch_bounds__(256) bm_count_kernel(IndexView ix, int level, 
         const int64_t qt = (int64_t)q * nT + t;
         const int64_t *bi = st.bm_item_bi + (int64_t)slot * m;
         const bool first = level == st.start[q];
-        const bool has_prev = !first && st.clist_n[(int64_t)((level - 1) & 1) * st.cln_par + qt] > 0;
+        // the previous level wrote this group's candidate word only if the
+        // tile had candidates and the group was live there
+        const int64_t pq = (int64_t)((level - 1) & 1) * st.cln_par + qt;
+        const bool has_prev = !first && st.clist_n[pq] > 0 &&
+                              ((st.bm_amask[pq * kSumWords + (g >> 5)] >> (g & 31)) & 1u);
         const uint4 prev = has_prev ? st.cbits[(int64_t)((level - 1) & 1) * st.cb_par + qt * kBmUint4 + g]
                                     : make_uint4(0, 0, 0, 0);
         Planes P;
@@ -1126,6 +1137,10 @@ qw_status launch_bm_level(const IndexView &ix, int nb, int level, int64_t R, int
         QW_CUDA_TRY(cudaGetLastError());
         bm_count_kernel<<<152 * 8, 256, 0, s>>>(ix, level, l, st, ctl);
         QW_CUDA_TRY(cudaGetLastError());
+        if (st.bm_prof) {
+            bm_prof_kernel<<<1, 1, 0, s>>>(st);
+            QW_CUDA_TRY(cudaGetLastError());
+        }
         return QW_OK;
     }
     int dev = 0, n_sm = 0;

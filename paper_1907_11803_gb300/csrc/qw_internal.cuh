@@ -176,9 +176,11 @@ struct QueryState {
     int32_t *bm_nwork = nullptr;
     int2 *bm_item_qt = nullptr;
     int64_t *bm_item_bi = nullptr;
+    uint32_t *bm_amask = nullptr;   // per (level parity, query, tile): live groups, 8 words
     int32_t *bm_work = nullptr;
     int32_t bm_item_cap = 0;
     int32_t bm_work_cap = 0;
+    unsigned long long *bm_prof = nullptr;  // profile mode: live items, live groups (summed)
 };
 
 // Candidates per query and level the bitmap path holds (more: the query is

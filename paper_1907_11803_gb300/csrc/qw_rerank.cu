@@ -64,39 +64,61 @@ __device__ void rerank_finish(const float *__restrict__ X, int d, const float *_
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) *sm.any_mark = 0;
 
-    // 1. FP32 squared distances, one warp per candidate row
-    for (int j = warp; j < P2; j += RR_WARPS) {
-        if (j >= nc) {
-            if (lane == 0) {
-                d32[j] = CUDART_INF_F;
-                sid[j] = INT32_MAX;
-            }
-            continue;
+    // 1. FP32 squared distances: a warp takes kRows candidate rows at a time,
+    //    so each lane has kRows independent loads in flight; every row keeps
+    //    its own per-lane chain and butterfly sum (the order rho covers)
+    constexpr int kRows = 4;
+    for (int j0 = warp * kRows; j0 < P2; j0 += RR_WARPS * kRows) {
+        const float *xr[kRows];
+        float acc[kRows];
+#pragma unroll
+        for (int u = 0; u < kRows; ++u) {
+            const int j = j0 + u;
+            xr[u] = j < nc ? X + (int64_t)sid[j] * d : nullptr;
+            acc[u] = 0.0f;
         }
-        const int32_t id = sid[j];
-        const float *x = X + (int64_t)id * d;
-        float acc = 0.0f;
         if (vec) {
-            const float4 *x4 = reinterpret_cast<const float4 *>(x);
             const float4 *q4 = reinterpret_cast<const float4 *>(qv);
             for (int c = lane; c < (d >> 2); c += 32) {
-                float4 a = __ldg(x4 + c), b = __ldg(q4 + c);
-                float t0 = a.x - b.x, t1 = a.y - b.y, t2 = a.z - b.z, t3 = a.w - b.w;
-                acc = fmaf(t0, t0, acc);
-                acc = fmaf(t1, t1, acc);
-                acc = fmaf(t2, t2, acc);
-                acc = fmaf(t3, t3, acc);
+                const float4 b = __ldg(q4 + c);
+                float4 a[kRows];
+#pragma unroll
+                for (int u = 0; u < kRows; ++u)
+                    a[u] = xr[u] ? __ldg(reinterpret_cast<const float4 *>(xr[u]) + c)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < kRows; ++u) {
+                    const float t0 = a[u].x - b.x, t1 = a[u].y - b.y, t2 = a[u].z - b.z,
+                                t3 = a[u].w - b.w;
+                    acc[u] = fmaf(t0, t0, acc[u]);
+                    acc[u] = fmaf(t1, t1, acc[u]);
+                    acc[u] = fmaf(t2, t2, acc[u]);
+                    acc[u] = fmaf(t3, t3, acc[u]);
+                }
             }
         } else {
             for (int c = lane; c < d; c += 32) {
-                float t0 = __ldg(x + c) - __ldg(qv + c);
-                acc = fmaf(t0, t0, acc);
+                const float qc = __ldg(qv + c);
+#pragma unroll
+                for (int u = 0; u < kRows; ++u) {
+                    const float t0 = xr[u] ? __ldg(xr[u] + c) - qc : 0.0f;
+                    acc[u] = fmaf(t0, t0, acc[u]);
+                }
             }
         }
-        acc = warp_sum(acc);
-        if (lane == 0) {
-            d32[j] = acc;
-            sid[j] = id;
+#pragma unroll
+        for (int u = 0; u < kRows; ++u) {
+            const int j = j0 + u;
+            if (j >= P2) break;
+            const float sum = warp_sum(acc[u]);
+            if (lane == 0) {
+                if (j < nc) {
+                    d32[j] = sum;
+                } else {
+                    d32[j] = CUDART_INF_F;
+                    sid[j] = INT32_MAX;
+                }
+            }
         }
     }
     __syncthreads();
