@@ -513,8 +513,9 @@ static qw_status host_level_loop(qw_index *ix, LaunchTimer &tm, const IndexView 
                               : launch_level(view, nb, level, R, Rp, ix->l, ix->c, st, s);
             }));
             QW_TRY(tm.run(QW_K_DECIDE, 1, [&] {
-                return launch_decide(nb, level, R, cap, st, s, nullptr,
-                                     bitmap ? scan_stats_of(view, ix->c) : ScanStats());
+                ScanStats ss = bitmap ? scan_stats_of(view, ix->c) : ScanStats();
+                ss.recount_first = bitmap && learned;
+                return launch_decide(nb, level, R, cap, st, s, nullptr, ss);
             }));
             if ((unsigned long long)R > max_top) break;
             if (level > 62) {
@@ -617,7 +618,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     if (use_bitmap) {
         QW_TRY(ix->w_cbits.ensure((size_t)B * cb_bytes));
         QW_TRY(ix->w_clist.ensure((size_t)B * cl_bytes + 64));
-        QW_TRY(ix->w_bmsel.ensure((size_t)B * (1 + kEqCap) * sizeof(int32_t)));
+        QW_TRY(ix->w_bmsel.ensure((size_t)B * (2 + kEqCap) * sizeof(int32_t)));
         // two-pass level: one slot per (query, tile), one work entry per group
         const size_t items = (size_t)B * ix->nT;
         QW_TRY(ix->w_bmwork.ensure(16 + items * (sizeof(int2) + (size_t)m * sizeof(int64_t)) +
@@ -722,7 +723,8 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         st.qbn_par = B;
         st.qbuf_n = st.clist_n + 2 * st.cln_par;
         st.bm_ovf = ix->w_bmsel.as<int32_t>();
-        st.eqbuf = st.bm_ovf + B;
+        st.recount = st.bm_ovf + B;
+        st.eqbuf = st.bm_ovf + 2 * B;
         const int64_t items = B * (int64_t)ix->nT;
         char *wp = ix->w_bmwork.as<char>();
         st.bm_nitems = reinterpret_cast<int32_t *>(wp);
@@ -850,8 +852,10 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                 (void)F;
                 (void)prob;
                 QW_TRY(tm.run(QW_K_START, 1, [&] {
+                    // bitmap path: start at the predicted last level (its previous
+                    // level is recounted); level path: one level before it
                     return launch_start_model(ix->start_model, Qb, HQb, nb, view, ix->xs,
-                                              ix->start_eps, st.start, s);
+                                              ix->start_eps, use_bitmap ? 0 : 1, st.start, s);
                 }));
                 QW_CUDA_TRY(cudaMemsetAsync(st.fb_count, 0, 16, s));
             }
@@ -864,7 +868,9 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                 QW_TRY(host_level_loop(ix, tm, view, nb, cap, learned, use_bitmap, tma_loads, err,
                                        st, s));
             }
-            QW_TRY(tm.run(QW_K_SELECT, use_bitmap ? 3 : 2, [&] {
+            QW_TRY(tm.run(QW_K_SELECT, use_bitmap ? (learned ? 2 : 1) : 2, [&] {
+                if (use_bitmap && learned)
+                    QW_TRY(launch_bm_recount(view, nb, ix->l, cap, ix->c, st, s));
                 return use_bitmap ? launch_bm_collect(view, nb, ix->l, cap, st, stats_b, s)
                                   : launch_collect(view, nb, ix->l, cap, st, stats_b, s);
             }));

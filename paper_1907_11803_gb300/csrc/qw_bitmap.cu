@@ -866,6 +866,111 @@ __global__ void __launch_bounds__(SEL_THREADS) bm_select_kernel(IndexView ix, in
     }
 }
 
+// Learned starts on the bitmap path: a query that stopped at its first level
+// L > 0 never counted level L - 1, whose candidates come first under the k + v
+// bound (reading R5).  Those are exactly the final candidates whose level-(L-1)
+// count reaches l (buckets nest, so C(L-1) is a subset of C(L)); they are
+// found by counting the final candidates' 128-id groups again at level L - 1.
+// The plain path would have stopped earlier if |C(L-1)| >= k + v or if radius
+// c^(L-1) already exceeded every useful radius of the query: such queries are
+// marked for the level path.  One block per marked query; the candidates of
+// one group are contiguous in the list (one thread appended them).
+constexpr int RC_THREADS = 256;
+constexpr int kRunCap = 2048;
+
+__global__ void __launch_bounds__(RC_THREADS) bm_recount_kernel(IndexView ix, int l, int cap,
+                                                                int cgrow, QueryState st)
+{
+    __shared__ int64_t lbase[QW_MAX_M + 8];
+    __shared__ int32_t pnb[QW_MAX_M + 8];
+    __shared__ int runs[kRunCap];
+    __shared__ int nruns, nprev;
+    const int q = blockIdx.x;
+    if (!st.recount[q]) return;
+    const int m = ix.m;
+    const int m8 = (m + 7) & ~7;
+    const int L = st.levels[q] - 1;
+    const int Lp = L - 1;
+    const int64_t R = st.finalR[q] / cgrow;  // radius of level L - 1
+    const int n = st.qbuf_n[(int64_t)(L & 1) * st.qbn_par + q];
+    uint64_t *E = st.qbuf + (int64_t)(L & 1) * st.qb_par + (int64_t)q * kQCap;
+    if (n > kQCap) return;  // the selection marks the query for the level path
+    if (R > st.top[q]) {
+        // the plain path stops at level L - 1 by radius: not this answer
+        if (threadIdx.x == 0) atomicOr(st.bm_ovf + q, 2);
+        return;
+    }
+    if (threadIdx.x < m) {
+        const int i = threadIdx.x;
+        const int64_t beta = floordiv64(st.g[(int64_t)q * m + i], R);
+        const int J = ix.bm_J[i];
+        int64_t b = -1;
+        if (Lp > J) {
+            if (beta == 0) b = ix.bm_base[i] + ix.bm_lvl[i * kBmLevels + J];
+        } else if (beta >= 0 && beta <= (int64_t)ix.span[i] / R) {
+            b = ix.bm_base[i] + ix.bm_lvl[i * kBmLevels + Lp] + beta;
+        }
+        lbase[i] = b;
+        pnb[i] = ix.bm_nb[i];
+    } else if (threadIdx.x < m8) {
+        lbase[threadIdx.x] = -1;
+        pnb[threadIdx.x] = 0;
+    }
+    if (threadIdx.x == 0) {
+        nruns = 0;
+        nprev = 0;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += RC_THREADS) {
+        const uint64_t grp = E[j] >> 39;  // (internal id >> 7): tile and group
+        if (j == 0 || grp != (E[j - 1] >> 39)) {
+            const int r = atomicAdd(&nruns, 1);
+            if (r < kRunCap) runs[r] = j;
+        }
+    }
+    __syncthreads();
+    if (nruns > kRunCap) {
+        if (threadIdx.x == 0) atomicOr(st.bm_ovf + q, 2);
+        return;
+    }
+    for (int r = threadIdx.x; r < nruns; r += RC_THREADS) {
+        const int j0 = runs[r];
+        const uint64_t grp = E[j0] >> 39;
+        const int64_t id0 = (int64_t)(E[j0] >> 32);
+        const int64_t t = id0 >> kTileShift;
+        const int g = (int)((id0 & (kTile - 1)) >> 7);
+        Planes P;
+#pragma unroll
+        for (int kk = 0; kk < 7; ++kk)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) P.s[kk][w] = 0;
+        for (int i0 = 0; i0 < m8; i0 += 8) {
+            uint4 x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t b = lbase[i0 + u];
+                x[u] = b >= 0 ? __ldg(ix.bm + (b + t * pnb[i0 + u]) * kBmUint4 + g)
+                              : make_uint4(0, 0, 0, 0);
+            }
+            add8(P, x);
+        }
+        int mine = 0;
+        for (int j = j0; j < n && (E[j] >> 39) == grp; ++j) {
+            const uint32_t id = (uint32_t)(E[j] >> 32) & 127u;
+            if (count_of(P, (int)(id >> 5), (int)(id & 31)) >= l) {
+                E[j] |= 1ull << 8;
+                ++mine;
+            }
+        }
+        if (mine) atomicAdd(&nprev, mine);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (nprev >= cap) atomicOr(st.bm_ovf + q, 2);  // the plain path stops at L - 1
+        else st.nprev[q] = nprev;
+    }
+}
+
 // Workload indices of the batch's queries marked for the level path.
 __global__ void bm_overflow_list_kernel(const QueryState st, int nb, const int32_t *order_perm,
                                         int64_t b0, int32_t *list, int32_t *count)
@@ -1156,10 +1261,17 @@ qw_status launch_bm_level(const IndexView &ix, int nb, int level, int64_t R, int
     return QW_OK;
 }
 
+qw_status launch_bm_recount(const IndexView &ix, int nb, int l, int cap, int cgrow, QueryState &st,
+                            cudaStream_t s)
+{
+    bm_recount_kernel<<<nb, RC_THREADS, 0, s>>>(ix, l, cap, cgrow, st);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
+
 qw_status launch_bm_collect(const IndexView &ix, int nb, int l, int cap, QueryState &st,
                             int64_t *stats_out, cudaStream_t s)
 {
-    QW_CUDA_TRY(cudaMemsetAsync(st.bm_ovf, 0, (size_t)nb * sizeof(int32_t), s));
     int P2 = 2;
     while (P2 < std::max(cap, kEqCap)) P2 <<= 1;
     const size_t smem = (size_t)P2 * sizeof(uint64_t);

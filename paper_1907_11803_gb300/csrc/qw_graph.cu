@@ -139,8 +139,9 @@ qw_status build(LevelGraphCache *c, const GraphKey &key, const IndexView &ix, in
                 QW_TRY(launch_bm_level(ix, nb, 0, 1, 1, l, cgrow, st, err, tma, cs, ctl));
             else
                 QW_TRY(launch_level(ix, nb, 0, 1, 1, l, cgrow, st, cs, ctl));
-            QW_TRY(launch_decide(nb, 0, 1, cap, st, cs, ctl,
-                                 bitmap ? scan_stats_of(ix, cgrow) : ScanStats()));
+            ScanStats ss = bitmap ? scan_stats_of(ix, cgrow) : ScanStats();
+            ss.recount_first = bitmap && learned;
+            QW_TRY(launch_decide(nb, 0, 1, cap, st, cs, ctl, ss));
             return launch_loop_ctl(ctl, st.max_top, cgrow, h, err, cs);
         };
     };

@@ -120,6 +120,9 @@ struct ScanStats {
     const int32_t *span = nullptr;
     int m = 0;
     int cgrow = 2;
+    // bitmap path, learned starts: a query that stops at its first level > 0
+    // stops there and is marked for the previous-level recount (no rerun)
+    bool recount_first = false;
 };
 
 // Most levels a bitmap table describes per projection (c >= 2, bids < 2^31).
@@ -170,6 +173,7 @@ struct QueryState {
     // tie lists of kEqCap original ids
     int32_t *bm_ovf = nullptr;
     int32_t *eqbuf = nullptr;
+    int32_t *recount = nullptr;     // per query: stopped at its learned first level (bitmap path)
     // bitmap path, two-pass level: item slots (query, tile) with their m bitmap
     // numbers, and the work list of live (slot << 8 | group) entries
     int32_t *bm_nitems = nullptr;   // 2 counters: items, work entries (per level)
@@ -296,8 +300,11 @@ qw_status launch_start_levels(const float *prob, int n, int C, float eps, int32_
                               cudaStream_t s);
 // Features, network, softmax and first-level rule in one launch (inference).
 qw_status launch_start_model(qw_mlp *mp, const float *Q, const int32_t *HQ, int nq,
-                             const IndexView &ix, float xs, float eps, int32_t *start,
+                             const IndexView &ix, float xs, float eps, int shift, int32_t *start,
                              cudaStream_t s);
+// Bitmap path: previous-level flags of the queries marked for recount.
+qw_status launch_bm_recount(const IndexView &ix, int nb, int l, int cap, int cgrow, QueryState &st,
+                            cudaStream_t s);
 qw_status data_rms(const float *X, int64_t count, double *dev_acc, double *out, cudaStream_t s);
 
 // Read-only view of a built index for entry points outside qw_api.cu.

@@ -512,15 +512,18 @@ __device__ __forceinline__ void dense_relu(const float *In, int K, const __half 
 
 // The start model's inference for SM_RB queries per block, in one launch:
 // the features (as features_kernel), the three layers with FP16 weights and
-// FP32 accumulation, the softmax, and the first-level rule of
-// start_level_kernel.  The prediction only chooses where a query starts, so
-// its rounding cannot change any result.
+// FP32 accumulation, the softmax, and the first-level rule: with s the first
+// level whose predicted probability of stopping at or before it exceeds eps,
+// start at s - shift (shift 1: one level early, so the previous level is
+// counted; shift 0: at s itself, where the previous level's candidates are
+// recounted afterwards).  The prediction only chooses where a query starts,
+// so its rounding cannot change any result.
 __global__ void __launch_bounds__(SM_THREADS) start_model_kernel(
     const float *__restrict__ Q, const int32_t *__restrict__ HQ, int nq, int d, int m,
     const int32_t *__restrict__ o, const int32_t *__restrict__ span, float xs,
     const __half *__restrict__ W1t, const float *__restrict__ b1, const __half *__restrict__ W2t,
     const float *__restrict__ b2, const __half *__restrict__ W3t, const float *__restrict__ b3,
-    int H, int C, float eps, int32_t *__restrict__ start)
+    int H, int C, float eps, int shift, int32_t *__restrict__ start)
 {
     extern __shared__ __align__(16) float smf[];
     const int nin = d + m;
@@ -572,14 +575,14 @@ __global__ void __launch_bounds__(SM_THREADS) start_model_kernel(
             cdf += __expf(z[c] - mx) * inv;
             if (cdf <= eps) s = c + 1; else break;
         }
-        start[r0 + threadIdx.x] = s > 0 ? s - 1 : 0;
+        start[r0 + threadIdx.x] = s > shift ? s - shift : 0;
     }
 }
 
 }  // namespace
 
 qw_status launch_start_model(qw_mlp *mp, const float *Q, const int32_t *HQ, int nq,
-                             const IndexView &ix, float xs, float eps, int32_t *start,
+                             const IndexView &ix, float xs, float eps, int shift, int32_t *start,
                              cudaStream_t s)
 {
     if (nq == 0) return QW_OK;
@@ -601,7 +604,7 @@ qw_status launch_start_model(qw_mlp *mp, const float *Q, const int32_t *HQ, int 
     const float *p = mp->p32.as<float>();
     start_model_kernel<<<(nq + SM_RB - 1) / SM_RB, SM_THREADS, smem, s>>>(
         Q, HQ, nq, ix.d, ix.m, ix.o, ix.span, xs, t + mp->oW1, p + mp->ob1, t + mp->oW2,
-        p + mp->ob2, t + mp->oW3, p + mp->ob3, H, C, eps, start);
+        p + mp->ob2, t + mp->oW3, p + mp->ob3, H, C, eps, shift, start);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }

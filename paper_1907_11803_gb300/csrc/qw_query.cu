@@ -59,6 +59,8 @@ __global__ void query_setup_kernel(const int32_t *__restrict__ HQ, int nb, int m
     st.nkeep[q] = 0;
     st.start[q] = 0;
     st.fb[q] = 0;
+    if (st.recount) st.recount[q] = 0;
+    if (st.bm_ovf) st.bm_ovf[q] = 0;
     if (st.qbuf_n) {
         st.qbuf_n[q] = 0;
         st.qbuf_n[st.qbn_par + q] = 0;
@@ -345,11 +347,17 @@ __global__ void decide_kernel(int nb, int level, int64_t R, int cap, QueryState 
     const bool enough = nc >= cap;        // the k + v bound (Section 3.1)
     const bool past = R > st.top[q];      // no further level can change C_R
     if ((enough || past) && first && level > 0) {
-        // stopped at a learned first level: the previous level is unknown,
-        // so the query is answered again from level 0
-        st.fb[q] = 1;
-        st.active[q] = 0;
-        return;
+        if (ss.recount_first) {
+            // bitmap path: stop here; the previous level's candidates are
+            // recounted from the bitmaps afterwards (and checked)
+            st.recount[q] = 1;
+        } else {
+            // stopped at a learned first level: the previous level is unknown,
+            // so the query is answered again from level 0
+            st.fb[q] = 1;
+            st.active[q] = 0;
+            return;
+        }
     }
     if (enough || past) {
         st.term[q] = enough ? 2 : 3;

@@ -81,13 +81,15 @@ def test_learned_start_same_results_fewer_levels(qwlib, cuda):
     assert torch.equal(ids0, ids3) and torch.equal(d0, d3) and torch.equal(st0, st3)
     assert prof3["start_levels_skipped"] == prof["start_levels_skipped"]
     assert prof3["start_fallbacks"] == prof["start_fallbacks"]
-    # bitmap path, host loop and graph mode
-    for graph, loads in ((False, "tma"), (True, "tma"), (False, "direct")):
+    # bitmap path, host loop and graph mode: it starts at the predicted last
+    # level itself (the previous level's candidates are recounted), so it
+    # skips at least as many levels
+    for graph, loads in ((False, "tma"), (True, "tma"), (False, "direct"), (True, "direct")):
         ids5, d5, st5 = index.query(Q, 20, stats=True, start="learned", path="bitmap", graph=graph,
                                     loads=loads)
         prof5 = index.profile(reset=True)
         assert torch.equal(ids0, ids5) and torch.equal(d0, d5) and torch.equal(st0, st5)
-        assert prof5["start_levels_skipped"] == prof["start_levels_skipped"]
+        assert prof5["start_levels_skipped"] >= prof["start_levels_skipped"]
     # an over-eager model (eps close to 1) starts too late for many queries:
     # they are recomputed from level 0 and the results still match
     index.set_start_model(mlp, eps=0.999)
@@ -99,5 +101,13 @@ def test_learned_start_same_results_fewer_levels(qwlib, cuda):
     prof4 = index.profile(reset=True)
     assert torch.equal(ids0, ids4) and torch.equal(st0, st4)
     assert prof4["start_fallbacks"] == prof2["start_fallbacks"]
+    # on the bitmap path an over-eager start leaves some queries whose
+    # previous level already met the stop rule: they go to the level path
+    for graph in (False, True):
+        ids6, d6, st6 = index.query(Q, 20, stats=True, start="learned", path="bitmap",
+                                    graph=graph, loads="direct")
+        prof6 = index.profile(reset=True)
+        assert torch.equal(ids0, ids6) and torch.equal(d0, d6) and torch.equal(st0, st6)
+        assert prof6["bitmap_fallbacks"] > 0
     index.free()
     mlp.free()
