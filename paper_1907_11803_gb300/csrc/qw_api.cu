@@ -70,7 +70,7 @@ struct qw_index {
     DevBuf X, A, b, o, span, lid, dir_bid, dir_off, dir_start, dir_cnt, Xb, xnorm;
     bool shadow = false;
     bool bitmaps = false;               // level bitmaps for QW_PATH_BITMAP
-    DevBuf bm, bm_base, bm_nb, bm_lvl, bm_J, bid_prefix, prefix_off, perm, bm_sum;
+    DevBuf bm, bm_base, bm_nb, bm_lvl, bm_J, bid_prefix, prefix_off, perm, bm_sum, Xloc, inv;
     int bm_maxJ = 0;
     float xs = 1.0f;                 // 1 / RMS coordinate of the data (start-model features)
     qw_mlp *start_model = nullptr;   // not owned
@@ -110,6 +110,8 @@ struct qw_index {
         v.bid_prefix = bid_prefix.as<int64_t>();
         v.perm = perm.as<int32_t>();
         v.bm_sum = bm_sum.as<uint32_t>();
+        v.Xloc = Xloc.as<float>();
+        v.inv = inv.as<int32_t>();
         v.prefix_off = prefix_off.as<int64_t>();
         return v;
     }
@@ -392,6 +394,10 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
         QW_TRY(ix->bm_sum.ensure((size_t)lay.total * (kBmUint4 / 32) * sizeof(uint32_t)));
         QW_TRY(launch_bitmap_build(ix->view(), ix->c, ix->bm_maxJ, Ht.as<int32_t>(),
                                    ix->bm.as<uint4>(), ix->bm_sum.as<uint32_t>(), lay.total, s));
+        QW_TRY(ix->Xloc.ensure((size_t)n * d * sizeof(float)));
+        QW_TRY(ix->inv.ensure((size_t)n * sizeof(int32_t)));
+        QW_TRY(launch_locality_copy(ix->X.as<float>(), ix->perm.as<int32_t>(), n, d,
+                                    ix->Xloc.as<float>(), ix->inv.as<int32_t>(), s));
         QW_CUDA_TRY(cudaStreamSynchronize(s));  // the host order must outlive its upload
         QW_TRY(launch_bid_prefix(ix->view(), ix->bid_prefix.as<int64_t>(),
                                  ix->prefix_off.as<int64_t>(), s));
@@ -407,7 +413,8 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
                                  ix->dir_off.bytes + ix->dir_start.bytes + ix->dir_cnt.bytes +
                                  ix->bm.bytes + ix->bm_base.bytes + ix->bm_nb.bytes +
                                  ix->bm_lvl.bytes + ix->bm_J.bytes + ix->bid_prefix.bytes +
-                                 ix->prefix_off.bytes + ix->perm.bytes + ix->bm_sum.bytes);
+                                 ix->prefix_off.bytes + ix->perm.bytes + ix->bm_sum.bytes +
+                                 ix->Xloc.bytes + ix->inv.bytes);
     return QW_OK;
 }
 
@@ -886,7 +893,12 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                                           ids_b, dists_b, tm.on ? rows_ctr : nullptr, s);
             }));
         else if (want_ids)
-            QW_TRY(tm.run(QW_K_RERANK, 1, [&] { return launch_rerank(view, Qb, nb, k, cap, st, ids_b, dists_b, s); }));
+            QW_TRY(tm.run(QW_K_RERANK, 1, [&] {
+                // bitmap path: candidate rows from the locality-ordered copy
+                return use_bitmap ? launch_rerank(view, Qb, nb, k, cap, st, ids_b, dists_b, s,
+                                                  ix->Xloc.as<float>(), ix->inv.as<int32_t>())
+                                  : launch_rerank(view, Qb, nb, k, cap, st, ids_b, dists_b, s);
+            }));
         if (want_ids && tm.on)
             QW_TRY(launch_sum_i32(st.nkeep, nb, cand_ctr, s));
         if (order) {
@@ -1328,7 +1340,7 @@ void qw_index_free(qw_index *ix)
     DevBuf *bmb[] = {&ix->bm,  &ix->bm_base,    &ix->bm_nb,      &ix->bm_lvl,
                      &ix->bm_J, &ix->bid_prefix, &ix->prefix_off, &ix->w_cbits,
                      &ix->w_clist, &ix->perm, &ix->bm_sum, &ix->w_bmsel, &ix->w_ovf,
-                     &ix->w_bmwork};
+                     &ix->w_bmwork, &ix->Xloc, &ix->inv};
     for (DevBuf *bb : bmb) bb->release();
     for (cudaEvent_t e : ix->event_pool) cudaEventDestroy(e);
     level_graph_cache_free(ix->graphs);

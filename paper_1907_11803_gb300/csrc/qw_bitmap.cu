@@ -116,6 +116,18 @@ __global__ void __launch_bounds__(BM_THREADS) bm_fill_level0_kernel(IndexView ix
     }
 }
 
+// Row j of Xloc is data row perm[j]; inv is the inverse of perm.
+__global__ void locality_copy_kernel(const float *__restrict__ X, const int32_t *__restrict__ perm,
+                                     int64_t n, int d, float *__restrict__ Xloc,
+                                     int32_t *__restrict__ inv)
+{
+    for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+        const int64_t src = perm[j];
+        for (int c = threadIdx.x; c < d; c += blockDim.x) Xloc[j * d + c] = X[src * d + c];
+        if (threadIdx.x == 0) inv[src] = (int32_t)j;
+    }
+}
+
 // Per bitmap, one bit per 128-id group: the group has at least one id.
 __global__ void __launch_bounds__(BM_THREADS) bm_summary_kernel(const uint4 *__restrict__ bm,
                                                                 int64_t total,
@@ -875,7 +887,7 @@ __global__ void __launch_bounds__(SEL_THREADS) bm_select_kernel(IndexView ix, in
 // c^(L-1) already exceeded every useful radius of the query: such queries are
 // marked for the level path.  One block per marked query; the candidates of
 // one group are contiguous in the list (one thread appended them).
-constexpr int RC_THREADS = 256;
+constexpr int RC_THREADS = 64;
 constexpr int kRunCap = 2048;
 
 __global__ void __launch_bounds__(RC_THREADS) bm_recount_kernel(IndexView ix, int l, int cap,
@@ -1257,6 +1269,16 @@ qw_status launch_bm_level(const IndexView &ix, int nb, int level, int64_t R, int
     const int64_t items = (int64_t)nb * ix.nT;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n_sm, items));
     bm_level_tma_kernel<<<grid, TMA_THREADS, smem, s>>>(ix, level, R, l, nb, st, ctl, err);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
+
+qw_status launch_locality_copy(const float *X, const int32_t *perm, int64_t n, int d, float *Xloc,
+                               int32_t *inv, cudaStream_t s)
+{
+    if (n == 0) return QW_OK;
+    locality_copy_kernel<<<(unsigned)std::min<int64_t>(n, 152 * 64), 128, 0, s>>>(X, perm, n, d,
+                                                                                 Xloc, inv);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }

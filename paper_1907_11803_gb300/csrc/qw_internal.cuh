@@ -102,6 +102,8 @@ struct IndexView {
     const uint4 *bm;
     const int32_t *perm;
     const uint32_t *bm_sum;
+    const float *Xloc;        // the data in locality order (row j = data id perm[j])
+    const int32_t *inv;       // data id -> internal id
     const int64_t *bm_base;
     const int32_t *bm_nb;
     const int32_t *bm_lvl;
@@ -286,9 +288,15 @@ qw_status launch_rerank_bf16(const IndexView &ix, const void *Xb, const float *x
                              unsigned long long *rows_fp32, cudaStream_t s);
 qw_status launch_shadow_bf16(const float *X, int64_t n, int d, void *Xb, float *xnorm,
                              cudaStream_t s);
+// Xrows/row_of (optional): read data id `id` from row row_of[id] of Xrows
+// (the bitmap path's copy of the data in locality order).
 qw_status launch_rerank(const IndexView &ix, const float *Qb, int nb, int k, int cap,
                         const QueryState &st, int64_t *ids_out, float *dists_out,
-                        cudaStream_t s);
+                        cudaStream_t s, const float *Xrows = nullptr,
+                        const int32_t *row_of = nullptr);
+// The data in locality order (Xloc[j] = X[perm[j]]) and the inverse order.
+qw_status launch_locality_copy(const float *X, const int32_t *perm, int64_t n, int d, float *Xloc,
+                               int32_t *inv, cudaStream_t s);
 
 // The learned start model (qw_mlp.cu).
 int mlp_inputs(const qw_mlp *mp);

@@ -51,7 +51,10 @@ struct RerankSmem {
 
 // Stages 1-6 for the nc candidates whose ids are in sm.sid[0..nc), using P2
 // (a power of two >= nc) slots; writes the query's k results.
-__device__ void rerank_finish(const float *__restrict__ X, int d, const float *__restrict__ qv,
+// row_of (optional): the row of data id `id` in X is row_of[id] (X in the
+// bitmap path's locality order), else id.
+__device__ void rerank_finish(const float *__restrict__ X, const int32_t *__restrict__ row_of,
+                              int d, const float *__restrict__ qv,
                               int k, int P2, int nc, RerankSmem sm, int64_t *__restrict__ ids_q,
                               float *__restrict__ dists_q, bool vec)
 {
@@ -74,7 +77,7 @@ __device__ void rerank_finish(const float *__restrict__ X, int d, const float *_
 #pragma unroll
         for (int u = 0; u < kRows; ++u) {
             const int j = j0 + u;
-            xr[u] = j < nc ? X + (int64_t)sid[j] * d : nullptr;
+            xr[u] = j < nc ? X + (int64_t)(row_of ? row_of[sid[j]] : sid[j]) * d : nullptr;
             acc[u] = 0.0f;
         }
         if (vec) {
@@ -169,7 +172,7 @@ __device__ void rerank_finish(const float *__restrict__ X, int d, const float *_
     // 4. FP64 recomputation of the marked runs, in the reference order
     for (int j = threadIdx.x; j < P2; j += RR_THREADS) {
         if (j < nc && mark[j]) {
-            const float *x = X + (int64_t)sid[j] * d;
+            const float *x = X + (int64_t)(row_of ? row_of[sid[j]] : sid[j]) * d;
             double s = 0.0;
             for (int c = 0; c < d; ++c) {
                 double t = __dsub_rn((double)x[c], (double)qv[c]);
@@ -232,7 +235,8 @@ __device__ __forceinline__ RerankSmem carve_rerank(unsigned char *base, int P2, 
 }
 
 __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(
-    const float *__restrict__ X, int d, const float *__restrict__ Qb, int k, int cap, int P2,
+    const float *__restrict__ X, const int32_t *__restrict__ row_of, int d,
+    const float *__restrict__ Qb, int k, int cap, int P2,
     const int32_t *__restrict__ cand, const int32_t *__restrict__ nkeep,
     int64_t *__restrict__ ids_out, float *__restrict__ dists_out, bool vec)
 {
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(
     const int32_t *cl = cand + (int64_t)q * cap;
     for (int j = threadIdx.x; j < nc; j += RR_THREADS) sm.sid[j] = cl[j];
     __syncthreads();
-    rerank_finish(X, d, Qb + (int64_t)q * d, k, P2, nc, sm, ids_out + (int64_t)q * k,
+    rerank_finish(X, row_of, d, Qb + (int64_t)q * d, k, P2, nc, sm, ids_out + (int64_t)q * k,
                   dists_out + (int64_t)q * k, vec);
 }
 
@@ -359,7 +363,7 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_bf16_kernel(
     if (rows_fp32 && threadIdx.x == 0) atomicAdd(rows_fp32, (unsigned long long)ns);
     int P2s = 2;
     while (P2s < ns) P2s <<= 1;
-    rerank_finish(X, d, qv, k, P2s, ns, sm, ids_out + (int64_t)q * k, dists_out + (int64_t)q * k,
+    rerank_finish(X, nullptr, d, qv, k, P2s, ns, sm, ids_out + (int64_t)q * k, dists_out + (int64_t)q * k,
                   vec);
 }
 
@@ -387,17 +391,18 @@ qw_status launch_rerank_bf16(const IndexView &ix, const void *Xb, const float *x
 
 qw_status launch_rerank(const IndexView &ix, const float *Qb, int nb, int k, int cap,
                         const QueryState &st, int64_t *ids_out, float *dists_out,
-                        cudaStream_t s)
+                        cudaStream_t s, const float *Xrows, const int32_t *row_of)
 {
+    const float *X = Xrows ? Xrows : ix.X;
     int P2 = 2;
     while (P2 < cap) P2 <<= 1;
     const size_t smem = (size_t)P2 * (sizeof(double) + 2 * sizeof(float) + sizeof(int32_t) + 1);
     QW_CUDA_TRY(cudaFuncSetAttribute(rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     // 16-byte row loads need d % 4 == 0 and 16-byte aligned bases
-    const bool vec = (ix.d % 4 == 0) && ((uintptr_t)Qb % 16 == 0) && ((uintptr_t)ix.X % 16 == 0);
-    rerank_kernel<<<nb, RR_THREADS, smem, s>>>(ix.X, ix.d, Qb, k, cap, P2, st.cand, st.nkeep,
-                                               ids_out, dists_out, vec);
+    const bool vec = (ix.d % 4 == 0) && ((uintptr_t)Qb % 16 == 0) && ((uintptr_t)X % 16 == 0);
+    rerank_kernel<<<nb, RR_THREADS, smem, s>>>(X, row_of, ix.d, Qb, k, cap, P2, st.cand,
+                                               st.nkeep, ids_out, dists_out, vec);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }
