@@ -220,9 +220,10 @@ def kernel_source_sha(kernel: str) -> str:
 
 
 def ncu_traffic(kernel: str, workload: str):
-    """Per-launch DRAM bytes (read + write) of a kernel from the committed ncu
-    summary profiles/traffic.txt, if that was taken on the current source of
-    the kernel (lines: kernel workload source-sha bytes-per-launch)."""
+    """DRAM bytes (read + write) per timed step of a kernel class from the
+    committed ncu summary profiles/traffic.txt, if that was taken on the
+    current source of the kernel (lines: kernel workload source-sha
+    bytes-per-step)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     sha = kernel_source_sha(kernel)
     try:
@@ -458,14 +459,16 @@ def run_ours(args):
         if bitmap else "level_kernel")
     roofline = {"kernel": dom_name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                "traffic": ncu_traffic(kname, args.workload), "peak_kind": peak_kind,
+                "traffic": (lambda t: None if t is None else t / max(dom_launches, 1))(
+                    ncu_traffic(kname, args.workload)), "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": per_launch_bytes,
                 "avg_launch_ms": per_launch_s * 1e3, "launches_per_step": dom_launches,
                 "share_of_step": round(dom_ms / (ms / steps), 4)}
     roofline_gather = {"kernel": "rerank_kernel (candidate gather + L2 + top-k)", "bound": "hbm",
                        "achieved": round(rr_achieved, 1), "peak": hbm,
                        "frac": round(rr_achieved / hbm, 4), "unit": "GB/s",
-                       "traffic": ncu_traffic("rerank_kernel", args.workload),
+                       "traffic": (lambda t: None if t is None else t / max(rr_launches, 1))(
+                           ncu_traffic("rerank_kernel", args.workload)),
                        "algorithmic_bytes_per_launch": rr_bytes / max(rr_launches, 1),
                        "avg_launch_ms": rr_ms / max(rr_launches, 1)}
     launches = int(sum(prof["launches"].values()))
