@@ -145,15 +145,19 @@ __device__ void rerank_finish(const float *__restrict__ X, const int32_t *__rest
         }
     }
 
-    // 3. runs of neighbours whose order FP32 cannot certify
+    // 3. runs of neighbours whose order FP32 cannot certify.  The test runs in
+    //    FP32 with the bound raised by 2^-20: fl(b - a) and fl(rho (a + b)) are
+    //    each within one rounding of the real values, so every pair the real
+    //    test flags is flagged here
     const double rho = (double)((d + 31) / 32 + 12) * 5.9604644775390625e-08 * 1.02;
+    const float rhof = (float)(rho * (1.0 + 9.5367431640625e-07));
     const int per = (P2 + RR_THREADS - 1) / RR_THREADS;
     const int j0 = threadIdx.x * per;
     const int j1 = min(P2, j0 + per);
     auto gap_uncertain = [&](int j) -> bool {  // between j and j + 1
         if (j < 0 || j + 1 >= nc) return false;
-        double a = (double)d32[j], b = (double)d32[j + 1];
-        return (b - a) <= rho * (a + b) * 1.0000001;
+        const float a = d32[j], b = d32[j + 1];
+        return (b - a) <= rhof * (a + b);
     };
     int last_start = -1;
     for (int j = j0; j < j1; ++j)
@@ -187,28 +191,31 @@ __device__ void rerank_finish(const float *__restrict__ X, const int32_t *__rest
     }
     __syncthreads();
 
-    // 5. re-sort on the certified keys when anything was recomputed
+    // 5. re-sort every recomputed run on (FP64 value, id).  Runs are bounded by
+    //    certain gaps, across which the FP64 values keep the FP32 order, so
+    //    sorting each run in place equals re-sorting the whole array
     if (*sm.any_mark) {
-        for (int kk = 2; kk <= P2; kk <<= 1) {
-            for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-                for (int x = threadIdx.x; x < (P2 >> 1); x += RR_THREADS) {
-                    int a = 2 * x - (x & (jj - 1));
-                    int c = a + jj;
-                    bool up = (a & kk) == 0;
-                    double ka = key[a], kc = key[c];
-                    int32_t ia = sid[a], ic = sid[c];
-                    bool gt = (ka > kc) || (ka == kc && ia > ic);
-                    if (gt == up) {
-                        key[a] = kc; key[c] = ka;
-                        sid[a] = ic; sid[c] = ia;
-                        float oa = outd[a];
-                        outd[a] = outd[c];
-                        outd[c] = oa;
-                    }
+        for (int j = threadIdx.x; j < nc; j += RR_THREADS) {
+            if (!mark[j] || (j > 0 && mark[j - 1] && gap_uncertain(j - 1))) continue;
+            int e = j + 1;
+            while (e < nc && mark[e] && gap_uncertain(e - 1)) ++e;
+            for (int a = j + 1; a < e; ++a) {  // insertion sort of [j, e)
+                const double ka = key[a];
+                const int32_t ia = sid[a];
+                const float oa = outd[a];
+                int b = a - 1;
+                while (b >= j && (key[b] > ka || (key[b] == ka && sid[b] > ia))) {
+                    key[b + 1] = key[b];
+                    sid[b + 1] = sid[b];
+                    outd[b + 1] = outd[b];
+                    --b;
                 }
-                __syncthreads();
+                key[b + 1] = ka;
+                sid[b + 1] = ia;
+                outd[b + 1] = oa;
             }
         }
+        __syncthreads();
     }
 
     // 6. the k nearest
