@@ -607,7 +607,10 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         (path == QW_PATH_AUTO || path == ix->tuned_path))
         B = ix->tuned_batch;
     if (B == 0) {
-        const int64_t budget = (int64_t)2 << 30;  // counters of one batch
+        // workspace of one batch: 2 GB of counters on the level path; the
+        // bitmap path (about 0.5 MB per query at 1M points) takes up to 8 GB,
+        // a small share of the 280 GB HBM, so most workloads run as one batch
+        const int64_t budget = use_bitmap ? (int64_t)8 << 30 : (int64_t)2 << 30;
         B = use_cluster ? (int64_t)65535
                         : std::max<int64_t>(1, budget / (use_bitmap ? cb_bytes + cl_bytes
                                                                     : wpq_bytes));
@@ -630,7 +633,9 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         const size_t items = (size_t)B * ix->nT;
         QW_TRY(ix->w_bmwork.ensure(16 + items * (sizeof(int2) + (size_t)m * sizeof(int64_t)) +
                                    items * kBmUint4 * sizeof(int32_t) +
-                                   2 * items * (kBmUint4 / 32) * sizeof(uint32_t)));
+                                   2 * items * (kBmUint4 / 32) * sizeof(uint32_t) +
+                                   items * kBmUint4 * (size_t)((m + 63) / 64) * 8 +
+                                   (size_t)B * m * sizeof(int64_t)));
         QW_TRY(ix->w_ovf.ensure(((size_t)nq + 1) * sizeof(int32_t)));
     }
     QW_TRY(ix->w_cand.ensure((size_t)B * cap * 2 * sizeof(int32_t)));
@@ -741,6 +746,8 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         st.bm_work = reinterpret_cast<int32_t *>(wp + 16 + items * sizeof(int2) +
                                                  items * m * sizeof(int64_t));
         st.bm_amask = reinterpret_cast<uint32_t *>(st.bm_work + items * kBmUint4);
+        st.bm_wmask = reinterpret_cast<unsigned long long *>(st.bm_amask + 2 * items * (kBmUint4 / 32));
+        st.bm_bq = reinterpret_cast<int64_t *>(st.bm_wmask + items * kBmUint4 * ((m + 63) / 64));
         st.bm_item_cap = (int32_t)std::min<int64_t>(items, (int64_t)1 << 23);
         st.bm_work_cap = (int32_t)std::min<int64_t>(items * kBmUint4, INT32_MAX);
     }
@@ -1155,7 +1162,7 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
                                  (int64_t)ix->nT * (int64_t)sizeof(int32_t) * 2 +
                                  ((int64_t)kQCap * (int64_t)sizeof(uint64_t) + 4) * 2;
             const int64_t bdef = std::min<int64_t>(
-                std::min<int64_t>(std::max<int64_t>(1, ((int64_t)2 << 30) / cb_b), nq), 65535);
+                std::min<int64_t>(std::max<int64_t>(1, ((int64_t)8 << 30) / cb_b), nq), 65535);
             const int64_t bc[2] = {bdef / 16, bdef / 4};
             const qw_query_params keepb = cur;
             for (int64_t bb : bc) {

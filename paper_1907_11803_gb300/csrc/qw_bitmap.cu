@@ -306,76 +306,138 @@ __device__ __forceinline__ int64_t bm_index(const IndexView &ix, int i, int t, i
 constexpr int FL_WARPS = 8;                   // warps per block in pass 1
 constexpr int kSumWords = kBmUint4 / 32;      // summary words per bitmap (8)
 
-__global__ void __launch_bounds__(FL_WARPS * 32) bm_filter_kernel(IndexView ix, int level,
-                                                                  int64_t R, int l, int nb,
-                                                                  QueryState st,
-                                                                  const LoopCtl *ctl)
+// Before pass 1, per (query, projection): the bitmap number of the query's
+// bucket at this level in tile 0 (tile t adds t * bm_nb[i]), or -1 when the
+// bucket holds no data.  Also clears the pass's item and work counters.
+__global__ void bm_bucket_kernel(IndexView ix, int level, int64_t R, int nb, QueryState st,
+                                 const LoopCtl *ctl)
 {
-    __shared__ int64_t wbi[FL_WARPS][QW_MAX_M + 1];
-    __shared__ uint32_t wsum[FL_WARPS][QW_MAX_M + 1][kSumWords];
-    __shared__ uint32_t walive[FL_WARPS][kSumWords];
     if (ctl) {
         level = ctl->level;
         R = ctl->R;
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st.bm_nitems[0] = 0;
+        st.bm_nwork[0] = 0;
+    }
+    const int m = ix.m;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)nb * m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(e / m), i = (int)(e % m);
+        if (!st.active[q] || level < st.start[q]) continue;
+        st.bm_bq[e] = bm_index(ix, i, 0, level, R, floordiv64(st.g[e], R));
+    }
+}
+
+// Bit transpose of a 32 x 32 block held one row per lane (bit b of lane i's
+// word is element (i, b)): returns column `lane`, whose bit i is element
+// (i, lane).  Five butterfly steps, each exchanging the off-diagonal halves
+// of the blocks of that size.
+__device__ __forceinline__ uint32_t transpose32(uint32_t a, int lane)
+{
+    const uint32_t keep[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int j = 16 >> s;
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, a, j);
+        a = (lane & j) ? (a & ~keep[s]) | ((y >> j) & keep[s])
+                       : (a & keep[s]) | ((y << j) & ~keep[s]);
+    }
+    return a;
+}
+
+// One warp per (query, run of FL_TILES tiles).  Lane j holds the summaries of
+// projections j, j + 32, ... (32 bytes each, two vector loads; the next tile's
+// are loaded while the current one is counted).  For each summary word, the
+// bit transpose of the lanes' rows gives lane g the projections touching group
+// w * 32 + g: their number decides whether the group is live, and the same
+// bits are the group's projection mask for pass 2.
+constexpr int FL_TILES = 8;
+
+template <int NROW>
+__device__ __forceinline__ void load_summaries(const IndexView &ix, const int64_t (&b0)[NROW],
+                                               const int32_t (&nbp)[NROW], int t,
+                                               uint4 (&sv)[NROW][2])
+{
+#pragma unroll
+    for (int r = 0; r < NROW; ++r) {
+        if (b0[r] >= 0) {
+            const uint4 *p = reinterpret_cast<const uint4 *>(
+                ix.bm_sum + (b0[r] + (int64_t)t * nbp[r]) * kSumWords);
+            sv[r][0] = __ldg(p);
+            sv[r][1] = __ldg(p + 1);
+        } else {
+            sv[r][0] = make_uint4(0, 0, 0, 0);
+            sv[r][1] = make_uint4(0, 0, 0, 0);
+        }
+    }
+}
+
+template <int NROW>
+__global__ void __launch_bounds__(FL_WARPS * 32, NROW <= 2 ? 3 : 2) bm_filter_kernel(IndexView ix, int level, int l,
+                                                                  int nb, QueryState st,
+                                                                  const LoopCtl *ctl)
+{
+    constexpr int MW = (NROW + 1) / 2;
+    // per warp: the projection masks of the current tile's groups
+    __shared__ unsigned long long wmk[FL_WARPS][kSumWords][MW][32];
+    if (ctl) level = ctl->level;
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const int m = ix.m, nT = ix.nT;
-    const int64_t items = (int64_t)nb * nT;
-    for (int64_t k = (int64_t)blockIdx.x * FL_WARPS + wi; k < items;
+    const int mw = (m + 63) >> 6;
+    const int nch = (nT + FL_TILES - 1) / FL_TILES;
+    const int64_t tasks = (int64_t)nb * nch;
+    const int par = level & 1;
+    for (int64_t k = (int64_t)blockIdx.x * FL_WARPS + (threadIdx.x >> 5); k < tasks;
          k += (int64_t)gridDim.x * FL_WARPS) {
-        const int q = (int)(k / nT), t = (int)(k % nT);
+        const int q = (int)(k / nch);
+        const int t0 = (int)(k % nch) * FL_TILES, t1 = min(nT, t0 + FL_TILES);
         if (!st.active[q] || level < st.start[q]) continue;
-        const int64_t qt = (int64_t)q * nT + t;
-        for (int i = lane; i < m; i += 32)
-            wbi[wi][i] = bm_index(ix, i, t, level, R, floordiv64(st.g[(int64_t)q * m + i], R));
-        __syncwarp();
-        for (int e = lane; e < m * kSumWords; e += 32) {
-            const int i = e / kSumWords, w = e % kSumWords;
-            const int64_t b = wbi[wi][i];
-            wsum[wi][i][w] = b >= 0 ? ix.bm_sum[b * kSumWords + w] : 0u;
+        int64_t b0[NROW];
+        int32_t nbp[NROW];
+#pragma unroll
+        for (int r = 0; r < NROW; ++r) {
+            const int i = lane + 32 * r;
+            b0[r] = i < m ? st.bm_bq[(int64_t)q * m + i] : -1;
+            nbp[r] = i < m ? ix.bm_nb[i] : 0;
         }
-        __syncwarp();
-        if (lane < kSumWords) {
-            // bit planes of the number of touching buckets, 32 groups per lane
-            uint32_t p[7] = {0, 0, 0, 0, 0, 0, 0};
-            for (int i0 = 0; i0 < m; i0 += 8) {
-                uint32_t xs[8];
+        uint4 sv[NROW][2];
+        load_summaries<NROW>(ix, b0, nbp, t0, sv);
+        for (int t = t0; t < t1; ++t) {
+            uint4 cur[NROW][2];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) xs[u] = i0 + u < m ? wsum[wi][i0 + u][lane] : 0u;
-                uint32_t t2a, t2b, t4a, t4b, t8;
-                csa(t2a, p[0], p[0], xs[0], xs[1]);
-                csa(t2b, p[0], p[0], xs[2], xs[3]);
-                csa(t4a, p[1], p[1], t2a, t2b);
-                csa(t2a, p[0], p[0], xs[4], xs[5]);
-                csa(t2b, p[0], p[0], xs[6], xs[7]);
-                csa(t4b, p[1], p[1], t2a, t2b);
-                csa(t8, p[2], p[2], t4a, t4b);
-                uint32_t cy = t8, nx;
-                nx = p[3] & cy; p[3] ^= cy; cy = nx;
-                nx = p[4] & cy; p[4] ^= cy; cy = nx;
-                nx = p[5] & cy; p[5] ^= cy; cy = nx;
-                p[6] ^= cy;
+            for (int r = 0; r < NROW; ++r) {
+                cur[r][0] = sv[r][0];
+                cur[r][1] = sv[r][1];
             }
-            uint32_t gt = 0, eq = 0xffffffffu;
+            if (t + 1 < t1) load_summaries<NROW>(ix, b0, nbp, t + 1, sv);
+            const int64_t qt = (int64_t)q * nT + t;
+            uint32_t x[kSumWords];
+            int n_alive = 0;
 #pragma unroll
-            for (int kk = 6; kk >= 0; --kk) {
-                if ((l >> kk) & 1) {
-                    eq &= p[kk];
-                } else {
-                    gt |= eq & p[kk];
-                    eq &= ~p[kk];
+            for (int w = 0; w < kSumWords; ++w) {
+                int cnt = 0;
+                unsigned long long mk[MW];
+#pragma unroll
+                for (int h = 0; h < MW; ++h) mk[h] = 0ull;
+#pragma unroll
+                for (int r = 0; r < NROW; ++r) {
+                    const uint32_t c = transpose32(word_of(cur[r][w >> 2], w & 3), lane);
+                    cnt += __popc(c);
+                    mk[r >> 1] |= (unsigned long long)c << (32 * (r & 1));
                 }
+#pragma unroll
+                for (int h = 0; h < MW; ++h) wmk[wi][w][h][lane] = mk[h];
+                x[w] = __ballot_sync(0xffffffffu, cnt >= l);
+                n_alive += __popc(x[w]);
             }
-            walive[wi][lane] = gt | eq;
-        }
-        __syncwarp();
-        const uint32_t aw = lane < kSumWords ? walive[wi][lane] : 0u;
-        const int n_alive = __reduce_add_sync(0xffffffffu, __popc(aw));
-        if (lane == 0) st.clist_n[(int64_t)(level & 1) * st.cln_par + qt] = 0;
-        if (n_alive > 0) {
+            if (lane == 0) st.clist_n[(int64_t)par * st.cln_par + qt] = 0;
+            if (n_alive == 0) continue;
             // which groups have a candidate word at this level
-            if (lane < kSumWords)
-                st.bm_amask[((int64_t)(level & 1) * st.cln_par + qt) * kSumWords + lane] = aw;
+            uint32_t xl = 0;
+#pragma unroll
+            for (int w = 0; w < kSumWords; ++w) xl = lane == w ? x[w] : xl;
+            if (lane < kSumWords) st.bm_amask[((int64_t)par * st.cln_par + qt) * kSumWords + lane] = xl;
             int slot = 0, base = 0;
             if (lane == 0) {
                 slot = atomicAdd(st.bm_nitems, 1);
@@ -383,23 +445,29 @@ __global__ void __launch_bounds__(FL_WARPS * 32) bm_filter_kernel(IndexView ix, 
             }
             slot = __shfl_sync(0xffffffffu, slot, 0);
             base = __shfl_sync(0xffffffffu, base, 0);
-            if (slot < st.bm_item_cap) {
-                for (int i = lane; i < m; i += 32) st.bm_item_bi[(int64_t)slot * m + i] = wbi[wi][i];
-                if (lane == 0) st.bm_item_qt[slot] = make_int2(q, t);
-                // live groups of the tile, in ascending order, after `base`
-                int pos = base;
-                for (int w = 0; w < kSumWords; ++w) {
-                    const uint32_t x = walive[wi][w];
-                    const int before = __popc(x & ((1u << lane) - 1u));
-                    if ((x >> lane) & 1u) {
-                        const int at = pos + before;
-                        if (at < st.bm_work_cap) st.bm_work[at] = (slot << 8) | (w * 32 + lane);
+            if (slot >= st.bm_item_cap) continue;
+#pragma unroll
+            for (int r = 0; r < NROW; ++r)
+                if (lane + 32 * r < m)
+                    st.bm_item_bi[(int64_t)slot * m + lane + 32 * r] =
+                        b0[r] >= 0 ? b0[r] + (int64_t)t * nbp[r] : -1;
+            if (lane == 0) st.bm_item_qt[slot] = make_int2(q, t);
+            // live groups of the tile, in ascending order, after `base`
+            int pos = base;
+#pragma unroll
+            for (int w = 0; w < kSumWords; ++w) {
+                if ((x[w] >> lane) & 1u) {
+                    const int at = pos + __popc(x[w] & ((1u << lane) - 1u));
+                    if (at < st.bm_work_cap) {
+                        st.bm_work[at] = (slot << 8) | (w * 32 + lane);
+#pragma unroll
+                        for (int h = 0; h < MW; ++h)
+                            if (h < mw) st.bm_wmask[(int64_t)at * mw + h] = wmk[wi][w][h][lane];
                     }
-                    pos += __popc(x);
                 }
+                pos += __popc(x[w]);
             }
         }
-        __syncwarp();
     }
 }
 
@@ -437,13 +505,18 @@ __global__ void __launch_bounds__(256, 3) bm_count_kernel(IndexView ix, int leve
         for (int kk = 0; kk < 7; ++kk)
 #pragma unroll
             for (int w = 0; w < 4; ++w) P.s[kk][w] = 0;
+        // words of projections whose summary misses the group are zero
+        const int mw = (m + 63) >> 6;
+        const unsigned long long mk0 = st.bm_wmask[(int64_t)wk * mw];
+        const unsigned long long mk1 = mw > 1 ? st.bm_wmask[(int64_t)wk * mw + 1] : 0ull;
         for (int i0 = 0; i0 < m; i0 += 8) {
+            const uint32_t bits = (uint32_t)(((i0 < 64 ? mk0 : mk1) >> (i0 & 63)) & 0xffu);
+            if (bits == 0) continue;
             uint4 x[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int64_t b = i0 + u < m ? bi[i0 + u] : -1;
-                x[u] = b >= 0 ? __ldg(ix.bm + b * kBmUint4 + g) : make_uint4(0, 0, 0, 0);
-            }
+            for (int u = 0; u < 8; ++u)
+                x[u] = (bits >> u) & 1u ? __ldg(ix.bm + bi[i0 + u] * kBmUint4 + g)
+                                        : make_uint4(0, 0, 0, 0);
             add8(P, x);
         }
         const uint4 cand = candidates_of(P, l);
@@ -1246,11 +1319,19 @@ qw_status launch_bm_level(const IndexView &ix, int nb, int level, int64_t R, int
     (void)cgrow;
     if (!tma) {
         // two passes: filter on the summaries, then count the live groups
-        QW_CUDA_TRY(cudaMemsetAsync(st.bm_nitems, 0, 2 * sizeof(int32_t), s));
-        const int64_t items = (int64_t)nb * ix.nT;
+        const int64_t qi = (int64_t)nb * ix.m;
+        bm_bucket_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((qi + 255) / 256, 152 * 8)),
+                           256, 0, s>>>(ix, level, R, nb, st, ctl);
+        QW_CUDA_TRY(cudaGetLastError());
+        const int64_t tasks = (int64_t)nb * ((ix.nT + FL_TILES - 1) / FL_TILES);
         const int fl_blocks = (int)std::max<int64_t>(
-            1, std::min<int64_t>((items + FL_WARPS - 1) / FL_WARPS, 152 * 16));
-        bm_filter_kernel<<<fl_blocks, FL_WARPS * 32, 0, s>>>(ix, level, R, l, nb, st, ctl);
+            1, std::min<int64_t>((tasks + FL_WARPS - 1) / FL_WARPS, 152 * 16));
+        if (ix.m <= 32)
+            bm_filter_kernel<1><<<fl_blocks, FL_WARPS * 32, 0, s>>>(ix, level, l, nb, st, ctl);
+        else if (ix.m <= 64)
+            bm_filter_kernel<2><<<fl_blocks, FL_WARPS * 32, 0, s>>>(ix, level, l, nb, st, ctl);
+        else
+            bm_filter_kernel<4><<<fl_blocks, FL_WARPS * 32, 0, s>>>(ix, level, l, nb, st, ctl);
         QW_CUDA_TRY(cudaGetLastError());
         bm_count_kernel<<<152 * 8, 256, 0, s>>>(ix, level, l, st, ctl);
         QW_CUDA_TRY(cudaGetLastError());

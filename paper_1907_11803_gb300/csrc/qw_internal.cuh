@@ -181,9 +181,13 @@ struct QueryState {
     int32_t *bm_nitems = nullptr;   // 2 counters: items, work entries (per level)
     int32_t *bm_nwork = nullptr;
     int2 *bm_item_qt = nullptr;
+    int64_t *bm_bq = nullptr;       // per (query, projection): bitmap number in tile 0, or -1
     int64_t *bm_item_bi = nullptr;
     uint32_t *bm_amask = nullptr;   // per (level parity, query, tile): live groups, 8 words
     int32_t *bm_work = nullptr;
+    // per work entry, (m + 63) / 64 words: the projections whose bucket touches
+    // the group (its summary bit); the others' words are zero and not read
+    unsigned long long *bm_wmask = nullptr;
     int32_t bm_item_cap = 0;
     int32_t bm_work_cap = 0;
     unsigned long long *bm_prof = nullptr;  // profile mode: live items, live groups (summed)

@@ -15,9 +15,10 @@ DIST_RTOL = 1e-5
 TILE = 32768
 # "graph": the level path with its level loop run as a CUDA graph; "bitmap":
 # counts from the index's level bitmaps staged by TMA ("bitmap_graph": the same
-# in graph mode; "bitmap_direct": plain loads, one CTA per tile and query)
+# in graph mode; "bitmap_direct": summary filter then counts of the live groups
+# by plain loads; "bitmap_direct_graph": the same in graph mode)
 PATHS = pytest.mark.parametrize("path", ["levels", "cluster", "graph", "bitmap", "bitmap_graph",
-                                         "bitmap_direct"])
+                                         "bitmap_direct", "bitmap_direct_graph"])
 
 
 def _t(x, dev):
@@ -65,9 +66,10 @@ def _gpu_workload(qw, dev, X, Q, A, b, *, w, k, v, l, c=2, batch=0, host=False, 
         Xd, Qd, Ad, bd = _t(X, dev), _t(Q, dev), _t(A, dev), _t(b, dev)
     index = qw.Index(Xd, Ad, bd, w=w, c=c, v=v, l=l, shadow_bf16=(rerank == "bf16"),
                      bitmaps=path.startswith("bitmap"))
-    graph = path in ("graph", "bitmap_graph")
-    loads = "direct" if path == "bitmap_direct" else "tma"
-    path = {"graph": "levels", "bitmap_graph": "bitmap", "bitmap_direct": "bitmap"}.get(path, path)
+    graph = path in ("graph", "bitmap_graph", "bitmap_direct_graph")
+    loads = "direct" if path.startswith("bitmap_direct") else "tma"
+    path = {"graph": "levels", "bitmap_graph": "bitmap", "bitmap_direct": "bitmap",
+            "bitmap_direct_graph": "bitmap"}.get(path, path)
     ids, dists, st = index.query(Qd, k, batch=batch, stats=True, path=path, order=order,
                                  rerank=rerank, graph=graph, loads=loads)
     cid, ccol, st2 = index.candidates(Qd, k, batch=batch, path=path, order=order, graph=graph,
@@ -230,6 +232,17 @@ def test_workload_tiny_index(orc, qwlib, cuda, path):
 def test_workload_k_equals_n(orc, qwlib, cuda, path):
     wl = workloads.make_workload("mix10k_d32", seed=8, n=64, nq=5, n_clusters=3)
     _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=64, v=0, l=4, path=path)
+
+
+@pytest.mark.parametrize("path", ["bitmap_direct", "bitmap_direct_graph", "bitmap"])
+@pytest.mark.parametrize("m", [40, 100, 127])
+def test_bitmap_many_projections(orc, qwlib, cuda, path, m):
+    """More than 32 and more than 64 projections: a tile's bucket summaries
+    span two or four lanes' rows in the filter, and a live group's projection
+    mask one or two words."""
+    wl = workloads.make_workload("mix10k_d32", seed=40 + m, n=TILE + 5000, nq=24, d=32, m=m,
+                                 n_clusters=30)
+    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=10, v=60, path=path)
 
 
 def test_empty_workload(qwlib, cuda):
