@@ -19,6 +19,11 @@
 // FP32 value otherwise, id).  The runs are separated from everything else by
 // certain gaps, so the first k ids are exactly those of the FP64 order, ties
 // broken by the smaller id.
+// Only a prefix of the sorted order matters: the positions up to the end of
+// the run holding position k - 1.  Its last value T is found without sorting
+// (radix selection of the k-th smallest FP32 value, then the next larger
+// value while the gap to it is uncertain), and only the candidates with FP32
+// distance <= T are sorted; the other stages see exactly that prefix.
 #include "qw_internal.cuh"
 #include "qw_scan.cuh"
 
@@ -38,7 +43,8 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-// Shared-memory arrays of one query's rerank (P2 entries each).
+// Shared-memory arrays of one query's rerank (P2 entries each), and small
+// scratch: scan_tmp (RR_WARPS ints), hist (256 ints), bc (4 ints).
 struct RerankSmem {
     double *key;
     float *d32;
@@ -47,7 +53,111 @@ struct RerankSmem {
     uint8_t *mark;
     int *scan_tmp;
     int *any_mark;
+    int *hist;
+    int *bc;
 };
+
+// Bitonic sort of P (a power of two) (key, id) pairs on (key, id), by the
+// whole block, or by warp 0 alone when `one_warp` (the other warps skip it;
+// the caller synchronises the block afterwards).
+__device__ __forceinline__ void sort_pairs(float *kf, int32_t *id, int P, bool one_warp)
+{
+    const int step = one_warp ? 32 : RR_THREADS;
+    if (one_warp && threadIdx.x >= 32) return;
+    for (int kk = 2; kk <= P; kk <<= 1) {
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int x = threadIdx.x; x < (P >> 1); x += step) {
+                const int a = 2 * x - (x & (jj - 1));
+                const int c = a + jj;
+                const bool up = (a & kk) == 0;
+                const float ka = kf[a], kc = kf[c];
+                const int32_t ia = id[a], ic = id[c];
+                const bool gt = (ka > kc) || (ka == kc && ia > ic);
+                if (gt == up) {
+                    kf[a] = kc;
+                    kf[c] = ka;
+                    id[a] = ic;
+                    id[c] = ia;
+                }
+            }
+            if (one_warp) __syncwarp();
+            else __syncthreads();
+        }
+    }
+}
+
+// The kk-th smallest (1-based, kk <= n) of n non-negative FP32 values, by
+// radix selection on their bit patterns (ordered like the values), 8 bits a
+// pass.  Block-wide; returns the value in every thread.
+__device__ float kth_smallest(const float *v, int n, int kk, int *hist, int *bc)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t prefix = 0, mask = 0;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int i = threadIdx.x; i < 256; i += RR_THREADS) hist[i] = 0;
+        __syncthreads();
+        // most values share the leading bits: one atomic per distinct bin of a warp
+        for (int j0 = 0; j0 < n; j0 += RR_THREADS) {
+            const int j = j0 + threadIdx.x;
+            const uint32_t u = j < n ? __float_as_uint(v[j]) : 0u;
+            const bool in = j < n && (u & mask) == prefix;
+            const uint32_t bin = in ? (u >> shift) & 255u : 256u + lane;
+            const uint32_t peers = __match_any_sync(0xffffffffu, bin);
+            if (in && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            // bin holding the kk-th: lane sums 8 bins, warp scan, then the lane
+            // where the running count reaches kk walks its bins
+            int c[8], sl = 0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                c[u] = hist[lane * 8 + u];
+                sl += c[u];
+            }
+            int incl = sl;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += y;
+            }
+            const int excl = incl - sl;
+            if (excl < kk && kk <= incl) {
+                int cum = excl;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (cum < kk && kk <= cum + c[u]) {
+                        bc[0] = lane * 8 + u;
+                        bc[1] = kk - cum;
+                    }
+                    cum += c[u];
+                }
+            }
+        }
+        __syncthreads();
+        prefix |= (uint32_t)bc[0] << shift;
+        mask |= 255u << shift;
+        kk = bc[1];
+        __syncthreads();
+    }
+    return __uint_as_float(prefix);
+}
+
+// Smallest of the n values above t, as bits (0xffffffff: none).  Block-wide.
+__device__ uint32_t min_above(const float *v, int n, float t, int *bc)
+{
+    uint32_t mn = 0xffffffffu;
+    for (int j = threadIdx.x; j < n; j += RR_THREADS)
+        if (v[j] > t) mn = min(mn, __float_as_uint(v[j]));
+    mn = __reduce_min_sync(0xffffffffu, mn);
+    if (threadIdx.x == 0) bc[2] = (int)0xffffffffu;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicMin(reinterpret_cast<unsigned int *>(bc + 2), mn);
+    __syncthreads();
+    const uint32_t r = (uint32_t)bc[2];
+    __syncthreads();
+    return r;
+}
 
 // Stages 1-6 for the nc candidates whose ids are in sm.sid[0..nc), using P2
 // (a power of two >= nc) slots; writes the query's k results.
@@ -66,18 +176,25 @@ __device__ void rerank_finish(const float *__restrict__ X, const int32_t *__rest
     int *scan_tmp = sm.scan_tmp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) *sm.any_mark = 0;
+    const double rho = (double)((d + 31) / 32 + 12) * 5.9604644775390625e-08 * 1.02;
+    const float rhof = (float)(rho * (1.0 + 9.5367431640625e-07));
+
+    // 0. the data row of every candidate (staged in `key`, free until stage 4)
+    int32_t *rowi = reinterpret_cast<int32_t *>(key);
+    for (int j = threadIdx.x; j < nc; j += RR_THREADS) rowi[j] = row_of ? row_of[sid[j]] : sid[j];
+    __syncthreads();
 
     // 1. FP32 squared distances: a warp takes kRows candidate rows at a time,
     //    so each lane has kRows independent loads in flight; every row keeps
     //    its own per-lane chain and butterfly sum (the order rho covers)
     constexpr int kRows = 4;
-    for (int j0 = warp * kRows; j0 < P2; j0 += RR_WARPS * kRows) {
+    for (int j0 = warp * kRows; j0 < nc; j0 += RR_WARPS * kRows) {
         const float *xr[kRows];
         float acc[kRows];
 #pragma unroll
         for (int u = 0; u < kRows; ++u) {
             const int j = j0 + u;
-            xr[u] = j < nc ? X + (int64_t)(row_of ? row_of[sid[j]] : sid[j]) * d : nullptr;
+            xr[u] = j < nc ? X + (int64_t)rowi[j] * d : nullptr;
             acc[u] = 0.0f;
         }
         if (vec) {
@@ -112,45 +229,77 @@ __device__ void rerank_finish(const float *__restrict__ X, const int32_t *__rest
 #pragma unroll
         for (int u = 0; u < kRows; ++u) {
             const int j = j0 + u;
-            if (j >= P2) break;
             const float sum = warp_sum(acc[u]);
-            if (lane == 0) {
-                if (j < nc) {
-                    d32[j] = sum;
-                } else {
-                    d32[j] = CUDART_INF_F;
-                    sid[j] = INT32_MAX;
-                }
-            }
+            if (lane == 0 && j < nc) d32[j] = sum;
         }
     }
     __syncthreads();
 
-    // 2. sort by (FP32 distance, id)
-    for (int kk = 2; kk <= P2; kk <<= 1) {
-        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-            for (int x = threadIdx.x; x < (P2 >> 1); x += RR_THREADS) {
-                int a = 2 * x - (x & (jj - 1));
-                int c = a + jj;
-                bool up = (a & kk) == 0;
-                float ka = d32[a], kc = d32[c];
-                int32_t ia = sid[a], ic = sid[c];
-                bool gt = (ka > kc) || (ka == kc && ia > ic);
-                if (gt == up) {
-                    d32[a] = kc; d32[c] = ka;
-                    sid[a] = ic; sid[c] = ia;
+    // 2. the prefix of the (FP32 distance, id) order that decides the result:
+    //    T = the k-th smallest distance, extended while the gap to the next
+    //    larger distance is uncertain (at most kExtend times, else the whole
+    //    array is sorted); the candidates with distance <= T, sorted
+    constexpr int kExtend = 16;
+    bool whole = nc <= k;
+    if (!whole) {
+        float T = kth_smallest(d32, nc, k, sm.hist, sm.bc);
+        whole = true;
+        for (int it = 0; it < kExtend; ++it) {
+            const uint32_t nb = min_above(d32, nc, T, sm.bc);
+            const float b = __uint_as_float(nb);
+            if (nb == 0xffffffffu || !((b - T) <= rhof * (T + b))) {
+                whole = false;
+                break;
+            }
+            T = b;
+        }
+        if (!whole) {
+            // compact, in list order, into (outd, key as ids); sort; copy back
+            float *db = outd;
+            int32_t *ib = reinterpret_cast<int32_t *>(key);
+            const int per0 = (nc + RR_THREADS - 1) / RR_THREADS;
+            const int a0 = min(nc, (int)threadIdx.x * per0), a1 = min(nc, a0 + per0);
+            int mine = 0;
+            for (int j = a0; j < a1; ++j) mine += d32[j] <= T ? 1 : 0;
+            int ns;
+            int pos = block_exclusive_scan<RR_THREADS>(mine, sm.scan_tmp, &ns);
+            for (int j = a0; j < a1; ++j)
+                if (d32[j] <= T) {
+                    db[pos] = d32[j];
+                    ib[pos] = sid[j];
+                    ++pos;
                 }
+            int P2s = 2;
+            while (P2s < ns) P2s <<= 1;
+            for (int j = ns + threadIdx.x; j < P2s; j += RR_THREADS) {
+                db[j] = CUDART_INF_F;
+                ib[j] = INT32_MAX;
             }
             __syncthreads();
+            sort_pairs(db, ib, P2s, P2s <= 256);
+            __syncthreads();
+            for (int j = threadIdx.x; j < P2s; j += RR_THREADS) {
+                d32[j] = db[j];
+                sid[j] = ib[j];
+            }
+            __syncthreads();
+            nc = ns;
+            P2 = P2s;
         }
+    }
+    if (whole) {
+        for (int j = nc + threadIdx.x; j < P2; j += RR_THREADS) {
+            d32[j] = CUDART_INF_F;
+            sid[j] = INT32_MAX;
+        }
+        __syncthreads();
+        sort_pairs(d32, sid, P2, false);
     }
 
     // 3. runs of neighbours whose order FP32 cannot certify.  The test runs in
     //    FP32 with the bound raised by 2^-20: fl(b - a) and fl(rho (a + b)) are
     //    each within one rounding of the real values, so every pair the real
     //    test flags is flagged here
-    const double rho = (double)((d + 31) / 32 + 12) * 5.9604644775390625e-08 * 1.02;
-    const float rhof = (float)(rho * (1.0 + 9.5367431640625e-07));
     const int per = (P2 + RR_THREADS - 1) / RR_THREADS;
     const int j0 = threadIdx.x * per;
     const int j1 = min(P2, j0 + per);
@@ -228,7 +377,7 @@ __device__ void rerank_finish(const float *__restrict__ X, const int32_t *__rest
 
 
 __device__ __forceinline__ RerankSmem carve_rerank(unsigned char *base, int P2, int *scan_tmp,
-                                                   int *any_mark)
+                                                   int *any_mark, int *hist, int *bc)
 {
     RerankSmem r;
     r.key = reinterpret_cast<double *>(base);
@@ -238,6 +387,8 @@ __device__ __forceinline__ RerankSmem carve_rerank(unsigned char *base, int P2, 
     r.mark = reinterpret_cast<uint8_t *>(r.sid + P2);
     r.scan_tmp = scan_tmp;
     r.any_mark = any_mark;
+    r.hist = hist;
+    r.bc = bc;
     return r;
 }
 
@@ -250,7 +401,9 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int scan_tmp[RR_WARPS];
     __shared__ int any_mark;
-    RerankSmem sm = carve_rerank(smraw, P2, scan_tmp, &any_mark);
+    __shared__ int hist[256];
+    __shared__ int bc[4];
+    RerankSmem sm = carve_rerank(smraw, P2, scan_tmp, &any_mark, hist, bc);
     const int q = blockIdx.x;
     const int nc = nkeep[q];
     const int32_t *cl = cand + (int64_t)q * cap;
@@ -280,7 +433,9 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_bf16_kernel(
     __shared__ int scan_tmp[RR_WARPS];
     __shared__ int any_mark;
     __shared__ float s_uk;
-    RerankSmem sm = carve_rerank(smraw, P2, scan_tmp, &any_mark);
+    __shared__ int hist[256];
+    __shared__ int bc[4];
+    RerankSmem sm = carve_rerank(smraw, P2, scan_tmp, &any_mark, hist, bc);
     int32_t *cid = reinterpret_cast<int32_t *>(sm.mark + P2 + 15 - ((P2 + 15) % 16));  // P2 ids
     float *ubs = reinterpret_cast<float *>(cid + P2);                                   // P2 bounds
     const int q = blockIdx.x;

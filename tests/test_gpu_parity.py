@@ -245,6 +245,29 @@ def test_bitmap_many_projections(orc, qwlib, cuda, path, m):
     _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=10, v=60, path=path)
 
 
+@pytest.mark.parametrize("path", ["levels", "bitmap_direct_graph"])
+@pytest.mark.parametrize("shell", [12, 60])
+def test_rerank_near_ties_at_k(orc, qwlib, cuda, path, shell):
+    """A shell of `shell` points whose distances to the query agree to about
+    1e-7 holds the k-th nearest: FP32 cannot order them, the rerank must take
+    the FP64 order (ties by id).  With 12 points the run past position k is
+    short; with 60 it is longer than the selection extends, and the whole
+    candidate array is sorted instead.  v >= n keeps every point."""
+    rng = np.random.default_rng(100 + shell)
+    d, n, k = 32, 600, 10
+    q = rng.standard_normal(d)
+    u = rng.standard_normal((n, d))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    r = np.concatenate([rng.uniform(0.3, 0.9, 5),                      # nearer than the shell
+                        1.0 + 2e-8 * np.arange(shell),                  # the shell
+                        rng.uniform(2.0, 5.0, n - 5 - shell)])           # farther
+    perm = rng.permutation(n)
+    X = (q + u * r[perm, None]).astype(np.float32)
+    Q = q[None, :].astype(np.float32)
+    wl = workloads.make_workload("mix10k_d32", seed=7, n=64, nq=1, d=d, m=8)
+    _full_parity(orc, qwlib, cuda, X, Q, wl.A, wl.b, w=4.0, k=k, v=n, l=2, path=path)
+
+
 def test_empty_workload(qwlib, cuda):
     import torch
     wl = workloads.make_workload("mix10k_d32", seed=1, n=500, nq=1)
