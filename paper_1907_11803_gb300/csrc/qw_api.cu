@@ -70,7 +70,8 @@ struct qw_index {
     DevBuf X, A, b, o, span, lid, dir_bid, dir_off, dir_start, dir_cnt, Xb, xnorm;
     bool shadow = false;
     bool bitmaps = false;               // level bitmaps for QW_PATH_BITMAP
-    DevBuf bm, bm_base, bm_nb, bm_lvl, bm_J, bid_prefix, prefix_off, perm, bm_sum, Xloc, inv;
+    DevBuf bm, bm_base, bm_nb, bm_lvl, bm_J, bid_prefix, prefix_off, perm, bm_sum, Xloc, inv, hloc;
+    int hloc_bytes = 0;
     int bm_maxJ = 0;
     float xs = 1.0f;                 // 1 / RMS coordinate of the data (start-model features)
     qw_mlp *start_model = nullptr;   // not owned
@@ -79,7 +80,6 @@ struct qw_index {
     bool tuned = false;                 // qw_autotune ran: QW_PATH_AUTO / batch 0 use these
     int32_t tuned_path = QW_PATH_LEVELS;
     int32_t tuned_batch = 0;
-    DevBuf w_feat;
     // workspace for queries (grow-only)
     DevBuf w_q, w_hq, w_state, w_counters, w_cand, w_out, w_err, w_order, w_qb, w_ob, w_cbits,
         w_clist, w_bmsel, w_ovf, w_bmwork;
@@ -113,6 +113,8 @@ struct qw_index {
         v.Xloc = Xloc.as<float>();
         v.inv = inv.as<int32_t>();
         v.prefix_off = prefix_off.as<int64_t>();
+        v.hloc = hloc.p;
+        v.hloc_bytes = hloc_bytes;
         return v;
     }
 };
@@ -398,6 +400,11 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
         QW_TRY(ix->inv.ensure((size_t)n * sizeof(int32_t)));
         QW_TRY(launch_locality_copy(ix->X.as<float>(), ix->perm.as<int32_t>(), n, d,
                                     ix->Xloc.as<float>(), ix->inv.as<int32_t>(), s));
+        // anchored bucket ids per internal id, in the narrowest width that holds the spans
+        const int32_t smax = *std::max_element(h_span.begin(), h_span.end());
+        ix->hloc_bytes = smax < 256 ? 1 : (smax < 65536 ? 2 : 4);
+        QW_TRY(ix->hloc.ensure((size_t)n * m * ix->hloc_bytes));
+        QW_TRY(launch_hloc_build(ix->view(), Ht.as<int32_t>(), ix->hloc.p, ix->hloc_bytes, s));
         QW_CUDA_TRY(cudaStreamSynchronize(s));  // the host order must outlive its upload
         QW_TRY(launch_bid_prefix(ix->view(), ix->bid_prefix.as<int64_t>(),
                                  ix->prefix_off.as<int64_t>(), s));
@@ -414,7 +421,7 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
                                  ix->bm.bytes + ix->bm_base.bytes + ix->bm_nb.bytes +
                                  ix->bm_lvl.bytes + ix->bm_J.bytes + ix->bid_prefix.bytes +
                                  ix->prefix_off.bytes + ix->perm.bytes + ix->bm_sum.bytes +
-                                 ix->Xloc.bytes + ix->inv.bytes);
+                                 ix->Xloc.bytes + ix->inv.bytes + ix->hloc.bytes);
     return QW_OK;
 }
 
@@ -643,14 +650,9 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     const size_t st_bytes = (size_t)B * m * 8 + (size_t)B * 8 * 16 + plan_ints * 4 + 256 +
                             (size_t)B * 4 * 2 + 64 + 16 * ((sizeof(LoopCtl) + 15) / 16);
     QW_TRY(ix->w_state.ensure(st_bytes));
-    int nclass = 0;
-    if (learned) {
-        nclass = mlp_classes(ix->start_model);
-        if (mlp_inputs(ix->start_model) != d + m) {
-            set_error("qw_run_workload: the start model's input size is not d + m");
-            return QW_ERR_ARG;
-        }
-        QW_TRY(ix->w_feat.ensure((size_t)B * (d + m + nclass) * sizeof(float)));
+    if (learned && mlp_inputs(ix->start_model) != d + m) {
+        set_error("qw_run_workload: the start model's input size is not d + m");
+        return QW_ERR_ARG;
     }
     // outputs of the whole workload in device memory (the caller's in device mode)
     const size_t o_ids = want_ids ? (size_t)nq * k * sizeof(int64_t) : 0;
@@ -861,10 +863,6 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         } else {
             QW_TRY(tm.run(QW_K_SETUP, 1, [&] { return launch_query_setup(view, HQb, nb, st, s); }));
             if (learned) {
-                float *F = ix->w_feat.as<float>();
-                float *prob = F + (size_t)B * (d + m);
-                (void)F;
-                (void)prob;
                 QW_TRY(tm.run(QW_K_START, 1, [&] {
                     // bitmap path: start at the predicted last level (its previous
                     // level is recounted); level path: one level before it
@@ -885,7 +883,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             QW_TRY(tm.run(QW_K_SELECT, use_bitmap ? (learned ? 2 : 1) : 2, [&] {
                 if (use_bitmap && learned)
                     QW_TRY(launch_bm_recount(view, nb, ix->l, cap, ix->c, st, s));
-                return use_bitmap ? launch_bm_collect(view, nb, ix->l, cap, st, stats_b, s)
+                return use_bitmap ? launch_bm_collect(view, nb, ix->l, cap, st, stats_b, want_cand, s)
                                   : launch_collect(view, nb, ix->l, cap, st, stats_b, s);
             }));
             if (use_bitmap)
@@ -1342,12 +1340,12 @@ void qw_index_free(qw_index *ix)
                       &ix->dir_bid,
                       &ix->dir_off, &ix->dir_start, &ix->dir_cnt, &ix->w_q, &ix->w_hq,
                       &ix->w_state, &ix->w_counters, &ix->w_cand, &ix->w_out, &ix->w_err,
-                      &ix->w_order, &ix->w_qb, &ix->w_ob, &ix->w_feat};
+                      &ix->w_order, &ix->w_qb, &ix->w_ob};
     for (DevBuf *bb : bufs) bb->release();
     DevBuf *bmb[] = {&ix->bm,  &ix->bm_base,    &ix->bm_nb,      &ix->bm_lvl,
                      &ix->bm_J, &ix->bid_prefix, &ix->prefix_off, &ix->w_cbits,
                      &ix->w_clist, &ix->perm, &ix->bm_sum, &ix->w_bmsel, &ix->w_ovf,
-                     &ix->w_bmwork, &ix->Xloc, &ix->inv};
+                     &ix->w_bmwork, &ix->Xloc, &ix->inv, &ix->hloc};
     for (DevBuf *bb : bmb) bb->release();
     for (cudaEvent_t e : ix->event_pool) cudaEventDestroy(e);
     level_graph_cache_free(ix->graphs);

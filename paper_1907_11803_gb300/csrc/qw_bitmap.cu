@@ -815,41 +815,56 @@ __device__ __forceinline__ void smem_bitonic(uint64_t *keys, int n, int P2)
 // its last level's candidates: the boundary count c* and how many ids at c*
 // are kept follow from the counts exactly as on the level path (Section 3.1,
 // readings R4/R5); candidates of the previous level and those above c* are
-// kept, and of those at c* the ones with the smallest original ids.  The kept
-// list is written in ascending original id with its counts, plus the per-query
-// statistics.  A query whose list or tie class exceeds the fixed buffers is
-// marked for the level path and keeps nothing here.
+// kept, and of those at c* the ones with the smallest original ids (radix
+// selection of the take-th smallest id of the tie class).  The kept list is
+// written with its counts in no particular order, or in ascending original id
+// when `sorted`, plus the per-query statistics.  A query whose list or tie
+// class exceeds the fixed buffers is marked for the level path and keeps
+// nothing here.
 constexpr int SEL_THREADS = 512;
+static_assert(kHistBins <= 256, "count histogram shares the radix histogram");
 
 __global__ void __launch_bounds__(SEL_THREADS) bm_select_kernel(IndexView ix, int l, int cap,
                                                                 QueryState st,
-                                                                int64_t *__restrict__ stats_out)
+                                                                int64_t *__restrict__ stats_out,
+                                                                bool sorted)
 {
     extern __shared__ uint64_t keys[];
-    __shared__ int hist[kHistBins];
-    __shared__ int s_np, s_nd, s_ne, s_cstar, s_take, s_keep;
+    __shared__ int hist[256];
+    __shared__ int bc[4];
+    __shared__ int s_np, s_nd, s_ne, s_nt, s_cstar, s_take, s_keep;
     const int q = blockIdx.x;
     const int m = ix.m;
+    const int lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;
     const int jf = st.levels[q] - 1;
     const int n = st.qbuf_n[(int64_t)(jf & 1) * st.qbn_par + q];
     const int nc = st.ncand[q];
     const uint64_t *E = st.qbuf + (int64_t)(jf & 1) * st.qb_par + (int64_t)q * kQCap;
     int32_t *cand = st.cand + (int64_t)q * cap;
     int32_t *col = st.cand_col + (int64_t)q * cap;
+    int32_t *eq = st.eqbuf + (int64_t)q * kEqCap;
     const bool ovf_list = n > kQCap || n != nc;
+    const int nl = ovf_list ? 0 : n;
     if (threadIdx.x == 0) {
         s_np = 0;
         s_nd = 0;
         s_ne = 0;
+        s_nt = 0;
     }
     for (int c = threadIdx.x; c < kHistBins; c += SEL_THREADS) hist[c] = 0;
     __syncthreads();
-    if (!ovf_list) {
-        for (int j = threadIdx.x; j < n; j += SEL_THREADS) {
-            const uint64_t e = E[j];
-            if ((e >> 8) & 1u) atomicAdd(&s_np, 1);
-            else atomicAdd(&hist[1 + (int)(e & 0xffu)], 1);
-        }
+    // counts of the candidates not of the previous level, and how many are
+    for (int j0 = 0; j0 < nl; j0 += SEL_THREADS) {
+        const int j = j0 + threadIdx.x;
+        const uint64_t e = j < nl ? E[j] : 0ull;
+        const bool pf = j < nl && ((e >> 8) & 1u);
+        const bool other = j < nl && !pf;
+        const uint32_t bp = __ballot_sync(0xffffffffu, pf);
+        if (lane == 0 && bp) atomicAdd(&s_np, __popc(bp));
+        const uint32_t bin = other ? 1u + (uint32_t)(e & 0xffu) : 1024u + lane;
+        const uint32_t peers = __match_any_sync(0xffffffffu, bin);
+        if (other && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -876,23 +891,36 @@ __global__ void __launch_bounds__(SEL_THREADS) bm_select_kernel(IndexView ix, in
     }
     __syncthreads();
     const int cstar = s_cstar, take = s_take, keep = s_keep;
-    // kept outright, and the tie class at c* (original ids)
-    if (!ovf_list) {
-        const int32_t *perm = ix.perm;
-        for (int j = threadIdx.x; j < n; j += SEL_THREADS) {
-            const uint64_t e = E[j];
-            const int c = (int)(e & 0xffu);
-            const bool pf = (e >> 8) & 1u;
+    // kept outright, and the tie class at c* (original ids); one slot
+    // reservation per warp
+    const int32_t *perm = ix.perm;
+    for (int j0 = 0; j0 < nl; j0 += SEL_THREADS) {
+        const int j = j0 + threadIdx.x;
+        const uint64_t e = j < nl ? E[j] : 0ull;
+        const int c = (int)(e & 0xffu);
+        const bool pf = (e >> 8) & 1u;
+        const bool kp = j < nl && (pf || c > cstar);
+        const bool ti = j < nl && !kp && c == cstar && take > 0;
+        const uint32_t bk = __ballot_sync(0xffffffffu, kp);
+        const uint32_t bt = __ballot_sync(0xffffffffu, ti);
+        int baseK = 0, baseT = 0;
+        if (lane == 0) {
+            if (bk) baseK = atomicAdd(&s_nd, __popc(bk));
+            if (bt) baseT = atomicAdd(&s_ne, __popc(bt));
+        }
+        baseK = __shfl_sync(0xffffffffu, baseK, 0);
+        baseT = __shfl_sync(0xffffffffu, baseT, 0);
+        if (kp || ti) {
             const int32_t orig = perm[e >> 32];
-            if (pf || c > cstar) {
-                const int d = atomicAdd(&s_nd, 1);
+            if (kp) {
+                const int d = baseK + __popc(bk & below);
                 if (d < cap) {
                     cand[d] = orig;
                     col[d] = c;
                 }
-            } else if (c == cstar && take > 0) {
-                const int e2 = atomicAdd(&s_ne, 1);
-                if (e2 < kEqCap) st.eqbuf[(int64_t)q * kEqCap + e2] = orig;
+            } else {
+                const int t = baseT + __popc(bt & below);
+                if (t < kEqCap) eq[t] = orig;
             }
         }
     }
@@ -911,25 +939,36 @@ __global__ void __launch_bounds__(SEL_THREADS) bm_select_kernel(IndexView ix, in
         return;
     }
     if (take > 0) {
-        int P2 = 2;
-        while (P2 < ne) P2 <<= 1;
-        for (int i = threadIdx.x; i < ne; i += SEL_THREADS)
-            keys[i] = (uint64_t)(uint32_t)st.eqbuf[(int64_t)q * kEqCap + i];
-        smem_bitonic(keys, ne, P2);
-        for (int r = threadIdx.x; r < take; r += SEL_THREADS) {
-            cand[nd + r] = (int32_t)keys[r];
-            col[nd + r] = cstar;
+        // the take smallest ids of the tie class: those <= its take-th smallest
+        // (ids are distinct, so exactly take of them)
+        const uint32_t T = take < ne ? block_kth_smallest<SEL_THREADS>(
+                                           reinterpret_cast<const uint32_t *>(eq), ne, take, hist, bc)
+                                     : 0xffffffffu;
+        for (int j0 = 0; j0 < ne; j0 += SEL_THREADS) {
+            const int j = j0 + threadIdx.x;
+            const uint32_t id = j < ne ? (uint32_t)eq[j] : 0u;
+            const bool in = j < ne && id <= T;
+            const uint32_t b = __ballot_sync(0xffffffffu, in);
+            int base = 0;
+            if (lane == 0 && b) base = atomicAdd(&s_nt, __popc(b));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (in) {
+                cand[nd + base + __popc(b & below)] = (int32_t)id;
+                col[nd + base + __popc(b & below)] = cstar;
+            }
         }
         __syncthreads();
     }
-    int P2 = 2;
-    while (P2 < keep) P2 <<= 1;
-    for (int i = threadIdx.x; i < keep; i += SEL_THREADS)
-        keys[i] = ((uint64_t)(uint32_t)cand[i] << 32) | (uint32_t)col[i];
-    smem_bitonic(keys, keep, P2);
-    for (int i = threadIdx.x; i < keep; i += SEL_THREADS) {
-        cand[i] = (int32_t)(keys[i] >> 32);
-        col[i] = (int32_t)(keys[i] & 0xffffffffu);
+    if (sorted) {
+        int P2 = 2;
+        while (P2 < keep) P2 <<= 1;
+        for (int i = threadIdx.x; i < keep; i += SEL_THREADS)
+            keys[i] = ((uint64_t)(uint32_t)cand[i] << 32) | (uint32_t)col[i];
+        smem_bitonic(keys, keep, P2);
+        for (int i = threadIdx.x; i < keep; i += SEL_THREADS) {
+            cand[i] = (int32_t)(keys[i] >> 32);
+            col[i] = (int32_t)(keys[i] & 0xffffffffu);
+        }
     }
     for (int p = keep + threadIdx.x; p < cap; p += SEL_THREADS) {
         cand[p] = -1;
@@ -954,28 +993,29 @@ __global__ void __launch_bounds__(SEL_THREADS) bm_select_kernel(IndexView ix, in
 // Learned starts on the bitmap path: a query that stopped at its first level
 // L > 0 never counted level L - 1, whose candidates come first under the k + v
 // bound (reading R5).  Those are exactly the final candidates whose level-(L-1)
-// count reaches l (buckets nest, so C(L-1) is a subset of C(L)); they are
-// found by counting the final candidates' 128-id groups again at level L - 1.
+// count reaches l (buckets nest, so C(L-1) is a subset of C(L)).  The count of
+// a candidate is taken from its row of anchored bucket ids: on projection i it
+// collides at radius R' = c^(L-1) when floor(h_i / R') == floor(g_i / R'), i.e.
+// when h_i lies in [beta_i R', (beta_i + 1) R').  One warp per query, lane j
+// holding the bounds of projections j, j + 32, ...; four candidates' rows are
+// read per step (each row one coalesced load per 32 projections).
 // The plain path would have stopped earlier if |C(L-1)| >= k + v or if radius
 // c^(L-1) already exceeded every useful radius of the query: such queries are
-// marked for the level path.  One block per marked query; the candidates of
-// one group are contiguous in the list (one thread appended them).
-constexpr int RC_THREADS = 64;
-constexpr int kRunCap = 2048;
+// marked for the level path.  One block of RC_WARPS warps per query; each
+// warp takes 32 candidates at a time and reads kRcBatch rows per step.
+constexpr int RC_WARPS = 4;
+constexpr int kRcBatch = 16;
 
-__global__ void __launch_bounds__(RC_THREADS) bm_recount_kernel(IndexView ix, int l, int cap,
-                                                                int cgrow, QueryState st)
+template <typename T, int NROW>
+__global__ void __launch_bounds__(RC_WARPS * 32) bm_recount_kernel(IndexView ix, int l, int cap,
+                                                                   int cgrow, QueryState st)
 {
-    __shared__ int64_t lbase[QW_MAX_M + 8];
-    __shared__ int32_t pnb[QW_MAX_M + 8];
-    __shared__ int runs[kRunCap];
-    __shared__ int nruns, nprev;
+    __shared__ int s_nprev;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int q = blockIdx.x;
     if (!st.recount[q]) return;
     const int m = ix.m;
-    const int m8 = (m + 7) & ~7;
     const int L = st.levels[q] - 1;
-    const int Lp = L - 1;
     const int64_t R = st.finalR[q] / cgrow;  // radius of level L - 1
     const int n = st.qbuf_n[(int64_t)(L & 1) * st.qbn_par + q];
     uint64_t *E = st.qbuf + (int64_t)(L & 1) * st.qb_par + (int64_t)q * kQCap;
@@ -985,74 +1025,67 @@ __global__ void __launch_bounds__(RC_THREADS) bm_recount_kernel(IndexView ix, in
         if (threadIdx.x == 0) atomicOr(st.bm_ovf + q, 2);
         return;
     }
-    if (threadIdx.x < m) {
-        const int i = threadIdx.x;
-        const int64_t beta = floordiv64(st.g[(int64_t)q * m + i], R);
-        const int J = ix.bm_J[i];
-        int64_t b = -1;
-        if (Lp > J) {
-            if (beta == 0) b = ix.bm_base[i] + ix.bm_lvl[i * kBmLevels + J];
-        } else if (beta >= 0 && beta <= (int64_t)ix.span[i] / R) {
-            b = ix.bm_base[i] + ix.bm_lvl[i * kBmLevels + Lp] + beta;
-        }
-        lbase[i] = b;
-        pnb[i] = ix.bm_nb[i];
-    } else if (threadIdx.x < m8) {
-        lbase[threadIdx.x] = -1;
-        pnb[threadIdx.x] = 0;
-    }
-    if (threadIdx.x == 0) {
-        nruns = 0;
-        nprev = 0;
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < n; j += RC_THREADS) {
-        const uint64_t grp = E[j] >> 39;  // (internal id >> 7): tile and group
-        if (j == 0 || grp != (E[j - 1] >> 39)) {
-            const int r = atomicAdd(&nruns, 1);
-            if (r < kRunCap) runs[r] = j;
+    if (threadIdx.x == 0) s_nprev = 0;
+    // bucket bounds [lo, hi) of the lane's projections (anchored ids are in
+    // [0, span], so the bounds are clamped to [-1, 2^31 - 1])
+    int32_t lo[NROW], hi[NROW];
+#pragma unroll
+    for (int r = 0; r < NROW; ++r) {
+        const int i = lane + 32 * r;
+        lo[r] = 1;
+        hi[r] = 0;
+        if (i < m) {
+            const int64_t beta = floordiv64(st.g[(int64_t)q * m + i], R);
+            lo[r] = (int32_t)clamp64(beta * R, -1, INT32_MAX);
+            hi[r] = (int32_t)clamp64(beta * R + R, -1, INT32_MAX);
         }
     }
     __syncthreads();
-    if (nruns > kRunCap) {
-        if (threadIdx.x == 0) atomicOr(st.bm_ovf + q, 2);
-        return;
-    }
-    for (int r = threadIdx.x; r < nruns; r += RC_THREADS) {
-        const int j0 = runs[r];
-        const uint64_t grp = E[j0] >> 39;
-        const int64_t id0 = (int64_t)(E[j0] >> 32);
-        const int64_t t = id0 >> kTileShift;
-        const int g = (int)((id0 & (kTile - 1)) >> 7);
-        Planes P;
+    const T *H = static_cast<const T *>(ix.hloc);
+    int nprev = 0;
+    for (int j0 = warp * 32; j0 < n; j0 += RC_WARPS * 32) {
+        const uint64_t mine = j0 + lane < n ? E[j0 + lane] : 0ull;
+        const int cnt = min(32, n - j0);
+        uint32_t prev = 0;
+        for (int u0 = 0; u0 < cnt; u0 += kRcBatch) {
+            int32_t h[kRcBatch][NROW];  // anchored ids are below 2^31
 #pragma unroll
-        for (int kk = 0; kk < 7; ++kk)
+            for (int b = 0; b < kRcBatch; ++b) {
+                const int u = min(u0 + b, cnt - 1);
+                const T *row = H + (int64_t)(__shfl_sync(0xffffffffu, mine, u) >> 32) * m;
 #pragma unroll
-            for (int w = 0; w < 4; ++w) P.s[kk][w] = 0;
-        for (int i0 = 0; i0 < m8; i0 += 8) {
-            uint4 x[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int64_t b = lbase[i0 + u];
-                x[u] = b >= 0 ? __ldg(ix.bm + (b + t * pnb[i0 + u]) * kBmUint4 + g)
-                              : make_uint4(0, 0, 0, 0);
+                for (int r = 0; r < NROW; ++r)
+                    h[b][r] = lane + 32 * r < m ? (int32_t)row[lane + 32 * r] : -2;
             }
-            add8(P, x);
-        }
-        int mine = 0;
-        for (int j = j0; j < n && (E[j] >> 39) == grp; ++j) {
-            const uint32_t id = (uint32_t)(E[j] >> 32) & 127u;
-            if (count_of(P, (int)(id >> 5), (int)(id & 31)) >= l) {
-                E[j] |= 1ull << 8;
-                ++mine;
+#pragma unroll
+            for (int b = 0; b < kRcBatch; ++b) {
+                int c = 0;
+#pragma unroll
+                for (int r = 0; r < NROW; ++r)
+                    c += __popc(__ballot_sync(0xffffffffu, h[b][r] >= lo[r] && h[b][r] < hi[r]));
+                if (u0 + b < cnt && c >= l) prev |= 1u << (u0 + b);
             }
         }
-        if (mine) atomicAdd(&nprev, mine);
+        if ((prev >> lane) & 1u) E[j0 + lane] = mine | (1ull << 8);
+        nprev += __popc(prev);
     }
+    if (lane == 0 && nprev) atomicAdd(&s_nprev, nprev);
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (nprev >= cap) atomicOr(st.bm_ovf + q, 2);  // the plain path stops at L - 1
-        else st.nprev[q] = nprev;
+        if (s_nprev >= cap) atomicOr(st.bm_ovf + q, 2);  // the plain path stops at L - 1
+        else st.nprev[q] = s_nprev;
+    }
+}
+
+template <typename T>
+__global__ void hloc_kernel(const int32_t *__restrict__ Ht, const int32_t *__restrict__ perm,
+                            const int32_t *__restrict__ o, int64_t n, int m, T *__restrict__ out)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / m;
+        const int i = (int)(e % m);
+        out[e] = (T)(Ht[(int64_t)i * n + perm[j]] - o[i]);
     }
 }
 
@@ -1364,23 +1397,56 @@ qw_status launch_locality_copy(const float *X, const int32_t *perm, int64_t n, i
     return QW_OK;
 }
 
+template <typename T>
+static void recount_launch(const IndexView &ix, int nb, int l, int cap, int cgrow,
+                           QueryState &st, cudaStream_t s)
+{
+    if (ix.m <= 32)
+        bm_recount_kernel<T, 1><<<nb, RC_WARPS * 32, 0, s>>>(ix, l, cap, cgrow, st);
+    else if (ix.m <= 64)
+        bm_recount_kernel<T, 2><<<nb, RC_WARPS * 32, 0, s>>>(ix, l, cap, cgrow, st);
+    else
+        bm_recount_kernel<T, 4><<<nb, RC_WARPS * 32, 0, s>>>(ix, l, cap, cgrow, st);
+}
+
 qw_status launch_bm_recount(const IndexView &ix, int nb, int l, int cap, int cgrow, QueryState &st,
                             cudaStream_t s)
 {
-    bm_recount_kernel<<<nb, RC_THREADS, 0, s>>>(ix, l, cap, cgrow, st);
+    if (nb == 0) return QW_OK;
+    if (ix.hloc_bytes == 1) recount_launch<uint8_t>(ix, nb, l, cap, cgrow, st, s);
+    else if (ix.hloc_bytes == 2) recount_launch<uint16_t>(ix, nb, l, cap, cgrow, st, s);
+    else recount_launch<uint32_t>(ix, nb, l, cap, cgrow, st, s);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
+
+qw_status launch_hloc_build(const IndexView &ix, const int32_t *Ht, void *hloc, int bytes,
+                            cudaStream_t s)
+{
+    if (ix.n == 0) return QW_OK;
+    const unsigned blocks = (unsigned)std::min<int64_t>((ix.n * ix.m + 255) / 256, 152 * 32);
+    if (bytes == 1)
+        hloc_kernel<uint8_t><<<blocks, 256, 0, s>>>(Ht, ix.perm, ix.o, ix.n, ix.m,
+                                                    static_cast<uint8_t *>(hloc));
+    else if (bytes == 2)
+        hloc_kernel<uint16_t><<<blocks, 256, 0, s>>>(Ht, ix.perm, ix.o, ix.n, ix.m,
+                                                     static_cast<uint16_t *>(hloc));
+    else
+        hloc_kernel<uint32_t><<<blocks, 256, 0, s>>>(Ht, ix.perm, ix.o, ix.n, ix.m,
+                                                     static_cast<uint32_t *>(hloc));
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }
 
 qw_status launch_bm_collect(const IndexView &ix, int nb, int l, int cap, QueryState &st,
-                            int64_t *stats_out, cudaStream_t s)
+                            int64_t *stats_out, bool sorted, cudaStream_t s)
 {
     int P2 = 2;
-    while (P2 < std::max(cap, kEqCap)) P2 <<= 1;
-    const size_t smem = (size_t)P2 * sizeof(uint64_t);
+    while (P2 < cap) P2 <<= 1;
+    const size_t smem = sorted ? (size_t)P2 * sizeof(uint64_t) : 0;
     QW_CUDA_TRY(cudaFuncSetAttribute(bm_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-    bm_select_kernel<<<nb, SEL_THREADS, smem, s>>>(ix, l, cap, st, stats_out);
+    bm_select_kernel<<<nb, SEL_THREADS, smem, s>>>(ix, l, cap, st, stats_out, sorted);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }

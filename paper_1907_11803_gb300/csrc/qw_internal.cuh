@@ -112,6 +112,10 @@ struct IndexView {
     // b = 0 .. span_i + 1 (built with the bitmaps; entries scanned per range)
     const int64_t *bid_prefix;
     const int64_t *prefix_off;
+    // anchored bucket ids in locality order, row j = internal id j (m entries
+    // of hloc_bytes = 1, 2 or 4 bytes each; built with the bitmaps)
+    const void *hloc;
+    int hloc_bytes;
 };
 
 // Entries-scanned statistics from the bid prefix counts (bitmap path), for
@@ -246,8 +250,9 @@ ScanStats scan_stats_of(const IndexView &ix, int c);
 qw_status launch_bm_level(const IndexView &ix, int nb, int level, int64_t R, int64_t Rp, int l,
                           int cgrow, QueryState &st, int *err, bool tma, cudaStream_t s,
                           const LoopCtl *ctl = nullptr);
+// sorted: the kept lists in ascending original id (else in no particular order)
 qw_status launch_bm_collect(const IndexView &ix, int nb, int l, int cap, QueryState &st,
-                            int64_t *stats_out, cudaStream_t s);
+                            int64_t *stats_out, bool sorted, cudaStream_t s);
 qw_status launch_select_plan(const IndexView &ix, int nb, int l, int cap, QueryState &st,
                              int64_t *stats_out, cudaStream_t s);
 qw_status launch_bm_overflow_list(const QueryState &st, int nb, const int32_t *order_perm,
@@ -301,6 +306,10 @@ qw_status launch_rerank(const IndexView &ix, const float *Qb, int nb, int k, int
 // The data in locality order (Xloc[j] = X[perm[j]]) and the inverse order.
 qw_status launch_locality_copy(const float *X, const int32_t *perm, int64_t n, int d, float *Xloc,
                                int32_t *inv, cudaStream_t s);
+// Anchored bucket ids in locality order: row j holds Ht[i][perm[j]] - o[i] for
+// i < m, as `bytes`-byte unsigned integers (every anchored id fits).
+qw_status launch_hloc_build(const IndexView &ix, const int32_t *Ht, void *hloc, int bytes,
+                            cudaStream_t s);
 
 // The learned start model (qw_mlp.cu).
 int mlp_inputs(const qw_mlp *mp);

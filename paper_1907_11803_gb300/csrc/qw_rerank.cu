@@ -86,63 +86,6 @@ __device__ __forceinline__ void sort_pairs(float *kf, int32_t *id, int P, bool o
     }
 }
 
-// The kk-th smallest (1-based, kk <= n) of n non-negative FP32 values, by
-// radix selection on their bit patterns (ordered like the values), 8 bits a
-// pass.  Block-wide; returns the value in every thread.
-__device__ float kth_smallest(const float *v, int n, int kk, int *hist, int *bc)
-{
-    const int lane = threadIdx.x & 31;
-    uint32_t prefix = 0, mask = 0;
-    for (int shift = 24; shift >= 0; shift -= 8) {
-        for (int i = threadIdx.x; i < 256; i += RR_THREADS) hist[i] = 0;
-        __syncthreads();
-        // most values share the leading bits: one atomic per distinct bin of a warp
-        for (int j0 = 0; j0 < n; j0 += RR_THREADS) {
-            const int j = j0 + threadIdx.x;
-            const uint32_t u = j < n ? __float_as_uint(v[j]) : 0u;
-            const bool in = j < n && (u & mask) == prefix;
-            const uint32_t bin = in ? (u >> shift) & 255u : 256u + lane;
-            const uint32_t peers = __match_any_sync(0xffffffffu, bin);
-            if (in && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
-        }
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            // bin holding the kk-th: lane sums 8 bins, warp scan, then the lane
-            // where the running count reaches kk walks its bins
-            int c[8], sl = 0;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                c[u] = hist[lane * 8 + u];
-                sl += c[u];
-            }
-            int incl = sl;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, off);
-                if (lane >= off) incl += y;
-            }
-            const int excl = incl - sl;
-            if (excl < kk && kk <= incl) {
-                int cum = excl;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    if (cum < kk && kk <= cum + c[u]) {
-                        bc[0] = lane * 8 + u;
-                        bc[1] = kk - cum;
-                    }
-                    cum += c[u];
-                }
-            }
-        }
-        __syncthreads();
-        prefix |= (uint32_t)bc[0] << shift;
-        mask |= 255u << shift;
-        kk = bc[1];
-        __syncthreads();
-    }
-    return __uint_as_float(prefix);
-}
-
 // Smallest of the n values above t, as bits (0xffffffff: none).  Block-wide.
 __device__ uint32_t min_above(const float *v, int n, float t, int *bc)
 {
@@ -242,7 +185,9 @@ __device__ void rerank_finish(const float *__restrict__ X, const int32_t *__rest
     constexpr int kExtend = 16;
     bool whole = nc <= k;
     if (!whole) {
-        float T = kth_smallest(d32, nc, k, sm.hist, sm.bc);
+        // non-negative FP32 values are ordered like their bit patterns
+        float T = __uint_as_float(block_kth_smallest<RR_THREADS>(
+            reinterpret_cast<const uint32_t *>(d32), nc, k, sm.hist, sm.bc));
         whole = true;
         for (int it = 0; it < kExtend; ++it) {
             const uint32_t nb = min_above(d32, nc, T, sm.bc);

@@ -53,4 +53,63 @@ __device__ __forceinline__ int block_exclusive_max(int v, int lowest, int *tmp)
     return max(wbase, excl);
 }
 
+// The kk-th smallest (1-based, 1 <= kk <= n) of n unsigned 32-bit keys, by
+// radix selection, 8 bits a pass (most keys share their leading bits, so a
+// warp adds one count per distinct bin).  Block-wide over NT threads; v may be
+// shared or global memory written before the call's first barrier.  hist: 256
+// ints and bc: 2 ints of shared memory.  Returns the key in every thread.
+template <int NT>
+__device__ uint32_t block_kth_smallest(const uint32_t *v, int n, int kk, int *hist, int *bc)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t prefix = 0, mask = 0;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int i = threadIdx.x; i < 256; i += NT) hist[i] = 0;
+        __syncthreads();
+        for (int j0 = 0; j0 < n; j0 += NT) {
+            const int j = j0 + threadIdx.x;
+            const uint32_t u = j < n ? v[j] : 0u;
+            const bool in = j < n && (u & mask) == prefix;
+            const uint32_t bin = in ? (u >> shift) & 255u : 256u + lane;
+            const uint32_t peers = __match_any_sync(0xffffffffu, bin);
+            if (in && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            // the bin holding the kk-th: lane sums 8 bins, warp scan, then the
+            // lane whose range holds kk walks its bins
+            int c[8], sl = 0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                c[u] = hist[lane * 8 + u];
+                sl += c[u];
+            }
+            int incl = sl;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += y;
+            }
+            const int excl = incl - sl;
+            if (excl < kk && kk <= incl) {
+                int cum = excl;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (cum < kk && kk <= cum + c[u]) {
+                        bc[0] = lane * 8 + u;
+                        bc[1] = kk - cum;
+                    }
+                    cum += c[u];
+                }
+            }
+        }
+        __syncthreads();
+        prefix |= (uint32_t)bc[0] << shift;
+        mask |= 255u << shift;
+        kk = bc[1];
+        __syncthreads();
+    }
+    return prefix;
+}
+
 }  // namespace qw

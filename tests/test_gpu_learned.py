@@ -58,12 +58,15 @@ def _train_start_model(qwlib, cuda, index, Q_train, k, epochs=30):
     return mlp, labels
 
 
-def test_learned_start_same_results_fewer_levels(qwlib, cuda):
+@pytest.mark.parametrize("w", [4.0, 0.4])
+def test_learned_start_same_results_fewer_levels(qwlib, cuda, w):
+    """w = 4 keeps every anchored bucket id below 256, w = 0.4 needs 16 bits:
+    the bitmap path's recount reads rows of either width."""
     import torch
     spec = dict(n=60_000, d=48, m=32, n_clusters=120, query_clusters=30)
     wl = workloads.make_workload("mix1m_d128", seed=7, nq=600, n_train=3000, **spec)
     X, A, b = (torch.from_numpy(a).to(cuda) for a in (wl.X, wl.A, wl.b))
-    index = qwlib.Index(X, A, b, w=4.0, v=300, bitmaps=True)
+    index = qwlib.Index(X, A, b, w=w, v=300, bitmaps=True)
     mlp, labels = _train_start_model(qwlib, cuda, index, wl.Q_train, 20)
     index.set_start_model(mlp, eps=0.02)
     Q = torch.from_numpy(wl.Q).to(cuda)
