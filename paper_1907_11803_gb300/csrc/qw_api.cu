@@ -71,7 +71,7 @@ struct qw_index {
     bool shadow = false;
     bool bitmaps = false;               // level bitmaps for QW_PATH_BITMAP
     DevBuf bm, bm_base, bm_nb, bm_lvl, bm_J, bid_prefix, prefix_off, perm, bm_sum, Xloc, inv, hloc;
-    int hloc_bytes = 0;
+    int hloc_bytes = 0, hloc_stride = 0;
     int bm_maxJ = 0;
     float xs = 1.0f;                 // 1 / RMS coordinate of the data (start-model features)
     qw_mlp *start_model = nullptr;   // not owned
@@ -115,6 +115,7 @@ struct qw_index {
         v.prefix_off = prefix_off.as<int64_t>();
         v.hloc = hloc.p;
         v.hloc_bytes = hloc_bytes;
+        v.hloc_stride = hloc_stride;
         return v;
     }
 };
@@ -403,8 +404,10 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
         // anchored bucket ids per internal id, in the narrowest width that holds the spans
         const int32_t smax = *std::max_element(h_span.begin(), h_span.end());
         ix->hloc_bytes = smax < 256 ? 1 : (smax < 65536 ? 2 : 4);
-        QW_TRY(ix->hloc.ensure((size_t)n * m * ix->hloc_bytes));
-        QW_TRY(launch_hloc_build(ix->view(), Ht.as<int32_t>(), ix->hloc.p, ix->hloc_bytes, s));
+        ix->hloc_stride = (m * ix->hloc_bytes + 15) / 16 * 16;
+        QW_TRY(ix->hloc.ensure((size_t)n * ix->hloc_stride));
+        QW_CUDA_TRY(cudaMemsetAsync(ix->hloc.p, 0, ix->hloc.bytes, s));
+        QW_TRY(launch_hloc_build(ix->view(), Ht.as<int32_t>(), ix->hloc.p, s));
         QW_CUDA_TRY(cudaStreamSynchronize(s));  // the host order must outlive its upload
         QW_TRY(launch_bid_prefix(ix->view(), ix->bid_prefix.as<int64_t>(),
                                  ix->prefix_off.as<int64_t>(), s));

@@ -996,22 +996,37 @@ __global__ void __launch_bounds__(SEL_THREADS) bm_select_kernel(IndexView ix, in
 // count reaches l (buckets nest, so C(L-1) is a subset of C(L)).  The count of
 // a candidate is taken from its row of anchored bucket ids: on projection i it
 // collides at radius R' = c^(L-1) when floor(h_i / R') == floor(g_i / R'), i.e.
-// when h_i lies in [beta_i R', (beta_i + 1) R').  One warp per query, lane j
-// holding the bounds of projections j, j + 32, ...; four candidates' rows are
-// read per step (each row one coalesced load per 32 projections).
+// when h_i lies in [beta_i R', (beta_i + 1) R' - 1].  One block per query, one
+// thread per candidate: the row is read in 16-byte pieces and compared with
+// the bounds (packed like the row, in shared memory) 4, 2 or 1 ids per 32-bit
+// word by SIMD compares.
 // The plain path would have stopped earlier if |C(L-1)| >= k + v or if radius
 // c^(L-1) already exceeded every useful radius of the query: such queries are
-// marked for the level path.  One block of RC_WARPS warps per query; each
-// warp takes 32 candidates at a time and reads kRcBatch rows per step.
-constexpr int RC_WARPS = 4;
-constexpr int kRcBatch = 16;
+// marked for the level path.
+constexpr int RC_THREADS = 128;
+constexpr int kRcChunks = (QW_MAX_M * 4 + 15) / 16;  // 16-byte pieces of the widest row
 
-template <typename T, int NROW>
-__global__ void __launch_bounds__(RC_WARPS * 32) bm_recount_kernel(IndexView ix, int l, int cap,
-                                                                   int cgrow, QueryState st)
+// Ids of a 32-bit word within [lo, hi] (element-wise, inclusive).
+template <typename T> __device__ __forceinline__ int in_range(uint32_t h, uint32_t lo, uint32_t hi);
+template <> __device__ __forceinline__ int in_range<uint8_t>(uint32_t h, uint32_t lo, uint32_t hi)
 {
+    return __popc(__vcmpgeu4(h, lo) & __vcmpleu4(h, hi)) >> 3;
+}
+template <> __device__ __forceinline__ int in_range<uint16_t>(uint32_t h, uint32_t lo, uint32_t hi)
+{
+    return __popc(__vcmpgeu2(h, lo) & __vcmpleu2(h, hi)) >> 4;
+}
+template <> __device__ __forceinline__ int in_range<uint32_t>(uint32_t h, uint32_t lo, uint32_t hi)
+{
+    return (h >= lo && h <= hi) ? 1 : 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RC_THREADS) bm_recount_kernel(IndexView ix, int l, int cap,
+                                                                int cgrow, QueryState st)
+{
+    __shared__ uint4 blo[kRcChunks], bhi[kRcChunks];
     __shared__ int s_nprev;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int q = blockIdx.x;
     if (!st.recount[q]) return;
     const int m = ix.m;
@@ -1025,51 +1040,46 @@ __global__ void __launch_bounds__(RC_WARPS * 32) bm_recount_kernel(IndexView ix,
         if (threadIdx.x == 0) atomicOr(st.bm_ovf + q, 2);
         return;
     }
-    if (threadIdx.x == 0) s_nprev = 0;
-    // bucket bounds [lo, hi) of the lane's projections (anchored ids are in
-    // [0, span], so the bounds are clamped to [-1, 2^31 - 1])
-    int32_t lo[NROW], hi[NROW];
-#pragma unroll
-    for (int r = 0; r < NROW; ++r) {
-        const int i = lane + 32 * r;
-        lo[r] = 1;
-        hi[r] = 0;
+    const int chunks = ix.hloc_stride / 16;
+    // per projection, the ids of the level-(L-1) bucket in the width of the row
+    // (an empty range as lo = max, hi = 0; padding never matches)
+    const int64_t tmax = sizeof(T) == 4 ? (int64_t)INT32_MAX : ((int64_t)1 << (8 * sizeof(T))) - 1;
+    T *lo_t = reinterpret_cast<T *>(blo), *hi_t = reinterpret_cast<T *>(bhi);
+    for (int i = threadIdx.x; i < chunks * (16 / (int)sizeof(T)); i += RC_THREADS) {
+        int64_t lo = tmax, hi = 0;
         if (i < m) {
             const int64_t beta = floordiv64(st.g[(int64_t)q * m + i], R);
-            lo[r] = (int32_t)clamp64(beta * R, -1, INT32_MAX);
-            hi[r] = (int32_t)clamp64(beta * R + R, -1, INT32_MAX);
+            const int64_t a = beta * R, b = beta * R + R - 1;
+            if (b >= 0 && a <= tmax) {
+                lo = a > 0 ? a : 0;
+                hi = b < tmax ? b : tmax;
+            }
         }
+        lo_t[i] = (T)lo;
+        hi_t[i] = (T)hi;
     }
+    if (threadIdx.x == 0) s_nprev = 0;
     __syncthreads();
-    const T *H = static_cast<const T *>(ix.hloc);
-    int nprev = 0;
-    for (int j0 = warp * 32; j0 < n; j0 += RC_WARPS * 32) {
-        const uint64_t mine = j0 + lane < n ? E[j0 + lane] : 0ull;
-        const int cnt = min(32, n - j0);
-        uint32_t prev = 0;
-        for (int u0 = 0; u0 < cnt; u0 += kRcBatch) {
-            int32_t h[kRcBatch][NROW];  // anchored ids are below 2^31
-#pragma unroll
-            for (int b = 0; b < kRcBatch; ++b) {
-                const int u = min(u0 + b, cnt - 1);
-                const T *row = H + (int64_t)(__shfl_sync(0xffffffffu, mine, u) >> 32) * m;
-#pragma unroll
-                for (int r = 0; r < NROW; ++r)
-                    h[b][r] = lane + 32 * r < m ? (int32_t)row[lane + 32 * r] : -2;
-            }
-#pragma unroll
-            for (int b = 0; b < kRcBatch; ++b) {
-                int c = 0;
-#pragma unroll
-                for (int r = 0; r < NROW; ++r)
-                    c += __popc(__ballot_sync(0xffffffffu, h[b][r] >= lo[r] && h[b][r] < hi[r]));
-                if (u0 + b < cnt && c >= l) prev |= 1u << (u0 + b);
-            }
+    const char *H = static_cast<const char *>(ix.hloc);
+    int mine = 0;
+    for (int j = threadIdx.x; j < n; j += RC_THREADS) {
+        const uint64_t e = E[j];
+        const uint4 *row = reinterpret_cast<const uint4 *>(H + (int64_t)(e >> 32) * ix.hloc_stride);
+        int c = 0;
+#pragma unroll 4
+        for (int v = 0; v < chunks; ++v) {
+            const uint4 h = __ldg(row + v);
+            const uint4 a = blo[v], b = bhi[v];
+            c += in_range<T>(h.x, a.x, b.x) + in_range<T>(h.y, a.y, b.y) +
+                 in_range<T>(h.z, a.z, b.z) + in_range<T>(h.w, a.w, b.w);
         }
-        if ((prev >> lane) & 1u) E[j0 + lane] = mine | (1ull << 8);
-        nprev += __popc(prev);
+        if (c >= l) {
+            E[j] = e | (1ull << 8);
+            ++mine;
+        }
     }
-    if (lane == 0 && nprev) atomicAdd(&s_nprev, nprev);
+    mine = __reduce_add_sync(0xffffffffu, mine);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&s_nprev, mine);
     __syncthreads();
     if (threadIdx.x == 0) {
         if (s_nprev >= cap) atomicOr(st.bm_ovf + q, 2);  // the plain path stops at L - 1
@@ -1079,13 +1089,14 @@ __global__ void __launch_bounds__(RC_WARPS * 32) bm_recount_kernel(IndexView ix,
 
 template <typename T>
 __global__ void hloc_kernel(const int32_t *__restrict__ Ht, const int32_t *__restrict__ perm,
-                            const int32_t *__restrict__ o, int64_t n, int m, T *__restrict__ out)
+                            const int32_t *__restrict__ o, int64_t n, int m, int stride,
+                            char *__restrict__ out)
 {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * m;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = e / m;
         const int i = (int)(e % m);
-        out[e] = (T)(Ht[(int64_t)i * n + perm[j]] - o[i]);
+        reinterpret_cast<T *>(out + j * stride)[i] = (T)(Ht[(int64_t)i * n + perm[j]] - o[i]);
     }
 }
 
@@ -1397,43 +1408,31 @@ qw_status launch_locality_copy(const float *X, const int32_t *perm, int64_t n, i
     return QW_OK;
 }
 
-template <typename T>
-static void recount_launch(const IndexView &ix, int nb, int l, int cap, int cgrow,
-                           QueryState &st, cudaStream_t s)
-{
-    if (ix.m <= 32)
-        bm_recount_kernel<T, 1><<<nb, RC_WARPS * 32, 0, s>>>(ix, l, cap, cgrow, st);
-    else if (ix.m <= 64)
-        bm_recount_kernel<T, 2><<<nb, RC_WARPS * 32, 0, s>>>(ix, l, cap, cgrow, st);
-    else
-        bm_recount_kernel<T, 4><<<nb, RC_WARPS * 32, 0, s>>>(ix, l, cap, cgrow, st);
-}
-
 qw_status launch_bm_recount(const IndexView &ix, int nb, int l, int cap, int cgrow, QueryState &st,
                             cudaStream_t s)
 {
     if (nb == 0) return QW_OK;
-    if (ix.hloc_bytes == 1) recount_launch<uint8_t>(ix, nb, l, cap, cgrow, st, s);
-    else if (ix.hloc_bytes == 2) recount_launch<uint16_t>(ix, nb, l, cap, cgrow, st, s);
-    else recount_launch<uint32_t>(ix, nb, l, cap, cgrow, st, s);
+    if (ix.hloc_bytes == 1)
+        bm_recount_kernel<uint8_t><<<nb, RC_THREADS, 0, s>>>(ix, l, cap, cgrow, st);
+    else if (ix.hloc_bytes == 2)
+        bm_recount_kernel<uint16_t><<<nb, RC_THREADS, 0, s>>>(ix, l, cap, cgrow, st);
+    else
+        bm_recount_kernel<uint32_t><<<nb, RC_THREADS, 0, s>>>(ix, l, cap, cgrow, st);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }
 
-qw_status launch_hloc_build(const IndexView &ix, const int32_t *Ht, void *hloc, int bytes,
-                            cudaStream_t s)
+qw_status launch_hloc_build(const IndexView &ix, const int32_t *Ht, void *hloc, cudaStream_t s)
 {
     if (ix.n == 0) return QW_OK;
     const unsigned blocks = (unsigned)std::min<int64_t>((ix.n * ix.m + 255) / 256, 152 * 32);
-    if (bytes == 1)
-        hloc_kernel<uint8_t><<<blocks, 256, 0, s>>>(Ht, ix.perm, ix.o, ix.n, ix.m,
-                                                    static_cast<uint8_t *>(hloc));
-    else if (bytes == 2)
-        hloc_kernel<uint16_t><<<blocks, 256, 0, s>>>(Ht, ix.perm, ix.o, ix.n, ix.m,
-                                                     static_cast<uint16_t *>(hloc));
+    char *out = static_cast<char *>(hloc);
+    if (ix.hloc_bytes == 1)
+        hloc_kernel<uint8_t><<<blocks, 256, 0, s>>>(Ht, ix.perm, ix.o, ix.n, ix.m, ix.hloc_stride, out);
+    else if (ix.hloc_bytes == 2)
+        hloc_kernel<uint16_t><<<blocks, 256, 0, s>>>(Ht, ix.perm, ix.o, ix.n, ix.m, ix.hloc_stride, out);
     else
-        hloc_kernel<uint32_t><<<blocks, 256, 0, s>>>(Ht, ix.perm, ix.o, ix.n, ix.m,
-                                                     static_cast<uint32_t *>(hloc));
+        hloc_kernel<uint32_t><<<blocks, 256, 0, s>>>(Ht, ix.perm, ix.o, ix.n, ix.m, ix.hloc_stride, out);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }

@@ -113,9 +113,11 @@ struct IndexView {
     const int64_t *bid_prefix;
     const int64_t *prefix_off;
     // anchored bucket ids in locality order, row j = internal id j (m entries
-    // of hloc_bytes = 1, 2 or 4 bytes each; built with the bitmaps)
+    // of hloc_bytes = 1, 2 or 4 bytes each, rows hloc_stride bytes apart, a
+    // multiple of 16; built with the bitmaps)
     const void *hloc;
     int hloc_bytes;
+    int hloc_stride;
 };
 
 // Entries-scanned statistics from the bid prefix counts (bitmap path), for
@@ -306,10 +308,10 @@ qw_status launch_rerank(const IndexView &ix, const float *Qb, int nb, int k, int
 // The data in locality order (Xloc[j] = X[perm[j]]) and the inverse order.
 qw_status launch_locality_copy(const float *X, const int32_t *perm, int64_t n, int d, float *Xloc,
                                int32_t *inv, cudaStream_t s);
-// Anchored bucket ids in locality order: row j holds Ht[i][perm[j]] - o[i] for
-// i < m, as `bytes`-byte unsigned integers (every anchored id fits).
-qw_status launch_hloc_build(const IndexView &ix, const int32_t *Ht, void *hloc, int bytes,
-                            cudaStream_t s);
+// Anchored bucket ids in locality order: row j (ix.hloc_stride bytes, zero
+// padded) holds Ht[i][perm[j]] - o[i] for i < m, as ix.hloc_bytes-byte
+// unsigned integers (every anchored id fits).
+qw_status launch_hloc_build(const IndexView &ix, const int32_t *Ht, void *hloc, cudaStream_t s);
 
 // The learned start model (qw_mlp.cu).
 int mlp_inputs(const qw_mlp *mp);
