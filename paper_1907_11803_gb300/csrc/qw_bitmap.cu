@@ -821,7 +821,7 @@ __device__ __forceinline__ void smem_bitonic(uint64_t *keys, int n, int P2)
 // when `sorted`, plus the per-query statistics.  A query whose list or tie
 // class exceeds the fixed buffers is marked for the level path and keeps
 // nothing here.
-constexpr int SEL_THREADS = 512;
+constexpr int SEL_THREADS = 256;
 static_assert(kHistBins <= 256, "count histogram shares the radix histogram");
 
 __global__ void __launch_bounds__(SEL_THREADS) bm_select_kernel(IndexView ix, int l, int cap,

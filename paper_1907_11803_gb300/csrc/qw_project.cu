@@ -3,9 +3,12 @@
 //
 // Pass 1 (FP32, tiled over rows x projections) computes t = a_i . v with FP32
 // fused multiply-adds summed over j = 0..d-1 in order, then u = (t + b_i) / w
-// with explicitly rounded FP32 operations.  For recursive FP32 summation the
-// error of t is at most gamma_d * sum_j |a_ij v_j| <= gamma_d ||a_i|| ||v||
-// (Cauchy-Schwarz), gamma_d = d u / (1 - d u), u = 2^-24.  Adding b and
+// with explicitly rounded FP32 operations.  Each fused multiply-add rounds
+// once, and in a recursive sum the rounding errors add up without being
+// amplified, so the error of t is at most u / (1 - u) * sum_j |s_j|, s_j the
+// computed partial sums (u = 2^-24); that sum is accumulated in FP32 beside
+// t and enlarged by (1 + 2 d u) * 1.01 for its own rounding.  (The a-priori
+// bound gamma_d ||a_i|| ||v|| is typically ten times larger.)  Adding b and
 // dividing by w add at most 2u |u| + u.  Whenever the distance of u to the
 // nearest integer is not larger than that bound (or than 1e-5, i.e. 1e-5 w
 // in projection units, whichever is larger), floor(u) is not trusted and the
@@ -34,8 +37,6 @@ __global__ void __launch_bounds__(NT) project_fp32_kernel(
 {
     __shared__ float Vs[BK][BM + 1];
     __shared__ float As[BK][BN + 1];
-    __shared__ float vnorm2[BM];
-    __shared__ float anorm2[BN];
 
     const int tid = threadIdx.x;
     const int tx = tid & 15;   // projection lane
@@ -43,12 +44,14 @@ __global__ void __launch_bounds__(NT) project_fp32_kernel(
     const int64_t row0 = (int64_t)blockIdx.x * BM;
     const int col0 = blockIdx.y * BN;
 
-    float acc[4][4];
+    float acc[4][4], run[4][4];  // partial sums and the sum of their magnitudes
 #pragma unroll
     for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = 0.0f;
-    float my_norm2 = 0.0f;  // threads 0..63: row norm; 64..127: projection norm
+        for (int jj = 0; jj < 4; ++jj) {
+            acc[ii][jj] = 0.0f;
+            run[ii][jj] = 0.0f;
+        }
 
     for (int k0 = 0; k0 < d; k0 += BK) {
         // Stage a BM x BK block of V and a BN x BK block of A, transposed.
@@ -63,14 +66,6 @@ __global__ void __launch_bounds__(NT) project_fp32_kernel(
             As[kk][r] = (gc < m && gk < d) ? A[(int64_t)gc * d + gk] : 0.0f;
         }
         __syncthreads();
-        if (tid < BM) {
-#pragma unroll 8
-            for (int kk = 0; kk < BK; ++kk) my_norm2 = fmaf(Vs[kk][tid], Vs[kk][tid], my_norm2);
-        } else if (tid < BM + BN) {
-            int c = tid - BM;
-#pragma unroll 8
-            for (int kk = 0; kk < BK; ++kk) my_norm2 = fmaf(As[kk][c], As[kk][c], my_norm2);
-        }
 #pragma unroll 8
         for (int kk = 0; kk < BK; ++kk) {
             float vr[4], ac[4];
@@ -81,29 +76,25 @@ __global__ void __launch_bounds__(NT) project_fp32_kernel(
 #pragma unroll
             for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = fmaf(vr[ii], ac[jj], acc[ii][jj]);
+                for (int jj = 0; jj < 4; ++jj) {
+                    acc[ii][jj] = fmaf(vr[ii], ac[jj], acc[ii][jj]);
+                    run[ii][jj] += fabsf(acc[ii][jj]);
+                }
         }
         __syncthreads();
     }
-    if (tid < BM) vnorm2[tid] = my_norm2;
-    else if (tid < BM + BN) anorm2[tid - BM] = my_norm2;
-    __syncthreads();
 
     const float unit = 5.9604645e-08f;  // 2^-24
-    const float du = (float)d * unit;
-    const float gamma_d = du / (1.0f - du);
-    const float inv_w_bound = 1.01f * gamma_d / w;
+    // error of t per unit of the running magnitude sum, over w
+    const float run_bound = unit * (1.0f + 2.0f * (float)d * unit) * 1.01f / w;
 #pragma unroll
     for (int ii = 0; ii < 4; ++ii) {
         int64_t r = row0 + ty + 16 * ii;
         if (r >= nv) continue;
-        // norms from FP32 sums of squares; 1.01 above absorbs their rounding
-        float vn = sqrtf(vnorm2[ty + 16 * ii]);
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
             int i = col0 + tx + 16 * jj;
             if (i >= m) continue;
-            float an = sqrtf(anorm2[tx + 16 * jj]);
             float u = __fdiv_rn(__fadd_rn(acc[ii][jj], b[i]), w);
             float f = floorf(u);
             int32_t h;
@@ -113,7 +104,7 @@ __global__ void __launch_bounds__(NT) project_fp32_kernel(
             } else {
                 float frac = u - f;                       // exact
                 float near = fminf(frac, 1.0f - frac);
-                float eps = fmaxf(inv_w_bound * an * vn + 4.0f * unit * (fabsf(u) + 1.0f), 1e-5f);
+                float eps = fmaxf(run_bound * run[ii][jj] + 4.0f * unit * (fabsf(u) + 1.0f), 1e-5f);
                 h = (near <= eps) ? kNeedsFp64 : (int32_t)f;
             }
             H[r * ld_row + (int64_t)i * ld_col] = h;
