@@ -346,6 +346,10 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
     if (ix->bitmaps) {
         BitmapLayout lay;
         QW_TRY(bitmap_layout(h_span, nT, ix->c, &lay));
+        if (lay.total > (int64_t)INT32_MAX) {  // bitmaps are numbered in 31 bits
+            set_error("qw_build_index: bitmap table too large");
+            return QW_ERR_RANGE;
+        }
         QW_TRY(ix->bm.ensure((size_t)lay.total * kBmUint4 * sizeof(uint4)));
         QW_TRY(ix->bm_base.ensure((size_t)m * sizeof(int64_t)));
         QW_TRY(ix->bm_nb.ensure((size_t)m * sizeof(int32_t)));
@@ -557,6 +561,37 @@ static qw_status host_level_loop(qw_index *ix, LaunchTimer &tm, const IndexView 
     return QW_OK;
 }
 
+// The bitmap path's two-pass work buffers for B queries: byte size, and (when
+// st is given) their places in `base`: counters; per item (query, tile) its
+// (q, t) and its m bitmap numbers (int32, rows padded to 4 entries); per group
+// a work entry and its projection mask; per (parity, item) the live-group
+// mask; per (query, projection) the bucket's bitmap number in tile 0.
+static size_t bm_work_layout(int64_t B, int nT, int m, QueryState *st, char *base = nullptr)
+{
+    const size_t items = (size_t)B * nT;
+    const size_t mpad = (size_t)(m + 3) / 4 * 4;
+    const size_t mw = (size_t)(m + 63) / 64;
+    auto up16 = [](size_t x) { return (x + 15) / 16 * 16; };
+    size_t off = 16;
+    const size_t o_qt = off;    off = up16(off + items * sizeof(int2));
+    const size_t o_bi = off;    off = up16(off + items * mpad * sizeof(int32_t));
+    const size_t o_work = off;  off = up16(off + items * kBmUint4 * sizeof(int32_t));
+    const size_t o_amask = off; off = up16(off + 2 * items * (kBmUint4 / 32) * sizeof(uint32_t));
+    const size_t o_wmask = off; off = up16(off + items * kBmUint4 * mw * 8);
+    const size_t o_bq = off;    off = up16(off + (size_t)B * m * sizeof(int64_t));
+    if (st && base) {
+        st->bm_nitems = reinterpret_cast<int32_t *>(base);
+        st->bm_nwork = st->bm_nitems + 1;
+        st->bm_item_qt = reinterpret_cast<int2 *>(base + o_qt);
+        st->bm_item_bi = reinterpret_cast<int32_t *>(base + o_bi);
+        st->bm_work = reinterpret_cast<int32_t *>(base + o_work);
+        st->bm_amask = reinterpret_cast<uint32_t *>(base + o_amask);
+        st->bm_wmask = reinterpret_cast<unsigned long long *>(base + o_wmask);
+        st->bm_bq = reinterpret_cast<int64_t *>(base + o_bq);
+    }
+    return off;
+}
+
 static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                           const qw_query_params *qp, int64_t *ids, float *dists,
                           int64_t *stats, int64_t *cand_ids, int32_t *cand_col, int32_t mem,
@@ -641,11 +676,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         QW_TRY(ix->w_bmsel.ensure((size_t)B * (2 + kEqCap) * sizeof(int32_t)));
         // two-pass level: one slot per (query, tile), one work entry per group
         const size_t items = (size_t)B * ix->nT;
-        QW_TRY(ix->w_bmwork.ensure(16 + items * (sizeof(int2) + (size_t)m * sizeof(int64_t)) +
-                                   items * kBmUint4 * sizeof(int32_t) +
-                                   2 * items * (kBmUint4 / 32) * sizeof(uint32_t) +
-                                   items * kBmUint4 * (size_t)((m + 63) / 64) * 8 +
-                                   (size_t)B * m * sizeof(int64_t)));
+        QW_TRY(ix->w_bmwork.ensure(bm_work_layout(B, ix->nT, m, nullptr)));
         QW_TRY(ix->w_ovf.ensure(((size_t)nq + 1) * sizeof(int32_t)));
     }
     QW_TRY(ix->w_cand.ensure((size_t)B * cap * 2 * sizeof(int32_t)));
@@ -743,16 +774,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         st.recount = st.bm_ovf + B;
         st.eqbuf = st.bm_ovf + 2 * B;
         const int64_t items = B * (int64_t)ix->nT;
-        char *wp = ix->w_bmwork.as<char>();
-        st.bm_nitems = reinterpret_cast<int32_t *>(wp);
-        st.bm_nwork = st.bm_nitems + 1;
-        st.bm_item_qt = reinterpret_cast<int2 *>(wp + 16);
-        st.bm_item_bi = reinterpret_cast<int64_t *>(wp + 16 + items * sizeof(int2));
-        st.bm_work = reinterpret_cast<int32_t *>(wp + 16 + items * sizeof(int2) +
-                                                 items * m * sizeof(int64_t));
-        st.bm_amask = reinterpret_cast<uint32_t *>(st.bm_work + items * kBmUint4);
-        st.bm_wmask = reinterpret_cast<unsigned long long *>(st.bm_amask + 2 * items * (kBmUint4 / 32));
-        st.bm_bq = reinterpret_cast<int64_t *>(st.bm_wmask + items * kBmUint4 * ((m + 63) / 64));
+        bm_work_layout(B, ix->nT, m, &st, ix->w_bmwork.as<char>());
         st.bm_item_cap = (int32_t)std::min<int64_t>(items, (int64_t)1 << 23);
         st.bm_work_cap = (int32_t)std::min<int64_t>(items * kBmUint4, INT32_MAX);
     }

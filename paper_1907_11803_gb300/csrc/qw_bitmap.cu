@@ -446,11 +446,12 @@ __global__ void __launch_bounds__(FL_WARPS * 32, NROW <= 2 ? 3 : 2) bm_filter_ke
             slot = __shfl_sync(0xffffffffu, slot, 0);
             base = __shfl_sync(0xffffffffu, base, 0);
             if (slot >= st.bm_item_cap) continue;
+            const int mpad = (m + 3) & ~3;
 #pragma unroll
             for (int r = 0; r < NROW; ++r)
-                if (lane + 32 * r < m)
-                    st.bm_item_bi[(int64_t)slot * m + lane + 32 * r] =
-                        b0[r] >= 0 ? b0[r] + (int64_t)t * nbp[r] : -1;
+                if (lane + 32 * r < mpad)
+                    st.bm_item_bi[(int64_t)slot * mpad + lane + 32 * r] =
+                        b0[r] >= 0 ? (int32_t)(b0[r] + (int64_t)t * nbp[r]) : -1;
             if (lane == 0) st.bm_item_qt[slot] = make_int2(q, t);
             // live groups of the tile, in ascending order, after `base`
             int pos = base;
@@ -491,7 +492,7 @@ __global__ void __launch_bounds__(256, 3) bm_count_kernel(IndexView ix, int leve
         const int2 qt2 = st.bm_item_qt[slot];
         const int q = qt2.x, t = qt2.y;
         const int64_t qt = (int64_t)q * nT + t;
-        const int64_t *bi = st.bm_item_bi + (int64_t)slot * m;
+        const int4 *bi4 = reinterpret_cast<const int4 *>(st.bm_item_bi + (int64_t)slot * ((m + 3) & ~3));
         const bool first = level == st.start[q];
         // the previous level wrote this group's candidate word only if the
         // tile had candidates and the group was live there
@@ -512,10 +513,15 @@ __global__ void __launch_bounds__(256, 3) bm_count_kernel(IndexView ix, int leve
         for (int i0 = 0; i0 < m; i0 += 8) {
             const uint32_t bits = (uint32_t)(((i0 < 64 ? mk0 : mk1) >> (i0 & 63)) & 0xffu);
             if (bits == 0) continue;
+            // eight bitmap numbers in two vector loads (the row is padded to a
+            // multiple of four; entries past m are never selected by the mask)
+            const int4 ba = bits & 0x0fu ? bi4[i0 >> 2] : make_int4(-1, -1, -1, -1);
+            const int4 bb = bits & 0xf0u ? bi4[(i0 >> 2) + 1] : make_int4(-1, -1, -1, -1);
+            const int32_t bn[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
             uint4 x[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-                x[u] = (bits >> u) & 1u ? __ldg(ix.bm + bi[i0 + u] * kBmUint4 + g)
+                x[u] = (bits >> u) & 1u ? __ldg(ix.bm + (int64_t)bn[u] * kBmUint4 + g)
                                         : make_uint4(0, 0, 0, 0);
             add8(P, x);
         }

@@ -188,7 +188,7 @@ struct QueryState {
     int32_t *bm_nwork = nullptr;
     int2 *bm_item_qt = nullptr;
     int64_t *bm_bq = nullptr;       // per (query, projection): bitmap number in tile 0, or -1
-    int64_t *bm_item_bi = nullptr;
+    int32_t *bm_item_bi = nullptr;  // per item, (m + 3) / 4 * 4 bitmap numbers (-1: none)
     uint32_t *bm_amask = nullptr;   // per (level parity, query, tile): live groups, 8 words
     int32_t *bm_work = nullptr;
     // per work entry, (m + 63) / 64 words: the projections whose bucket touches
