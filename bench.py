@@ -49,7 +49,11 @@ L2_BYTES = 129 * 1024 * 1024
 def parse_args(argv=None):
     p = argparse.ArgumentParser(description=__doc__)
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    # default: about one second of timed GPU steps (so that clocks are sampled
+    # while they run); 5 steps of the CPU reference arm
+    p.add_argument("--steps", type=int, default=None)
+    p.add_argument("--plain-steps", type=int, default=3,
+                   help="timed steps of the plain path (at most --steps)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="mix1m_d128")
@@ -205,7 +209,7 @@ KERNEL_SOURCES = {
     "bm_filter_count": ("qw_bitmap.cu", "qw_dir.cuh", "qw_scan.cuh", "qw_internal.cuh"),
     "bm_level_tma_kernel": ("qw_bitmap.cu", "qw_tma.cuh", "qw_internal.cuh"),
     "cluster_query_kernel": ("qw_cluster.cu", "qw_count.cuh", "qw_internal.cuh"),
-    "rerank_kernel": ("qw_rerank.cu", "qw_internal.cuh"),
+    "rerank_kernel": ("qw_rerank.cu", "qw_scan.cuh", "qw_internal.cuh"),
 }
 
 
@@ -380,7 +384,8 @@ def run_ours(args):
     # the plain path first: its results are the reference for the chosen one
     _, _, st = index.query(Q, s.k, stats=True, **plain_kw)
     st = st.cpu().numpy()
-    p_ms, p_ms_max, p_prof = timed(plain_kw, args.steps)
+    p_steps = max(1, min(args.steps, args.plain_steps))
+    p_ms, p_ms_max, p_prof = timed(plain_kw, p_steps)
     ids_plain, dists_plain = ids.clone(), dists.clone()
 
     clocks = ClockSampler(gpu_uuid(torch))
@@ -389,10 +394,10 @@ def run_ours(args):
     clk = clocks.stop()
     value = world * s.nq * args.steps / (ms_max / 1e3)
     same = bool(torch.equal(ids, ids_plain) and torch.equal(dists, dists_plain))
-    plain = {"value": world * s.nq * args.steps / (p_ms_max / 1e3),
-             "ms_per_step": p_ms_max / args.steps, "settings": plain_kw,
+    plain = {"value": world * s.nq * p_steps / (p_ms_max / 1e3),
+             "ms_per_step": p_ms_max / p_steps, "steps": p_steps, "settings": plain_kw,
              "results_identical_to_chosen": same,
-             "kernel_ms_per_step": {k2: round(v2 / args.steps, 3)
+             "kernel_ms_per_step": {k2: round(v2 / p_steps, 3)
                                     for k2, v2 in p_prof["ms"].items()}}
 
     # end to end through the public API: pinned host queries in, host results out
@@ -429,14 +434,16 @@ def run_ours(args):
     if bitmap and dom == "level":
         if chosen_kw.get("loads", "tma") == "direct":
             # two passes: per (query, tile, level) the m bucket summaries (32 B);
-            # per live item its m bitmap numbers and its candidate words (4 KiB);
-            # per live 128-id group m bitmap words, the previous and the new
-            # candidate word (16 B each)
+            # per live item its m bitmap numbers (int32, written and read); per
+            # live 128-id group its work entry and projection mask (written and
+            # read), the previous and the new candidate word (16 B each), and
+            # the bitmap words of the projections touching it (16 B each)
             dom_name = ("bm_filter_kernel + bm_count_kernel (summary filter, then bit-sliced "
                         "collision counts of the live 128-id groups)")
             count_bytes = ((prof["level_passes"] / steps) * index.info.n_tiles * s.m * 32.0
-                           + (prof["bitmap_live_items"] / steps) * (s.m * 8.0 + 4096.0)
-                           + (prof["bitmap_live_groups"] / steps) * (s.m + 2) * 16.0)
+                           + (prof["bitmap_live_items"] / steps) * s.m * 8.0
+                           + (prof["bitmap_live_groups"] / steps) * (2 * 12.0 + 32.0)
+                           + (prof["bitmap_live_words"] / steps) * 16.0)
         else:
             # per (query, level) pass and tile: the m bucket bitmaps, the previous
             # level's candidate bitmap and the new one, 4 KiB each
@@ -502,6 +509,7 @@ def run_ours(args):
         "stats": {"levels_median": float(np.median(st[:, 0])),
                   "bitmap_live_items_per_step": prof["bitmap_live_items"] / steps,
                   "bitmap_live_groups_per_step": prof["bitmap_live_groups"] / steps,
+                  "bitmap_live_words_per_step": prof["bitmap_live_words"] / steps,
                   "level_passes_per_step": prof["level_passes"] / steps,
                   "entries_scanned_per_query": float(np.mean(st[:, 5])),
                   "kernel_ms_per_step": {k2: round(v2 / steps, 3) for k2, v2 in prof["ms"].items()}},
@@ -560,6 +568,8 @@ def run_reference(args):
 
 def main(argv=None):
     args = parse_args(argv)
+    if args.steps is None:
+        args.steps = 5 if args.impl == "reference" else 300
     if args.steps < 1 or args.warmup < 0:
         raise SystemExit("--steps must be >= 1 and --warmup >= 0")
     if args.impl == "reference":

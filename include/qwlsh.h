@@ -190,6 +190,8 @@ typedef struct {
     int64_t bitmap_live_items;     /* QW_PATH_BITMAP, direct loads: (query, tile, level) items
                                       with a live 128-id group (profile mode) */
     int64_t bitmap_live_groups;    /* ... and live groups counted from the bitmaps */
+    int64_t bitmap_live_words;     /* ... and the 16-byte bitmap words those groups read (the
+                                      projections whose bucket summary touches the group) */
 } qw_profile;
 
 typedef struct {

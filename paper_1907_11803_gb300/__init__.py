@@ -84,7 +84,8 @@ class qw_profile(C.Structure):
                 ("rerank_candidates", C.c_int64), ("rerank_fp32_rows", C.c_int64),
                 ("start_levels_skipped", C.c_int64), ("start_fallbacks", C.c_int64),
                 ("level_passes", C.c_int64), ("bitmap_fallbacks", C.c_int64),
-                ("bitmap_live_items", C.c_int64), ("bitmap_live_groups", C.c_int64)]
+                ("bitmap_live_items", C.c_int64), ("bitmap_live_groups", C.c_int64),
+                ("bitmap_live_words", C.c_int64)]
 
 
 class qw_index_info(C.Structure):
@@ -351,7 +352,8 @@ class Index:
                 "level_passes": int(p.level_passes),
                 "bitmap_fallbacks": int(p.bitmap_fallbacks),
                 "bitmap_live_items": int(p.bitmap_live_items),
-                "bitmap_live_groups": int(p.bitmap_live_groups)}
+                "bitmap_live_groups": int(p.bitmap_live_groups),
+                "bitmap_live_words": int(p.bitmap_live_words)}
 
     def query(self, Q, k: int, *, batch: int = 0, stats: bool = False, out=None,
               profile: bool = False, path: str = "auto", clusters: int = 0,

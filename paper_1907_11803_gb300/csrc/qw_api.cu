@@ -790,7 +790,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     const IndexView view = ix->view();
     LaunchTimer tm{ix, s, qp && qp->profile != 0};
     if (tm.on) {
-        QW_CUDA_TRY(cudaMemsetAsync(ix->w_err.as<char>() + 40, 0, 40, s));
+        QW_CUDA_TRY(cudaMemsetAsync(ix->w_err.as<char>() + 40, 0, 48, s));
         st.level_passes = reinterpret_cast<unsigned long long *>(ix->w_err.as<char>() + 56);
         if (use_bitmap)
             st.bm_prof = reinterpret_cast<unsigned long long *>(ix->w_err.as<char>() + 64);
@@ -998,13 +998,14 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     }
     QW_TRY(tm.finish());
     if (tm.on) {
-        unsigned long long ctr[5] = {0, 0, 0, 0, 0};
+        unsigned long long ctr[6] = {0, 0, 0, 0, 0, 0};
         QW_CUDA_TRY(cudaMemcpy(ctr, ix->w_err.as<char>() + 40, sizeof(ctr), cudaMemcpyDeviceToHost));
         ix->prof.rerank_fp32_rows += (int64_t)(bf16 ? ctr[0] : ctr[1]);
         ix->prof.rerank_candidates += (int64_t)ctr[1];
         ix->prof.level_passes += (int64_t)ctr[2];
         ix->prof.bitmap_live_items += (int64_t)ctr[3];
         ix->prof.bitmap_live_groups += (int64_t)ctr[4];
+        ix->prof.bitmap_live_words += (int64_t)ctr[5];
     }
     ix->prof.queries += nq;
     return QW_OK;

@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(FL_WARPS * 32, NROW <= 2 ? 3 : 2) bm_filter_ke
                         b0[r] >= 0 ? (int32_t)(b0[r] + (int64_t)t * nbp[r]) : -1;
             if (lane == 0) st.bm_item_qt[slot] = make_int2(q, t);
             // live groups of the tile, in ascending order, after `base`
-            int pos = base;
+            int pos = base, words = 0;
 #pragma unroll
             for (int w = 0; w < kSumWords; ++w) {
                 if ((x[w] >> lane) & 1u) {
@@ -463,10 +463,18 @@ __global__ void __launch_bounds__(FL_WARPS * 32, NROW <= 2 ? 3 : 2) bm_filter_ke
                         st.bm_work[at] = (slot << 8) | (w * 32 + lane);
 #pragma unroll
                         for (int h = 0; h < MW; ++h)
-                            if (h < mw) st.bm_wmask[(int64_t)at * mw + h] = wmk[wi][w][h][lane];
+                            if (h < mw) {
+                                const unsigned long long mk = wmk[wi][w][h][lane];
+                                st.bm_wmask[(int64_t)at * mw + h] = mk;
+                                words += __popcll(mk);
+                            }
                     }
                 }
                 pos += __popc(x[w]);
+            }
+            if (st.bm_prof) {
+                words = __reduce_add_sync(0xffffffffu, words);
+                if (lane == 0) atomicAdd(st.bm_prof + 2, (unsigned long long)words);
             }
         }
     }

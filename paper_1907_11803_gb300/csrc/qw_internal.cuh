@@ -196,7 +196,7 @@ struct QueryState {
     unsigned long long *bm_wmask = nullptr;
     int32_t bm_item_cap = 0;
     int32_t bm_work_cap = 0;
-    unsigned long long *bm_prof = nullptr;  // profile mode: live items, live groups (summed)
+    unsigned long long *bm_prof = nullptr;  // profile mode: live items, groups, words (summed)
 };
 
 // Candidates per query and level the bitmap path holds (more: the query is

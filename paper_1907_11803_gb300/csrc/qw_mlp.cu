@@ -483,30 +483,75 @@ __global__ void transpose_half_kernel(const __half *__restrict__ in, int rows, i
 
 constexpr int SM_RB = 16;  // queries per block of the fused inference kernel
 constexpr int SM_THREADS = 256;
+static_assert(SM_RB % 8 == 0, "two halves of the rows, four per float4");
 
-// Out[k][r] = ReLU(b[j] + sum_k In[k][r] Wt[k][j]) for the block's SM_RB rows;
-// activations are k-major in shared memory so four rows load as one float4.
+// Out[j][r] = ReLU(b[j] + sum_k In[k][r] Wt[k][j]) for the block's SM_RB rows
+// (In, Out in shared memory, k-major; Wt: K x N FP16).  Thread t computes the
+// neuron pair (2p, 2p + 1), p = t mod (SM_THREADS / 2), for half of the rows,
+// reading both weights with one 4-byte load (N even; an odd last neuron takes
+// the pair's first half) and keeping eight k steps of weights in flight.
 __device__ __forceinline__ void dense_relu(const float *In, int K, const __half *__restrict__ Wt,
                                            const float *__restrict__ b, int N, float *Out)
 {
-    for (int j = threadIdx.x; j < N; j += SM_THREADS) {
-        float acc[SM_RB];
+    constexpr int PAIRS = SM_THREADS / 2;
+    constexpr int RH = SM_RB / 2;  // rows per thread
+    const int rh = threadIdx.x / PAIRS;
+    // pairs load as one __half2 when every pair starts 4-byte aligned
+    const bool even = (N & 1) == 0 && (reinterpret_cast<uintptr_t>(Wt) & 3u) == 0;
+    for (int p = threadIdx.x % PAIRS; 2 * p < N; p += PAIRS) {
+        const int j = 2 * p;
+        const bool two = j + 1 < N;
+        float acc0[RH], acc1[RH];
 #pragma unroll
-        for (int r = 0; r < SM_RB; ++r) acc[r] = b[j];
-        for (int k = 0; k < K; ++k) {
-            const float w = __half2float(Wt[(int64_t)k * N + j]);
-            const float4 *x4 = reinterpret_cast<const float4 *>(In + k * SM_RB);
+        for (int r = 0; r < RH; ++r) {
+            acc0[r] = b[j];
+            acc1[r] = two ? b[j + 1] : 0.0f;
+        }
+        int k = 0;
+        for (; k + 8 <= K; k += 8) {
+            float2 w[8];
 #pragma unroll
-            for (int r4 = 0; r4 < SM_RB / 4; ++r4) {
-                const float4 x = x4[r4];
-                acc[4 * r4 + 0] = fmaf(x.x, w, acc[4 * r4 + 0]);
-                acc[4 * r4 + 1] = fmaf(x.y, w, acc[4 * r4 + 1]);
-                acc[4 * r4 + 2] = fmaf(x.z, w, acc[4 * r4 + 2]);
-                acc[4 * r4 + 3] = fmaf(x.w, w, acc[4 * r4 + 3]);
+            for (int u = 0; u < 8; ++u) {
+                const __half *wp = Wt + (int64_t)(k + u) * N + j;
+                if (even) {
+                    w[u] = __half22float2(*reinterpret_cast<const __half2 *>(wp));
+                } else {
+                    w[u].x = __half2float(wp[0]);
+                    w[u].y = two ? __half2float(wp[1]) : 0.0f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float4 *x4 = reinterpret_cast<const float4 *>(In + (k + u) * SM_RB + rh * RH);
+#pragma unroll
+                for (int r4 = 0; r4 < RH / 4; ++r4) {
+                    const float4 x = x4[r4];
+                    acc0[4 * r4 + 0] = fmaf(x.x, w[u].x, acc0[4 * r4 + 0]);
+                    acc0[4 * r4 + 1] = fmaf(x.y, w[u].x, acc0[4 * r4 + 1]);
+                    acc0[4 * r4 + 2] = fmaf(x.z, w[u].x, acc0[4 * r4 + 2]);
+                    acc0[4 * r4 + 3] = fmaf(x.w, w[u].x, acc0[4 * r4 + 3]);
+                    acc1[4 * r4 + 0] = fmaf(x.x, w[u].y, acc1[4 * r4 + 0]);
+                    acc1[4 * r4 + 1] = fmaf(x.y, w[u].y, acc1[4 * r4 + 1]);
+                    acc1[4 * r4 + 2] = fmaf(x.z, w[u].y, acc1[4 * r4 + 2]);
+                    acc1[4 * r4 + 3] = fmaf(x.w, w[u].y, acc1[4 * r4 + 3]);
+                }
+            }
+        }
+        for (; k < K; ++k) {
+            const float w0 = __half2float(Wt[(int64_t)k * N + j]);
+            const float w1 = two ? __half2float(Wt[(int64_t)k * N + j + 1]) : 0.0f;
+#pragma unroll
+            for (int r = 0; r < RH; ++r) {
+                const float x = In[k * SM_RB + rh * RH + r];
+                acc0[r] = fmaf(x, w0, acc0[r]);
+                acc1[r] = fmaf(x, w1, acc1[r]);
             }
         }
 #pragma unroll
-        for (int r = 0; r < SM_RB; ++r) Out[j * SM_RB + r] = fmaxf(acc[r], 0.0f);
+        for (int r = 0; r < RH; ++r) {
+            Out[j * SM_RB + rh * RH + r] = fmaxf(acc0[r], 0.0f);
+            if (two) Out[(j + 1) * SM_RB + rh * RH + r] = fmaxf(acc1[r], 0.0f);
+        }
     }
 }
 
