@@ -38,8 +38,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 # Operating points (v, l) meeting recall >= 0.9 and ratio <= 1.05, from sweeps
-# of v and l on the GPU; the paper's v = 100 gives recall 0.35 on mix1m_d128.
-OPERATING_POINTS = {"mix1m_d128": (700, 43)}
+# of v and l on the GPU (recall on 200 seeded queries against exact k-NN; l = 0
+# derives l from Eq. 1): the paper's v = 100 gives recall 0.35 on mix1m_d128,
+# 0.24 on mix4m_d512 and 0.34 on mix10m_d128; v = 1000 gives 0.9997 and 0.997
+# on the latter two.  zipf1m_d256 reaches 0.56 at v = 1000 (its largest
+# clusters hold most points at nearly equal distances) and keeps the default.
+OPERATING_POINTS = {"mix1m_d128": (700, 43), "mix4m_d512": (1000, 0), "mix10m_d128": (1000, 0)}
 
 METRIC = "workload queries/sec at recall>=0.9, ratio<=1.05 (plain vs chosen); HBM roofline %"
 UNIT = "queries/s"
@@ -85,6 +89,13 @@ def parse_args(argv=None):
                    help="with --no-tune and --path bitmap: how the bitmap kernel reads bitmaps")
     p.add_argument("--graph", action="store_true",
                    help="with --no-tune: run the level loop as a CUDA graph")
+    p.add_argument("--l2", default="off",
+                   help="with --no-tune: persisting-L2 split of the chosen path (off, model, or "
+                        "the index window's permille of the set-aside)")
+    p.add_argument("--l2-sweep", action="store_true",
+                   help="also time the chosen path under the paper's cache splits (index share "
+                        "1, 10, ..., 90, 99 %% of the persisting-L2 set-aside, off, cost model)")
+    p.add_argument("--sweep-steps", type=int, default=20)
     p.add_argument("--v", type=int, default=-1,
                    help="allowed false positives (-1 = the workload's operating point)")
     p.add_argument("--l", type=int, default=-1,
@@ -210,6 +221,7 @@ KERNEL_SOURCES = {
     "bm_level_tma_kernel": ("qw_bitmap.cu", "qw_tma.cuh", "qw_internal.cuh"),
     "cluster_query_kernel": ("qw_cluster.cu", "qw_count.cuh", "qw_internal.cuh"),
     "rerank_kernel": ("qw_rerank.cu", "qw_scan.cuh", "qw_internal.cuh"),
+    "rerank_bf16_kernel": ("qw_rerank.cu", "qw_scan.cuh", "qw_internal.cuh"),
 }
 
 
@@ -341,12 +353,16 @@ def run_ours(args):
                      shadow_bf16=args.rerank == "bf16", bitmaps=not args.no_bitmaps)
     ids = torch.empty((s.nq, s.k), dtype=torch.int64, device=dev)
     dists = torch.empty((s.nq, s.k), dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    # the library's calls run on a created stream (persisting-L2 windows are
+    # stream attributes; the legacy default stream takes none)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
 
     plain_kw = dict(batch=args.batch, path="levels", order="given", rerank="fp32",
                     start="plain", graph=False)
+    l2_arg = None if args.l2 == "off" else ("model" if args.l2 == "model" else int(args.l2))
     chosen_kw = dict(batch=args.batch, path=args.path, order=args.order, rerank=args.rerank,
-                     start=args.start, graph=args.graph, loads=args.loads)
+                     start=args.start, graph=args.graph, loads=args.loads, l2=l2_arg)
     mlp = None
     train_info = None
     wt = workloads.make_workload(args.workload, seed=args.seed, nq=1, n_train=args.train_queries)
@@ -392,6 +408,8 @@ def run_ours(args):
     clocks.start()
     ms, ms_max, prof = timed(chosen_kw, args.steps)
     clk = clocks.stop()
+    l2_prof = {"setaside_bytes": prof["l2_setaside_bytes"],
+               "index_permille": prof["l2_index_permille"]} if chosen_kw.get("l2") else None
     value = world * s.nq * args.steps / (ms_max / 1e3)
     same = bool(torch.equal(ids, ids_plain) and torch.equal(dists, dists_plain))
     plain = {"value": world * s.nq * p_steps / (p_ms_max / 1e3),
@@ -399,6 +417,23 @@ def run_ours(args):
              "results_identical_to_chosen": same,
              "kernel_ms_per_step": {k2: round(v2 / p_steps, 3)
                                     for k2, v2 in p_prof["ms"].items()}}
+
+    # the paper's cache-split grid (QALSH_Ci/Cd/CiCd/Opt settings, Section 6) on
+    # the GPU's persisting L2, with the chosen path's other settings
+    l2_sweep = None
+    if args.l2_sweep:
+        ids_c, dists_c = ids.clone(), dists.clone()
+        grid = [None, 10, 100, 200, 300, 400, 500, 600, 700, 800, 900, 990, "model"]
+        rows = []
+        for g in grid:
+            kw = dict(chosen_kw, l2=g)
+            t_ms, t_max, t_prof = timed(kw, args.sweep_steps)
+            rows.append({"l2": "off" if g is None else g,
+                         "ms_per_step": round(t_max / args.sweep_steps, 4),
+                         "index_permille": t_prof["l2_index_permille"] if g is not None else None,
+                         "setaside_bytes": t_prof["l2_setaside_bytes"] if g is not None else None,
+                         "identical": bool(torch.equal(ids, ids_c) and torch.equal(dists, dists_c))})
+        l2_sweep = {"steps": args.sweep_steps, "rows": rows}
 
     # end to end through the public API: pinned host queries in, host results out
     Qh = torch.from_numpy(wl.Q).pin_memory()
@@ -456,7 +491,17 @@ def run_ours(args):
     per_launch_s = (dom_ms / 1e3) / max(dom_launches, 1)
     achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
     kept = float(st[:, 3].sum())
-    rr_bytes = kept * s.d * 4 + s.nq * s.d * 4 + s.nq * s.k * 12
+    bf16_rr = chosen_kw.get("rerank") == "bf16"
+    if bf16_rr:
+        # BF16 pass: per kept candidate its residual row and its group's mean
+        # (2 d bytes each); FP32 stage: 4 d bytes per surviving row
+        rr_bytes = (kept * s.d * 4 + prof["rerank_fp32_rows"] / steps * s.d * 4
+                    + s.nq * s.d * 4 + s.nq * s.k * 12)
+        rr_name = ("rerank_bf16_kernel (residual BF16 pre-filter, then FP32 gather + L2 + "
+                   "top-k of the survivors)")
+    else:
+        rr_bytes = kept * s.d * 4 + s.nq * s.d * 4 + s.nq * s.k * 12
+        rr_name = "rerank_kernel (candidate gather + L2 + top-k)"
     rr_launches = prof["timed_launches"]["rerank"] / steps
     rr_ms = prof["ms"]["rerank"] / steps
     rr_achieved = (rr_bytes / max(rr_launches, 1)) / ((rr_ms / 1e3) / max(rr_launches, 1)) / 1e9 \
@@ -471,11 +516,12 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": per_launch_bytes,
                 "avg_launch_ms": per_launch_s * 1e3, "launches_per_step": dom_launches,
                 "share_of_step": round(dom_ms / (ms / steps), 4)}
-    roofline_gather = {"kernel": "rerank_kernel (candidate gather + L2 + top-k)", "bound": "hbm",
+    roofline_gather = {"kernel": rr_name, "bound": "hbm",
                        "achieved": round(rr_achieved, 1), "peak": hbm,
                        "frac": round(rr_achieved / hbm, 4), "unit": "GB/s",
                        "traffic": (lambda t: None if t is None else t / max(rr_launches, 1))(
-                           ncu_traffic("rerank_kernel", args.workload)),
+                           ncu_traffic("rerank_bf16_kernel" if bf16_rr else "rerank_kernel",
+                                       args.workload)),
                        "algorithmic_bytes_per_launch": rr_bytes / max(rr_launches, 1),
                        "avg_launch_ms": rr_ms / max(rr_launches, 1)}
     launches = int(sum(prof["launches"].values()))
@@ -503,6 +549,7 @@ def run_ours(args):
         "quality": {"recall": round(recall, 4), "ratio": round(ratio, 5),
                     "sample": int(pick.numel()), "meets_target": recall >= 0.9 and ratio <= 1.05},
         "plain": plain,
+        "l2_windows": l2_prof, "l2_sweep": l2_sweep,
         "roofline": roofline, "roofline_gather": roofline_gather,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk,
@@ -511,6 +558,8 @@ def run_ours(args):
                   "bitmap_live_groups_per_step": prof["bitmap_live_groups"] / steps,
                   "bitmap_live_words_per_step": prof["bitmap_live_words"] / steps,
                   "level_passes_per_step": prof["level_passes"] / steps,
+                  "rerank_candidates_per_step": prof["rerank_candidates"] / steps,
+                  "rerank_fp32_rows_per_step": prof["rerank_fp32_rows"] / steps,
                   "entries_scanned_per_query": float(np.mean(st[:, 5])),
                   "kernel_ms_per_step": {k2: round(v2 / steps, 3) for k2, v2 in prof["ms"].items()}},
     }

@@ -82,8 +82,11 @@ typedef struct {
     int32_t l;     /* collision threshold 1..m; 0 = derive from Eq. 1 (see
                       qw_collision_threshold) with beta = v / n */
     float delta;   /* error probability used when deriving l; <= 0 means 1/e (Section 6) */
-    int32_t shadow_bf16;  /* non-zero: also keep a BF16 copy of the data and row-norm bounds,
-                             for the QW_RERANK_BF16 pre-filter (2 * n * d + 4 * n bytes) */
+    int32_t shadow_bf16;  /* non-zero: also keep a BF16 copy of the data for the
+                             QW_RERANK_BF16 pre-filter: rows in the rerank's row order (the
+                             locality order when bitmaps are built) grouped by 128, each stored
+                             as the BF16 residual to its group's FP32 mean, with residual-norm
+                             bounds (2 * n * d + 4 * n + 4 * d * ceil(n / 128) bytes) */
     int32_t bitmaps;      /* non-zero: also build the level bitmaps of QW_PATH_BITMAP: per
                              projection i, id tile and level L, one bitmap of the tile's ids
                              per level-L bucket; about m * n_tiles * (c/(c-1)) * (span_i + 1)
@@ -113,8 +116,33 @@ typedef struct {
                              in shared memory with TMA bulk copies in a persistent kernel;
                              QW_LOADS_DIRECT loads them straight from global memory, one CTA
                              per (tile, query).  Same results */
+    int32_t l2_mode;      /* persisting-L2 division between the index and the data (the
+                             workload cache split of Section 4, on the GPU's L2): QW_L2_OFF
+                             (default) attaches no access-policy window; QW_L2_SPLIT gives
+                             l2_index_permille of the set-aside to the index window and the
+                             rest to the data window; QW_L2_MODEL takes the split from
+                             qw_l2_split_model.  Speed only: the results do not change */
+    int32_t l2_index_permille;  /* QW_L2_SPLIT: 0..1000, the paper's size(C_I) / size(C) */
     int32_t reserved[1];  /* must be zero */
 } qw_query_params;
+
+/* Persisting-L2 modes (qw_query_params.l2_mode).  With a window mode the call
+ * attaches an access-policy window over the index structure that every
+ * (query, tile, level) pass reads first (bucket summaries on the bitmap path,
+ * sorted id arrays on the level path) to the collision-counting launches, and
+ * one over the data rows the candidates are read from to the rerank launch,
+ * each with the hit ratio that makes its persisting footprint its share of
+ * the set-aside, and puts the stream's window attribute back before
+ * returning.  The index's first such call raises the context's persisting-L2
+ * set-aside (cudaLimitPersistingL2CacheSize) to the device maximum; it stays
+ * raised, shared by the whole context, until qw_index_free, or a later call
+ * on the index with QW_L2_OFF, puts back the value found and demotes the
+ * persisting lines (cudaCtxResetPersistingL2Cache).
+ * Nothing outlives the process.  On the legacy default stream (NULL), or where
+ * the device has no set-aside (MIG, MPS), the call runs without windows. */
+#define QW_L2_OFF 0
+#define QW_L2_SPLIT 1
+#define QW_L2_MODEL 2
 
 #define QW_LOADS_TMA 0
 #define QW_LOADS_DIRECT 1
@@ -131,9 +159,9 @@ typedef struct {
 
 /* Candidate distance stage.  QW_RERANK_FP32: FP32 distances of every kept
  * candidate, FP64 for neighbours FP32 cannot order.  QW_RERANK_BF16: distances
- * from the BF16 copy first, with a proven error bound; only candidates that
- * could still be among the k nearest go through the FP32/FP64 stage.  Both
- * return the same ids and distances. */
+ * from the residual BF16 copy first (see shadow_bf16), with a proven error
+ * bound; only candidates that could still be among the k nearest go through
+ * the FP32/FP64 stage.  Both return the same ids and distances. */
 #define QW_RERANK_FP32 0
 #define QW_RERANK_BF16 1
 
@@ -192,6 +220,9 @@ typedef struct {
     int64_t bitmap_live_groups;    /* ... and live groups counted from the bitmaps */
     int64_t bitmap_live_words;     /* ... and the 16-byte bitmap words those groups read (the
                                       projections whose bucket summary touches the group) */
+    int64_t l2_setaside_bytes;     /* last call with a window mode: persisting-L2 set-aside used
+                                      (0: windows could not be attached) */
+    int64_t l2_index_permille;     /* ... and the share of it given to the index window */
 } qw_profile;
 
 typedef struct {
@@ -321,6 +352,24 @@ qw_status qw_workload_candidates(qw_index *index, const float *queries, int64_t 
 qw_status qw_run_workload_noalloc(qw_index *index, const float *queries, int64_t nq, int32_t k,
                                   int64_t *ids, float *dists, int64_t *stats, void *stream);
 
+/* Cost model of the L2 split (Section 4, Eq. 4: choose size(C_I) +
+ * size(C_D) = size(C) to minimise the workload's index IO plus data IO),
+ * restated for a hardware cache.  A region X (index or data) of U_X bytes is
+ * read A_X >= U_X bytes in total by the workload.  Its DRAM traffic with S_X
+ * persisting bytes is modelled as
+ *   D_X(S_X) = U_X + (A_X - U_X) * (1 - min(1, S_X / U_X)),
+ * i.e. the first read of every byte misses and a re-read hits when the byte
+ * is among the persisting share.  The function returns the permille p of the
+ * set-aside S given to the index (S_I = p S / 1000, S_D = S - S_I) that
+ * minimises D_I(S_I) + D_D(S_D); on a tie the smaller p.  The index reads
+ * scale with the cardinality (the paper's alpha_card: every pass reads the
+ * index of every tile) and the data reads with the dimensionality (alpha_dim:
+ * at most k + v rows of 4 d bytes per query).
+ * All sizes are bytes, >= 0.  Returns -1 on invalid arguments (negative or
+ * non-finite values, setaside == 0). */
+int32_t qw_l2_split_model(double setaside, double index_bytes, double index_reads,
+                          double data_bytes, double data_reads);
+
 /* Copy the index's profile counters into *out (host); reset them afterwards
  * when `reset` is non-zero. */
 qw_status qw_index_profile(qw_index *index, qw_profile *out, int32_t reset);
@@ -342,8 +391,9 @@ typedef struct {
  * default and 1/16, 1/4, 4x of it) and graph mode; the bitmap path (when the
  * index has bitmaps) with its default batch, 1/16 and 1/4 of it, and graph
  * mode and direct loads; then the cluster path against the best so far (when the index fits it
- * and the start is plain); order (signature / given) and rerank (FP32 / BF16,
- * when the index has the BF16 copy).  Every setting returns the same results, so the choice cannot change
+ * and the start is plain); order (signature / given), rerank (FP32 / BF16,
+ * when the index has the BF16 copy) and the persisting-L2 windows (off /
+ * QW_L2_MODEL).  Every setting returns the same results, so the choice cannot change
  * them.  Each setting runs once untimed, then `reps` (>= 1) times timed with
  * CUDA events on `stream`; the median counts.  The chosen setting is written
  * to *best (host) and stored in the index: later calls with QW_PATH_AUTO take

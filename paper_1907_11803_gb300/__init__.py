@@ -36,7 +36,7 @@ EXPORTED = ("qw_version", "qw_last_error", "qw_collision_probability",
             "qw_index_get_info", "qw_mlp_create", "qw_mlp_param_count", "qw_mlp_set_params",
             "qw_mlp_get_params", "qw_mlp_loss_grad", "qw_mlp_train", "qw_mlp_predict",
             "qw_mlp_free", "qw_query_features", "qw_index_set_start_model", "qw_autotune",
-            "qw_index_export", "qw_index_free")
+            "qw_index_export", "qw_index_free", "qw_l2_split_model")
 
 
 class qw_index_params(C.Structure):
@@ -49,6 +49,7 @@ class qw_query_params(C.Structure):
     _fields_ = [("batch", C.c_int32), ("profile", C.c_int32), ("path", C.c_int32),
                 ("clusters", C.c_int32), ("order", C.c_int32), ("rerank", C.c_int32),
                 ("start", C.c_int32), ("graph", C.c_int32), ("bitmap_loads", C.c_int32),
+                ("l2_mode", C.c_int32), ("l2_index_permille", C.c_int32),
                 ("reserved", C.c_int32 * 1)]
 
 
@@ -71,6 +72,7 @@ QW_START_PLAIN, QW_START_LEARNED = 0, 1
 STARTS = {"plain": QW_START_PLAIN, "learned": QW_START_LEARNED}
 QW_LOADS_TMA, QW_LOADS_DIRECT = 0, 1
 LOADS = {"tma": QW_LOADS_TMA, "direct": QW_LOADS_DIRECT}
+QW_L2_OFF, QW_L2_SPLIT, QW_L2_MODEL = 0, 1, 2
 (QW_K_PROJECT, QW_K_SETUP, QW_K_LEVEL, QW_K_DECIDE, QW_K_SELECT, QW_K_RERANK, QW_K_CLUSTER,
  QW_K_ORDER, QW_K_START) = range(9)
 QW_K_COUNT = 9
@@ -85,7 +87,8 @@ class qw_profile(C.Structure):
                 ("start_levels_skipped", C.c_int64), ("start_fallbacks", C.c_int64),
                 ("level_passes", C.c_int64), ("bitmap_fallbacks", C.c_int64),
                 ("bitmap_live_items", C.c_int64), ("bitmap_live_groups", C.c_int64),
-                ("bitmap_live_words", C.c_int64)]
+                ("bitmap_live_words", C.c_int64), ("l2_setaside_bytes", C.c_int64),
+                ("l2_index_permille", C.c_int64)]
 
 
 class qw_index_info(C.Structure):
@@ -171,6 +174,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.qw_index_export.argtypes = [vp, vp, vp, vp, vp, vp]
     L.qw_index_free.restype = None
     L.qw_index_free.argtypes = [vp]
+    L.qw_l2_split_model.restype = C.c_int32
+    L.qw_l2_split_model.argtypes = [C.c_double] * 5
     if path is None:
         _lib = L
     return L
@@ -193,6 +198,26 @@ def qw_collision_probability(r: float, w: float) -> float:
 
 def qw_collision_threshold(m: int, w: float, c: int, n: int, v: int, delta: float = 0.0) -> int:
     return int(load().qw_collision_threshold(m, w, c, n, v, delta))
+
+
+def qw_l2_split_model(setaside: float, index_bytes: float, index_reads: float,
+                      data_bytes: float, data_reads: float) -> int:
+    """Permille of the persisting-L2 set-aside for the index window (-1: bad
+    arguments)."""
+    return int(load().qw_l2_split_model(setaside, index_bytes, index_reads, data_bytes,
+                                        data_reads))
+
+
+def _l2_fields(l2) -> dict:
+    """qw_query_params fields of query()'s ``l2`` argument: None / "off", "model",
+    or an int 0..1000 (permille of the set-aside for the index window)."""
+    if l2 is None or l2 == "off":
+        return {"l2_mode": QW_L2_OFF, "l2_index_permille": 0}
+    if l2 == "model":
+        return {"l2_mode": QW_L2_MODEL, "l2_index_permille": 0}
+    if isinstance(l2, int) and not isinstance(l2, bool):
+        return {"l2_mode": QW_L2_SPLIT, "l2_index_permille": int(l2)}
+    raise ValueError("l2 must be None, 'off', 'model' or a permille 0..1000")
 
 
 def qw_hash(V: int, nv: int, d: int, A: int, b: int, m: int, w: float, H: int, stream: int = 0):
@@ -263,7 +288,9 @@ def _params_kwargs(p) -> dict:
     inv = lambda d, v: next(k for k, x in d.items() if x == v)  # noqa: E731
     return {"batch": int(p.batch), "path": inv(PATHS, p.path), "order": inv(ORDERS, p.order),
             "rerank": inv(RERANKS, p.rerank), "start": inv(STARTS, p.start),
-            "graph": bool(p.graph), "loads": inv(LOADS, p.bitmap_loads)}
+            "graph": bool(p.graph), "loads": inv(LOADS, p.bitmap_loads),
+            "l2": (None if p.l2_mode == QW_L2_OFF else "model" if p.l2_mode == QW_L2_MODEL
+                   else int(p.l2_index_permille))}
 
 
 def _stream_of(t) -> int:
@@ -353,15 +380,19 @@ class Index:
                 "bitmap_fallbacks": int(p.bitmap_fallbacks),
                 "bitmap_live_items": int(p.bitmap_live_items),
                 "bitmap_live_groups": int(p.bitmap_live_groups),
-                "bitmap_live_words": int(p.bitmap_live_words)}
+                "bitmap_live_words": int(p.bitmap_live_words),
+                "l2_setaside_bytes": int(p.l2_setaside_bytes),
+                "l2_index_permille": int(p.l2_index_permille)}
 
     def query(self, Q, k: int, *, batch: int = 0, stats: bool = False, out=None,
               profile: bool = False, path: str = "auto", clusters: int = 0,
               order: str = "auto", rerank: str = "fp32", start: str = "plain",
-              graph: bool = False, loads: str = "tma"):
+              graph: bool = False, loads: str = "tma", l2=None):
         """Top-k of every query row.  Returns (ids int64 nq x k, dists float32
         nq x k[, stats int64 nq x QW_NSTAT]) on Q's device (host tensors in,
-        host tensors out).  ``out`` may give preallocated (ids, dists[, stats])."""
+        host tensors out).  ``out`` may give preallocated (ids, dists[, stats]).
+        ``l2``: persisting-L2 split (None / "off", "model", or the index
+        window's permille of the set-aside); speed only."""
         torch = _torch()
         _f32(Q, "Q")
         nq, d = Q.shape
@@ -380,7 +411,7 @@ class Index:
         qp = qw_query_params(batch=int(batch), profile=1 if profile else 0, path=PATHS[path],
                              clusters=int(clusters), order=ORDERS[order], rerank=RERANKS[rerank],
                              start=STARTS[start], graph=1 if graph else 0,
-                             bitmap_loads=LOADS[loads])
+                             bitmap_loads=LOADS[loads], **_l2_fields(l2))
         qw_run_workload(self._h, Q.data_ptr(), nq, int(k), qp, ids.data_ptr(), dists.data_ptr(),
                         st.data_ptr() if st is not None else 0, mem, _stream_of(Q))
         return (ids, dists, st) if stats else (ids, dists)

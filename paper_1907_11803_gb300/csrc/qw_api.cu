@@ -2,6 +2,7 @@
 // of the index and its workspace, and the order of kernel launches.  No step
 // of the method's arithmetic runs on the host.
 #include "qw_internal.cuh"
+#include "qw_l2.cuh"
 
 #include <math.h>
 #include <stdio.h>
@@ -67,7 +68,7 @@ struct qw_index {
     int nT = 0;
     int32_t span_max = 0;
     int64_t n_fixups = 0;
-    DevBuf X, A, b, o, span, lid, dir_bid, dir_off, dir_start, dir_cnt, Xb, xnorm;
+    DevBuf X, A, b, o, span, lid, dir_bid, dir_off, dir_start, dir_cnt, Xb, xnorm, Cg;
     bool shadow = false;
     bool bitmaps = false;               // level bitmaps for QW_PATH_BITMAP
     DevBuf bm, bm_base, bm_nb, bm_lvl, bm_J, bid_prefix, prefix_off, perm, bm_sum, Xloc, inv, hloc;
@@ -80,6 +81,8 @@ struct qw_index {
     bool tuned = false;                 // qw_autotune ran: QW_PATH_AUTO / batch 0 use these
     int32_t tuned_path = QW_PATH_LEVELS;
     int32_t tuned_batch = 0;
+    double l2_levels = 4.0;             // levels per batch of the last call (L2 cost model)
+    L2Owner l2_owner;                   // the persisting-L2 set-aside this index raised
     // workspace for queries (grow-only)
     DevBuf w_q, w_hq, w_state, w_counters, w_cand, w_out, w_err, w_order, w_qb, w_ob, w_cbits,
         w_clist, w_bmsel, w_ovf, w_bmwork;
@@ -417,12 +420,16 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
                                  ix->prefix_off.as<int64_t>(), s));
     }
     if (ix->shadow) {
+        // residuals to 128-row group means, in the rows' order of the rerank
+        // (the locality-ordered copy when the index has bitmaps)
         QW_TRY(ix->Xb.ensure((size_t)n * d * 2));
         QW_TRY(ix->xnorm.ensure((size_t)n * sizeof(float)));
-        QW_TRY(launch_shadow_bf16(ix->X.as<float>(), n, d, ix->Xb.p, ix->xnorm.as<float>(), s));
+        QW_TRY(ix->Cg.ensure((size_t)((n + 127) / 128) * d * 2));
+        const float *Xs = ix->bitmaps ? ix->Xloc.as<float>() : ix->X.as<float>();
+        QW_TRY(launch_shadow_bf16(Xs, n, d, ix->Xb.p, ix->xnorm.as<float>(), ix->Cg.p, s));
     }
     QW_CUDA_TRY(cudaStreamSynchronize(s));
-    ix->device_bytes = (int64_t)(ix->Xb.bytes + ix->xnorm.bytes + ix->X.bytes + ix->A.bytes + ix->b.bytes + ix->o.bytes +
+    ix->device_bytes = (int64_t)(ix->Xb.bytes + ix->xnorm.bytes + ix->Cg.bytes + ix->X.bytes + ix->A.bytes + ix->b.bytes + ix->o.bytes +
                                  ix->span.bytes + ix->lid.bytes + ix->dir_bid.bytes +
                                  ix->dir_off.bytes + ix->dir_start.bytes + ix->dir_cnt.bytes +
                                  ix->bm.bytes + ix->bm_base.bytes + ix->bm_nb.bytes +
@@ -521,7 +528,7 @@ static qw_status level_path_rerun(qw_index *ix, const float *Qall, const int32_t
 // that stopped at their learned first level.
 static qw_status host_level_loop(qw_index *ix, LaunchTimer &tm, const IndexView &view, int nb,
                                  int cap, bool learned, bool bitmap, bool tma, int *err,
-                                 QueryState &st, cudaStream_t s)
+                                 QueryState &st, cudaStream_t s, int *levels_run)
 {
     unsigned long long max_top = 0;
     QW_CUDA_TRY(cudaMemcpyAsync(&max_top, st.max_top, sizeof(max_top), cudaMemcpyDeviceToHost, s));
@@ -538,6 +545,7 @@ static qw_status host_level_loop(qw_index *ix, LaunchTimer &tm, const IndexView 
                 ss.recount_first = bitmap && learned;
                 return launch_decide(nb, level, R, cap, st, s, nullptr, ss);
             }));
+            ++*levels_run;
             if ((unsigned long long)R > max_top) break;
             if (level > 62) {
                 set_error("qw_run_workload: level limit reached");
@@ -796,6 +804,39 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             st.bm_prof = reinterpret_cast<unsigned long long *>(ix->w_err.as<char>() + 64);
     }
 
+    // ---- persisting-L2 windows (the workload's index / data cache split)
+    L2Session l2;
+    const int l2_mode = qp ? qp->l2_mode : QW_L2_OFF;
+    if (l2_mode != QW_L2_OFF) {
+        // expected reads: per (query, level) the summaries of every tile
+        // (bitmap path) or the 2-byte ids of the level's bucket ranges (level
+        // and cluster paths: about c^(L-1) of the span + 1 bids); per query at
+        // most k + v data rows
+        const double L = std::max(1.0, ix->l2_levels);
+        L2Region ri, rd;
+        if (use_bitmap) {
+            ri.base = ix->bm_sum.p;
+            ri.bytes = ix->bm_sum.bytes;
+            ri.reads = (double)nq * L * ix->nT * m * 32.0;
+            rd.base = ix->Xloc.p;
+        } else {
+            ri.base = ix->lid.p;
+            ri.bytes = ix->lid.bytes;
+            const double frac = std::min(1.0, pow((double)ix->c, L - 1.0) / (ix->span_max + 1.0));
+            ri.reads = (double)nq * 2.0 * m * (double)ix->n * frac;
+            rd.base = ix->X.p;
+        }
+        rd.bytes = (size_t)ix->n * d * sizeof(float);
+        rd.reads = (double)nq * cap * d * sizeof(float);
+        QW_TRY(l2.begin(&ix->l2_owner, l2_mode, qp->l2_index_permille, ri, rd, s));
+    } else if (ix->l2_owner.raised) {
+        // a call without windows after calls with them: put the set-aside back
+        // and demote their persisting lines, so this call sees the plain L2
+        QW_CUDA_TRY(cudaStreamSynchronize(s));
+        l2_release(&ix->l2_owner);
+    }
+    int levels_run = 0;
+
     // ---- the whole workload: copy in (host mode), hash, order
     if (host)
         QW_CUDA_TRY(cudaMemcpyAsync(ix->w_q.p, queries, (size_t)nq * d * sizeof(float),
@@ -870,6 +911,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             if (want_cand) cids_b = f_cids + b0 * cap;
             if (want_cand && cand_col) ccol_b = f_ccol + b0 * cap;
         }
+        QW_TRY(l2.use(L2Use::Index, s));
         if (use_cluster) {
             int used = 0;
             QW_CUDA_TRY(cudaMemsetAsync(st.nkeep, 0, (size_t)nb * sizeof(int32_t), s));
@@ -899,11 +941,12 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             if (graph) {
                 QW_TRY(tm.run(QW_K_LEVEL, 0, [&] {
                     return run_level_graph(ix->graphs, view, nb, ix->l, ix->c, cap, learned,
-                                           use_bitmap, tma_loads, st, ctl, err, s);
+                                           use_bitmap, tma_loads, st, ctl, err, s,
+                                           l2.window(L2Use::Index));
                 }));
             } else {
                 QW_TRY(host_level_loop(ix, tm, view, nb, cap, learned, use_bitmap, tma_loads, err,
-                                       st, s));
+                                       st, s, &levels_run));
             }
             QW_TRY(tm.run(QW_K_SELECT, use_bitmap ? (learned ? 2 : 1) : 2, [&] {
                 if (use_bitmap && learned)
@@ -917,9 +960,11 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         }
         if (want_cand)
             QW_TRY(tm.run(QW_K_SELECT, 1, [&] { return launch_candidates_out(st, nb, cap, cids_b, ccol_b, s); }));
+        if (want_ids) QW_TRY(l2.use(L2Use::Data, s));
         if (want_ids && bf16)
             QW_TRY(tm.run(QW_K_RERANK, 1, [&] {
-                return launch_rerank_bf16(view, ix->Xb.p, ix->xnorm.as<float>(), Qb, nb, k, cap, st,
+                return launch_rerank_bf16(view, ix->Xb.p, ix->xnorm.as<float>(), ix->Cg.p,
+                                          Qb, nb, k, cap, st,
                                           ids_b, dists_b, tm.on ? rows_ctr : nullptr, s);
             }));
         else if (want_ids)
@@ -965,6 +1010,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             return QW_ERR_TIMEOUT;
         }
         ix->prof.launches[QW_K_LEVEL] += (int64_t)h_ctl.iters;
+        levels_run = (int)h_ctl.iters;
         ix->prof.launches[QW_K_DECIDE] += 2 * (int64_t)h_ctl.iters + n_batches * (learned ? 3 : 1);
         if (learned) {
             ix->prof.start_fallbacks += (int64_t)h_ctl.fb_total;
@@ -1008,6 +1054,12 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         ix->prof.bitmap_live_words += (int64_t)ctr[5];
     }
     ix->prof.queries += nq;
+    if (n_batches > 0 && levels_run > 0 && !use_cluster)
+        ix->l2_levels = (double)levels_run / (double)n_batches;
+    if (l2_mode != QW_L2_OFF) {
+        ix->prof.l2_setaside_bytes = (int64_t)l2.setaside;
+        ix->prof.l2_index_permille = l2.on ? l2.index_permille : 0;
+    }
     return QW_OK;
 }
 
@@ -1034,6 +1086,10 @@ static qw_status check_workload_args(const qw_index *ix, const float *queries, i
         if (qp->graph != 0 && qp->graph != 1) return arg_error("qw_run_workload: graph must be 0 or 1");
         if (qp->bitmap_loads != QW_LOADS_TMA && qp->bitmap_loads != QW_LOADS_DIRECT)
             return arg_error("qw_run_workload: unknown bitmap_loads");
+        if (qp->l2_mode < QW_L2_OFF || qp->l2_mode > QW_L2_MODEL)
+            return arg_error("qw_run_workload: unknown l2_mode");
+        if (qp->l2_index_permille < 0 || qp->l2_index_permille > 1000)
+            return arg_error("qw_run_workload: l2_index_permille must be in [0, 1000]");
         for (int r = 0; r < 1; ++r)
             if (qp->reserved[r] != 0) return arg_error("qw_run_workload: reserved field set");
     }
@@ -1066,6 +1122,8 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
     p0.start = QW_START_PLAIN;
     p0.graph = 0;
     p0.clusters = 0;
+    p0.l2_mode = QW_L2_OFF;
+    p0.l2_index_permille = 0;
     QW_TRY(check_workload_args(ix, queries, nq, k, &p0, mem));
     if (!best) return arg_error("qw_autotune: best is null");
     if (reps < 1) return arg_error("qw_autotune: reps < 1");
@@ -1228,6 +1286,13 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
             alt.rerank = QW_RERANK_BF16;
             if ((status = try_alt(alt)) != QW_OK) break;
         }
+        // 8. persisting-L2 windows split by the cost model
+        {
+            qw_query_params alt = cur;
+            alt.l2_mode = QW_L2_MODEL;
+            alt.l2_index_permille = 0;
+            if ((status = try_alt(alt)) != QW_OK) break;
+        }
     } while (false);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1362,7 +1427,8 @@ void qw_index_free(qw_index *ix)
 {
     if (!ix) return;
     cudaDeviceSynchronize();
-    DevBuf *bufs[] = {&ix->X, &ix->Xb, &ix->xnorm, &ix->A, &ix->b, &ix->o, &ix->span, &ix->lid,
+    l2_release(&ix->l2_owner);
+    DevBuf *bufs[] = {&ix->X, &ix->Xb, &ix->xnorm, &ix->Cg, &ix->A, &ix->b, &ix->o, &ix->span, &ix->lid,
                       &ix->dir_bid,
                       &ix->dir_off, &ix->dir_start, &ix->dir_cnt, &ix->w_q, &ix->w_hq,
                       &ix->w_state, &ix->w_counters, &ix->w_cand, &ix->w_out, &ix->w_err,

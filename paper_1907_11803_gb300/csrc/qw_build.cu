@@ -210,33 +210,59 @@ __global__ void export_kernel(const uint16_t *__restrict__ lid, const int32_t *_
     }
 }
 
-// BF16 copy of the data (round to nearest even) and an upper bound of each
-// row's Euclidean norm (FP64 sum, rounded up to float).
-__global__ void shadow_bf16_kernel(const float *__restrict__ X, int64_t n, int d,
-                                   __nv_bfloat16 *__restrict__ Xb, float *__restrict__ xnorm)
+// Residual BF16 copy of the data, for the BF16 pre-filter of the rerank.
+// Rows are taken in the index's row order (the locality order when the index
+// has bitmaps: 128 consecutive rows are then spatially compact) and grouped
+// by 128.  C[g] is the mean of group g (FP64 sums) rounded to BF16; row r is
+// stored as Rb[r] = bf16(fl32(x_r - C[r / 128])), with rnorm[r] an upper bound
+// of the Euclidean norm of the FP32 residual fl32(x_r - C[r / 128]).  Within a
+// group the residuals are about the group's spread, far smaller than the rows
+// themselves, so the BF16 rounding error (2^-8 of the residual) is small.  The
+// mean itself is any fixed vector for the error bound, so it is kept in BF16
+// (exact in FP32) to halve what the pre-filter reads.
+__global__ void group_centroid_kernel(const float *__restrict__ Xs, int64_t n, int d,
+                                      __nv_bfloat16 *__restrict__ C)
+{
+    const int64_t g = blockIdx.x;
+    const int64_t r0 = g * 128, r1 = min(n, r0 + 128);
+    for (int c = threadIdx.x; c < d; c += blockDim.x) {
+        double s = 0.0;
+        for (int64_t r = r0; r < r1; ++r) s += (double)Xs[r * d + c];
+        C[g * d + c] = __double2bfloat16(s / (double)(r1 - r0));
+    }
+}
+
+__global__ void shadow_residual_kernel(const float *__restrict__ Xs, int64_t n, int d,
+                                       const __nv_bfloat16 *__restrict__ C,
+                                       __nv_bfloat16 *__restrict__ Rb, float *__restrict__ rnorm)
 {
     const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= n) return;
-    const float *x = X + r * d;
+    const float *x = Xs + r * d;
+    const __nv_bfloat16 *cg = C + (r >> 7) * d;
     double s = 0.0;
     for (int j = lane; j < d; j += 32) {
-        const float v = x[j];
-        Xb[r * d + j] = __float2bfloat16_rn(v);
+        const float v = __fsub_rn(x[j], __bfloat162float(cg[j]));
+        Rb[r * d + j] = __float2bfloat16_rn(v);
         s += (double)v * (double)v;
     }
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) xnorm[r] = __double2float_ru(sqrt(s) * (1.0 + 1e-12));
+    if (lane == 0) rnorm[r] = __double2float_ru(sqrt(s) * (1.0 + 1e-12));
 }
 
 }  // namespace
 
-qw_status launch_shadow_bf16(const float *X, int64_t n, int d, void *Xb, float *xnorm,
-                             cudaStream_t s)
+qw_status launch_shadow_bf16(const float *Xs, int64_t n, int d, void *Rb, float *rnorm,
+                             void *C, cudaStream_t s)
 {
+    const int64_t groups = (n + 127) / 128;
+    __nv_bfloat16 *Cb = reinterpret_cast<__nv_bfloat16 *>(C);
+    group_centroid_kernel<<<(unsigned)groups, 128, 0, s>>>(Xs, n, d, Cb);
+    QW_CUDA_TRY(cudaGetLastError());
     const int64_t blocks = (n + 7) / 8;
-    shadow_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(
-        X, n, d, reinterpret_cast<__nv_bfloat16 *>(Xb), xnorm);
+    shadow_residual_kernel<<<(unsigned)blocks, 256, 0, s>>>(
+        Xs, n, d, Cb, reinterpret_cast<__nv_bfloat16 *>(Rb), rnorm);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }

@@ -13,10 +13,12 @@
 // those of the host loop, so the results are the same.
 //
 // Graphs are cached per batch shape (batch size, every workspace pointer the
-// kernels take, and the index's parameters): a workload of full batches and
-// one short batch instantiates two graphs on its first call and none
-// afterwards.
+// kernels take, and the index's parameters) and per persisting-L2 window: a
+// workload of full batches and one short batch instantiates two graphs on its
+// first call and none afterwards.  The window (see qw_l2.cu) is set on every
+// kernel node of the graph, loop bodies included.
 #include "qw_internal.cuh"
+#include "qw_l2.cuh"
 
 #include <string.h>
 
@@ -31,12 +33,16 @@ struct GraphKey {
     const void *lid;       // the index
     const void *ctl;
     const void *err;
+    const void *win_base;  // persisting-L2 window of the kernel nodes
+    size_t win_bytes;
+    float win_hit;
     bool operator==(const GraphKey &o) const
     {
         return nb == o.nb && l == o.l && cgrow == o.cgrow && cap == o.cap &&
                learned == o.learned && bitmap == o.bitmap && tma == o.tma &&
                memcmp(&st, &o.st, sizeof(QueryState)) == 0 && lid == o.lid && ctl == o.ctl &&
-               err == o.err;
+               err == o.err && win_base == o.win_base && win_bytes == o.win_bytes &&
+               win_hit == o.win_hit;
     }
 };
 
@@ -97,6 +103,26 @@ qw_status sinks(cudaGraph_t g, std::vector<cudaGraphNode_t> &out)
     return QW_OK;
 }
 
+// Set the access-policy window on every kernel node of g (num_bytes 0
+// clears it).
+qw_status set_window(cudaGraph_t g, const cudaAccessPolicyWindow &win)
+{
+    size_t n = 0;
+    QW_CUDA_TRY(cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    QW_CUDA_TRY(cudaGraphGetNodes(g, nodes.data(), &n));
+    cudaKernelNodeAttrValue v{};
+    v.accessPolicyWindow = win;
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        QW_CUDA_TRY(cudaGraphNodeGetType(nd, &t));
+        if (t == cudaGraphNodeTypeKernel)
+            QW_CUDA_TRY(cudaGraphKernelNodeSetAttribute(
+                nd, cudaKernelNodeAttributeAccessPolicyWindow, &v));
+    }
+    return QW_OK;
+}
+
 qw_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
                     cudaGraphConditionalHandle h, cudaGraph_t *body)
 {
@@ -113,7 +139,8 @@ qw_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
 
 qw_status build(LevelGraphCache *c, const GraphKey &key, const IndexView &ix, int nb, int l,
                 int cgrow, int cap, bool learned, bool bitmap, bool tma, QueryState &st,
-                LoopCtl *ctl, int *err, cudaGraph_t *graph_out)
+                LoopCtl *ctl, int *err, const cudaAccessPolicyWindow &win,
+                cudaGraph_t *graph_out)
 {
     cudaStream_t cs = c->cap_stream;
     cudaGraph_t g = nullptr;
@@ -146,6 +173,7 @@ qw_status build(LevelGraphCache *c, const GraphKey &key, const IndexView &ix, in
         };
     };
     if ((s = capture_into(cs, body, nullptr, 0, level_body(h1))) != QW_OK) return fail(s);
+    if (win.num_bytes > 0 && (s = set_window(body, win)) != QW_OK) return fail(s);
     if (learned) {
         // loop 2: the queries that stopped at their learned first level, from level 0
         e = cudaGraphConditionalHandleCreate(&h2, g, 0, cudaGraphCondAssignDefault);
@@ -158,7 +186,9 @@ qw_status build(LevelGraphCache *c, const GraphKey &key, const IndexView &ix, in
         cudaGraph_t body2;
         if ((s = add_while(g, tail, h2, &body2)) != QW_OK) return fail(s);
         if ((s = capture_into(cs, body2, nullptr, 0, level_body(h2))) != QW_OK) return fail(s);
+        if (win.num_bytes > 0 && (s = set_window(body2, win)) != QW_OK) return fail(s);
     }
+    if (win.num_bytes > 0 && (s = set_window(g, win)) != QW_OK) return fail(s);
     (void)key;
     *graph_out = g;
     return QW_OK;
@@ -169,6 +199,15 @@ qw_status build(LevelGraphCache *c, const GraphKey &key, const IndexView &ix, in
 qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l, int cgrow,
                           int cap, bool learned, bool bitmap, bool tma, QueryState &st,
                           LoopCtl *ctl, int *err, cudaStream_t s)
+{
+    return run_level_graph(c, ix, nb, l, cgrow, cap, learned, bitmap, tma, st, ctl, err, s,
+                           cudaAccessPolicyWindow{});
+}
+
+qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l, int cgrow,
+                          int cap, bool learned, bool bitmap, bool tma, QueryState &st,
+                          LoopCtl *ctl, int *err, cudaStream_t s,
+                          const cudaAccessPolicyWindow &win)
 {
     if (!c) {
         set_error("internal: no graph cache");
@@ -187,6 +226,11 @@ qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l
     key.lid = ix.lid;
     key.ctl = ctl;
     key.err = err;
+    if (win.num_bytes > 0) {
+        key.win_base = win.base_ptr;
+        key.win_bytes = win.num_bytes;
+        key.win_hit = win.hitRatio;
+    }
     for (auto &en : c->entries)
         if (en.key == key) {
             QW_CUDA_TRY(cudaGraphLaunch(en.exec, s));
@@ -199,7 +243,7 @@ qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l
         c->entries.erase(c->entries.begin());
     }
     cudaGraph_t g = nullptr;
-    QW_TRY(build(c, key, ix, nb, l, cgrow, cap, learned, bitmap, tma, st, ctl, err, &g));
+    QW_TRY(build(c, key, ix, nb, l, cgrow, cap, learned, bitmap, tma, st, ctl, err, win, &g));
     cudaGraphExec_t ex = nullptr;
     const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
     if (e != cudaSuccess) {

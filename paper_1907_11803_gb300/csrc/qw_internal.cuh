@@ -293,12 +293,17 @@ qw_status launch_scatter(const int32_t *perm, int64_t b0, int nb, int k, int cap
 qw_status launch_sum_i32(const int32_t *v, int n, unsigned long long *out, cudaStream_t s);
 qw_status launch_candidates_out(const QueryState &st, int nb, int cap, int64_t *cand_ids,
                                 int32_t *cand_col, cudaStream_t s);
-qw_status launch_rerank_bf16(const IndexView &ix, const void *Xb, const float *xnorm,
-                             const float *Qb, int nb, int k, int cap, const QueryState &st,
-                             int64_t *ids_out, float *dists_out,
+// BF16 pre-filter then the FP32 / FP64 stages.  Rb, rnorm, C: the residual
+// BF16 copy built by launch_shadow_bf16 over the index's row order (the
+// locality order when the index has bitmaps, read through ix.inv).
+qw_status launch_rerank_bf16(const IndexView &ix, const void *Rb, const float *rnorm,
+                             const void *C, const float *Qb, int nb, int k, int cap,
+                             const QueryState &st, int64_t *ids_out, float *dists_out,
                              unsigned long long *rows_fp32, cudaStream_t s);
-qw_status launch_shadow_bf16(const float *X, int64_t n, int d, void *Xb, float *xnorm,
-                             cudaStream_t s);
+// Rows Xs (n x d) grouped by 128: C (ceil(n / 128) x d BF16) the group means,
+// Rb (n x d BF16) the residuals to them, rnorm (n) bounds of the residual norms.
+qw_status launch_shadow_bf16(const float *Xs, int64_t n, int d, void *Rb, float *rnorm,
+                             void *C, cudaStream_t s);
 // Xrows/row_of (optional): read data id `id` from row row_of[id] of Xrows
 // (the bitmap path's copy of the data in locality order).
 qw_status launch_rerank(const IndexView &ix, const float *Qb, int nb, int k, int cap,

@@ -359,104 +359,161 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(
 }
 
 // BF16 pre-filter.  Distances to every kept candidate are first computed from
-// the index's BF16 copy of the data (half the bytes).  With x_bf16 = x (1 + e),
-// |e| <= 2^-8, the BF16 value a of sum (q - x)^2 obeys
-//   |a - exact| <= rho t + 2^-7 (sqrt(t) + 2^-8 |x|) |x| + 2^-16 |x|^2,
-// t = a / (1 - rho), with rho the FP32 summation bound of the FP32 stage and
-// |x| an upper bound of the row's norm kept with the copy.  A candidate whose
-// lower bound exceeds the k-th smallest upper bound cannot be among the k
-// nearest; all others go through the exact FP32 + FP64 stages.  The result is
-// the same as without the pre-filter.
+// the index's residual BF16 copy (half the bytes of the rows): row r of the
+// rerank's row order is stored as r~ = bf16(r), r = fl32(x - C_g), C_g the
+// mean of its 128-row group g = r / 128 rounded to BF16 (in the locality order the group
+// is spatially compact, so |r| is about the group's spread).  The kernel forms
+// u = fl32(q - C_g) and a = the FP32 sum of fl32(u - r~)^2 (per-lane FMA
+// chains, butterfly sum: relative error <= rho, as in the FP32 stage).
+// With w = u - r~ (exact), v = q - x, and R >= |r|:
+//   |w - v| <= |u - (q - C_g)| + |(x - C_g) - r| + |r - r~|
+//           <= 2^-24 |q - C_g| + 2^-24 |x - C_g| + 2^-8 R,
+// and |q - C_g| <= |v| + |x - C_g|, |v| <= |w| + |w - v|, |x - C_g| <=
+// R / (1 - 2^-24), so |w - v| <= E = 1.001 (2^-8 R + 2^-23 R + 2^-24 W_hi),
+// W_hi = sqrt(a / (1 - rho)) >= |w|, W_lo = sqrt(a / (1 + rho)) <= |w|.
+// Hence |v|^2 lies in [max(0, W_lo - E)^2, (W_hi + E)^2]; every bound is
+// formed in FP32 with relative margins of 2^-18 that cover the rounding of the
+// bound arithmetic itself (no FP64 work per candidate).  A
+// candidate whose lower bound exceeds the k-th smallest upper bound cannot be
+// among the k nearest (the k candidates with the smallest upper bounds all lie
+// within it); all others go through the exact FP32 + FP64 stages on the FP32
+// rows, so the result is the same as without the pre-filter.
 __global__ void __launch_bounds__(RR_THREADS) rerank_bf16_kernel(
-    const float *__restrict__ X, const __nv_bfloat16 *__restrict__ Xb,
-    const float *__restrict__ xnorm, int d, const float *__restrict__ Qb, int k, int cap, int P2,
+    const float *__restrict__ Xr, const int32_t *__restrict__ row_of,
+    const __nv_bfloat16 *__restrict__ Rb, const float *__restrict__ rnorm,
+    const __nv_bfloat16 *__restrict__ Cg, int d, const float *__restrict__ Qb, int k, int cap, int P2,
     const int32_t *__restrict__ cand, const int32_t *__restrict__ nkeep,
-    int64_t *__restrict__ ids_out, float *__restrict__ dists_out, bool vec,
-    unsigned long long *__restrict__ rows_fp32)
+    int64_t *__restrict__ ids_out, float *__restrict__ dists_out, bool vec, float inv_omr,
+    float inv_opr, unsigned long long *__restrict__ rows_fp32)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int scan_tmp[RR_WARPS];
     __shared__ int any_mark;
-    __shared__ float s_uk;
     __shared__ int hist[256];
     __shared__ int bc[4];
     RerankSmem sm = carve_rerank(smraw, P2, scan_tmp, &any_mark, hist, bc);
     int32_t *cid = reinterpret_cast<int32_t *>(sm.mark + P2 + 15 - ((P2 + 15) % 16));  // P2 ids
-    float *ubs = reinterpret_cast<float *>(cid + P2);                                   // P2 bounds
     const int q = blockIdx.x;
     const int nc = nkeep[q];
     const float *qv = Qb + (int64_t)q * d;
     const int32_t *cl = cand + (int64_t)q * cap;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const double rho = (double)((d + 31) / 32 + 12) * 5.9604644775390625e-08 * 1.02;
 
-    // A. BF16 distances and their bounds (d32 <- lower, outd <- upper)
-    for (int j = warp; j < P2; j += RR_WARPS) {
-        if (j >= nc) {
-            if (lane == 0) ubs[j] = CUDART_INF_F;
-            continue;
-        }
+    // A. BF16 distances and their bounds (d32 <- lower, outd <- upper).  A
+    //    warp takes kRows candidates at a time (kRows independent row loads
+    //    per lane in flight); lane u then forms the bounds of row u.
+    // 0. the row of every candidate (staged in `key`, free until the FP32
+    //    stage), so the loop below starts its row loads without a dependent
+    //    chain of global reads
+    int32_t *rowi = reinterpret_cast<int32_t *>(sm.key);
+    for (int j = threadIdx.x; j < nc; j += RR_THREADS) {
         const int32_t id = cl[j];
-        const __nv_bfloat16 *xb = Xb + (int64_t)id * d;
-        float acc = 0.0f;
+        rowi[j] = row_of ? row_of[id] : id;
+        cid[j] = id;
+    }
+    __syncthreads();
+    constexpr int kRows = 4;
+    // the query's 16-byte chunks c = lane + 32 i (i < kQReg) stay in registers
+    constexpr int kQReg = 2;
+    const int nch4 = d >> 2;
+    float4 qreg[kQReg];
+#pragma unroll
+    for (int i = 0; i < kQReg; ++i) {
+        const int c = lane + 32 * i;
+        qreg[i] = (vec && c < nch4) ? __ldg(reinterpret_cast<const float4 *>(qv) + c)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int j0 = warp * kRows; j0 < nc; j0 += RR_WARPS * kRows) {
+        int64_t row[kRows];
+        float acc[kRows];
+#pragma unroll
+        for (int u = 0; u < kRows; ++u) {
+            const int j = j0 + u;
+            row[u] = j < nc ? (int64_t)rowi[j] : -1;
+            acc[u] = 0.0f;
+        }
+        // lane u fetches row u's residual-norm bound early
+        const int jm = j0 + lane;
+        const float R = (lane < kRows && jm < nc) ? __ldg(rnorm + rowi[jm]) : 0.0f;
         if (vec) {
-            const uint2 *x2 = reinterpret_cast<const uint2 *>(xb);
-            const float4 *q4 = reinterpret_cast<const float4 *>(qv);
-            for (int c = lane; c < (d >> 2); c += 32) {
-                const uint2 raw = __ldg(x2 + c);
-                const float4 b = __ldg(q4 + c);
-                const float x0 = __uint_as_float(raw.x << 16), x1 = __uint_as_float(raw.x & 0xffff0000u);
-                const float x2v = __uint_as_float(raw.y << 16), x3 = __uint_as_float(raw.y & 0xffff0000u);
-                float t0 = b.x - x0, t1 = b.y - x1, t2 = b.z - x2v, t3 = b.w - x3;
-                acc = fmaf(t0, t0, acc);
-                acc = fmaf(t1, t1, acc);
-                acc = fmaf(t2, t2, acc);
-                acc = fmaf(t3, t3, acc);
+            const uint2 *r2[kRows];
+            const uint2 *g2[kRows];
+#pragma unroll
+            for (int u = 0; u < kRows; ++u) {
+                const int64_t rr = row[u] >= 0 ? row[u] : row[0];
+                r2[u] = reinterpret_cast<const uint2 *>(Rb + rr * d);
+                g2[u] = reinterpret_cast<const uint2 *>(Cg + (rr >> 7) * d);
             }
+            // one 16-byte chunk of the query against 4 BF16 of each row
+            auto chunk = [&](int c, const float4 b) {
+                uint2 raw[kRows], gr[kRows];
+#pragma unroll
+                for (int u = 0; u < kRows; ++u) {
+                    raw[u] = __ldg(r2[u] + c);
+                    gr[u] = __ldg(g2[u] + c);
+                }
+#pragma unroll
+                for (int u = 0; u < kRows; ++u) {
+                    const float t0 = (b.x - __uint_as_float(gr[u].x << 16)) -
+                                     __uint_as_float(raw[u].x << 16);
+                    const float t1 = (b.y - __uint_as_float(gr[u].x & 0xffff0000u)) -
+                                     __uint_as_float(raw[u].x & 0xffff0000u);
+                    const float t2 = (b.z - __uint_as_float(gr[u].y << 16)) -
+                                     __uint_as_float(raw[u].y << 16);
+                    const float t3 = (b.w - __uint_as_float(gr[u].y & 0xffff0000u)) -
+                                     __uint_as_float(raw[u].y & 0xffff0000u);
+                    acc[u] = fmaf(t0, t0, acc[u]);
+                    acc[u] = fmaf(t1, t1, acc[u]);
+                    acc[u] = fmaf(t2, t2, acc[u]);
+                    acc[u] = fmaf(t3, t3, acc[u]);
+                }
+            };
+#pragma unroll
+            for (int i = 0; i < kQReg; ++i) {
+                const int c = lane + 32 * i;
+                if (c < nch4) chunk(c, qreg[i]);
+            }
+            for (int c = lane + 32 * kQReg; c < nch4; c += 32)
+                chunk(c, __ldg(reinterpret_cast<const float4 *>(qv) + c));
         } else {
             for (int c = lane; c < d; c += 32) {
-                const float t0 = __ldg(qv + c) - __bfloat162float(xb[c]);
-                acc = fmaf(t0, t0, acc);
-            }
-        }
-        acc = warp_sum(acc);
-        if (lane == 0) {
-            const double a = (double)acc;
-            const double xn = (double)xnorm[id];
-            const double t = a / (1.0 - rho);
-            const double bound = rho * t + 0.0078125 * (sqrt(t) + 0.00390625 * xn) * xn +
-                                 1.52587890625e-05 * xn * xn + 1e-12 * t;
-            sm.d32[j] = __double2float_rd(a - bound);
-            const float ub = __double2float_ru(a + bound);
-            sm.outd[j] = ub;
-            ubs[j] = ub;
-            cid[j] = id;
-        }
-    }
-    __syncthreads();
-    // B. the k-th smallest upper bound
-    if (nc > k) {
-        for (int kk = 2; kk <= P2; kk <<= 1) {
-            for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-                for (int x = threadIdx.x; x < (P2 >> 1); x += RR_THREADS) {
-                    const int a = 2 * x - (x & (jj - 1));
-                    const int c = a + jj;
-                    const bool up = (a & kk) == 0;
-                    if ((ubs[a] > ubs[c]) == up) {
-                        const float t = ubs[a];
-                        ubs[a] = ubs[c];
-                        ubs[c] = t;
-                    }
+                const float qc = __ldg(qv + c);
+#pragma unroll
+                for (int u = 0; u < kRows; ++u) {
+                    if (row[u] < 0) continue;
+                    const float t0 = (qc - __bfloat162float(Cg[(row[u] >> 7) * d + c])) -
+                                     __bfloat162float(Rb[row[u] * d + c]);
+                    acc[u] = fmaf(t0, t0, acc[u]);
                 }
-                __syncthreads();
             }
         }
-        if (threadIdx.x == 0) s_uk = ubs[k - 1];
-    } else if (threadIdx.x == 0) {
-        s_uk = CUDART_INF_F;
+        float mine = 0.0f;
+#pragma unroll
+        for (int u = 0; u < kRows; ++u) {
+            const float sum = warp_sum(acc[u]);
+            if (lane == u) mine = sum;
+        }
+        const int j = j0 + lane;
+        if (lane < kRows && j < nc) {
+            // bounds in FP32: every quantity below is within a few units in
+            // the last place of its exact value (rsqrtf: 2 ulp), covered by
+            // the 2^-18 margins
+            const float thi = mine * inv_omr, tlo = mine * inv_opr;
+            const float whi = thi > 0.0f ? thi * rsqrtf(thi) : 0.0f;
+            const float wlo = tlo > 0.0f ? tlo * rsqrtf(tlo) : 0.0f;
+            const float e = 1.001f * (0x1.02p-8f * R + 0x1p-24f * whi);
+            const float lo = fmaxf(wlo * (1.0f - 0x1p-18f) - e * (1.0f + 0x1p-18f), 0.0f);
+            const float hi = (whi + e) * (1.0f + 0x1p-18f);
+            sm.d32[j] = lo * lo * (1.0f - 0x1p-18f);
+            sm.outd[j] = hi * hi * (1.0f + 0x1p-18f);
+        }
     }
     __syncthreads();
-    const float uk = s_uk;
+    // B. the k-th smallest upper bound (non-negative: ordered like its bits)
+    float uk = CUDART_INF_F;
+    if (nc > k)
+        uk = __uint_as_float(block_kth_smallest<RR_THREADS>(
+            reinterpret_cast<const uint32_t *>(sm.outd), nc, k, sm.hist, sm.bc));
     // C. keep the candidates that could be among the k nearest, in list order
     const int per = (nc + RR_THREADS - 1) / RR_THREADS;
     const int j0 = min(nc, (int)threadIdx.x * per), j1 = min(nc, j0 + per);
@@ -470,28 +527,35 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_bf16_kernel(
     if (rows_fp32 && threadIdx.x == 0) atomicAdd(rows_fp32, (unsigned long long)ns);
     int P2s = 2;
     while (P2s < ns) P2s <<= 1;
-    rerank_finish(X, nullptr, d, qv, k, P2s, ns, sm, ids_out + (int64_t)q * k, dists_out + (int64_t)q * k,
-                  vec);
+    rerank_finish(Xr, row_of, d, qv, k, P2s, ns, sm, ids_out + (int64_t)q * k,
+                  dists_out + (int64_t)q * k, vec);
 }
 
 }  // namespace
 
-qw_status launch_rerank_bf16(const IndexView &ix, const void *Xb, const float *xnorm,
-                             const float *Qb, int nb, int k, int cap, const QueryState &st,
-                             int64_t *ids_out, float *dists_out,
+qw_status launch_rerank_bf16(const IndexView &ix, const void *Rb, const float *rnorm,
+                             const void *C, const float *Qb, int nb, int k, int cap,
+                             const QueryState &st, int64_t *ids_out, float *dists_out,
                              unsigned long long *rows_fp32, cudaStream_t s)
 {
     int P2 = 2;
     while (P2 < cap) P2 <<= 1;
     const size_t smem = (size_t)P2 * (sizeof(double) + 2 * sizeof(float) + sizeof(int32_t) + 1) +
-                        16 + (size_t)P2 * (sizeof(int32_t) + sizeof(float));
+                        16 + (size_t)P2 * sizeof(int32_t);
     QW_CUDA_TRY(cudaFuncSetAttribute(rerank_bf16_kernel,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const bool vec = (ix.d % 4 == 0) && ((uintptr_t)Qb % 16 == 0) && ((uintptr_t)ix.X % 16 == 0) &&
-                     ((uintptr_t)Xb % 8 == 0);
+    // rows in the locality order when the index has them (the copy's order)
+    const float *Xr = ix.Xloc ? ix.Xloc : ix.X;
+    const int32_t *row_of = ix.Xloc ? ix.inv : nullptr;
+    const bool vec = (ix.d % 4 == 0) && ((uintptr_t)Qb % 16 == 0) && ((uintptr_t)Xr % 16 == 0) &&
+                     ((uintptr_t)Rb % 8 == 0) && ((uintptr_t)C % 8 == 0);
+    // rho of the FP32 summation (the FP32 stage's bound): 1 / (1 -/+ rho)
+    const double rho = (double)((ix.d + 31) / 32 + 12) * 5.9604644775390625e-08 * 1.02;
+    const float inv_omr = (float)(1.0 / (1.0 - rho)), inv_opr = (float)(1.0 / (1.0 + rho));
     rerank_bf16_kernel<<<nb, RR_THREADS, smem, s>>>(
-        ix.X, reinterpret_cast<const __nv_bfloat16 *>(Xb), xnorm, ix.d, Qb, k, cap, P2, st.cand,
-        st.nkeep, ids_out, dists_out, vec, rows_fp32);
+        Xr, row_of, reinterpret_cast<const __nv_bfloat16 *>(Rb), rnorm,
+        reinterpret_cast<const __nv_bfloat16 *>(C), ix.d, Qb, k, cap, P2,
+        st.cand, st.nkeep, ids_out, dists_out, vec, inv_omr, inv_opr, rows_fp32);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }

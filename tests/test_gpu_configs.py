@@ -47,3 +47,16 @@ def test_config_parity(qwlib, cuda, name, path):
     assert np.array_equal(g["stats2"], ref["stats"])
     _check_candidates(g["cid"], g["ccol"], ref["cand_ids"], ref["cand_col"])
     g["index"].free()
+
+
+@pytest.mark.parametrize("path", ["levels", "bitmap_direct_graph"])
+def test_bf16_rerank_config_parity(qwlib, cuda, path):
+    """The BF16 pre-filter on the 512-dimensional shape with k = 50 (the
+    configuration the pre-filter is specified for): oracle ids and distances."""
+    wl, l, ref = _case("mix4m_d512")
+    s = wl.spec
+    g = _gpu_workload(qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=s.w, k=s.k, v=s.v, l=l, c=s.c,
+                      path=path, order="signature", batch=17, rerank="bf16")
+    _check_results(g["ids"], g["dists"], ref["ids"], ref["dists"])
+    assert np.array_equal(g["stats"], ref["stats"])
+    g["index"].free()

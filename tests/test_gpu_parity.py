@@ -245,9 +245,10 @@ def test_bitmap_many_projections(orc, qwlib, cuda, path, m):
     _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=10, v=60, path=path)
 
 
+@pytest.mark.parametrize("rerank", ["fp32", "bf16"])
 @pytest.mark.parametrize("path", ["levels", "bitmap_direct_graph"])
 @pytest.mark.parametrize("shell", [12, 60])
-def test_rerank_near_ties_at_k(orc, qwlib, cuda, path, shell):
+def test_rerank_near_ties_at_k(orc, qwlib, cuda, path, shell, rerank):
     """A shell of `shell` points whose distances to the query agree to about
     1e-7 holds the k-th nearest: FP32 cannot order them, the rerank must take
     the FP64 order (ties by id).  With 12 points the run past position k is
@@ -265,7 +266,8 @@ def test_rerank_near_ties_at_k(orc, qwlib, cuda, path, shell):
     X = (q + u * r[perm, None]).astype(np.float32)
     Q = q[None, :].astype(np.float32)
     wl = workloads.make_workload("mix10k_d32", seed=7, n=64, nq=1, d=d, m=8)
-    _full_parity(orc, qwlib, cuda, X, Q, wl.A, wl.b, w=4.0, k=k, v=n, l=2, path=path)
+    _full_parity(orc, qwlib, cuda, X, Q, wl.A, wl.b, w=4.0, k=k, v=n, l=2, path=path,
+                 rerank=rerank)
 
 
 def test_empty_workload(qwlib, cuda):
@@ -277,13 +279,29 @@ def test_empty_workload(qwlib, cuda):
     index.free()
 
 
+@pytest.mark.parametrize("path", ["levels", "bitmap_direct_graph"])
 @pytest.mark.parametrize("d", [32, 30])
-def test_bf16_prefilter_rerank_is_exact(orc, qwlib, cuda, d):
+def test_bf16_prefilter_rerank_is_exact(orc, qwlib, cuda, d, path):
     """The BF16 pre-filter keeps every candidate that could be among the k
     nearest: same ids as the oracle, distances within 1e-5 (d = 30 takes the
-    scalar, unaligned path)."""
+    scalar, unaligned path; an index with bitmaps keeps its residual copy in
+    the locality order, one without in data order)."""
     wl = workloads.make_workload("mix10k_d32", seed=31, n=6000, nq=80, d=d)
-    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=10, v=300, rerank="bf16")
+    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=10, v=300, rerank="bf16",
+                 path=path)
+
+
+def test_bf16_prefilter_ragged_groups_and_duplicates(orc, qwlib, cuda):
+    """Residual groups of 128 rows with a ragged last group, exact duplicate
+    rows (zero residual spread within a tie) and queries that are data rows
+    (distance 0): the bound must hold at both ends."""
+    wl = workloads.make_workload("mix10k_d32", seed=33, n=5 * 128 + 37, nq=30, n_clusters=4)
+    X = wl.X.copy()
+    X[100:140] = X[99]
+    Q = np.concatenate([X[[3, 99, 120, 600]], wl.Q[:26]]).astype(np.float32)
+    for path in ("levels", "bitmap_direct"):
+        _full_parity(orc, qwlib, cuda, X, Q, wl.A, wl.b, w=4.0, k=12, v=200, rerank="bf16",
+                     path=path)
 
 
 def test_bf16_prefilter_reads_fewer_fp32_rows(qwlib, cuda):
