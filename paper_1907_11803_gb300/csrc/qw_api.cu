@@ -486,16 +486,27 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                           const qw_query_params *qp, int64_t *ids, float *dists, int64_t *stats,
                           int64_t *cand_ids, int32_t *cand_col, int32_t mem, cudaStream_t s);
 
-// Answer the workload queries listed in `list` (device, n of them) again on
-// the level path and write their rows of the outputs.  Used for the rare
-// queries whose candidates overflow the bitmap path's fixed buffers.
+// Workspace of one batch on the bitmap path (its default batch size).
+constexpr int64_t kBitmapBudget = (int64_t)48 << 30;
+
+// Answer the workload queries listed in `list` (device, n of them) again and
+// write their rows of the outputs: on the level path (`rerun` null) for the
+// rare queries whose candidates overflow the bitmap path's fixed buffers, or
+// with the given settings (the bitmap path from level 0, for queries whose
+// learned first level was too late).  The list is copied first: the nested
+// call reuses the workspace it lives in.
 static qw_status level_path_rerun(qw_index *ix, const float *Qall, const int32_t *HQall,
                                   const int32_t *list, int n, int k, int cap, int64_t *f_ids,
                                   float *f_dists, int64_t *f_stats, int64_t *f_cids,
-                                  int32_t *f_ccol, cudaStream_t s)
+                                  int32_t *f_ccol, cudaStream_t s,
+                                  const qw_query_params *rerun = nullptr)
 {
     const int d = ix->d, m = ix->m;
-    DevBuf q_in, hq_in, o_ids, o_dists, o_stats, o_cids, o_ccol;
+    DevBuf lst, q_in, hq_in, o_ids, o_dists, o_stats, o_cids, o_ccol;
+    QW_TRY(lst.ensure((size_t)n * sizeof(int32_t)));
+    QW_CUDA_TRY(cudaMemcpyAsync(lst.p, list, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                s));
+    list = lst.as<int32_t>();
     QW_TRY(q_in.ensure((size_t)n * d * sizeof(float)));
     QW_TRY(hq_in.ensure((size_t)n * m * sizeof(int32_t)));
     QW_TRY(launch_gather(Qall, HQall, list, 0, n, d, m, q_in.as<float>(), hq_in.as<int32_t>(), s));
@@ -507,14 +518,24 @@ static qw_status level_path_rerun(qw_index *ix, const float *Qall, const int32_t
     if (f_cids) QW_TRY(o_cids.ensure((size_t)n * cap * sizeof(int64_t)));
     if (f_ccol) QW_TRY(o_ccol.ensure((size_t)n * cap * sizeof(int32_t)));
     qw_query_params p{};
-    p.path = QW_PATH_LEVELS;
-    p.order = QW_ORDER_GIVEN;
+    if (rerun) {
+        p = *rerun;
+    } else {
+        p.path = QW_PATH_LEVELS;
+        p.order = QW_ORDER_GIVEN;
+    }
     const qw_profile saved = ix->prof;
     QW_TRY(run_impl(ix, q_in.as<float>(), n, k, &p, o_ids.as<int64_t>(), o_dists.as<float>(),
                     o_stats.as<int64_t>(), o_cids.as<int64_t>(), o_ccol.as<int32_t>(),
                     QW_MEM_DEVICE, s));
+    const int64_t nested_fallbacks = ix->prof.bitmap_fallbacks - saved.bitmap_fallbacks;
     ix->prof = saved;
-    ix->prof.bitmap_fallbacks += n;
+    if (rerun) {
+        ix->prof.start_fallbacks += n;
+        ix->prof.bitmap_fallbacks += nested_fallbacks;
+    } else {
+        ix->prof.bitmap_fallbacks += n;
+    }
     QW_TRY(launch_scatter(list, 0, n, k, cap, o_ids.as<int64_t>(), o_dists.as<float>(),
                           o_stats.as<int64_t>(), o_cids.as<int64_t>(), o_ccol.as<int32_t>(), f_ids,
                           f_dists, f_stats, f_cids, f_ccol, s));
@@ -661,9 +682,9 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         B = ix->tuned_batch;
     if (B == 0) {
         // workspace of one batch: 2 GB of counters on the level path; the
-        // bitmap path (about 0.5 MB per query at 1M points) takes up to 8 GB,
-        // a small share of the 280 GB HBM, so most workloads run as one batch
-        const int64_t budget = use_bitmap ? (int64_t)8 << 30 : (int64_t)2 << 30;
+        // bitmap path (about 4.3 MB per query at 1M points) takes up to 48 GB,
+        // a sixth of the 280 GB HBM, so most workloads run as one batch
+        const int64_t budget = use_bitmap ? kBitmapBudget : (int64_t)2 << 30;
         B = use_cluster ? (int64_t)65535
                         : std::max<int64_t>(1, budget / (use_bitmap ? cb_bytes + cl_bytes
                                                                     : wpq_bytes));
@@ -685,7 +706,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         // two-pass level: one slot per (query, tile), one work entry per group
         const size_t items = (size_t)B * ix->nT;
         QW_TRY(ix->w_bmwork.ensure(bm_work_layout(B, ix->nT, m, nullptr)));
-        QW_TRY(ix->w_ovf.ensure(((size_t)nq + 1) * sizeof(int32_t)));
+        QW_TRY(ix->w_ovf.ensure(((size_t)nq + 1) * 2 * sizeof(int32_t)));
     }
     QW_TRY(ix->w_cand.ensure((size_t)B * cap * 2 * sizeof(int32_t)));
     const size_t plan_ints = (size_t)B * ix->nT * (kHistBins + 3) + (size_t)B * 2;
@@ -786,9 +807,11 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         st.bm_item_cap = (int32_t)std::min<int64_t>(items, (int64_t)1 << 23);
         st.bm_work_cap = (int32_t)std::min<int64_t>(items * kBmUint4, INT32_MAX);
     }
+    // two counters, then the two lists of queries to answer again
     int32_t *ovf_count = use_bitmap ? ix->w_ovf.as<int32_t>() : nullptr;
-    int32_t *ovf_list = use_bitmap ? ovf_count + 1 : nullptr;
-    if (use_bitmap) QW_CUDA_TRY(cudaMemsetAsync(ovf_count, 0, sizeof(int32_t), s));
+    int32_t *ovf_list = use_bitmap ? ovf_count + 2 : nullptr;
+    int32_t *late_list = use_bitmap ? ovf_list + nq : nullptr;
+    if (use_bitmap) QW_CUDA_TRY(cudaMemsetAsync(ovf_count, 0, 2 * sizeof(int32_t), s));
     st.cand = ix->w_cand.as<int32_t>();
     st.cand_col = st.cand + (size_t)B * cap;
     int *err = ix->w_err.as<int>();
@@ -956,7 +979,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             }));
             if (use_bitmap)
                 QW_TRY(launch_bm_overflow_list(st, nb, order ? perm : nullptr, b0, ovf_list,
-                                               ovf_count, s));
+                                               late_list, ovf_count, s));
         }
         if (want_cand)
             QW_TRY(tm.run(QW_K_SELECT, 1, [&] { return launch_candidates_out(st, nb, cap, cids_b, ccol_b, s); }));
@@ -1019,15 +1042,26 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     }
     if (use_bitmap) {
         // queries whose candidate lists overflowed the bitmap path's buffers:
-        // answered again by the level path (same results by construction);
-        // after every read of this call's flags and loop state, which the
-        // level path's call reuses
-        int32_t n_ovf = 0;
-        QW_CUDA_TRY(cudaMemcpyAsync(&n_ovf, ovf_count, sizeof(n_ovf), cudaMemcpyDeviceToHost, s));
+        // answered again by the level path; queries whose learned first level
+        // was too late: answered again by the bitmap path from level 0 (same
+        // results by construction either way); after every read of this
+        // call's flags and loop state, which the nested calls reuse
+        int32_t n_ovf[2] = {0, 0};
+        QW_CUDA_TRY(cudaMemcpyAsync(n_ovf, ovf_count, sizeof(n_ovf), cudaMemcpyDeviceToHost, s));
         QW_CUDA_TRY(cudaStreamSynchronize(s));
-        if (n_ovf > 0)
-            QW_TRY(level_path_rerun(ix, Qall, HQall, ovf_list, n_ovf, k, cap, f_ids, f_dists,
+        if (n_ovf[0] > 0)
+            QW_TRY(level_path_rerun(ix, Qall, HQall, ovf_list, n_ovf[0], k, cap, f_ids, f_dists,
                                     f_stats, f_cids, f_ccol, s));
+        if (n_ovf[1] > 0) {
+            qw_query_params p{};
+            p.path = QW_PATH_BITMAP;
+            p.order = QW_ORDER_GIVEN;
+            p.start = QW_START_PLAIN;
+            p.graph = graph ? 1 : 0;
+            p.bitmap_loads = tma_loads ? QW_LOADS_TMA : QW_LOADS_DIRECT;
+            QW_TRY(level_path_rerun(ix, Qall, HQall, late_list, n_ovf[1], k, cap, f_ids, f_dists,
+                                    f_stats, f_cids, f_ccol, s, &p));
+        }
     }
     if (host) {
         if (want_ids) {
@@ -1244,7 +1278,7 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
                                  (int64_t)ix->nT * (int64_t)sizeof(int32_t) * 2 +
                                  ((int64_t)kQCap * (int64_t)sizeof(uint64_t) + 4) * 2;
             const int64_t bdef = std::min<int64_t>(
-                std::min<int64_t>(std::max<int64_t>(1, ((int64_t)8 << 30) / cb_b), nq), 65535);
+                std::min<int64_t>(std::max<int64_t>(1, kBitmapBudget / cb_b), nq), 65535);
             const int64_t bc[2] = {bdef / 16, bdef / 4};
             const qw_query_params keepb = cur;
             for (int64_t bb : bc) {

@@ -940,7 +940,7 @@ __global__ void __launch_bounds__(SEL_THREADS) bm_select_kernel(IndexView ix, in
     }
     __syncthreads();
     const int nd = s_nd, ne = s_ne;
-    const bool ovf = ovf_list || ne > kEqCap || nd + take != keep || take > ne;
+    const bool ovf = ovf_list || nd + take != keep || take > ne;
     if (ovf) {
         if (threadIdx.x == 0) {
             atomicOr(st.bm_ovf + q, 1);
@@ -952,7 +952,33 @@ __global__ void __launch_bounds__(SEL_THREADS) bm_select_kernel(IndexView ix, in
         }
         return;
     }
-    if (take > 0) {
+    if (take > 0 && ne > kEqCap) {
+        // a tie class larger than its list: select from the candidate list
+        // itself (members: not of the previous level, count c*), keyed by
+        // original id
+        auto tie = [&](int j, uint32_t *u) {
+            const uint64_t e = E[j];
+            if (((e >> 8) & 1u) || (int)(e & 0xffu) != cstar) return false;
+            *u = (uint32_t)perm[e >> 32];
+            return true;
+        };
+        const uint32_t T =
+            take < ne ? block_kth_smallest_if<SEL_THREADS>(nl, take, tie, hist, bc) : 0xffffffffu;
+        for (int j0 = 0; j0 < nl; j0 += SEL_THREADS) {
+            const int j = j0 + threadIdx.x;
+            uint32_t id = 0u;
+            const bool in = j < nl && tie(j, &id) && id <= T;
+            const uint32_t b = __ballot_sync(0xffffffffu, in);
+            int base = 0;
+            if (lane == 0 && b) base = atomicAdd(&s_nt, __popc(b));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (in) {
+                cand[nd + base + __popc(b & below)] = (int32_t)id;
+                col[nd + base + __popc(b & below)] = cstar;
+            }
+        }
+        __syncthreads();
+    } else if (take > 0) {
         // the take smallest ids of the tie class: those <= its take-th smallest
         // (ids are distinct, so exactly take of them)
         const uint32_t T = take < ne ? block_kth_smallest<SEL_THREADS>(
@@ -1114,14 +1140,21 @@ __global__ void hloc_kernel(const int32_t *__restrict__ Ht, const int32_t *__res
     }
 }
 
-// Workload indices of the batch's queries marked for the level path.
+// Workload indices of the batch's queries to answer again: list[0] those whose
+// candidates overflowed the bitmap path's lists (flag 1: the level path), list
+// [1] those whose learned first level was too late (flag 2 alone: the bitmap
+// path from level 0); count[0], count[1] their numbers.
 __global__ void bm_overflow_list_kernel(const QueryState st, int nb, const int32_t *order_perm,
-                                        int64_t b0, int32_t *list, int32_t *count)
+                                        int64_t b0, int32_t *list0, int32_t *list1,
+                                        int32_t *count)
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nb || !st.bm_ovf[q]) return;
-    const int pos = atomicAdd(count, 1);
-    list[pos] = order_perm ? order_perm[b0 + q] : (int32_t)(b0 + q);
+    if (q >= nb) return;
+    const int f = st.bm_ovf[q];
+    if (!f) return;
+    const int which = (f & 1) ? 0 : 1;
+    const int pos = atomicAdd(count + which, 1);
+    (which == 0 ? list0 : list1)[pos] = order_perm ? order_perm[b0 + q] : (int32_t)(b0 + q);
 }
 
 // Data objects per bid of every projection, then the exclusive prefix over
@@ -1465,9 +1498,11 @@ qw_status launch_bm_collect(const IndexView &ix, int nb, int l, int cap, QuerySt
 }
 
 qw_status launch_bm_overflow_list(const QueryState &st, int nb, const int32_t *order_perm,
-                                  int64_t b0, int32_t *list, int32_t *count, cudaStream_t s)
+                                  int64_t b0, int32_t *list0, int32_t *list1, int32_t *count,
+                                  cudaStream_t s)
 {
-    bm_overflow_list_kernel<<<(nb + 255) / 256, 256, 0, s>>>(st, nb, order_perm, b0, list, count);
+    bm_overflow_list_kernel<<<(nb + 255) / 256, 256, 0, s>>>(st, nb, order_perm, b0, list0, list1,
+                                                             count);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }

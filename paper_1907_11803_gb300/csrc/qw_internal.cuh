@@ -200,11 +200,11 @@ struct QueryState {
 };
 
 // Candidates per query and level the bitmap path holds (more: the query is
-// answered by the level path).
-constexpr int kQCap = 16384;
+// answered by the level path).  4 MiB of lists per query (two levels).
+constexpr int kQCap = 262144;
 // Tie-list capacity per query on the bitmap path (larger tie classes are
 // answered by the level path).
-constexpr int kEqCap = 4096;
+constexpr int kEqCap = 16384;
 
 
 // Level of a loop that runs on the device (graph mode): the level kernels
@@ -257,8 +257,12 @@ qw_status launch_bm_collect(const IndexView &ix, int nb, int l, int cap, QuerySt
                             int64_t *stats_out, bool sorted, cudaStream_t s);
 qw_status launch_select_plan(const IndexView &ix, int nb, int l, int cap, QueryState &st,
                              int64_t *stats_out, cudaStream_t s);
+// Queries of the batch to answer again (workload indices): list0 / count[0]
+// those whose candidates overflowed the bitmap path's lists, list1 / count[1]
+// those whose learned first level was too late.
 qw_status launch_bm_overflow_list(const QueryState &st, int nb, const int32_t *order_perm,
-                                  int64_t b0, int32_t *list, int32_t *count, cudaStream_t s);
+                                  int64_t b0, int32_t *list0, int32_t *list1, int32_t *count,
+                                  cudaStream_t s);
 
 // Device-driven loop control (qw_graph.cu builds the graphs that use them).
 qw_status launch_loop_init(LoopCtl *ctl, const QueryState &st, int nb, int cgrow, cudaStream_t s);

@@ -58,8 +58,11 @@ __device__ __forceinline__ int block_exclusive_max(int v, int lowest, int *tmp)
 // warp adds one count per distinct bin).  Block-wide over NT threads; v may be
 // shared or global memory written before the call's first barrier.  hist: 256
 // ints and bc: 2 ints of shared memory.  Returns the key in every thread.
-template <int NT>
-__device__ uint32_t block_kth_smallest(const uint32_t *v, int n, int kk, int *hist, int *bc)
+// block_kth_smallest_if: the same over the keys of the members of a set
+// given by `get(j, &key)` (true: element j < n is a member, with that key);
+// kk counts members only.
+template <int NT, class Get>
+__device__ uint32_t block_kth_smallest_if(int n, int kk, Get get, int *hist, int *bc)
 {
     const int lane = threadIdx.x & 31;
     uint32_t prefix = 0, mask = 0;
@@ -68,8 +71,9 @@ __device__ uint32_t block_kth_smallest(const uint32_t *v, int n, int kk, int *hi
         __syncthreads();
         for (int j0 = 0; j0 < n; j0 += NT) {
             const int j = j0 + threadIdx.x;
-            const uint32_t u = j < n ? v[j] : 0u;
-            const bool in = j < n && (u & mask) == prefix;
+            uint32_t u = 0u;
+            const bool member = j < n && get(j, &u);
+            const bool in = member && (u & mask) == prefix;
             const uint32_t bin = in ? (u >> shift) & 255u : 256u + lane;
             const uint32_t peers = __match_any_sync(0xffffffffu, bin);
             if (in && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
@@ -110,6 +114,18 @@ __device__ uint32_t block_kth_smallest(const uint32_t *v, int n, int kk, int *hi
         __syncthreads();
     }
     return prefix;
+}
+
+template <int NT>
+__device__ uint32_t block_kth_smallest(const uint32_t *v, int n, int kk, int *hist, int *bc)
+{
+    return block_kth_smallest_if<NT>(
+        n, kk,
+        [v](int j, uint32_t *u) {
+            *u = v[j];
+            return true;
+        },
+        hist, bc);
 }
 
 }  // namespace qw

@@ -105,12 +105,14 @@ def test_learned_start_same_results_fewer_levels(qwlib, cuda, w):
     assert torch.equal(ids0, ids4) and torch.equal(st0, st4)
     assert prof4["start_fallbacks"] == prof2["start_fallbacks"]
     # on the bitmap path an over-eager start leaves some queries whose
-    # previous level already met the stop rule: they go to the level path
-    for graph in (False, True):
+    # previous level already met the stop rule: they are answered again by the
+    # bitmap path from level 0 (none of them needs the level path)
+    for graph, loads in ((False, "direct"), (True, "direct"), (True, "tma")):
         ids6, d6, st6 = index.query(Q, 20, stats=True, start="learned", path="bitmap",
-                                    graph=graph, loads="direct")
+                                    graph=graph, loads=loads)
         prof6 = index.profile(reset=True)
         assert torch.equal(ids0, ids6) and torch.equal(d0, d6) and torch.equal(st0, st6)
-        assert prof6["bitmap_fallbacks"] > 0
+        assert prof6["start_fallbacks"] > 0
+        assert prof6["bitmap_fallbacks"] == 0
     index.free()
     mlp.free()

@@ -417,19 +417,42 @@ def test_full_size_sampled(orc, qwlib, cuda):
 
 
 @pytest.mark.parametrize("graph", [False, True])
-def test_bitmap_path_overflow_answered_by_level_path(orc, qwlib, cuda, graph):
-    """Ten distinct points, 7,000 copies each: whole tiles of candidates and
-    tie classes of thousands of ids with the same count.  The bitmap path's
-    fixed lists overflow; those queries are answered by the level path and
-    every output still equals the oracle's."""
-    import torch
+def test_bitmap_path_large_tie_classes(orc, qwlib, cuda, graph):
+    """Ten distinct points, 20,000 copies each: whole tiles of candidates and
+    tie classes of 20,000 ids with the same count, more than the bitmap path's
+    tie list holds.  The selection then picks the smallest ids of the tie
+    class from the candidate list itself; every output equals the oracle's
+    and no query needs the level path."""
     rng = np.random.default_rng(31)
     base = rng.uniform(-10, 10, size=(10, 16)).astype(np.float32)
-    X = np.repeat(base, 7_000, axis=0)
+    X = np.repeat(base, 20_000, axis=0)
     Q = (base[[0, 3, 7, 9]] + rng.normal(0, 0.05, size=(4, 16))).astype(np.float32)
     wl = workloads.make_workload("mix10k_d32", seed=3, n=1000, nq=1, d=16, m=16)
+    for loads in ("tma", "direct"):
+        _full_parity(orc, qwlib, cuda, X, Q, wl.A, wl.b, w=4.0, k=10, v=90, l=12,
+                     path=("bitmap_graph" if graph else "bitmap") if loads == "tma" else
+                     ("bitmap_direct_graph" if graph else "bitmap_direct"))
+    index = qwlib.Index(_t(X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=4.0, v=90, l=12,
+                        bitmaps=True)
+    index.profile(reset=True)
+    index.query(_t(Q, cuda), 10, path="bitmap", graph=graph, loads="direct")
+    assert index.profile()["bitmap_fallbacks"] == 0
+    index.free()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_bitmap_path_overflow_answered_by_level_path(orc, qwlib, cuda, graph):
+    """270,000 copies of one point (plus a few others): the query's first
+    level holds 270,000 candidates, more than the bitmap path's per-query list
+    (262,144).  That query is answered by the level path and every output
+    still equals the oracle's."""
+    rng = np.random.default_rng(37)
+    base = rng.uniform(-10, 10, size=(4, 16)).astype(np.float32)
+    X = np.concatenate([np.repeat(base[:1], 270_000, axis=0), np.repeat(base[1:], 300, axis=0)])
+    Q = (base[[0, 1, 2]] + rng.normal(0, 0.05, size=(3, 16))).astype(np.float32)
+    wl = workloads.make_workload("mix10k_d32", seed=3, n=1000, nq=1, d=16, m=16)
     _full_parity(orc, qwlib, cuda, X, Q, wl.A, wl.b, w=4.0, k=10, v=90, l=12,
-                 path="bitmap_graph" if graph else "bitmap")
+                 path="bitmap_direct_graph" if graph else "bitmap_direct")
     index = qwlib.Index(_t(X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=4.0, v=90, l=12,
                         bitmaps=True)
     index.profile(reset=True)
