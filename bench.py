@@ -86,6 +86,9 @@ def parse_args(argv=None):
                         "the autotuner")
     p.add_argument("--no-bitmaps", action="store_true",
                    help="build the index without the level bitmaps of the bitmap path")
+    p.add_argument("--host-bitmaps", action="store_true",
+                   help="keep the level bitmaps in pinned host memory, read over NVLink-C2C "
+                        "(an index larger than the GPU's memory)")
     p.add_argument("--loads", choices=["tma", "direct"], default="direct",
                    help="with --no-tune and --path bitmap: how the bitmap kernel reads bitmaps")
     p.add_argument("--graph", action="store_true",
@@ -377,7 +380,8 @@ def run_ours(args):
     Q = torch.from_numpy(wl.Q).to(dev)
     v_used, l_arg = operating_point(args, s)
     index = qw.Index(X, A, b, w=s.w, c=s.c, v=v_used, l=l_arg,
-                     shadow_bf16=args.rerank == "bf16", bitmaps=not args.no_bitmaps)
+                     shadow_bf16=args.rerank == "bf16", bitmaps=not args.no_bitmaps,
+                     host_bitmaps=args.host_bitmaps)
     ids = torch.empty((s.nq, s.k), dtype=torch.int64, device=dev)
     dists = torch.empty((s.nq, s.k), dtype=torch.float32, device=dev)
     # the library's calls run on a created stream (persisting-L2 windows are

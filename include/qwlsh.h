@@ -91,6 +91,12 @@ typedef struct {
                              projection i, id tile and level L, one bitmap of the tile's ids
                              per level-L bucket; about m * n_tiles * (c/(c-1)) * (span_i + 1)
                              * 4 KiB (qw_index_info.bitmap_bytes) */
+    int32_t host_bitmaps; /* non-zero (with bitmaps): keep the level bitmaps in pinned host
+                             memory that the kernels read directly (on GB300 the Grace
+                             memory, over NVLink-C2C) -- an index larger than the GPU's
+                             memory, the paper's external-storage setting.  The bitmap path
+                             then reads them with plain loads (QW_LOADS_TMA acts as
+                             QW_LOADS_DIRECT).  Same results */
 } qw_index_params;
 
 /* Per-workload options.  Zero-initialise; unknown non-zero fields are rejected. */
@@ -238,7 +244,9 @@ typedef struct {
     int32_t span_max;      /* largest anchored bucket id over all projections */
     int64_t n_fixups;      /* data projections recomputed in FP64 at build time */
     int64_t device_bytes;  /* device memory held by the index (excluding workspace) */
-    int64_t bitmap_bytes;  /* of which the level bitmaps (0 without them) */
+    int64_t bitmap_bytes;  /* the level bitmaps (0 without them), in device memory unless
+                              host_bitmaps */
+    int64_t host_bytes;    /* pinned host memory held by the index (host_bitmaps) */
 } qw_index_info;
 
 /* Library version string. */

@@ -42,7 +42,7 @@ EXPORTED = ("qw_version", "qw_last_error", "qw_collision_probability",
 class qw_index_params(C.Structure):
     _fields_ = [("m", C.c_int32), ("w", C.c_float), ("c", C.c_int32), ("v", C.c_int32),
                 ("l", C.c_int32), ("delta", C.c_float), ("shadow_bf16", C.c_int32),
-                ("bitmaps", C.c_int32)]
+                ("bitmaps", C.c_int32), ("host_bitmaps", C.c_int32)]
 
 
 class qw_query_params(C.Structure):
@@ -95,7 +95,8 @@ class qw_index_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("m", C.c_int32), ("w", C.c_float),
                 ("c", C.c_int32), ("v", C.c_int32), ("l", C.c_int32), ("tile", C.c_int32),
                 ("n_tiles", C.c_int32), ("span_max", C.c_int32), ("n_fixups", C.c_int64),
-                ("device_bytes", C.c_int64), ("bitmap_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("bitmap_bytes", C.c_int64),
+                ("host_bytes", C.c_int64)]
 
 
 class QwError(RuntimeError):
@@ -338,7 +339,8 @@ class Index:
     threshold from Eq. 1 (see ``qw_collision_threshold``)."""
 
     def __init__(self, data, A, b, *, w: float, c: int = 2, v: int = 100, l: int = 0,
-                 delta: float = 0.0, shadow_bf16: bool = False, bitmaps: bool = False):
+                 delta: float = 0.0, shadow_bf16: bool = False, bitmaps: bool = False,
+                 host_bitmaps: bool = False):
         _f32(data, "data"), _f32(A, "A"), _f32(b, "b")
         mem = _mem_of(data, A, b)
         n, d = data.shape
@@ -346,7 +348,8 @@ class Index:
         if d2 != d or b.shape != (m,):
             raise ValueError("shape mismatch between data, A and b")
         p = qw_index_params(m=m, w=float(w), c=int(c), v=int(v), l=int(l), delta=float(delta),
-                            shadow_bf16=1 if shadow_bf16 else 0, bitmaps=1 if bitmaps else 0)
+                            shadow_bf16=1 if shadow_bf16 else 0, bitmaps=1 if bitmaps else 0,
+                            host_bitmaps=1 if host_bitmaps else 0)
         self._h = 0
         self._h = qw_build_index(data.data_ptr(), n, d, A.data_ptr(), b.data_ptr(), p, mem,
                                  _stream_of(data))

@@ -51,6 +51,47 @@ void DevBuf::release()
     bytes = 0;
 }
 
+// Pinned host memory the GPU reads directly (on GB300: Grace memory over
+// NVLink-C2C).  The pointer is valid on host and device (unified addressing).
+struct HostBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    HostBuf() = default;
+    HostBuf(const HostBuf &) = delete;
+    HostBuf &operator=(const HostBuf &) = delete;
+    ~HostBuf() { release(); }
+    qw_status ensure(size_t want)
+    {
+        if (want <= bytes) return QW_OK;
+        release();
+        void *h = nullptr;
+        cudaError_t e = cudaHostAlloc(&h, want, cudaHostAllocMapped | cudaHostAllocPortable);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            set_error("pinned host allocation of " + std::to_string(want) + " bytes failed");
+            return QW_ERR_OOM;
+        }
+        void *dp = nullptr;
+        e = cudaHostGetDevicePointer(&dp, h, 0);
+        if (e != cudaSuccess || dp != h) {
+            (void)cudaGetLastError();
+            cudaFreeHost(h);
+            set_error("pinned host memory is not addressable at the same address on the device");
+            return QW_ERR_CUDA;
+        }
+        p = h;
+        bytes = want;
+        return QW_OK;
+    }
+    void release()
+    {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
 static qw_status arg_error(const std::string &msg)
 {
     set_error(msg);
@@ -71,6 +112,8 @@ struct qw_index {
     DevBuf X, A, b, o, span, lid, dir_bid, dir_off, dir_start, dir_cnt, Xb, xnorm, Cg;
     bool shadow = false;
     bool bitmaps = false;               // level bitmaps for QW_PATH_BITMAP
+    bool host_bitmaps = false;          // ... kept in pinned host memory (bm_host)
+    HostBuf bm_host;
     DevBuf bm, bm_base, bm_nb, bm_lvl, bm_J, bid_prefix, prefix_off, perm, bm_sum, Xloc, inv, hloc;
     int hloc_bytes = 0, hloc_stride = 0;
     int bm_maxJ = 0;
@@ -105,7 +148,7 @@ struct qw_index {
         v.dir_off = dir_off.as<int32_t>();
         v.dir_start = dir_start.as<int64_t>();
         v.dir_cnt = dir_cnt.as<int32_t>();
-        v.bm = bm.as<uint4>();
+        v.bm = host_bitmaps ? bm_host.as<uint4>() : bm.as<uint4>();
         v.bm_base = bm_base.as<int64_t>();
         v.bm_nb = bm_nb.as<int32_t>();
         v.bm_lvl = bm_lvl.as<int32_t>();
@@ -353,12 +396,19 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
             set_error("qw_build_index: bitmap table too large");
             return QW_ERR_RANGE;
         }
-        QW_TRY(ix->bm.ensure((size_t)lay.total * kBmUint4 * sizeof(uint4)));
+        const size_t bm_bytes = (size_t)lay.total * kBmUint4 * sizeof(uint4);
+        if (ix->host_bitmaps)
+            QW_TRY(ix->bm_host.ensure(bm_bytes));
+        else
+            QW_TRY(ix->bm.ensure(bm_bytes));
         QW_TRY(ix->bm_base.ensure((size_t)m * sizeof(int64_t)));
         QW_TRY(ix->bm_nb.ensure((size_t)m * sizeof(int32_t)));
         QW_TRY(ix->bm_lvl.ensure((size_t)m * kBmLevels * sizeof(int32_t)));
         QW_TRY(ix->bm_J.ensure((size_t)m * sizeof(int32_t)));
-        QW_CUDA_TRY(cudaMemsetAsync(ix->bm.p, 0, ix->bm.bytes, s));
+        if (ix->host_bitmaps)
+            memset(ix->bm_host.p, 0, ix->bm_host.bytes);
+        else
+            QW_CUDA_TRY(cudaMemsetAsync(ix->bm.p, 0, ix->bm.bytes, s));
         QW_CUDA_TRY(cudaMemcpyAsync(ix->bm_base.p, lay.base.data(), m * sizeof(int64_t),
                                     cudaMemcpyHostToDevice, s));
         QW_CUDA_TRY(cudaMemcpyAsync(ix->bm_nb.p, lay.nb.data(), m * sizeof(int32_t),
@@ -403,7 +453,8 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
                                     cudaMemcpyHostToDevice, s));
         QW_TRY(ix->bm_sum.ensure((size_t)lay.total * (kBmUint4 / 32) * sizeof(uint32_t)));
         QW_TRY(launch_bitmap_build(ix->view(), ix->c, ix->bm_maxJ, Ht.as<int32_t>(),
-                                   ix->bm.as<uint4>(), ix->bm_sum.as<uint32_t>(), lay.total, s));
+                                   ix->host_bitmaps ? ix->bm_host.as<uint4>() : ix->bm.as<uint4>(),
+                                   ix->bm_sum.as<uint32_t>(), lay.total, s));
         QW_TRY(ix->Xloc.ensure((size_t)n * d * sizeof(float)));
         QW_TRY(ix->inv.ensure((size_t)n * sizeof(int32_t)));
         QW_TRY(launch_locality_copy(ix->X.as<float>(), ix->perm.as<int32_t>(), n, d,
@@ -454,6 +505,8 @@ qw_status qw_build_index(const float *data, int64_t n, int32_t d, const float *A
     if (p->c < 2) return arg_error("qw_build_index: c must be an integer >= 2");
     if (p->v < 0) return arg_error("qw_build_index: v must be >= 0");
     if (p->l < 0 || p->l > p->m) return arg_error("qw_build_index: l must be in [0, m]");
+    if (p->host_bitmaps && !p->bitmaps)
+        return arg_error("qw_build_index: host_bitmaps needs bitmaps");
     qw_index *ix = new (std::nothrow) qw_index();
     if (!ix) {
         set_error("qw_build_index: host allocation failed");
@@ -473,6 +526,7 @@ qw_status qw_build_index(const float *data, int64_t n, int32_t d, const float *A
     ix->nT = (int)((n + kTile - 1) / kTile);
     ix->shadow = p->shadow_bf16 != 0;
     ix->bitmaps = p->bitmaps != 0;
+    ix->host_bitmaps = ix->bitmaps && p->host_bitmaps != 0;
     qw_status st = build_impl(ix, data, A, b, mem, (cudaStream_t)stream);
     if (st != QW_OK) {
         qw_index_free(ix);
@@ -670,7 +724,9 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     if (eff_path == QW_PATH_BITMAP && !ix->bitmaps) eff_path = QW_PATH_LEVELS;
     const bool use_cluster = eff_path == QW_PATH_CLUSTER && fits;
     const bool use_bitmap = eff_path == QW_PATH_BITMAP;
-    const bool tma_loads = !qp || qp->bitmap_loads == QW_LOADS_TMA;
+    // bitmaps in host memory are read with plain loads (the TMA variant stages
+    // device memory only)
+    const bool tma_loads = (!qp || qp->bitmap_loads == QW_LOADS_TMA) && !ix->host_bitmaps;
     // bitmap path, per query: two levels of (tile) candidate bitmaps and lists
     const int64_t cb_bytes = (int64_t)ix->nT * kBmUint4 * (int64_t)sizeof(uint4) * 2;
     // (per query: two levels of tile candidate counts and candidate lists)
@@ -1420,7 +1476,8 @@ qw_status qw_index_get_info(const qw_index *ix, qw_index_info *info)
     info->span_max = ix->span_max;
     info->n_fixups = ix->n_fixups;
     info->device_bytes = ix->device_bytes;
-    info->bitmap_bytes = (int64_t)ix->bm.bytes;
+    info->bitmap_bytes = (int64_t)(ix->host_bitmaps ? ix->bm_host.bytes : ix->bm.bytes);
+    info->host_bytes = (int64_t)ix->bm_host.bytes;
     return QW_OK;
 }
 
@@ -1462,6 +1519,7 @@ void qw_index_free(qw_index *ix)
     if (!ix) return;
     cudaDeviceSynchronize();
     l2_release(&ix->l2_owner);
+    ix->bm_host.release();
     DevBuf *bufs[] = {&ix->X, &ix->Xb, &ix->xnorm, &ix->Cg, &ix->A, &ix->b, &ix->o, &ix->span, &ix->lid,
                       &ix->dir_bid,
                       &ix->dir_off, &ix->dir_start, &ix->dir_cnt, &ix->w_q, &ix->w_hq,
