@@ -438,6 +438,14 @@ qw_status qw_mlp_train(qw_mlp *mlp, const float *X, const int32_t *y, int64_t n,
                        int32_t batch, float lr, float *final_loss, void *stream);
 /* Class probabilities (DEVICE n x classes) of DEVICE rows X. */
 qw_status qw_mlp_predict(qw_mlp *mlp, const float *X, int64_t n, float *prob, void *stream);
+/* The same forward pass on the tensor cores (tcgen05.mma, FP16 activations
+ * and weights, FP32 accumulators in tensor memory), 128 rows per CTA: the form
+ * qw_run_workload uses for learned starts whenever the network has this shape
+ * -- hidden = 256, classes a multiple of 16 up to 32, n_in a multiple of 64 up
+ * to 576 -- and QW_ERR_ARG for any other shape.  Probabilities differ from
+ * qw_mlp_predict by the FP16 rounding of the activations (about 1e-3).  Waits
+ * for the stream; QW_ERR_TIMEOUT if a tensor-core wait gave up. */
+qw_status qw_mlp_predict_tc(qw_mlp *mlp, const float *X, int64_t n, float *prob, void *stream);
 void qw_mlp_free(qw_mlp *mlp);
 
 /* Features of queries for the start model (DEVICE pointers): per query its

@@ -36,7 +36,7 @@ EXPORTED = ("qw_version", "qw_last_error", "qw_collision_probability",
             "qw_index_get_info", "qw_mlp_create", "qw_mlp_param_count", "qw_mlp_set_params",
             "qw_mlp_get_params", "qw_mlp_loss_grad", "qw_mlp_train", "qw_mlp_predict",
             "qw_mlp_free", "qw_query_features", "qw_index_set_start_model", "qw_autotune",
-            "qw_index_export", "qw_index_free", "qw_l2_split_model")
+            "qw_index_export", "qw_index_free", "qw_l2_split_model", "qw_mlp_predict_tc")
 
 
 class qw_index_params(C.Structure):
@@ -157,6 +157,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
                                C.POINTER(C.c_float), vp]
     L.qw_mlp_predict.restype = C.c_int32
     L.qw_mlp_predict.argtypes = [vp, vp, C.c_int64, vp, vp]
+    L.qw_mlp_predict_tc.restype = C.c_int32
+    L.qw_mlp_predict_tc.argtypes = [vp, vp, C.c_int64, vp, vp]
     L.qw_mlp_free.restype = None
     L.qw_mlp_free.argtypes = [vp]
     L.qw_autotune.restype = C.c_int32
@@ -531,11 +533,14 @@ class Mlp:
                                    lr, C.byref(loss), _stream_of(X) or None))
         return float(loss.value)
 
-    def predict(self, X):
+    def predict(self, X, tensor_cores: bool = False):
+        """Class probabilities of CUDA float32 rows X; tensor_cores: the
+        tcgen05 forward pass (qw_mlp_predict_tc), else the SIMT one."""
         torch = _torch()
+        _f32(X, "X")
         P = torch.empty((X.shape[0], self.classes), dtype=torch.float32, device=X.device)
-        _check(load().qw_mlp_predict(self._h, X.data_ptr(), X.shape[0], P.data_ptr(),
-                                     _stream_of(X) or None))
+        fn = load().qw_mlp_predict_tc if tensor_cores else load().qw_mlp_predict
+        _check(fn(self._h, X.data_ptr(), X.shape[0], P.data_ptr(), _stream_of(X) or None))
         return P
 
     def free(self):

@@ -239,6 +239,7 @@ struct qw_mlp {
     int64_t oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0;
     DevBuf p32, p16, grad, m1, m2, work, scalar;
     DevBuf p16t;  // k-major FP16 copies of W1, W2, W3 for the fused inference kernel
+    DevBuf tc_err;  // error word of the tensor-core forward pass
     int cap = 0;  // rows the work buffers hold
     int64_t step = 0;
     int64_t version = 0, t_version = -1;  // weights changed / k-major copies made at
@@ -624,13 +625,319 @@ __global__ void __launch_bounds__(SM_THREADS) start_model_kernel(
     }
 }
 
+// ---- the same forward pass on the fifth-generation tensor cores (tcgen05)
+//
+// One CTA of 128 threads answers 128 rows.  The layers are chained GEMMs
+// [128 x K] x [K x N]: the activations (FP16) are the A operand in shared
+// memory, the FP16 weight copies (row-major N x K, i.e. K-major) are the B
+// operand, streamed through shared memory 64 k at a time, and the FP32
+// accumulators live in tensor memory (TMEM): layer 1 in columns [0, 256),
+// layer 2 in [256, 512), layer 3 again from column 0.  One thread issues the
+// tcgen05.mma instructions (M = 128, N = the layer's width, K = 16 each) and
+// commits them to an mbarrier; after the (bounded) wait, warp w reads TMEM
+// lanes 32w .. 32w + 31, i.e. row = thread, adds the bias, applies ReLU and
+// writes the next layer's A operand.  Operands use the no-swizzle K-major
+// layout of 8-row x 16-byte core matrices: core matrix (i, j) (rows 8i..8i+7,
+// k 8j..8j+7) at byte (i * K / 8 + j) * 128 of the tile, so core matrices
+// adjacent in k are 128 bytes apart (the descriptor's leading-dimension
+// offset) and adjacent in rows K * 16 bytes apart (its stride offset).
+constexpr int TC_ROWS = 128;
+constexpr int TC_KC = 64;          // k per weight chunk
+constexpr int TC_MAXN = 256;       // widest layer
+constexpr int TC_MAXK = 576;       // widest input (d + m)
+constexpr int TC_MAXC = 32;        // classes
+
+__device__ __forceinline__ uint32_t tc_smem(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: no swizzle, K-major; start, leading
+// (k-direction) and stride (row-direction) byte offsets in 16-byte units;
+// bits 46-47 hold the descriptor version of this architecture (1).
+__device__ __forceinline__ uint64_t tc_desc(const void *start, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = (uint64_t)((tc_smem(start) >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP16 A and B (K-major), FP32 D, M x N.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t dcol, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     tc_smem(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Bounded wait on an mbarrier phase (about 2 s); false when it gave up.
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(tc_smem(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > 4000000000LL) return false;
+    }
+}
+
+// Byte offset of element (r, k) in a no-swizzle K-major tile with K columns.
+__device__ __forceinline__ uint32_t tc_off(int r, int k, int K)
+{
+    return (uint32_t)(((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Rows' inputs: X (n x K0 FP32, the features) when X is given, else the
+// features of queries Q / HQ as start_model_kernel forms them.  Output: the
+// class probabilities (prob, n x C) when prob is given, else each row's first
+// level (start_model_kernel's rule).  W1, W2, W3: FP16, row-major (N x K).
+// err (optional): bit 16 set when a wait gave up (rows then get level 0 or NaN).
+__global__ void __launch_bounds__(TC_ROWS, 1) mlp_forward_tc_kernel(
+    const float *__restrict__ X, const float *__restrict__ Q, const int32_t *__restrict__ HQ,
+    int n, int d, int m, const int32_t *__restrict__ o, const int32_t *__restrict__ span, float xs,
+    int K0, const __half *__restrict__ W1, const float *__restrict__ b1,
+    const __half *__restrict__ W2, const float *__restrict__ b2, const __half *__restrict__ W3,
+    const float *__restrict__ b3, int H, int C, float *__restrict__ prob, float eps, int shift,
+    int32_t *__restrict__ start, int *__restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tbase_s;
+    __shared__ int s_stuck;
+    const int Ka = K0 > H ? K0 : H;
+    unsigned char *act = tsm;                                  // 128 x Ka FP16
+    unsigned char *wb = tsm + (size_t)TC_ROWS * Ka * 2;       // 256 x 64 FP16
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * TC_ROWS;
+    if (tid == 0) {
+        s_stuck = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                         tc_smem(&tbase_s))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // the first layer's input in FP16
+    for (int e = tid; e < TC_ROWS * K0; e += TC_ROWS) {
+        const int r = e / K0, j = e - r * K0;
+        const int64_t q = r0 + r;
+        float v = 0.0f;
+        if (q < n) {
+            if (X) {
+                v = X[q * K0 + j];
+            } else if (j < d) {
+                v = Q[q * d + j] * xs;
+            } else {
+                const int i = j - d;
+                const double g = (double)HQ[q * m + i] - (double)o[i];
+                double pos = (g + 0.5) / ((double)span[i] + 1.0);
+                pos = pos < -1.0 ? -1.0 : (pos > 2.0 ? 2.0 : pos);
+                v = (float)(pos - 0.5);
+            }
+        }
+        *reinterpret_cast<__half *>(act + tc_off(r, j, K0)) = __float2half_rn(v);
+    }
+    tc_fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tbase_s;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;  // this warp's TMEM lanes
+    uint32_t phase = 0;
+
+    // D[:, dcol .. dcol + N) = act[128 x K] x W^T
+    auto layer = [&](int K, const __half *__restrict__ W, int N, uint32_t dcol) {
+        for (int kc = 0; kc < K; kc += TC_KC) {
+            for (int p = tid; p < N * (TC_KC / 8); p += TC_ROWS) {
+                const int nr = p >> 3, j = p & 7;
+                const uint4 v = *reinterpret_cast<const uint4 *>(W + (int64_t)nr * K + kc + 8 * j);
+                *reinterpret_cast<uint4 *>(wb + ((nr >> 3) * (TC_KC / 8) + j) * 128 + (nr & 7) * 16) = v;
+            }
+            tc_fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            const bool go = s_stuck == 0;
+            if (tid == 0 && go) {
+                tc_fence_after();
+                const uint32_t idesc = tc_idesc(TC_ROWS, N);
+#pragma unroll
+                for (int s2 = 0; s2 < TC_KC / 16; ++s2) {
+                    const int kg = kc + 16 * s2;
+                    const uint64_t a = tc_desc(act + (kg >> 3) * 128, 128, (uint32_t)K * 16);
+                    const uint64_t b = tc_desc(wb + (2 * s2) * 128, 128, (TC_KC / 8) * 128);
+                    tc_mma(tbase + dcol, a, b, idesc, (kc | s2) != 0 ? 1u : 0u);
+                }
+                tc_commit(&bar);
+            }
+            if (go) {
+                if (!tc_wait(&bar, phase)) s_stuck = 1;
+                phase ^= 1;
+            }
+            tc_fence_after();
+        }
+    };
+    // bias, ReLU, FP16: the next layer's input (K = N columns)
+    auto relu_out = [&](uint32_t dcol, const float *__restrict__ bias, int N) {
+        for (int n0 = 0; n0 < N; n0 += 16) {
+            float v[16];
+            tc_ld16(tbase + lane_base + dcol + (uint32_t)n0, v);
+            __align__(16) __half hv[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) hv[i] = __float2half_rn(fmaxf(v[i] + __ldg(bias + n0 + i), 0.0f));
+            *reinterpret_cast<uint4 *>(act + tc_off(tid, n0, N)) = *reinterpret_cast<const uint4 *>(hv);
+            *reinterpret_cast<uint4 *>(act + tc_off(tid, n0 + 8, N)) =
+                *reinterpret_cast<const uint4 *>(hv + 8);
+        }
+        tc_fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    };
+    layer(K0, W1, H, 0);
+    relu_out(0, b1, H);
+    layer(H, W2, H, 256);
+    relu_out(256, b2, H);
+    layer(H, W3, C, 0);
+    // logits, softmax, and the row's output
+    float z[TC_MAXC];
+#pragma unroll
+    for (int h2 = 0; h2 < TC_MAXC / 16; ++h2) {
+        if (h2 * 16 < C) {
+            float v[16];
+            tc_ld16(tbase + lane_base + (uint32_t)(h2 * 16), v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) z[h2 * 16 + i] = h2 * 16 + i < C ? v[i] + __ldg(b3 + h2 * 16 + i) : -INFINITY;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) z[h2 * 16 + i] = -INFINITY;
+        }
+    }
+    const int64_t q = r0 + tid;
+    const bool stuck = s_stuck != 0;
+    if (q < n) {
+        float mx = -INFINITY;
+#pragma unroll
+        for (int c = 0; c < TC_MAXC; ++c) mx = fmaxf(mx, z[c]);
+        float sum = 0.0f;
+#pragma unroll
+        for (int c = 0; c < TC_MAXC; ++c) sum += c < C ? __expf(z[c] - mx) : 0.0f;
+        const float inv = 1.0f / sum;
+        if (prob) {
+#pragma unroll
+            for (int c = 0; c < TC_MAXC; ++c)
+                if (c < C) prob[q * C + c] = stuck ? NAN : __expf(z[c] - mx) * inv;
+        } else {
+            float cdf = 0.0f;
+            int sl = 0;
+            for (int c = 0; c < C - 1; ++c) {
+                cdf += __expf(z[c] - mx) * inv;
+                if (cdf <= eps) sl = c + 1; else break;
+            }
+            start[q] = (stuck || sl <= shift) ? 0 : sl - shift;
+        }
+    }
+    if (tid == 0 && stuck && err) atomicOr(err, 16);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
+    }
+}
+
 }  // namespace
+
+// The tensor-core forward pass takes networks with hidden = 256, classes a
+// multiple of 16 up to 32, and n_in a multiple of 64 up to 576 (weights
+// 16-byte aligned in the FP16 copy).
+static bool tc_eligible(const qw_mlp *mp)
+{
+    if (mp->H != TC_MAXN || mp->C % 16 != 0 || mp->C > TC_MAXC || mp->n_in % TC_KC != 0 ||
+        mp->n_in > TC_MAXK)
+        return false;
+    const __half *h = mp->p16.as<__half>();
+    for (int64_t off : {mp->oW1, mp->oW2, mp->oW3})
+        if (reinterpret_cast<uintptr_t>(h + off) % 16 != 0) return false;
+    return true;
+}
+
+static qw_status launch_mlp_tc(qw_mlp *mp, const float *X, const float *Q, const int32_t *HQ,
+                               int64_t n, const IndexView *ix, float xs, float *prob, float eps,
+                               int shift, int32_t *start, int *err, cudaStream_t s)
+{
+    if (n == 0) return QW_OK;
+    const int K0 = mp->n_in, Ka = std::max(K0, mp->H);
+    // at least 120 KiB, so one CTA per SM: each holds all 512 TMEM columns
+    const size_t smem = std::max<size_t>((size_t)TC_ROWS * Ka * 2 + (size_t)TC_MAXN * TC_KC * 2,
+                                         (size_t)120 << 10);
+    QW_CUDA_TRY(cudaFuncSetAttribute(mlp_forward_tc_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const __half *h = mp->p16.as<__half>();
+    const float *p = mp->p32.as<float>();
+    mlp_forward_tc_kernel<<<(unsigned)((n + TC_ROWS - 1) / TC_ROWS), TC_ROWS, smem, s>>>(
+        X, Q, HQ, (int)n, ix ? ix->d : 0, ix ? ix->m : 0, ix ? ix->o : nullptr,
+        ix ? ix->span : nullptr, xs, K0, h + mp->oW1, p + mp->ob1, h + mp->oW2, p + mp->ob2,
+        h + mp->oW3, p + mp->ob3, mp->H, mp->C, prob, eps, shift, start, err);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
 
 qw_status launch_start_model(qw_mlp *mp, const float *Q, const int32_t *HQ, int nq,
                              const IndexView &ix, float xs, float eps, int shift, int32_t *start,
                              cudaStream_t s)
 {
     if (nq == 0) return QW_OK;
+    if (tc_eligible(mp))
+        return launch_mlp_tc(mp, nullptr, Q, HQ, nq, &ix, xs, nullptr, eps, shift, start, nullptr,
+                             s);
     const int H = mp->H, C = mp->C, nin = mp->n_in;
     if (mp->t_version != mp->version) {
         QW_TRY(mp->p16t.ensure((size_t)(mp->oW3 + (int64_t)C * H) * sizeof(__half)));
@@ -690,3 +997,26 @@ qw_status data_rms(const float *X, int64_t count, double *dev_acc, double *out, 
 }
 
 }  // namespace qw
+
+extern "C" qw_status qw_mlp_predict_tc(qw_mlp *mp, const float *X, int64_t n, float *prob, void *stream)
+{
+    clear_error();
+    if (!mp || !X || !prob) return mlp_error("null pointer");
+    if (n < 0 || n > INT32_MAX) return mlp_error("n out of range");
+    if (!tc_eligible(mp))
+        return mlp_error("qw_mlp_predict_tc: needs hidden = 256, classes a multiple of 16 up to "
+                         "32 and n_in a multiple of 64 up to 576");
+    cudaStream_t s = (cudaStream_t)stream;
+    QW_TRY(mp->tc_err.ensure(sizeof(int)));
+    QW_CUDA_TRY(cudaMemsetAsync(mp->tc_err.p, 0, sizeof(int), s));
+    QW_TRY(launch_mlp_tc(mp, X, nullptr, nullptr, n, nullptr, 1.0f, prob, 0.0f, 0, nullptr,
+                         mp->tc_err.as<int>(), s));
+    int h_err = 0;
+    QW_CUDA_TRY(cudaMemcpyAsync(&h_err, mp->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    QW_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h_err & 16) {
+        set_error("qw_mlp_predict_tc: a tensor-core wait gave up");
+        return QW_ERR_TIMEOUT;
+    }
+    return QW_OK;
+}

@@ -46,6 +46,44 @@ def test_mlp_training_reduces_loss(qwlib, cuda):
     mlp.free()
 
 
+@pytest.mark.parametrize("n_in,classes,n", [(192, 16, 1000), (576, 32, 300), (64, 16, 128)])
+def test_mlp_tensor_core_forward(qwlib, cuda, n_in, classes, n):
+    """The tcgen05 forward pass (FP16 activations, FP32 accumulation in tensor
+    memory) against the FP64 definition and the SIMT pass, on ragged row
+    counts (several 128-row tiles and a partial one) and the input widths of
+    the 1M x 128, 4M x 512 and a minimal network."""
+    import torch
+    hidden = 256
+    rng = np.random.default_rng(n_in + classes)
+    p = rng.standard_normal(M.param_count(n_in, hidden, classes)) * (1.0 / np.sqrt(n_in))
+    p = p.astype(np.float16).astype(np.float32)  # FP16-representable: the copies equal the masters
+    X = rng.uniform(-1.5, 1.5, size=(n, n_in)).astype(np.float32)
+    mlp = qwlib.Mlp(n_in, hidden, classes)
+    mlp.set_params(p)
+    Xd = torch.from_numpy(X).to(cuda)
+    p_tc = mlp.predict(Xd, tensor_cores=True).cpu().numpy().astype(np.float64)
+    p_simt = mlp.predict(Xd).cpu().numpy().astype(np.float64)
+    want = M.predict_proba(p.astype(np.float64), X.astype(np.float64), n_in, hidden, classes)
+    assert np.all(np.isfinite(p_tc))
+    assert np.abs(p_simt - want).max() <= 1e-4
+    assert np.abs(p_tc - want).max() <= 5e-3
+    assert np.abs(p_tc.sum(axis=1) - 1.0).max() <= 1e-5
+    # same decision for clear-cut rows
+    clear = want.max(axis=1) > 0.6
+    assert np.array_equal(p_tc[clear].argmax(1), want[clear].argmax(1))
+    mlp.free()
+
+
+def test_mlp_tensor_core_rejects_other_shapes(qwlib, cuda):
+    import torch
+    mlp = qwlib.Mlp(80, 256, 16)
+    mlp.set_params(qwlib.mlp_init(80, 256, 16, seed=2))
+    X = torch.zeros((10, 80), dtype=torch.float32, device=cuda)
+    with pytest.raises(qwlib.QwError):
+        mlp.predict(X, tensor_cores=True)
+    mlp.free()
+
+
 def _train_start_model(qwlib, cuda, index, Q_train, k, epochs=30):
     import torch
     Qt = torch.from_numpy(Q_train).to(cuda)
