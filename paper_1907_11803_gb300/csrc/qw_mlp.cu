@@ -737,9 +737,11 @@ __device__ __forceinline__ uint32_t tc_off(int r, int k, int K)
 // class probabilities (prob, n x C) when prob is given, else each row's first
 // level (start_model_kernel's rule).  W1, W2, W3: FP16, row-major (N x K).
 // err (optional): bit 16 set when a wait gave up (rows then get level 0 or NaN).
+// A CTA answers `rows` <= 128 rows (the MMA tiles stay 128 high, the rest
+// zero), so that small workloads still spread over every SM.
 __global__ void __launch_bounds__(TC_ROWS, 1) mlp_forward_tc_kernel(
     const float *__restrict__ X, const float *__restrict__ Q, const int32_t *__restrict__ HQ,
-    int n, int d, int m, const int32_t *__restrict__ o, const int32_t *__restrict__ span, float xs,
+    int n, int rows, int d, int m, const int32_t *__restrict__ o, const int32_t *__restrict__ span, float xs,
     int K0, const __half *__restrict__ W1, const float *__restrict__ b1,
     const __half *__restrict__ W2, const float *__restrict__ b2, const __half *__restrict__ W3,
     const float *__restrict__ b3, int H, int C, float *__restrict__ prob, float eps, int shift,
@@ -753,7 +755,7 @@ __global__ void __launch_bounds__(TC_ROWS, 1) mlp_forward_tc_kernel(
     unsigned char *act = tsm;                                  // 128 x Ka FP16
     unsigned char *wb = tsm + (size_t)TC_ROWS * Ka * 2;       // 256 x 64 FP16
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int64_t r0 = (int64_t)blockIdx.x * TC_ROWS;
+    const int64_t r0 = (int64_t)blockIdx.x * rows;
     if (tid == 0) {
         s_stuck = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&bar)) : "memory");
@@ -770,17 +772,19 @@ __global__ void __launch_bounds__(TC_ROWS, 1) mlp_forward_tc_kernel(
         const int r = e / K0, j = e - r * K0;
         const int64_t q = r0 + r;
         float v = 0.0f;
-        if (q < n) {
+        if (r < rows && q < n) {
             if (X) {
                 v = X[q * K0 + j];
             } else if (j < d) {
                 v = Q[q * d + j] * xs;
             } else {
+                // the bucket position of features_kernel, in FP32 (FP64
+                // division is slow here, and the value is rounded to FP16)
                 const int i = j - d;
-                const double g = (double)HQ[q * m + i] - (double)o[i];
-                double pos = (g + 0.5) / ((double)span[i] + 1.0);
-                pos = pos < -1.0 ? -1.0 : (pos > 2.0 ? 2.0 : pos);
-                v = (float)(pos - 0.5);
+                const float g = (float)(HQ[q * m + i] - o[i]);
+                float pos = (g + 0.5f) / ((float)span[i] + 1.0f);
+                pos = pos < -1.0f ? -1.0f : (pos > 2.0f ? 2.0f : pos);
+                v = pos - 0.5f;
             }
         }
         *reinterpret_cast<__half *>(act + tc_off(r, j, K0)) = __float2half_rn(v);
@@ -793,13 +797,32 @@ __global__ void __launch_bounds__(TC_ROWS, 1) mlp_forward_tc_kernel(
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;  // this warp's TMEM lanes
     uint32_t phase = 0;
 
-    // D[:, dcol .. dcol + N) = act[128 x K] x W^T
+    // D[:, dcol .. dcol + N) = act[128 x K] x W^T.  A thread holds its
+    // PER 16-byte pieces of a weight chunk in registers: the next chunk's
+    // loads are issued before the wait for the current chunk's MMAs.
+    constexpr int PER = TC_MAXN * (TC_KC / 8) / TC_ROWS;
     auto layer = [&](int K, const __half *__restrict__ W, int N, uint32_t dcol) {
+        const int pieces = N * (TC_KC / 8);
+        uint4 reg[PER];
+        auto fetch = [&](int kc) {
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const int p = tid + u * TC_ROWS;
+                if (p < pieces)
+                    reg[u] = *reinterpret_cast<const uint4 *>(W + (int64_t)(p >> 3) * K + kc +
+                                                              8 * (p & 7));
+            }
+        };
+        fetch(0);
         for (int kc = 0; kc < K; kc += TC_KC) {
-            for (int p = tid; p < N * (TC_KC / 8); p += TC_ROWS) {
-                const int nr = p >> 3, j = p & 7;
-                const uint4 v = *reinterpret_cast<const uint4 *>(W + (int64_t)nr * K + kc + 8 * j);
-                *reinterpret_cast<uint4 *>(wb + ((nr >> 3) * (TC_KC / 8) + j) * 128 + (nr & 7) * 16) = v;
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const int p = tid + u * TC_ROWS;
+                if (p < pieces) {
+                    const int nr = p >> 3, j = p & 7;
+                    *reinterpret_cast<uint4 *>(wb + ((nr >> 3) * (TC_KC / 8) + j) * 128 +
+                                               (nr & 7) * 16) = reg[u];
+                }
             }
             tc_fence_async_smem();
             tc_fence_before();
@@ -817,6 +840,7 @@ __global__ void __launch_bounds__(TC_ROWS, 1) mlp_forward_tc_kernel(
                 }
                 tc_commit(&bar);
             }
+            if (kc + TC_KC < K) fetch(kc + TC_KC);  // in flight while the MMAs run
             if (go) {
                 if (!tc_wait(&bar, phase)) s_stuck = 1;
                 phase ^= 1;
@@ -862,7 +886,7 @@ __global__ void __launch_bounds__(TC_ROWS, 1) mlp_forward_tc_kernel(
     }
     const int64_t q = r0 + tid;
     const bool stuck = s_stuck != 0;
-    if (q < n) {
+    if (tid < rows && q < n) {
         float mx = -INFINITY;
 #pragma unroll
         for (int c = 0; c < TC_MAXC; ++c) mx = fmaxf(mx, z[c]);
@@ -922,8 +946,14 @@ static qw_status launch_mlp_tc(qw_mlp *mp, const float *X, const float *Q, const
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const __half *h = mp->p16.as<__half>();
     const float *p = mp->p32.as<float>();
-    mlp_forward_tc_kernel<<<(unsigned)((n + TC_ROWS - 1) / TC_ROWS), TC_ROWS, smem, s>>>(
-        X, Q, HQ, (int)n, ix ? ix->d : 0, ix ? ix->m : 0, ix ? ix->o : nullptr,
+    // rows per CTA: enough CTAs for every SM (one CTA per SM), 16 to 128
+    int dev = 0, sms = 152;
+    QW_CUDA_TRY(cudaGetDevice(&dev));
+    QW_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int64_t rows = (n + sms - 1) / sms;
+    rows = std::min<int64_t>(TC_ROWS, std::max<int64_t>(16, (rows + 15) / 16 * 16));
+    mlp_forward_tc_kernel<<<(unsigned)((n + rows - 1) / rows), TC_ROWS, smem, s>>>(
+        X, Q, HQ, (int)n, (int)rows, ix ? ix->d : 0, ix ? ix->m : 0, ix ? ix->o : nullptr,
         ix ? ix->span : nullptr, xs, K0, h + mp->oW1, p + mp->ob1, h + mp->oW2, p + mp->ob2,
         h + mp->oW3, p + mp->ob3, mp->H, mp->C, prob, eps, shift, start, err);
     QW_CUDA_TRY(cudaGetLastError());
