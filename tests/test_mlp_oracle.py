@@ -42,3 +42,26 @@ def test_probabilities_sum_to_one():
     p, X, y, dims = _setup(seed=3)
     P = M.predict_proba(p, X, *dims)
     assert np.allclose(P.sum(axis=1), 1.0) and np.all(P > 0)
+
+
+def test_probabilities_match_the_loss():
+    """The forward pass the tensor-core test compares with is the one whose
+    loss the finite differences pin: mean(-log P[i, y_i]) equals the loss."""
+    p, X, y, dims = _setup(seed=4)
+    P = M.predict_proba(p, X, *dims)
+    loss, _ = M.loss_and_grad(p, X, y, *dims)
+    assert abs(-np.mean(np.log(P[np.arange(len(y)), y])) - loss) < 1e-12
+
+
+def test_identity_network_closed_form():
+    """W1 = W2 = W3 = I, zero biases: the logits are ReLU(x), so the
+    probabilities are softmax(max(x, 0)) -- with the ReLU visible on a
+    negative input."""
+    n_in = hidden = classes = 3
+    eye = np.eye(3)
+    p = np.concatenate([eye.ravel(), np.zeros(3), eye.ravel(), np.zeros(3), eye.ravel(),
+                        np.zeros(3)])
+    X = np.array([[0.5, -2.0, 1.5], [3.0, 1.0, -0.25]])
+    z = np.maximum(X, 0.0)
+    want = np.exp(z) / np.exp(z).sum(axis=1, keepdims=True)
+    assert np.allclose(M.predict_proba(p, X, n_in, hidden, classes), want, rtol=0, atol=1e-15)
