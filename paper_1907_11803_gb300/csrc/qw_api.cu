@@ -549,11 +549,10 @@ constexpr int64_t kBitmapBudget = (int64_t)48 << 30;
 // with the given settings (the bitmap path from level 0, for queries whose
 // learned first level was too late).  The list is copied first: the nested
 // call reuses the workspace it lives in.
-static qw_status level_path_rerun(qw_index *ix, const float *Qall, const int32_t *HQall,
-                                  const int32_t *list, int n, int k, int cap, int64_t *f_ids,
-                                  float *f_dists, int64_t *f_stats, int64_t *f_cids,
-                                  int32_t *f_ccol, cudaStream_t s,
-                                  const qw_query_params *rerun = nullptr)
+static qw_status answer_again(qw_index *ix, const float *Qall, const int32_t *HQall,
+                              const int32_t *list, int n, int k, int cap, int64_t *f_ids,
+                              float *f_dists, int64_t *f_stats, int64_t *f_cids, int32_t *f_ccol,
+                              cudaStream_t s, const qw_query_params *rerun = nullptr)
 {
     const int d = ix->d, m = ix->m;
     DevBuf lst, q_in, hq_in, o_ids, o_dists, o_stats, o_cids, o_ccol;
@@ -1106,8 +1105,8 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         QW_CUDA_TRY(cudaMemcpyAsync(n_ovf, ovf_count, sizeof(n_ovf), cudaMemcpyDeviceToHost, s));
         QW_CUDA_TRY(cudaStreamSynchronize(s));
         if (n_ovf[0] > 0)
-            QW_TRY(level_path_rerun(ix, Qall, HQall, ovf_list, n_ovf[0], k, cap, f_ids, f_dists,
-                                    f_stats, f_cids, f_ccol, s));
+            QW_TRY(answer_again(ix, Qall, HQall, ovf_list, n_ovf[0], k, cap, f_ids, f_dists,
+                                f_stats, f_cids, f_ccol, s));
         if (n_ovf[1] > 0) {
             qw_query_params p{};
             p.path = QW_PATH_BITMAP;
@@ -1115,8 +1114,8 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             p.start = QW_START_PLAIN;
             p.graph = graph ? 1 : 0;
             p.bitmap_loads = tma_loads ? QW_LOADS_TMA : QW_LOADS_DIRECT;
-            QW_TRY(level_path_rerun(ix, Qall, HQall, late_list, n_ovf[1], k, cap, f_ids, f_dists,
-                                    f_stats, f_cids, f_ccol, s, &p));
+            QW_TRY(answer_again(ix, Qall, HQall, late_list, n_ovf[1], k, cap, f_ids, f_dists,
+                                f_stats, f_cids, f_ccol, s, &p));
         }
     }
     if (host) {
