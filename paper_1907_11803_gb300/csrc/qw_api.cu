@@ -574,8 +574,13 @@ static qw_status answer_again(qw_index *ix, const float *Qall, const int32_t *HQ
     if (rerun) {
         p = *rerun;
     } else {
+        // the level path in graph mode, from the learned first levels when a
+        // start model is attached (both leave the results unchanged)
         p.path = QW_PATH_LEVELS;
         p.order = QW_ORDER_GIVEN;
+        p.graph = 1;
+        if (ix->start_model && mlp_inputs(ix->start_model) == ix->d + ix->m)
+            p.start = QW_START_LEARNED;
     }
     const qw_profile saved = ix->prof;
     QW_TRY(run_impl(ix, q_in.as<float>(), n, k, &p, o_ids.as<int64_t>(), o_dists.as<float>(),
