@@ -8,14 +8,19 @@ top-k) against an index already resident in HBM.  The default workload is
 projections, w = 4, 10,000 queries from 100 clusters, k = 100.
 
 Two configurations of the same call are timed, with identical results: the
-plain path (queries in the given order, collision counting from level 0, FP32
-distances) and the chosen path (queries grouped by bucket signature, learned
-first levels, BF16 distance pre-filter).  ``value`` is the chosen path's; the
-plain path's figures are reported beside it.  The start model is trained
-before the timed region on queries drawn from the same workload.
+plain path (level path, queries in the given order, collision counting from
+level 0, FP32 distances, host-driven loop) and the chosen path (the settings
+qw_autotune picks on training queries of the same workload among the counting
+paths, batch sizes, graph mode, workload order, learned first levels, the BF16
+distance pre-filter and the persisting-L2 split).  ``value`` is the chosen
+path's; the plain path's figures are reported beside it, with the roofline of
+the dominant kernels, the end-to-end rate from pinned host memory, and the
+CPU oracle timed on all host threads.  The start model is trained before the
+timed region on queries drawn from the same workload.
 
 Prints one JSON line.  ``--impl reference`` times the CPU oracle on a bounded
-sample of the same workload instead.  Under torchrun (``--gpus N``) every rank
+sample of the same workload instead; ``--l2-sweep`` adds the chosen path under
+the paper's cache splits.  Under torchrun (``--gpus N``) every rank
 answers its own copy of the workload against its own replica of the index
 (the path has no exchange step); the timed region is bracketed by barriers and
 the slowest rank's time is used.
