@@ -8,9 +8,12 @@
 // gives no network.  This one is x (n_in) -> ReLU(W1 x + b1) -> ReLU(W2 . + b2)
 // -> W3 . + b3 (C logits), trained with mean softmax cross-entropy and Adam.
 // Weights are used as FP16 copies of FP32 master weights; every product is
-// accumulated in FP32.  Forward, backward and the optimizer step are the
-// kernels below (tiled SIMT GEMMs: the layers are a few hundred wide, far too
-// small for the tensor cores to matter next to the counting kernels).
+// accumulated in FP32.  Training (forward, backward, the optimizer step) runs
+// on tiled CUDA-core GEMMs, once and outside the query path.  The forward
+// pass of the query path (the first levels of a workload's queries) runs on
+// the tensor cores (mlp_forward_tc_kernel: tcgen05.mma, accumulators in tensor
+// memory) when the network has its shape, else on the fused CUDA-core kernel
+// start_model_kernel.
 #include "qw_internal.cuh"
 
 #include <cuda_fp16.h>
