@@ -99,3 +99,27 @@ def test_product_path_has_no_oracle_import():
             text = open(path).read()
             code = re.sub(r"(#|//).*", "", text)
             assert not re.search(r"\bimport\s+oracle|from\s+oracle|liboracle|qwlsh_oracle", code), path
+
+
+def test_l2_split_arguments_of_the_binding(qwlib):
+    """query(l2=...) maps to the ABI's l2_mode / l2_index_permille fields."""
+    assert qwlib._l2_fields(None) == {"l2_mode": qwlib.QW_L2_OFF, "l2_index_permille": 0}
+    assert qwlib._l2_fields("off") == {"l2_mode": qwlib.QW_L2_OFF, "l2_index_permille": 0}
+    assert qwlib._l2_fields("model") == {"l2_mode": qwlib.QW_L2_MODEL, "l2_index_permille": 0}
+    assert qwlib._l2_fields(250) == {"l2_mode": qwlib.QW_L2_SPLIT, "l2_index_permille": 250}
+    for bad in (True, 0.5, "half"):
+        with pytest.raises(ValueError):
+            qwlib._l2_fields(bad)
+    qp = qwlib.qw_query_params(**qwlib._l2_fields(990))
+    assert qp.l2_mode == qwlib.QW_L2_SPLIT and qp.l2_index_permille == 990
+    assert list(qp.reserved) == [0]
+
+
+def test_host_bitmaps_need_bitmaps_without_device(qwlib):
+    """The argument check runs before any device work."""
+    L = qwlib.load()
+    h = C.c_void_p()
+    fake = C.c_void_p(16)
+    p = qwlib.qw_index_params(m=8, w=4.0, c=2, v=10, host_bitmaps=1)
+    assert L.qw_build_index(fake, 10, 4, fake, fake, C.byref(p), 0, None, C.byref(h)) == qwlib.QW_ERR_ARG
+    assert b"host_bitmaps" in L.qw_last_error()
