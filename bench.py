@@ -3,9 +3,10 @@
 
 One step = one call answering the whole synthetic query workload (project the
 queries, collision counting over all levels, candidate selection, distances,
-top-k) against an index already resident in HBM.  The default workload is
-1,000,000 x 128 float32 points (Gaussian mixture of 1,000 clusters), 64
-projections, w = 4, 10,000 queries from 100 clusters, k = 100.
+top-k) against an index already resident in HBM.  The default workload is the
+largest single-GPU one: 10,000,000 x 128 float32 points (Gaussian mixture of
+10,000 clusters), 64 projections, w = 4, 100,000 queries with mixed difficulty
+(noise sigma 0.05, 0.5 and 2.0 in equal thirds), k = 10.
 
 Two configurations of the same call are timed, with identical results: the
 plain path (level path, queries in the given order, collision counting from
@@ -61,11 +62,11 @@ def parse_args(argv=None):
     # default: about one second of timed GPU steps (so that clocks are sampled
     # while they run); 5 steps of the CPU reference arm
     p.add_argument("--steps", type=int, default=None)
-    p.add_argument("--plain-steps", type=int, default=3,
+    p.add_argument("--plain-steps", type=int, default=2,
                    help="timed steps of the plain path (at most --steps)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="mix1m_d128")
+    p.add_argument("--workload", default="mix10m_d128")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--quality-sample", type=int, default=200,
                    help="queries checked against exact k-NN for recall / ratio")
@@ -119,6 +120,14 @@ def operating_point(args, spec):
     v = args.v if args.v >= 0 else dv
     l = args.l if args.l >= 0 else dl
     return v, l
+
+
+_T0 = time.perf_counter()
+
+
+def log(msg: str):
+    """Progress of the run on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
 
 
 # ---------------------------------------------------------------- ranks
@@ -322,16 +331,35 @@ def oracle_query_threads(orc, wl, idx, Qs, HQ, *, k, v, l, c, threads):
     return time.perf_counter() - t0
 
 
-def oracle_sample(wl, l, n_queries, seed=1, v=None, threads=1):
+def oracle_hash_threads(orc, V, A, b, w, threads):
+    """The oracle's hash of the rows of V, the rows split into `threads`
+    contiguous slices hashed at the same time (each row's bucket ids depend on
+    that row alone)."""
+    import concurrent.futures as cf
+
+    import numpy as np
+    parts = [p for p in np.array_split(np.arange(V.shape[0]), max(1, threads)) if p.size]
+    with cf.ThreadPoolExecutor(max_workers=len(parts)) as ex:
+        Hs = list(ex.map(lambda p: orc.hash(V[p[0]:p[-1] + 1], A, b, w), parts))
+    return np.concatenate(Hs) if Hs else np.empty((0, A.shape[0]), np.int32)
+
+
+def oracle_index(wl, threads):
+    """The oracle and its index of the workload's data (anchors and spans; the
+    query procedure recounts collisions from the bucket-id rows)."""
+    import oracle
+    orc = oracle.get()
+    H = oracle_hash_threads(orc, wl.X, wl.A, wl.b, wl.spec.w, threads)
+    return orc, orc.build_index(H, sorted_arrays=False)
+
+
+def oracle_sample(wl, l, n_queries, seed=1, v=None, threads=1, built=None):
     """Time the oracle's query procedure on a seeded sample of the workload's
     queries (the index build is excluded, as on the GPU) on `threads` host
     cores.  Returns (queries/s, seconds, sample size, (oracle, its index))."""
     import numpy as np
-    import oracle
-    orc = oracle.get()
     s = wl.spec
-    H = orc.hash(wl.X, wl.A, wl.b, s.w)
-    idx = orc.build_index(H, sorted_arrays=False)
+    orc, idx = built if built is not None else oracle_index(wl, threads)
     rng = np.random.default_rng(seed)
     pick = np.sort(rng.choice(s.nq, size=min(n_queries, s.nq), replace=False))
     Qs = wl.Q[pick]
@@ -373,12 +401,19 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
     nq = args.queries or None
-    wl = workloads.make_workload(args.workload, seed=args.seed, nq=nq)
+    # the timed queries and, from a separate stream, the training queries of
+    # the start model and the autotuner (same data, cluster pool and noise mix)
+    wl = workloads.make_workload(args.workload, seed=args.seed, nq=nq,
+                                 n_train=args.train_queries)
+    s = wl.spec
     if world > 1 and rank > 0:
         # each rank answers its own seeded query workload against the same data
-        other = workloads.make_workload(args.workload, seed=args.seed + 1000 * rank, nq=nq)
-        wl.Q = other.Q
-    s = wl.spec
+        wl.Q, _ = workloads.make_queries(
+            wl.X, wl.labels, s.nq, np.random.default_rng(args.seed + 1000 * rank),
+            n_clusters=s.n_clusters, query_clusters=s.query_clusters, zipf=s.zipf,
+            noise=s.query_noise, pool=wl.extra["query_pool"])
+    log(f"workload {s.name}: {s.n} x {s.d}, {s.nq} queries, {args.train_queries} training "
+        f"queries drawn")
     X = torch.from_numpy(wl.X).to(dev)
     A = torch.from_numpy(wl.A).to(dev)
     b = torch.from_numpy(wl.b).to(dev)
@@ -401,10 +436,12 @@ def run_ours(args):
                      start=args.start, graph=args.graph, loads=args.loads, l2=l2_arg)
     mlp = None
     train_info = None
-    wt = workloads.make_workload(args.workload, seed=args.seed, nq=1, n_train=args.train_queries)
-    Qt = torch.from_numpy(wt.Q_train).to(dev)
+    log(f"index built: {index.info.device_bytes / 1e9:.2f} GB on the device, "
+        f"l = {index.l}")
+    Qt = torch.from_numpy(wl.Q_train).to(dev)
     if args.start == "learned":
         mlp, train_info = train_start_model(qw, torch, index, Qt, s.k, args)
+        log(f"start model trained: {train_info}")
         if args.no_tune and chosen_kw["path"] in ("auto", "cluster"):
             chosen_kw["path"] = "levels"  # learned first levels need a level loop
     tune = None
@@ -414,9 +451,16 @@ def run_ours(args):
         chosen_kw, trials = index.autotune(Qt[:s.nq], s.k, reps=1)
         tune = {"seconds": round(time.perf_counter() - t0, 2), "queries": int(min(s.nq, Qt.shape[0])),
                 "trials": [dict(t, ms=round(ms, 3)) for t, ms in trials]}
+        log(f"autotuned in {tune['seconds']} s: {chosen_kw}")
 
-    def timed(kw, steps):
-        for _ in range(args.warmup):
+    def timed(kw, steps, warmup=None, profiled=True):
+        """`warmup` untimed steps, then `steps` timed ones bracketed by a
+        barrier and a synchronize (CUDA events on the library's stream); the
+        timed steps run uninstrumented.  With `profiled`, the same number of
+        steps is then run again in profile mode (every launch timed by CUDA
+        events on the stream) for the per-kernel breakdown.  Returns (ms, max
+        over ranks, profile counters of the timed steps, of the profiled)."""
+        for _ in range(args.warmup if warmup is None else warmup):
             index.query(Q, s.k, out=(ids, dists), **kw)
         torch.cuda.synchronize()
         index.profile(reset=True)
@@ -426,24 +470,39 @@ def run_ours(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
-            index.query(Q, s.k, out=(ids, dists), profile=True, **kw)
+            index.query(Q, s.k, out=(ids, dists), **kw)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier(world)
         ms = e0.elapsed_time(e1)
-        return ms, max_over_ranks(ms, world), index.profile(reset=True)
+        counted = index.profile(reset=True)
+        prof = None
+        if profiled:
+            for _ in range(steps):
+                index.query(Q, s.k, out=(ids, dists), profile=True, **kw)
+            torch.cuda.synchronize()
+            prof = index.profile(reset=True)
+        return ms, max_over_ranks(ms, world), counted, prof
 
-    # the plain path first: its results are the reference for the chosen one
-    _, _, st = index.query(Q, s.k, stats=True, **plain_kw)
+    # the plain path first: its results are the reference for the chosen one.
+    # Its first call (statistics, every launch timed) is its first warm-up step
+    # and gives its kernel breakdown; one more warm-up step follows (a plain
+    # step over the large workloads takes tens of seconds).
+    index.profile(reset=True)
+    _, _, st = index.query(Q, s.k, stats=True, profile=True, **plain_kw)
+    torch.cuda.synchronize()
+    p_prof = index.profile(reset=True)
     st = st.cpu().numpy()
     p_steps = max(1, min(args.steps, args.plain_steps))
-    p_ms, p_ms_max, p_prof = timed(plain_kw, p_steps)
+    p_ms, p_ms_max, _, _ = timed(plain_kw, p_steps, warmup=min(args.warmup, 1), profiled=False)
     ids_plain, dists_plain = ids.clone(), dists.clone()
+    log(f"plain path: {p_ms_max / p_steps:.2f} ms per step")
 
     clocks = ClockSampler(gpu_uuid(torch))
     clocks.start()
-    ms, ms_max, prof = timed(chosen_kw, args.steps)
+    ms, ms_max, counted, prof = timed(chosen_kw, args.steps)
     clk = clocks.stop()
+    log(f"chosen path: {ms_max / args.steps:.3f} ms per step")
     l2_prof = {"setaside_bytes": prof["l2_setaside_bytes"],
                "index_permille": prof["l2_index_permille"]} if chosen_kw.get("l2") else None
     value = world * s.nq * args.steps / (ms_max / 1e3)
@@ -451,8 +510,8 @@ def run_ours(args):
     plain = {"value": world * s.nq * p_steps / (p_ms_max / 1e3),
              "ms_per_step": p_ms_max / p_steps, "steps": p_steps, "settings": plain_kw,
              "results_identical_to_chosen": same,
-             "kernel_ms_per_step": {k2: round(v2 / p_steps, 3)
-                                    for k2, v2 in p_prof["ms"].items()}}
+             "warmup": 1 + min(args.warmup, 1),
+             "kernel_ms_first_step": {k2: round(v2, 3) for k2, v2 in p_prof["ms"].items()}}
 
     # the paper's cache-split grid (QALSH_Ci/Cd/CiCd/Opt settings, Section 6) on
     # the GPU's persisting L2, with the chosen path's other settings
@@ -463,7 +522,7 @@ def run_ours(args):
         rows = []
         for g in grid:
             kw = dict(chosen_kw, l2=g)
-            t_ms, t_max, t_prof = timed(kw, args.sweep_steps)
+            t_ms, t_max, t_prof, _ = timed(kw, args.sweep_steps, profiled=False)
             rows.append({"l2": "off" if g is None else g,
                          "ms_per_step": round(t_max / args.sweep_steps, 4),
                          "index_permille": t_prof["l2_index_permille"] if g is not None else None,
@@ -491,6 +550,7 @@ def run_ours(args):
                                                replace=False))).to(dev)
     tids, tdists = exact_knn_gpu(X, Q[pick], s.k)
     recall, ratio = recall_ratio(ids[pick], dists[pick], tids, tdists)
+    log(f"quality: recall {recall:.4f}, ratio {ratio:.5f}; end to end {e2e['value']:.1f} q/s")
 
     # roofline of the dominant kernel and of the candidate-distance kernel
     peaks, peak_kind = measured_peaks()
@@ -560,16 +620,24 @@ def run_ours(args):
                                        args.workload)),
                        "algorithmic_bytes_per_launch": rr_bytes / max(rr_launches, 1),
                        "avg_launch_ms": rr_ms / max(rr_launches, 1)}
-    launches = int(sum(prof["launches"].values()))
+    # kernels launched in the (uninstrumented) timed region
+    launches = int(sum(counted["launches"].values()))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nth = host_threads()
+        built = oracle_index(wl, nth)
         qps, dt, nsamp, _ = oracle_sample(wl, index.l, max(1, args.cpu_sample) * nth, v=v_used,
-                                          threads=nth)
+                                          threads=nth, built=built)
+        qps1, dt1, nsamp1, _ = oracle_sample(wl, index.l, max(1, args.cpu_sample), seed=2,
+                                             v=v_used, threads=1, built=built)
         cpu = {"value": qps, "unit": UNIT, "cores": nth, "kind": "oracle",
                "sample": f"{nsamp} seeded queries of the same workload, query procedure only, "
-                         f"split over {nth} host threads ({dt:.1f} s wall, FP64)"}
+                         f"split over {nth} host threads ({dt:.1f} s wall, FP64)",
+               "single_thread": {"value": qps1, "unit": UNIT, "cores": 1,
+                                 "sample": f"{nsamp1} other seeded queries on one host thread "
+                                           f"({dt1:.1f} s wall, FP64)"}}
+        log(f"cpu baseline: {qps:.2f} q/s on {nth} threads, {qps1:.3f} q/s on one")
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -627,7 +695,7 @@ def run_reference(args):
     l = l_arg if l_arg > 0 else oracle.get().threshold(s.m, s.w, s.c, s.n, v_used)
     nth = host_threads()
     per_step = max(1, args.cpu_sample) * nth
-    qps0, _, _, (orc, idx) = oracle_sample(wl, l, nth, seed=0, v=v_used, threads=nth)
+    orc, idx = oracle_index(wl, nth)
     rng = np.random.default_rng(99)
     times = []
     for step in range(args.warmup + args.steps):

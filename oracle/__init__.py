@@ -219,20 +219,3 @@ def get() -> Oracle:
 
 STAT_FIELDS = ("levels", "final_R", "n_cand_raw", "n_cand", "term", "scanned_last",
                "scanned_full", "n_prev")
-
-
-def recall_and_ratio(ids: np.ndarray, dists: np.ndarray, true_ids: np.ndarray,
-                     true_dists: np.ndarray):
-    """Recall = |result & true top-k| / k; ratio = mean over ranks of
-    dist(o_i, q) / dist(o_i*, q) (the c-k-ANN ratio of Section 3), over the
-    ranks where both exist and the true distance is non-zero."""
-    nq, k = ids.shape
-    rec = np.empty(nq)
-    rat = np.full(nq, np.nan)
-    for q in range(nq):
-        got = set(int(i) for i in ids[q] if i >= 0)
-        rec[q] = len(got & set(int(i) for i in true_ids[q])) / k
-        ok = (ids[q] >= 0) & (true_dists[q] > 0)
-        if ok.any():
-            rat[q] = float(np.mean(dists[q][ok] / true_dists[q][ok]))
-    return float(rec.mean()), float(np.nanmean(rat)) if np.isfinite(rat).any() else float("nan")

@@ -344,8 +344,63 @@ def pin_duplicates_tie_by_id(orc):
     return fails
 
 
+def pin_hand_worked_golden(orc):
+    """A workload of 10 points, 3 projections and 3 queries worked out by hand
+    (tests/golden/hand_worked_query.json): bucket ids, anchors and spans,
+    every level's collision counts, the stop level (the k + v bound of
+    Section 3.1, or the radius past every bucket), the kept candidates in
+    truncation order, the statistics and the top-k."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "hand_worked_query.json")
+    with open(path) as fh:
+        g = json.load(fh)
+    p = g["params"]
+    X = np.array(g["X"], np.float32)
+    Q = np.array(g["Q"], np.float32)
+    A = np.array(g["A"], np.float32)
+    b = np.array(g["b"], np.float32)
+    fails = []
+    H = orc.hash(X, A, b, p["w"])
+    HQ = orc.hash(Q, A, b, p["w"])
+    if not np.array_equal(H, np.array(g["H"])) or not np.array_equal(HQ, np.array(g["HQ"])):
+        return ["bucket ids differ from the hand-worked ones"]
+    ix = orc.build_index(H)
+    if ix.o.tolist() != g["o"] or ix.span.tolist() != g["span"]:
+        fails.append(f"anchors {ix.o.tolist()} / spans {ix.span.tolist()} differ")
+    for qi, q in enumerate(g["queries"]):
+        for lv in q["levels"]:
+            col = orc.collision_counts(ix, HQ[qi], lv["R"])
+            if col.tolist() != lv["col"]:
+                fails.append(f"query {qi}, R = {lv['R']}: counts {col.tolist()} want {lv['col']}")
+    res = orc.query(X, ix, Q, HQ, k=p["k"], v=p["v"], l=p["l"], c=p["c"])
+    cap = p["k"] + p["v"]
+    for qi, q in enumerate(g["queries"]):
+        st = res["stats"][qi].tolist()
+        if st != q["stats"]:
+            fails.append(f"query {qi}: stats {st} want {q['stats']}")
+        kept = res["cand_ids"][qi].tolist()
+        want_kept = q["kept"] + [-1] * (cap - len(q["kept"]))
+        if kept != want_kept:
+            fails.append(f"query {qi}: kept {kept} want {want_kept} (truncation order)")
+        kcol = res["cand_col"][qi][: len(q["kept"])].tolist()
+        if kcol != q["kept_col"]:
+            fails.append(f"query {qi}: kept counts {kcol} want {q['kept_col']}")
+        if res["ids"][qi].tolist() != q["ids"]:
+            fails.append(f"query {qi}: ids {res['ids'][qi].tolist()} want {q['ids']}")
+        want_d = [math.sqrt(x) if x is not None else math.inf for x in q["sqdists"]]
+        if not np.array_equal(res["dists"][qi], np.array(want_d)):
+            fails.append(f"query {qi}: dists {res['dists'][qi].tolist()} want {want_d}")
+    for qi, q in enumerate(g["queries"]):
+        for t, i in enumerate(q["kept"]):
+            if orc.sqdist(X[i], Q[qi]) != q["kept_sqdist"][t]:
+                fails.append(f"query {qi}: squared distance to {i} differs")
+    return fails
+
+
 ALL_PINS = [pin_collision_prob_quadrature, pin_collision_prob_limits, pin_threshold_balance,
             pin_hash_exact_sum, pin_index_sorted_arrays, pin_collision_counts,
             pin_single_projection_is_e2lsh, pin_bruteforce, pin_v_ge_n_exact,
             pin_workload_semantics, pin_t3_fixpoint, pin_ratio_invariant,
-            pin_duplicates_tie_by_id]
+            pin_duplicates_tie_by_id, pin_hand_worked_golden]

@@ -7,6 +7,7 @@ their collision counts, statistics and result ids bit-exact; distances within
 import numpy as np
 import pytest
 
+import oracle_par
 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -95,6 +96,41 @@ def _full_parity(orc, qw, dev, X, Q, A, b, *, w, k, v, l=None, c=2, batch=0, hos
     _check_candidates(g["cid"], g["ccol"], ref["cand_ids"], ref["cand_col"])
     g["index"].free()
     return ref, g
+
+
+# ---------------------------------------------------------------- hand-worked case
+@PATHS
+def test_hand_worked_golden(qwlib, cuda, path):
+    """The workload worked out by hand (tests/golden/hand_worked_query.json):
+    every path returns its statistics, kept candidates with their counts,
+    ids and distances (the oracle is pinned to the same values)."""
+    import json
+    import math
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "hand_worked_query.json")) as fh:
+        g = json.load(fh)
+    p = g["params"]
+    X, Q = (np.array(g[key], np.float32) for key in ("X", "Q"))
+    A, b = np.array(g["A"], np.float32), np.array(g["b"], np.float32)
+    H, _ = qwlib.hash(_t(X, cuda), _t(A, cuda), _t(b, cuda), p["w"])
+    assert np.array_equal(H.cpu().numpy(), np.array(g["H"]))
+    out = _gpu_workload(qwlib, cuda, X, Q, A, b, w=p["w"], k=p["k"], v=p["v"], l=p["l"],
+                        c=p["c"], path=path)
+    cap = p["k"] + p["v"]
+    for qi, q in enumerate(g["queries"]):
+        assert out["stats"][qi].tolist() == q["stats"], f"query {qi} statistics"
+        assert out["stats2"][qi].tolist() == q["stats"]
+        assert out["ids"][qi].tolist() == q["ids"], f"query {qi} ids"
+        want_d = [math.sqrt(x) if x is not None else math.inf for x in q["sqdists"]]
+        fin = np.isfinite(want_d)
+        assert np.array_equal(np.isfinite(out["dists"][qi]), fin)
+        assert np.allclose(out["dists"][qi][fin], np.array(want_d)[fin], rtol=DIST_RTOL, atol=0)
+        order = np.argsort(q["kept"], kind="stable")
+        kept = np.array(q["kept"], np.int64)[order]
+        col = np.array(q["kept_col"], np.int32)[order]
+        assert out["cid"][qi].tolist() == kept.tolist() + [-1] * (cap - kept.size)
+        assert out["ccol"][qi][: kept.size].tolist() == col.tolist()
+    out["index"].free()
 
 
 # ---------------------------------------------------------------- a1 + a2: hashing
@@ -370,7 +406,7 @@ def test_full_size_sampled(orc, qwlib, cuda):
     """The benchmarked workload (1M x 128, 64 projections, 10,000 queries,
     k = 100, v = 700, l = 43) run whole on the GPU in the benchmark's launch
     configuration (bitmap path, signature order, learned first levels, graph
-    mode) and in the plain one; the oracle recomputes a seeded sample of
+    mode) and in the plain one; the oracle recomputes a seeded sample of 128
     queries one by one."""
     import torch
     wl = workloads.make_workload("mix1m_d128", seed=0, n_train=8_000)
@@ -399,13 +435,14 @@ def test_full_size_sampled(orc, qwlib, cuda):
     assert np.array_equal(st, st2.cpu().numpy())
     assert np.array_equal(dists, dists2.cpu().numpy())
     assert prof["start_levels_skipped"] > 0
-    H = orc.hash(wl.X, wl.A, wl.b, s.w)
+    H = oracle_par.hash_rows(orc, wl.X, wl.A, wl.b, s.w)
     oidx = orc.build_index(H, sorted_arrays=True)
     assert index.info.l == l
-    sample = np.random.default_rng(123).choice(s.nq, size=12, replace=False)
+    # 128 seeded queries recomputed by the oracle, spread over the host threads
+    sample = np.random.default_rng(123).choice(s.nq, size=128, replace=False)
     sample.sort()
     HQ = orc.hash(wl.Q[sample], wl.A, wl.b, s.w)
-    ref = orc.query(wl.X, oidx, wl.Q[sample], HQ, k=s.k, v=v, l=l, c=s.c)
+    ref = oracle_par.query_rows(orc, wl.X, oidx, wl.Q[sample], HQ, k=s.k, v=v, l=l, c=s.c)
     _check_results(ids[sample], dists[sample], ref["ids"], ref["dists"])
     assert np.array_equal(st[sample], ref["stats"])
     # properties that hold for every query

@@ -13,22 +13,30 @@ MUTANTS = [
      "double u = (t[i] + (double)b[i]) / (double)w;\n            double f = trunc(u);",
      ["pin_hash_exact_sum"]),
     ("level_floor_division_truncates", "if ((a % R != 0) && (a < 0)) q -= 1;", "",
-     ["pin_collision_counts", "pin_t3_fixpoint", "pin_workload_semantics"]),
+     ["pin_collision_counts", "pin_t3_fixpoint", "pin_workload_semantics",
+      "pin_hand_worked_golden"]),
     ("threshold_strict", "for (int64_t j = 0; j < n; ++j) if (col[j] >= l) ncand += 1;",
      "for (int64_t j = 0; j < n; ++j) if (col[j] > l) ncand += 1;",
-     ["pin_workload_semantics", "pin_v_ge_n_exact"]),
+     ["pin_workload_semantics", "pin_v_ge_n_exact", "pin_hand_worked_golden"]),
     ("truncation_fewest_collisions_first", "if (a->col != b->col) return a->col > b->col ? -1 : 1;",
-     "if (a->col != b->col) return a->col < b->col ? -1 : 1;", ["pin_workload_semantics"]),
+     "if (a->col != b->col) return a->col < b->col ? -1 : 1;",
+     ["pin_workload_semantics", "pin_hand_worked_golden"]),
     ("truncation_ignores_previous_level", "cs[nc].prev = prev[j];", "cs[nc].prev = 0;",
-     ["pin_workload_semantics"]),
+     ["pin_workload_semantics", "pin_hand_worked_golden"]),
+    ("truncation_larger_id_first",
+     "if (a->col != b->col) return a->col > b->col ? -1 : 1;\n    if (a->id != b->id) return a->id < b->id ? -1 : 1;",
+     "if (a->col != b->col) return a->col > b->col ? -1 : 1;\n    if (a->id != b->id) return a->id > b->id ? -1 : 1;",
+     ["pin_hand_worked_golden"]),
+    ("stop_rule_strict", "if (ncand >= cap) { term = 2; break; }",
+     "if (ncand > cap) { term = 2; break; }", ["pin_hand_worked_golden"]),
     ("radius_grows_additively", "R *= c;", "R += 1;",
-     ["pin_workload_semantics"]),
+     ["pin_workload_semantics", "pin_hand_worked_golden"]),
     ("distance_not_squared", "s = s + diff * diff;", "s = s + fabs(diff);",
      ["pin_bruteforce", "pin_v_ge_n_exact"]),
     ("ties_by_larger_id",
      "if (a->dist != b->dist) return a->dist < b->dist ? -1 : 1;\n    if (a->id != b->id) return a->id < b->id ? -1 : 1;",
      "if (a->dist != b->dist) return a->dist < b->dist ? -1 : 1;\n    if (a->id != b->id) return a->id > b->id ? -1 : 1;",
-     ["pin_duplicates_tie_by_id"]),
+     ["pin_duplicates_tie_by_id", "pin_hand_worked_golden"]),
     ("index_not_anchored", "p[j].bid = H[(size_t)j * m + i] - o[i];", "p[j].bid = H[(size_t)j * m + i];",
      ["pin_index_sorted_arrays"]),
     ("eq1_tail_sign", "return 1.0 - two_phi_neg - tail;", "return 1.0 - two_phi_neg + tail;",
@@ -54,3 +62,7 @@ def test_mutant_is_caught(tmp_path, name, old, new, pins):
         if fails:
             caught.append(pname)
     assert caught, f"mutant {name} survived pins {pins}"
+    # the hand-worked case alone pins the stop rule and the truncation order,
+    # independently of the numpy restatement of the level loop
+    if "pin_hand_worked_golden" in pins:
+        assert "pin_hand_worked_golden" in caught, f"the hand-worked case misses {name}"
