@@ -76,6 +76,10 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--queries", type=int, default=0,
                    help="override the workload's query count (smaller cases for profiling)")
+    p.add_argument("--n", type=int, default=0,
+                   help="override the workload's point count (smaller cases for profiling)")
+    p.add_argument("--clusters", type=int, default=0,
+                   help="override the workload's cluster count (with --n)")
     p.add_argument("--batch", type=int, default=0, help="queries per pass (0 = library choice)")
     p.add_argument("--path", choices=["auto", "cluster", "levels", "bitmap"], default="auto",
                    help="execution path of the query loop (identical results)")
@@ -111,6 +115,16 @@ def parse_args(argv=None):
     p.add_argument("--l", type=int, default=-1,
                    help="collision threshold (0 = derived from Eq. 1, -1 = operating point)")
     return p.parse_args(argv)
+
+
+def size_overrides(args) -> dict:
+    """make_workload keyword arguments of --n / --clusters."""
+    kw = {}
+    if args.n:
+        kw["n"] = args.n
+    if args.clusters:
+        kw["n_clusters"] = args.clusters
+    return kw
 
 
 def operating_point(args, spec):
@@ -404,7 +418,7 @@ def run_ours(args):
     # the timed queries and, from a separate stream, the training queries of
     # the start model and the autotuner (same data, cluster pool and noise mix)
     wl = workloads.make_workload(args.workload, seed=args.seed, nq=nq,
-                                 n_train=args.train_queries)
+                                 n_train=args.train_queries, **size_overrides(args))
     s = wl.spec
     if world > 1 and rank > 0:
         # each rank answers its own seeded query workload against the same data
@@ -478,8 +492,12 @@ def run_ours(args):
         counted = index.profile(reset=True)
         prof = None
         if profiled:
+            # the level loop driven from the host, so that every kernel class
+            # (bucket numbers, filter + count, decide, ...) is timed on its own;
+            # the kernels are those of the timed steps
+            pkw = dict(kw, graph=False)
             for _ in range(steps):
-                index.query(Q, s.k, out=(ids, dists), profile=True, **kw)
+                index.query(Q, s.k, out=(ids, dists), profile=True, **pkw)
             torch.cuda.synchronize()
             prof = index.profile(reset=True)
         return ms, max_over_ranks(ms, world), counted, prof
@@ -552,7 +570,10 @@ def run_ours(args):
     recall, ratio = recall_ratio(ids[pick], dists[pick], tids, tdists)
     log(f"quality: recall {recall:.4f}, ratio {ratio:.5f}; end to end {e2e['value']:.1f} q/s")
 
-    # roofline of the dominant kernel and of the candidate-distance kernel
+    # roofline of the dominant kernel and of the candidate-distance kernel;
+    # the L2 read rate (a 64 MiB buffer read with the library's own kernel) is
+    # the ceiling of kernels whose reads hit L2
+    l2_gbs = qw.qw_measure_read_bandwidth(64 << 20, 20)
     peaks, peak_kind = measured_peaks()
     steps = args.steps
     hbm = float(peaks["hbm_gbs"])
@@ -580,8 +601,11 @@ def run_ours(args):
             # level's candidate bitmap and the new one, 4 KiB each
             dom_name = "bm_level_tma_kernel (bit-sliced collision counts, TMA-staged bitmaps)"
             count_bytes = (prof["level_passes"] / steps) * index.info.n_tiles * (s.m + 2) * 4096.0
-    # launches actually run (graph mode counts the device-driven level passes)
-    dom_launches = prof["launches"][dom] / steps
+    # launches actually run; for the two-pass bitmap level a "launch" is one
+    # level pass (its filter and count launches; the bucket numbers of each
+    # pass are timed apart in their own class)
+    two_pass = bitmap and dom == "level" and chosen_kw.get("loads", "tma") == "direct"
+    dom_launches = (prof["timed_launches"]["bucket"] if two_pass else prof["launches"][dom]) / steps
     dom_ms = prof["ms"][dom] / steps
     per_launch_bytes = count_bytes / max(dom_launches, 1)
     per_launch_s = (dom_ms / 1e3) / max(dom_launches, 1)
@@ -611,7 +635,8 @@ def run_ours(args):
                     ncu_traffic(kname, args.workload)), "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": per_launch_bytes,
                 "avg_launch_ms": per_launch_s * 1e3, "launches_per_step": dom_launches,
-                "share_of_step": round(dom_ms / (ms / steps), 4)}
+                "share_of_step": round(dom_ms / (ms / steps), 4),
+                "l2_read_peak": round(l2_gbs, 1), "frac_l2": round(achieved / l2_gbs, 4)}
     roofline_gather = {"kernel": rr_name, "bound": "hbm",
                        "achieved": round(rr_achieved, 1), "peak": hbm,
                        "frac": round(rr_achieved / hbm, 4), "unit": "GB/s",
@@ -619,7 +644,8 @@ def run_ours(args):
                            ncu_traffic("rerank_bf16_kernel" if bf16_rr else "rerank_kernel",
                                        args.workload)),
                        "algorithmic_bytes_per_launch": rr_bytes / max(rr_launches, 1),
-                       "avg_launch_ms": rr_ms / max(rr_launches, 1)}
+                       "avg_launch_ms": rr_ms / max(rr_launches, 1),
+                       "l2_read_peak": round(l2_gbs, 1), "frac_l2": round(rr_achieved / l2_gbs, 4)}
     # kernels launched in the (uninstrumented) timed region
     launches = int(sum(counted["launches"].values()))
 
@@ -643,7 +669,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "n": s.n, "d": s.d, "m": s.m, "w": s.w, "c": s.c,
+        "config": {"workload": args.workload, "n": s.n, "clusters": s.n_clusters, "d": s.d,
+                   "m": s.m, "w": s.w, "c": s.c,
                    "k": s.k, "v": v_used, "l": index.l, "queries_per_gpu": s.nq,
                    "query_clusters": s.query_clusters, "seed": args.seed,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -666,6 +693,7 @@ def run_ours(args):
                   "level_passes_per_step": prof["level_passes"] / steps,
                   "rerank_candidates_per_step": prof["rerank_candidates"] / steps,
                   "bitmap_fallbacks_per_step": prof["bitmap_fallbacks"] / steps,
+                  "bitmap_overflows_per_step": prof["bitmap_overflows"] / steps,
                   "rerank_fp32_rows_per_step": prof["rerank_fp32_rows"] / steps,
                   "entries_scanned_per_query": float(np.mean(st[:, 5])),
                   "kernel_ms_per_step": {k2: round(v2 / steps, 3) for k2, v2 in prof["ms"].items()}},
@@ -689,7 +717,8 @@ def run_reference(args):
 
     import oracle
     import workloads
-    wl = workloads.make_workload(args.workload, seed=args.seed, nq=args.queries or None)
+    wl = workloads.make_workload(args.workload, seed=args.seed, nq=args.queries or None,
+                                 **size_overrides(args))
     s = wl.spec
     v_used, l_arg = operating_point(args, s)
     l = l_arg if l_arg > 0 else oracle.get().threshold(s.m, s.w, s.c, s.n, v_used)

@@ -97,6 +97,9 @@ typedef struct {
                              memory, the paper's external-storage setting.  The bitmap path
                              then reads them with plain loads (QW_LOADS_TMA acts as
                              QW_LOADS_DIRECT).  Same results */
+    uint64_t seed;        /* used only when qw_build_index gets A == NULL and b == NULL: the
+                             projections are then drawn on the host by qw_draw_projections(seed,
+                             m, d, w, ...); read them back with qw_index_get_projections */
 } qw_index_params;
 
 /* Per-workload options.  Zero-initialise; unknown non-zero fields are rejected. */
@@ -195,7 +198,9 @@ typedef struct {
 /* Kernel classes of the query path, for qw_profile. */
 #define QW_K_PROJECT 0   /* query projection + FP64 boundary pass */
 #define QW_K_SETUP 1     /* per-query state */
-#define QW_K_LEVEL 2     /* bucket-range search + collision counting, one launch per level */
+#define QW_K_LEVEL 2     /* bucket-range search + collision counting, one launch per level
+                            (bitmap path with direct loads and a host-driven loop: the
+                            summary filter and the count pass only, see QW_K_BUCKET) */
 #define QW_K_DECIDE 3    /* per-level termination test */
 #define QW_K_SELECT 4    /* candidate selection under the k + v bound */
 #define QW_K_RERANK 5    /* candidate distances + top-k */
@@ -203,7 +208,10 @@ typedef struct {
                             query in one persistent launch */
 #define QW_K_ORDER 7     /* workload ordering: signature sort, gather, scatter of results */
 #define QW_K_START 8     /* learned start levels: features + network forward */
-#define QW_K_COUNT 9
+#define QW_K_BUCKET 9    /* bitmap path, direct loads, host-driven loop: the bitmap numbers of
+                            the query's buckets before each level's filter (in graph mode they
+                            are part of QW_K_LEVEL) */
+#define QW_K_COUNT 10
 
 /* Launch counts and (profile mode) summed kernel times of qw_run_workload /
  * qw_workload_candidates calls on one index since the last reset. */
@@ -218,9 +226,10 @@ typedef struct {
     int64_t start_fallbacks;       /* queries recomputed from R = 1 (always counted) */
     int64_t level_passes;          /* (query, level) pairs counted by the level paths
                                       (profile mode) */
-    int64_t bitmap_fallbacks;      /* QW_PATH_BITMAP queries whose candidates overflowed its
-                                      fixed lists and were answered by the level path
-                                      (always counted; same results) */
+    int64_t bitmap_fallbacks;      /* QW_PATH_BITMAP queries answered by the level path: a
+                                      last level whose kept entries and tie class do not fit
+                                      the candidate list even when rebuilt (always counted;
+                                      same results) */
     int64_t bitmap_live_items;     /* QW_PATH_BITMAP, direct loads: (query, tile, level) items
                                       with a live 128-id group (profile mode) */
     int64_t bitmap_live_groups;    /* ... and live groups counted from the bitmaps */
@@ -229,6 +238,9 @@ typedef struct {
     int64_t l2_setaside_bytes;     /* last call with a window mode: persisting-L2 set-aside used
                                       (0: windows could not be attached) */
     int64_t l2_index_permille;     /* ... and the share of it given to the index window */
+    int64_t bitmap_overflows;      /* QW_PATH_BITMAP queries whose last level held more
+                                      candidates than the list: the list is rebuilt with the
+                                      kept entries and the tie class only (profile mode) */
 } qw_profile;
 
 typedef struct {
@@ -281,8 +293,23 @@ int32_t qw_collision_threshold(int32_t m, float w, int32_t c, int64_t n, int32_t
 qw_status qw_hash(const float *V, int64_t nv, int32_t d, const float *A, const float *b,
                   int32_t m, float w, int32_t *H, int64_t *n_fixups, void *stream);
 
+/* The hash family's random draws (Section 3: a_i ~ N(0, I_d), b_i ~ U[0, w))
+ * from a seed, on the host, the same on every machine.  The generator is
+ * SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) used by counter: draw k is
+ *   z = seed + (k + 1) * 0x9E3779B97F4A7C15 (mod 2^64),
+ *   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9,  z = (z ^ (z >> 27)) * 0x94D049BB133111EB,
+ *   z = z ^ (z >> 31),   u_k = (z >> 11) * 2^-53  in [0, 1).
+ * A (m x d, row-major, HOST) is filled in pairs by the Box-Muller transform:
+ * entries 2j and 2j + 1 are r cos(2 pi u_{2j+1}) and r sin(2 pi u_{2j+1}) with
+ * r = sqrt(-2 ln(1 - u_{2j})), computed in double and rounded to float.
+ * b (m, HOST): b_i = float(u_{k0 + i} w) with k0 = m d rounded up to even,
+ * replaced by the largest float below w if it rounds up to w.
+ * Nothing is written for m < 1, d < 1 or a null pointer. */
+void qw_draw_projections(uint64_t seed, int32_t m, int32_t d, float w, float *A, float *b);
+
 /* Build an index over data (n x d float32) with projections A (m x d float32)
- * and offsets b (m float32), all in `mem` space.  The index keeps its own
+ * and offsets b (m float32), all in `mem` space; A and b both NULL: they are
+ * drawn with qw_draw_projections(params->seed, m, d, w, ...).  The index keeps its own
  * device copies of data, A and b; the caller's buffers may be freed after the
  * call returns (device mode: after the stream has passed the call).
  * Layout built (Section 2: one sorted structure per hash function):
@@ -298,13 +325,25 @@ qw_status qw_build_index(const float *data, int64_t n, int32_t d, const float *A
                          const float *b, const qw_index_params *params, int32_t mem,
                          void *stream, qw_index **out);
 
+/* The index's projections and anchors (Section 3's a_i and b_i, and the
+ * anchors o_i = min over the data of h_i that make every data bucket id
+ * non-negative): A (m x d float32), b (m float32), offsets (m int32), all
+ * HOST pointers, each optional (NULL: not copied).  These are the values the
+ * index hashes with -- the caller's A and b, or the ones drawn from the seed
+ * -- so an independent implementation given them computes the same bucket
+ * ids.  Waits for the device.  Errors: QW_ERR_ARG (null index), QW_ERR_CUDA. */
+qw_status qw_index_get_projections(const qw_index *index, float *A, float *b, int32_t *offsets);
+
 /* Answer a workload of nq queries (nq x d float32) for the k nearest
  * neighbours each (Sections 3.1, 4).  Per query: levels R = 1, c, c^2, ...;
  * C_R = { o : o collides with q on >= l projections at radius R }; stop at the
  * first level with |C_R| >= k + v, or when R exceeds every bucket id of the
  * data and the query; keep at most k + v candidates (those of the previous
  * level first, then more collisions, then smaller id); return the k nearest
- * by exact distance (ties by smaller id).
+ * by exact distance (ties by smaller id).  The optional stopping rule of
+ * collision-counting LSH -- stop once k candidates lie within c R of the
+ * query -- is not supported: a query stops by the k + v bound or the radius
+ * rule only.
  * Outputs: ids (nq x k int64, -1 where fewer than k candidates), dists
  * (nq x k float32, Euclidean distance, +inf where id is -1), stats (optional,
  * nq x QW_NSTAT int64, slots above).  All in `mem` space.
@@ -347,16 +386,20 @@ qw_status qw_workload_candidates(qw_index *index, const float *queries, int64_t 
  *
  * Arguments as qw_run_workload, except that queries, ids, dists and stats
  * (optional) are DEVICE pointers and there are no per-call options.
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it; make that
- * first call before any stream capture.  Every call on a device shares the
+ * Every call looks up the scratch array's device address on the current
+ * device (cudaGetSymbolAddress); the first call on a device also loads the
+ * library's module there, so make that first call before any stream capture.
+ * The index must live on the current device.  Every call on a device shares the
  * same array, so calls whose work overlaps on the GPU (different streams or
  * threads without ordering between them) race and corrupt each other's
  * results: order them on one stream.  The call waits for `stream` once per
  * batch.
- * Errors: as qw_run_workload; QW_ERR_ARG also when one query's working memory
- * (about n + 64 * n_tiles * 33 + 8 * (k + v) bytes) exceeds the static array,
- * i.e. indexes of more than about 64 million points. */
+ * Errors: as qw_run_workload; QW_ERR_ARG also when the index is on another
+ * device, or when one query's working memory exceeds the static array.  One
+ * query needs n_tiles * (32768 + 528) + 12 m + 8 (k + v) bytes (collision
+ * counters, per-tile candidate profiles and plans, bucket ids, candidate
+ * lists) plus about 5.5 KB of block alignment, n_tiles = ceil(n / 32768):
+ * indexes of up to about 65 million points fit. */
 qw_status qw_run_workload_noalloc(qw_index *index, const float *queries, int64_t nq, int32_t k,
                                   int64_t *ids, float *dists, int64_t *stats, void *stream);
 
@@ -377,6 +420,17 @@ qw_status qw_run_workload_noalloc(qw_index *index, const float *queries, int64_t
  * non-finite values, setaside == 0). */
 int32_t qw_l2_split_model(double setaside, double index_bytes, double index_reads,
                           double data_bytes, double data_reads);
+
+/* Read bandwidth of a device buffer of `bytes` bytes (a measuring tool; the
+ * paper has no counterpart): the library allocates the buffer, reads all of it
+ * `reps` + 1 times with 16-byte loads cached in L2 only, one launch per read,
+ * and writes the best rate of the timed `reps` reads (CUDA events on
+ * `stream`) to *gbs in GB/s.  A buffer well below the L2 size (126 MB usable
+ * on GB300) gives the rate L2 delivers to the SMs -- the ceiling of kernels
+ * whose reads hit L2 -- and one well above it the HBM rate.  Waits for the
+ * stream.  Errors: QW_ERR_ARG (bytes < 16, reps < 1, null gbs), QW_ERR_OOM,
+ * QW_ERR_CUDA. */
+qw_status qw_measure_read_bandwidth(int64_t bytes, int32_t reps, double *gbs, void *stream);
 
 /* Copy the index's profile counters into *out (host); reset them afterwards
  * when `reset` is non-zero. */

@@ -36,13 +36,14 @@ EXPORTED = ("qw_version", "qw_last_error", "qw_collision_probability",
             "qw_index_get_info", "qw_mlp_create", "qw_mlp_param_count", "qw_mlp_set_params",
             "qw_mlp_get_params", "qw_mlp_loss_grad", "qw_mlp_train", "qw_mlp_predict",
             "qw_mlp_free", "qw_query_features", "qw_index_set_start_model", "qw_autotune",
-            "qw_index_export", "qw_index_free", "qw_l2_split_model", "qw_mlp_predict_tc")
+            "qw_index_export", "qw_index_free", "qw_l2_split_model", "qw_mlp_predict_tc",
+            "qw_draw_projections", "qw_index_get_projections", "qw_measure_read_bandwidth")
 
 
 class qw_index_params(C.Structure):
     _fields_ = [("m", C.c_int32), ("w", C.c_float), ("c", C.c_int32), ("v", C.c_int32),
                 ("l", C.c_int32), ("delta", C.c_float), ("shadow_bf16", C.c_int32),
-                ("bitmaps", C.c_int32), ("host_bitmaps", C.c_int32)]
+                ("bitmaps", C.c_int32), ("host_bitmaps", C.c_int32), ("seed", C.c_uint64)]
 
 
 class qw_query_params(C.Structure):
@@ -74,10 +75,10 @@ QW_LOADS_TMA, QW_LOADS_DIRECT = 0, 1
 LOADS = {"tma": QW_LOADS_TMA, "direct": QW_LOADS_DIRECT}
 QW_L2_OFF, QW_L2_SPLIT, QW_L2_MODEL = 0, 1, 2
 (QW_K_PROJECT, QW_K_SETUP, QW_K_LEVEL, QW_K_DECIDE, QW_K_SELECT, QW_K_RERANK, QW_K_CLUSTER,
- QW_K_ORDER, QW_K_START) = range(9)
-QW_K_COUNT = 9
+ QW_K_ORDER, QW_K_START, QW_K_BUCKET) = range(10)
+QW_K_COUNT = 10
 KERNEL_CLASSES = ("project", "setup", "level", "decide", "select", "rerank", "cluster", "order",
-                  "start")
+                  "start", "bucket")
 
 
 class qw_profile(C.Structure):
@@ -88,7 +89,7 @@ class qw_profile(C.Structure):
                 ("level_passes", C.c_int64), ("bitmap_fallbacks", C.c_int64),
                 ("bitmap_live_items", C.c_int64), ("bitmap_live_groups", C.c_int64),
                 ("bitmap_live_words", C.c_int64), ("l2_setaside_bytes", C.c_int64),
-                ("l2_index_permille", C.c_int64)]
+                ("l2_index_permille", C.c_int64), ("bitmap_overflows", C.c_int64)]
 
 
 class qw_index_info(C.Structure):
@@ -177,6 +178,12 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.qw_index_export.argtypes = [vp, vp, vp, vp, vp, vp]
     L.qw_index_free.restype = None
     L.qw_index_free.argtypes = [vp]
+    L.qw_draw_projections.restype = None
+    L.qw_draw_projections.argtypes = [C.c_uint64, C.c_int32, C.c_int32, C.c_float, vp, vp]
+    L.qw_index_get_projections.restype = C.c_int32
+    L.qw_index_get_projections.argtypes = [vp, vp, vp, vp]
+    L.qw_measure_read_bandwidth.restype = C.c_int32
+    L.qw_measure_read_bandwidth.argtypes = [C.c_int64, C.c_int32, C.POINTER(C.c_double), vp]
     L.qw_l2_split_model.restype = C.c_int32
     L.qw_l2_split_model.argtypes = [C.c_double] * 5
     if path is None:
@@ -275,6 +282,34 @@ def qw_index_export(index: int, o: int, span: int, entry_bid: int, entry_id: int
                                   entry_id or None, stream or None))
 
 
+def qw_draw_projections(seed: int, m: int, d: int, w: float):
+    """The hash family's draws from a seed (host): returns numpy (A m x d, b m)
+    float32."""
+    import numpy as np
+    A = np.empty((m, d), np.float32)
+    b = np.empty(m, np.float32)
+    load().qw_draw_projections(int(seed), int(m), int(d), float(w), A.ctypes.data, b.ctypes.data)
+    return A, b
+
+
+def qw_index_get_projections(index: int, m: int, d: int):
+    """(A m x d, b m, offsets m) of an index as numpy arrays."""
+    import numpy as np
+    A = np.empty((m, d), np.float32)
+    b = np.empty(m, np.float32)
+    o = np.empty(m, np.int32)
+    _check(load().qw_index_get_projections(index, A.ctypes.data, b.ctypes.data, o.ctypes.data))
+    return A, b, o
+
+
+def qw_measure_read_bandwidth(nbytes: int, reps: int = 20, stream: int = 0) -> float:
+    """Best read rate (GB/s) of a device buffer of nbytes (L2 below its size,
+    HBM above)."""
+    g = C.c_double(0.0)
+    _check(load().qw_measure_read_bandwidth(int(nbytes), int(reps), C.byref(g), stream or None))
+    return float(g.value)
+
+
 def qw_index_free(index: int):
     if index:
         load().qw_index_free(index)
@@ -340,20 +375,29 @@ class Index:
     passed in so callers control the seed.  ``l = 0`` derives the collision
     threshold from Eq. 1 (see ``qw_collision_threshold``)."""
 
-    def __init__(self, data, A, b, *, w: float, c: int = 2, v: int = 100, l: int = 0,
+    def __init__(self, data, A=None, b=None, *, w: float, c: int = 2, v: int = 100, l: int = 0,
                  delta: float = 0.0, shadow_bf16: bool = False, bitmaps: bool = False,
-                 host_bitmaps: bool = False):
-        _f32(data, "data"), _f32(A, "A"), _f32(b, "b")
-        mem = _mem_of(data, A, b)
+                 host_bitmaps: bool = False, m: int = 0, seed: int = 0):
+        _f32(data, "data")
         n, d = data.shape
-        m, d2 = A.shape
-        if d2 != d or b.shape != (m,):
-            raise ValueError("shape mismatch between data, A and b")
+        if A is None and b is None:
+            # drawn by the library from the seed (qw_draw_projections)
+            if m < 1:
+                raise ValueError("give A and b, or m (and seed) to draw them")
+            mem = _mem_of(data)
+            a_ptr = b_ptr = 0
+        else:
+            _f32(A, "A"), _f32(b, "b")
+            mem = _mem_of(data, A, b)
+            m, d2 = A.shape
+            if d2 != d or b.shape != (m,):
+                raise ValueError("shape mismatch between data, A and b")
+            a_ptr, b_ptr = A.data_ptr(), b.data_ptr()
         p = qw_index_params(m=m, w=float(w), c=int(c), v=int(v), l=int(l), delta=float(delta),
                             shadow_bf16=1 if shadow_bf16 else 0, bitmaps=1 if bitmaps else 0,
-                            host_bitmaps=1 if host_bitmaps else 0)
+                            host_bitmaps=1 if host_bitmaps else 0, seed=int(seed))
         self._h = 0
-        self._h = qw_build_index(data.data_ptr(), n, d, A.data_ptr(), b.data_ptr(), p, mem,
+        self._h = qw_build_index(data.data_ptr(), n, d, a_ptr or None, b_ptr or None, p, mem,
                                  _stream_of(data))
         self.n, self.d, self.m = n, d, m
         self.info = qw_index_get_info(self._h)
@@ -387,7 +431,8 @@ class Index:
                 "bitmap_live_groups": int(p.bitmap_live_groups),
                 "bitmap_live_words": int(p.bitmap_live_words),
                 "l2_setaside_bytes": int(p.l2_setaside_bytes),
-                "l2_index_permille": int(p.l2_index_permille)}
+                "l2_index_permille": int(p.l2_index_permille),
+                "bitmap_overflows": int(p.bitmap_overflows)}
 
     def query(self, Q, k: int, *, batch: int = 0, stats: bool = False, out=None,
               profile: bool = False, path: str = "auto", clusters: int = 0,
@@ -465,6 +510,11 @@ class Index:
                                   C.byref(best), C.byref(rep), _stream_of(Q) or None))
         trials = [(_params_kwargs(rep.params[i]), float(rep.ms[i])) for i in range(rep.tried)]
         return _params_kwargs(best), trials
+
+    def projections(self):
+        """(A m x d, b m, offsets m) numpy copies: the projections the index
+        hashes with and its anchors."""
+        return qw_index_get_projections(self._h, self.m, self.d)
 
     def export(self):
         """Host numpy copies: o (m), span (m), entry_bid and entry_id (m x n),

@@ -297,18 +297,20 @@ qw_status qw_hash(const float *V, int64_t nv, int32_t d, const float *A, const f
 }
 
 static qw_status build_impl(qw_index *ix, const float *data, const float *A, const float *b,
-                            int32_t mem, cudaStream_t s)
+                            int32_t mem, int32_t ab_mem, cudaStream_t s)
 {
     const int64_t n = ix->n;
     const int d = ix->d, m = ix->m;
     const cudaMemcpyKind kind = mem == QW_MEM_HOST ? cudaMemcpyHostToDevice
                                                    : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind ab_kind = ab_mem == QW_MEM_HOST ? cudaMemcpyHostToDevice
+                                                         : cudaMemcpyDeviceToDevice;
     QW_TRY(ix->X.ensure((size_t)n * d * sizeof(float)));
     QW_TRY(ix->A.ensure((size_t)m * d * sizeof(float)));
     QW_TRY(ix->b.ensure((size_t)m * sizeof(float)));
     QW_CUDA_TRY(cudaMemcpyAsync(ix->X.p, data, (size_t)n * d * sizeof(float), kind, s));
-    QW_CUDA_TRY(cudaMemcpyAsync(ix->A.p, A, (size_t)m * d * sizeof(float), kind, s));
-    QW_CUDA_TRY(cudaMemcpyAsync(ix->b.p, b, (size_t)m * sizeof(float), kind, s));
+    QW_CUDA_TRY(cudaMemcpyAsync(ix->A.p, A, (size_t)m * d * sizeof(float), ab_kind, s));
+    QW_CUDA_TRY(cudaMemcpyAsync(ix->b.p, b, (size_t)m * sizeof(float), ab_kind, s));
 
     // 1. bucket ids of the data, projection-major (m x n)
     DevBuf Ht, scratch;
@@ -496,7 +498,9 @@ qw_status qw_build_index(const float *data, int64_t n, int32_t d, const float *A
     clear_error();
     if (!out) return arg_error("qw_build_index: out is null");
     *out = nullptr;
-    if (!data || !A || !b || !p) return arg_error("qw_build_index: null pointer");
+    if (!data || !p) return arg_error("qw_build_index: null pointer");
+    if ((A == nullptr) != (b == nullptr))
+        return arg_error("qw_build_index: give both A and b, or neither (drawn from params->seed)");
     if (mem != QW_MEM_DEVICE && mem != QW_MEM_HOST) return arg_error("qw_build_index: bad mem flag");
     if (n < 1 || n > 2147483647LL) return arg_error("qw_build_index: n must be in [1, 2^31)");
     if (d < 1) return arg_error("qw_build_index: d must be >= 1");
@@ -527,7 +531,19 @@ qw_status qw_build_index(const float *data, int64_t n, int32_t d, const float *A
     ix->shadow = p->shadow_bf16 != 0;
     ix->bitmaps = p->bitmaps != 0;
     ix->host_bitmaps = ix->bitmaps && p->host_bitmaps != 0;
-    qw_status st = build_impl(ix, data, A, b, mem, (cudaStream_t)stream);
+    // no projections given: draw them on the host from the seed (Section 3's
+    // a ~ N(0, I_d), b ~ U[0, w); see qw_draw_projections)
+    std::vector<float> drawn_A, drawn_b;
+    int32_t ab_mem = mem;
+    if (!A) {
+        drawn_A.resize((size_t)p->m * d);
+        drawn_b.resize((size_t)p->m);
+        qw_draw_projections(p->seed, p->m, d, p->w, drawn_A.data(), drawn_b.data());
+        A = drawn_A.data();
+        b = drawn_b.data();
+        ab_mem = QW_MEM_HOST;
+    }
+    qw_status st = build_impl(ix, data, A, b, mem, ab_mem, (cudaStream_t)stream);
     if (st != QW_OK) {
         qw_index_free(ix);
         return st;
@@ -615,10 +631,24 @@ static qw_status host_level_loop(qw_index *ix, LaunchTimer &tm, const IndexView 
     for (int pass = 0; pass < 2; ++pass) {
         int64_t R = 1, Rp = 1;
         for (int level = 0;; ++level) {
-            QW_TRY(tm.run(QW_K_LEVEL, 1, [&] {
-                return bitmap ? launch_bm_level(view, nb, level, R, Rp, ix->l, ix->c, st, err, tma, s)
-                              : launch_level(view, nb, level, R, Rp, ix->l, ix->c, st, s);
-            }));
+            if (bitmap && !tma) {
+                // the bucket numbers apart, so that QW_K_LEVEL times the filter
+                // and count passes alone
+                QW_TRY(tm.run(QW_K_BUCKET, 1, [&] {
+                    return launch_bm_level(view, nb, level, R, Rp, ix->l, ix->c, st, err, tma, s,
+                                           nullptr, 1);
+                }));
+                QW_TRY(tm.run(QW_K_LEVEL, st.bm_prof ? 3 : 2, [&] {
+                    return launch_bm_level(view, nb, level, R, Rp, ix->l, ix->c, st, err, tma, s,
+                                           nullptr, 2);
+                }));
+            } else {
+                QW_TRY(tm.run(QW_K_LEVEL, 1, [&] {
+                    return bitmap ? launch_bm_level(view, nb, level, R, Rp, ix->l, ix->c, st, err,
+                                                    tma, s)
+                                  : launch_level(view, nb, level, R, Rp, ix->l, ix->c, st, s);
+                }));
+            }
             QW_TRY(tm.run(QW_K_DECIDE, 1, [&] {
                 ScanStats ss = bitmap ? scan_stats_of(view, ix->c) : ScanStats();
                 ss.recount_first = bitmap && learned;
@@ -762,7 +792,11 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     if (use_bitmap) {
         QW_TRY(ix->w_cbits.ensure((size_t)B * cb_bytes));
         QW_TRY(ix->w_clist.ensure((size_t)B * cl_bytes + 64));
-        QW_TRY(ix->w_bmsel.ensure((size_t)B * (2 + kEqCap) * sizeof(int32_t)));
+        // per query: flags, recount mark, tie list; then the list-rebuild
+        // slots (count, plans, count histograms)
+        QW_TRY(ix->w_bmsel.ensure((size_t)B * (2 + kEqCap) * sizeof(int32_t) + 16 +
+                                  (size_t)B * sizeof(RdPlan) +
+                                  (size_t)B * kHistBins * sizeof(int32_t)));
         // two-pass level: one slot per (query, tile), one work entry per group
         const size_t items = (size_t)B * ix->nT;
         QW_TRY(ix->w_bmwork.ensure(bm_work_layout(B, ix->nT, m, nullptr)));
@@ -862,6 +896,9 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         st.bm_ovf = ix->w_bmsel.as<int32_t>();
         st.recount = st.bm_ovf + B;
         st.eqbuf = st.bm_ovf + 2 * B;
+        st.rd_n = st.eqbuf + (size_t)B * kEqCap;
+        st.rd_plan = reinterpret_cast<RdPlan *>(st.rd_n + 4);
+        st.rd_hist = reinterpret_cast<int32_t *>(st.rd_plan + B);
         const int64_t items = B * (int64_t)ix->nT;
         bm_work_layout(B, ix->nT, m, &st, ix->w_bmwork.as<char>());
         st.bm_item_cap = (int32_t)std::min<int64_t>(items, (int64_t)1 << 23);
@@ -1019,6 +1056,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                     return launch_start_model(ix->start_model, Qb, HQb, nb, view, ix->xs,
                                               ix->start_eps, use_bitmap ? 0 : 1, st.start, s);
                 }));
+                QW_TRY(tm.run(QW_K_START, 1, [&] { return launch_clamp_start(nb, st, ix->c, s); }));
                 QW_CUDA_TRY(cudaMemsetAsync(st.fb_count, 0, 16, s));
             }
             if (graph) {
@@ -1031,7 +1069,9 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                 QW_TRY(host_level_loop(ix, tm, view, nb, cap, learned, use_bitmap, tma_loads, err,
                                        st, s, &levels_run));
             }
-            QW_TRY(tm.run(QW_K_SELECT, use_bitmap ? (learned ? 2 : 1) : 2, [&] {
+            QW_TRY(tm.run(QW_K_SELECT, use_bitmap ? (learned ? 9 : 8) : 2, [&] {
+                if (use_bitmap)
+                    QW_TRY(launch_bm_reduce(view, nb, ix->l, cap, ix->c, st, tma_loads, s));
                 if (use_bitmap && learned)
                     QW_TRY(launch_bm_recount(view, nb, ix->l, cap, ix->c, st, s));
                 return use_bitmap ? launch_bm_collect(view, nb, ix->l, cap, st, stats_b, want_cand, s)
@@ -1040,6 +1080,12 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             if (use_bitmap)
                 QW_TRY(launch_bm_overflow_list(st, nb, order ? perm : nullptr, b0, ovf_list,
                                                late_list, ovf_count, s));
+            if (use_bitmap && tm.on) {
+                int32_t h_rd = 0;
+                QW_CUDA_TRY(cudaMemcpyAsync(&h_rd, st.rd_n, sizeof(h_rd), cudaMemcpyDeviceToHost, s));
+                QW_CUDA_TRY(cudaStreamSynchronize(s));
+                ix->prof.bitmap_overflows += h_rd;
+            }
         }
         if (want_cand)
             QW_TRY(tm.run(QW_K_SELECT, 1, [&] { return launch_candidates_out(st, nb, cap, cids_b, ccol_b, s); }));
@@ -1092,7 +1138,9 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             set_error("qw_run_workload: a staged-copy wait in the bitmap kernel gave up");
             return QW_ERR_TIMEOUT;
         }
-        ix->prof.launches[QW_K_LEVEL] += (int64_t)h_ctl.iters;
+        // per level: the bucket numbers, filter and count (bitmap path, direct
+        // loads), else one counting launch
+        ix->prof.launches[QW_K_LEVEL] += (int64_t)h_ctl.iters * (use_bitmap && !tma_loads ? 3 : 1);
         levels_run = (int)h_ctl.iters;
         ix->prof.launches[QW_K_DECIDE] += 2 * (int64_t)h_ctl.iters + n_batches * (learned ? 3 : 1);
         if (learned) {
@@ -1482,6 +1530,60 @@ qw_status qw_index_get_info(const qw_index *ix, qw_index_info *info)
     info->device_bytes = ix->device_bytes;
     info->bitmap_bytes = (int64_t)(ix->host_bitmaps ? ix->bm_host.bytes : ix->bm.bytes);
     info->host_bytes = (int64_t)ix->bm_host.bytes;
+    return QW_OK;
+}
+
+// SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014) used as a counter-based generator: the value of
+// counter k under `seed` is the mixing function applied to
+// seed + (k + 1) * 0x9E3779B97F4A7C15.
+static uint64_t splitmix64_at(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Uniform double in [0, 1) from the top 53 bits.
+static double uniform_at(uint64_t seed, uint64_t k)
+{
+    return (double)(splitmix64_at(seed, k) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+void qw_draw_projections(uint64_t seed, int32_t m, int32_t d, float w, float *A, float *b)
+{
+    if (m < 1 || d < 1 || !A || !b) return;
+    const uint64_t na = (uint64_t)m * (uint64_t)d;
+    const double two_pi = 6.283185307179586476925286766559;
+    // entries of A in row-major order, two per Box-Muller pair: entry e uses
+    // the uniforms of counters 2 (e / 2) and 2 (e / 2) + 1
+    for (uint64_t e = 0; e < na; e += 2) {
+        const double u1 = uniform_at(seed, e);
+        const double u2 = uniform_at(seed, e + 1);
+        const double r = sqrt(-2.0 * log(1.0 - u1));
+        const double t = two_pi * u2;
+        A[e] = (float)(r * cos(t));
+        if (e + 1 < na) A[e + 1] = (float)(r * sin(t));
+    }
+    // offsets from the counters after A's: b_i = u w, kept below w in float
+    const uint64_t k0 = (na + 1) / 2 * 2;
+    for (int32_t i = 0; i < m; ++i) {
+        float bi = (float)(uniform_at(seed, k0 + (uint64_t)i) * (double)w);
+        if (!(bi < w)) bi = nextafterf(w, 0.0f);
+        b[i] = bi;
+    }
+}
+
+qw_status qw_index_get_projections(const qw_index *ix, float *A, float *b, int32_t *offsets)
+{
+    clear_error();
+    if (!ix) return arg_error("qw_index_get_projections: index is null");
+    const int m = ix->m, d = ix->d;
+    if (A) QW_CUDA_TRY(cudaMemcpy(A, ix->A.p, (size_t)m * d * sizeof(float), cudaMemcpyDeviceToHost));
+    if (b) QW_CUDA_TRY(cudaMemcpy(b, ix->b.p, (size_t)m * sizeof(float), cudaMemcpyDeviceToHost));
+    if (offsets)
+        QW_CUDA_TRY(cudaMemcpy(offsets, ix->o.p, (size_t)m * sizeof(int32_t), cudaMemcpyDeviceToHost));
     return QW_OK;
 }
 

@@ -858,7 +858,8 @@ __global__ void __launch_bounds__(SEL_THREADS) bm_select_kernel(IndexView ix, in
     int32_t *cand = st.cand + (int64_t)q * cap;
     int32_t *col = st.cand_col + (int64_t)q * cap;
     int32_t *eq = st.eqbuf + (int64_t)q * kEqCap;
-    const bool ovf_list = n > kQCap || n != nc;
+    // a rebuilt list (flag 4) holds only the kept entries and the tie class
+    const bool ovf_list = n > kQCap || (n != nc && !(st.bm_ovf[q] & 4));
     const int nl = ovf_list ? 0 : n;
     if (threadIdx.x == 0) {
         s_np = 0;
@@ -1030,6 +1031,295 @@ __global__ void __launch_bounds__(SEL_THREADS) bm_select_kernel(IndexView ix, in
     }
 }
 
+// ---- a last level that overflows the candidate list
+//
+// The count kernels list every candidate of a level, up to kQCap per query.
+// When one doubling of the radius sweeps whole clusters into a query's last
+// level, that level can hold more.  Of them the k + v bound keeps only the
+// previous level's candidates, every candidate whose count is above the
+// boundary count c*, and the smallest original ids of the tie class at c*
+// (Section 3.1, readings R4/R5).  These kernels rebuild the list of such a
+// query with only those entries, from the candidate words of its last level
+// (still in place: a stopped query's tiles are not touched by later levels)
+// and the level bitmaps:
+//   pass 0  per candidate: its count, recounted from the m bitmap words of
+//           its 128-id group, and whether it was a candidate at the previous
+//           level (that level's candidate word, or, at a learned first level,
+//           its count there from the bitmaps of that level); the histogram
+//           of the counts of the others, and how many previous ones;
+//   plan 0  c* and how many ids at c* are kept, as the selection computes
+//           them; if the whole tie class does not fit the list,
+//   pass 1  a histogram of the tie class's original ids in kRdBins bins;
+//   plan 1  the bin holding the take-th smallest of them: the tie class is
+//           listed up to that bin (at most take + one bin of ids);
+//   pass 2  the kept entries, written as the count kernels write them;
+//   plan 2  the list's length.
+// The selection then runs on the rebuilt list as on any other, with the same
+// result as from the whole list.  A query whose rebuilt list would still
+// overflow keeps the level-path answer.
+constexpr int kRdBins = 4096;
+constexpr int RD_THREADS = kBmUint4;  // one thread per 128-id group of a tile
+static_assert(kRdBins <= kEqCap, "tie-class id bins share the tie list");
+
+__global__ void bm_rd_compact_kernel(QueryState st, int nb, RdPlan *plan, int32_t *rd_n,
+                                     int32_t *hist)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nb) return;
+    const int L = st.levels[q] - 1;
+    if (L < 0 || st.qbuf_n[(int64_t)(L & 1) * st.qbn_par + q] <= kQCap) return;
+    const int slot = atomicAdd(rd_n, 1);
+    RdPlan p;
+    p.q = q;
+    p.np = 0;
+    p.cstar = 0;
+    p.take = 0;
+    p.mode = 1;
+    p.bound = kRdBins - 1;
+    p.pos = 0;
+    p.pad = 0;
+    plan[slot] = p;
+    for (int c = 0; c < kHistBins; ++c) hist[(int64_t)slot * kHistBins + c] = 0;
+}
+
+// Bit planes of one 128-id group's counts from the bitmaps bn[i] (-1: the
+// bucket holds no data) whose summaries sm[i] touch the group.
+__device__ __forceinline__ void group_planes(const IndexView &ix, const int64_t *bn,
+                                             const uint32_t (*sm)[kSumWords], int m, int g,
+                                             Planes &P)
+{
+#pragma unroll
+    for (int kk = 0; kk < 7; ++kk)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) P.s[kk][w] = 0;
+    for (int i0 = 0; i0 < m; i0 += 8) {
+        uint4 x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u;
+            const bool touch = i < m && ((sm[i][g >> 5] >> (g & 31)) & 1u);
+            x[u] = touch ? __ldg(ix.bm + bn[i] * kBmUint4 + g) : make_uint4(0, 0, 0, 0);
+        }
+        add8(P, x);
+    }
+}
+
+// Bits of word w whose count equals c.
+__device__ __forceinline__ uint32_t count_eq_planes(const Planes &P, int w, int c)
+{
+    uint32_t eq = 0xffffffffu;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) eq &= ((c >> k) & 1) ? P.s[k][w] : ~P.s[k][w];
+    return eq;
+}
+
+// The histogram is cumulative: hist[c] = candidates not of the previous level
+// whose count is >= c (c = l .. m), summed from the bit planes without a
+// per-candidate loop.
+template <int PASS>
+__global__ void __launch_bounds__(RD_THREADS) bm_rd_pass_kernel(IndexView ix, int l, int cgrow,
+                                                                QueryState st, RdPlan *plan,
+                                                                const int32_t *rd_n,
+                                                                int32_t *hist, bool tma)
+{
+    __shared__ int64_t bnL[QW_MAX_M], bnP[QW_MAX_M];
+    __shared__ uint32_t smL[QW_MAX_M][kSumWords], smP[QW_MAX_M][kSumWords];
+    __shared__ int sh_hist[kHistBins];
+    __shared__ int sh_np;
+    const int m = ix.m, nT = ix.nT;
+    const int nslot = *rd_n;
+    const int g = threadIdx.x, lane = threadIdx.x & 31;
+    const int64_t binw = (ix.n + kRdBins - 1) / kRdBins;
+    for (int64_t it = blockIdx.x; it < (int64_t)nslot * nT; it += gridDim.x) {
+        const int slot = (int)(it / nT), t = (int)(it % nT);
+        const RdPlan pl = plan[slot];
+        if (pl.mode == 0 || (PASS == 1 && pl.mode != 2)) continue;
+        const int q = pl.q;
+        const int L = st.levels[q] - 1;
+        const int64_t qt = (int64_t)q * nT + t;
+        const int64_t pcur = (int64_t)(L & 1) * st.cln_par + qt;
+        if (st.clist_n[pcur] == 0) continue;  // no candidate in this tile
+        const int64_t R = st.finalR[q];
+        // the previous level: its candidate words if this query counted it,
+        // else (learned first level L > 0) recounted from its bitmaps
+        const bool prev_words = L - 1 >= st.start[q];
+        const bool prev_recount = !prev_words && L > 0;
+        for (int e = threadIdx.x; e < m * (kSumWords + 1); e += RD_THREADS) {
+            const int i = e / (kSumWords + 1), w = e % (kSumWords + 1);
+            const int64_t gi = st.g[(int64_t)q * m + i];
+            const int64_t b1 = bm_index(ix, i, t, L, R, floordiv64(gi, R));
+            const int64_t b2 = prev_recount
+                                   ? bm_index(ix, i, t, L - 1, R / cgrow, floordiv64(gi, R / cgrow))
+                                   : -1;
+            if (w == kSumWords) {
+                bnL[i] = b1;
+                bnP[i] = b2;
+            } else {
+                smL[i][w] = b1 >= 0 ? ix.bm_sum[b1 * kSumWords + w] : 0u;
+                smP[i][w] = b2 >= 0 ? ix.bm_sum[b2 * kSumWords + w] : 0u;
+            }
+        }
+        if (PASS == 0) {
+            for (int c = threadIdx.x; c < kHistBins; c += RD_THREADS) sh_hist[c] = 0;
+            if (threadIdx.x == 0) sh_np = 0;
+        }
+        __syncthreads();
+        const bool live = tma || ((st.bm_amask[pcur * kSumWords + (g >> 5)] >> (g & 31)) & 1u);
+        const uint4 cw = live ? st.cbits[(int64_t)(L & 1) * st.cb_par + qt * kBmUint4 + g]
+                              : make_uint4(0, 0, 0, 0);
+        const bool any = (cw.x | cw.y | cw.z | cw.w) != 0u;
+        uint4 pw = make_uint4(0, 0, 0, 0);
+        Planes P;
+        if (any) {
+            if (prev_words) {
+                const int64_t pp = (int64_t)((L - 1) & 1) * st.cln_par + qt;
+                const bool pv = st.clist_n[pp] > 0 &&
+                                (tma || ((st.bm_amask[pp * kSumWords + (g >> 5)] >> (g & 31)) & 1u));
+                if (pv) pw = st.cbits[(int64_t)((L - 1) & 1) * st.cb_par + qt * kBmUint4 + g];
+            } else if (prev_recount) {
+                group_planes(ix, bnP, smP, m, g, P);
+                pw = candidates_of(P, l);
+            }
+            group_planes(ix, bnL, smL, m, g, P);
+        }
+        if (PASS == 0) {
+            int my_np = 0;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) my_np += __popc(word_of(cw, w) & word_of(pw, w));
+            my_np = __reduce_add_sync(0xffffffffu, my_np);
+            if (lane == 0 && my_np) atomicAdd(&sh_np, my_np);
+            // cumulative counts from m down to l (the warp's threads agree on c)
+            for (int c = m; c >= l; --c) {
+                int nge = 0;
+                if (any) {
+#pragma unroll
+                    for (int w = 0; w < 4; ++w)
+                        nge += __popc(count_ge_planes(P, w, c) & word_of(cw, w) & ~word_of(pw, w));
+                }
+                nge = __reduce_add_sync(0xffffffffu, nge);
+                if (lane == 0 && nge) atomicAdd(&sh_hist[c], nge);
+            }
+        } else if (any) {
+            // PASS 1: id bins of the tie class; PASS 2: the kept entries
+            uint4 keep;
+            int my_n = 0;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const uint32_t c_w = word_of(cw, w), p_w = word_of(pw, w);
+                const uint32_t oth = c_w & ~p_w;
+                const uint32_t above = pl.cstar < m ? count_ge_planes(P, w, pl.cstar + 1) & oth : 0u;
+                const uint32_t tie = count_eq_planes(P, w, pl.cstar) & oth;
+                uint32_t kw = (c_w & p_w) | above;
+                if (pl.mode == 1) {
+                    kw |= tie;
+                } else {
+                    uint32_t x = tie;
+                    while (x) {
+                        const int b = __ffs(x) - 1;
+                        x &= x - 1;
+                        const int64_t iid = (int64_t)t * kTile + (int64_t)g * 128 + w * 32 + b;
+                        const int bin = (int)((int64_t)ix.perm[iid] / binw);
+                        if (PASS == 1) atomicAdd(st.eqbuf + (int64_t)q * kEqCap + bin, 1);
+                        else if (bin <= pl.bound) kw |= 1u << b;
+                    }
+                }
+                if (w == 0) keep.x = kw;
+                else if (w == 1) keep.y = kw;
+                else if (w == 2) keep.z = kw;
+                else keep.w = kw;
+                my_n += __popc(kw);
+            }
+            if (PASS == 2 && my_n) {
+                uint64_t *E = st.qbuf + (int64_t)(L & 1) * st.qb_par + (int64_t)q * kQCap;
+                int pos = atomicAdd(&plan[slot].pos, my_n);
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    uint32_t x = word_of(keep, w);
+                    const uint32_t p_w = word_of(pw, w);
+                    while (x) {
+                        const int b = __ffs(x) - 1;
+                        x &= x - 1;
+                        const int64_t iid = (int64_t)t * kTile + (int64_t)g * 128 + w * 32 + b;
+                        if (pos < kQCap)
+                            E[pos] = ((uint64_t)iid << 32) | ((uint64_t)((p_w >> b) & 1u) << 8) |
+                                     (uint64_t)count_of(P, w, b);
+                        ++pos;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (PASS == 0) {
+            for (int c = threadIdx.x; c < kHistBins; c += RD_THREADS)
+                if (sh_hist[c]) atomicAdd(hist + (int64_t)slot * kHistBins + c, sh_hist[c]);
+            if (threadIdx.x == 0 && sh_np) atomicAdd(&plan[slot].np, sh_np);
+        }
+        __syncthreads();  // shared arrays are rewritten by the next item
+    }
+}
+
+__global__ void bm_rd_plan_kernel(int l, int m, int cap, int cgrow, QueryState st, RdPlan *plan,
+                                  const int32_t *rd_n, const int32_t *hist, int stage)
+{
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= *rd_n) return;
+    RdPlan p = plan[slot];
+    if (p.mode == 0) return;
+    const int q = p.q;
+    const int L = st.levels[q] - 1;
+    if (stage == 0) {
+        if (st.recount[q] && (st.finalR[q] / cgrow > st.top[q] || p.np >= cap)) {
+            // a learned first level after the level where the plain path stops:
+            // answered again from level 0
+            atomicOr(st.bm_ovf + q, 2);
+            p.mode = 0;
+        } else {
+            // cumulative: h[c] = candidates not of the previous level with count >= c
+            const int32_t *h = hist + (int64_t)slot * kHistBins;
+            const int need = cap - p.np;
+            int cstar = -1;
+            for (int c = m; c >= l; --c) {
+                if (h[c] >= need) {
+                    cstar = c;
+                    break;
+                }
+            }
+            if (cstar < 0) {
+                p.mode = 0;  // fewer candidates than the bound: cannot overflow
+            } else {
+                const int above = cstar < m ? h[cstar + 1] : 0;
+                p.cstar = cstar;
+                p.take = need - above;
+                if ((int64_t)p.np + h[cstar] <= kQCap) {
+                    p.mode = 1;
+                } else {
+                    p.mode = 2;
+                    for (int b = 0; b < kRdBins; ++b) st.eqbuf[(int64_t)q * kEqCap + b] = 0;
+                }
+            }
+        }
+    } else if (stage == 1) {
+        if (p.mode == 2) {
+            const int32_t *ih = st.eqbuf + (int64_t)q * kEqCap;
+            int acc = 0, b = 0;
+            for (; b < kRdBins - 1; ++b) {
+                acc += ih[b];
+                if (acc >= p.take) break;
+            }
+            p.bound = b;
+        }
+    } else {
+        // the rebuilt list (more than kQCap entries: the level path answers)
+        st.qbuf_n[(int64_t)(L & 1) * st.qbn_par + q] = p.pos;
+        st.bm_ovf[q] |= 4;
+        if (st.recount[q]) {
+            st.nprev[q] = p.np;
+            st.recount[q] = 0;
+        }
+    }
+    plan[slot] = p;
+}
+
 // Learned starts on the bitmap path: a query that stopped at its first level
 // L > 0 never counted level L - 1, whose candidates come first under the k + v
 // bound (reading R5).  Those are exactly the final candidates whose level-(L-1)
@@ -1150,9 +1440,11 @@ __global__ void bm_overflow_list_kernel(const QueryState st, int nb, const int32
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nb) return;
-    const int f = st.bm_ovf[q];
+    const int f = st.bm_ovf[q] & 3;
     if (!f) return;
-    const int which = (f & 1) ? 0 : 1;
+    // a learned first level that was too late is answered again from level 0
+    // on the bitmap path, whatever else happened to the query
+    const int which = (f & 2) ? 1 : 0;
     const int pos = atomicAdd(count + which, 1);
     (which == 0 ? list0 : list1)[pos] = order_perm ? order_perm[b0 + q] : (int32_t)(b0 + q);
 }
@@ -1404,16 +1696,20 @@ ScanStats scan_stats_of(const IndexView &ix, int c)
 
 qw_status launch_bm_level(const IndexView &ix, int nb, int level, int64_t R, int64_t Rp, int l,
                           int cgrow, QueryState &st, int *err, bool tma, cudaStream_t s,
-                          const LoopCtl *ctl)
+                          const LoopCtl *ctl, int part)
 {
     (void)Rp;
     (void)cgrow;
     if (!tma) {
         // two passes: filter on the summaries, then count the live groups
-        const int64_t qi = (int64_t)nb * ix.m;
-        bm_bucket_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((qi + 255) / 256, 152 * 8)),
-                           256, 0, s>>>(ix, level, R, nb, st, ctl);
-        QW_CUDA_TRY(cudaGetLastError());
+        if (part != 2) {
+            const int64_t qi = (int64_t)nb * ix.m;
+            bm_bucket_kernel<<<(unsigned)std::max<int64_t>(
+                                   1, std::min<int64_t>((qi + 255) / 256, 152 * 8)),
+                               256, 0, s>>>(ix, level, R, nb, st, ctl);
+            QW_CUDA_TRY(cudaGetLastError());
+        }
+        if (part == 1) return QW_OK;
         const int64_t tasks = (int64_t)nb * ((ix.nT + FL_TILES - 1) / FL_TILES);
         const int fl_blocks = (int)std::max<int64_t>(
             1, std::min<int64_t>((tasks + FL_WARPS - 1) / FL_WARPS, 152 * 16));
@@ -1493,6 +1789,33 @@ qw_status launch_bm_collect(const IndexView &ix, int nb, int l, int cap, QuerySt
     QW_CUDA_TRY(cudaFuncSetAttribute(bm_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     bm_select_kernel<<<nb, SEL_THREADS, smem, s>>>(ix, l, cap, st, stats_out, sorted);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
+
+qw_status launch_bm_reduce(const IndexView &ix, int nb, int l, int cap, int cgrow,
+                           QueryState &st, bool tma, cudaStream_t s)
+{
+    if (nb == 0) return QW_OK;
+    QW_CUDA_TRY(cudaMemsetAsync(st.rd_n, 0, sizeof(int32_t), s));
+    const unsigned qb = (unsigned)((nb + 127) / 128);
+    bm_rd_compact_kernel<<<qb, 128, 0, s>>>(st, nb, st.rd_plan, st.rd_n, st.rd_hist);
+    QW_CUDA_TRY(cudaGetLastError());
+    const unsigned grid = 152 * 4;
+    bm_rd_pass_kernel<0><<<grid, RD_THREADS, 0, s>>>(ix, l, cgrow, st, st.rd_plan, st.rd_n,
+                                                    st.rd_hist, tma);
+    QW_CUDA_TRY(cudaGetLastError());
+    bm_rd_plan_kernel<<<qb, 128, 0, s>>>(l, ix.m, cap, cgrow, st, st.rd_plan, st.rd_n, st.rd_hist, 0);
+    QW_CUDA_TRY(cudaGetLastError());
+    bm_rd_pass_kernel<1><<<grid, RD_THREADS, 0, s>>>(ix, l, cgrow, st, st.rd_plan, st.rd_n,
+                                                    st.rd_hist, tma);
+    QW_CUDA_TRY(cudaGetLastError());
+    bm_rd_plan_kernel<<<qb, 128, 0, s>>>(l, ix.m, cap, cgrow, st, st.rd_plan, st.rd_n, st.rd_hist, 1);
+    QW_CUDA_TRY(cudaGetLastError());
+    bm_rd_pass_kernel<2><<<grid, RD_THREADS, 0, s>>>(ix, l, cgrow, st, st.rd_plan, st.rd_n,
+                                                    st.rd_hist, tma);
+    QW_CUDA_TRY(cudaGetLastError());
+    bm_rd_plan_kernel<<<qb, 128, 0, s>>>(l, ix.m, cap, cgrow, st, st.rd_plan, st.rd_n, st.rd_hist, 2);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }

@@ -137,6 +137,18 @@ struct ScanStats {
 constexpr int kBmLevels = 32;
 constexpr int kBmUint4 = kTile / 128;  // uint4 per bitmap
 
+// Bitmap path: the rebuild of a last level's overflowing candidate list.
+struct RdPlan {
+    int32_t q;      // query of the batch
+    int32_t np;     // candidates of the previous level
+    int32_t cstar;  // boundary count
+    int32_t take;   // ids kept at the boundary count
+    int32_t mode;   // 0: not rebuilt, 1: whole tie class listed, 2: tie class listed by id bins
+    int32_t bound;  // mode 2: last original-id bin listed
+    int32_t pos;    // entries of the rebuilt list
+    int32_t pad;
+};
+
 // Per-batch query state, all device arrays of length nb (or nb x m).
 struct QueryState {
     int64_t *g = nullptr;             // nb x m: h_i(q) - o_i
@@ -182,6 +194,11 @@ struct QueryState {
     int32_t *bm_ovf = nullptr;
     int32_t *eqbuf = nullptr;
     int32_t *recount = nullptr;     // per query: stopped at its learned first level (bitmap path)
+    // bitmap path, last levels whose candidates overflowed the list: the
+    // number of such queries, per slot its plan and its count histogram
+    int32_t *rd_n = nullptr;
+    struct RdPlan *rd_plan = nullptr;
+    int32_t *rd_hist = nullptr;     // slots x kHistBins
     // bitmap path, two-pass level: item slots (query, tile) with their m bitmap
     // numbers, and the work list of live (slot << 8 | group) entries
     int32_t *bm_nitems = nullptr;   // 2 counters: items, work entries (per level)
@@ -223,6 +240,8 @@ struct LoopCtl {
 
 qw_status launch_query_setup(const IndexView &ix, const int32_t *HQ, int nb, QueryState &st,
                              cudaStream_t s);
+// Learned first levels: at most each query's last useful level.
+qw_status launch_clamp_start(int nb, QueryState &st, int cgrow, cudaStream_t s);
 qw_status launch_level(const IndexView &ix, int nb, int level, int64_t R, int64_t Rp, int l,
                        int cgrow, QueryState &st, cudaStream_t s, const LoopCtl *ctl = nullptr);
 qw_status launch_fallback(int nb, QueryState &st, cudaStream_t s);
@@ -249,9 +268,15 @@ qw_status launch_bid_prefix(const IndexView &ix, int64_t *prefix, const int64_t 
 ScanStats scan_stats_of(const IndexView &ix, int c);
 // tma: stage the bitmaps with TMA bulk copies in a persistent kernel (else
 // plain loads, one CTA per (tile, query)); err bit 4: a staged-copy wait gave up.
+// part (direct loads): 0 every launch of the level, 1 the bucket numbers (and
+// the profile counters), 2 the summary filter and the count pass.
 qw_status launch_bm_level(const IndexView &ix, int nb, int level, int64_t R, int64_t Rp, int l,
                           int cgrow, QueryState &st, int *err, bool tma, cudaStream_t s,
-                          const LoopCtl *ctl = nullptr);
+                          const LoopCtl *ctl = nullptr, int part = 0);
+// Rebuild the candidate lists of the queries whose last level overflowed them
+// (kept entries and tie class only); tma: the level ran bm_level_tma_kernel.
+qw_status launch_bm_reduce(const IndexView &ix, int nb, int l, int cap, int cgrow,
+                           QueryState &st, bool tma, cudaStream_t s);
 // sorted: the kept lists in ascending original id (else in no particular order)
 qw_status launch_bm_collect(const IndexView &ix, int nb, int l, int cap, QueryState &st,
                             int64_t *stats_out, bool sorted, cudaStream_t s);

@@ -183,3 +183,80 @@ extern "C" int32_t qw_l2_split_model(double setaside, double index_bytes, double
 {
     return qw::l2_split_model(setaside, index_bytes, index_reads, data_bytes, data_reads);
 }
+
+// ---- read bandwidth of a buffer of a given size (a measuring tool)
+//
+// Every thread reads 16-byte words of the buffer in a grid-stride loop with
+// loads cached in L2 only (ld.global.cg), so a buffer smaller than L2 measures
+// what L2 delivers to the SMs and a buffer much larger than L2 measures HBM.
+// The XOR of what was read goes to a sink so the loads are not removed.
+namespace {
+
+__global__ void __launch_bounds__(256) read_probe_kernel(const uint4 *__restrict__ p, int64_t n16,
+                                                         unsigned int *sink)
+{
+    uint32_t acc = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n16; i += 4 * stride) {
+        const uint4 a = __ldcg(p + i), b = __ldcg(p + i + stride);
+        const uint4 c = __ldcg(p + i + 2 * stride), d = __ldcg(p + i + 3 * stride);
+        acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w ^ c.x ^ c.y ^ c.z ^ c.w ^ d.x ^ d.y ^
+               d.z ^ d.w;
+    }
+    for (; i < n16; i += stride) {
+        const uint4 a = __ldcg(p + i);
+        acc ^= a.x ^ a.y ^ a.z ^ a.w;
+    }
+    acc = __reduce_xor_sync(0xffffffffu, acc);
+    if ((threadIdx.x & 31) == 0 && acc == 0x9e3779b9u) atomicAdd(sink, 1u);
+}
+
+}  // namespace
+
+extern "C" qw_status qw_measure_read_bandwidth(int64_t bytes, int32_t reps, double *gbs,
+                                               void *stream)
+{
+    using namespace qw;
+    clear_error();
+    if (bytes < 16 || reps < 1 || !gbs) {
+        set_error("qw_measure_read_bandwidth: bytes >= 16, reps >= 1, gbs non-null");
+        return QW_ERR_ARG;
+    }
+    const int64_t n16 = bytes / 16;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevBuf buf, sink;
+    QW_TRY(buf.ensure((size_t)n16 * 16));
+    QW_TRY(sink.ensure(16));
+    QW_CUDA_TRY(cudaMemsetAsync(buf.p, 0x5a, (size_t)n16 * 16, s));
+    QW_CUDA_TRY(cudaMemsetAsync(sink.p, 0, 16, s));
+    int dev = 0, n_sm = 0;
+    QW_CUDA_TRY(cudaGetDevice(&dev));
+    QW_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = n_sm * 8;
+    cudaEvent_t e0, e1;
+    QW_CUDA_TRY(cudaEventCreate(&e0));
+    QW_CUDA_TRY(cudaEventCreate(&e1));
+    double best = 0.0;
+    // one untimed pass brings a small buffer into L2
+    read_probe_kernel<<<grid, 256, 0, s>>>(buf.as<uint4>(), n16, sink.as<unsigned int>());
+    for (int r = 0; r < reps; ++r) {
+        cudaEventRecord(e0, s);
+        read_probe_kernel<<<grid, 256, 0, s>>>(buf.as<uint4>(), n16, sink.as<unsigned int>());
+        cudaEventRecord(e1, s);
+        const cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_status(e, "qw_measure_read_bandwidth");
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms > 0.0f) best = fmax(best, (double)n16 * 16.0 / (ms * 1e-3) / 1e9);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    QW_CUDA_TRY(cudaGetLastError());
+    *gbs = best;
+    return QW_OK;
+}

@@ -9,7 +9,6 @@
 #include "qw_internal.cuh"
 
 #include <algorithm>
-#include <mutex>
 #include <string>
 
 namespace qw {
@@ -19,32 +18,35 @@ namespace {
 // device address: host code passes the address cudaGetSymbolAddress returns.
 static __device__ __align__(256) unsigned char g_qw_static_scratch[QW_STATIC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mutex;
-void *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current) and cached.
+// Device address of the scratch array on the current device, looked up with
+// that device current at every call: the lookup is cheap, and an address
+// cached across calls would outlive a cudaDeviceReset that reloads the module.
+// The first lookup on a device loads the library's module there.
 qw_status scratch_address(unsigned char **out)
+{
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_qw_static_scratch);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(static scratch)");
+    if (!p) {
+        set_error("qw_run_workload_noalloc: static scratch has no device address");
+        return QW_ERR_CUDA;
+    }
+    *out = reinterpret_cast<unsigned char *>(p);
+    return QW_OK;
+}
+
+// The index's arrays must be on the current device, where the scratch is.
+qw_status index_on_current_device(const IndexView &ix)
 {
     int dev = -1;
     QW_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("qw_run_workload_noalloc: device ordinal out of range");
+    cudaPointerAttributes attr{};
+    QW_CUDA_TRY(cudaPointerGetAttributes(&attr, ix.X));
+    if (attr.type != cudaMemoryTypeDevice || attr.device != dev) {
+        set_error("qw_run_workload_noalloc: the index lives on another device than the current "
+                  "one; make its device current");
         return QW_ERR_ARG;
     }
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_qw_static_scratch);
-        if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(static scratch)");
-        if (!p) {
-            set_error("qw_run_workload_noalloc: static scratch has no device address");
-            return QW_ERR_CUDA;
-        }
-        g_scratch_addr[dev] = p;
-    }
-    *out = reinterpret_cast<unsigned char *>(g_scratch_addr[dev]);
     return QW_OK;
 }
 
@@ -110,6 +112,7 @@ extern "C" qw_status qw_run_workload_noalloc(qw_index *index, const float *queri
         while (B > 1 && batch_bytes(B, m, nT, cap) > QW_STATIC_SCRATCH_BYTES) --B;
         B = std::min<size_t>(B, (size_t)std::min<int64_t>(nq, 65535));
     }
+    QW_TRY(index_on_current_device(ix));
     unsigned char *base = nullptr;
     QW_TRY(scratch_address(&base));
 

@@ -686,6 +686,27 @@ qw_status launch_query_setup(const IndexView &ix, const int32_t *HQ, int nb, Que
     return QW_OK;
 }
 
+// A learned first level never lies past the query's own last useful level,
+// the first L with c^L > top (there the radius rule stops the plain path, and
+// the level loops run at least that far for every query of the batch); a
+// later prediction would leave the query unstarted.
+__global__ void clamp_start_kernel(QueryState st, int nb, int cgrow)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nb) return;
+    int L = 0;
+    for (int64_t R = 1; R <= st.top[q]; R *= cgrow) ++L;
+    if (st.start[q] > L) st.start[q] = L;
+}
+
+qw_status launch_clamp_start(int nb, QueryState &st, int cgrow, cudaStream_t s)
+{
+    if (nb == 0) return QW_OK;
+    clamp_start_kernel<<<(nb + 127) / 128, 128, 0, s>>>(st, nb, cgrow);
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
+
 qw_status launch_level(const IndexView &ix, int nb, int level, int64_t R, int64_t Rp, int l,
                        int cgrow, QueryState &st, cudaStream_t s, const LoopCtl *ctl)
 {

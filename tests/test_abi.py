@@ -123,3 +123,63 @@ def test_host_bitmaps_need_bitmaps_without_device(qwlib):
     p = qwlib.qw_index_params(m=8, w=4.0, c=2, v=10, host_bitmaps=1)
     assert L.qw_build_index(fake, 10, 4, fake, fake, C.byref(p), 0, None, C.byref(h)) == qwlib.QW_ERR_ARG
     assert b"host_bitmaps" in L.qw_last_error()
+
+
+# ---------------------------------------------------------------- seeded projections
+_GAMMA = 0x9E3779B97F4A7C15
+_M64 = (1 << 64) - 1
+
+
+def _splitmix64(seed, k):
+    """SplitMix64's output for counter k (Steele, Lea and Flood, OOPSLA 2014):
+    the state after k + 1 steps of adding the golden-ratio increment, mixed."""
+    z = (seed + (k + 1) * _GAMMA) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def _draw_reference(seed, m, d, w):
+    """The documented draw restated: uniforms from the top 53 bits, normals by
+    the Box-Muller transform in pairs, offsets from the following counters."""
+    import numpy as np
+    u = lambda k: (_splitmix64(seed, k) >> 11) * 2.0 ** -53  # noqa: E731
+    na = m * d
+    A = np.empty(na, np.float32)
+    for e in range(0, na, 2):
+        r = math.sqrt(-2.0 * math.log(1.0 - u(e)))
+        t = 2.0 * math.pi * u(e + 1)
+        A[e] = np.float32(r * math.cos(t))
+        if e + 1 < na:
+            A[e + 1] = np.float32(r * math.sin(t))
+    k0 = (na + 1) // 2 * 2
+    wf = float(np.float32(w))  # the bucket width as the float the library takes
+    b = np.array([np.float32(u(k0 + i) * wf) for i in range(m)], np.float32)
+    b = np.where(b < np.float32(w), b, np.nextafter(np.float32(w), np.float32(0)))
+    return A.reshape(m, d), b
+
+
+@pytest.mark.parametrize("seed,m,d,w", [(0, 16, 32, 4.0), (12345, 7, 5, 2.719),
+                                        (2 ** 63 + 11, 3, 3, 1.0)])
+def test_draw_projections_is_the_documented_generator(qwlib, seed, m, d, w):
+    import numpy as np
+    A, b = qwlib.qw_draw_projections(seed, m, d, w)
+    wantA, wantb = _draw_reference(seed, m, d, w)
+    assert np.array_equal(A, wantA)
+    assert np.array_equal(b, wantb)
+
+
+def test_draw_projections_distribution(qwlib):
+    """a ~ N(0, I): mean 0, variance 1, no correlation between neighbouring
+    entries; b ~ U[0, w): inside the interval, mean w / 2; seeds differ."""
+    import numpy as np
+    A, b = qwlib.qw_draw_projections(7, 200, 500, 4.0)
+    x = A.astype(np.float64).ravel()
+    assert abs(x.mean()) < 0.01 and abs(x.var() - 1.0) < 0.01
+    assert abs(np.corrcoef(x[:-1], x[1:])[0, 1]) < 0.01
+    assert abs((x ** 4).mean() / x.var() ** 2 - 3.0) < 0.05  # Gaussian kurtosis
+    assert np.all((b >= 0) & (b < 4.0)) and abs(b.mean() - 2.0) < 0.25
+    A2, _ = qwlib.qw_draw_projections(8, 200, 500, 4.0)
+    assert not np.array_equal(A, A2)
+    A3, b3 = qwlib.qw_draw_projections(7, 200, 500, 4.0)
+    assert np.array_equal(A, A3) and np.array_equal(b, b3)

@@ -12,13 +12,14 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 STRUCTS = {
     "qw_index_params": ["m", "w", "c", "v", "l", "delta", "shadow_bf16", "bitmaps",
-                        "host_bitmaps"],
+                        "host_bitmaps", "seed"],
     "qw_query_params": ["batch", "profile", "path", "clusters", "order", "rerank", "start",
                         "graph", "bitmap_loads", "l2_mode", "l2_index_permille", "reserved"],
     "qw_profile": ["launches", "ms", "timed_launches", "queries", "rerank_candidates",
                    "rerank_fp32_rows", "start_levels_skipped", "start_fallbacks", "level_passes",
                    "bitmap_fallbacks", "bitmap_live_items", "bitmap_live_groups",
-                   "bitmap_live_words", "l2_setaside_bytes", "l2_index_permille"],
+                   "bitmap_live_words", "l2_setaside_bytes", "l2_index_permille",
+                   "bitmap_overflows"],
     "qw_index_info": ["n", "d", "m", "w", "c", "v", "l", "tile", "n_tiles", "span_max",
                       "n_fixups", "device_bytes", "bitmap_bytes", "host_bytes"],
     "qw_tune_report": ["tried", "params", "ms", "best"],

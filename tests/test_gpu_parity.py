@@ -133,6 +133,31 @@ def test_hand_worked_golden(qwlib, cuda, path):
     out["index"].free()
 
 
+# ---------------------------------------------------------------- boundary: seeded draws
+def test_seeded_projections_and_getter(orc, qwlib, cuda):
+    """An index built without A and b draws them from its seed
+    (qw_draw_projections); qw_index_get_projections returns exactly those and
+    the anchors, and the oracle given them reproduces the index's answers."""
+    wl = workloads.make_workload("mix10k_d32", seed=44, n=6000, nq=40, d=24, m=12)
+    index = qwlib.Index(_t(wl.X, cuda), w=4.0, v=60, m=12, seed=99, bitmaps=True)
+    A, b, o = index.projections()
+    wantA, wantb = qwlib.qw_draw_projections(99, 12, 24, 4.0)
+    assert np.array_equal(A, wantA) and np.array_equal(b, wantb)
+    l = index.l
+    H, HQ, oidx, ref = _oracle_run(orc, wl.X, wl.Q, A, b, 4.0, 10, 60, l)
+    assert np.array_equal(o, oidx.o)
+    for path in ("levels", "bitmap"):
+        ids, dists, st = index.query(_t(wl.Q, cuda), 10, stats=True, path=path)
+        _check_results(ids.cpu().numpy(), dists.cpu().numpy(), ref["ids"], ref["dists"])
+        assert np.array_equal(st.cpu().numpy(), ref["stats"])
+    index.free()
+    # given projections are returned unchanged
+    ix2 = qwlib.Index(_t(wl.X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=4.0, v=60)
+    A2, b2, _ = ix2.projections()
+    assert np.array_equal(A2, wl.A) and np.array_equal(b2, wl.b)
+    ix2.free()
+
+
 # ---------------------------------------------------------------- a1 + a2: hashing
 @pytest.mark.parametrize("n,d,m,scale", [(10_000, 32, 16, 1.0), (1_007, 33, 5, 3.0),
                                          (20_000, 128, 64, 1.0), (4_099, 512, 7, 0.5)])
@@ -478,21 +503,106 @@ def test_bitmap_path_large_tie_classes(orc, qwlib, cuda, graph):
 
 
 @pytest.mark.parametrize("graph", [False, True])
-def test_bitmap_path_overflow_answered_by_level_path(orc, qwlib, cuda, graph):
+def test_bitmap_path_overflow_of_duplicates(orc, qwlib, cuda, graph):
     """270,000 copies of one point (plus a few others): the query's first
-    level holds 270,000 candidates, more than the bitmap path's per-query list
-    (262,144).  That query is answered by the level path and every output
-    still equals the oracle's."""
+    level holds 270,000 candidates with one count, more than the bitmap path's
+    per-query list (262,144).  The list is rebuilt with the smallest original
+    ids of that tie class (by id bins), no query needs the level path, and
+    every output equals the oracle's."""
     rng = np.random.default_rng(37)
     base = rng.uniform(-10, 10, size=(4, 16)).astype(np.float32)
     X = np.concatenate([np.repeat(base[:1], 270_000, axis=0), np.repeat(base[1:], 300, axis=0)])
     Q = (base[[0, 1, 2]] + rng.normal(0, 0.05, size=(3, 16))).astype(np.float32)
     wl = workloads.make_workload("mix10k_d32", seed=3, n=1000, nq=1, d=16, m=16)
-    _full_parity(orc, qwlib, cuda, X, Q, wl.A, wl.b, w=4.0, k=10, v=90, l=12,
-                 path="bitmap_direct_graph" if graph else "bitmap_direct")
+    for path in (("bitmap_direct_graph", "bitmap_graph") if graph else ("bitmap_direct", "bitmap")):
+        _full_parity(orc, qwlib, cuda, X, Q, wl.A, wl.b, w=4.0, k=10, v=90, l=12, path=path)
     index = qwlib.Index(_t(X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=4.0, v=90, l=12,
                         bitmaps=True)
     index.profile(reset=True)
-    index.query(_t(Q, cuda), 10, path="bitmap", graph=graph, loads="direct")
-    assert index.profile()["bitmap_fallbacks"] > 0
+    index.query(_t(Q, cuda), 10, path="bitmap", graph=graph, loads="direct", profile=True)
+    prof = index.profile()
+    assert prof["bitmap_overflows"] >= 1
+    assert prof["bitmap_fallbacks"] == 0
     index.free()
+
+
+def _cluster_overflow_case():
+    """400,000 points, most in one tight Gaussian cluster (sigma 0.3, d = 16),
+    and 96 queries at distances 4 to 9 from its centre: one doubling of the
+    radius sweeps most of the cluster into the last level of about a quarter
+    of the queries (262,000 to 380,000 candidates, with up to 83 of the
+    previous level's), above the bitmap path's list of 262,144."""
+    rng = np.random.default_rng(43)
+    d, m, n = 16, 16, 400_000
+    base = rng.uniform(-10, 10, size=(3, d)).astype(np.float32)
+    X = np.concatenate([base[0] + rng.normal(0, 0.3, size=(n - 20_000, d)),
+                        base[1] + rng.normal(0, 0.3, size=(20_000, d))]).astype(np.float32)
+    A = rng.standard_normal((m, d), dtype=np.float32)
+    b = (rng.random(m) * 4).astype(np.float32)
+    rq = np.random.default_rng(5)
+
+    def queries(count):
+        dirs = rq.normal(size=(count, d))
+        dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+        return (base[0] + dirs * rq.uniform(4, 9, size=count)[:, None]).astype(np.float32)
+
+    Q = queries(96)
+    return X, Q, A, b, queries(3000)
+
+
+@pytest.mark.slow
+def test_bitmap_path_overflow_from_clusters(orc, qwlib, cuda):
+    """Last levels larger than the candidate list, from a real cluster: every
+    bitmap variant rebuilds those lists and returns the oracle's candidate
+    sets, counts, statistics and results, with no query on the level path;
+    learned first levels (recounted previous level) and over-eager ones
+    (answered again from level 0) give the same results."""
+    import torch
+    X, Q, A, b, Qt = _cluster_overflow_case()
+    kw = dict(w=4.0, k=10, v=90, l=10)
+    ref, _ = _full_parity(orc, qwlib, cuda, X, Q, A, b, path="bitmap", **kw)
+    for path in ("bitmap_direct", "bitmap_direct_graph"):
+        _check_same(qwlib, cuda, X, Q, A, b, ref, path=path, **kw)
+    assert int((ref["stats"][:, 2] > 262_144).sum()) >= 10
+    index = qwlib.Index(_t(X, cuda), _t(A, cuda), _t(b, cuda), w=4.0, v=90, l=10, bitmaps=True)
+    Qd, Qtd = _t(Q, cuda), _t(Qt, cuda)
+    index.profile(reset=True)
+    ids0, d0, st0 = index.query(Qd, 10, stats=True, path="bitmap", loads="direct", profile=True)
+    prof = index.profile(reset=True)
+    assert prof["bitmap_overflows"] >= 10 and prof["bitmap_fallbacks"] == 0
+    assert np.array_equal(ids0.cpu().numpy(), ref["ids"])
+    # learned first levels
+    _, _, stt = index.query(Qtd, 10, stats=True, path="bitmap", loads="direct")
+    labels = (stt[:, 0] - 1).clamp(0, 15).to(torch.int32).contiguous()
+    F = index.features(Qtd)
+    mlp = qwlib.Mlp(F.shape[1], 256, 16)
+    mlp.set_params(qwlib.mlp_init(F.shape[1], 256, 16, seed=7))
+    mlp.train(F, labels, epochs=10, batch=256, lr=1e-3)
+    # eps = 0.999 predicts some first levels past the last level the loop
+    # runs for the batch; they start at their own last useful level instead
+    for eps in (0.02, 0.999):
+        index.set_start_model(mlp, eps=eps)
+        for path, graph, loads in (("bitmap", False, "direct"), ("bitmap", True, "direct"),
+                                   ("bitmap", True, "tma"), ("levels", False, "tma"),
+                                   ("levels", True, "tma")):
+            ids, dd, st = index.query(Qd, 10, stats=True, path=path, start="learned",
+                                      graph=graph, loads=loads, profile=True)
+            p = index.profile(reset=True)
+            assert torch.equal(ids, ids0) and torch.equal(dd, d0) and torch.equal(st, st0), \
+                (eps, path, graph, loads)
+            assert p["bitmap_fallbacks"] == 0
+            if eps < 0.5 and path == "bitmap":
+                assert p["start_levels_skipped"] > 0
+    index.free()
+    mlp.free()
+
+
+def _check_same(qwlib, cuda, X, Q, A, b, ref, *, w, k, v, l, path):
+    """Another path's outputs against an oracle run already checked."""
+    g = _gpu_workload(qwlib, cuda, X, Q, A, b, w=w, k=k, v=v, l=l, path=path)
+    _check_results(g["ids"], g["dists"], ref["ids"], ref["dists"])
+    assert np.array_equal(g["stats"], ref["stats"]), "per-query statistics differ"
+    assert np.array_equal(g["stats2"], ref["stats"])
+    _check_candidates(g["cid"], g["ccol"], ref["cand_ids"], ref["cand_col"])
+    g["index"].free()
+    return g

@@ -61,3 +61,38 @@ def test_noalloc_matches_run_workload_twice(qwlib, cuda):
         got = _call_noalloc(qwlib, index, Q, k)
         _check_same(got, want)
     index.free()
+
+
+def test_noalloc_arguments_empty_workload_and_no_stats(qwlib, cuda):
+    """Bad arguments are refused with QW_ERR_ARG and a message naming the
+    entry point; an empty workload is a no-op; without the statistics output
+    the results are those of the call with it."""
+    import torch
+    wl = workloads.make_workload("mix10k_d32", seed=23, n=5000, nq=200, d=16, m=8, n_clusters=10)
+    index = qwlib.Index(torch.from_numpy(wl.X).to(cuda), torch.from_numpy(wl.A).to(cuda),
+                        torch.from_numpy(wl.b).to(cuda), w=4.0, v=30)
+    Q = torch.from_numpy(wl.Q).to(cuda)
+    lib = qwlib.load()
+    stream = int(torch.cuda.current_stream(cuda).cuda_stream)
+    ids = torch.empty((200, 4096), dtype=torch.int64, device=cuda)
+    dists = torch.empty((200, 4096), dtype=torch.float32, device=cuda)
+    for k, i_ptr, q_ptr in ((4090, ids.data_ptr(), Q.data_ptr()),   # k + v > 4096
+                            (5001, ids.data_ptr(), Q.data_ptr()),   # k > n
+                            (0, ids.data_ptr(), Q.data_ptr()),      # k < 1
+                            (5, None, Q.data_ptr()),                # null ids
+                            (5, ids.data_ptr(), None)):             # null queries
+        st = lib.qw_run_workload_noalloc(index.handle, q_ptr, 200, k, i_ptr, dists.data_ptr(),
+                                         None, stream)
+        assert st == qwlib.QW_ERR_ARG
+        assert b"qw_run_workload_noalloc" in lib.qw_last_error()
+    assert lib.qw_run_workload_noalloc(index.handle, None, 0, 5, None, None, None, stream) == qwlib.QW_OK
+    k = 7
+    with_stats = _call_noalloc(qwlib, index, Q, k)
+    ids2 = torch.empty((200, k), dtype=torch.int64, device=cuda)
+    d2 = torch.empty((200, k), dtype=torch.float32, device=cuda)
+    qwlib.qw_run_workload_noalloc(index.handle, Q.data_ptr(), 200, k, ids2.data_ptr(),
+                                  d2.data_ptr(), 0, stream)
+    torch.cuda.synchronize()
+    assert np.array_equal(ids2.cpu().numpy(), with_stats[0])
+    assert np.array_equal(d2.cpu().numpy(), with_stats[1])
+    index.free()
