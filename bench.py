@@ -99,7 +99,7 @@ def parse_args(argv=None):
     p.add_argument("--host-bitmaps", action="store_true",
                    help="keep the level bitmaps in pinned host memory, read over NVLink-C2C "
                         "(an index larger than the GPU's memory)")
-    p.add_argument("--loads", choices=["tma", "direct"], default="direct",
+    p.add_argument("--loads", choices=["tma", "direct", "fused"], default="direct",
                    help="with --no-tune and --path bitmap: how the bitmap kernel reads bitmaps")
     p.add_argument("--graph", action="store_true",
                    help="with --no-tune: run the level loop as a CUDA graph")
@@ -250,6 +250,7 @@ def measured_peaks():
 KERNEL_SOURCES = {
     "level_kernel": ("qw_query.cu", "qw_count.cuh", "qw_dir.cuh", "qw_internal.cuh"),
     "bm_filter_count": ("qw_bitmap.cu", "qw_dir.cuh", "qw_scan.cuh", "qw_internal.cuh"),
+    "bm_fused_kernel": ("qw_bitmap.cu", "qw_dir.cuh", "qw_scan.cuh", "qw_internal.cuh"),
     "bm_level_tma_kernel": ("qw_bitmap.cu", "qw_tma.cuh", "qw_internal.cuh"),
     "cluster_query_kernel": ("qw_cluster.cu", "qw_count.cuh", "qw_internal.cuh"),
     "rerank_kernel": ("qw_rerank.cu", "qw_scan.cuh", "qw_internal.cuh"),
@@ -584,7 +585,16 @@ def run_ours(args):
     dom_name = {"cluster": "cluster_query_kernel (all levels of collision counting, persistent)",
                 "level": "level_kernel (bucket-range search + collision counting)"}[dom]
     if bitmap and dom == "level":
-        if chosen_kw.get("loads", "tma") == "direct":
+        if chosen_kw.get("loads", "tma") == "fused":
+            # one pass: per (query, tile, level) the m bucket summaries (32 B);
+            # per live 128-id group the previous and the new candidate word and
+            # the bitmap words of the projections touching it (16 B each)
+            dom_name = ("bm_fused_kernel (summary filter and bit-sliced collision counts of the "
+                        "live 128-id groups in one launch)")
+            count_bytes = ((prof["level_passes"] / steps) * index.info.n_tiles * s.m * 32.0
+                           + (prof["bitmap_live_groups"] / steps) * 32.0
+                           + (prof["bitmap_live_words"] / steps) * 16.0)
+        elif chosen_kw.get("loads", "tma") == "direct":
             # two passes: per (query, tile, level) the m bucket summaries (32 B);
             # per live item its m bitmap numbers (int32, written and read); per
             # live 128-id group its work entry and projection mask (written and
@@ -604,7 +614,7 @@ def run_ours(args):
     # launches actually run; for the two-pass bitmap level a "launch" is one
     # level pass (its filter and count launches; the bucket numbers of each
     # pass are timed apart in their own class)
-    two_pass = bitmap and dom == "level" and chosen_kw.get("loads", "tma") == "direct"
+    two_pass = bitmap and dom == "level" and chosen_kw.get("loads", "tma") in ("direct", "fused")
     dom_launches = (prof["timed_launches"]["bucket"] if two_pass else prof["launches"][dom]) / steps
     dom_ms = prof["ms"][dom] / steps
     per_launch_bytes = count_bytes / max(dom_launches, 1)
@@ -627,8 +637,8 @@ def run_ours(args):
     rr_achieved = (rr_bytes / max(rr_launches, 1)) / ((rr_ms / 1e3) / max(rr_launches, 1)) / 1e9 \
         if rr_ms > 0 else 0.0
     kname = "cluster_query_kernel" if dom == "cluster" else (
-        ("bm_filter_count" if chosen_kw.get("loads", "tma") == "direct" else "bm_level_tma_kernel")
-        if bitmap else "level_kernel")
+        {"direct": "bm_filter_count", "fused": "bm_fused_kernel"}.get(
+            chosen_kw.get("loads", "tma"), "bm_level_tma_kernel") if bitmap else "level_kernel")
     roofline = {"kernel": dom_name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "unit": "GB/s", "frac": round(achieved / hbm, 4),
                 "traffic": (lambda t: None if t is None else t / max(dom_launches, 1))(

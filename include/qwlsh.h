@@ -100,6 +100,8 @@ typedef struct {
     uint64_t seed;        /* used only when qw_build_index gets A == NULL and b == NULL: the
                              projections are then drawn on the host by qw_draw_projections(seed,
                              m, d, w, ...); read them back with qw_index_get_projections */
+    int32_t projection;   /* QW_PROJ_FP32 (default) or QW_PROJ_TENSOR: how the data are
+                             projected at build time (same bucket ids) */
 } qw_index_params;
 
 /* Per-workload options.  Zero-initialise; unknown non-zero fields are rejected. */
@@ -123,8 +125,10 @@ typedef struct {
                              for the stream once at its end.  Same kernels, same results */
     int32_t bitmap_loads; /* QW_PATH_BITMAP: QW_LOADS_TMA (default) stages the bucket bitmaps
                              in shared memory with TMA bulk copies in a persistent kernel;
-                             QW_LOADS_DIRECT loads them straight from global memory, one CTA
-                             per (tile, query).  Same results */
+                             QW_LOADS_DIRECT runs a summary filter, then counts the live
+                             128-id groups with plain loads in a second launch;
+                             QW_LOADS_FUSED does both in one launch, one warp per (query,
+                             run of tiles).  Same results */
     int32_t l2_mode;      /* persisting-L2 division between the index and the data (the
                              workload cache split of Section 4, on the GPU's L2): QW_L2_OFF
                              (default) attaches no access-policy window; QW_L2_SPLIT gives
@@ -132,7 +136,9 @@ typedef struct {
                              rest to the data window; QW_L2_MODEL takes the split from
                              qw_l2_split_model.  Speed only: the results do not change */
     int32_t l2_index_permille;  /* QW_L2_SPLIT: 0..1000, the paper's size(C_I) / size(C) */
-    int32_t reserved[1];  /* must be zero */
+    int32_t projection;   /* QW_PROJ_FP32 (default): the queries' projection on CUDA cores in
+                             FP32; QW_PROJ_TENSOR: on the tensor cores (split BF16 products,
+                             FP32 accumulation, m <= 128; see qw_hash_tc).  Same bucket ids */
 } qw_query_params;
 
 /* Persisting-L2 modes (qw_query_params.l2_mode).  With a window mode the call
@@ -153,8 +159,12 @@ typedef struct {
 #define QW_L2_SPLIT 1
 #define QW_L2_MODEL 2
 
+#define QW_PROJ_FP32 0
+#define QW_PROJ_TENSOR 1
+
 #define QW_LOADS_TMA 0
 #define QW_LOADS_DIRECT 1
+#define QW_LOADS_FUSED 2
 
 /* First level of the collision-counting loop.  QW_START_PLAIN: every query
  * starts at radius R = 1.  QW_START_LEARNED: the index's start model predicts,
@@ -293,6 +303,19 @@ int32_t qw_collision_threshold(int32_t m, float w, int32_t c, int64_t n, int32_t
 qw_status qw_hash(const float *V, int64_t nv, int32_t d, const float *A, const float *b,
                   int32_t m, float w, int32_t *H, int64_t *n_fixups, void *stream);
 
+/* qw_hash on the fifth-generation tensor cores (tcgen05.mma, BF16 operands in
+ * shared memory, FP32 accumulators in tensor memory), m <= 128.  Each FP32
+ * input is split into BF16 hi and lo parts; the products hi*hi, hi*lo and
+ * lo*hi are accumulated in FP32, which leaves an error of at most
+ * (3.01 * 2^-16 + (d - 1) * 2^-22 + 2^-23) * ||a_i|| ||V_r|| for any order of
+ * the tensor cores' additions, taking each to lose at most two units in the
+ * last place.  Entries within that bound (and at least 1e-5 w) of a bucket
+ * boundary are recomputed in FP64 as in qw_hash, so H equals the FP64 result;
+ * the wider bound means more recomputations (*n_fixups).  Arguments, pointer
+ * spaces and errors as qw_hash; QW_ERR_ARG also for m > 128. */
+qw_status qw_hash_tc(const float *V, int64_t nv, int32_t d, const float *A, const float *b,
+                     int32_t m, float w, int32_t *H, int64_t *n_fixups, void *stream);
+
 /* The hash family's random draws (Section 3: a_i ~ N(0, I_d), b_i ~ U[0, w))
  * from a seed, on the host, the same on every machine.  The generator is
  * SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) used by counter: draw k is
@@ -351,7 +374,7 @@ qw_status qw_index_get_projections(const qw_index *index, float *A, float *b, in
  * every candidate whose order against a neighbour is not certain under the
  * FP32 error bound is recomputed in FP64.
  * Errors: QW_ERR_ARG (null pointer, nq < 0, k < 1, k > n, k + v > QW_MAX_CAND,
- * non-zero reserved fields), QW_ERR_RANGE (query bucket id outside int32),
+ * unknown option values), QW_ERR_RANGE (query bucket id outside int32),
  * QW_ERR_OOM, QW_ERR_CUDA. */
 qw_status qw_run_workload(qw_index *index, const float *queries, int64_t nq, int32_t k,
                           const qw_query_params *qparams, int64_t *ids, float *dists,

@@ -37,13 +37,15 @@ EXPORTED = ("qw_version", "qw_last_error", "qw_collision_probability",
             "qw_mlp_get_params", "qw_mlp_loss_grad", "qw_mlp_train", "qw_mlp_predict",
             "qw_mlp_free", "qw_query_features", "qw_index_set_start_model", "qw_autotune",
             "qw_index_export", "qw_index_free", "qw_l2_split_model", "qw_mlp_predict_tc",
-            "qw_draw_projections", "qw_index_get_projections", "qw_measure_read_bandwidth")
+            "qw_draw_projections", "qw_index_get_projections", "qw_measure_read_bandwidth",
+            "qw_hash_tc")
 
 
 class qw_index_params(C.Structure):
     _fields_ = [("m", C.c_int32), ("w", C.c_float), ("c", C.c_int32), ("v", C.c_int32),
                 ("l", C.c_int32), ("delta", C.c_float), ("shadow_bf16", C.c_int32),
-                ("bitmaps", C.c_int32), ("host_bitmaps", C.c_int32), ("seed", C.c_uint64)]
+                ("bitmaps", C.c_int32), ("host_bitmaps", C.c_int32), ("seed", C.c_uint64),
+                ("projection", C.c_int32)]
 
 
 class qw_query_params(C.Structure):
@@ -51,7 +53,7 @@ class qw_query_params(C.Structure):
                 ("clusters", C.c_int32), ("order", C.c_int32), ("rerank", C.c_int32),
                 ("start", C.c_int32), ("graph", C.c_int32), ("bitmap_loads", C.c_int32),
                 ("l2_mode", C.c_int32), ("l2_index_permille", C.c_int32),
-                ("reserved", C.c_int32 * 1)]
+                ("projection", C.c_int32)]
 
 
 QW_TUNE_MAX = 32
@@ -71,8 +73,10 @@ RERANKS = {"fp32": QW_RERANK_FP32, "bf16": QW_RERANK_BF16}
 ORDERS = {"auto": QW_ORDER_AUTO, "signature": QW_ORDER_SIGNATURE, "given": QW_ORDER_GIVEN}
 QW_START_PLAIN, QW_START_LEARNED = 0, 1
 STARTS = {"plain": QW_START_PLAIN, "learned": QW_START_LEARNED}
-QW_LOADS_TMA, QW_LOADS_DIRECT = 0, 1
-LOADS = {"tma": QW_LOADS_TMA, "direct": QW_LOADS_DIRECT}
+QW_PROJ_FP32, QW_PROJ_TENSOR = 0, 1
+PROJECTIONS = {"fp32": QW_PROJ_FP32, "tensor": QW_PROJ_TENSOR}
+QW_LOADS_TMA, QW_LOADS_DIRECT, QW_LOADS_FUSED = 0, 1, 2
+LOADS = {"tma": QW_LOADS_TMA, "direct": QW_LOADS_DIRECT, "fused": QW_LOADS_FUSED}
 QW_L2_OFF, QW_L2_SPLIT, QW_L2_MODEL = 0, 1, 2
 (QW_K_PROJECT, QW_K_SETUP, QW_K_LEVEL, QW_K_DECIDE, QW_K_SELECT, QW_K_RERANK, QW_K_CLUSTER,
  QW_K_ORDER, QW_K_START, QW_K_BUCKET) = range(10)
@@ -132,6 +136,9 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.qw_hash.restype = C.c_int32
     L.qw_hash.argtypes = [vp, C.c_int64, C.c_int32, vp, vp, C.c_int32, C.c_float, vp,
                           C.POINTER(C.c_int64), vp]
+    L.qw_hash_tc.restype = C.c_int32
+    L.qw_hash_tc.argtypes = [vp, C.c_int64, C.c_int32, vp, vp, C.c_int32, C.c_float, vp,
+                             C.POINTER(C.c_int64), vp]
     L.qw_build_index.restype = C.c_int32
     L.qw_build_index.argtypes = [vp, C.c_int64, C.c_int32, vp, vp, C.POINTER(qw_index_params),
                                  C.c_int32, vp, C.POINTER(vp)]
@@ -237,6 +244,14 @@ def qw_hash(V: int, nv: int, d: int, A: int, b: int, m: int, w: float, H: int, s
     return int(fix.value)
 
 
+def qw_hash_tc(V: int, nv: int, d: int, A: int, b: int, m: int, w: float, H: int,
+               stream: int = 0):
+    """qw_hash on the tensor cores; returns the number of FP64 recomputations."""
+    fix = C.c_int64(0)
+    _check(load().qw_hash_tc(V, nv, d, A, b, m, w, H, C.byref(fix), stream or None))
+    return int(fix.value)
+
+
 def qw_build_index(data: int, n: int, d: int, A: int, b: int, params: qw_index_params, mem: int,
                    stream: int = 0) -> int:
     h = C.c_void_p()
@@ -328,7 +343,8 @@ def _params_kwargs(p) -> dict:
             "rerank": inv(RERANKS, p.rerank), "start": inv(STARTS, p.start),
             "graph": bool(p.graph), "loads": inv(LOADS, p.bitmap_loads),
             "l2": (None if p.l2_mode == QW_L2_OFF else "model" if p.l2_mode == QW_L2_MODEL
-                   else int(p.l2_index_permille))}
+                   else int(p.l2_index_permille)),
+            "projection": inv(PROJECTIONS, p.projection)}
 
 
 def _stream_of(t) -> int:
@@ -352,10 +368,10 @@ def _f32(t, name):
     return t
 
 
-def hash(V, A, b, w: float):
-    """Bucket ids floor((A V^T + b) / w) of CUDA float32 tensors.
-
-    Returns (H int32 nv x m on V's device, number of FP64 recomputations)."""
+def hash(V, A, b, w: float, tensor_cores: bool = False):
+    """Bucket ids floor((A V^T + b) / w) of CUDA float32 tensors (tensor_cores:
+    qw_hash_tc).  Returns (H int32 nv x m on V's device, number of FP64
+    recomputations)."""
     torch = _torch()
     _f32(V, "V"), _f32(A, "A"), _f32(b, "b")
     if not (V.is_cuda and A.is_cuda and b.is_cuda):
@@ -363,8 +379,9 @@ def hash(V, A, b, w: float):
     nv, d = V.shape
     m = A.shape[0]
     H = torch.empty((nv, m), dtype=torch.int32, device=V.device)
-    fix = qw_hash(V.data_ptr(), nv, d, A.data_ptr(), b.data_ptr(), m, float(w), H.data_ptr(),
-                  _stream_of(V))
+    fn = qw_hash_tc if tensor_cores else qw_hash
+    fix = fn(V.data_ptr(), nv, d, A.data_ptr(), b.data_ptr(), m, float(w), H.data_ptr(),
+             _stream_of(V))
     return H, fix
 
 
@@ -377,7 +394,8 @@ class Index:
 
     def __init__(self, data, A=None, b=None, *, w: float, c: int = 2, v: int = 100, l: int = 0,
                  delta: float = 0.0, shadow_bf16: bool = False, bitmaps: bool = False,
-                 host_bitmaps: bool = False, m: int = 0, seed: int = 0):
+                 host_bitmaps: bool = False, m: int = 0, seed: int = 0,
+                 projection: str = "fp32"):
         _f32(data, "data")
         n, d = data.shape
         if A is None and b is None:
@@ -395,7 +413,8 @@ class Index:
             a_ptr, b_ptr = A.data_ptr(), b.data_ptr()
         p = qw_index_params(m=m, w=float(w), c=int(c), v=int(v), l=int(l), delta=float(delta),
                             shadow_bf16=1 if shadow_bf16 else 0, bitmaps=1 if bitmaps else 0,
-                            host_bitmaps=1 if host_bitmaps else 0, seed=int(seed))
+                            host_bitmaps=1 if host_bitmaps else 0, seed=int(seed),
+                            projection=PROJECTIONS[projection])
         self._h = 0
         self._h = qw_build_index(data.data_ptr(), n, d, a_ptr or None, b_ptr or None, p, mem,
                                  _stream_of(data))
@@ -437,7 +456,7 @@ class Index:
     def query(self, Q, k: int, *, batch: int = 0, stats: bool = False, out=None,
               profile: bool = False, path: str = "auto", clusters: int = 0,
               order: str = "auto", rerank: str = "fp32", start: str = "plain",
-              graph: bool = False, loads: str = "tma", l2=None):
+              graph: bool = False, loads: str = "tma", l2=None, projection: str = "fp32"):
         """Top-k of every query row.  Returns (ids int64 nq x k, dists float32
         nq x k[, stats int64 nq x QW_NSTAT]) on Q's device (host tensors in,
         host tensors out).  ``out`` may give preallocated (ids, dists[, stats]).
@@ -461,7 +480,8 @@ class Index:
         qp = qw_query_params(batch=int(batch), profile=1 if profile else 0, path=PATHS[path],
                              clusters=int(clusters), order=ORDERS[order], rerank=RERANKS[rerank],
                              start=STARTS[start], graph=1 if graph else 0,
-                             bitmap_loads=LOADS[loads], **_l2_fields(l2))
+                             bitmap_loads=LOADS[loads], projection=PROJECTIONS[projection],
+                             **_l2_fields(l2))
         qw_run_workload(self._h, Q.data_ptr(), nq, int(k), qp, ids.data_ptr(), dists.data_ptr(),
                         st.data_ptr() if st is not None else 0, mem, _stream_of(Q))
         return (ids, dists, st) if stats else (ids, dists)

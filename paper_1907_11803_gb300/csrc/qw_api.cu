@@ -113,6 +113,7 @@ struct qw_index {
     bool shadow = false;
     bool bitmaps = false;               // level bitmaps for QW_PATH_BITMAP
     bool host_bitmaps = false;          // ... kept in pinned host memory (bm_host)
+    bool proj_tc = false;               // data projected on the tensor cores at build
     HostBuf bm_host;
     DevBuf bm, bm_base, bm_nb, bm_lvl, bm_J, bid_prefix, prefix_off, perm, bm_sum, Xloc, inv, hloc;
     int hloc_bytes = 0, hloc_stride = 0;
@@ -128,7 +129,7 @@ struct qw_index {
     L2Owner l2_owner;                   // the persisting-L2 set-aside this index raised
     // workspace for queries (grow-only)
     DevBuf w_q, w_hq, w_state, w_counters, w_cand, w_out, w_err, w_order, w_qb, w_ob, w_cbits,
-        w_clist, w_bmsel, w_ovf, w_bmwork;
+        w_clist, w_bmsel, w_ovf, w_bmwork, w_rdstore;
     int64_t device_bytes = 0;
     qw_profile prof{};
     std::vector<cudaEvent_t> event_pool;
@@ -265,19 +266,21 @@ int32_t qw_collision_threshold(int32_t m, float w, int32_t c, int64_t n, int32_t
     return std::min(m, std::max(1, l));
 }
 
-qw_status qw_hash(const float *V, int64_t nv, int32_t d, const float *A, const float *b,
-                  int32_t m, float w, int32_t *H, int64_t *n_fixups, void *stream)
+static qw_status hash_impl(const float *V, int64_t nv, int32_t d, const float *A, const float *b,
+                           int32_t m, float w, int32_t *H, int64_t *n_fixups, void *stream,
+                           bool tc)
 {
     clear_error();
     if (!V || !A || !b || !H) return arg_error("qw_hash: null pointer");
     if (nv < 0 || d < 1 || m < 1 || !(w > 0.0f)) return arg_error("qw_hash: bad size or width");
+    if (tc && m > 128) return arg_error("qw_hash_tc: m must be <= 128");
     cudaStream_t s = (cudaStream_t)stream;
     DevBuf scratch;  // err word + fixup counter
     QW_TRY(scratch.ensure(16));
     int *err = scratch.as<int>();
     unsigned long long *fix = reinterpret_cast<unsigned long long *>(scratch.as<char>() + 8);
     QW_CUDA_TRY(cudaMemsetAsync(scratch.p, 0, 16, s));
-    qw_status st = launch_hash(V, nv, d, A, b, m, w, H, m, 1, err, fix, s);
+    qw_status st = launch_hash(V, nv, d, A, b, m, w, H, m, 1, err, fix, s, tc);
     if (st != QW_OK) { scratch.release(); return st; }
     int h_err = 0;
     unsigned long long h_fix = 0;
@@ -294,6 +297,18 @@ qw_status qw_hash(const float *V, int64_t nv, int32_t d, const float *A, const f
         return QW_ERR_RANGE;
     }
     return QW_OK;
+}
+
+qw_status qw_hash(const float *V, int64_t nv, int32_t d, const float *A, const float *b,
+                  int32_t m, float w, int32_t *H, int64_t *n_fixups, void *stream)
+{
+    return hash_impl(V, nv, d, A, b, m, w, H, n_fixups, stream, false);
+}
+
+qw_status qw_hash_tc(const float *V, int64_t nv, int32_t d, const float *A, const float *b,
+                     int32_t m, float w, int32_t *H, int64_t *n_fixups, void *stream)
+{
+    return hash_impl(V, nv, d, A, b, m, w, H, n_fixups, stream, true);
 }
 
 static qw_status build_impl(qw_index *ix, const float *data, const float *A, const float *b,
@@ -320,7 +335,7 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
     unsigned long long *fix = reinterpret_cast<unsigned long long *>(scratch.as<char>() + 8);
     QW_CUDA_TRY(cudaMemsetAsync(scratch.p, 0, 16, s));
     QW_TRY(launch_hash(ix->X.as<float>(), n, d, ix->A.as<float>(), ix->b.as<float>(), m, ix->w,
-                       Ht.as<int32_t>(), 1, n, err, fix, s));
+                       Ht.as<int32_t>(), 1, n, err, fix, s, ix->proj_tc));
 
     // 2. anchors and spans
     QW_TRY(ix->o.ensure((size_t)m * sizeof(int32_t)));
@@ -531,6 +546,15 @@ qw_status qw_build_index(const float *data, int64_t n, int32_t d, const float *A
     ix->shadow = p->shadow_bf16 != 0;
     ix->bitmaps = p->bitmaps != 0;
     ix->host_bitmaps = ix->bitmaps && p->host_bitmaps != 0;
+    if (p->projection != QW_PROJ_FP32 && p->projection != QW_PROJ_TENSOR) {
+        delete ix;
+        return arg_error("qw_build_index: unknown projection");
+    }
+    if (p->projection == QW_PROJ_TENSOR && p->m > 128) {
+        delete ix;
+        return arg_error("qw_build_index: QW_PROJ_TENSOR needs m <= 128");
+    }
+    ix->proj_tc = p->projection == QW_PROJ_TENSOR;
     // no projections given: draw them on the host from the seed (Section 3's
     // a ~ N(0, I_d), b ~ U[0, w); see qw_draw_projections)
     std::vector<float> drawn_A, drawn_b;
@@ -622,7 +646,7 @@ static qw_status answer_again(qw_index *ix, const float *Qall, const int32_t *HQ
 // stopped); with learned starts, a second pass from level 0 for the queries
 // that stopped at their learned first level.
 static qw_status host_level_loop(qw_index *ix, LaunchTimer &tm, const IndexView &view, int nb,
-                                 int cap, bool learned, bool bitmap, bool tma, int *err,
+                                 int cap, bool learned, bool bitmap, int loads, int *err,
                                  QueryState &st, cudaStream_t s, int *levels_run)
 {
     unsigned long long max_top = 0;
@@ -631,21 +655,22 @@ static qw_status host_level_loop(qw_index *ix, LaunchTimer &tm, const IndexView 
     for (int pass = 0; pass < 2; ++pass) {
         int64_t R = 1, Rp = 1;
         for (int level = 0;; ++level) {
-            if (bitmap && !tma) {
+            if (bitmap && loads != QW_LOADS_TMA) {
                 // the bucket numbers apart, so that QW_K_LEVEL times the filter
                 // and count passes alone
                 QW_TRY(tm.run(QW_K_BUCKET, 1, [&] {
-                    return launch_bm_level(view, nb, level, R, Rp, ix->l, ix->c, st, err, tma, s,
-                                           nullptr, 1);
+                    return launch_bm_level(view, nb, level, R, Rp, ix->l, ix->c, st, err, loads,
+                                           s, nullptr, 1);
                 }));
-                QW_TRY(tm.run(QW_K_LEVEL, st.bm_prof ? 3 : 2, [&] {
-                    return launch_bm_level(view, nb, level, R, Rp, ix->l, ix->c, st, err, tma, s,
-                                           nullptr, 2);
+                const int nl = loads == QW_LOADS_FUSED ? 1 : (st.bm_prof ? 3 : 2);
+                QW_TRY(tm.run(QW_K_LEVEL, nl, [&] {
+                    return launch_bm_level(view, nb, level, R, Rp, ix->l, ix->c, st, err, loads,
+                                           s, nullptr, 2);
                 }));
             } else {
                 QW_TRY(tm.run(QW_K_LEVEL, 1, [&] {
                     return bitmap ? launch_bm_level(view, nb, level, R, Rp, ix->l, ix->c, st, err,
-                                                    tma, s)
+                                                    loads, s)
                                   : launch_level(view, nb, level, R, Rp, ix->l, ix->c, st, s);
                 }));
             }
@@ -760,7 +785,9 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     const bool use_bitmap = eff_path == QW_PATH_BITMAP;
     // bitmaps in host memory are read with plain loads (the TMA variant stages
     // device memory only)
-    const bool tma_loads = (!qp || qp->bitmap_loads == QW_LOADS_TMA) && !ix->host_bitmaps;
+    int loads = qp ? qp->bitmap_loads : QW_LOADS_TMA;
+    if (loads == QW_LOADS_TMA && ix->host_bitmaps) loads = QW_LOADS_DIRECT;
+    const bool tma_loads = loads == QW_LOADS_TMA;
     // bitmap path, per query: two levels of (tile) candidate bitmaps and lists
     const int64_t cb_bytes = (int64_t)ix->nT * kBmUint4 * (int64_t)sizeof(uint4) * 2;
     // (per query: two levels of tile candidate counts and candidate lists)
@@ -794,12 +821,16 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         QW_TRY(ix->w_clist.ensure((size_t)B * cl_bytes + 64));
         // per query: flags, recount mark, tie list; then the list-rebuild
         // slots (count, plans, count histograms)
-        QW_TRY(ix->w_bmsel.ensure((size_t)B * (2 + kEqCap) * sizeof(int32_t) + 16 +
+        QW_TRY(ix->w_bmsel.ensure((size_t)B * (2 + kEqCap) * sizeof(int32_t) + 256 +
                                   (size_t)B * sizeof(RdPlan) +
-                                  (size_t)B * kHistBins * sizeof(int32_t)));
+                                  (size_t)B * 2 * kHistBins * sizeof(int32_t) +
+                                  (size_t)B * 2 * QW_MAX_M * sizeof(int64_t)));
         // two-pass level: one slot per (query, tile), one work entry per group
         const size_t items = (size_t)B * ix->nT;
         QW_TRY(ix->w_bmwork.ensure(bm_work_layout(B, ix->nT, m, nullptr)));
+        // the overflow rebuild's plane store: one wave of slots
+        QW_TRY(ix->w_rdstore.ensure((size_t)std::min<int64_t>(B, bm_reduce_wave(ix->nT)) *
+                                    ix->nT * kBmUint4 * 8 * sizeof(uint4)));
         QW_TRY(ix->w_ovf.ensure(((size_t)nq + 1) * 2 * sizeof(int32_t)));
     }
     QW_TRY(ix->w_cand.ensure((size_t)B * cap * 2 * sizeof(int32_t)));
@@ -896,9 +927,19 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         st.bm_ovf = ix->w_bmsel.as<int32_t>();
         st.recount = st.bm_ovf + B;
         st.eqbuf = st.bm_ovf + 2 * B;
-        st.rd_n = st.eqbuf + (size_t)B * kEqCap;
-        st.rd_plan = reinterpret_cast<RdPlan *>(st.rd_n + 4);
+        {
+            // control words and plans on 16-byte boundaries
+            uintptr_t a = reinterpret_cast<uintptr_t>(st.eqbuf + (size_t)B * kEqCap);
+            st.rd_ctl = reinterpret_cast<int32_t *>((a + 15) & ~(uintptr_t)15);
+        }
+        st.rd_plan = reinterpret_cast<RdPlan *>(st.rd_ctl + 16);
         st.rd_hist = reinterpret_cast<int32_t *>(st.rd_plan + B);
+        {
+            // int64 bitmap numbers on an 8-byte boundary
+            uintptr_t a = reinterpret_cast<uintptr_t>(st.rd_hist + (size_t)B * 2 * kHistBins);
+            st.rd_bq = reinterpret_cast<int64_t *>((a + 15) & ~(uintptr_t)15);
+        }
+        st.rd_store = ix->w_rdstore.as<uint4>();
         const int64_t items = B * (int64_t)ix->nT;
         bm_work_layout(B, ix->nT, m, &st, ix->w_bmwork.as<char>());
         st.bm_item_cap = (int32_t)std::min<int64_t>(items, (int64_t)1 << 23);
@@ -965,7 +1006,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     QW_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
     QW_TRY(tm.run(QW_K_PROJECT, 2, [&] {
         return launch_hash(Qall, nq, d, ix->A.as<float>(), ix->b.as<float>(), m, ix->w, HQall, m, 1,
-                           err, nullptr, s);
+                           err, nullptr, s, qp && qp->projection == QW_PROJ_TENSOR);
     }));
     int32_t *perm = nullptr;
     if (order) {
@@ -1062,16 +1103,17 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             if (graph) {
                 QW_TRY(tm.run(QW_K_LEVEL, 0, [&] {
                     return run_level_graph(ix->graphs, view, nb, ix->l, ix->c, cap, learned,
-                                           use_bitmap, tma_loads, st, ctl, err, s,
+                                           use_bitmap, loads, st, ctl, err, s,
                                            l2.window(L2Use::Index));
                 }));
             } else {
-                QW_TRY(host_level_loop(ix, tm, view, nb, cap, learned, use_bitmap, tma_loads, err,
+                QW_TRY(host_level_loop(ix, tm, view, nb, cap, learned, use_bitmap, loads, err,
                                        st, s, &levels_run));
             }
-            QW_TRY(tm.run(QW_K_SELECT, use_bitmap ? (learned ? 9 : 8) : 2, [&] {
+            QW_TRY(tm.run(QW_K_SELECT, use_bitmap ? (learned ? 3 : 2) : 2, [&] {
                 if (use_bitmap)
-                    QW_TRY(launch_bm_reduce(view, nb, ix->l, cap, ix->c, st, tma_loads, s));
+                    QW_TRY(launch_bm_reduce(view, nb, ix->l, cap, ix->c, st, tma_loads,
+                                            (int)std::min<int64_t>(B, bm_reduce_wave(ix->nT)), s));
                 if (use_bitmap && learned)
                     QW_TRY(launch_bm_recount(view, nb, ix->l, cap, ix->c, st, s));
                 return use_bitmap ? launch_bm_collect(view, nb, ix->l, cap, st, stats_b, want_cand, s)
@@ -1082,7 +1124,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                                                late_list, ovf_count, s));
             if (use_bitmap && tm.on) {
                 int32_t h_rd = 0;
-                QW_CUDA_TRY(cudaMemcpyAsync(&h_rd, st.rd_n, sizeof(h_rd), cudaMemcpyDeviceToHost, s));
+                QW_CUDA_TRY(cudaMemcpyAsync(&h_rd, st.rd_ctl, sizeof(h_rd), cudaMemcpyDeviceToHost, s));
                 QW_CUDA_TRY(cudaStreamSynchronize(s));
                 ix->prof.bitmap_overflows += h_rd;
             }
@@ -1140,7 +1182,9 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         }
         // per level: the bucket numbers, filter and count (bitmap path, direct
         // loads), else one counting launch
-        ix->prof.launches[QW_K_LEVEL] += (int64_t)h_ctl.iters * (use_bitmap && !tma_loads ? 3 : 1);
+        ix->prof.launches[QW_K_LEVEL] +=
+            (int64_t)h_ctl.iters *
+            (use_bitmap && loads == QW_LOADS_DIRECT ? 3 : (use_bitmap && loads == QW_LOADS_FUSED ? 2 : 1));
         levels_run = (int)h_ctl.iters;
         ix->prof.launches[QW_K_DECIDE] += 2 * (int64_t)h_ctl.iters + n_batches * (learned ? 3 : 1);
         if (learned) {
@@ -1166,7 +1210,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             p.order = QW_ORDER_GIVEN;
             p.start = QW_START_PLAIN;
             p.graph = graph ? 1 : 0;
-            p.bitmap_loads = tma_loads ? QW_LOADS_TMA : QW_LOADS_DIRECT;
+            p.bitmap_loads = loads;
             QW_TRY(answer_again(ix, Qall, HQall, late_list, n_ovf[1], k, cap, f_ids, f_dists,
                                 f_stats, f_cids, f_ccol, s, &p));
         }
@@ -1226,14 +1270,17 @@ static qw_status check_workload_args(const qw_index *ix, const float *queries, i
         if (qp->start < QW_START_PLAIN || qp->start > QW_START_LEARNED)
             return arg_error("qw_run_workload: unknown start");
         if (qp->graph != 0 && qp->graph != 1) return arg_error("qw_run_workload: graph must be 0 or 1");
-        if (qp->bitmap_loads != QW_LOADS_TMA && qp->bitmap_loads != QW_LOADS_DIRECT)
+        if (qp->bitmap_loads != QW_LOADS_TMA && qp->bitmap_loads != QW_LOADS_DIRECT &&
+            qp->bitmap_loads != QW_LOADS_FUSED)
             return arg_error("qw_run_workload: unknown bitmap_loads");
         if (qp->l2_mode < QW_L2_OFF || qp->l2_mode > QW_L2_MODEL)
             return arg_error("qw_run_workload: unknown l2_mode");
         if (qp->l2_index_permille < 0 || qp->l2_index_permille > 1000)
             return arg_error("qw_run_workload: l2_index_permille must be in [0, 1000]");
-        for (int r = 0; r < 1; ++r)
-            if (qp->reserved[r] != 0) return arg_error("qw_run_workload: reserved field set");
+        if (qp->projection != QW_PROJ_FP32 && qp->projection != QW_PROJ_TENSOR)
+            return arg_error("qw_run_workload: unknown projection");
+        if (qp->projection == QW_PROJ_TENSOR && ix->m > 128)
+            return arg_error("qw_run_workload: QW_PROJ_TENSOR needs m <= 128");
     }
     return QW_OK;
 }
@@ -1403,6 +1450,9 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
             alt = cur;
             alt.bitmap_loads = QW_LOADS_DIRECT;
             if ((status = try_alt(alt)) != QW_OK) break;
+            alt = cur;
+            alt.bitmap_loads = QW_LOADS_FUSED;
+            if ((status = try_alt(alt)) != QW_OK) break;
             if (best_levels_ms < cur_ms) {
                 cur = best_levels;
                 cur_ms = best_levels_ms;
@@ -1428,7 +1478,13 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
             alt.rerank = QW_RERANK_BF16;
             if ((status = try_alt(alt)) != QW_OK) break;
         }
-        // 8. persisting-L2 windows split by the cost model
+        // 8. the queries' projection on the tensor cores
+        if (ix->m <= 128) {
+            qw_query_params alt = cur;
+            alt.projection = QW_PROJ_TENSOR;
+            if ((status = try_alt(alt)) != QW_OK) break;
+        }
+        // 9. persisting-L2 windows split by the cost model
         {
             qw_query_params alt = cur;
             alt.l2_mode = QW_L2_MODEL;
@@ -1635,7 +1691,7 @@ void qw_index_free(qw_index *ix)
     DevBuf *bmb[] = {&ix->bm,  &ix->bm_base,    &ix->bm_nb,      &ix->bm_lvl,
                      &ix->bm_J, &ix->bid_prefix, &ix->prefix_off, &ix->w_cbits,
                      &ix->w_clist, &ix->perm, &ix->bm_sum, &ix->w_bmsel, &ix->w_ovf,
-                     &ix->w_bmwork, &ix->Xloc, &ix->inv, &ix->hloc};
+                     &ix->w_bmwork, &ix->w_rdstore, &ix->Xloc, &ix->inv, &ix->hloc};
     for (DevBuf *bb : bmb) bb->release();
     for (cudaEvent_t e : ix->event_pool) cudaEventDestroy(e);
     level_graph_cache_free(ix->graphs);

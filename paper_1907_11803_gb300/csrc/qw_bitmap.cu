@@ -545,6 +545,193 @@ __global__ void __launch_bounds__(256, 3) bm_count_kernel(IndexView ix, int leve
     }
 }
 
+// ---- the same level in one pass (filter and count fused)
+//
+// One warp per (query, run of FL_TILES tiles), as in pass 1 above: the bucket
+// summaries give every 128-id group the set of the query's buckets touching
+// it, and the groups touched by at least l buckets are live.  The same warp
+// then counts its live groups, 32 at a time (lane k takes the k-th live group
+// of the tile): the m bitmap numbers of the tile stay in the lanes' registers
+// (lane j holds projections j and j + 32) and are broadcast by shuffles, so a
+// group's m word loads depend on nothing but its own projection mask, which
+// the filter step left in shared memory.  No work list, item slots or masks go
+// through global memory.  Results (candidate words, live-group masks, tile
+// counts, candidate lists, profile counters) are those of the two passes.
+// Position of the n-th (0-based) set bit of v; n < popc(v).
+__device__ __forceinline__ int nth_set_bit(uint32_t v, int n)
+{
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const int c = __popc(v & ((1u << w) - 1u));
+        if (n >= c) {
+            n -= c;
+            v >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
+template <int NROW>
+__global__ void __launch_bounds__(FL_WARPS * 32, 2) bm_fused_kernel(IndexView ix, int level,
+                                                                   int l, int nb, QueryState st,
+                                                                   const LoopCtl *ctl)
+{
+    constexpr int MW = (NROW + 1) / 2;
+    __shared__ unsigned long long wmk[FL_WARPS][kSumWords][MW][32];
+    __shared__ uint32_t wlive[FL_WARPS][kSumWords];
+    if (ctl) level = ctl->level;
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int m = ix.m, nT = ix.nT;
+    const int nch = (nT + FL_TILES - 1) / FL_TILES;
+    const int64_t tasks = (int64_t)nb * nch;
+    const int par = level & 1;
+    unsigned long long p_items = 0, p_groups = 0, p_words = 0;
+    for (int64_t k = (int64_t)blockIdx.x * FL_WARPS + wi; k < tasks;
+         k += (int64_t)gridDim.x * FL_WARPS) {
+        const int q = (int)(k / nch);
+        const int t0 = (int)(k % nch) * FL_TILES, t1 = min(nT, t0 + FL_TILES);
+        if (!st.active[q] || level < st.start[q]) continue;
+        const bool first = level == st.start[q];
+        int64_t b0[NROW];
+        int32_t nbp[NROW];
+#pragma unroll
+        for (int r = 0; r < NROW; ++r) {
+            const int i = lane + 32 * r;
+            b0[r] = i < m ? st.bm_bq[(int64_t)q * m + i] : -1;
+            nbp[r] = i < m ? ix.bm_nb[i] : 0;
+        }
+        uint4 sv[NROW][2];
+        load_summaries<NROW>(ix, b0, nbp, t0, sv);
+        for (int t = t0; t < t1; ++t) {
+            const int64_t qt = (int64_t)q * nT + t;
+            int n_alive = 0;
+#pragma unroll
+            for (int w = 0; w < kSumWords; ++w) {
+                int cnt = 0;
+                unsigned long long mk[MW];
+#pragma unroll
+                for (int h = 0; h < MW; ++h) mk[h] = 0ull;
+#pragma unroll
+                for (int r = 0; r < NROW; ++r) {
+                    const uint32_t c = transpose32(word_of(sv[r][w >> 2], w & 3), lane);
+                    cnt += __popc(c);
+                    mk[r >> 1] |= (unsigned long long)c << (32 * (r & 1));
+                }
+#pragma unroll
+                for (int h = 0; h < MW; ++h) wmk[wi][w][h][lane] = mk[h];
+                const uint32_t xw = __ballot_sync(0xffffffffu, cnt >= l);
+                if (lane == 0) wlive[wi][w] = xw;
+                n_alive += __popc(xw);
+            }
+            __syncwarp();
+            // the next tile's summaries load while this tile is counted
+            if (t + 1 < t1) load_summaries<NROW>(ix, b0, nbp, t + 1, sv);
+            if (n_alive == 0) {
+                if (lane == 0) st.clist_n[(int64_t)par * st.cln_par + qt] = 0;
+                continue;
+            }
+            if (lane < kSumWords)
+                st.bm_amask[((int64_t)par * st.cln_par + qt) * kSumWords + lane] = wlive[wi][lane];
+            // this tile's bitmap numbers, one per lane and row
+            int64_t bt[NROW];
+#pragma unroll
+            for (int r = 0; r < NROW; ++r) bt[r] = b0[r] >= 0 ? b0[r] + (int64_t)t * nbp[r] : -1;
+            const int64_t pq = (int64_t)((level - 1) & 1) * st.cln_par + qt;
+            const bool tile_prev = !first && st.clist_n[pq] > 0;
+            int tile_n = 0;
+            for (int base = 0; base < n_alive; base += 32) {
+                // the (base + lane)-th live group of the tile
+                const int kk = base + lane;
+                int g = -1;
+                {
+                    int acc = 0;
+#pragma unroll
+                    for (int w = 0; w < kSumWords; ++w) {
+                        const uint32_t xw = wlive[wi][w];
+                        const int c = __popc(xw);
+                        if (g < 0 && kk < acc + c) g = w * 32 + nth_set_bit(xw, kk - acc);
+                        acc += c;
+                    }
+                }
+                unsigned long long mk[MW];
+#pragma unroll
+                for (int h = 0; h < MW; ++h)
+                    mk[h] = g >= 0 ? wmk[wi][g >> 5][h][g & 31] : 0ull;
+                const bool has_prev =
+                    g >= 0 && tile_prev &&
+                    ((st.bm_amask[pq * kSumWords + (g >> 5)] >> (g & 31)) & 1u);
+                const uint4 prev = has_prev ? st.cbits[(int64_t)((level - 1) & 1) * st.cb_par +
+                                                       qt * kBmUint4 + g]
+                                            : make_uint4(0, 0, 0, 0);
+                Planes P;
+#pragma unroll
+                for (int kq = 0; kq < 7; ++kq)
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) P.s[kq][w] = 0;
+                int words = 0;
+#pragma unroll
+                for (int h = 0; h < MW; ++h) words += __popcll(mk[h]);
+                for (int i0 = 0; i0 < m; i0 += 8) {
+                    uint4 xv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int i = i0 + u;
+                        const int r = i >> 5;
+                        int64_t bn = 0;
+#pragma unroll
+                        for (int rr = 0; rr < NROW; ++rr)
+                            if (rr == r) bn = __shfl_sync(0xffffffffu, bt[rr], i & 31);
+                        const bool on = i < m && ((mk[i >> 6] >> (i & 63)) & 1ull);
+                        xv[u] = on ? __ldg(ix.bm + bn * kBmUint4 + g) : make_uint4(0, 0, 0, 0);
+                    }
+                    add8(P, xv);
+                }
+                uint4 cand = make_uint4(0, 0, 0, 0);
+                int nc = 0;
+                if (g >= 0) {
+                    cand = candidates_of(P, l);
+                    st.cbits[(int64_t)par * st.cb_par + qt * kBmUint4 + g] = cand;
+                    nc = __popc(cand.x) + __popc(cand.y) + __popc(cand.z) + __popc(cand.w);
+                    p_words += (unsigned long long)words;
+                }
+                // list positions: one reservation per warp
+                int incl = nc;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                    if (lane >= off) incl += y;
+                }
+                const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                int pos0 = 0;
+                if (lane == 0 && tot)
+                    pos0 = atomicAdd(st.qbuf_n + (int64_t)par * st.qbn_par + q, tot);
+                pos0 = __shfl_sync(0xffffffffu, pos0, 0);
+                if (nc)
+                    append_candidates(P, cand, prev,
+                                      st.qbuf + (int64_t)par * st.qb_par + (int64_t)q * kQCap,
+                                      pos0 + incl - nc, (int64_t)t * kTile + (int64_t)g * 128);
+                tile_n += tot;
+            }
+            if (lane == 0) {
+                st.clist_n[(int64_t)par * st.cln_par + qt] = tile_n;
+                if (tile_n) atomicAdd(st.cross + q, tile_n);
+            }
+            p_items += 1;
+            p_groups += (unsigned long long)n_alive;
+        }
+    }
+    if (st.bm_prof) {
+        p_words = __reduce_add_sync(0xffffffffu, (unsigned)p_words);
+        if (lane == 0 && (p_items || p_words)) {
+            atomicAdd(st.bm_prof + 0, p_items);
+            atomicAdd(st.bm_prof + 1, p_groups);
+            atomicAdd(st.bm_prof + 2, p_words);
+        }
+    }
+}
+
 // ---- the same level with the bitmaps staged by TMA
 //
 // One persistent CTA per SM walks the (query, tile) items of the batch,
@@ -1038,56 +1225,51 @@ __global__ void __launch_bounds__(SEL_THREADS) bm_select_kernel(IndexView ix, in
 // level, that level can hold more.  Of them the k + v bound keeps only the
 // previous level's candidates, every candidate whose count is above the
 // boundary count c*, and the smallest original ids of the tie class at c*
-// (Section 3.1, readings R4/R5).  These kernels rebuild the list of such a
-// query with only those entries, from the candidate words of its last level
+// (Section 3.1, readings R4/R5).  The kernels below rebuild the list of such
+// a query with only those entries, from the candidate words of its last level
 // (still in place: a stopped query's tiles are not touched by later levels)
-// and the level bitmaps:
-//   pass 0  per candidate: its count, recounted from the m bitmap words of
-//           its 128-id group, and whether it was a candidate at the previous
-//           level (that level's candidate word, or, at a learned first level,
-//           its count there from the bitmaps of that level); the histogram
-//           of the counts of the others, and how many previous ones;
-//   plan 0  c* and how many ids at c* are kept, as the selection computes
-//           them; if the whole tie class does not fit the list,
-//   pass 1  a histogram of the tie class's original ids in kRdBins bins;
-//   plan 1  the bin holding the take-th smallest of them: the tie class is
-//           listed up to that bin (at most take + one bin of ids);
-//   pass 2  the kept entries, written as the count kernels write them;
-//   plan 2  the list's length.
+// and the level bitmaps, each read once:
+//   rd_compact  lists the overflowing queries (slots) and their buckets;
+//   rd_count    one thread per 128-id group holding candidates: the counts
+//               from the m bitmap words of the last level, the previous
+//               level's candidate word (at a learned first level: their
+//               counts there, from that level's bitmaps), stored as seven bit
+//               planes and the word (128 bytes per group); the histogram of
+//               the counts of the candidates not of the previous level;
+//   rd_plan 0   c* and how many ids at c* are kept, as the selection derives
+//               them;
+//   rd_scan     when the tie class at c* holds more than kRdTieList ids: walks
+//               the original ids upward (data id -> internal id -> candidate
+//               word, stored count, previous-level word) and lists the take
+//               smallest tie members, so that the list stays short;
+//   rd_emit     the other kept entries (and a short tie class) from the
+//               stored planes, written as the count kernels write them;
+//   rd_plan 2   the list lengths.
 // The selection then runs on the rebuilt list as on any other, with the same
 // result as from the whole list.  A query whose rebuilt list would still
-// overflow keeps the level-path answer.
-constexpr int kRdBins = 4096;
-constexpr int RD_THREADS = kBmUint4;  // one thread per 128-id group of a tile
-static_assert(kRdBins <= kEqCap, "tie-class id bins share the tie list");
+// overflow keeps the level-path answer, and so do the slots beyond one
+// store's worth (kRdStoreBytes).
+constexpr int kRdTieList = 4096;   // larger tie classes are cut by the original-id walk
+constexpr int kRdStoreWords = 8;  // uint4 per group: 7 count planes, previous-level word
+constexpr int RD_THREADS = 256;
+static_assert(RD_THREADS == kBmUint4, "one block covers the groups of one tile");
 
-__global__ void bm_rd_compact_kernel(QueryState st, int nb, RdPlan *plan, int32_t *rd_n,
-                                     int32_t *hist)
+// The candidate word of group g at level L (zero where the level wrote none).
+__device__ __forceinline__ uint4 rd_word(const QueryState &st, int L, int64_t qt, int g, bool tma)
 {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nb) return;
-    const int L = st.levels[q] - 1;
-    if (L < 0 || st.qbuf_n[(int64_t)(L & 1) * st.qbn_par + q] <= kQCap) return;
-    const int slot = atomicAdd(rd_n, 1);
-    RdPlan p;
-    p.q = q;
-    p.np = 0;
-    p.cstar = 0;
-    p.take = 0;
-    p.mode = 1;
-    p.bound = kRdBins - 1;
-    p.pos = 0;
-    p.pad = 0;
-    plan[slot] = p;
-    for (int c = 0; c < kHistBins; ++c) hist[(int64_t)slot * kHistBins + c] = 0;
+    const int64_t pc = (int64_t)(L & 1) * st.cln_par + qt;
+    if (st.clist_n[pc] == 0) return make_uint4(0, 0, 0, 0);
+    if (!tma && !((st.bm_amask[pc * kSumWords + (g >> 5)] >> (g & 31)) & 1u))
+        return make_uint4(0, 0, 0, 0);
+    return st.cbits[(int64_t)(L & 1) * st.cb_par + qt * kBmUint4 + g];
 }
 
-// Bit planes of one 128-id group's counts from the bitmaps bn[i] (-1: the
-// bucket holds no data) whose summaries sm[i] touch the group.
-__device__ __forceinline__ void group_planes(const IndexView &ix, const int64_t *bn,
-                                             const uint32_t (*sm)[kSumWords], int m, int g,
-                                             Planes &P)
+// Count planes of group g of tile t from the bitmaps of one level: bq[i] is
+// the bucket's bitmap in tile 0 (-1: no data), tile t adds t * bm_nb[i].
+__device__ __forceinline__ void rd_planes(const IndexView &ix, const int64_t *bq, int t, int g,
+                                          Planes &P)
 {
+    const int m = ix.m;
 #pragma unroll
     for (int kk = 0; kk < 7; ++kk)
 #pragma unroll
@@ -1097,8 +1279,9 @@ __device__ __forceinline__ void group_planes(const IndexView &ix, const int64_t 
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int i = i0 + u;
-            const bool touch = i < m && ((sm[i][g >> 5] >> (g & 31)) & 1u);
-            x[u] = touch ? __ldg(ix.bm + bn[i] * kBmUint4 + g) : make_uint4(0, 0, 0, 0);
+            const int64_t b = i < m ? bq[i] : -1;
+            x[u] = b >= 0 ? __ldg(ix.bm + (b + (int64_t)t * ix.bm_nb[i]) * kBmUint4 + g)
+                          : make_uint4(0, 0, 0, 0);
         }
         add8(P, x);
     }
@@ -1113,202 +1296,126 @@ __device__ __forceinline__ uint32_t count_eq_planes(const Planes &P, int w, int 
     return eq;
 }
 
-// The histogram is cumulative: hist[c] = candidates not of the previous level
-// whose count is >= c (c = l .. m), summed from the bit planes without a
-// per-candidate loop.
-template <int PASS>
-__global__ void __launch_bounds__(RD_THREADS) bm_rd_pass_kernel(IndexView ix, int l, int cgrow,
-                                                                QueryState st, RdPlan *plan,
-                                                                const int32_t *rd_n,
-                                                                int32_t *hist, bool tma)
+__global__ void rd_compact_kernel(IndexView ix, int cgrow, QueryState st, int nb)
 {
-    __shared__ int64_t bnL[QW_MAX_M], bnP[QW_MAX_M];
-    __shared__ uint32_t smL[QW_MAX_M][kSumWords], smP[QW_MAX_M][kSumWords];
-    __shared__ int sh_hist[kHistBins];
-    __shared__ int sh_np;
-    const int m = ix.m, nT = ix.nT;
-    const int nslot = *rd_n;
-    const int g = threadIdx.x, lane = threadIdx.x & 31;
-    const int64_t binw = (ix.n + kRdBins - 1) / kRdBins;
-    for (int64_t it = blockIdx.x; it < (int64_t)nslot * nT; it += gridDim.x) {
-        const int slot = (int)(it / nT), t = (int)(it % nT);
-        const RdPlan pl = plan[slot];
-        if (pl.mode == 0 || (PASS == 1 && pl.mode != 2)) continue;
-        const int q = pl.q;
-        const int L = st.levels[q] - 1;
-        const int64_t qt = (int64_t)q * nT + t;
-        const int64_t pcur = (int64_t)(L & 1) * st.cln_par + qt;
-        if (st.clist_n[pcur] == 0) continue;  // no candidate in this tile
-        const int64_t R = st.finalR[q];
-        // the previous level: its candidate words if this query counted it,
-        // else (learned first level L > 0) recounted from its bitmaps
-        const bool prev_words = L - 1 >= st.start[q];
-        const bool prev_recount = !prev_words && L > 0;
-        for (int e = threadIdx.x; e < m * (kSumWords + 1); e += RD_THREADS) {
-            const int i = e / (kSumWords + 1), w = e % (kSumWords + 1);
-            const int64_t gi = st.g[(int64_t)q * m + i];
-            const int64_t b1 = bm_index(ix, i, t, L, R, floordiv64(gi, R));
-            const int64_t b2 = prev_recount
-                                   ? bm_index(ix, i, t, L - 1, R / cgrow, floordiv64(gi, R / cgrow))
-                                   : -1;
-            if (w == kSumWords) {
-                bnL[i] = b1;
-                bnP[i] = b2;
-            } else {
-                smL[i][w] = b1 >= 0 ? ix.bm_sum[b1 * kSumWords + w] : 0u;
-                smP[i][w] = b2 >= 0 ? ix.bm_sum[b2 * kSumWords + w] : 0u;
-            }
-        }
-        if (PASS == 0) {
-            for (int c = threadIdx.x; c < kHistBins; c += RD_THREADS) sh_hist[c] = 0;
-            if (threadIdx.x == 0) sh_np = 0;
-        }
-        __syncthreads();
-        const bool live = tma || ((st.bm_amask[pcur * kSumWords + (g >> 5)] >> (g & 31)) & 1u);
-        const uint4 cw = live ? st.cbits[(int64_t)(L & 1) * st.cb_par + qt * kBmUint4 + g]
-                              : make_uint4(0, 0, 0, 0);
-        const bool any = (cw.x | cw.y | cw.z | cw.w) != 0u;
-        uint4 pw = make_uint4(0, 0, 0, 0);
-        Planes P;
-        if (any) {
-            if (prev_words) {
-                const int64_t pp = (int64_t)((L - 1) & 1) * st.cln_par + qt;
-                const bool pv = st.clist_n[pp] > 0 &&
-                                (tma || ((st.bm_amask[pp * kSumWords + (g >> 5)] >> (g & 31)) & 1u));
-                if (pv) pw = st.cbits[(int64_t)((L - 1) & 1) * st.cb_par + qt * kBmUint4 + g];
-            } else if (prev_recount) {
-                group_planes(ix, bnP, smP, m, g, P);
-                pw = candidates_of(P, l);
-            }
-            group_planes(ix, bnL, smL, m, g, P);
-        }
-        if (PASS == 0) {
-            int my_np = 0;
-#pragma unroll
-            for (int w = 0; w < 4; ++w) my_np += __popc(word_of(cw, w) & word_of(pw, w));
-            my_np = __reduce_add_sync(0xffffffffu, my_np);
-            if (lane == 0 && my_np) atomicAdd(&sh_np, my_np);
-            // cumulative counts from m down to l (the warp's threads agree on c)
-            for (int c = m; c >= l; --c) {
-                int nge = 0;
-                if (any) {
-#pragma unroll
-                    for (int w = 0; w < 4; ++w)
-                        nge += __popc(count_ge_planes(P, w, c) & word_of(cw, w) & ~word_of(pw, w));
-                }
-                nge = __reduce_add_sync(0xffffffffu, nge);
-                if (lane == 0 && nge) atomicAdd(&sh_hist[c], nge);
-            }
-        } else if (any) {
-            // PASS 1: id bins of the tie class; PASS 2: the kept entries
-            uint4 keep;
-            int my_n = 0;
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                const uint32_t c_w = word_of(cw, w), p_w = word_of(pw, w);
-                const uint32_t oth = c_w & ~p_w;
-                const uint32_t above = pl.cstar < m ? count_ge_planes(P, w, pl.cstar + 1) & oth : 0u;
-                const uint32_t tie = count_eq_planes(P, w, pl.cstar) & oth;
-                uint32_t kw = (c_w & p_w) | above;
-                if (pl.mode == 1) {
-                    kw |= tie;
-                } else {
-                    uint32_t x = tie;
-                    while (x) {
-                        const int b = __ffs(x) - 1;
-                        x &= x - 1;
-                        const int64_t iid = (int64_t)t * kTile + (int64_t)g * 128 + w * 32 + b;
-                        const int bin = (int)((int64_t)ix.perm[iid] / binw);
-                        if (PASS == 1) atomicAdd(st.eqbuf + (int64_t)q * kEqCap + bin, 1);
-                        else if (bin <= pl.bound) kw |= 1u << b;
-                    }
-                }
-                if (w == 0) keep.x = kw;
-                else if (w == 1) keep.y = kw;
-                else if (w == 2) keep.z = kw;
-                else keep.w = kw;
-                my_n += __popc(kw);
-            }
-            if (PASS == 2 && my_n) {
-                uint64_t *E = st.qbuf + (int64_t)(L & 1) * st.qb_par + (int64_t)q * kQCap;
-                int pos = atomicAdd(&plan[slot].pos, my_n);
-#pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                    uint32_t x = word_of(keep, w);
-                    const uint32_t p_w = word_of(pw, w);
-                    while (x) {
-                        const int b = __ffs(x) - 1;
-                        x &= x - 1;
-                        const int64_t iid = (int64_t)t * kTile + (int64_t)g * 128 + w * 32 + b;
-                        if (pos < kQCap)
-                            E[pos] = ((uint64_t)iid << 32) | ((uint64_t)((p_w >> b) & 1u) << 8) |
-                                     (uint64_t)count_of(P, w, b);
-                        ++pos;
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        if (PASS == 0) {
-            for (int c = threadIdx.x; c < kHistBins; c += RD_THREADS)
-                if (sh_hist[c]) atomicAdd(hist + (int64_t)slot * kHistBins + c, sh_hist[c]);
-            if (threadIdx.x == 0 && sh_np) atomicAdd(&plan[slot].np, sh_np);
-        }
-        __syncthreads();  // shared arrays are rewritten by the next item
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nb) return;
+    const int L = st.levels[q] - 1;
+    if (L < 0 || st.qbuf_n[(int64_t)(L & 1) * st.qbn_par + q] <= kQCap) return;
+    const int slot = atomicAdd(st.rd_ctl, 1);
+    RdPlan p;
+    memset(&p, 0, sizeof(p));
+    p.q = q;
+    p.mode = 1;
+    p.prev_recount = (L - 1 < st.start[q] && L > 0) ? 1 : 0;
+    st.rd_plan[slot] = p;
+    int32_t *h = st.rd_hist + (int64_t)slot * kHistBins;
+    for (int c = 0; c < kHistBins; ++c) h[c] = 0;
+    const int64_t R = st.finalR[q];
+    int64_t *bq = st.rd_bq + (int64_t)slot * 2 * QW_MAX_M;
+    for (int i = 0; i < ix.m; ++i) {
+        const int64_t gi = st.g[(int64_t)q * ix.m + i];
+        bq[i] = bm_index(ix, i, 0, L, R, floordiv64(gi, R));
+        bq[QW_MAX_M + i] =
+            L > 0 ? bm_index(ix, i, 0, L - 1, R / cgrow, floordiv64(gi, R / cgrow)) : -1;
     }
 }
 
-__global__ void bm_rd_plan_kernel(int l, int m, int cap, int cgrow, QueryState st, RdPlan *plan,
-                                  const int32_t *rd_n, const int32_t *hist, int stage)
+// One block per (slot, tile) at a time, one thread per group.
+__global__ void __launch_bounds__(RD_THREADS, 2) rd_count_kernel(IndexView ix, int l,
+                                                                  QueryState st, bool tma, int s0,
+                                                                  int wave)
 {
-    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-    if (slot >= *rd_n) return;
-    RdPlan p = plan[slot];
-    if (p.mode == 0) return;
+    __shared__ int sh_hist[kHistBins];
+    const int nslot = min(st.rd_ctl[0] - s0, wave);
+    const int nT = ix.nT, g = threadIdx.x;
+    for (int64_t it = blockIdx.x; it < (int64_t)max(nslot, 0) * nT; it += gridDim.x) {
+        const int slot = s0 + (int)(it / nT), t = (int)(it % nT);
+        const RdPlan pl = st.rd_plan[slot];
+        const int q = pl.q, L = st.levels[q] - 1;
+        const int64_t qt = (int64_t)q * nT + t;
+        if (st.clist_n[(int64_t)(L & 1) * st.cln_par + qt] == 0) continue;  // block-uniform
+        for (int c = threadIdx.x; c < kHistBins; c += RD_THREADS) sh_hist[c] = 0;
+        __syncthreads();
+        const uint4 cw = rd_word(st, L, qt, g, tma);
+        int my_np = 0;
+        if (cw.x | cw.y | cw.z | cw.w) {
+            const int64_t *bq = st.rd_bq + (int64_t)slot * 2 * QW_MAX_M;
+            Planes P;
+            uint4 pw = make_uint4(0, 0, 0, 0);
+            if (pl.prev_recount) {
+                rd_planes(ix, bq + QW_MAX_M, t, g, P);
+                pw = candidates_of(P, l);
+            } else if (L > 0) {
+                pw = rd_word(st, L - 1, qt, g, tma);
+            }
+            rd_planes(ix, bq, t, g, P);
+            uint4 *store = st.rd_store +
+                           ((int64_t)(slot - s0) * nT * kBmUint4 + (int64_t)t * kBmUint4 + g) *
+                               kRdStoreWords;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) store[k] = make_uint4(P.s[k][0], P.s[k][1], P.s[k][2], P.s[k][3]);
+            store[7] = pw;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                my_np += __popc(word_of(cw, w) & word_of(pw, w));
+                uint32_t x = word_of(cw, w) & ~word_of(pw, w);
+                while (x) {
+                    const int b = __ffs(x) - 1;
+                    x &= x - 1;
+                    atomicAdd(&sh_hist[count_of(P, w, b)], 1);
+                }
+            }
+        }
+        my_np = __reduce_add_sync(0xffffffffu, my_np);
+        if ((threadIdx.x & 31) == 0 && my_np) atomicAdd(&st.rd_plan[slot].np, my_np);
+        __syncthreads();
+        int32_t *h = st.rd_hist + (int64_t)slot * kHistBins;
+        for (int c = threadIdx.x; c < kHistBins; c += RD_THREADS)
+            if (sh_hist[c]) atomicAdd(h + c, sh_hist[c]);
+        __syncthreads();
+    }
+}
+
+__global__ void rd_plan_kernel(int l, int m, int cap, int cgrow, QueryState st, int s0, int wave,
+                               int stage)
+{
+    const int nslot = min(st.rd_ctl[0] - s0, wave);
+    const int slot = s0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= s0 + nslot) return;
+    RdPlan p = st.rd_plan[slot];
     const int q = p.q;
     const int L = st.levels[q] - 1;
     if (stage == 0) {
+        if (!p.prev_recount) p.np = st.nprev[q];
         if (st.recount[q] && (st.finalR[q] / cgrow > st.top[q] || p.np >= cap)) {
             // a learned first level after the level where the plain path stops:
             // answered again from level 0
             atomicOr(st.bm_ovf + q, 2);
             p.mode = 0;
         } else {
-            // cumulative: h[c] = candidates not of the previous level with count >= c
-            const int32_t *h = hist + (int64_t)slot * kHistBins;
+            // histogram of counts -> the count c* at which the bound is reached
+            const int32_t *h = st.rd_hist + (int64_t)slot * kHistBins;
             const int need = cap - p.np;
-            int cstar = -1;
+            int acc = 0, cstar = -1, take = 0;
             for (int c = m; c >= l; --c) {
-                if (h[c] >= need) {
+                if (acc + h[c] >= need) {
                     cstar = c;
+                    take = need - acc;
                     break;
                 }
+                acc += h[c];
             }
             if (cstar < 0) {
-                p.mode = 0;  // fewer candidates than the bound: cannot overflow
+                p.mode = 0;  // cannot happen for a list that overflowed
             } else {
-                const int above = cstar < m ? h[cstar + 1] : 0;
                 p.cstar = cstar;
-                p.take = need - above;
-                if ((int64_t)p.np + h[cstar] <= kQCap) {
-                    p.mode = 1;
-                } else {
-                    p.mode = 2;
-                    for (int b = 0; b < kRdBins; ++b) st.eqbuf[(int64_t)q * kEqCap + b] = 0;
-                }
+                p.take = take;
+                // a short tie class is listed whole, a long one cut by rd_scan
+                p.mode = h[cstar] <= kRdTieList ? 1 : 2;
             }
         }
-    } else if (stage == 1) {
-        if (p.mode == 2) {
-            const int32_t *ih = st.eqbuf + (int64_t)q * kEqCap;
-            int acc = 0, b = 0;
-            for (; b < kRdBins - 1; ++b) {
-                acc += ih[b];
-                if (acc >= p.take) break;
-            }
-            p.bound = b;
-        }
-    } else {
+    } else if (p.mode != 0) {
         // the rebuilt list (more than kQCap entries: the level path answers)
         st.qbuf_n[(int64_t)(L & 1) * st.qbn_par + q] = p.pos;
         st.bm_ovf[q] |= 4;
@@ -1317,7 +1424,133 @@ __global__ void bm_rd_plan_kernel(int l, int m, int cap, int cgrow, QueryState s
             st.recount[q] = 0;
         }
     }
-    plan[slot] = p;
+    st.rd_plan[slot] = p;
+}
+
+// The stored planes of group g of tile t of a slot.
+__device__ __forceinline__ void rd_stored(const QueryState &st, int slot, int nT, int t, int g,
+                                          Planes &P, uint4 &pw)
+{
+    const uint4 *store = st.rd_store +
+                         ((int64_t)slot * nT * kBmUint4 + (int64_t)t * kBmUint4 + g) * kRdStoreWords;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const uint4 v = store[k];
+        P.s[k][0] = v.x;
+        P.s[k][1] = v.y;
+        P.s[k][2] = v.z;
+        P.s[k][3] = v.w;
+    }
+    pw = store[7];
+}
+
+// The kept entries of every rebuilt slot, one thread per group: previous-level
+// candidates, counts above c*, and (a short tie class) the tie class.
+__global__ void __launch_bounds__(RD_THREADS, 3) rd_emit_kernel(IndexView ix, QueryState st,
+                                                                 bool tma, int wave)
+{
+    const int nslot = min(st.rd_ctl[0], wave);
+    const int m = ix.m, nT = ix.nT, g = threadIdx.x;
+    for (int64_t it = blockIdx.x; it < (int64_t)nslot * nT; it += gridDim.x) {
+        const int slot = (int)(it / nT), t = (int)(it % nT);
+        const RdPlan pl = st.rd_plan[slot];
+        if (pl.mode == 0) continue;
+        const int q = pl.q, L = st.levels[q] - 1;
+        const int64_t qt = (int64_t)q * nT + t;
+        const uint4 cw = rd_word(st, L, qt, g, tma);
+        if (!(cw.x | cw.y | cw.z | cw.w)) continue;
+        Planes P;
+        uint4 pw;
+        rd_stored(st, slot, nT, t, g, P, pw);
+        uint4 keep;
+        int my_n = 0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const uint32_t c_w = word_of(cw, w), p_w = word_of(pw, w);
+            const uint32_t oth = c_w & ~p_w;
+            uint32_t kw = (c_w & p_w) | (pl.cstar < m ? count_ge_planes(P, w, pl.cstar + 1) & oth : 0u);
+            if (pl.mode == 1) kw |= count_eq_planes(P, w, pl.cstar) & oth;
+            if (w == 0) keep.x = kw;
+            else if (w == 1) keep.y = kw;
+            else if (w == 2) keep.z = kw;
+            else keep.w = kw;
+            my_n += __popc(kw);
+        }
+        if (my_n) {
+            uint64_t *E = st.qbuf + (int64_t)(L & 1) * st.qb_par + (int64_t)q * kQCap;
+            int pos = atomicAdd(&st.rd_plan[slot].pos, my_n);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                uint32_t x = word_of(keep, w);
+                const uint32_t p_w = word_of(pw, w);
+                while (x) {
+                    const int b = __ffs(x) - 1;
+                    x &= x - 1;
+                    const int64_t iid = (int64_t)t * kTile + (int64_t)g * 128 + w * 32 + b;
+                    if (pos < kQCap)
+                        E[pos] = ((uint64_t)iid << 32) | ((uint64_t)((p_w >> b) & 1u) << 8) |
+                                 (uint64_t)count_of(P, w, b);
+                    ++pos;
+                }
+            }
+        }
+    }
+}
+
+// One block per slot with a long tie class: data ids 0, 1, 2, ... are tested
+// 256 at a time (tie member: a candidate of the last level, not of the
+// previous one, with count c*) until `take` members are found; those are the
+// take smallest original ids of the tie class (reading R5), listed with count
+// c*.  The walk reads about take * n / (tie class size) ids.
+__global__ void __launch_bounds__(RD_THREADS) rd_scan_kernel(IndexView ix, QueryState st,
+                                                              bool tma, int wave)
+{
+    __shared__ int s_wc[RD_THREADS / 32];
+    __shared__ int s_base;
+    const int nslot = min(st.rd_ctl[0], wave);
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    for (int slot = blockIdx.x; slot < nslot; slot += gridDim.x) {
+        const RdPlan pl = st.rd_plan[slot];
+        if (pl.mode != 2 || pl.take <= 0) continue;
+        const int q = pl.q, L = st.levels[q] - 1;
+        uint64_t *E = st.qbuf + (int64_t)(L & 1) * st.qb_par + (int64_t)q * kQCap;
+        if (threadIdx.x == 0) s_base = atomicAdd(&st.rd_plan[slot].pos, pl.take);
+        __syncthreads();
+        const int base = s_base;
+        int found = 0;
+        for (int64_t o0 = 0; o0 < ix.n && found < pl.take; o0 += RD_THREADS) {
+            const int64_t o = o0 + threadIdx.x;
+            bool tie = false;
+            int64_t iid = 0;
+            if (o < ix.n) {
+                iid = ix.inv[o];
+                const int t = (int)(iid / kTile), g = (int)((iid % kTile) >> 7), b = (int)(iid & 127);
+                const int64_t qt = (int64_t)q * ix.nT + t;
+                const uint4 cw = rd_word(st, L, qt, g, tma);
+                if ((word_of(cw, b >> 5) >> (b & 31)) & 1u) {
+                    Planes P;
+                    uint4 pw;
+                    rd_stored(st, slot, ix.nT, t, g, P, pw);
+                    tie = !((word_of(pw, b >> 5) >> (b & 31)) & 1u) &&
+                          count_of(P, b >> 5, b & 31) == pl.cstar;
+                }
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, tie);
+            if (lane == 0) s_wc[wi] = __popc(bal);
+            __syncthreads();
+            int before = 0, total = 0;
+#pragma unroll
+            for (int w = 0; w < RD_THREADS / 32; ++w) {
+                if (w < wi) before += s_wc[w];
+                total += s_wc[w];
+            }
+            const int rank = found + before + __popc(bal & ((1u << lane) - 1u));
+            if (tie && rank < pl.take && base + rank < kQCap)
+                E[base + rank] = ((uint64_t)iid << 32) | (uint64_t)pl.cstar;
+            found += total;
+            __syncthreads();  // s_wc is rewritten next
+        }
+    }
 }
 
 // Learned starts on the bitmap path: a query that stopped at its first level
@@ -1695,12 +1928,33 @@ ScanStats scan_stats_of(const IndexView &ix, int c)
 }
 
 qw_status launch_bm_level(const IndexView &ix, int nb, int level, int64_t R, int64_t Rp, int l,
-                          int cgrow, QueryState &st, int *err, bool tma, cudaStream_t s,
+                          int cgrow, QueryState &st, int *err, int loads, cudaStream_t s,
                           const LoopCtl *ctl, int part)
 {
     (void)Rp;
     (void)cgrow;
-    if (!tma) {
+    if (loads == QW_LOADS_FUSED) {
+        if (part != 2) {
+            const int64_t qi = (int64_t)nb * ix.m;
+            bm_bucket_kernel<<<(unsigned)std::max<int64_t>(
+                                   1, std::min<int64_t>((qi + 255) / 256, 152 * 8)),
+                               256, 0, s>>>(ix, level, R, nb, st, ctl);
+            QW_CUDA_TRY(cudaGetLastError());
+        }
+        if (part == 1) return QW_OK;
+        const int64_t tasks = (int64_t)nb * ((ix.nT + FL_TILES - 1) / FL_TILES);
+        const int blocks = (int)std::max<int64_t>(
+            1, std::min<int64_t>((tasks + FL_WARPS - 1) / FL_WARPS, 152 * 16));
+        if (ix.m <= 32)
+            bm_fused_kernel<1><<<blocks, FL_WARPS * 32, 0, s>>>(ix, level, l, nb, st, ctl);
+        else if (ix.m <= 64)
+            bm_fused_kernel<2><<<blocks, FL_WARPS * 32, 0, s>>>(ix, level, l, nb, st, ctl);
+        else
+            bm_fused_kernel<4><<<blocks, FL_WARPS * 32, 0, s>>>(ix, level, l, nb, st, ctl);
+        QW_CUDA_TRY(cudaGetLastError());
+        return QW_OK;
+    }
+    if (loads == QW_LOADS_DIRECT) {
         // two passes: filter on the summaries, then count the live groups
         if (part != 2) {
             const int64_t qi = (int64_t)nb * ix.m;
@@ -1793,29 +2047,28 @@ qw_status launch_bm_collect(const IndexView &ix, int nb, int l, int cap, QuerySt
     return QW_OK;
 }
 
+int bm_reduce_wave(int nT)
+{
+    return (int)std::max<int64_t>(1, kRdStoreBytes / ((int64_t)nT * kBmUint4 * kRdStoreWords * 16));
+}
+
 qw_status launch_bm_reduce(const IndexView &ix, int nb, int l, int cap, int cgrow,
-                           QueryState &st, bool tma, cudaStream_t s)
+                           QueryState &st, bool tma, int wave_slots, cudaStream_t s)
 {
     if (nb == 0) return QW_OK;
-    QW_CUDA_TRY(cudaMemsetAsync(st.rd_n, 0, sizeof(int32_t), s));
+    QW_CUDA_TRY(cudaMemsetAsync(st.rd_ctl, 0, sizeof(int32_t), s));
     const unsigned qb = (unsigned)((nb + 127) / 128);
-    bm_rd_compact_kernel<<<qb, 128, 0, s>>>(st, nb, st.rd_plan, st.rd_n, st.rd_hist);
+    rd_compact_kernel<<<qb, 128, 0, s>>>(ix, cgrow, st, nb);
     QW_CUDA_TRY(cudaGetLastError());
-    const unsigned grid = 152 * 4;
-    bm_rd_pass_kernel<0><<<grid, RD_THREADS, 0, s>>>(ix, l, cgrow, st, st.rd_plan, st.rd_n,
-                                                    st.rd_hist, tma);
-    QW_CUDA_TRY(cudaGetLastError());
-    bm_rd_plan_kernel<<<qb, 128, 0, s>>>(l, ix.m, cap, cgrow, st, st.rd_plan, st.rd_n, st.rd_hist, 0);
-    QW_CUDA_TRY(cudaGetLastError());
-    bm_rd_pass_kernel<1><<<grid, RD_THREADS, 0, s>>>(ix, l, cgrow, st, st.rd_plan, st.rd_n,
-                                                    st.rd_hist, tma);
-    QW_CUDA_TRY(cudaGetLastError());
-    bm_rd_plan_kernel<<<qb, 128, 0, s>>>(l, ix.m, cap, cgrow, st, st.rd_plan, st.rd_n, st.rd_hist, 1);
-    QW_CUDA_TRY(cudaGetLastError());
-    bm_rd_pass_kernel<2><<<grid, RD_THREADS, 0, s>>>(ix, l, cgrow, st, st.rd_plan, st.rd_n,
-                                                    st.rd_hist, tma);
-    QW_CUDA_TRY(cudaGetLastError());
-    bm_rd_plan_kernel<<<qb, 128, 0, s>>>(l, ix.m, cap, cgrow, st, st.rd_plan, st.rd_n, st.rd_hist, 2);
+    // one store's worth of slots (wave_slots); queries past it keep the
+    // level-path answer
+    const unsigned grid = 152 * 6;
+    const unsigned pb = (unsigned)((wave_slots + 127) / 128);
+    rd_count_kernel<<<grid, RD_THREADS, 0, s>>>(ix, l, st, tma, 0, wave_slots);
+    rd_plan_kernel<<<pb, 128, 0, s>>>(l, ix.m, cap, cgrow, st, 0, wave_slots, 0);
+    rd_scan_kernel<<<152 * 4, RD_THREADS, 0, s>>>(ix, st, tma, wave_slots);
+    rd_emit_kernel<<<grid, RD_THREADS, 0, s>>>(ix, st, tma, wave_slots);
+    rd_plan_kernel<<<pb, 128, 0, s>>>(l, ix.m, cap, cgrow, st, 0, wave_slots, 2);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }

@@ -64,9 +64,11 @@ struct DevBuf {
 // FP64 recomputation of every entry near a bucket boundary.  err (device int)
 // gets bit 1 set when a bucket id falls outside int32.  fixups (device
 // unsigned long long, may be null) counts FP64 recomputations.
+// tensor_cores (m <= 128): the projection on the tensor cores (split BF16
+// products, FP32 accumulation) with its own proven bound; same bucket ids.
 qw_status launch_hash(const float *V, int64_t nv, int d, const float *A, const float *b, int m,
                       float w, int32_t *H, int64_t ld_row, int64_t ld_col, int *err,
-                      unsigned long long *fixups, cudaStream_t s);
+                      unsigned long long *fixups, cudaStream_t s, bool tensor_cores = false);
 
 // ---------------------------------------------------------------- index build
 qw_status launch_minmax(const int32_t *Ht, int64_t n, int m, int32_t *hmin, int32_t *hmax,
@@ -143,10 +145,11 @@ struct RdPlan {
     int32_t np;     // candidates of the previous level
     int32_t cstar;  // boundary count
     int32_t take;   // ids kept at the boundary count
-    int32_t mode;   // 0: not rebuilt, 1: whole tie class listed, 2: tie class listed by id bins
-    int32_t bound;  // mode 2: last original-id bin listed
+    int32_t mode;   // 0: not rebuilt, 1: whole tie class listed, 2: its take smallest ids
+    int32_t pad0;
     int32_t pos;    // entries of the rebuilt list
-    int32_t pad;
+    int32_t prev_recount;  // learned first level: previous level from its bitmaps
+    int32_t pad[8];
 };
 
 // Per-batch query state, all device arrays of length nb (or nb x m).
@@ -196,9 +199,11 @@ struct QueryState {
     int32_t *recount = nullptr;     // per query: stopped at its learned first level (bitmap path)
     // bitmap path, last levels whose candidates overflowed the list: the
     // number of such queries, per slot its plan and its count histogram
-    int32_t *rd_n = nullptr;
+    int32_t *rd_ctl = nullptr;      // [0]: slots
     struct RdPlan *rd_plan = nullptr;
-    int32_t *rd_hist = nullptr;     // slots x kHistBins
+    int32_t *rd_hist = nullptr;     // slots x kHistBins: counts of candidates not of C_{R/c}
+    int64_t *rd_bq = nullptr;       // slots x 2 x QW_MAX_M: bitmap numbers in tile 0 (L, L - 1)
+    uint4 *rd_store = nullptr;      // per slot of a wave, per group: 7 count planes + prev word
     // bitmap path, two-pass level: item slots (query, tile) with their m bitmap
     // numbers, and the work list of live (slot << 8 | group) entries
     int32_t *bm_nitems = nullptr;   // 2 counters: items, work entries (per level)
@@ -266,17 +271,24 @@ qw_status launch_bitmap_build(const IndexView &ix, int c, int maxJ, const int32_
 qw_status launch_bid_prefix(const IndexView &ix, int64_t *prefix, const int64_t *off,
                             cudaStream_t s);
 ScanStats scan_stats_of(const IndexView &ix, int c);
-// tma: stage the bitmaps with TMA bulk copies in a persistent kernel (else
-// plain loads, one CTA per (tile, query)); err bit 4: a staged-copy wait gave up.
-// part (direct loads): 0 every launch of the level, 1 the bucket numbers (and
-// the profile counters), 2 the summary filter and the count pass.
+// loads: QW_LOADS_TMA stages the bitmaps with TMA bulk copies in a persistent
+// kernel; QW_LOADS_DIRECT filters on the summaries, then counts the live groups
+// in a second launch; QW_LOADS_FUSED does both in one launch.  err bit 4: a
+// staged-copy wait gave up.
+// part (direct and fused loads): 0 every launch of the level, 1 the bucket
+// numbers, 2 the summary filter and the count pass (and the profile counters).
 qw_status launch_bm_level(const IndexView &ix, int nb, int level, int64_t R, int64_t Rp, int l,
-                          int cgrow, QueryState &st, int *err, bool tma, cudaStream_t s,
+                          int cgrow, QueryState &st, int *err, int loads, cudaStream_t s,
                           const LoopCtl *ctl = nullptr, int part = 0);
 // Rebuild the candidate lists of the queries whose last level overflowed them
 // (kept entries and tie class only); tma: the level ran bm_level_tma_kernel.
 qw_status launch_bm_reduce(const IndexView &ix, int nb, int l, int cap, int cgrow,
-                           QueryState &st, bool tma, cudaStream_t s);
+                           QueryState &st, bool tma, int wave_slots, cudaStream_t s);
+// Bytes of the rebuild's plane store, and how many slots it holds for an index
+// of nT tiles (more overflowing queries in one batch keep the level-path
+// answer).
+constexpr int64_t kRdStoreBytes = (int64_t)1 << 32;
+int bm_reduce_wave(int nT);
 // sorted: the kept lists in ascending original id (else in no particular order)
 qw_status launch_bm_collect(const IndexView &ix, int nb, int l, int cap, QueryState &st,
                             int64_t *stats_out, bool sorted, cudaStream_t s);
@@ -301,7 +313,7 @@ struct LevelGraphCache;
 LevelGraphCache *level_graph_cache_new();
 void level_graph_cache_free(LevelGraphCache *c);
 qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l, int cgrow,
-                          int cap, bool learned, bool bitmap, bool tma, QueryState &st,
+                          int cap, bool learned, bool bitmap, int loads, QueryState &st,
                           LoopCtl *ctl, int *err, cudaStream_t s);
 qw_status launch_collect(const IndexView &ix, int nb, int l, int cap, QueryState &st,
                          int64_t *stats_out, cudaStream_t s);

@@ -112,7 +112,7 @@ def test_l2_split_arguments_of_the_binding(qwlib):
             qwlib._l2_fields(bad)
     qp = qwlib.qw_query_params(**qwlib._l2_fields(990))
     assert qp.l2_mode == qwlib.QW_L2_SPLIT and qp.l2_index_permille == 990
-    assert list(qp.reserved) == [0]
+    assert qp.projection == qwlib.QW_PROJ_FP32
 
 
 def test_host_bitmaps_need_bitmaps_without_device(qwlib):

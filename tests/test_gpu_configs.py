@@ -36,7 +36,7 @@ def _case(name):
 
 
 @pytest.mark.parametrize("name", list(CONFIGS))
-@pytest.mark.parametrize("path", ["levels", "bitmap_direct", "bitmap_graph"])
+@pytest.mark.parametrize("path", ["levels", "bitmap_direct", "bitmap_graph", "bitmap_fused_graph"])
 def test_config_parity(qwlib, cuda, name, path):
     wl, l, ref = _case(name)
     s = wl.spec

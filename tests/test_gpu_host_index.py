@@ -42,7 +42,7 @@ def test_host_bitmaps_match_oracle(qwlib, cuda):
     assert index.info.device_bytes + info.bitmap_bytes == dev.info.device_bytes
     dev.free()
     for graph in (False, True):
-        for loads in ("direct", "tma"):  # the TMA variant reads host bitmaps directly too
+        for loads in ("direct", "tma", "fused"):  # TMA reads host bitmaps directly too
             ids, dists, st = index.query(Q, s.k, stats=True, path="bitmap", graph=graph,
                                          loads=loads, order="signature", batch=17)
             cid, ccol, st2 = index.candidates(Q, s.k, path="bitmap", graph=graph, loads=loads)

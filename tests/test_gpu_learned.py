@@ -125,7 +125,8 @@ def test_learned_start_same_results_fewer_levels(qwlib, cuda, w):
     # bitmap path, host loop and graph mode: it starts at the predicted last
     # level itself (the previous level's candidates are recounted), so it
     # skips at least as many levels
-    for graph, loads in ((False, "tma"), (True, "tma"), (False, "direct"), (True, "direct")):
+    for graph, loads in ((False, "tma"), (True, "tma"), (False, "direct"), (True, "direct"),
+                         (False, "fused"), (True, "fused")):
         ids5, d5, st5 = index.query(Q, 20, stats=True, start="learned", path="bitmap", graph=graph,
                                     loads=loads)
         prof5 = index.profile(reset=True)
@@ -145,7 +146,7 @@ def test_learned_start_same_results_fewer_levels(qwlib, cuda, w):
     # on the bitmap path an over-eager start leaves some queries whose
     # previous level already met the stop rule: they are answered again by the
     # bitmap path from level 0 (none of them needs the level path)
-    for graph, loads in ((False, "direct"), (True, "direct"), (True, "tma")):
+    for graph, loads in ((False, "direct"), (True, "direct"), (True, "tma"), (True, "fused")):
         ids6, d6, st6 = index.query(Q, 20, stats=True, start="learned", path="bitmap",
                                     graph=graph, loads=loads)
         prof6 = index.profile(reset=True)

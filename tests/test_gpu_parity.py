@@ -19,7 +19,8 @@ TILE = 32768
 # in graph mode; "bitmap_direct": summary filter then counts of the live groups
 # by plain loads; "bitmap_direct_graph": the same in graph mode)
 PATHS = pytest.mark.parametrize("path", ["levels", "cluster", "graph", "bitmap", "bitmap_graph",
-                                         "bitmap_direct", "bitmap_direct_graph"])
+                                         "bitmap_direct", "bitmap_direct_graph", "bitmap_fused",
+                                         "bitmap_fused_graph"])
 
 
 def _t(x, dev):
@@ -67,10 +68,12 @@ def _gpu_workload(qw, dev, X, Q, A, b, *, w, k, v, l, c=2, batch=0, host=False, 
         Xd, Qd, Ad, bd = _t(X, dev), _t(Q, dev), _t(A, dev), _t(b, dev)
     index = qw.Index(Xd, Ad, bd, w=w, c=c, v=v, l=l, shadow_bf16=(rerank == "bf16"),
                      bitmaps=path.startswith("bitmap"))
-    graph = path in ("graph", "bitmap_graph", "bitmap_direct_graph")
-    loads = "direct" if path.startswith("bitmap_direct") else "tma"
+    graph = path in ("graph", "bitmap_graph", "bitmap_direct_graph", "bitmap_fused_graph")
+    loads = ("direct" if path.startswith("bitmap_direct") else
+             "fused" if path.startswith("bitmap_fused") else "tma")
     path = {"graph": "levels", "bitmap_graph": "bitmap", "bitmap_direct": "bitmap",
-            "bitmap_direct_graph": "bitmap"}.get(path, path)
+            "bitmap_direct_graph": "bitmap", "bitmap_fused": "bitmap",
+            "bitmap_fused_graph": "bitmap"}.get(path, path)
     ids, dists, st = index.query(Qd, k, batch=batch, stats=True, path=path, order=order,
                                  rerank=rerank, graph=graph, loads=loads)
     cid, ccol, st2 = index.candidates(Qd, k, batch=batch, path=path, order=order, graph=graph,
@@ -159,16 +162,39 @@ def test_seeded_projections_and_getter(orc, qwlib, cuda):
 
 
 # ---------------------------------------------------------------- a1 + a2: hashing
+@pytest.mark.parametrize("tc", [False, True], ids=["fp32", "tensor"])
 @pytest.mark.parametrize("n,d,m,scale", [(10_000, 32, 16, 1.0), (1_007, 33, 5, 3.0),
-                                         (20_000, 128, 64, 1.0), (4_099, 512, 7, 0.5)])
-def test_hash_bit_exact(orc, qwlib, cuda, n, d, m, scale):
+                                         (20_000, 128, 64, 1.0), (4_099, 512, 7, 0.5),
+                                         (3_000, 64, 128, 2.0), (129, 200, 100, 1.0)])
+def test_hash_bit_exact(orc, qwlib, cuda, n, d, m, scale, tc):
+    """FP32 CUDA-core and tensor-core projections (several 128-row tiles and a
+    ragged one, d not a multiple of the staged chunk, m not a multiple of 16)
+    against the FP64 definition."""
     wl = workloads.make_workload("mix10k_d32", seed=n, n=n, nq=1, d=d, m=m)
     X = (wl.X * scale).astype(np.float32)
     want = orc.hash(X, wl.A, wl.b, 4.0)
-    H, fix = qwlib.hash(_t(X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), 4.0)
+    H, fix = qwlib.hash(_t(X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), 4.0, tensor_cores=tc)
     got = H.cpu().numpy()
     assert np.array_equal(got, want), f"{int((got != want).sum())} bucket ids differ"
-    assert fix >= 0
+    assert 0 <= fix <= want.size * (0.2 if tc else 0.05)
+
+
+def test_hash_tensor_cores_on_1e8_entries(qwlib, cuda):
+    """The tensor-core projection's window holds on 2,000,000 rows x 64
+    projections (1.28e8 entries, d = 128, the benchmark's data scale): its
+    bucket ids equal those of the FP32 pass (itself exact against the FP64
+    definition), and the share recomputed in FP64 stays small."""
+    import torch
+    g = torch.Generator(device=cuda).manual_seed(11)
+    n, d, m = 2_000_000, 128, 64
+    X = torch.randn((n, d), generator=g, device=cuda, dtype=torch.float32) * 1.0
+    X += torch.rand((n // 1000 + 1, d), generator=g, device=cuda).repeat_interleave(1000, 0)[:n] * 20 - 10
+    A = torch.randn((m, d), generator=g, device=cuda, dtype=torch.float32)
+    b = torch.rand((m,), generator=g, device=cuda, dtype=torch.float32) * 4.0
+    H1, fix1 = qwlib.hash(X.contiguous(), A, b, 4.0)
+    H2, fix2 = qwlib.hash(X.contiguous(), A, b, 4.0, tensor_cores=True)
+    assert torch.equal(H1, H2)
+    assert fix2 < 0.1 * n * m, f"{fix2} recomputations"
 
 
 def test_hash_boundary_points_take_fp64(orc, qwlib, cuda):
@@ -184,9 +210,32 @@ def test_hash_boundary_points_take_fp64(orc, qwlib, cuda):
     target = np.round(t0 / w) * w + rng.uniform(-1e-6, 1e-6, size=t0.shape) * w
     X = (X0 + np.outer(target - t0, a0) / (a0 @ a0)).astype(np.float32)
     want = orc.hash(X, A, b, w)
-    H, fix = qwlib.hash(_t(X, cuda), _t(A, cuda), _t(b, cuda), w)
-    assert np.array_equal(H.cpu().numpy(), want)
-    assert fix >= 2000, f"only {fix} entries were recomputed in FP64"
+    for tc in (False, True):
+        H, fix = qwlib.hash(_t(X, cuda), _t(A, cuda), _t(b, cuda), w, tensor_cores=tc)
+        assert np.array_equal(H.cpu().numpy(), want)
+        assert fix >= 2000, f"only {fix} entries were recomputed in FP64"
+
+
+@pytest.mark.parametrize("path", ["levels", "bitmap_direct_graph"])
+def test_workload_with_tensor_core_projection(orc, qwlib, cuda, path):
+    """Index built and queries projected on the tensor cores: the oracle's
+    statistics, candidates and results."""
+    import torch
+    wl = workloads.make_workload("mix10k_d32", seed=17, n=9000, nq=60, d=48, m=24)
+    l = orc.threshold(24, 4.0, 2, 9000, 80)
+    H, HQ, oidx, ref = _oracle_run(orc, wl.X, wl.Q, wl.A, wl.b, 4.0, 10, 80, l)
+    index = qwlib.Index(_t(wl.X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=4.0, v=80, l=l,
+                        bitmaps=True, projection="tensor")
+    o, span, _, _ = index.export()
+    assert np.array_equal(o, oidx.o) and np.array_equal(span, oidx.span)
+    graph = path.endswith("graph")
+    ids, dists, st = index.query(_t(wl.Q, cuda), 10, stats=True, projection="tensor",
+                                 path="bitmap" if path != "levels" else "levels", graph=graph,
+                                 loads="direct")
+    torch.cuda.synchronize()
+    _check_results(ids.cpu().numpy(), dists.cpu().numpy(), ref["ids"], ref["dists"])
+    assert np.array_equal(st.cpu().numpy(), ref["stats"])
+    index.free()
 
 
 # ---------------------------------------------------------------- a3: index build
@@ -561,7 +610,7 @@ def test_bitmap_path_overflow_from_clusters(orc, qwlib, cuda):
     X, Q, A, b, Qt = _cluster_overflow_case()
     kw = dict(w=4.0, k=10, v=90, l=10)
     ref, _ = _full_parity(orc, qwlib, cuda, X, Q, A, b, path="bitmap", **kw)
-    for path in ("bitmap_direct", "bitmap_direct_graph"):
+    for path in ("bitmap_direct", "bitmap_direct_graph", "bitmap_fused", "bitmap_fused_graph"):
         _check_same(qwlib, cuda, X, Q, A, b, ref, path=path, **kw)
     assert int((ref["stats"][:, 2] > 262_144).sum()) >= 10
     index = qwlib.Index(_t(X, cuda), _t(A, cuda), _t(b, cuda), w=4.0, v=90, l=10, bitmaps=True)
@@ -583,7 +632,8 @@ def test_bitmap_path_overflow_from_clusters(orc, qwlib, cuda):
     for eps in (0.02, 0.999):
         index.set_start_model(mlp, eps=eps)
         for path, graph, loads in (("bitmap", False, "direct"), ("bitmap", True, "direct"),
-                                   ("bitmap", True, "tma"), ("levels", False, "tma"),
+                                   ("bitmap", True, "tma"), ("bitmap", False, "fused"),
+                                   ("bitmap", True, "fused"), ("levels", False, "tma"),
                                    ("levels", True, "tma")):
             ids, dd, st = index.query(Qd, 10, stats=True, path=path, start="learned",
                                       graph=graph, loads=loads, profile=True)
