@@ -139,6 +139,19 @@ typedef struct {
     int32_t projection;   /* QW_PROJ_FP32 (default): the queries' projection on CUDA cores in
                              FP32; QW_PROJ_TENSOR: on the tensor cores (split BF16 products,
                              FP32 accumulation, m <= 128; see qw_hash_tc).  Same bucket ids */
+    int32_t rerank_rows;  /* tile shape of the distance kernels: candidate rows a warp takes
+                             at a time (2, 4 or 8; 0 = 4).  Same results */
+    int32_t tiles_per_warp; /* tile shape of the bitmap path's filter and fused kernels: id
+                             tiles a warp walks for one query (4, 8 or 16; 0 = 8).  Same
+                             results */
+    int32_t probes;       /* multi-probe (Section 2 on probing the neighbouring buckets of the
+                             query's bucket): at radius R an object collides on projection i
+                             when its level-R bucket floor(bid / R) lies within `probes` of the
+                             query's, i.e. bid in [(beta_i - probes) R, (beta_i + probes + 1) R
+                             - 1]; the radius rule then also waits for R > -g_i.  0 (default):
+                             the plain rule.  0..64; > 0 runs on the level path (QW_PATH_AUTO
+                             and QW_PATH_LEVELS; the bitmap and cluster paths refuse it).
+                             Changes the candidate sets, as it changes the method */
 } qw_query_params;
 
 /* Persisting-L2 modes (qw_query_params.l2_mode).  With a window mode the call
@@ -445,10 +458,11 @@ int32_t qw_l2_split_model(double setaside, double index_bytes, double index_read
                           double data_bytes, double data_reads);
 
 /* Read bandwidth of a device buffer of `bytes` bytes (a measuring tool; the
- * paper has no counterpart): the library allocates the buffer, reads all of it
- * `reps` + 1 times with 16-byte loads cached in L2 only, one launch per read,
- * and writes the best rate of the timed `reps` reads (CUDA events on
- * `stream`) to *gbs in GB/s.  A buffer well below the L2 size (126 MB usable
+ * paper has no counterpart): the library allocates the buffer and reads all of
+ * it with 16-byte loads cached in L2 only, one launch per read; after one
+ * untimed read it times `reps` measurements of back-to-back reads of about
+ * 2 GB each (CUDA events on `stream`) and writes the best rate to *gbs in
+ * GB/s.  A buffer well below the L2 size (126 MB usable
  * on GB300) gives the rate L2 delivers to the SMs -- the ceiling of kernels
  * whose reads hit L2 -- and one well above it the HBM rate.  Waits for the
  * stream.  Errors: QW_ERR_ARG (bytes < 16, reps < 1, null gbs), QW_ERR_OOM,

@@ -104,6 +104,26 @@ class Oracle:
         L.orc_range_count.argtypes = [_i32p, C.c_int64, C.c_int64, C.c_int64]
         L.orc_sqdist.restype = C.c_double
         L.orc_sqdist.argtypes = [_f32p, _f32p, C.c_int32]
+        L.orc_collision_counts_probes.restype = None
+        L.orc_collision_counts_probes.argtypes = [_i32p, C.c_int64, C.c_int32, _i32p, _i32p,
+                                                  C.c_int64, C.c_int32, _i32p]
+        L.orc_query_probes.restype = C.c_int
+        L.orc_query_probes.argtypes = [_f32p, C.c_int64, C.c_int32, _i32p, _i32p, _i32p,
+                                       C.c_int32, _opt(_i32p), _f32p, _i32p, C.c_int64,
+                                       C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                       _i64p, _f64p, _opt(_i64p), _opt(_i32p), _opt(_i64p)]
+        L.orc_project.restype = C.c_int
+        L.orc_project.argtypes = [_f32p, C.c_int64, C.c_int32, _f32p, C.c_int32, _f64p]
+        L.orc_qalsh_counts.restype = None
+        L.orc_qalsh_counts.argtypes = [_f64p, C.c_int64, C.c_int32, _f64p, C.c_double, C.c_int64,
+                                       _i32p]
+        L.orc_qalsh_query.restype = C.c_int
+        L.orc_qalsh_query.argtypes = [_f32p, C.c_int64, C.c_int32, _f64p, C.c_int32, _f32p, _f64p,
+                                      C.c_int64, C.c_double, C.c_int32, C.c_int32, C.c_int32,
+                                      C.c_int32, _i64p, _f64p, _opt(_i64p), _opt(_i32p),
+                                      _opt(_i64p)]
+        L.orc_qalsh_prob.restype = C.c_double
+        L.orc_qalsh_prob.argtypes = [C.c_double, C.c_double]
         L.orc_query.restype = C.c_int
         L.orc_query.argtypes = [_f32p, C.c_int64, C.c_int32, _i32p, _i32p, _i32p, C.c_int32,
                                 _opt(_i32p), _f32p, _i32p, C.c_int64, C.c_int32, C.c_int32,
@@ -150,11 +170,16 @@ class Oracle:
             raise OracleError(f"orc_build_index status {st}")
         return OracleIndex(H=H, o=o, span=span, sbid=sbid, sid=sid)
 
-    def collision_counts(self, index: OracleIndex, hq: np.ndarray, R: int) -> np.ndarray:
+    def collision_counts(self, index: OracleIndex, hq: np.ndarray, R: int,
+                         probes: int = 0) -> np.ndarray:
         n, m = index.H.shape
         col = np.empty(n, np.int32)
-        self.lib.orc_collision_counts(index.H, n, m, index.o,
-                                      np.ascontiguousarray(hq, np.int32), int(R), col)
+        hq = np.ascontiguousarray(hq, np.int32)
+        if probes:
+            self.lib.orc_collision_counts_probes(index.H, n, m, index.o, hq, int(R), int(probes),
+                                                 col)
+        else:
+            self.lib.orc_collision_counts(index.H, n, m, index.o, hq, int(R), col)
         return col
 
     def range_count(self, index: OracleIndex, i: int, lo: int, hi: int) -> int:
@@ -170,7 +195,7 @@ class Oracle:
     # -- the query workload ------------------------------------------------
     def query(self, X: np.ndarray, index: OracleIndex, Q: np.ndarray, HQ: np.ndarray, *,
               k: int, v: int, l: int, c: int = 2, want_candidates: bool = True,
-              want_stats: bool = True):
+              want_stats: bool = True, probes: int = 0):
         X = np.ascontiguousarray(X, np.float32)
         Q = np.ascontiguousarray(Q, np.float32)
         HQ = np.ascontiguousarray(HQ, np.int32)
@@ -183,8 +208,13 @@ class Oracle:
         cids = np.empty((nq, cap), np.int64) if want_candidates else None
         ccol = np.empty((nq, cap), np.int32) if want_candidates else None
         stats = np.empty((nq, NSTAT), np.int64) if want_stats else None
-        st = self.lib.orc_query(X, n, d, index.H, index.o, index.span, m, index.sbid, Q, HQ, nq,
-                                k, v, l, c, ids, dists, cids, ccol, stats)
+        if probes:
+            st = self.lib.orc_query_probes(X, n, d, index.H, index.o, index.span, m, index.sbid,
+                                           Q, HQ, nq, k, v, l, c, int(probes), ids, dists, cids,
+                                           ccol, stats)
+        else:
+            st = self.lib.orc_query(X, n, d, index.H, index.o, index.span, m, index.sbid, Q, HQ,
+                                    nq, k, v, l, c, ids, dists, cids, ccol, stats)
         if st != 0:
             raise OracleError(f"orc_query status {st}")
         out = {"ids": ids, "dists": dists}
@@ -194,6 +224,47 @@ class Oracle:
         if want_stats:
             out["stats"] = stats
         return out
+
+    # -- QALSH's query-aware buckets (reading R17) ---------------------------
+    def project(self, V: np.ndarray, A: np.ndarray) -> np.ndarray:
+        """a_i . v in double (nv x m), summed in coordinate order."""
+        V = np.ascontiguousarray(V, np.float32)
+        A = np.ascontiguousarray(A, np.float32)
+        P = np.empty((V.shape[0], A.shape[0]), np.float64)
+        st = self.lib.orc_project(V, V.shape[0], V.shape[1], A, A.shape[0], P)
+        if st != 0:
+            raise OracleError(f"orc_project status {st}")
+        return P
+
+    def qalsh_counts(self, P: np.ndarray, pq: np.ndarray, w: float, R: int) -> np.ndarray:
+        P = np.ascontiguousarray(P, np.float64)
+        col = np.empty(P.shape[0], np.int32)
+        self.lib.orc_qalsh_counts(P, P.shape[0], P.shape[1],
+                                  np.ascontiguousarray(pq, np.float64), float(w), int(R), col)
+        return col
+
+    def qalsh_prob(self, r: float, w: float) -> float:
+        return float(self.lib.orc_qalsh_prob(r, w))
+
+    def qalsh_query(self, X: np.ndarray, P: np.ndarray, Q: np.ndarray, PQ: np.ndarray, *,
+                    w: float, k: int, v: int, l: int, c: int = 2):
+        X = np.ascontiguousarray(X, np.float32)
+        Q = np.ascontiguousarray(Q, np.float32)
+        P = np.ascontiguousarray(P, np.float64)
+        PQ = np.ascontiguousarray(PQ, np.float64)
+        n, d = X.shape
+        nq, m = PQ.shape
+        cap = k + v
+        ids = np.empty((nq, k), np.int64)
+        dists = np.empty((nq, k), np.float64)
+        cids = np.empty((nq, cap), np.int64)
+        ccol = np.empty((nq, cap), np.int32)
+        stats = np.empty((nq, NSTAT), np.int64)
+        st = self.lib.orc_qalsh_query(X, n, d, P, m, Q, PQ, nq, float(w), k, v, l, c, ids, dists,
+                                      cids, ccol, stats)
+        if st != 0:
+            raise OracleError(f"orc_qalsh_query status {st}")
+        return {"ids": ids, "dists": dists, "cand_ids": cids, "cand_col": ccol, "stats": stats}
 
     def bruteforce(self, X: np.ndarray, Q: np.ndarray, k: int):
         X = np.ascontiguousarray(X, np.float32)

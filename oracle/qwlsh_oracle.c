@@ -183,17 +183,21 @@ static int64_t orc_floordiv(int64_t a, int64_t R)
  * projection i is floor(bid / R); a data object collides with the query on
  * projection i when floor(bid / R) == floor(g_i / R), g_i = h_i(q) - o_i.
  * Equivalently bid lies in [beta_i R, beta_i R + R - 1].  col[o] counts the
- * projections on which o collides (Section 3.1). */
-void orc_collision_counts(const int32_t *H, int64_t n, int32_t m, const int32_t *o,
-                          const int32_t *hq, int64_t R, int32_t *col)
+ * projections on which o collides (Section 3.1).
+ * With P probes per side (multi-probe: the neighbouring buckets of the query's
+ * bucket are looked into as well, Section 2 on Lv et al.; reading R16) the
+ * object collides when floor(bid / R) lies in [beta_i - P, beta_i + P], i.e.
+ * bid in [(beta_i - P) R, (beta_i + P + 1) R - 1].  P = 0 is the plain rule. */
+void orc_collision_counts_probes(const int32_t *H, int64_t n, int32_t m, const int32_t *o,
+                                 const int32_t *hq, int64_t R, int32_t probes, int32_t *col)
 {
     int64_t *lo = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
     int64_t *hi = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
     for (int32_t i = 0; i < m; ++i) {
         int64_t g = (int64_t)hq[i] - (int64_t)o[i];
         int64_t beta = orc_floordiv(g, R);
-        lo[i] = beta * R;
-        hi[i] = beta * R + R - 1;
+        lo[i] = (beta - probes) * R;
+        hi[i] = (beta + probes + 1) * R - 1;
     }
     for (int64_t j = 0; j < n; ++j) {
         int32_t cnt = 0;
@@ -206,6 +210,12 @@ void orc_collision_counts(const int32_t *H, int64_t n, int32_t m, const int32_t 
     }
     free(lo);
     free(hi);
+}
+
+void orc_collision_counts(const int32_t *H, int64_t n, int32_t m, const int32_t *o,
+                          const int32_t *hq, int64_t R, int32_t *col)
+{
+    orc_collision_counts_probes(H, n, m, o, hq, R, 0, col);
 }
 
 /* Number of sorted entries of projection i with bid in [lo, hi]: the range
@@ -284,15 +294,16 @@ static int orc_res_cmp(const void *pa, const void *pb)
  * ids, dists: nq x k.  cand_ids / cand_col (optional): nq x (k + v), the kept
  * candidates in truncation order, padded with -1 / 0.  stats (optional):
  * nq x ORC_NSTAT.  sbid (optional, m x n) is used only for the scan counts. */
-int orc_query(const float *X, int64_t n, int32_t d, const int32_t *H, const int32_t *o,
-              const int32_t *span, int32_t m, const int32_t *sbid,
-              const float *Q, const int32_t *HQ, int64_t nq, int32_t k, int32_t v,
-              int32_t l, int32_t c,
-              int64_t *ids, double *dists, int64_t *cand_ids, int32_t *cand_col,
-              int64_t *stats)
+int orc_query_probes(const float *X, int64_t n, int32_t d, const int32_t *H, const int32_t *o,
+                     const int32_t *span, int32_t m, const int32_t *sbid,
+                     const float *Q, const int32_t *HQ, int64_t nq, int32_t k, int32_t v,
+                     int32_t l, int32_t c, int32_t probes,
+                     int64_t *ids, double *dists, int64_t *cand_ids, int32_t *cand_col,
+                     int64_t *stats)
 {
     if (!X || !H || !o || !span || !Q || !HQ || !ids || !dists) return ORC_ERR_ARG;
-    if (n <= 0 || d <= 0 || m <= 0 || nq < 0 || k <= 0 || v < 0 || l < 1 || l > m || c < 2)
+    if (n <= 0 || d <= 0 || m <= 0 || nq < 0 || k <= 0 || v < 0 || l < 1 || l > m || c < 2 ||
+        probes < 0)
         return ORC_ERR_ARG;
     int64_t cap = (int64_t)k + (int64_t)v;
     int32_t *col = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
@@ -303,25 +314,30 @@ int orc_query(const float *X, int64_t n, int32_t d, const int32_t *H, const int3
 
     for (int64_t q = 0; q < nq; ++q) {
         const int32_t *hq = HQ + (size_t)q * m;
+        /* past radius `top` no level changes C_R: every data bid lies in
+         * [0, span_i]; without probes a query bid g_i < 0 never collides, with
+         * probes it does once R > -g_i (reading R16) */
         int64_t top = 0;
         for (int32_t i = 0; i < m; ++i) {
             int64_t g = (int64_t)hq[i] - (int64_t)o[i];
             if (span[i] > top) top = span[i];
             if (g > top) top = g;
+            if (probes > 0 && -g > top) top = -g;
         }
         memset(prev, 0, (size_t)n);
         int64_t R = 1, levels = 0, ncand = 0, nprev = 0, scanned_full = 0, scanned_last = 0;
         int term = 0;
         for (;;) {
             levels += 1;
-            orc_collision_counts(H, n, m, o, hq, R, col);
+            orc_collision_counts_probes(H, n, m, o, hq, R, probes, col);
             ncand = 0;
             for (int64_t j = 0; j < n; ++j) if (col[j] >= l) ncand += 1;
             if (sbid) {
                 scanned_last = 0;
                 for (int32_t i = 0; i < m; ++i) {
                     int64_t beta = orc_floordiv((int64_t)hq[i] - (int64_t)o[i], R);
-                    scanned_last += orc_range_count(sbid + (size_t)i * n, n, beta * R, beta * R + R - 1);
+                    scanned_last += orc_range_count(sbid + (size_t)i * n, n, (beta - probes) * R,
+                                                    (beta + probes + 1) * R - 1);
                 }
                 scanned_full += scanned_last;
             }
@@ -368,6 +384,164 @@ int orc_query(const float *X, int64_t n, int32_t d, const int32_t *H, const int3
     }
     free(col); free(prev); free(cs); free(rs);
     return ORC_OK;
+}
+
+int orc_query(const float *X, int64_t n, int32_t d, const int32_t *H, const int32_t *o,
+              const int32_t *span, int32_t m, const int32_t *sbid,
+              const float *Q, const int32_t *HQ, int64_t nq, int32_t k, int32_t v,
+              int32_t l, int32_t c,
+              int64_t *ids, double *dists, int64_t *cand_ids, int32_t *cand_col,
+              int64_t *stats)
+{
+    return orc_query_probes(X, n, d, H, o, span, m, sbid, Q, HQ, nq, k, v, l, c, 0, ids, dists,
+                            cand_ids, cand_col, stats);
+}
+
+/* ------------------------------------------------------------------------- */
+/* QALSH's query-aware buckets (Section 2; the base method of the paper's      */
+/* experiments, Section 6, w = 2.719): the hash function is the projection    */
+/* p_i(v) = a_i . v itself (no offset, no floor), and at level radius R the   */
+/* bucket of projection i is the interval of width w R centred on the query:  */
+/* an object collides with the query on projection i when                     */
+/*     |p_i(o) - p_i(q)| <= w R / 2        (reading R17).                     */
+/* Everything else -- counts, threshold l, the k + v stop, truncation order,  */
+/* top-k -- is as in orc_query.  Past the radius at which every projection's  */
+/* interval holds all the data no level changes C_R (the radius rule).        */
+/* ------------------------------------------------------------------------- */
+
+/* P (nv x m, row-major) = a_i . v in double, summed j = 0 .. d-1 in order. */
+int orc_project(const float *V, int64_t nv, int32_t d, const float *A, int32_t m, double *P)
+{
+    if (!V || !A || !P || nv < 0 || d <= 0 || m <= 0) return ORC_ERR_ARG;
+    for (int64_t r = 0; r < nv; ++r) {
+        const float *x = V + (size_t)r * d;
+        for (int32_t i = 0; i < m; ++i) {
+            const float *a = A + (size_t)i * d;
+            double t = 0.0;
+            for (int32_t j = 0; j < d; ++j) t = t + (double)a[j] * (double)x[j];
+            P[(size_t)r * m + i] = t;
+        }
+    }
+    return ORC_OK;
+}
+
+/* Collision counts at radius R: col[o] = #{ i : |P[o][i] - pq[i]| <= w R / 2 }. */
+void orc_qalsh_counts(const double *P, int64_t n, int32_t m, const double *pq, double w,
+                      int64_t R, int32_t *col)
+{
+    const double half = 0.5 * w * (double)R;
+    for (int64_t j = 0; j < n; ++j) {
+        int32_t cnt = 0;
+        for (int32_t i = 0; i < m; ++i) {
+            const double dlt = P[(size_t)j * m + i] - pq[i];
+            if (fabs(dlt) <= half) cnt += 1;
+        }
+        col[j] = cnt;
+    }
+}
+
+/* The query procedure with query-aware buckets.  P: n x m data projections,
+ * PQ: nq x m query projections (orc_project); stats as orc_query, with [5] /
+ * [6] the entries inside the last level's / every level's intervals. */
+int orc_qalsh_query(const float *X, int64_t n, int32_t d, const double *P, int32_t m,
+                    const float *Q, const double *PQ, int64_t nq, double w, int32_t k,
+                    int32_t v, int32_t l, int32_t c, int64_t *ids, double *dists,
+                    int64_t *cand_ids, int32_t *cand_col, int64_t *stats)
+{
+    if (!X || !P || !Q || !PQ || !ids || !dists) return ORC_ERR_ARG;
+    if (n <= 0 || d <= 0 || m <= 0 || nq < 0 || k <= 0 || v < 0 || l < 1 || l > m || c < 2 ||
+        !(w > 0.0))
+        return ORC_ERR_ARG;
+    int64_t cap = (int64_t)k + (int64_t)v;
+    int32_t *col = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    char *prev = (char *)malloc((size_t)n);
+    orc_cand *cs = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)n);
+    orc_res *rs = (orc_res *)malloc(sizeof(orc_res) * (size_t)(cap > 0 ? cap : 1));
+    double *pmin = (double *)malloc(sizeof(double) * (size_t)m);
+    double *pmax = (double *)malloc(sizeof(double) * (size_t)m);
+    if (!col || !prev || !cs || !rs || !pmin || !pmax) {
+        free(col); free(prev); free(cs); free(rs); free(pmin); free(pmax);
+        return ORC_ERR_OOM;
+    }
+    for (int32_t i = 0; i < m; ++i) {
+        pmin[i] = P[i];
+        pmax[i] = P[i];
+        for (int64_t j = 1; j < n; ++j) {
+            const double p = P[(size_t)j * m + i];
+            if (p < pmin[i]) pmin[i] = p;
+            if (p > pmax[i]) pmax[i] = p;
+        }
+    }
+    for (int64_t q = 0; q < nq; ++q) {
+        const double *pq = PQ + (size_t)q * m;
+        memset(prev, 0, (size_t)n);
+        int64_t R = 1, levels = 0, ncand = 0, nprev = 0, scanned_full = 0, scanned_last = 0;
+        int term = 0;
+        for (;;) {
+            levels += 1;
+            orc_qalsh_counts(P, n, m, pq, w, R, col);
+            ncand = 0;
+            scanned_last = 0;
+            for (int64_t j = 0; j < n; ++j) {
+                if (col[j] >= l) ncand += 1;
+                scanned_last += col[j];
+            }
+            scanned_full += scanned_last;
+            if (ncand >= cap) { term = 2; break; }
+            /* every interval holds all the data: no later level changes C_R */
+            int all = 1;
+            const double half = 0.5 * w * (double)R;
+            for (int32_t i = 0; i < m; ++i)
+                if (!(fabs(pmin[i] - pq[i]) <= half && fabs(pmax[i] - pq[i]) <= half)) all = 0;
+            if (all) { term = 3; break; }
+            nprev = ncand;
+            for (int64_t j = 0; j < n; ++j) prev[j] = (char)(col[j] >= l);
+            R *= c;
+        }
+        /* the stop level's candidates, truncated to k + v as in orc_query */
+        int64_t nc = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (col[j] >= l) {
+                cs[nc].prev = prev[j];
+                cs[nc].col = col[j];
+                cs[nc].id = j;
+                nc += 1;
+            }
+        }
+        qsort(cs, (size_t)nc, sizeof(orc_cand), orc_cand_cmp);
+        int64_t keep = nc < cap ? nc : cap;
+        if (cand_ids) {
+            for (int64_t t = 0; t < cap; ++t) {
+                cand_ids[(size_t)q * cap + t] = t < keep ? cs[t].id : -1;
+                if (cand_col) cand_col[(size_t)q * cap + t] = t < keep ? cs[t].col : 0;
+            }
+        }
+        const float *qv = Q + (size_t)q * d;
+        for (int64_t t = 0; t < keep; ++t) {
+            rs[t].id = cs[t].id;
+            rs[t].dist = orc_sqdist(X + (size_t)cs[t].id * d, qv, d);
+        }
+        qsort(rs, (size_t)keep, sizeof(orc_res), orc_res_cmp);
+        for (int32_t t = 0; t < k; ++t) {
+            ids[(size_t)q * k + t] = t < keep ? rs[t].id : -1;
+            dists[(size_t)q * k + t] = t < keep ? sqrt(rs[t].dist) : INFINITY;
+        }
+        if (stats) {
+            int64_t *st = stats + (size_t)q * ORC_NSTAT;
+            st[0] = levels; st[1] = R; st[2] = ncand; st[3] = keep;
+            st[4] = term; st[5] = scanned_last; st[6] = scanned_full; st[7] = nprev;
+        }
+    }
+    free(col); free(prev); free(cs); free(rs); free(pmin); free(pmax);
+    return ORC_OK;
+}
+
+/* QALSH's collision probability for two points at distance r with a bucket
+ * of width w centred on one of them: P(|N(0, r^2)| <= w / 2) = erf(w / (2 sqrt2 r)). */
+double orc_qalsh_prob(double r, double w)
+{
+    if (!(r > 0.0) || !(w > 0.0)) return NAN;
+    return erf(w / (2.0 * sqrt(2.0) * r));
 }
 
 /* Exact k nearest neighbours by FP64 distance, ties by id (ground truth for

@@ -53,7 +53,8 @@ class qw_query_params(C.Structure):
                 ("clusters", C.c_int32), ("order", C.c_int32), ("rerank", C.c_int32),
                 ("start", C.c_int32), ("graph", C.c_int32), ("bitmap_loads", C.c_int32),
                 ("l2_mode", C.c_int32), ("l2_index_permille", C.c_int32),
-                ("projection", C.c_int32)]
+                ("projection", C.c_int32), ("rerank_rows", C.c_int32),
+                ("tiles_per_warp", C.c_int32), ("probes", C.c_int32)]
 
 
 QW_TUNE_MAX = 32
@@ -344,7 +345,8 @@ def _params_kwargs(p) -> dict:
             "graph": bool(p.graph), "loads": inv(LOADS, p.bitmap_loads),
             "l2": (None if p.l2_mode == QW_L2_OFF else "model" if p.l2_mode == QW_L2_MODEL
                    else int(p.l2_index_permille)),
-            "projection": inv(PROJECTIONS, p.projection)}
+            "projection": inv(PROJECTIONS, p.projection), "rerank_rows": int(p.rerank_rows),
+            "tiles_per_warp": int(p.tiles_per_warp), "probes": int(p.probes)}
 
 
 def _stream_of(t) -> int:
@@ -456,7 +458,8 @@ class Index:
     def query(self, Q, k: int, *, batch: int = 0, stats: bool = False, out=None,
               profile: bool = False, path: str = "auto", clusters: int = 0,
               order: str = "auto", rerank: str = "fp32", start: str = "plain",
-              graph: bool = False, loads: str = "tma", l2=None, projection: str = "fp32"):
+              graph: bool = False, loads: str = "tma", l2=None, projection: str = "fp32",
+              rerank_rows: int = 0, tiles_per_warp: int = 0, probes: int = 0):
         """Top-k of every query row.  Returns (ids int64 nq x k, dists float32
         nq x k[, stats int64 nq x QW_NSTAT]) on Q's device (host tensors in,
         host tensors out).  ``out`` may give preallocated (ids, dists[, stats]).
@@ -481,13 +484,14 @@ class Index:
                              clusters=int(clusters), order=ORDERS[order], rerank=RERANKS[rerank],
                              start=STARTS[start], graph=1 if graph else 0,
                              bitmap_loads=LOADS[loads], projection=PROJECTIONS[projection],
-                             **_l2_fields(l2))
+                             rerank_rows=int(rerank_rows), tiles_per_warp=int(tiles_per_warp),
+                             probes=int(probes), **_l2_fields(l2))
         qw_run_workload(self._h, Q.data_ptr(), nq, int(k), qp, ids.data_ptr(), dists.data_ptr(),
                         st.data_ptr() if st is not None else 0, mem, _stream_of(Q))
         return (ids, dists, st) if stats else (ids, dists)
 
     def candidates(self, Q, k: int, *, batch: int = 0, path: str = "auto", order: str = "auto",
-                   graph: bool = False, loads: str = "tma"):
+                   graph: bool = False, loads: str = "tma", probes: int = 0):
         """Kept candidates per query (ascending ids, -1 padded) with their
         collision counts, and the per-query statistics, on Q's device."""
         torch = _torch()
@@ -499,7 +503,8 @@ class Index:
         st = torch.empty((nq, QW_NSTAT), dtype=torch.int64, device=Q.device)
         mem = _mem_of(Q, cid, ccol, st)
         qp = qw_query_params(batch=int(batch), path=PATHS[path], order=ORDERS[order],
-                             graph=1 if graph else 0, bitmap_loads=LOADS[loads])
+                             graph=1 if graph else 0, bitmap_loads=LOADS[loads],
+                             probes=int(probes))
         qw_workload_candidates(self._h, Q.data_ptr(), nq, int(k), qp, cid.data_ptr(),
                                ccol.data_ptr(), st.data_ptr(), mem, _stream_of(Q))
         return cid, ccol, st

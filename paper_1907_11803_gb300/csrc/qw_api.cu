@@ -646,7 +646,7 @@ static qw_status answer_again(qw_index *ix, const float *Qall, const int32_t *HQ
 // stopped); with learned starts, a second pass from level 0 for the queries
 // that stopped at their learned first level.
 static qw_status host_level_loop(qw_index *ix, LaunchTimer &tm, const IndexView &view, int nb,
-                                 int cap, bool learned, bool bitmap, int loads, int *err,
+                                 int cap, bool learned, bool bitmap, int loads, int tpw, int *err,
                                  QueryState &st, cudaStream_t s, int *levels_run)
 {
     unsigned long long max_top = 0;
@@ -660,12 +660,12 @@ static qw_status host_level_loop(qw_index *ix, LaunchTimer &tm, const IndexView 
                 // and count passes alone
                 QW_TRY(tm.run(QW_K_BUCKET, 1, [&] {
                     return launch_bm_level(view, nb, level, R, Rp, ix->l, ix->c, st, err, loads,
-                                           s, nullptr, 1);
+                                           s, nullptr, 1, tpw);
                 }));
                 const int nl = loads == QW_LOADS_FUSED ? 1 : (st.bm_prof ? 3 : 2);
                 QW_TRY(tm.run(QW_K_LEVEL, nl, [&] {
                     return launch_bm_level(view, nb, level, R, Rp, ix->l, ix->c, st, err, loads,
-                                           s, nullptr, 2);
+                                           s, nullptr, 2, tpw);
                 }));
             } else {
                 QW_TRY(tm.run(QW_K_LEVEL, 1, [&] {
@@ -776,6 +776,8 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     int eff_path = path;
     if (eff_path == QW_PATH_AUTO)
         eff_path = (ix->tuned && !learned && !graph) ? ix->tuned_path : QW_PATH_LEVELS;
+    // multi-probe runs on the level path only
+    if (qp && qp->probes > 0) eff_path = QW_PATH_LEVELS;
     if (path == QW_PATH_BITMAP && !ix->bitmaps) {
         set_error("qw_run_workload: QW_PATH_BITMAP needs an index built with bitmaps");
         return QW_ERR_ARG;
@@ -788,6 +790,8 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     int loads = qp ? qp->bitmap_loads : QW_LOADS_TMA;
     if (loads == QW_LOADS_TMA && ix->host_bitmaps) loads = QW_LOADS_DIRECT;
     const bool tma_loads = loads == QW_LOADS_TMA;
+    const int tpw = qp && qp->tiles_per_warp ? qp->tiles_per_warp : 8;
+    const int rr_rows = qp && qp->rerank_rows ? qp->rerank_rows : 4;
     // bitmap path, per query: two levels of (tile) candidate bitmaps and lists
     const int64_t cb_bytes = (int64_t)ix->nT * kBmUint4 * (int64_t)sizeof(uint4) * 2;
     // (per query: two levels of tile candidate counts and candidate lists)
@@ -882,6 +886,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                                up16(b_ccol) + 16));
     }
     QueryState st;
+    st.probes = qp ? qp->probes : 0;
     LoopCtl *ctl = nullptr;
     {
         char *p = ix->w_state.as<char>();
@@ -1103,11 +1108,11 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             if (graph) {
                 QW_TRY(tm.run(QW_K_LEVEL, 0, [&] {
                     return run_level_graph(ix->graphs, view, nb, ix->l, ix->c, cap, learned,
-                                           use_bitmap, loads, st, ctl, err, s,
+                                           use_bitmap, loads, tpw, st, ctl, err, s,
                                            l2.window(L2Use::Index));
                 }));
             } else {
-                QW_TRY(host_level_loop(ix, tm, view, nb, cap, learned, use_bitmap, loads, err,
+                QW_TRY(host_level_loop(ix, tm, view, nb, cap, learned, use_bitmap, loads, tpw, err,
                                        st, s, &levels_run));
             }
             QW_TRY(tm.run(QW_K_SELECT, use_bitmap ? (learned ? 3 : 2) : 2, [&] {
@@ -1136,14 +1141,16 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             QW_TRY(tm.run(QW_K_RERANK, 1, [&] {
                 return launch_rerank_bf16(view, ix->Xb.p, ix->xnorm.as<float>(), ix->Cg.p,
                                           Qb, nb, k, cap, st,
-                                          ids_b, dists_b, tm.on ? rows_ctr : nullptr, s);
+                                          ids_b, dists_b, tm.on ? rows_ctr : nullptr, s, rr_rows);
             }));
         else if (want_ids)
             QW_TRY(tm.run(QW_K_RERANK, 1, [&] {
                 // bitmap path: candidate rows from the locality-ordered copy
                 return use_bitmap ? launch_rerank(view, Qb, nb, k, cap, st, ids_b, dists_b, s,
-                                                  ix->Xloc.as<float>(), ix->inv.as<int32_t>())
-                                  : launch_rerank(view, Qb, nb, k, cap, st, ids_b, dists_b, s);
+                                                  ix->Xloc.as<float>(), ix->inv.as<int32_t>(),
+                                                  rr_rows)
+                                  : launch_rerank(view, Qb, nb, k, cap, st, ids_b, dists_b, s,
+                                                  nullptr, nullptr, rr_rows);
             }));
         if (want_ids && tm.on)
             QW_TRY(launch_sum_i32(st.nkeep, nb, cand_ctr, s));
@@ -1211,6 +1218,8 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
             p.start = QW_START_PLAIN;
             p.graph = graph ? 1 : 0;
             p.bitmap_loads = loads;
+            p.tiles_per_warp = qp ? qp->tiles_per_warp : 0;
+            p.rerank_rows = qp ? qp->rerank_rows : 0;
             QW_TRY(answer_again(ix, Qall, HQall, late_list, n_ovf[1], k, cap, f_ids, f_dists,
                                 f_stats, f_cids, f_ccol, s, &p));
         }
@@ -1279,6 +1288,16 @@ static qw_status check_workload_args(const qw_index *ix, const float *queries, i
             return arg_error("qw_run_workload: l2_index_permille must be in [0, 1000]");
         if (qp->projection != QW_PROJ_FP32 && qp->projection != QW_PROJ_TENSOR)
             return arg_error("qw_run_workload: unknown projection");
+        if (qp->probes < 0 || qp->probes > 64)
+            return arg_error("qw_run_workload: probes must be in [0, 64]");
+        if (qp->probes > 0 && (qp->path == QW_PATH_BITMAP || qp->path == QW_PATH_CLUSTER))
+            return arg_error("qw_run_workload: multi-probe (probes > 0) runs on the level path");
+        if (qp->rerank_rows != 0 && qp->rerank_rows != 2 && qp->rerank_rows != 4 &&
+            qp->rerank_rows != 8)
+            return arg_error("qw_run_workload: rerank_rows must be 0, 2, 4 or 8");
+        if (qp->tiles_per_warp != 0 && qp->tiles_per_warp != 4 && qp->tiles_per_warp != 8 &&
+            qp->tiles_per_warp != 16)
+            return arg_error("qw_run_workload: tiles_per_warp must be 0, 4, 8 or 16");
         if (qp->projection == QW_PROJ_TENSOR && ix->m > 128)
             return arg_error("qw_run_workload: QW_PROJ_TENSOR needs m <= 128");
     }
@@ -1415,7 +1434,8 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
             if ((status = try_alt(alt)) != QW_OK) break;
         }
         // 4. the bitmap path (when built): default batch, then its batch and graph
-        if (ix->bitmaps) {
+        //    (multi-probe runs on the level path only)
+        if (ix->bitmaps && p0.probes == 0) {
             const qw_query_params best_levels = cur;
             const float best_levels_ms = cur_ms;
             const int best_levels_slot = cur_slot;
@@ -1453,6 +1473,16 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
             alt = cur;
             alt.bitmap_loads = QW_LOADS_FUSED;
             if ((status = try_alt(alt)) != QW_OK) break;
+            // tile shape of the filter / fused kernels: tiles per warp
+            if (cur.bitmap_loads != QW_LOADS_TMA) {
+                const qw_query_params keept = cur;
+                for (int tw : {4, 16}) {
+                    qw_query_params a2 = keept;
+                    a2.tiles_per_warp = tw;
+                    if ((status = try_alt(a2)) != QW_OK) break;
+                }
+                if (status != QW_OK) break;
+            }
             if (best_levels_ms < cur_ms) {
                 cur = best_levels;
                 cur_ms = best_levels_ms;
@@ -1460,7 +1490,8 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
             }
         }
         // 5. path: the cluster path (plain starts only) against the best so far
-        if (cur.start == QW_START_PLAIN && cluster_path_fits(ix->view(), &csize, &tpc)) {
+        if (cur.start == QW_START_PLAIN && cur.probes == 0 &&
+            cluster_path_fits(ix->view(), &csize, &tpc)) {
             qw_query_params alt = cur;
             alt.path = QW_PATH_CLUSTER;
             alt.batch = 0;
@@ -1477,6 +1508,16 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
             qw_query_params alt = cur;
             alt.rerank = QW_RERANK_BF16;
             if ((status = try_alt(alt)) != QW_OK) break;
+        }
+        // tile shape of the rerank: candidate rows per warp
+        {
+            const qw_query_params keepr = cur;
+            for (int rows : {2, 8}) {
+                qw_query_params alt = keepr;
+                alt.rerank_rows = rows;
+                if ((status = try_alt(alt)) != QW_OK) break;
+            }
+            if (status != QW_OK) break;
         }
         // 8. the queries' projection on the tensor cores
         if (ix->m <= 128) {

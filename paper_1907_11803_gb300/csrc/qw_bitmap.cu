@@ -352,7 +352,7 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t a, int lane)
 // bit transpose of the lanes' rows gives lane g the projections touching group
 // w * 32 + g: their number decides whether the group is live, and the same
 // bits are the group's projection mask for pass 2.
-constexpr int FL_TILES = 8;
+constexpr int FL_TILES = 8;  // tiles per warp unless the caller picks 4 or 16
 
 template <int NROW>
 __device__ __forceinline__ void load_summaries(const IndexView &ix, const int64_t (&b0)[NROW],
@@ -373,7 +373,7 @@ __device__ __forceinline__ void load_summaries(const IndexView &ix, const int64_
     }
 }
 
-template <int NROW>
+template <int NROW, int TPW>
 __global__ void __launch_bounds__(FL_WARPS * 32, NROW <= 2 ? 3 : 2) bm_filter_kernel(IndexView ix, int level, int l,
                                                                   int nb, QueryState st,
                                                                   const LoopCtl *ctl)
@@ -385,13 +385,13 @@ __global__ void __launch_bounds__(FL_WARPS * 32, NROW <= 2 ? 3 : 2) bm_filter_ke
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const int m = ix.m, nT = ix.nT;
     const int mw = (m + 63) >> 6;
-    const int nch = (nT + FL_TILES - 1) / FL_TILES;
+    const int nch = (nT + TPW - 1) / TPW;
     const int64_t tasks = (int64_t)nb * nch;
     const int par = level & 1;
     for (int64_t k = (int64_t)blockIdx.x * FL_WARPS + (threadIdx.x >> 5); k < tasks;
          k += (int64_t)gridDim.x * FL_WARPS) {
         const int q = (int)(k / nch);
-        const int t0 = (int)(k % nch) * FL_TILES, t1 = min(nT, t0 + FL_TILES);
+        const int t0 = (int)(k % nch) * TPW, t1 = min(nT, t0 + TPW);
         if (!st.active[q] || level < st.start[q]) continue;
         int64_t b0[NROW];
         int32_t nbp[NROW];
@@ -573,7 +573,7 @@ __device__ __forceinline__ int nth_set_bit(uint32_t v, int n)
     return pos;
 }
 
-template <int NROW>
+template <int NROW, int TPW>
 __global__ void __launch_bounds__(FL_WARPS * 32, 2) bm_fused_kernel(IndexView ix, int level,
                                                                    int l, int nb, QueryState st,
                                                                    const LoopCtl *ctl)
@@ -584,14 +584,14 @@ __global__ void __launch_bounds__(FL_WARPS * 32, 2) bm_fused_kernel(IndexView ix
     if (ctl) level = ctl->level;
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const int m = ix.m, nT = ix.nT;
-    const int nch = (nT + FL_TILES - 1) / FL_TILES;
+    const int nch = (nT + TPW - 1) / TPW;
     const int64_t tasks = (int64_t)nb * nch;
     const int par = level & 1;
     unsigned long long p_items = 0, p_groups = 0, p_words = 0;
     for (int64_t k = (int64_t)blockIdx.x * FL_WARPS + wi; k < tasks;
          k += (int64_t)gridDim.x * FL_WARPS) {
         const int q = (int)(k / nch);
-        const int t0 = (int)(k % nch) * FL_TILES, t1 = min(nT, t0 + FL_TILES);
+        const int t0 = (int)(k % nch) * TPW, t1 = min(nT, t0 + TPW);
         if (!st.active[q] || level < st.start[q]) continue;
         const bool first = level == st.start[q];
         int64_t b0[NROW];
@@ -1927,9 +1927,41 @@ ScanStats scan_stats_of(const IndexView &ix, int c)
     return ss;
 }
 
+template <int TPW>
+static void launch_filter_or_fused(const IndexView &ix, int nb, int level, int l, QueryState &st,
+                                   const LoopCtl *ctl, bool fused, cudaStream_t s)
+{
+    const int64_t tasks = (int64_t)nb * ((ix.nT + TPW - 1) / TPW);
+    const int blocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>((tasks + FL_WARPS - 1) / FL_WARPS, 152 * 16));
+    if (fused) {
+        if (ix.m <= 32)
+            bm_fused_kernel<1, TPW><<<blocks, FL_WARPS * 32, 0, s>>>(ix, level, l, nb, st, ctl);
+        else if (ix.m <= 64)
+            bm_fused_kernel<2, TPW><<<blocks, FL_WARPS * 32, 0, s>>>(ix, level, l, nb, st, ctl);
+        else
+            bm_fused_kernel<4, TPW><<<blocks, FL_WARPS * 32, 0, s>>>(ix, level, l, nb, st, ctl);
+    } else {
+        if (ix.m <= 32)
+            bm_filter_kernel<1, TPW><<<blocks, FL_WARPS * 32, 0, s>>>(ix, level, l, nb, st, ctl);
+        else if (ix.m <= 64)
+            bm_filter_kernel<2, TPW><<<blocks, FL_WARPS * 32, 0, s>>>(ix, level, l, nb, st, ctl);
+        else
+            bm_filter_kernel<4, TPW><<<blocks, FL_WARPS * 32, 0, s>>>(ix, level, l, nb, st, ctl);
+    }
+}
+
+static void launch_filter_or_fused(const IndexView &ix, int nb, int level, int l, QueryState &st,
+                                   const LoopCtl *ctl, bool fused, int tpw, cudaStream_t s)
+{
+    if (tpw == 4) launch_filter_or_fused<4>(ix, nb, level, l, st, ctl, fused, s);
+    else if (tpw == 16) launch_filter_or_fused<16>(ix, nb, level, l, st, ctl, fused, s);
+    else launch_filter_or_fused<8>(ix, nb, level, l, st, ctl, fused, s);
+}
+
 qw_status launch_bm_level(const IndexView &ix, int nb, int level, int64_t R, int64_t Rp, int l,
                           int cgrow, QueryState &st, int *err, int loads, cudaStream_t s,
-                          const LoopCtl *ctl, int part)
+                          const LoopCtl *ctl, int part, int tpw)
 {
     (void)Rp;
     (void)cgrow;
@@ -1942,15 +1974,7 @@ qw_status launch_bm_level(const IndexView &ix, int nb, int level, int64_t R, int
             QW_CUDA_TRY(cudaGetLastError());
         }
         if (part == 1) return QW_OK;
-        const int64_t tasks = (int64_t)nb * ((ix.nT + FL_TILES - 1) / FL_TILES);
-        const int blocks = (int)std::max<int64_t>(
-            1, std::min<int64_t>((tasks + FL_WARPS - 1) / FL_WARPS, 152 * 16));
-        if (ix.m <= 32)
-            bm_fused_kernel<1><<<blocks, FL_WARPS * 32, 0, s>>>(ix, level, l, nb, st, ctl);
-        else if (ix.m <= 64)
-            bm_fused_kernel<2><<<blocks, FL_WARPS * 32, 0, s>>>(ix, level, l, nb, st, ctl);
-        else
-            bm_fused_kernel<4><<<blocks, FL_WARPS * 32, 0, s>>>(ix, level, l, nb, st, ctl);
+        launch_filter_or_fused(ix, nb, level, l, st, ctl, true, tpw, s);
         QW_CUDA_TRY(cudaGetLastError());
         return QW_OK;
     }
@@ -1964,15 +1988,7 @@ qw_status launch_bm_level(const IndexView &ix, int nb, int level, int64_t R, int
             QW_CUDA_TRY(cudaGetLastError());
         }
         if (part == 1) return QW_OK;
-        const int64_t tasks = (int64_t)nb * ((ix.nT + FL_TILES - 1) / FL_TILES);
-        const int fl_blocks = (int)std::max<int64_t>(
-            1, std::min<int64_t>((tasks + FL_WARPS - 1) / FL_WARPS, 152 * 16));
-        if (ix.m <= 32)
-            bm_filter_kernel<1><<<fl_blocks, FL_WARPS * 32, 0, s>>>(ix, level, l, nb, st, ctl);
-        else if (ix.m <= 64)
-            bm_filter_kernel<2><<<fl_blocks, FL_WARPS * 32, 0, s>>>(ix, level, l, nb, st, ctl);
-        else
-            bm_filter_kernel<4><<<fl_blocks, FL_WARPS * 32, 0, s>>>(ix, level, l, nb, st, ctl);
+        launch_filter_or_fused(ix, nb, level, l, st, ctl, false, tpw, s);
         QW_CUDA_TRY(cudaGetLastError());
         bm_count_kernel<<<152 * 8, 256, 0, s>>>(ix, level, l, st, ctl);
         QW_CUDA_TRY(cudaGetLastError());

@@ -29,7 +29,7 @@ namespace qw {
 struct GraphKey {
     int nb, l, cgrow, cap;
     bool learned, bitmap;
-    int loads;
+    int loads, tpw;
     QueryState st;         // every workspace pointer the graph's kernels take by value
     const void *lid;       // the index
     const void *ctl;
@@ -40,7 +40,7 @@ struct GraphKey {
     bool operator==(const GraphKey &o) const
     {
         return nb == o.nb && l == o.l && cgrow == o.cgrow && cap == o.cap &&
-               learned == o.learned && bitmap == o.bitmap && loads == o.loads &&
+               learned == o.learned && bitmap == o.bitmap && loads == o.loads && tpw == o.tpw &&
                memcmp(&st, &o.st, sizeof(QueryState)) == 0 && lid == o.lid && ctl == o.ctl &&
                err == o.err && win_base == o.win_base && win_bytes == o.win_bytes &&
                win_hit == o.win_hit;
@@ -139,7 +139,7 @@ qw_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
 }
 
 qw_status build(LevelGraphCache *c, const GraphKey &key, const IndexView &ix, int nb, int l,
-                int cgrow, int cap, bool learned, bool bitmap, int loads, QueryState &st,
+                int cgrow, int cap, bool learned, bool bitmap, int loads, int tpw, QueryState &st,
                 LoopCtl *ctl, int *err, const cudaAccessPolicyWindow &win,
                 cudaGraph_t *graph_out)
 {
@@ -164,7 +164,7 @@ qw_status build(LevelGraphCache *c, const GraphKey &key, const IndexView &ix, in
     auto level_body = [&](cudaGraphConditionalHandle h) {
         return [&, h] {
             if (bitmap)
-                QW_TRY(launch_bm_level(ix, nb, 0, 1, 1, l, cgrow, st, err, loads, cs, ctl));
+                QW_TRY(launch_bm_level(ix, nb, 0, 1, 1, l, cgrow, st, err, loads, cs, ctl, 0, tpw));
             else
                 QW_TRY(launch_level(ix, nb, 0, 1, 1, l, cgrow, st, cs, ctl));
             ScanStats ss = bitmap ? scan_stats_of(ix, cgrow) : ScanStats();
@@ -198,15 +198,15 @@ qw_status build(LevelGraphCache *c, const GraphKey &key, const IndexView &ix, in
 }  // namespace
 
 qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l, int cgrow,
-                          int cap, bool learned, bool bitmap, int loads, QueryState &st,
+                          int cap, bool learned, bool bitmap, int loads, int tpw, QueryState &st,
                           LoopCtl *ctl, int *err, cudaStream_t s)
 {
-    return run_level_graph(c, ix, nb, l, cgrow, cap, learned, bitmap, loads, st, ctl, err, s,
+    return run_level_graph(c, ix, nb, l, cgrow, cap, learned, bitmap, loads, tpw, st, ctl, err, s,
                            cudaAccessPolicyWindow{});
 }
 
 qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l, int cgrow,
-                          int cap, bool learned, bool bitmap, int loads, QueryState &st,
+                          int cap, bool learned, bool bitmap, int loads, int tpw, QueryState &st,
                           LoopCtl *ctl, int *err, cudaStream_t s,
                           const cudaAccessPolicyWindow &win)
 {
@@ -223,6 +223,7 @@ qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l
     key.learned = learned;
     key.bitmap = bitmap;
     key.loads = loads;
+    key.tpw = tpw;
     key.st = st;
     key.lid = ix.lid;
     key.ctl = ctl;
@@ -244,7 +245,7 @@ qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l
         c->entries.erase(c->entries.begin());
     }
     cudaGraph_t g = nullptr;
-    QW_TRY(build(c, key, ix, nb, l, cgrow, cap, learned, bitmap, loads, st, ctl, err, win, &g));
+    QW_TRY(build(c, key, ix, nb, l, cgrow, cap, learned, bitmap, loads, tpw, st, ctl, err, win, &g));
     cudaGraphExec_t ex = nullptr;
     const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
     if (e != cudaSuccess) {

@@ -154,6 +154,9 @@ struct RdPlan {
 
 // Per-batch query state, all device arrays of length nb (or nb x m).
 struct QueryState {
+    // multi-probe: buckets looked into on each side of the query's (0: none;
+    // level path only)
+    int32_t probes = 0;
     int64_t *g = nullptr;             // nb x m: h_i(q) - o_i
     int64_t *top = nullptr;           // nb: max_i max(span_i, g_i)
     int32_t *active = nullptr;        // nb
@@ -277,9 +280,10 @@ ScanStats scan_stats_of(const IndexView &ix, int c);
 // staged-copy wait gave up.
 // part (direct and fused loads): 0 every launch of the level, 1 the bucket
 // numbers, 2 the summary filter and the count pass (and the profile counters).
+// tpw: tiles a warp of the filter / fused kernel takes (4, 8 or 16; else 8).
 qw_status launch_bm_level(const IndexView &ix, int nb, int level, int64_t R, int64_t Rp, int l,
                           int cgrow, QueryState &st, int *err, int loads, cudaStream_t s,
-                          const LoopCtl *ctl = nullptr, int part = 0);
+                          const LoopCtl *ctl = nullptr, int part = 0, int tpw = 8);
 // Rebuild the candidate lists of the queries whose last level overflowed them
 // (kept entries and tie class only); tma: the level ran bm_level_tma_kernel.
 qw_status launch_bm_reduce(const IndexView &ix, int nb, int l, int cap, int cgrow,
@@ -313,7 +317,7 @@ struct LevelGraphCache;
 LevelGraphCache *level_graph_cache_new();
 void level_graph_cache_free(LevelGraphCache *c);
 qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l, int cgrow,
-                          int cap, bool learned, bool bitmap, int loads, QueryState &st,
+                          int cap, bool learned, bool bitmap, int loads, int tpw, QueryState &st,
                           LoopCtl *ctl, int *err, cudaStream_t s);
 qw_status launch_collect(const IndexView &ix, int nb, int l, int cap, QueryState &st,
                          int64_t *stats_out, cudaStream_t s);
@@ -340,17 +344,18 @@ qw_status launch_candidates_out(const QueryState &st, int nb, int cap, int64_t *
 qw_status launch_rerank_bf16(const IndexView &ix, const void *Rb, const float *rnorm,
                              const void *C, const float *Qb, int nb, int k, int cap,
                              const QueryState &st, int64_t *ids_out, float *dists_out,
-                             unsigned long long *rows_fp32, cudaStream_t s);
+                             unsigned long long *rows_fp32, cudaStream_t s, int rows = 4);
 // Rows Xs (n x d) grouped by 128: C (ceil(n / 128) x d BF16) the group means,
 // Rb (n x d BF16) the residuals to them, rnorm (n) bounds of the residual norms.
 qw_status launch_shadow_bf16(const float *Xs, int64_t n, int d, void *Rb, float *rnorm,
                              void *C, cudaStream_t s);
 // Xrows/row_of (optional): read data id `id` from row row_of[id] of Xrows
 // (the bitmap path's copy of the data in locality order).
+// rows: candidate rows a warp takes at a time (2, 4 or 8; other values: 4).
 qw_status launch_rerank(const IndexView &ix, const float *Qb, int nb, int k, int cap,
                         const QueryState &st, int64_t *ids_out, float *dists_out,
                         cudaStream_t s, const float *Xrows = nullptr,
-                        const int32_t *row_of = nullptr);
+                        const int32_t *row_of = nullptr, int rows = 4);
 // The data in locality order (Xloc[j] = X[perm[j]]) and the inverse order.
 qw_status launch_locality_copy(const float *X, const int32_t *perm, int64_t n, int d, float *Xloc,
                                int32_t *inv, cudaStream_t s);

@@ -53,7 +53,7 @@ struct L2Session {
 // Graph mode of the level loop (qw_graph.cu) with the access-policy window
 // `win` on every kernel node of the batch's graph (num_bytes 0: none).
 qw_status run_level_graph(LevelGraphCache *c, const IndexView &ix, int nb, int l, int cgrow,
-                          int cap, bool learned, bool bitmap, int loads, QueryState &st,
+                          int cap, bool learned, bool bitmap, int loads, int tpw, QueryState &st,
                           LoopCtl *ctl, int *err, cudaStream_t s,
                           const cudaAccessPolicyWindow &win);
 

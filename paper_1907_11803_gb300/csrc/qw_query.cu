@@ -44,6 +44,8 @@ __global__ void query_setup_kernel(const int32_t *__restrict__ HQ, int nb, int m
         int64_t g = (int64_t)HQ[(int64_t)q * m + i] - (int64_t)o[i];
         st.g[(int64_t)q * m + i] = g;
         top = max(top, max((int64_t)span[i], g));
+        // with probes a query bucket id below the data collides once R > -g
+        if (st.probes > 0) top = max(top, -g);
     }
     st.top[q] = top;
     st.active[q] = 1;
@@ -145,14 +147,17 @@ __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int lev
         const int32_t *ub = ix.dir_bid + ix.dir_start[dslot];
         const int32_t *uo = ix.dir_off + ix.dir_start[dslot];
         const int cnt = ix.dir_cnt[dslot];
-        const int64_t lo = floordiv64(gi, R) * R;
-        const int64_t A = clamp64(lo, 0, sp1), B = clamp64(lo + R, 0, sp1);
+        // the level's bid range, widened to P buckets on each side with probes
+        const int64_t P = st.probes;
+        const int64_t lo = (floordiv64(gi, R) - P) * R;
+        const int64_t A = clamp64(lo, 0, sp1), B = clamp64(lo + (2 * P + 1) * R, 0, sp1);
         const int pA = dir_lower(ub, uo, cnt, len, A);
         const int pB = dir_lower(ub, uo, cnt, len, B);
         int s0 = pA, e0 = pB, s1 = 0, e1 = 0;
         if (!first) {
-            const int64_t lo2 = floordiv64(gi, Rp) * Rp;
-            const int64_t A2 = clamp64(lo2, 0, sp1), B2 = clamp64(lo2 + Rp, 0, sp1);
+            // ranges nest from level to level, so only the two new flanks are read
+            const int64_t lo2 = (floordiv64(gi, Rp) - P) * Rp;
+            const int64_t A2 = clamp64(lo2, 0, sp1), B2 = clamp64(lo2 + (2 * P + 1) * Rp, 0, sp1);
             if (A2 < B2) {
                 e0 = dir_lower(ub, uo, cnt, len, A2);
                 s1 = dir_lower(ub, uo, cnt, len, B2);
@@ -164,8 +169,8 @@ __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int lev
             int64_t Rs = R;
             for (int L2 = level - 1; L2 >= 0; --L2) {
                 Rs /= cgrow;
-                const int64_t lo3 = floordiv64(gi, Rs) * Rs;
-                const int64_t A3 = clamp64(lo3, 0, sp1), B3 = clamp64(lo3 + Rs, 0, sp1);
+                const int64_t lo3 = (floordiv64(gi, Rs) - P) * Rs;
+                const int64_t A3 = clamp64(lo3, 0, sp1), B3 = clamp64(lo3 + (2 * P + 1) * Rs, 0, sp1);
                 skipped += (unsigned long long)(dir_lower(ub, uo, cnt, len, B3) -
                                                 dir_lower(ub, uo, cnt, len, A3));
             }

@@ -106,6 +106,7 @@ __device__ uint32_t min_above(const float *v, int n, float t, int *bc)
 // (a power of two >= nc) slots; writes the query's k results.
 // row_of (optional): the row of data id `id` in X is row_of[id] (X in the
 // bitmap path's locality order), else id.
+template <int kRows>
 __device__ void rerank_finish(const float *__restrict__ X, const int32_t *__restrict__ row_of,
                               int d, const float *__restrict__ qv,
                               int k, int P2, int nc, RerankSmem sm, int64_t *__restrict__ ids_q,
@@ -130,7 +131,6 @@ __device__ void rerank_finish(const float *__restrict__ X, const int32_t *__rest
     // 1. FP32 squared distances: a warp takes kRows candidate rows at a time,
     //    so each lane has kRows independent loads in flight; every row keeps
     //    its own per-lane chain and butterfly sum (the order rho covers)
-    constexpr int kRows = 4;
     for (int j0 = warp * kRows; j0 < nc; j0 += RR_WARPS * kRows) {
         const float *xr[kRows];
         float acc[kRows];
@@ -337,6 +337,7 @@ __device__ __forceinline__ RerankSmem carve_rerank(unsigned char *base, int P2, 
     return r;
 }
 
+template <int kRows>
 __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(
     const float *__restrict__ X, const int32_t *__restrict__ row_of, int d,
     const float *__restrict__ Qb, int k, int cap, int P2,
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(
     const int32_t *cl = cand + (int64_t)q * cap;
     for (int j = threadIdx.x; j < nc; j += RR_THREADS) sm.sid[j] = cl[j];
     __syncthreads();
-    rerank_finish(X, row_of, d, Qb + (int64_t)q * d, k, P2, nc, sm, ids_out + (int64_t)q * k,
+    rerank_finish<kRows>(X, row_of, d, Qb + (int64_t)q * d, k, P2, nc, sm, ids_out + (int64_t)q * k,
                   dists_out + (int64_t)q * k, vec);
 }
 
@@ -378,6 +379,7 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(
 // among the k nearest (the k candidates with the smallest upper bounds all lie
 // within it); all others go through the exact FP32 + FP64 stages on the FP32
 // rows, so the result is the same as without the pre-filter.
+template <int kRows>
 __global__ void __launch_bounds__(RR_THREADS) rerank_bf16_kernel(
     const float *__restrict__ Xr, const int32_t *__restrict__ row_of,
     const __nv_bfloat16 *__restrict__ Rb, const float *__restrict__ rnorm,
@@ -412,7 +414,6 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_bf16_kernel(
         cid[j] = id;
     }
     __syncthreads();
-    constexpr int kRows = 4;
     // the query's 16-byte chunks c = lane + 32 i (i < kQReg) stay in registers
     constexpr int kQReg = 2;
     const int nch4 = d >> 2;
@@ -527,23 +528,33 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_bf16_kernel(
     if (rows_fp32 && threadIdx.x == 0) atomicAdd(rows_fp32, (unsigned long long)ns);
     int P2s = 2;
     while (P2s < ns) P2s <<= 1;
-    rerank_finish(Xr, row_of, d, qv, k, P2s, ns, sm, ids_out + (int64_t)q * k,
+    rerank_finish<kRows>(Xr, row_of, d, qv, k, P2s, ns, sm, ids_out + (int64_t)q * k,
                   dists_out + (int64_t)q * k, vec);
 }
 
 }  // namespace
 
+// Rows a warp takes at a time: 2, 4 (default) or 8.
+#define QW_RERANK_ROWS_DISPATCH(rows, KERNEL, ...)                     \
+    switch (rows) {                                                    \
+    case 2: KERNEL<2>__VA_ARGS__; break;                               \
+    case 8: KERNEL<8>__VA_ARGS__; break;                               \
+    default: KERNEL<4>__VA_ARGS__; break;                              \
+    }
+
 qw_status launch_rerank_bf16(const IndexView &ix, const void *Rb, const float *rnorm,
                              const void *C, const float *Qb, int nb, int k, int cap,
                              const QueryState &st, int64_t *ids_out, float *dists_out,
-                             unsigned long long *rows_fp32, cudaStream_t s)
+                             unsigned long long *rows_fp32, cudaStream_t s, int rows)
 {
     int P2 = 2;
     while (P2 < cap) P2 <<= 1;
     const size_t smem = (size_t)P2 * (sizeof(double) + 2 * sizeof(float) + sizeof(int32_t) + 1) +
                         16 + (size_t)P2 * sizeof(int32_t);
-    QW_CUDA_TRY(cudaFuncSetAttribute(rerank_bf16_kernel,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const void *fn = rows == 2 ? (const void *)rerank_bf16_kernel<2>
+                     : rows == 8 ? (const void *)rerank_bf16_kernel<8>
+                                 : (const void *)rerank_bf16_kernel<4>;
+    QW_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // rows in the locality order when the index has them (the copy's order)
     const float *Xr = ix.Xloc ? ix.Xloc : ix.X;
     const int32_t *row_of = ix.Xloc ? ix.inv : nullptr;
@@ -552,28 +563,29 @@ qw_status launch_rerank_bf16(const IndexView &ix, const void *Rb, const float *r
     // rho of the FP32 summation (the FP32 stage's bound): 1 / (1 -/+ rho)
     const double rho = (double)((ix.d + 31) / 32 + 12) * 5.9604644775390625e-08 * 1.02;
     const float inv_omr = (float)(1.0 / (1.0 - rho)), inv_opr = (float)(1.0 / (1.0 + rho));
-    rerank_bf16_kernel<<<nb, RR_THREADS, smem, s>>>(
+    QW_RERANK_ROWS_DISPATCH(rows, rerank_bf16_kernel, <<<nb, RR_THREADS, smem, s>>>(
         Xr, row_of, reinterpret_cast<const __nv_bfloat16 *>(Rb), rnorm,
         reinterpret_cast<const __nv_bfloat16 *>(C), ix.d, Qb, k, cap, P2,
-        st.cand, st.nkeep, ids_out, dists_out, vec, inv_omr, inv_opr, rows_fp32);
+        st.cand, st.nkeep, ids_out, dists_out, vec, inv_omr, inv_opr, rows_fp32))
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }
 
 qw_status launch_rerank(const IndexView &ix, const float *Qb, int nb, int k, int cap,
                         const QueryState &st, int64_t *ids_out, float *dists_out,
-                        cudaStream_t s, const float *Xrows, const int32_t *row_of)
+                        cudaStream_t s, const float *Xrows, const int32_t *row_of, int rows)
 {
     const float *X = Xrows ? Xrows : ix.X;
     int P2 = 2;
     while (P2 < cap) P2 <<= 1;
     const size_t smem = (size_t)P2 * (sizeof(double) + 2 * sizeof(float) + sizeof(int32_t) + 1);
-    QW_CUDA_TRY(cudaFuncSetAttribute(rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+    const void *fn = rows == 2 ? (const void *)rerank_kernel<2>
+                     : rows == 8 ? (const void *)rerank_kernel<8> : (const void *)rerank_kernel<4>;
+    QW_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // 16-byte row loads need d % 4 == 0 and 16-byte aligned bases
     const bool vec = (ix.d % 4 == 0) && ((uintptr_t)Qb % 16 == 0) && ((uintptr_t)X % 16 == 0);
-    rerank_kernel<<<nb, RR_THREADS, smem, s>>>(X, row_of, ix.d, Qb, k, cap, P2, st.cand,
-                                               st.nkeep, ids_out, dists_out, vec);
+    QW_RERANK_ROWS_DISPATCH(rows, rerank_kernel, <<<nb, RR_THREADS, smem, s>>>(
+        X, row_of, ix.d, Qb, k, cap, P2, st.cand, st.nkeep, ids_out, dists_out, vec))
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }

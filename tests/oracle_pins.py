@@ -396,11 +396,252 @@ def pin_hand_worked_golden(orc):
         for t, i in enumerate(q["kept"]):
             if orc.sqdist(X[i], Q[qi]) != q["kept_sqdist"][t]:
                 fails.append(f"query {qi}: squared distance to {i} differs")
+    # the same points with one probe on each side
+    mp = g["multi_probe"]
+    P = mp["probes"]
+    Qp = np.array(mp["Q"], np.float32)
+    HQp = orc.hash(Qp, A, b, p["w"])
+    if not np.array_equal(HQp, np.array(mp["HQ"])):
+        return fails + ["multi-probe query bucket ids differ"]
+    for qi, q in enumerate(mp["queries"]):
+        for lv in q["levels"]:
+            col = orc.collision_counts(ix, HQp[qi], lv["R"], probes=P)
+            if col.tolist() != lv["col"]:
+                fails.append(f"probe query {qi}, R = {lv['R']}: counts {col.tolist()}")
+    res = orc.query(X, ix, Qp, HQp, k=p["k"], v=p["v"], l=p["l"], c=p["c"], probes=P)
+    for qi, q in enumerate(mp["queries"]):
+        if res["stats"][qi].tolist() != q["stats"]:
+            fails.append(f"probe query {qi}: stats {res['stats'][qi].tolist()} want {q['stats']}")
+        kept = res["cand_ids"][qi].tolist()
+        if kept != q["kept"] + [-1] * (cap - len(q["kept"])):
+            fails.append(f"probe query {qi}: kept {kept} want {q['kept']}")
+        if res["ids"][qi].tolist() != q["ids"]:
+            fails.append(f"probe query {qi}: ids {res['ids'][qi].tolist()} want {q['ids']}")
+        want_d = [math.sqrt(x) for x in q["sqdists"]]
+        if not np.array_equal(res["dists"][qi], np.array(want_d)):
+            fails.append(f"probe query {qi}: dists differ")
     return fails
+
+
+def pin_multi_probe_semantics(orc):
+    """Multi-probe restated independently: an object collides on projection i
+    when its level-R bucket index floor(bid / R) is within P of the query's
+    (a distance between bucket indices, not the oracle's bid range); the level
+    loop stops at the first level with |C_R| >= k + v or past every bucket
+    index the query can still reach (for P > 0 also R > -g_i); the kept set
+    and the result follow as without probes.  Queries far below and above the
+    data are included, and C_R grows with P."""
+    fails = []
+    for seed, P, c in ((21, 1, 2), (22, 2, 2), (23, 1, 3)):
+        wl = _small(seed=seed, n=1200, nq=20, m=10)
+        X, Q = wl.X, wl.Q
+        # queries below the data on every projection (A dq = -300: bucket ids
+        # far under the anchors), and above it
+        shift = np.linalg.pinv(wl.A.astype(np.float64)) @ np.full(wl.A.shape[0], 300.0)
+        Q[:3] = (Q[:3] - shift).astype(np.float32)
+        Q[3:5] = (Q[3:5] + shift).astype(np.float32)
+        H = orc.hash(X, wl.A, wl.b, 4.0)
+        HQ = orc.hash(Q, wl.A, wl.b, 4.0)
+        ix = orc.build_index(H)
+        k, v, l = 5, 25, 7
+        res = orc.query(X, ix, Q, HQ, k=k, v=v, l=l, c=c, probes=P)
+        res0 = orc.query(X, ix, Q, HQ, k=k, v=v, l=l, c=c)
+        B = (H - ix.o).astype(np.int64)
+        cap = k + v
+        for q in range(Q.shape[0]):
+            g = HQ[q].astype(np.int64) - ix.o
+            top = max(int(ix.span.max()), int(g.max()), int((-g).max()))
+            R, prev_set, levels = 1, np.zeros(X.shape[0], bool), 0
+            while True:
+                levels += 1
+                col = (np.abs(np.floor_divide(B, R) - np.floor_divide(g, R)[None, :]) <= P).sum(1)
+                cand = col >= l
+                if cand.sum() >= cap:
+                    term = 2
+                    break
+                if R > top:
+                    term = 3
+                    break
+                prev_set = cand
+                R *= c
+            st = res["stats"][q]
+            if (st[0], st[1], st[2], st[4], st[7]) != (levels, R, int(cand.sum()), term,
+                                                       int(prev_set.sum())):
+                fails.append(f"seed {seed} q {q}: stats {st[[0, 1, 2, 4, 7]]} want "
+                             f"{(levels, R, int(cand.sum()), term, int(prev_set.sum()))}")
+                continue
+            idx = np.nonzero(cand)[0]
+            order = np.lexsort((idx, -col[idx], ~prev_set[idx]))
+            kept = idx[order][:cap]
+            if kept.tolist() != res["cand_ids"][q][res["cand_ids"][q] >= 0].tolist():
+                fails.append(f"seed {seed} q {q}: kept candidates differ")
+            col0 = orc.collision_counts(ix, HQ[q], R)
+            colP = orc.collision_counts(ix, HQ[q], R, probes=P)
+            if np.any(colP < col0):
+                fails.append(f"seed {seed} q {q}: a count falls when probes are added")
+        if np.all(res["stats"][:, 0] == res0["stats"][:, 0]):
+            fails.append(f"seed {seed}: probes never change the stop level")
+    return fails[:6]
+
+
+# ---------------------------------------------------------------- QALSH (Section 2)
+def pin_qalsh_hand_worked(orc):
+    """The ten hand-worked points with QALSH's query-centred buckets
+    (tests/golden/hand_worked_query.json, section "qalsh"): every level's
+    counts, with points exactly on an interval end counted as inside; the stop
+    level, the kept candidates in truncation order, the statistics and the
+    top-k, all worked out by hand."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "hand_worked_query.json")
+    with open(path) as fh:
+        g = json.load(fh)
+    p = g["params"]
+    qa = g["qalsh"]
+    X = np.array(g["X"], np.float32)
+    A = np.array(g["A"], np.float32)
+    Q = np.array(qa["Q"], np.float32)
+    P = orc.project(X, A)
+    PQ = orc.project(Q, A)
+    if not np.array_equal(P, X[:, :3].astype(np.float64)):
+        return ["projections of the hand-worked points differ from their first three coordinates"]
+    fails = []
+    for qi, q in enumerate(qa["queries"]):
+        for lv in q["levels"]:
+            col = orc.qalsh_counts(P, PQ[qi], qa["w"], lv["R"])
+            if col.tolist() != lv["col"]:
+                fails.append(f"qalsh query {qi}, R = {lv['R']}: counts {col.tolist()} want {lv['col']}")
+    res = orc.qalsh_query(X, P, Q, PQ, w=qa["w"], k=p["k"], v=p["v"], l=p["l"], c=p["c"])
+    cap = p["k"] + p["v"]
+    for qi, q in enumerate(qa["queries"]):
+        st = res["stats"][qi].tolist()
+        if st != q["stats"]:
+            fails.append(f"qalsh query {qi}: stats {st} want {q['stats']}")
+        kept = res["cand_ids"][qi].tolist()
+        if kept != q["kept"] + [-1] * (cap - len(q["kept"])):
+            fails.append(f"qalsh query {qi}: kept {kept} want {q['kept']} (truncation order)")
+        if res["cand_col"][qi][: len(q["kept"])].tolist() != q["kept_col"]:
+            fails.append(f"qalsh query {qi}: kept counts differ")
+        if res["ids"][qi].tolist() != q["ids"]:
+            fails.append(f"qalsh query {qi}: ids {res['ids'][qi].tolist()} want {q['ids']}")
+        want_d = [math.sqrt(x) for x in q["sqdists"]]
+        if not np.array_equal(res["dists"][qi], np.array(want_d)):
+            fails.append(f"qalsh query {qi}: dists {res['dists'][qi].tolist()} want {want_d}")
+    return fails
+
+
+def pin_qalsh_prob_quadrature(orc):
+    """QALSH's collision probability: for a projection a with i.i.d. N(0, 1)
+    entries, a . (o - q) is N(0, r^2), and the probability that it lands in a
+    bucket of width w centred on q is the normal density integrated over
+    [-w/2, w/2] -- evaluated here by adaptive quadrature -- and, sampled, the
+    fraction of Gaussian projections within w/2."""
+    from scipy.integrate import quad
+    fails = []
+    for w in (0.5, 2.719, 4.0):
+        for r in (0.05, 0.5, 1.0, 2.0, 7.5, 40.0):
+            dens = lambda t: math.exp(-t * t / (2 * r * r)) / (r * math.sqrt(2 * math.pi))
+            want, _ = quad(dens, -w / 2, w / 2, epsabs=1e-14, epsrel=1e-13)
+            got = orc.qalsh_prob(r, w)
+            if not abs(got - want) <= 1e-10:
+                fails.append(f"qalsh P(r={r}, w={w}) = {got}, quadrature {want}")
+    rng = np.random.default_rng(5)
+    o = np.zeros(16)
+    q = np.zeros(16)
+    q[0] = 1.5                                            # r = 1.5
+    proj = rng.standard_normal((200000, 16)) @ (o - q)
+    frac = float(np.mean(np.abs(proj) <= 2.719 / 2))
+    want = orc.qalsh_prob(1.5, 2.719)
+    if not abs(frac - want) <= 5 * math.sqrt(want * (1 - want) / 200000):
+        fails.append(f"sampled collision rate {frac} vs {want}")
+    return fails
+
+
+def pin_qalsh_project_exact(orc):
+    """a_i . v on small integers is exact in any summation order: the
+    projections equal the integer matrix product."""
+    rng = np.random.default_rng(8)
+    V = rng.integers(-50, 50, size=(300, 33)).astype(np.float32)
+    A = rng.integers(-9, 9, size=(11, 33)).astype(np.float32)
+    want = (V.astype(np.int64) @ A.astype(np.int64).T).astype(np.float64)
+    got = orc.project(V, A)
+    return [] if np.array_equal(got, want) else ["projections differ from the integer product"]
+
+
+def pin_qalsh_v_ge_n_exact(orc):
+    """With k + v > n no level can reach the k + v bound, so the query runs
+    until every interval holds all the data (the radius rule), keeps every
+    object and returns the exact k nearest neighbours; the stop radius is the
+    first R = c^j with w R / 2 >= max_i max_o |p_i(o) - p_i(q)|."""
+    fails = []
+    wl = _small(seed=31, n=300, nq=12, d=8, m=6, n_clusters=5)
+    P = orc.project(wl.X, wl.A)
+    PQ = orc.project(wl.Q, wl.A)
+    res = orc.qalsh_query(wl.X, P, wl.Q, PQ, w=2.719, k=7, v=400, l=3, c=2)
+    want_ids, want_d = _exact_knn_numpy(wl.X, wl.Q, 7)
+    if not np.array_equal(res["ids"], want_ids):
+        fails.append("v >= n: ids are not the exact neighbours")
+    if not np.allclose(res["dists"], want_d, rtol=1e-12, atol=0):
+        fails.append("v >= n: distances differ from the exact ones")
+    for qi in range(wl.Q.shape[0]):
+        spread = np.abs(P - PQ[qi][None, :]).max()
+        R = 1
+        while 2.719 * R / 2 < spread:
+            R *= 2
+        st = res["stats"][qi]
+        if st[4] != 3 or st[3] != 300 or st[1] != R:
+            fails.append(f"v >= n, query {qi}: term {st[4]}, kept {st[3]}, R {st[1]} want 3, 300, {R}")
+    return fails
+
+
+def pin_qalsh_semantics(orc):
+    """The query-centred level loop restated with numpy broadcasting on small
+    workloads (c = 2 and 3): per level, counts of projections within w R / 2,
+    the k + v stop, the radius rule, the kept set in truncation order and the
+    statistics."""
+    fails = []
+    for seed, c in ((41, 2), (42, 3)):
+        wl = _small(seed=seed, n=1500, nq=16, m=10)
+        P = orc.project(wl.X, wl.A)
+        PQ = orc.project(wl.Q, wl.A)
+        w, k, v, l = 2.719, 5, 30, 6
+        res = orc.qalsh_query(wl.X, P, wl.Q, PQ, w=w, k=k, v=v, l=l, c=c)
+        cap = k + v
+        for q in range(wl.Q.shape[0]):
+            dev = np.abs(P - PQ[q][None, :])
+            spread = dev.max()
+            R, prev_set, levels, full = 1, np.zeros(P.shape[0], bool), 0, 0
+            while True:
+                levels += 1
+                inside = dev <= w * R / 2
+                col = inside.sum(1)
+                full += int(inside.sum())
+                cand = col >= l
+                if cand.sum() >= cap:
+                    term = 2
+                    break
+                if w * R / 2 >= spread:
+                    term = 3
+                    break
+                prev_set = cand
+                R *= c
+            want = (levels, R, int(cand.sum()), min(int(cand.sum()), cap), term,
+                    int(inside.sum()), full, int(prev_set.sum()))
+            if tuple(res["stats"][q].tolist()) != want:
+                fails.append(f"seed {seed} q {q}: stats {res['stats'][q].tolist()} want {want}")
+                continue
+            idx = np.nonzero(cand)[0]
+            kept = idx[np.lexsort((idx, -col[idx], ~prev_set[idx]))][:cap]
+            if kept.tolist() != res["cand_ids"][q][res["cand_ids"][q] >= 0].tolist():
+                fails.append(f"seed {seed} q {q}: kept candidates differ")
+    return fails[:6]
 
 
 ALL_PINS = [pin_collision_prob_quadrature, pin_collision_prob_limits, pin_threshold_balance,
             pin_hash_exact_sum, pin_index_sorted_arrays, pin_collision_counts,
             pin_single_projection_is_e2lsh, pin_bruteforce, pin_v_ge_n_exact,
             pin_workload_semantics, pin_t3_fixpoint, pin_ratio_invariant,
-            pin_duplicates_tie_by_id, pin_hand_worked_golden]
+            pin_duplicates_tie_by_id, pin_hand_worked_golden, pin_multi_probe_semantics,
+            pin_qalsh_hand_worked, pin_qalsh_prob_quadrature, pin_qalsh_project_exact,
+            pin_qalsh_v_ge_n_exact, pin_qalsh_semantics]

@@ -14,7 +14,8 @@ STRUCTS = {
     "qw_index_params": ["m", "w", "c", "v", "l", "delta", "shadow_bf16", "bitmaps",
                         "host_bitmaps", "seed", "projection"],
     "qw_query_params": ["batch", "profile", "path", "clusters", "order", "rerank", "start",
-                        "graph", "bitmap_loads", "l2_mode", "l2_index_permille", "projection"],
+                        "graph", "bitmap_loads", "l2_mode", "l2_index_permille", "projection",
+                        "rerank_rows", "tiles_per_warp", "probes"],
     "qw_profile": ["launches", "ms", "timed_launches", "queries", "rerank_candidates",
                    "rerank_fp32_rows", "start_levels_skipped", "start_fallbacks", "level_passes",
                    "bitmap_fallbacks", "bitmap_live_items", "bitmap_live_groups",

@@ -136,6 +136,82 @@ def test_hand_worked_golden(qwlib, cuda, path):
     out["index"].free()
 
 
+# ---------------------------------------------------------------- multi-probe
+@pytest.mark.parametrize("graph", [False, True])
+def test_multi_probe_hand_worked(qwlib, cuda, graph):
+    """The hand-worked multi-probe cases (one probe on each side) on the level
+    path: statistics, kept candidates and results."""
+    import json
+    import math
+    import os
+    import torch
+    with open(os.path.join(os.path.dirname(__file__), "golden", "hand_worked_query.json")) as fh:
+        g = json.load(fh)
+    p, mp = g["params"], g["multi_probe"]
+    X = np.array(g["X"], np.float32)
+    A, b = np.array(g["A"], np.float32), np.array(g["b"], np.float32)
+    Q = _t(np.array(mp["Q"], np.float32), cuda)
+    index = qwlib.Index(_t(X, cuda), _t(A, cuda), _t(b, cuda), w=p["w"], c=p["c"], v=p["v"],
+                        l=p["l"])
+    ids, dists, st = index.query(Q, p["k"], stats=True, path="levels", graph=graph,
+                                 probes=mp["probes"])
+    cid, ccol, st2 = index.candidates(Q, p["k"], path="levels", graph=graph, probes=mp["probes"])
+    torch.cuda.synchronize()
+    cap = p["k"] + p["v"]
+    for qi, q in enumerate(mp["queries"]):
+        assert st[qi].tolist() == q["stats"] and st2[qi].tolist() == q["stats"]
+        assert ids[qi].tolist() == q["ids"]
+        assert np.allclose(dists[qi].cpu().numpy(), [math.sqrt(x) for x in q["sqdists"]],
+                           rtol=DIST_RTOL, atol=0)
+        assert cid[qi].tolist() == sorted(q["kept"]) + [-1] * (cap - len(q["kept"]))
+    with pytest.raises(qwlib.QwError):
+        index.query(Q, p["k"], path="bitmap", probes=1)
+    index.free()
+
+
+@pytest.mark.parametrize("probes", [1, 2])
+def test_multi_probe_matches_oracle(orc, qwlib, cuda, probes):
+    """Multi-probe on the level path (host loop, graph mode, learned first
+    levels) against the oracle, with queries far below and above the data on
+    every projection (the radius rule waits for R > -g_i) over several tiles."""
+    import torch
+    wl = workloads.make_workload("mix10k_d32", seed=40 + probes, n=2 * TILE + 999, nq=60, d=24,
+                                 m=16, n_clusters=25)
+    Q = wl.Q.copy()
+    shift = np.linalg.pinv(wl.A.astype(np.float64)) @ np.full(16, 300.0)
+    Q[:4] = (Q[:4] - shift).astype(np.float32)
+    Q[4:7] = (Q[4:7] + shift).astype(np.float32)
+    k, v = 10, 120
+    l = orc.threshold(16, 4.0, 2, wl.X.shape[0], v)
+    H = orc.hash(wl.X, wl.A, wl.b, 4.0)
+    HQ = orc.hash(Q, wl.A, wl.b, 4.0)
+    oidx = orc.build_index(H)
+    ref = orc.query(wl.X, oidx, Q, HQ, k=k, v=v, l=l, probes=probes)
+    index = qwlib.Index(_t(wl.X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=4.0, v=v, l=l)
+    Qd = _t(Q, cuda)
+    for graph in (False, True):
+        ids, dists, st = index.query(Qd, k, stats=True, graph=graph, probes=probes)
+        cid, ccol, _ = index.candidates(Qd, k, graph=graph, probes=probes)
+        torch.cuda.synchronize()
+        _check_results(ids.cpu().numpy(), dists.cpu().numpy(), ref["ids"], ref["dists"])
+        assert np.array_equal(st.cpu().numpy(), ref["stats"])
+        _check_candidates(cid.cpu().numpy(), ccol.cpu().numpy(), ref["cand_ids"], ref["cand_col"])
+    # learned first levels (recomputed where a first level was the last)
+    _, _, stt = index.query(Qd, k, stats=True, probes=probes)
+    labels = (stt[:, 0] - 1).clamp(0, 15).to(torch.int32).contiguous()
+    F = index.features(Qd)
+    mlp = qwlib.Mlp(F.shape[1], 256, 16)
+    mlp.set_params(qwlib.mlp_init(F.shape[1], 256, 16, seed=3))
+    mlp.train(F, labels, epochs=5, batch=64, lr=1e-3)
+    index.set_start_model(mlp, eps=0.5)
+    ids2, dists2, st2 = index.query(Qd, k, stats=True, start="learned", probes=probes)
+    torch.cuda.synchronize()
+    _check_results(ids2.cpu().numpy(), dists2.cpu().numpy(), ref["ids"], ref["dists"])
+    assert np.array_equal(st2.cpu().numpy(), ref["stats"])
+    index.free()
+    mlp.free()
+
+
 # ---------------------------------------------------------------- boundary: seeded draws
 def test_seeded_projections_and_getter(orc, qwlib, cuda):
     """An index built without A and b draws them from its seed
@@ -235,6 +311,38 @@ def test_workload_with_tensor_core_projection(orc, qwlib, cuda, path):
     torch.cuda.synchronize()
     _check_results(ids.cpu().numpy(), dists.cpu().numpy(), ref["ids"], ref["dists"])
     assert np.array_equal(st.cpu().numpy(), ref["stats"])
+    index.free()
+
+
+@pytest.mark.parametrize("loads", ["direct", "fused"])
+def test_tile_shapes_same_results(orc, qwlib, cuda, loads):
+    """Every tile shape the autotuner may pick (tiles per warp of the filter /
+    fused kernels, candidate rows per warp of the distance kernels, FP32 and
+    BF16 pre-filter) gives the oracle's results; the index spans several tiles
+    and a ragged one."""
+    import torch
+    wl = workloads.make_workload("mix10k_d32", seed=19, n=5 * TILE + 777, nq=70, d=40, m=20,
+                                 n_clusters=30)
+    l = orc.threshold(20, 4.0, 2, wl.X.shape[0], 150)
+    _, _, _, ref = _oracle_run(orc, wl.X, wl.Q, wl.A, wl.b, 4.0, 12, 150, l)
+    index = qwlib.Index(_t(wl.X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=4.0, v=150, l=l,
+                        bitmaps=True, shadow_bf16=True)
+    Q = _t(wl.Q, cuda)
+    for tpw in (4, 8, 16):
+        for rows in (2, 4, 8):
+            for rerank in ("fp32", "bf16"):
+                for graph in (False, True):
+                    ids, dists, st = index.query(Q, 12, stats=True, path="bitmap", loads=loads,
+                                                 graph=graph, tiles_per_warp=tpw,
+                                                 rerank_rows=rows, rerank=rerank)
+                    torch.cuda.synchronize()
+                    _check_results(ids.cpu().numpy(), dists.cpu().numpy(), ref["ids"],
+                                   ref["dists"])
+                    assert np.array_equal(st.cpu().numpy(), ref["stats"])
+    with pytest.raises(qwlib.QwError):
+        index.query(Q, 12, path="bitmap", loads=loads, tiles_per_warp=5)
+    with pytest.raises(qwlib.QwError):
+        index.query(Q, 12, rerank_rows=3)
     index.free()
 
 

@@ -21,15 +21,22 @@ MUTANTS = [
     ("truncation_fewest_collisions_first", "if (a->col != b->col) return a->col > b->col ? -1 : 1;",
      "if (a->col != b->col) return a->col < b->col ? -1 : 1;",
      ["pin_workload_semantics", "pin_hand_worked_golden"]),
-    ("truncation_ignores_previous_level", "cs[nc].prev = prev[j];", "cs[nc].prev = 0;",
+    ("truncation_ignores_previous_level",
+     "truncated to k + v */\n        int64_t nc = 0;\n        for (int64_t j = 0; j < n; ++j) {\n            if (col[j] >= l) {\n                cs[nc].prev = prev[j];",
+     "truncated to k + v */\n        int64_t nc = 0;\n        for (int64_t j = 0; j < n; ++j) {\n            if (col[j] >= l) {\n                cs[nc].prev = 0;",
      ["pin_workload_semantics", "pin_hand_worked_golden"]),
     ("truncation_larger_id_first",
      "if (a->col != b->col) return a->col > b->col ? -1 : 1;\n    if (a->id != b->id) return a->id < b->id ? -1 : 1;",
      "if (a->col != b->col) return a->col > b->col ? -1 : 1;\n    if (a->id != b->id) return a->id > b->id ? -1 : 1;",
      ["pin_hand_worked_golden"]),
-    ("stop_rule_strict", "if (ncand >= cap) { term = 2; break; }",
-     "if (ncand > cap) { term = 2; break; }", ["pin_hand_worked_golden"]),
-    ("radius_grows_additively", "R *= c;", "R += 1;",
+    ("stop_rule_strict", "if (ncand >= cap) { term = 2; break; }\n            if (R > top)",
+     "if (ncand > cap) { term = 2; break; }\n            if (R > top)", ["pin_hand_worked_golden"]),
+    ("probes_ignored", "lo[i] = (beta - probes) * R;", "lo[i] = beta * R;",
+     ["pin_hand_worked_golden", "pin_multi_probe_semantics"]),
+    ("probes_radius_rule_ignores_negative_ids", "if (probes > 0 && -g > top) top = -g;", "",
+     ["pin_multi_probe_semantics"]),
+    ("radius_grows_additively", "if (R > top) { term = 3; break; }\n            nprev = ncand;\n            for (int64_t j = 0; j < n; ++j) prev[j] = (char)(col[j] >= l);\n            R *= c;",
+     "if (R > top) { term = 3; break; }\n            nprev = ncand;\n            for (int64_t j = 0; j < n; ++j) prev[j] = (char)(col[j] >= l);\n            R += 1;",
      ["pin_workload_semantics", "pin_hand_worked_golden"]),
     ("distance_not_squared", "s = s + diff * diff;", "s = s + fabs(diff);",
      ["pin_bruteforce", "pin_v_ge_n_exact"]),
@@ -43,6 +50,21 @@ MUTANTS = [
      ["pin_collision_prob_quadrature"]),
     ("alpha_swaps_p1_p2", "return (z * p1 + p2) / (1.0 + z);", "return (z * p2 + p1) / (1.0 + z);",
      ["pin_threshold_balance"]),
+    ("qalsh_interval_open", "if (fabs(dlt) <= half) cnt += 1;", "if (fabs(dlt) < half) cnt += 1;",
+     ["pin_qalsh_hand_worked"]),
+    ("qalsh_interval_full_width", "const double half = 0.5 * w * (double)R;\n    for (int64_t j",
+     "const double half = w * (double)R;\n    for (int64_t j", ["pin_qalsh_hand_worked", "pin_qalsh_semantics"]),
+    ("qalsh_prob_drops_sqrt2", "return erf(w / (2.0 * sqrt(2.0) * r));", "return erf(w / (2.0 * r));",
+     ["pin_qalsh_prob_quadrature"]),
+    ("qalsh_truncation_ignores_previous_level",
+     "as in orc_query */\n        int64_t nc = 0;\n        for (int64_t j = 0; j < n; ++j) {\n            if (col[j] >= l) {\n                cs[nc].prev = prev[j];",
+     "as in orc_query */\n        int64_t nc = 0;\n        for (int64_t j = 0; j < n; ++j) {\n            if (col[j] >= l) {\n                cs[nc].prev = 0;",
+     ["pin_qalsh_hand_worked", "pin_qalsh_semantics"]),
+    ("qalsh_radius_rule_one_sided",
+     "if (!(fabs(pmin[i] - pq[i]) <= half && fabs(pmax[i] - pq[i]) <= half)) all = 0;",
+     "if (!(fabs(pmax[i] - pq[i]) <= half)) all = 0;", ["pin_qalsh_v_ge_n_exact", "pin_qalsh_semantics"]),
+    ("project_transposed", "const float *a = A + (size_t)i * d;", "const float *a = A + (size_t)i;",
+     ["pin_qalsh_project_exact", "pin_qalsh_hand_worked"]),
     ("query_not_anchored", "int64_t g = (int64_t)hq[i] - (int64_t)o[i];\n        int64_t beta",
      "int64_t g = (int64_t)hq[i];\n        int64_t beta", ["pin_collision_counts", "pin_single_projection_is_e2lsh"]),
 ]
