@@ -60,7 +60,8 @@ typedef int32_t qw_status;
  *  2 |C_R|, candidates (collision count >= l) at the last level
  *  3 candidates kept after the k + v bound
  *  4 termination: 2 = |C_R| >= k + v; 3 = R exceeds every bucket id of the
- *    data and of the query, so no further level can change C_R
+ *    data and of the query, so no further level can change C_R (QALSH: every
+ *    projection's interval holds the whole data)
  *  5 sorted index entries inside the last level's bucket ranges, summed over
  *    projections (the entries an incremental scan reads in total)
  *  6 sum over levels of the entries inside that level's ranges
@@ -102,7 +103,30 @@ typedef struct {
                              m, d, w, ...); read them back with qw_index_get_projections */
     int32_t projection;   /* QW_PROJ_FP32 (default) or QW_PROJ_TENSOR: how the data are
                              projected at build time (same bucket ids) */
+    int32_t family;       /* hash family (QW_FAMILY_*, below); default QW_FAMILY_E2LSH */
 } qw_index_params;
+
+/* Hash families (qw_index_params.family).
+ *
+ * QW_FAMILY_E2LSH (0): Section 3's h(v) = floor((a . v + b) / w) with anchored
+ * bucket ids and virtual rehashing (C2LSH): at radius R an object collides on
+ * projection i when floor(bid / R) equals the query's.
+ *
+ * QW_FAMILY_QALSH (1): QALSH's query-aware buckets (Section 2; the method the
+ * paper's experiments build on, Section 6, w = 2.719).  The hash is the
+ * projection p_i(v) = a_i . v itself (b is not used), computed in FP64 with the
+ * products summed in coordinate order; at radius R an object collides on
+ * projection i when |p_i(o) - p_i(q)| <= w R / 2 (the difference rounded once
+ * in FP64, ends included).  The radius rule: a query stops at the first R at
+ * which every projection's interval holds the whole data.  The threshold l,
+ * the k + v bound, truncation and top-k are unchanged; l = 0 derives l from
+ * QALSH's collision probability (qw_qalsh_collision_threshold).  Layout: per
+ * projection and id tile, the tile's FP64 projections in ascending order with
+ * their 16-bit in-tile ids (10 bytes per entry).  Runs on the level path only:
+ * no bitmaps, learned start levels, multi-probe, tensor-core projection or
+ * bucket-signature order (the workload runs in the given order). */
+#define QW_FAMILY_E2LSH 0
+#define QW_FAMILY_QALSH 1
 
 /* Per-workload options.  Zero-initialise; unknown non-zero fields are rejected. */
 typedef struct {
@@ -282,6 +306,7 @@ typedef struct {
     int64_t bitmap_bytes;  /* the level bitmaps (0 without them), in device memory unless
                               host_bitmaps */
     int64_t host_bytes;    /* pinned host memory held by the index (host_bitmaps) */
+    int32_t family;        /* QW_FAMILY_E2LSH or QW_FAMILY_QALSH */
 } qw_index_info;
 
 /* Library version string. */
@@ -302,6 +327,17 @@ double qw_collision_probability(double r, double w);
  *   alpha = (z p1 + p2) / (1 + z),  l = ceil(alpha m)  clamped to [1, m].
  * delta <= 0 means 1/e.  Returns -1 on invalid arguments. */
 int32_t qw_collision_threshold(int32_t m, float w, int32_t c, int64_t n, int32_t v, float delta);
+
+/* QALSH's collision probability (Section 2): for a projection a with i.i.d.
+ * N(0, 1) entries, a . (o - q) is N(0, r^2) for ||o - q|| = r, and the bucket
+ * of width w centred on the query catches it with probability
+ *   P(|N(0, r^2)| <= w / 2) = erf(w / (2 sqrt(2) r)).
+ * Returns NaN for r <= 0 or w <= 0. */
+double qw_qalsh_collision_probability(double r, double w);
+
+/* qw_collision_threshold with p1, p2 from qw_qalsh_collision_probability. */
+int32_t qw_qalsh_collision_threshold(int32_t m, float w, int32_t c, int64_t n, int32_t v,
+                                     float delta);
 
 /* Hash vectors (Section 3): H[r * m + i] = floor((a_i . V_r + b_i) / w).
  * V: nv x d float32, A: m x d float32, b: m float32, H: nv x m int32; all
@@ -352,11 +388,14 @@ void qw_draw_projections(uint64_t seed, int32_t m, int32_t d, float w, float *A,
  *   anchor o_i = min over data of h_i, bucket id bid = h_i - o_i >= 0,
  *   and, for every projection, the (bid, id) pairs sorted by bid (ids within
  *   a bucket in the bank-spread order described at qw_index_export),
- *   grouped by id tile, with a directory of the distinct bids of each tile.
+ *   grouped by id tile, with a directory of the distinct bids of each tile;
+ * with QW_FAMILY_QALSH the sorted FP64 projections instead (anchors and spans
+ * are then zero).
  * The call waits for the stream.  *out receives the handle (free with
  * qw_index_free).
  * Errors: QW_ERR_ARG (null pointer, n < 1, n >= 2^31, d < 1, bad params),
- * QW_ERR_RANGE (bucket id or span outside int32), QW_ERR_OOM, QW_ERR_CUDA. */
+ * QW_ERR_RANGE (bucket id or span outside int32; QALSH: a projection not
+ * finite), QW_ERR_OOM, QW_ERR_CUDA. */
 qw_status qw_build_index(const float *data, int64_t n, int32_t d, const float *A,
                          const float *b, const qw_index_params *params, int32_t mem,
                          void *stream, qw_index **out);
@@ -559,7 +598,8 @@ qw_status qw_index_get_info(const qw_index *index, qw_index_info *info);
  * bucket, ids are arranged so that consecutive entries fall into different
  * shared-memory banks of the counting kernels (groups of 8 ids of one bank,
  * the groups cycling through the banks).
- * Any output pointer may be NULL.  Waits for the stream. */
+ * Any output pointer may be NULL.  Waits for the stream.  A QALSH index has no
+ * bucket ids: entry_bid / entry_id are refused with QW_ERR_ARG. */
 qw_status qw_index_export(const qw_index *index, int32_t *o, int32_t *span,
                           int32_t *entry_bid, int32_t *entry_id, void *stream);
 

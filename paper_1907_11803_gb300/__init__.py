@@ -38,14 +38,14 @@ EXPORTED = ("qw_version", "qw_last_error", "qw_collision_probability",
             "qw_mlp_free", "qw_query_features", "qw_index_set_start_model", "qw_autotune",
             "qw_index_export", "qw_index_free", "qw_l2_split_model", "qw_mlp_predict_tc",
             "qw_draw_projections", "qw_index_get_projections", "qw_measure_read_bandwidth",
-            "qw_hash_tc")
+            "qw_hash_tc", "qw_qalsh_collision_probability", "qw_qalsh_collision_threshold")
 
 
 class qw_index_params(C.Structure):
     _fields_ = [("m", C.c_int32), ("w", C.c_float), ("c", C.c_int32), ("v", C.c_int32),
                 ("l", C.c_int32), ("delta", C.c_float), ("shadow_bf16", C.c_int32),
                 ("bitmaps", C.c_int32), ("host_bitmaps", C.c_int32), ("seed", C.c_uint64),
-                ("projection", C.c_int32)]
+                ("projection", C.c_int32), ("family", C.c_int32)]
 
 
 class qw_query_params(C.Structure):
@@ -76,6 +76,8 @@ QW_START_PLAIN, QW_START_LEARNED = 0, 1
 STARTS = {"plain": QW_START_PLAIN, "learned": QW_START_LEARNED}
 QW_PROJ_FP32, QW_PROJ_TENSOR = 0, 1
 PROJECTIONS = {"fp32": QW_PROJ_FP32, "tensor": QW_PROJ_TENSOR}
+QW_FAMILY_E2LSH, QW_FAMILY_QALSH = 0, 1
+FAMILIES = {"e2lsh": QW_FAMILY_E2LSH, "qalsh": QW_FAMILY_QALSH}
 QW_LOADS_TMA, QW_LOADS_DIRECT, QW_LOADS_FUSED = 0, 1, 2
 LOADS = {"tma": QW_LOADS_TMA, "direct": QW_LOADS_DIRECT, "fused": QW_LOADS_FUSED}
 QW_L2_OFF, QW_L2_SPLIT, QW_L2_MODEL = 0, 1, 2
@@ -102,7 +104,7 @@ class qw_index_info(C.Structure):
                 ("c", C.c_int32), ("v", C.c_int32), ("l", C.c_int32), ("tile", C.c_int32),
                 ("n_tiles", C.c_int32), ("span_max", C.c_int32), ("n_fixups", C.c_int64),
                 ("device_bytes", C.c_int64), ("bitmap_bytes", C.c_int64),
-                ("host_bytes", C.c_int64)]
+                ("host_bytes", C.c_int64), ("family", C.c_int32)]
 
 
 class QwError(RuntimeError):
@@ -134,6 +136,11 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.qw_collision_threshold.restype = C.c_int32
     L.qw_collision_threshold.argtypes = [C.c_int32, C.c_float, C.c_int32, C.c_int64, C.c_int32,
                                          C.c_float]
+    L.qw_qalsh_collision_probability.restype = C.c_double
+    L.qw_qalsh_collision_probability.argtypes = [C.c_double, C.c_double]
+    L.qw_qalsh_collision_threshold.restype = C.c_int32
+    L.qw_qalsh_collision_threshold.argtypes = [C.c_int32, C.c_float, C.c_int32, C.c_int64,
+                                               C.c_int32, C.c_float]
     L.qw_hash.restype = C.c_int32
     L.qw_hash.argtypes = [vp, C.c_int64, C.c_int32, vp, vp, C.c_int32, C.c_float, vp,
                           C.POINTER(C.c_int64), vp]
@@ -216,6 +223,15 @@ def qw_collision_probability(r: float, w: float) -> float:
 
 def qw_collision_threshold(m: int, w: float, c: int, n: int, v: int, delta: float = 0.0) -> int:
     return int(load().qw_collision_threshold(m, w, c, n, v, delta))
+
+
+def qw_qalsh_collision_probability(r: float, w: float) -> float:
+    return float(load().qw_qalsh_collision_probability(r, w))
+
+
+def qw_qalsh_collision_threshold(m: int, w: float, c: int, n: int, v: int,
+                                 delta: float = 0.0) -> int:
+    return int(load().qw_qalsh_collision_threshold(m, w, c, n, v, delta))
 
 
 def qw_l2_split_model(setaside: float, index_bytes: float, index_reads: float,
@@ -392,12 +408,14 @@ class Index:
 
     ``A`` (m x d) and ``b`` (m) are the hash family's random draws (Section 3),
     passed in so callers control the seed.  ``l = 0`` derives the collision
-    threshold from Eq. 1 (see ``qw_collision_threshold``)."""
+    threshold from Eq. 1 (see ``qw_collision_threshold``).  ``family="qalsh"``
+    builds QALSH's query-aware buckets instead (Section 2; ``b`` is then not
+    used, and queries run on the level path)."""
 
     def __init__(self, data, A=None, b=None, *, w: float, c: int = 2, v: int = 100, l: int = 0,
                  delta: float = 0.0, shadow_bf16: bool = False, bitmaps: bool = False,
                  host_bitmaps: bool = False, m: int = 0, seed: int = 0,
-                 projection: str = "fp32"):
+                 projection: str = "fp32", family: str = "e2lsh"):
         _f32(data, "data")
         n, d = data.shape
         if A is None and b is None:
@@ -416,7 +434,7 @@ class Index:
         p = qw_index_params(m=m, w=float(w), c=int(c), v=int(v), l=int(l), delta=float(delta),
                             shadow_bf16=1 if shadow_bf16 else 0, bitmaps=1 if bitmaps else 0,
                             host_bitmaps=1 if host_bitmaps else 0, seed=int(seed),
-                            projection=PROJECTIONS[projection])
+                            projection=PROJECTIONS[projection], family=FAMILIES[family])
         self._h = 0
         self._h = qw_build_index(data.data_ptr(), n, d, a_ptr or None, b_ptr or None, p, mem,
                                  _stream_of(data))

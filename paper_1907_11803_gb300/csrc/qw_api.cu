@@ -114,6 +114,8 @@ struct qw_index {
     bool bitmaps = false;               // level bitmaps for QW_PATH_BITMAP
     bool host_bitmaps = false;          // ... kept in pinned host memory (bm_host)
     bool proj_tc = false;               // data projected on the tensor cores at build
+    int family = QW_FAMILY_E2LSH;       // bucket family (QW_FAMILY_*)
+    DevBuf qkey, qmin, qmax;            // QALSH: sorted FP64 projections, their extent
     HostBuf bm_host;
     DevBuf bm, bm_base, bm_nb, bm_lvl, bm_J, bid_prefix, prefix_off, perm, bm_sum, Xloc, inv, hloc;
     int hloc_bytes = 0, hloc_stride = 0;
@@ -163,6 +165,12 @@ struct qw_index {
         v.hloc = hloc.p;
         v.hloc_bytes = hloc_bytes;
         v.hloc_stride = hloc_stride;
+        if (family == QW_FAMILY_QALSH) {
+            v.qkey = qkey.as<double>();
+            v.qmin = qmin.as<double>();
+            v.qmax = qmax.as<double>();
+            v.qhalf = 0.5 * (double)w;
+        }
         return v;
     }
 };
@@ -250,13 +258,23 @@ double qw_collision_probability(double r, double w)
            (0.79788456080286535588 / x) * (1.0 - exp(-0.5 * x * x));
 }
 
-int32_t qw_collision_threshold(int32_t m, float w, int32_t c, int64_t n, int32_t v, float delta)
+double qw_qalsh_collision_probability(double r, double w)
+{
+    if (!(r > 0.0) || !(w > 0.0)) return NAN;
+    // a . (o - q) ~ N(0, r^2): P(|N(0, r^2)| <= w / 2) = erf(w / (2 sqrt(2) r))
+    return erf(w / (2.0 * 1.41421356237309504880 * r));
+}
+
+// l = ceil(alpha m), alpha the balance point of p1 = P(1) and p2 = P(c)
+// (Section 3.1's collision threshold), for the family's probability P.
+static int32_t threshold_of(double (*prob)(double, double), int32_t m, float w, int32_t c,
+                            int64_t n, int32_t v, float delta)
 {
     if (m < 1 || !(w > 0.0f) || c < 2 || n < 1 || v < 0) return -1;
     const double dl = delta > 0.0f ? (double)delta : exp(-1.0);
     if (!(dl < 1.0)) return -1;
-    const double p1 = qw_collision_probability(1.0, w);
-    const double p2 = qw_collision_probability((double)c, w);
+    const double p1 = prob(1.0, w);
+    const double p2 = prob((double)c, w);
     double beta = (double)v / (double)n;
     if (beta > 1.0) beta = 1.0;
     if (!(beta > 0.0)) return m;  // no false positive allowed: demand every projection
@@ -264,6 +282,17 @@ int32_t qw_collision_threshold(int32_t m, float w, int32_t c, int64_t n, int32_t
     const double alpha = (z * p1 + p2) / (1.0 + z);
     int32_t l = (int32_t)ceil(alpha * (double)m);
     return std::min(m, std::max(1, l));
+}
+
+int32_t qw_collision_threshold(int32_t m, float w, int32_t c, int64_t n, int32_t v, float delta)
+{
+    return threshold_of(qw_collision_probability, m, w, c, n, v, delta);
+}
+
+int32_t qw_qalsh_collision_threshold(int32_t m, float w, int32_t c, int64_t n, int32_t v,
+                                     float delta)
+{
+    return threshold_of(qw_qalsh_collision_probability, m, w, c, n, v, delta);
 }
 
 static qw_status hash_impl(const float *V, int64_t nv, int32_t d, const float *A, const float *b,
@@ -311,6 +340,69 @@ qw_status qw_hash_tc(const float *V, int64_t nv, int32_t d, const float *A, cons
     return hash_impl(V, nv, d, A, b, m, w, H, n_fixups, stream, true);
 }
 
+// QALSH index: FP64 projections of the data, per (projection, tile) sorted
+// with their in-tile ids; the projections' extent for the radius rule.  No
+// bucket ids: anchors and spans are zero.
+static qw_status build_qalsh(qw_index *ix, cudaStream_t s)
+{
+    const int64_t n = ix->n;
+    const int d = ix->d, m = ix->m, nT = ix->nT;
+    const size_t slots = (size_t)m * nT * kTile;
+    DevBuf P, tlid, scratch;
+    QW_TRY(P.ensure(slots * sizeof(double)));
+    QW_TRY(tlid.ensure(slots * sizeof(uint16_t)));
+    QW_TRY(scratch.ensure(16 + (size_t)m * 16));
+    int *err = scratch.as<int>();
+    QW_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+    // row j of projection i at P[i * nT * kTile + j]: each (projection, tile)
+    // segment sits where its sorted copy goes
+    QW_TRY(launch_fp64_project(ix->X.as<float>(), n, d, ix->A.as<float>(), m, P.as<double>(), 1,
+                               (int64_t)nT * kTile, s));
+    QW_TRY(ix->qmin.ensure((size_t)m * sizeof(double)));
+    QW_TRY(ix->qmax.ensure((size_t)m * sizeof(double)));
+    QW_TRY(launch_qalsh_extent(P.as<double>(), n, (int64_t)nT * kTile, m,
+                               reinterpret_cast<unsigned long long *>(scratch.as<char>() + 16),
+                               ix->qmin.as<double>(), ix->qmax.as<double>(), err, s));
+    QW_TRY(ix->lid.ensure(slots * sizeof(uint16_t)));
+    QW_TRY(ix->qkey.ensure(slots * sizeof(double)));
+    QW_CUDA_TRY(cudaMemsetAsync(ix->lid.p, 0, ix->lid.bytes, s));
+    QW_CUDA_TRY(cudaMemsetAsync(ix->qkey.p, 0, ix->qkey.bytes, s));
+    QW_TRY(launch_qalsh_sort(P.as<double>(), n, m, nT, tlid.as<uint16_t>(), ix->qkey.as<double>(),
+                             ix->lid.as<uint16_t>(), s));
+    QW_TRY(ix->o.ensure((size_t)m * sizeof(int32_t)));
+    QW_TRY(ix->span.ensure((size_t)m * sizeof(int32_t)));
+    QW_CUDA_TRY(cudaMemsetAsync(ix->o.p, 0, ix->o.bytes, s));
+    QW_CUDA_TRY(cudaMemsetAsync(ix->span.p, 0, ix->span.bytes, s));
+    ix->span_max = 0;
+    int h_err = 0;
+    QW_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    QW_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h_err & 2) {
+        set_error("qw_build_index: a data projection is not finite");
+        return QW_ERR_RANGE;
+    }
+    {
+        DevBuf acc;
+        QW_TRY(acc.ensure(16));
+        double rms = 1.0;
+        QW_TRY(data_rms(ix->X.as<float>(), n * (int64_t)d, acc.as<double>(), &rms, s));
+        ix->xs = rms > 0.0 ? (float)(1.0 / rms) : 1.0f;
+    }
+    if (ix->shadow) {
+        QW_TRY(ix->Xb.ensure((size_t)n * d * 2));
+        QW_TRY(ix->xnorm.ensure((size_t)n * sizeof(float)));
+        QW_TRY(ix->Cg.ensure((size_t)((n + 127) / 128) * d * 2));
+        QW_TRY(launch_shadow_bf16(ix->X.as<float>(), n, d, ix->Xb.p, ix->xnorm.as<float>(),
+                                  ix->Cg.p, s));
+    }
+    QW_CUDA_TRY(cudaStreamSynchronize(s));
+    ix->device_bytes = (int64_t)(ix->X.bytes + ix->A.bytes + ix->b.bytes + ix->o.bytes +
+                                 ix->span.bytes + ix->lid.bytes + ix->qkey.bytes +
+                                 ix->qmin.bytes + ix->qmax.bytes + ix->Xb.bytes +
+                                 ix->xnorm.bytes + ix->Cg.bytes);
+    return QW_OK;
+}
+
 static qw_status build_impl(qw_index *ix, const float *data, const float *A, const float *b,
                             int32_t mem, int32_t ab_mem, cudaStream_t s)
 {
@@ -326,6 +418,7 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
     QW_CUDA_TRY(cudaMemcpyAsync(ix->X.p, data, (size_t)n * d * sizeof(float), kind, s));
     QW_CUDA_TRY(cudaMemcpyAsync(ix->A.p, A, (size_t)m * d * sizeof(float), ab_kind, s));
     QW_CUDA_TRY(cudaMemcpyAsync(ix->b.p, b, (size_t)m * sizeof(float), ab_kind, s));
+    if (ix->family == QW_FAMILY_QALSH) return build_qalsh(ix, s);
 
     // 1. bucket ids of the data, projection-major (m x n)
     DevBuf Ht, scratch;
@@ -526,6 +619,13 @@ qw_status qw_build_index(const float *data, int64_t n, int32_t d, const float *A
     if (p->l < 0 || p->l > p->m) return arg_error("qw_build_index: l must be in [0, m]");
     if (p->host_bitmaps && !p->bitmaps)
         return arg_error("qw_build_index: host_bitmaps needs bitmaps");
+    if (p->family != QW_FAMILY_E2LSH && p->family != QW_FAMILY_QALSH)
+        return arg_error("qw_build_index: unknown family");
+    if (p->family == QW_FAMILY_QALSH && p->bitmaps)
+        return arg_error("qw_build_index: QW_FAMILY_QALSH has no level bitmaps");
+    if (p->family == QW_FAMILY_QALSH && p->projection != QW_PROJ_FP32)
+        return arg_error("qw_build_index: QW_FAMILY_QALSH projects in FP64 (projection must be "
+                         "QW_PROJ_FP32)");
     qw_index *ix = new (std::nothrow) qw_index();
     if (!ix) {
         set_error("qw_build_index: host allocation failed");
@@ -537,7 +637,11 @@ qw_status qw_build_index(const float *data, int64_t n, int32_t d, const float *A
     ix->w = p->w;
     ix->c = p->c;
     ix->v = p->v;
-    ix->l = p->l > 0 ? p->l : qw_collision_threshold(p->m, p->w, p->c, n, p->v, p->delta);
+    ix->family = p->family;
+    ix->l = p->l > 0 ? p->l
+                     : (p->family == QW_FAMILY_QALSH
+                            ? qw_qalsh_collision_threshold(p->m, p->w, p->c, n, p->v, p->delta)
+                            : qw_collision_threshold(p->m, p->w, p->c, n, p->v, p->delta));
     if (ix->l < 1) {
         delete ix;
         return arg_error("qw_build_index: cannot derive the collision threshold (bad delta?)");
@@ -745,7 +849,9 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     const int cap = k + ix->v;
     const int64_t wpq_bytes = (int64_t)ix->nT * kTile;  // counter bytes per query
     const int path = qp ? qp->path : QW_PATH_AUTO;
-    const bool order = !qp || qp->order != QW_ORDER_GIVEN;
+    const bool qalsh = ix->family == QW_FAMILY_QALSH;
+    // the workload order groups queries by bucket signature (bucketed family)
+    const bool order = !qalsh && (!qp || qp->order != QW_ORDER_GIVEN);
     const bool host = mem == QW_MEM_HOST;
     const bool bf16 = qp && qp->rerank == QW_RERANK_BF16;
     if (bf16 && !ix->shadow) {
@@ -1009,10 +1115,11 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                                     cudaMemcpyHostToDevice, s));
     int32_t *HQall = ix->w_hq.as<int32_t>();
     QW_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-    QW_TRY(tm.run(QW_K_PROJECT, 2, [&] {
-        return launch_hash(Qall, nq, d, ix->A.as<float>(), ix->b.as<float>(), m, ix->w, HQall, m, 1,
-                           err, nullptr, s, qp && qp->projection == QW_PROJ_TENSOR);
-    }));
+    if (!qalsh)
+        QW_TRY(tm.run(QW_K_PROJECT, 2, [&] {
+            return launch_hash(Qall, nq, d, ix->A.as<float>(), ix->b.as<float>(), m, ix->w, HQall,
+                               m, 1, err, nullptr, s, qp && qp->projection == QW_PROJ_TENSOR);
+        }));
     int32_t *perm = nullptr;
     if (order) {
         char *o = ix->w_order.as<char>();
@@ -1094,7 +1201,26 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                 return QW_ERR_TIMEOUT;
             }
         } else {
-            QW_TRY(tm.run(QW_K_SETUP, 1, [&] { return launch_query_setup(view, HQb, nb, st, s); }));
+            if (qalsh) {
+                // the batch's FP64 projections go to st.g, then the radius rule
+                QW_TRY(tm.run(QW_K_PROJECT, 1, [&] {
+                    return launch_fp64_project(Qb, nb, d, ix->A.as<float>(), m,
+                                               reinterpret_cast<double *>(st.g), m, 1, s);
+                }));
+                QW_TRY(tm.run(QW_K_SETUP, 1, [&] {
+                    return launch_qalsh_setup(view, nb, st, ix->c, err, s);
+                }));
+                int h_err = 0;
+                QW_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+                QW_CUDA_TRY(cudaStreamSynchronize(s));
+                if (h_err & 2) {
+                    set_error("qw_run_workload: no radius below 2^63 makes a query's intervals "
+                              "hold the whole data");
+                    return QW_ERR_RANGE;
+                }
+            } else {
+                QW_TRY(tm.run(QW_K_SETUP, 1, [&] { return launch_query_setup(view, HQb, nb, st, s); }));
+            }
             if (learned) {
                 QW_TRY(tm.run(QW_K_START, 1, [&] {
                     // bitmap path: start at the predicted last level (its previous
@@ -1300,6 +1426,17 @@ static qw_status check_workload_args(const qw_index *ix, const float *queries, i
             return arg_error("qw_run_workload: tiles_per_warp must be 0, 4, 8 or 16");
         if (qp->projection == QW_PROJ_TENSOR && ix->m > 128)
             return arg_error("qw_run_workload: QW_PROJ_TENSOR needs m <= 128");
+        if (ix->family == QW_FAMILY_QALSH) {
+            if (qp->path == QW_PATH_BITMAP || qp->path == QW_PATH_CLUSTER)
+                return arg_error("qw_run_workload: a QALSH index runs on the level path");
+            if (qp->start == QW_START_LEARNED)
+                return arg_error("qw_run_workload: learned start levels need the bucketed family");
+            if (qp->probes > 0)
+                return arg_error("qw_run_workload: multi-probe needs the bucketed family");
+            if (qp->projection != QW_PROJ_FP32)
+                return arg_error("qw_run_workload: a QALSH index projects queries in FP64 "
+                                 "(projection must be QW_PROJ_FP32)");
+        }
     }
     return QW_OK;
 }
@@ -1412,7 +1549,8 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
         if ((status = time_one(cur, &cur_ms)) != QW_OK) break;
         int csize = 0, tpc = 0;
         // 1. first level
-        if (ix->start_model && mlp_inputs(ix->start_model) == ix->d + ix->m) {
+        if (ix->family == QW_FAMILY_E2LSH && ix->start_model &&
+            mlp_inputs(ix->start_model) == ix->d + ix->m) {
             qw_query_params alt = cur;
             alt.start = QW_START_LEARNED;
             if ((status = try_alt(alt)) != QW_OK) break;
@@ -1490,7 +1628,7 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
             }
         }
         // 5. path: the cluster path (plain starts only) against the best so far
-        if (cur.start == QW_START_PLAIN && cur.probes == 0 &&
+        if (ix->family == QW_FAMILY_E2LSH && cur.start == QW_START_PLAIN && cur.probes == 0 &&
             cluster_path_fits(ix->view(), &csize, &tpc)) {
             qw_query_params alt = cur;
             alt.path = QW_PATH_CLUSTER;
@@ -1520,7 +1658,7 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
             if (status != QW_OK) break;
         }
         // 8. the queries' projection on the tensor cores
-        if (ix->m <= 128) {
+        if (ix->family == QW_FAMILY_E2LSH && ix->m <= 128) {
             qw_query_params alt = cur;
             alt.projection = QW_PROJ_TENSOR;
             if ((status = try_alt(alt)) != QW_OK) break;
@@ -1627,6 +1765,7 @@ qw_status qw_index_get_info(const qw_index *ix, qw_index_info *info)
     info->device_bytes = ix->device_bytes;
     info->bitmap_bytes = (int64_t)(ix->host_bitmaps ? ix->bm_host.bytes : ix->bm.bytes);
     info->host_bytes = (int64_t)ix->bm_host.bytes;
+    info->family = ix->family;
     return QW_OK;
 }
 
@@ -1695,6 +1834,8 @@ qw_status qw_index_export(const qw_index *ix, int32_t *o, int32_t *span, int32_t
     if (o) QW_CUDA_TRY(cudaMemcpyAsync(o, ix->o.p, m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     if (span)
         QW_CUDA_TRY(cudaMemcpyAsync(span, ix->span.p, m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if ((entry_bid || entry_id) && ix->family == QW_FAMILY_QALSH)
+        return arg_error("qw_index_export: a QALSH index has no bucket ids");
     if (entry_bid || entry_id) {
         DevBuf eb, ei;
         if (entry_bid) QW_TRY(eb.ensure((size_t)m * n * sizeof(int32_t)));
@@ -1732,7 +1873,8 @@ void qw_index_free(qw_index *ix)
     DevBuf *bmb[] = {&ix->bm,  &ix->bm_base,    &ix->bm_nb,      &ix->bm_lvl,
                      &ix->bm_J, &ix->bid_prefix, &ix->prefix_off, &ix->w_cbits,
                      &ix->w_clist, &ix->perm, &ix->bm_sum, &ix->w_bmsel, &ix->w_ovf,
-                     &ix->w_bmwork, &ix->w_rdstore, &ix->Xloc, &ix->inv, &ix->hloc};
+                     &ix->w_bmwork, &ix->w_rdstore, &ix->Xloc, &ix->inv, &ix->hloc,
+                     &ix->qkey, &ix->qmin, &ix->qmax};
     for (DevBuf *bb : bmb) bb->release();
     for (cudaEvent_t e : ix->event_pool) cudaEventDestroy(e);
     level_graph_cache_free(ix->graphs);

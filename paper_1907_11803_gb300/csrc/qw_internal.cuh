@@ -70,6 +70,20 @@ qw_status launch_hash(const float *V, int64_t nv, int d, const float *A, const f
                       float w, int32_t *H, int64_t ld_row, int64_t ld_col, int *err,
                       unsigned long long *fixups, cudaStream_t s, bool tensor_cores = false);
 
+// ---------------------------------------------------------------- QALSH (qw_qalsh.cu)
+// out[r * ld_r + i * ld_i] = a_i . V_r in FP64, summed in coordinate order.
+qw_status launch_fp64_project(const float *V, int64_t nv, int d, const float *A, int m,
+                              double *out, int64_t ld_r, int64_t ld_i, cudaStream_t s);
+// qmin / qmax (device, m) of the projections P (m rows of ldp doubles, n used);
+// kscratch: 2 m words; err bit 1 when one is not finite.
+qw_status launch_qalsh_extent(const double *P, int64_t n, int64_t ldp, int m,
+                              unsigned long long *kscratch, double *qmin, double *qmax, int *err,
+                              cudaStream_t s);
+// Sort every (tile, projection) segment of P (m rows of nT * kTile doubles,
+// overwritten) into qkey / lid; tlid: scratch of the same shape in uint16.
+qw_status launch_qalsh_sort(double *P, int64_t n, int m, int nT, uint16_t *tlid, double *qkey,
+                            uint16_t *lid, cudaStream_t s);
+
 // ---------------------------------------------------------------- index build
 qw_status launch_minmax(const int32_t *Ht, int64_t n, int m, int32_t *hmin, int32_t *hmax,
                         cudaStream_t s);
@@ -120,6 +134,15 @@ struct IndexView {
     const void *hloc;
     int hloc_bytes;
     int hloc_stride;
+    // QALSH index (null for the bucketed family): per projection i and tile t
+    // the FP64 projections a_i . x of the tile's objects, ascending and aligned
+    // with lid (qkey[i * nT * kTile + t * kTile + p] belongs to lid[same]);
+    // per projection the smallest and largest projection over the data; and
+    // w / 2 in FP64 (the level-R interval is p_i(q) +- qhalf * R)
+    const double *qkey = nullptr;
+    const double *qmin = nullptr;
+    const double *qmax = nullptr;
+    double qhalf = 0.0;
 };
 
 // Entries-scanned statistics from the bid prefix counts (bitmap path), for
@@ -246,6 +269,11 @@ struct LoopCtl {
     uint32_t active;              // queries still running or not yet started after a level
 };
 
+// QALSH: the queries' FP64 projections are in st.g (as double bits); sets
+// every query's radius-rule bound and resets its state (err bit 1: no radius
+// of int64 reaches the whole data).
+qw_status launch_qalsh_setup(const IndexView &ix, int nb, QueryState &st, int cgrow, int *err,
+                             cudaStream_t s);
 qw_status launch_query_setup(const IndexView &ix, const int32_t *HQ, int nb, QueryState &st,
                              cudaStream_t s);
 // Learned first levels: at most each query's last useful level.

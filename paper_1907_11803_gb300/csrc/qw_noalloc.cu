@@ -161,15 +161,24 @@ extern "C" qw_status qw_run_workload_noalloc(qw_index *index, const float *queri
         const float *Qb = queries + b0 * d;
         // the error word and the largest anchored id start at zero every batch
         QW_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-        QW_TRY(launch_hash(Qb, nb, d, P.A, P.b, m, P.w, hq, m, 1, err, nullptr, s));
-        QW_TRY(launch_query_setup(ix, hq, nb, st, s));
+        if (ix.qkey) {
+            // QALSH index: FP64 projections into st.g, then the radius rule
+            QW_TRY(launch_fp64_project(Qb, nb, d, P.A, m, reinterpret_cast<double *>(st.g), m, 1,
+                                       s));
+            QW_TRY(launch_qalsh_setup(ix, nb, st, P.c, err, s));
+        } else {
+            QW_TRY(launch_hash(Qb, nb, d, P.A, P.b, m, P.w, hq, m, 1, err, nullptr, s));
+            QW_TRY(launch_query_setup(ix, hq, nb, st, s));
+        }
         unsigned long long max_top = 0;
         int h_err = 0;
         QW_CUDA_TRY(cudaMemcpyAsync(&max_top, st.max_top, sizeof(max_top), cudaMemcpyDeviceToHost, s));
         QW_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
         QW_CUDA_TRY(cudaStreamSynchronize(s));
         if (h_err & 2) {
-            set_error("qw_run_workload_noalloc: a query bucket id falls outside int32");
+            set_error(ix.qkey ? "qw_run_workload_noalloc: no radius below 2^63 makes a query's "
+                                "intervals hold the whole data"
+                              : "qw_run_workload_noalloc: a query bucket id falls outside int32");
             return QW_ERR_RANGE;
         }
         int64_t R = 1, Rp = 1;

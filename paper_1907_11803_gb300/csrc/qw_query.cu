@@ -139,7 +139,50 @@ __global__ void __launch_bounds__(LV_THREADS) level_kernel(IndexView ix, int lev
     // 1. flank boundaries of every projection (one thread per projection)
     unsigned long long my_scan = 0;
     int my_c0 = 0, my_c1 = 0;
-    if (threadIdx.x < m) {
+    if (ix.qkey) {
+        // QALSH: the run of the tile's sorted projections inside this level's
+        // interval p_i(q) +- qhalf R, and inside the previous level's; thread
+        // 2i + j searches both ends of interval j of projection i (two binary
+        // searches advancing together) and leaves (end << 32 | start) in
+        // f_gc0[2i + j], which projection i's thread reads before it writes
+        // its flanks there
+        if (threadIdx.x < 2 * m && (threadIdx.x & 1) <= (first ? 0 : 1)) {
+            const int i = threadIdx.x >> 1;
+            const double h = __dmul_rn(ix.qhalf, (double)((threadIdx.x & 1) ? Rp : R));
+            const double pq = __longlong_as_double((long long)st.g[(int64_t)q * m + i]);
+            const double *kk = ix.qkey + (int64_t)i * ix.nT * kTile + tbase;
+            int la = 0, ha = len, lb = 0, hb = len;
+            while (la < ha || lb < hb) {
+                if (la < ha) {
+                    const int mid = (la + ha) >> 1;
+                    if (__dsub_rn(kk[mid], pq) < -h) la = mid + 1; else ha = mid;
+                }
+                if (lb < hb) {
+                    const int mid = (lb + hb) >> 1;
+                    if (!(__dsub_rn(kk[mid], pq) > h)) lb = mid + 1; else hb = mid;
+                }
+            }
+            f_gc0[threadIdx.x] = ((int64_t)lb << 32) | (int64_t)la;
+        }
+        __syncthreads();
+        if (threadIdx.x < m) {
+            const int i = threadIdx.x;
+            const int64_t cur = f_gc0[2 * i];
+            const int pA = (int)(cur & 0xffffffff), pB = (int)(cur >> 32);
+            int s0 = pA, e0 = pB, s1 = 0, e1 = 0;
+            if (!first) {
+                // intervals nest from level to level: the two new flanks
+                const int64_t prv = f_gc0[2 * i + 1];
+                e0 = (int)(prv & 0xffffffff);
+                s1 = (int)(prv >> 32);
+                e1 = pB;
+            }
+            const int64_t ebase = (int64_t)i * ix.nT * kTile + tbase;
+            flank_set(fl, 2 * i, ebase + s0, ebase + e0, 0, &my_c0);
+            flank_set(fl, 2 * i + 1, ebase + s1, ebase + e1, 0, &my_c1);
+            my_scan = (unsigned long long)(pB - pA);
+        }
+    } else if (threadIdx.x < m) {
         const int i = threadIdx.x;
         const int64_t gi = st.g[(int64_t)q * m + i];
         const int64_t sp1 = (int64_t)ix.span[i] + 1;

@@ -44,3 +44,24 @@ def query_rows(orc, X, idx, Q, HQ, *, k, v, l, c=2, nthreads=None):
     with cf.ThreadPoolExecutor(max_workers=len(parts)) as ex:
         outs = list(ex.map(one, parts))
     return {key: np.concatenate([o[key] for o in outs]) for key in outs[0]}
+
+
+def project_rows(orc, V, A, nthreads=None):
+    """orc.project over slices of the rows."""
+    parts = _slices(V.shape[0], nthreads or threads())
+    with cf.ThreadPoolExecutor(max_workers=len(parts)) as ex:
+        Ps = list(ex.map(lambda p: orc.project(V[p[0]:p[-1] + 1], A), parts))
+    return np.concatenate(Ps)
+
+
+def qalsh_query_rows(orc, X, P, Q, PQ, *, w, k, v, l, c=2, nthreads=None):
+    """orc.qalsh_query over slices of the queries, concatenated in query order."""
+    parts = _slices(Q.shape[0], nthreads or threads())
+
+    def one(p):
+        s, e = p[0], p[-1] + 1
+        return orc.qalsh_query(X, P, Q[s:e], PQ[s:e], w=w, k=k, v=v, l=l, c=c)
+
+    with cf.ThreadPoolExecutor(max_workers=len(parts)) as ex:
+        outs = list(ex.map(one, parts))
+    return {key: np.concatenate([o[key] for o in outs]) for key in outs[0]}

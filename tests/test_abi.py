@@ -53,6 +53,35 @@ def test_threshold_matches_oracle(qwlib, orc, m, w, c, n, v):
     assert qwlib.collision_threshold(m, w, c, n, v) == orc.threshold(m, w, c, n, v)
 
 
+def test_qalsh_collision_probability_matches_oracle(qwlib, orc):
+    for w in (1.0, 2.719, 4.0):
+        for r in (0.2, 1.0, 2.0, 5.0):
+            assert abs(qwlib.qw_qalsh_collision_probability(r, w) - orc.qalsh_prob(r, w)) < 1e-15
+    assert math.isnan(qwlib.qw_qalsh_collision_probability(-1.0, 4.0))
+
+
+@pytest.mark.parametrize("m,w,c,n,v", [(16, 2.719, 2, 10_000, 100), (64, 2.719, 2, 1_000_000, 700),
+                                       (64, 1.0, 3, 4_000_000, 100), (8, 2.719, 2, 50, 100)])
+def test_qalsh_threshold_is_the_balance_of_its_probabilities(qwlib, orc, m, w, c, n, v):
+    """Section 3.1's rule l = ceil(alpha m) with QALSH's p1 = P(1), p2 = P(c)."""
+    p1, p2 = orc.qalsh_prob(1.0, w), orc.qalsh_prob(float(c), w)
+    beta = min(1.0, v / n)
+    z = math.sqrt(math.log(2.0 / beta) / math.log(math.e))
+    want = min(m, max(1, math.ceil((z * p1 + p2) / (1.0 + z) * m)))
+    assert qwlib.qw_qalsh_collision_threshold(m, w, c, n, v) == want
+
+
+def test_family_arguments_without_device(qwlib):
+    L = qwlib.load()
+    h = C.c_void_p()
+    fake = C.c_void_p(16)
+    for bad, word in ((qwlib.qw_index_params(m=8, w=2.7, c=2, v=10, family=2), b"family"),
+                      (qwlib.qw_index_params(m=8, w=2.7, c=2, v=10, family=1, bitmaps=1), b"bitmaps"),
+                      (qwlib.qw_index_params(m=8, w=2.7, c=2, v=10, family=1, projection=1), b"FP64")):
+        assert L.qw_build_index(fake, 10, 4, fake, fake, C.byref(bad), 0, None, C.byref(h)) == qwlib.QW_ERR_ARG
+        assert word in L.qw_last_error()
+
+
 def test_threshold_rejects_bad_arguments(qwlib):
     assert qwlib.collision_threshold(0, 4.0, 2, 100, 10) == -1
     assert qwlib.collision_threshold(8, -1.0, 2, 100, 10) == -1

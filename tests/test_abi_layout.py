@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 STRUCTS = {
     "qw_index_params": ["m", "w", "c", "v", "l", "delta", "shadow_bf16", "bitmaps",
-                        "host_bitmaps", "seed", "projection"],
+                        "host_bitmaps", "seed", "projection", "family"],
     "qw_query_params": ["batch", "profile", "path", "clusters", "order", "rerank", "start",
                         "graph", "bitmap_loads", "l2_mode", "l2_index_permille", "projection",
                         "rerank_rows", "tiles_per_warp", "probes"],
@@ -22,7 +22,7 @@ STRUCTS = {
                    "bitmap_live_words", "l2_setaside_bytes", "l2_index_permille",
                    "bitmap_overflows"],
     "qw_index_info": ["n", "d", "m", "w", "c", "v", "l", "tile", "n_tiles", "span_max",
-                      "n_fixups", "device_bytes", "bitmap_bytes", "host_bytes"],
+                      "n_fixups", "device_bytes", "bitmap_bytes", "host_bytes", "family"],
     "qw_tune_report": ["tried", "params", "ms", "best"],
 }
 
