@@ -50,6 +50,11 @@ if ROOT not in sys.path:
 # on the latter two.  zipf1m_d256 reaches 0.56 at v = 1000 (its largest
 # clusters hold most points at nearly equal distances) and keeps the default.
 OPERATING_POINTS = {"mix1m_d128": (700, 43), "mix4m_d512": (1000, 0), "mix10m_d128": (1000, 0)}
+# QALSH's query-aware buckets (--family qalsh) with the bucket width of the
+# paper's experiments (Section 6: w = 2.719); l = 0 derives l from QALSH's
+# collision probability.
+QALSH_W = 2.719
+QALSH_OPERATING_POINTS = {"mix1m_d128": (700, 0)}
 
 METRIC = "workload queries/sec at recall>=0.9, ratio<=1.05 (plain vs chosen); HBM roofline %"
 UNIT = "queries/s"
@@ -67,6 +72,9 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="mix10m_d128")
+    p.add_argument("--family", choices=["e2lsh", "qalsh"], default="e2lsh",
+                   help="hash family: Section 3's bucketed h(v) = floor((a.v + b) / w), or "
+                        "QALSH's query-centred intervals (level path, w = 2.719)")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--quality-sample", type=int, default=200,
                    help="queries checked against exact k-NN for recall / ratio")
@@ -130,7 +138,8 @@ def size_overrides(args) -> dict:
 def operating_point(args, spec):
     """(v, l) for this run: explicit flags, else the workload's operating
     point, else the spec's v with l derived from Eq. 1 (l = 0)."""
-    dv, dl = OPERATING_POINTS.get(args.workload, (spec.v, 0))
+    points = QALSH_OPERATING_POINTS if args.family == "qalsh" else OPERATING_POINTS
+    dv, dl = points.get(args.workload, (spec.v, 0))
     v = args.v if args.v >= 0 else dv
     l = args.l if args.l >= 0 else dl
     return v, l
@@ -368,6 +377,51 @@ def oracle_index(wl, threads):
     return orc, orc.build_index(H, sorted_arrays=False)
 
 
+def oracle_qalsh_index(wl, threads):
+    """The oracle and the FP64 projections of the workload's data (QALSH)."""
+    import concurrent.futures as cf
+
+    import numpy as np
+
+    import oracle
+    orc = oracle.get()
+    parts = [p for p in np.array_split(np.arange(wl.X.shape[0]), max(1, threads)) if p.size]
+    with cf.ThreadPoolExecutor(max_workers=len(parts)) as ex:
+        Ps = list(ex.map(lambda p: orc.project(wl.X[p[0]:p[-1] + 1], wl.A), parts))
+    return orc, np.concatenate(Ps)
+
+
+def oracle_qalsh_threads(orc, wl, P, Qs, *, w, k, v, l, c, threads):
+    """The oracle's QALSH query procedure over Qs (projections included), the
+    queries split into `threads` slices answered at the same time.  Returns
+    the wall time in seconds."""
+    import concurrent.futures as cf
+
+    import numpy as np
+    parts = [p for p in np.array_split(np.arange(Qs.shape[0]), threads) if p.size]
+
+    def one(p):
+        PQ = orc.project(Qs[p], wl.A)
+        orc.qalsh_query(wl.X, P, Qs[p], PQ, w=w, k=k, v=v, l=l, c=c)
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=len(parts)) as ex:
+        list(ex.map(one, parts))
+    return time.perf_counter() - t0
+
+
+def oracle_qalsh_sample(wl, w, l, n_queries, seed=1, v=None, threads=1, built=None):
+    """oracle_sample for QALSH's query-aware buckets."""
+    import numpy as np
+    s = wl.spec
+    orc, P = built if built is not None else oracle_qalsh_index(wl, threads)
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(s.nq, size=min(n_queries, s.nq), replace=False))
+    dt = oracle_qalsh_threads(orc, wl, P, wl.Q[pick], w=w, k=s.k, v=s.v if v is None else v,
+                              l=l, c=s.c, threads=threads)
+    return len(pick) / dt, dt, len(pick), (orc, P)
+
+
 def oracle_sample(wl, l, n_queries, seed=1, v=None, threads=1, built=None):
     """Time the oracle's query procedure on a seeded sample of the workload's
     queries (the index build is excluded, as on the GPU) on `threads` host
@@ -434,9 +488,15 @@ def run_ours(args):
     b = torch.from_numpy(wl.b).to(dev)
     Q = torch.from_numpy(wl.Q).to(dev)
     v_used, l_arg = operating_point(args, s)
-    index = qw.Index(X, A, b, w=s.w, c=s.c, v=v_used, l=l_arg,
+    qalsh = args.family == "qalsh"
+    w_used = QALSH_W if qalsh else s.w
+    if qalsh:
+        # the query-aware family runs on the level path from level 0
+        args.start = "plain"
+        args.no_bitmaps = True
+    index = qw.Index(X, A, b, w=w_used, c=s.c, v=v_used, l=l_arg,
                      shadow_bf16=args.rerank == "bf16", bitmaps=not args.no_bitmaps,
-                     host_bitmaps=args.host_bitmaps)
+                     host_bitmaps=args.host_bitmaps, family=args.family)
     ids = torch.empty((s.nq, s.k), dtype=torch.int64, device=dev)
     dists = torch.empty((s.nq, s.k), dtype=torch.float32, device=dev)
     # the library's calls run on a created stream (persisting-L2 windows are
@@ -579,11 +639,21 @@ def run_ours(args):
     steps = args.steps
     hbm = float(peaks["hbm_gbs"])
     entries = float(st[:, 5].sum())      # index entries scanned per step (incremental flanks)
-    count_bytes = entries * 2.0          # 16-bit ids
+    # level path: the 16-bit ids of the flanks, and per (query, tile, level)
+    # pass the tile's byte counters read and written (2 x 32 KiB); QALSH adds
+    # the FP64 keys its range searches read (4 searches of ceil(log2 32768) + 1
+    # probes per projection)
+    tiles = index.info.n_tiles
+    level_passes = prof["level_passes"] / steps
+    count_bytes = entries * 2.0 + level_passes * tiles * 2 * 32768.0
+    if qalsh:
+        count_bytes += level_passes * tiles * s.m * 4 * 16 * 8.0
     dom = "cluster" if prof["ms"]["cluster"] >= prof["ms"]["level"] else "level"
     bitmap = chosen_kw.get("path") == "bitmap"
     dom_name = {"cluster": "cluster_query_kernel (all levels of collision counting, persistent)",
-                "level": "level_kernel (bucket-range search + collision counting)"}[dom]
+                "level": ("level_kernel (QALSH interval search on sorted FP64 projections + "
+                          "collision counting)" if qalsh else
+                          "level_kernel (bucket-range search + collision counting)")}[dom]
     if bitmap and dom == "level":
         if chosen_kw.get("loads", "tma") == "fused":
             # one pass: per (query, tile, level) the m bucket summaries (32 B);
@@ -595,16 +665,15 @@ def run_ours(args):
                            + (prof["bitmap_live_groups"] / steps) * 32.0
                            + (prof["bitmap_live_words"] / steps) * 16.0)
         elif chosen_kw.get("loads", "tma") == "direct":
-            # two passes: per (query, tile, level) the m bucket summaries (32 B);
-            # per live item its m bitmap numbers (int32, written and read); per
-            # live 128-id group its work entry and projection mask (written and
-            # read), the previous and the new candidate word (16 B each), and
-            # the bitmap words of the projections touching it (16 B each)
+            # the same algorithmic bytes as the one-pass form: per (query, tile,
+            # level) the m bucket summaries (32 B); per live 128-id group the
+            # previous and the new candidate word and the bitmap words of the
+            # projections touching it (16 B each).  The work list between the
+            # passes is the implementation's, not the method's.
             dom_name = ("bm_filter_kernel + bm_count_kernel (summary filter, then bit-sliced "
                         "collision counts of the live 128-id groups)")
             count_bytes = ((prof["level_passes"] / steps) * index.info.n_tiles * s.m * 32.0
-                           + (prof["bitmap_live_items"] / steps) * s.m * 8.0
-                           + (prof["bitmap_live_groups"] / steps) * (2 * 12.0 + 32.0)
+                           + (prof["bitmap_live_groups"] / steps) * 32.0
                            + (prof["bitmap_live_words"] / steps) * 16.0)
         else:
             # per (query, level) pass and tile: the m bucket bitmaps, the previous
@@ -662,11 +731,20 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nth = host_threads()
-        built = oracle_index(wl, nth)
-        qps, dt, nsamp, _ = oracle_sample(wl, index.l, max(1, args.cpu_sample) * nth, v=v_used,
-                                          threads=nth, built=built)
-        qps1, dt1, nsamp1, _ = oracle_sample(wl, index.l, max(1, args.cpu_sample), seed=2,
-                                             v=v_used, threads=1, built=built)
+        if qalsh:
+            built = oracle_qalsh_index(wl, nth)
+            qps, dt, nsamp, _ = oracle_qalsh_sample(wl, w_used, index.l,
+                                                    max(1, args.cpu_sample) * nth, v=v_used,
+                                                    threads=nth, built=built)
+            qps1, dt1, nsamp1, _ = oracle_qalsh_sample(wl, w_used, index.l,
+                                                       max(1, args.cpu_sample), seed=2,
+                                                       v=v_used, threads=1, built=built)
+        else:
+            built = oracle_index(wl, nth)
+            qps, dt, nsamp, _ = oracle_sample(wl, index.l, max(1, args.cpu_sample) * nth,
+                                              v=v_used, threads=nth, built=built)
+            qps1, dt1, nsamp1, _ = oracle_sample(wl, index.l, max(1, args.cpu_sample), seed=2,
+                                                 v=v_used, threads=1, built=built)
         cpu = {"value": qps, "unit": UNIT, "cores": nth, "kind": "oracle",
                "sample": f"{nsamp} seeded queries of the same workload, query procedure only, "
                          f"split over {nth} host threads ({dt:.1f} s wall, FP64)",
@@ -679,8 +757,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "n": s.n, "clusters": s.n_clusters, "d": s.d,
-                   "m": s.m, "w": s.w, "c": s.c,
+        "config": {"workload": args.workload, "family": args.family, "n": s.n,
+                   "clusters": s.n_clusters, "d": s.d, "m": s.m, "w": w_used, "c": s.c,
                    "k": s.k, "v": v_used, "l": index.l, "queries_per_gpu": s.nq,
                    "query_clusters": s.query_clusters, "seed": args.seed,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -731,18 +809,32 @@ def run_reference(args):
                                  **size_overrides(args))
     s = wl.spec
     v_used, l_arg = operating_point(args, s)
-    l = l_arg if l_arg > 0 else oracle.get().threshold(s.m, s.w, s.c, s.n, v_used)
+    qalsh = args.family == "qalsh"
+    w_used = float(np.float32(QALSH_W)) if qalsh else s.w
+    if l_arg > 0:
+        l = l_arg
+    elif qalsh:
+        l = oracle.get().qalsh_threshold(s.m, w_used, s.c, s.n, v_used)
+    else:
+        l = oracle.get().threshold(s.m, s.w, s.c, s.n, v_used)
     nth = host_threads()
     per_step = max(1, args.cpu_sample) * nth
-    orc, idx = oracle_index(wl, nth)
+    if qalsh:
+        orc, P = oracle_qalsh_index(wl, nth)
+    else:
+        orc, idx = oracle_index(wl, nth)
     rng = np.random.default_rng(99)
     times = []
     for step in range(args.warmup + args.steps):
         pick = np.sort(rng.choice(s.nq, size=per_step, replace=False))
         Qs = wl.Q[pick]
-        HQ = orc.hash(Qs, wl.A, wl.b, s.w)
-        dt = oracle_query_threads(orc, wl, idx, Qs, HQ, k=s.k, v=v_used, l=l, c=s.c,
-                                  threads=nth)
+        if qalsh:
+            dt = oracle_qalsh_threads(orc, wl, P, Qs, w=w_used, k=s.k, v=v_used, l=l, c=s.c,
+                                      threads=nth)
+        else:
+            HQ = orc.hash(Qs, wl.A, wl.b, s.w)
+            dt = oracle_query_threads(orc, wl, idx, Qs, HQ, k=s.k, v=v_used, l=l, c=s.c,
+                                      threads=nth)
         if step >= args.warmup:
             times.append(dt)
     total = sum(times)
@@ -751,8 +843,8 @@ def run_reference(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total / len(times) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n": s.n, "d": s.d, "m": s.m, "k": s.k,
-                       "v": v_used, "l": l},
+            "config": {"workload": args.workload, "family": args.family, "n": s.n, "d": s.d,
+                       "m": s.m, "w": w_used, "k": s.k, "v": v_used, "l": l},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": nth, "kind": "oracle",
                              "sample": f"{per_step} seeded queries per step, query procedure "
                                        f"only, split over {nth} host threads, FP64"},
@@ -764,7 +856,7 @@ def run_reference(args):
 def main(argv=None):
     args = parse_args(argv)
     if args.steps is None:
-        args.steps = 5 if args.impl == "reference" else 300
+        args.steps = 5 if args.impl == "reference" else 20
     if args.steps < 1 or args.warmup < 0:
         raise SystemExit("--steps must be >= 1 and --warmup >= 0")
     if args.impl == "reference":

@@ -88,6 +88,9 @@ class Oracle:
         L.orc_collision_prob.argtypes = [C.c_double, C.c_double]
         L.orc_alpha.restype = C.c_double
         L.orc_alpha.argtypes = [C.c_double] * 4
+        L.orc_qalsh_threshold.restype = C.c_int32
+        L.orc_qalsh_threshold.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_int64,
+                                          C.c_int32, C.c_double]
         L.orc_threshold.restype = C.c_int32
         L.orc_threshold.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_int64, C.c_int32,
                                     C.c_double]
@@ -144,6 +147,10 @@ class Oracle:
     def threshold(self, m: int, w: float, c: float, n: int, v: int,
                   delta: float = float(np.exp(-1.0))) -> int:
         return int(self.lib.orc_threshold(m, w, c, n, v, delta))
+
+    def qalsh_threshold(self, m: int, w: float, c: float, n: int, v: int,
+                        delta: float = float(np.exp(-1.0))) -> int:
+        return int(self.lib.orc_qalsh_threshold(m, w, c, n, v, delta))
 
     # -- hashing and index -------------------------------------------------
     def hash(self, V: np.ndarray, A: np.ndarray, b: np.ndarray, w: float) -> np.ndarray:

@@ -544,6 +544,20 @@ double orc_qalsh_prob(double r, double w)
     return erf(w / (2.0 * sqrt(2.0) * r));
 }
 
+/* orc_threshold with QALSH's p1 = P(1) and p2 = P(c). */
+int32_t orc_qalsh_threshold(int32_t m, double w, double c, int64_t n, int32_t v, double delta)
+{
+    double p1 = orc_qalsh_prob(1.0, w);
+    double p2 = orc_qalsh_prob(c, w);
+    double beta = (double)v / (double)n;
+    if (beta >= 1.0) beta = 1.0;
+    double alpha = orc_alpha(p1, p2, beta, delta);
+    int32_t l = (int32_t)ceil(alpha * (double)m);
+    if (l < 1) l = 1;
+    if (l > m) l = m;
+    return l;
+}
+
 /* Exact k nearest neighbours by FP64 distance, ties by id (ground truth for
  * recall and the c-k-ANN ratio of Section 3). */
 int orc_bruteforce(const float *X, int64_t n, int32_t d, const float *Q, int64_t nq, int32_t k,

@@ -292,7 +292,9 @@ __device__ __forceinline__ int64_t bm_index(const IndexView &ix, int i, int t, i
 
 // ---- the same level in two passes (the bitmap path's default)
 //
-// Pass 1, one warp per (query, tile): only the bucket summaries are read (8
+// Pass 1, one warp per (query, tile), the tasks taken tile-major (a wave of
+// warps covers one run of tiles for many queries, whose bucket bitmaps then
+// serve all of them from L2): only the bucket summaries are read (8
 // words of 32 bits per projection, one bit per 128-id group), and a carry-save
 // sum over the m projections gives every group the number of the query's
 // buckets that touch it.  Groups below l cannot hold a candidate.  A tile
@@ -390,8 +392,11 @@ __global__ void __launch_bounds__(FL_WARPS * 32, NROW <= 2 ? 3 : 2) bm_filter_ke
     const int par = level & 1;
     for (int64_t k = (int64_t)blockIdx.x * FL_WARPS + (threadIdx.x >> 5); k < tasks;
          k += (int64_t)gridDim.x * FL_WARPS) {
-        const int q = (int)(k / nch);
-        const int t0 = (int)(k % nch) * TPW, t1 = min(nT, t0 + TPW);
+        // tile-major: the warps of a wave take one run of tiles for many
+        // queries, so the bitmaps they touch (and the count pass after them)
+        // stay in L2 across queries
+        const int q = (int)(k % nb);
+        const int t0 = (int)(k / nb) * TPW, t1 = min(nT, t0 + TPW);
         if (!st.active[q] || level < st.start[q]) continue;
         int64_t b0[NROW];
         int32_t nbp[NROW];
@@ -590,8 +595,11 @@ __global__ void __launch_bounds__(FL_WARPS * 32, 2) bm_fused_kernel(IndexView ix
     unsigned long long p_items = 0, p_groups = 0, p_words = 0;
     for (int64_t k = (int64_t)blockIdx.x * FL_WARPS + wi; k < tasks;
          k += (int64_t)gridDim.x * FL_WARPS) {
-        const int q = (int)(k / nch);
-        const int t0 = (int)(k % nch) * TPW, t1 = min(nT, t0 + TPW);
+        // tile-major: the warps of a wave take one run of tiles for many
+        // queries, so the bitmaps they touch (and the count pass after them)
+        // stay in L2 across queries
+        const int q = (int)(k % nb);
+        const int t0 = (int)(k / nb) * TPW, t1 = min(nT, t0 + TPW);
         if (!st.active[q] || level < st.start[q]) continue;
         const bool first = level == st.start[q];
         int64_t b0[NROW];
@@ -852,7 +860,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) bm_level_tma_kernel(IndexView 
         int act_n = 0, start_n = 0;
         auto prefetch = [&](int64_t kk) {
             if (kk >= items) return;
-            const int qq = (int)(kk / nT);
+            const int qq = (int)(kk % nb);
             act_n = st.active[qq];
             start_n = st.start[qq];
 #pragma unroll
@@ -863,7 +871,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) bm_level_tma_kernel(IndexView 
         };
         prefetch(k);
         for (; k < items && !stuck; k += gridDim.x) {
-            const int q = (int)(k / nT), t = (int)(k % nT);
+            // tile-major item order (one tile's bitmaps serve many queries in L2)
+            const int q = (int)(k % nb), t = (int)(k / nb);
             int64_t g[kPL];
 #pragma unroll
             for (int u = 0; u < kPL; ++u) g[u] = gn[u];

@@ -558,6 +558,27 @@ def pin_qalsh_prob_quadrature(orc):
     return fails
 
 
+def pin_qalsh_threshold_balance(orc):
+    """QALSH's l: the balance point of the two Hoeffding bounds (root finder)
+    between p2 = erf(w / (2 sqrt2 c)) and p1 = erf(w / (2 sqrt2)), taken from
+    scipy's erf, and l = ceil(alpha m)."""
+    from scipy.optimize import brentq
+    from scipy.special import erf
+    fails = []
+    delta = math.exp(-1.0)
+    for w, c, n, v, m in ((2.719, 2, 10_000, 100, 16), (2.719, 2, 1_000_000, 700, 64),
+                          (1.0, 3, 4_000_000, 100, 64)):
+        p1 = float(erf(w / (2 * math.sqrt(2.0))))
+        p2 = float(erf(w / (2 * math.sqrt(2.0) * c)))
+        beta = v / n
+        f = lambda a: math.log(1 / delta) / (p1 - a) ** 2 - math.log(2 / beta) / (a - p2) ** 2
+        root = brentq(f, p2 + 1e-9, p1 - 1e-9, xtol=1e-15)
+        l = orc.qalsh_threshold(m, w, c, n, v, delta)
+        if l != min(m, max(1, math.ceil(root * m))):
+            fails.append(f"qalsh l = {l} for alpha {root}, m {m}")
+    return fails
+
+
 def pin_qalsh_project_exact(orc):
     """a_i . v on small integers is exact in any summation order: the
     projections equal the integer matrix product."""
@@ -643,5 +664,6 @@ ALL_PINS = [pin_collision_prob_quadrature, pin_collision_prob_limits, pin_thresh
             pin_single_projection_is_e2lsh, pin_bruteforce, pin_v_ge_n_exact,
             pin_workload_semantics, pin_t3_fixpoint, pin_ratio_invariant,
             pin_duplicates_tie_by_id, pin_hand_worked_golden, pin_multi_probe_semantics,
-            pin_qalsh_hand_worked, pin_qalsh_prob_quadrature, pin_qalsh_project_exact,
+            pin_qalsh_hand_worked, pin_qalsh_prob_quadrature, pin_qalsh_threshold_balance,
+            pin_qalsh_project_exact,
             pin_qalsh_v_ge_n_exact, pin_qalsh_semantics]

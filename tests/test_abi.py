@@ -62,13 +62,9 @@ def test_qalsh_collision_probability_matches_oracle(qwlib, orc):
 
 @pytest.mark.parametrize("m,w,c,n,v", [(16, 2.719, 2, 10_000, 100), (64, 2.719, 2, 1_000_000, 700),
                                        (64, 1.0, 3, 4_000_000, 100), (8, 2.719, 2, 50, 100)])
-def test_qalsh_threshold_is_the_balance_of_its_probabilities(qwlib, orc, m, w, c, n, v):
+def test_qalsh_threshold_matches_oracle(qwlib, orc, m, w, c, n, v):
     """Section 3.1's rule l = ceil(alpha m) with QALSH's p1 = P(1), p2 = P(c)."""
-    p1, p2 = orc.qalsh_prob(1.0, w), orc.qalsh_prob(float(c), w)
-    beta = min(1.0, v / n)
-    z = math.sqrt(math.log(2.0 / beta) / math.log(math.e))
-    want = min(m, max(1, math.ceil((z * p1 + p2) / (1.0 + z) * m)))
-    assert qwlib.qw_qalsh_collision_threshold(m, w, c, n, v) == want
+    assert qwlib.qw_qalsh_collision_threshold(m, w, c, n, v) == orc.qalsh_threshold(m, w, c, n, v)
 
 
 def test_family_arguments_without_device(qwlib):

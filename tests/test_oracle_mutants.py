@@ -63,6 +63,10 @@ MUTANTS = [
     ("qalsh_radius_rule_one_sided",
      "if (!(fabs(pmin[i] - pq[i]) <= half && fabs(pmax[i] - pq[i]) <= half)) all = 0;",
      "if (!(fabs(pmax[i] - pq[i]) <= half)) all = 0;", ["pin_qalsh_v_ge_n_exact", "pin_qalsh_semantics"]),
+    ("qalsh_threshold_uses_e2lsh_probability",
+     "double p1 = orc_qalsh_prob(1.0, w);\n    double p2 = orc_qalsh_prob(c, w);",
+     "double p1 = orc_collision_prob(1.0, w);\n    double p2 = orc_collision_prob(c, w);",
+     ["pin_qalsh_threshold_balance"]),
     ("project_transposed", "const float *a = A + (size_t)i * d;", "const float *a = A + (size_t)i;",
      ["pin_qalsh_project_exact", "pin_qalsh_hand_worked"]),
     ("query_not_anchored", "int64_t g = (int64_t)hq[i] - (int64_t)o[i];\n        int64_t beta",
