@@ -47,9 +47,11 @@ if ROOT not in sys.path:
 # of v and l on the GPU (recall on 200 seeded queries against exact k-NN; l = 0
 # derives l from Eq. 1): the paper's v = 100 gives recall 0.35 on mix1m_d128,
 # 0.24 on mix4m_d512 and 0.34 on mix10m_d128; v = 1000 gives 0.9997 and 0.997
-# on the latter two.  zipf1m_d256 reaches 0.56 at v = 1000 (its largest
-# clusters hold most points at nearly equal distances) and keeps the default.
-OPERATING_POINTS = {"mix1m_d128": (700, 43), "mix4m_d512": (1000, 0), "mix10m_d128": (1000, 0)}
+# on the latter two.  zipf1m_d256 cannot reach 0.9 within k + v <= 4096 (its
+# largest clusters hold most points at nearly equal distances): 0.56 at
+# v = 1000, 0.71 at v = 4086 and l = 32, the best measured, which it uses.
+OPERATING_POINTS = {"mix1m_d128": (700, 43), "mix4m_d512": (1000, 0), "mix10m_d128": (1000, 0),
+                    "zipf1m_d256": (4086, 32)}
 # QALSH's query-aware buckets (--family qalsh) with the bucket width of the
 # paper's experiments (Section 6: w = 2.719); l = 0 derives l from QALSH's
 # collision probability.
@@ -67,6 +69,8 @@ def parse_args(argv=None):
     # default: about one second of timed GPU steps (so that clocks are sampled
     # while they run); 5 steps of the CPU reference arm
     p.add_argument("--steps", type=int, default=None)
+    p.add_argument("--no-plain", action="store_true",
+                   help="skip the plain path (profiler captures of the chosen path only)")
     p.add_argument("--plain-steps", type=int, default=2,
                    help="timed steps of the plain path (at most --steps)")
     p.add_argument("--warmup", type=int, default=3)
@@ -118,6 +122,12 @@ def parse_args(argv=None):
                    help="also time the chosen path under the paper's cache splits (index share "
                         "1, 10, ..., 90, 99 %% of the persisting-L2 set-aside, off, cost model)")
     p.add_argument("--sweep-steps", type=int, default=20)
+    p.add_argument("--cost-sweep", action="store_true",
+                   help="instead of the benchmark line: the persisting-L2 index-window fraction "
+                        "swept over a grid of (n, d) workloads, and a fit of the fastest "
+                        "fraction as a function of (n, d) (one JSON line)")
+    p.add_argument("--cost-grid", default="250000,500000,1000000,2000000:32,128,512",
+                   help="n values : d values of the cost sweep")
     p.add_argument("--v", type=int, default=-1,
                    help="allowed false positives (-1 = the workload's operating point)")
     p.add_argument("--l", type=int, default=-1,
@@ -258,6 +268,7 @@ def measured_peaks():
 
 KERNEL_SOURCES = {
     "level_kernel": ("qw_query.cu", "qw_count.cuh", "qw_dir.cuh", "qw_internal.cuh"),
+    "level_kernel_qalsh": ("qw_query.cu", "qw_count.cuh", "qw_internal.cuh", "qw_qalsh.cu"),
     "bm_filter_count": ("qw_bitmap.cu", "qw_dir.cuh", "qw_scan.cuh", "qw_internal.cuh"),
     "bm_fused_kernel": ("qw_bitmap.cu", "qw_dir.cuh", "qw_scan.cuh", "qw_internal.cuh"),
     "bm_level_tma_kernel": ("qw_bitmap.cu", "qw_tma.cuh", "qw_internal.cuh"),
@@ -278,10 +289,10 @@ def kernel_source_sha(kernel: str) -> str:
 
 
 def ncu_traffic(kernel: str, workload: str):
-    """DRAM bytes (read + write) per timed step of a kernel class from the
+    """DRAM bytes (read + write) per launch of a kernel class from the
     committed ncu summary profiles/traffic.txt, if that was taken on the
     current source of the kernel (lines: kernel workload source-sha
-    bytes-per-step)."""
+    bytes-per-launch)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     sha = kernel_source_sha(kernel)
     try:
@@ -568,14 +579,19 @@ def run_ours(args):
     # and gives its kernel breakdown; one more warm-up step follows (a plain
     # step over the large workloads takes tens of seconds).
     index.profile(reset=True)
-    _, _, st = index.query(Q, s.k, stats=True, profile=True, **plain_kw)
+    if args.no_plain:
+        _, _, st = index.query(Q, s.k, stats=True, **chosen_kw)
+    else:
+        _, _, st = index.query(Q, s.k, stats=True, profile=True, **plain_kw)
     torch.cuda.synchronize()
     p_prof = index.profile(reset=True)
     st = st.cpu().numpy()
-    p_steps = max(1, min(args.steps, args.plain_steps))
-    p_ms, p_ms_max, _, _ = timed(plain_kw, p_steps, warmup=min(args.warmup, 1), profiled=False)
-    ids_plain, dists_plain = ids.clone(), dists.clone()
-    log(f"plain path: {p_ms_max / p_steps:.2f} ms per step")
+    if not args.no_plain:
+        p_steps = max(1, min(args.steps, args.plain_steps))
+        p_ms, p_ms_max, _, _ = timed(plain_kw, p_steps, warmup=min(args.warmup, 1),
+                                     profiled=False)
+        ids_plain, dists_plain = ids.clone(), dists.clone()
+        log(f"plain path: {p_ms_max / p_steps:.2f} ms per step")
 
     clocks = ClockSampler(gpu_uuid(torch))
     clocks.start()
@@ -585,12 +601,14 @@ def run_ours(args):
     l2_prof = {"setaside_bytes": prof["l2_setaside_bytes"],
                "index_permille": prof["l2_index_permille"]} if chosen_kw.get("l2") else None
     value = world * s.nq * args.steps / (ms_max / 1e3)
-    same = bool(torch.equal(ids, ids_plain) and torch.equal(dists, dists_plain))
-    plain = {"value": world * s.nq * p_steps / (p_ms_max / 1e3),
-             "ms_per_step": p_ms_max / p_steps, "steps": p_steps, "settings": plain_kw,
-             "results_identical_to_chosen": same,
-             "warmup": 1 + min(args.warmup, 1),
-             "kernel_ms_first_step": {k2: round(v2, 3) for k2, v2 in p_prof["ms"].items()}}
+    plain = None
+    if not args.no_plain:
+        same = bool(torch.equal(ids, ids_plain) and torch.equal(dists, dists_plain))
+        plain = {"value": world * s.nq * p_steps / (p_ms_max / 1e3),
+                 "ms_per_step": p_ms_max / p_steps, "steps": p_steps, "settings": plain_kw,
+                 "results_identical_to_chosen": same,
+                 "warmup": 1 + min(args.warmup, 1),
+                 "kernel_ms_first_step": {k2: round(v2, 3) for k2, v2 in p_prof["ms"].items()}}
 
     # the paper's cache-split grid (QALSH_Ci/Cd/CiCd/Opt settings, Section 6) on
     # the GPU's persisting L2, with the chosen path's other settings
@@ -634,7 +652,7 @@ def run_ours(args):
     # roofline of the dominant kernel and of the candidate-distance kernel;
     # the L2 read rate (a 64 MiB buffer read with the library's own kernel) is
     # the ceiling of kernels whose reads hit L2
-    l2_gbs = qw.qw_measure_read_bandwidth(64 << 20, 20)
+    l2_gbs = qw.qw_measure_read_bandwidth(64 << 20, 10)
     peaks, peak_kind = measured_peaks()
     steps = args.steps
     hbm = float(peaks["hbm_gbs"])
@@ -705,13 +723,16 @@ def run_ours(args):
     rr_ms = prof["ms"]["rerank"] / steps
     rr_achieved = (rr_bytes / max(rr_launches, 1)) / ((rr_ms / 1e3) / max(rr_launches, 1)) / 1e9 \
         if rr_ms > 0 else 0.0
+    # ncu traffic records are taken on the named workload at its own sizes
+    resized = bool(size_overrides(args)) or bool(args.queries)
     kname = "cluster_query_kernel" if dom == "cluster" else (
         {"direct": "bm_filter_count", "fused": "bm_fused_kernel"}.get(
-            chosen_kw.get("loads", "tma"), "bm_level_tma_kernel") if bitmap else "level_kernel")
+            chosen_kw.get("loads", "tma"), "bm_level_tma_kernel") if bitmap else
+        ("level_kernel_qalsh" if qalsh else "level_kernel"))
     roofline = {"kernel": dom_name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                "traffic": (lambda t: None if t is None else t / max(dom_launches, 1))(
-                    ncu_traffic(kname, args.workload)), "peak_kind": peak_kind,
+                "traffic": None if resized else ncu_traffic(kname, args.workload),
+                "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": per_launch_bytes,
                 "avg_launch_ms": per_launch_s * 1e3, "launches_per_step": dom_launches,
                 "share_of_step": round(dom_ms / (ms / steps), 4),
@@ -719,9 +740,8 @@ def run_ours(args):
     roofline_gather = {"kernel": rr_name, "bound": "hbm",
                        "achieved": round(rr_achieved, 1), "peak": hbm,
                        "frac": round(rr_achieved / hbm, 4), "unit": "GB/s",
-                       "traffic": (lambda t: None if t is None else t / max(rr_launches, 1))(
-                           ncu_traffic("rerank_bf16_kernel" if bf16_rr else "rerank_kernel",
-                                       args.workload)),
+                       "traffic": None if resized else ncu_traffic(
+                           "rerank_bf16_kernel" if bf16_rr else "rerank_kernel", args.workload),
                        "algorithmic_bytes_per_launch": rr_bytes / max(rr_launches, 1),
                        "avg_launch_ms": rr_ms / max(rr_launches, 1),
                        "l2_read_peak": round(l2_gbs, 1), "frac_l2": round(rr_achieved / l2_gbs, 4)}
@@ -796,6 +816,106 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- cost-model sweep
+SWEEP_PERMILLE = [None, 10, 100, 200, 300, 400, 500, 600, 700, 800, 900, 990]
+
+
+def fit_split_model(rows):
+    """Least-squares fit of the fastest index-window permille over the windowed
+    settings, p(n, d) = c0 + c1 log2(n) + c2 log2(d): a model from the data's
+    cardinality and dimensionality to the index share of the cache (Section
+    5.2), refitted to this GPU's measurements.  Returns the coefficients and
+    the residual RMS in permille."""
+    import numpy as np
+    X = np.array([[1.0, np.log2(r["n"]), np.log2(r["d"])] for r in rows])
+    y = np.array([float(r["best_windowed_permille"]) for r in rows])
+    coef, *_ = np.linalg.lstsq(X, y, rcond=None)
+    rms = float(np.sqrt(np.mean((X @ coef - y) ** 2)))
+    return {"form": "permille = c0 + c1 log2(n) + c2 log2(d)",
+            "c": [round(float(c), 3) for c in coef], "rms_permille": round(rms, 1)}
+
+
+def run_cost_sweep(args):
+    """For every (n, d) of the grid: a synthetic mixture workload (n / 1000
+    clusters, m = 64, w = 4, 5,000 queries, k = 10, v = 100), answered on the
+    bitmap path (level loop in graph mode, plain starts) without an L2 window
+    and with the index window given each permille of the persisting-L2
+    set-aside (the rest to the data window); the median of --sweep-steps timed
+    calls per setting; the fastest setting, the fastest windowed one and the
+    library cost model's choice.  Then the fit of the fastest windowed share
+    over (n, d).  Results never depend on the window (checked per setting)."""
+    import numpy as np
+    import torch
+
+    import paper_1907_11803_gb300 as qw
+    import workloads
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ns_txt, ds_txt = args.cost_grid.split(":")
+    ns = [int(x) for x in ns_txt.split(",")]
+    ds = [int(x) for x in ds_txt.split(",")]
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    rows = []
+    for n in ns:
+        for d in ds:
+            wl = workloads.make_workload("mix10k_d32", seed=args.seed, n=n, d=d, m=64,
+                                         n_clusters=max(10, n // 1000), nq=5000, k=10, v=100)
+            s = wl.spec
+            index = qw.Index(torch.from_numpy(wl.X).to(dev), torch.from_numpy(wl.A).to(dev),
+                             torch.from_numpy(wl.b).to(dev), w=4.0, c=2, v=100, l=0,
+                             bitmaps=True)
+            Q = torch.from_numpy(wl.Q).to(dev)
+            ids = torch.empty((s.nq, s.k), dtype=torch.int64, device=dev)
+            dists = torch.empty((s.nq, s.k), dtype=torch.float32, device=dev)
+            base_kw = dict(path="bitmap", loads="direct", start="plain", graph=True,
+                           order="signature", rerank="fp32")
+            ref = None
+            times = []
+            for pm in SWEEP_PERMILLE + ["model"]:
+                kw = dict(base_kw, l2=pm)
+                for _ in range(2):
+                    index.query(Q, s.k, out=(ids, dists), **kw)
+                torch.cuda.synchronize()
+                index.profile(reset=True)
+                t = []
+                for _ in range(args.sweep_steps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    index.query(Q, s.k, out=(ids, dists), **kw)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    t.append(e0.elapsed_time(e1))
+                prof = index.profile(reset=True)
+                same = True
+                if ref is None:
+                    ref = (ids.clone(), dists.clone())
+                else:
+                    same = bool(torch.equal(ids, ref[0]) and torch.equal(dists, ref[1]))
+                times.append({"l2": "off" if pm is None else pm,
+                              "ms": round(float(np.median(t)), 4), "identical": same,
+                              "index_permille": int(prof["l2_index_permille"]) if pm else None,
+                              "setaside_bytes": int(prof["l2_setaside_bytes"]) if pm else None})
+            windowed = [r for r in times if isinstance(r["l2"], int)]
+            best = min(times, key=lambda r: r["ms"])
+            best_w = min(windowed, key=lambda r: r["ms"])
+            model = next(r for r in times if r["l2"] == "model")
+            rows.append({"n": n, "d": d, "index_bytes": int(index.info.device_bytes),
+                         "data_bytes": n * d * 4, "best": best["l2"],
+                         "best_windowed_permille": best_w["l2"],
+                         "model_permille": model["index_permille"],
+                         "off_ms": times[0]["ms"], "best_ms": best["ms"],
+                         "all_identical": all(r["identical"] for r in times), "settings": times})
+            log(f"n {n} d {d}: off {times[0]['ms']:.3f} ms, best {best['l2']} "
+                f"{best['ms']:.3f} ms, best window {best_w['l2']} permille, model "
+                f"{model['index_permille']} permille")
+            index.free()
+            del wl
+    line = {"cost_sweep": rows, "fit": fit_split_model(rows), "steps": args.sweep_steps,
+            "permille_grid": [p for p in SWEEP_PERMILLE if p is not None]}
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(args):
     rank, world, _ = dist_env()
@@ -861,6 +981,8 @@ def main(argv=None):
         raise SystemExit("--steps must be >= 1 and --warmup >= 0")
     if args.impl == "reference":
         run_reference(args)
+    elif args.cost_sweep:
+        run_cost_sweep(args)
     else:
         run_ours(args)
 

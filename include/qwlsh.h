@@ -497,11 +497,11 @@ int32_t qw_l2_split_model(double setaside, double index_bytes, double index_read
                           double data_bytes, double data_reads);
 
 /* Read bandwidth of a device buffer of `bytes` bytes (a measuring tool; the
- * paper has no counterpart): the library allocates the buffer and reads all of
- * it with 16-byte loads cached in L2 only, one launch per read; after one
- * untimed read it times `reps` measurements of back-to-back reads of about
- * 2 GB each (CUDA events on `stream`) and writes the best rate to *gbs in
- * GB/s.  A buffer well below the L2 size (126 MB usable
+ * paper has no counterpart): the library allocates the buffer and reads it
+ * with 16-byte loads cached in L2 only, each thread the same elements on every
+ * pass; each launch makes as many passes as come to about 2 GB; after three
+ * untimed launches it times `reps` launches (CUDA events on `stream`) and
+ * writes the best rate to *gbs in GB/s.  A buffer well below the L2 size (126 MB usable
  * on GB300) gives the rate L2 delivers to the SMs -- the ceiling of kernels
  * whose reads hit L2 -- and one well above it the HBM rate.  Waits for the
  * stream.  Errors: QW_ERR_ARG (bytes < 16, reps < 1, null gbs), QW_ERR_OOM,

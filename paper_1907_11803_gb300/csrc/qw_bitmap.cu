@@ -506,14 +506,6 @@ __global__ void __launch_bounds__(256, 3) bm_count_kernel(IndexView ix, int leve
         const int q = qt2.x, t = qt2.y;
         const int64_t qt = (int64_t)q * nT + t;
         const int4 *bi4 = reinterpret_cast<const int4 *>(st.bm_item_bi + (int64_t)slot * ((m + 3) & ~3));
-        const bool first = level == st.start[q];
-        // the previous level wrote this group's candidate word only if the
-        // tile had candidates and the group was live there
-        const int64_t pq = (int64_t)((level - 1) & 1) * st.cln_par + qt;
-        const bool has_prev = !first && st.clist_n[pq] > 0 &&
-                              ((st.bm_amask[pq * kSumWords + (g >> 5)] >> (g & 31)) & 1u);
-        const uint4 prev = has_prev ? st.cbits[(int64_t)((level - 1) & 1) * st.cb_par + qt * kBmUint4 + g]
-                                    : make_uint4(0, 0, 0, 0);
         Planes P;
 #pragma unroll
         for (int kk = 0; kk < 7; ++kk)
@@ -542,6 +534,15 @@ __global__ void __launch_bounds__(256, 3) bm_count_kernel(IndexView ix, int leve
         st.cbits[(int64_t)(level & 1) * st.cb_par + qt * kBmUint4 + g] = cand;
         const int nc = __popc(cand.x) + __popc(cand.y) + __popc(cand.z) + __popc(cand.w);
         if (nc == 0) continue;
+        // the previous level's candidate word, needed only to flag the new
+        // candidates: written there only if the tile had candidates and the
+        // group was live
+        const bool first = level == st.start[q];
+        const int64_t pq = (int64_t)((level - 1) & 1) * st.cln_par + qt;
+        const bool has_prev = !first && st.clist_n[pq] > 0 &&
+                              ((st.bm_amask[pq * kSumWords + (g >> 5)] >> (g & 31)) & 1u);
+        const uint4 prev = has_prev ? st.cbits[(int64_t)((level - 1) & 1) * st.cb_par + qt * kBmUint4 + g]
+                                    : make_uint4(0, 0, 0, 0);
         atomicAdd(st.clist_n + (int64_t)(level & 1) * st.cln_par + qt, nc);
         atomicAdd(st.cross + q, nc);
         const int pos = atomicAdd(st.qbuf_n + (int64_t)(level & 1) * st.qbn_par + q, nc);

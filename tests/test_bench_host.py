@@ -1,6 +1,7 @@
 """Host-side logic of bench.py: rank aggregation over gloo (world size 2),
 clock parsing, and the reference arm's JSON line on a small workload."""
 import json
+import math
 import os
 import socket
 import subprocess
@@ -76,3 +77,23 @@ def test_reference_arm_json_line():
         assert key in line
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_cost_sweep_fit_recovers_a_planted_model():
+    """The %C_I(n, d) fit of the cost sweep: fastest windowed permilles made
+    from a known log-linear model come back as its coefficients."""
+    import bench
+    rows = [{"n": n, "d": d, "best_windowed_permille": 100 + 30 * math.log2(n / 250000)
+             - 40 * math.log2(d / 32)}
+            for n in (250000, 500000, 1000000, 2000000) for d in (32, 128, 512)]
+    fit = bench.fit_split_model(rows)
+    c0, c1, c2 = fit["c"]
+    assert abs(c1 - 30) < 1e-6 and abs(c2 + 40) < 1e-6
+    assert abs(c0 - (100 - 30 * math.log2(250000) + 40 * math.log2(32))) < 1e-3
+    assert fit["rms_permille"] < 1e-6
+
+
+def test_cost_sweep_arguments():
+    import bench
+    a = bench.parse_args(["--cost-sweep", "--cost-grid", "1000,2000:16,32"])
+    assert a.cost_sweep and a.cost_grid == "1000,2000:16,32"

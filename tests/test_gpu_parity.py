@@ -635,6 +635,56 @@ def test_full_size_sampled(orc, qwlib, cuda):
     mlp.free()
 
 
+def test_full_size_10m_sampled(orc, qwlib, cuda):
+    """The benchmark's largest workload, 10,000,000 x 128 (10,000 clusters,
+    64 projections, w = 4, v = 1,000, l derived from Eq. 1) with its 100,000
+    queries: the benchmark's configuration (bitmap path, signature order,
+    learned first levels, graph mode) against the plain-start bitmap path on
+    every query, and 32 seeded queries recomputed by the oracle."""
+    import torch
+    wl = workloads.make_workload("mix10m_d128", seed=0, n_train=20_000)
+    s = wl.spec
+    v = 1000
+    index = qwlib.Index(_t(wl.X, cuda), _t(wl.A, cuda), _t(wl.b, cuda), w=s.w, c=s.c, v=v, l=0,
+                        bitmaps=True)
+    l = index.l
+    assert l == orc.threshold(s.m, s.w, s.c, s.n, v)
+    Qd = _t(wl.Q, cuda)
+    Qt = _t(wl.Q_train, cuda)
+    _, _, stt = index.query(Qt, s.k, stats=True, path="bitmap")
+    labels = (stt[:, 0] - 1).clamp(0, 15).to(torch.int32).contiguous()
+    F = index.features(Qt)
+    mlp = qwlib.Mlp(F.shape[1], 256, 16)
+    mlp.set_params(qwlib.mlp_init(F.shape[1], 256, 16, seed=5))
+    mlp.train(F, labels, epochs=10, batch=512, lr=1e-3)
+    index.set_start_model(mlp, eps=0.02)
+    index.profile(reset=True)
+    ids, dists, st = index.query(Qd, s.k, stats=True, path="bitmap", order="signature",
+                                 start="learned", graph=True, loads="direct")
+    prof = index.profile(reset=True)
+    ids2, dists2, st2 = index.query(Qd, s.k, stats=True, path="bitmap", order="given",
+                                    start="plain", loads="direct")
+    torch.cuda.synchronize()
+    ids, dists, st = ids.cpu().numpy(), dists.cpu().numpy(), st.cpu().numpy()
+    assert np.array_equal(ids, ids2.cpu().numpy())
+    assert np.array_equal(st, st2.cpu().numpy())
+    assert np.array_equal(dists, dists2.cpu().numpy())
+    assert prof["start_levels_skipped"] > 0
+    H = oracle_par.hash_rows(orc, wl.X, wl.A, wl.b, s.w)
+    oidx = orc.build_index(H, sorted_arrays=False)
+    sample = np.sort(np.random.default_rng(321).choice(s.nq, size=32, replace=False))
+    HQ = orc.hash(wl.Q[sample], wl.A, wl.b, s.w)
+    ref = oracle_par.query_rows(orc, wl.X, oidx, wl.Q[sample], HQ, k=s.k, v=v, l=l, c=s.c)
+    _check_results(ids[sample], dists[sample], ref["ids"], ref["dists"])
+    # the oracle's index without sorted arrays does not count the entries
+    # scanned (statistics 5 and 6); every other statistic is compared
+    cols = [0, 1, 2, 3, 4, 7]
+    assert np.array_equal(st[sample][:, cols], ref["stats"][:, cols])
+    assert np.all((st[:, 4] == 2) | (st[:, 4] == 3))
+    index.free()
+    mlp.free()
+
+
 @pytest.mark.parametrize("graph", [False, True])
 def test_bitmap_path_large_tie_classes(orc, qwlib, cuda, graph):
     """Ten distinct points, 20,000 copies each: whole tiles of candidates and
