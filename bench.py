@@ -97,7 +97,7 @@ def parse_args(argv=None):
                    help="execution path of the query loop (identical results)")
     p.add_argument("--order", choices=["auto", "signature", "given"], default="auto",
                    help="workload order: grouped by bucket signature, or as given")
-    p.add_argument("--rerank", choices=["fp32", "bf16"], default="bf16",
+    p.add_argument("--rerank", choices=["fp32", "bf16", "bf16_tc"], default="bf16",
                    help="distance arithmetic of the chosen path (identical results)")
     p.add_argument("--start", choices=["plain", "learned"], default="learned",
                    help="first level of the chosen path (identical results)")
@@ -275,6 +275,7 @@ KERNEL_SOURCES = {
     "cluster_query_kernel": ("qw_cluster.cu", "qw_count.cuh", "qw_internal.cuh"),
     "rerank_kernel": ("qw_rerank.cu", "qw_scan.cuh", "qw_internal.cuh"),
     "rerank_bf16_kernel": ("qw_rerank.cu", "qw_scan.cuh", "qw_internal.cuh"),
+    "rerank_tc_kernel": ("qw_rerank.cu", "qw_scan.cuh", "qw_tc.cuh", "qw_internal.cuh"),
 }
 
 
@@ -506,7 +507,7 @@ def run_ours(args):
         args.start = "plain"
         args.no_bitmaps = True
     index = qw.Index(X, A, b, w=w_used, c=s.c, v=v_used, l=l_arg,
-                     shadow_bf16=args.rerank == "bf16", bitmaps=not args.no_bitmaps,
+                     shadow_bf16=args.rerank in ("bf16", "bf16_tc"), bitmaps=not args.no_bitmaps,
                      host_bitmaps=args.host_bitmaps, family=args.family)
     ids = torch.empty((s.nq, s.k), dtype=torch.int64, device=dev)
     dists = torch.empty((s.nq, s.k), dtype=torch.float32, device=dev)
@@ -708,8 +709,15 @@ def run_ours(args):
     per_launch_s = (dom_ms / 1e3) / max(dom_launches, 1)
     achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
     kept = float(st[:, 3].sum())
-    bf16_rr = chosen_kw.get("rerank") == "bf16"
-    if bf16_rr:
+    bf16_rr = chosen_kw.get("rerank") in ("bf16", "bf16_tc")
+    if chosen_kw.get("rerank") == "bf16_tc":
+        # tensor-core pre-filter: per kept candidate its residual row (2 d) and
+        # its two per-row constants (8 B); FP32 stage: 4 d bytes per survivor
+        rr_bytes = (kept * (s.d * 2 + 8) + prof["rerank_fp32_rows"] / steps * s.d * 4
+                    + s.nq * s.d * 4 + s.nq * s.k * 12)
+        rr_name = ("rerank_tc_kernel (residual BF16 pre-filter with q.r on the tensor cores, "
+                   "then FP32 gather + L2 + top-k of the survivors)")
+    elif bf16_rr:
         # BF16 pass: per kept candidate its residual row and its group's mean
         # (2 d bytes each); FP32 stage: 4 d bytes per surviving row
         rr_bytes = (kept * s.d * 4 + prof["rerank_fp32_rows"] / steps * s.d * 4
@@ -741,7 +749,8 @@ def run_ours(args):
                        "achieved": round(rr_achieved, 1), "peak": hbm,
                        "frac": round(rr_achieved / hbm, 4), "unit": "GB/s",
                        "traffic": None if resized else ncu_traffic(
-                           "rerank_bf16_kernel" if bf16_rr else "rerank_kernel", args.workload),
+                           {"bf16": "rerank_bf16_kernel", "bf16_tc": "rerank_tc_kernel"}.get(
+                               chosen_kw.get("rerank"), "rerank_kernel"), args.workload),
                        "algorithmic_bytes_per_launch": rr_bytes / max(rr_launches, 1),
                        "avg_launch_ms": rr_ms / max(rr_launches, 1),
                        "l2_read_peak": round(l2_gbs, 1), "frac_l2": round(rr_achieved / l2_gbs, 4)}

@@ -140,7 +140,12 @@ typedef struct {
                              coarse bucket signature (queries of one region share index
                              entries in L2); QW_ORDER_GIVEN: in the caller's order.  Results are
                              returned in the caller's order either way and do not depend on it */
-    int32_t rerank;       /* QW_RERANK_FP32 (default) or QW_RERANK_BF16 (needs shadow_bf16) */
+    int32_t rerank;       /* QW_RERANK_FP32 (default), QW_RERANK_BF16 or QW_RERANK_BF16_TC
+                             (both need shadow_bf16): the BF16 pre-filter on CUDA cores, or with
+                             its dot products q . r~ on the tensor cores (tcgen05, FP32
+                             accumulation in tensor memory, a certified bound per candidate);
+                             both keep every candidate that could be among the k nearest for
+                             the exact FP32 / FP64 stages.  Same results */
     int32_t start;        /* QW_START_PLAIN (default) or QW_START_LEARNED (level path; needs a
                              start model, see qw_index_set_start_model) */
     int32_t graph;        /* non-zero (level path): each batch's level loop runs as one CUDA
@@ -217,9 +222,15 @@ typedef struct {
  * candidate, FP64 for neighbours FP32 cannot order.  QW_RERANK_BF16: distances
  * from the residual BF16 copy first (see shadow_bf16), with a proven error
  * bound; only candidates that could still be among the k nearest go through
- * the FP32/FP64 stage.  Both return the same ids and distances. */
+ * the FP32/FP64 stage.  QW_RERANK_BF16_TC: the same pre-filter with the
+ * candidates' residual rows multiplied by the query on the tensor cores
+ * (tcgen05.mma, BF16 operands, the query split into BF16 hi + lo parts, FP32
+ * accumulation in tensor memory; the per-row constants C_g . r~ and |r~|^2
+ * kept with the residual copy) and its own proven bound.  All three return the
+ * same ids and distances. */
 #define QW_RERANK_FP32 0
 #define QW_RERANK_BF16 1
+#define QW_RERANK_BF16_TC 2
 
 #define QW_ORDER_AUTO 0
 #define QW_ORDER_SIGNATURE 1

@@ -69,8 +69,8 @@ QW_PATH_AUTO, QW_PATH_CLUSTER, QW_PATH_LEVELS, QW_PATH_BITMAP = 0, 1, 2, 3
 PATHS = {"auto": QW_PATH_AUTO, "cluster": QW_PATH_CLUSTER, "levels": QW_PATH_LEVELS,
          "bitmap": QW_PATH_BITMAP}
 QW_ORDER_AUTO, QW_ORDER_SIGNATURE, QW_ORDER_GIVEN = 0, 1, 2
-QW_RERANK_FP32, QW_RERANK_BF16 = 0, 1
-RERANKS = {"fp32": QW_RERANK_FP32, "bf16": QW_RERANK_BF16}
+QW_RERANK_FP32, QW_RERANK_BF16, QW_RERANK_BF16_TC = 0, 1, 2
+RERANKS = {"fp32": QW_RERANK_FP32, "bf16": QW_RERANK_BF16, "bf16_tc": QW_RERANK_BF16_TC}
 ORDERS = {"auto": QW_ORDER_AUTO, "signature": QW_ORDER_SIGNATURE, "given": QW_ORDER_GIVEN}
 QW_START_PLAIN, QW_START_LEARNED = 0, 1
 STARTS = {"plain": QW_START_PLAIN, "learned": QW_START_LEARNED}

@@ -109,7 +109,7 @@ struct qw_index {
     int nT = 0;
     int32_t span_max = 0;
     int64_t n_fixups = 0;
-    DevBuf X, A, b, o, span, lid, dir_bid, dir_off, dir_start, dir_cnt, Xb, xnorm, Cg;
+    DevBuf X, A, b, o, span, lid, dir_bid, dir_off, dir_start, dir_cnt, Xb, xnorm, Cg, Xcr;
     bool shadow = false;
     bool bitmaps = false;               // level bitmaps for QW_PATH_BITMAP
     bool host_bitmaps = false;          // ... kept in pinned host memory (bm_host)
@@ -392,14 +392,15 @@ static qw_status build_qalsh(qw_index *ix, cudaStream_t s)
         QW_TRY(ix->Xb.ensure((size_t)n * d * 2));
         QW_TRY(ix->xnorm.ensure((size_t)n * sizeof(float)));
         QW_TRY(ix->Cg.ensure((size_t)((n + 127) / 128) * d * 2));
+        QW_TRY(ix->Xcr.ensure((size_t)n * sizeof(float2)));
         QW_TRY(launch_shadow_bf16(ix->X.as<float>(), n, d, ix->Xb.p, ix->xnorm.as<float>(),
-                                  ix->Cg.p, s));
+                                  ix->Cg.p, s, ix->Xcr.as<float2>()));
     }
     QW_CUDA_TRY(cudaStreamSynchronize(s));
     ix->device_bytes = (int64_t)(ix->X.bytes + ix->A.bytes + ix->b.bytes + ix->o.bytes +
                                  ix->span.bytes + ix->lid.bytes + ix->qkey.bytes +
                                  ix->qmin.bytes + ix->qmax.bytes + ix->Xb.bytes +
-                                 ix->xnorm.bytes + ix->Cg.bytes);
+                                 ix->xnorm.bytes + ix->Cg.bytes + ix->Xcr.bytes);
     return QW_OK;
 }
 
@@ -587,10 +588,12 @@ static qw_status build_impl(qw_index *ix, const float *data, const float *A, con
         QW_TRY(ix->xnorm.ensure((size_t)n * sizeof(float)));
         QW_TRY(ix->Cg.ensure((size_t)((n + 127) / 128) * d * 2));
         const float *Xs = ix->bitmaps ? ix->Xloc.as<float>() : ix->X.as<float>();
-        QW_TRY(launch_shadow_bf16(Xs, n, d, ix->Xb.p, ix->xnorm.as<float>(), ix->Cg.p, s));
+        QW_TRY(ix->Xcr.ensure((size_t)n * sizeof(float2)));
+        QW_TRY(launch_shadow_bf16(Xs, n, d, ix->Xb.p, ix->xnorm.as<float>(), ix->Cg.p, s,
+                                  ix->Xcr.as<float2>()));
     }
     QW_CUDA_TRY(cudaStreamSynchronize(s));
-    ix->device_bytes = (int64_t)(ix->Xb.bytes + ix->xnorm.bytes + ix->Cg.bytes + ix->X.bytes + ix->A.bytes + ix->b.bytes + ix->o.bytes +
+    ix->device_bytes = (int64_t)(ix->Xb.bytes + ix->xnorm.bytes + ix->Cg.bytes + ix->Xcr.bytes + ix->X.bytes + ix->A.bytes + ix->b.bytes + ix->o.bytes +
                                  ix->span.bytes + ix->lid.bytes + ix->dir_bid.bytes +
                                  ix->dir_off.bytes + ix->dir_start.bytes + ix->dir_cnt.bytes +
                                  ix->bm.bytes + ix->bm_base.bytes + ix->bm_nb.bytes +
@@ -854,8 +857,13 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     const bool order = !qalsh && (!qp || qp->order != QW_ORDER_GIVEN);
     const bool host = mem == QW_MEM_HOST;
     const bool bf16 = qp && qp->rerank == QW_RERANK_BF16;
+    const bool bf16_tc = qp && qp->rerank == QW_RERANK_BF16_TC;
     if (bf16 && !ix->shadow) {
         set_error("qw_run_workload: QW_RERANK_BF16 needs an index built with shadow_bf16");
+        return QW_ERR_ARG;
+    }
+    if (bf16_tc && !ix->shadow) {
+        set_error("qw_run_workload: QW_RERANK_BF16_TC needs an index built with shadow_bf16");
         return QW_ERR_ARG;
     }
     int csize = 0, tpc = 0;
@@ -1269,6 +1277,12 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                                           Qb, nb, k, cap, st,
                                           ids_b, dists_b, tm.on ? rows_ctr : nullptr, s, rr_rows);
             }));
+        else if (want_ids && bf16_tc)
+            QW_TRY(tm.run(QW_K_RERANK, 1, [&] {
+                return launch_rerank_tc(view, ix->Xb.p, ix->xnorm.as<float>(),
+                                        ix->Xcr.as<float2>(), ix->Cg.p, Qb, nb, k, cap, st,
+                                        ids_b, dists_b, tm.on ? rows_ctr : nullptr, err, s);
+            }));
         else if (want_ids)
             QW_TRY(tm.run(QW_K_RERANK, 1, [&] {
                 // bitmap path: candidate rows from the locality-ordered copy
@@ -1285,6 +1299,17 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                 return launch_scatter(perm, b0, nb, k, cap, ids_b, dists_b, stats_b, cids_b, ccol_b,
                                       f_ids, f_dists, f_stats, f_cids, f_ccol, s);
             }));
+        }
+    }
+    if (want_ids && bf16_tc) {
+        // a tensor-core wait of the pre-filter that gave up (bounded waits; the
+        // answers are still exact, every candidate having gone to the exact stages)
+        int h_err = 0;
+        QW_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        QW_CUDA_TRY(cudaStreamSynchronize(s));
+        if (h_err & 32) {
+            set_error("qw_run_workload: a tensor-core wait in the BF16 pre-filter gave up");
+            return QW_ERR_TIMEOUT;
         }
     }
     if (use_bitmap && !graph) {
@@ -1367,7 +1392,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
     if (tm.on) {
         unsigned long long ctr[6] = {0, 0, 0, 0, 0, 0};
         QW_CUDA_TRY(cudaMemcpy(ctr, ix->w_err.as<char>() + 40, sizeof(ctr), cudaMemcpyDeviceToHost));
-        ix->prof.rerank_fp32_rows += (int64_t)(bf16 ? ctr[0] : ctr[1]);
+        ix->prof.rerank_fp32_rows += (int64_t)((bf16 || bf16_tc) ? ctr[0] : ctr[1]);
         ix->prof.rerank_candidates += (int64_t)ctr[1];
         ix->prof.level_passes += (int64_t)ctr[2];
         ix->prof.bitmap_live_items += (int64_t)ctr[3];
@@ -1400,7 +1425,7 @@ static qw_status check_workload_args(const qw_index *ix, const float *queries, i
         if (qp->clusters < 0) return arg_error("qw_run_workload: clusters < 0");
         if (qp->order < QW_ORDER_AUTO || qp->order > QW_ORDER_GIVEN)
             return arg_error("qw_run_workload: unknown order");
-        if (qp->rerank < QW_RERANK_FP32 || qp->rerank > QW_RERANK_BF16)
+        if (qp->rerank < QW_RERANK_FP32 || qp->rerank > QW_RERANK_BF16_TC)
             return arg_error("qw_run_workload: unknown rerank");
         if (qp->start < QW_START_PLAIN || qp->start > QW_START_LEARNED)
             return arg_error("qw_run_workload: unknown start");
@@ -1643,9 +1668,13 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
             if ((status = try_alt(alt)) != QW_OK) break;
         }
         if (ix->shadow) {
-            qw_query_params alt = cur;
-            alt.rerank = QW_RERANK_BF16;
-            if ((status = try_alt(alt)) != QW_OK) break;
+            const qw_query_params keepb = cur;
+            for (int32_t mode : {QW_RERANK_BF16, QW_RERANK_BF16_TC}) {
+                qw_query_params alt = keepb;
+                alt.rerank = mode;
+                if ((status = try_alt(alt)) != QW_OK) break;
+            }
+            if (status != QW_OK) break;
         }
         // tile shape of the rerank: candidate rows per warp
         {
@@ -1864,7 +1893,7 @@ void qw_index_free(qw_index *ix)
     cudaDeviceSynchronize();
     l2_release(&ix->l2_owner);
     ix->bm_host.release();
-    DevBuf *bufs[] = {&ix->X, &ix->Xb, &ix->xnorm, &ix->Cg, &ix->A, &ix->b, &ix->o, &ix->span, &ix->lid,
+    DevBuf *bufs[] = {&ix->X, &ix->Xb, &ix->xnorm, &ix->Cg, &ix->Xcr, &ix->A, &ix->b, &ix->o, &ix->span, &ix->lid,
                       &ix->dir_bid,
                       &ix->dir_off, &ix->dir_start, &ix->dir_cnt, &ix->w_q, &ix->w_hq,
                       &ix->w_state, &ix->w_counters, &ix->w_cand, &ix->w_out, &ix->w_err,

@@ -232,29 +232,44 @@ __global__ void group_centroid_kernel(const float *__restrict__ Xs, int64_t n, i
     }
 }
 
+// Per row r: the BF16 residual r~ to its group mean, a bound R >= |r| of the
+// FP32 residual's norm, and (for the tensor-core pre-filter) C_g . r~ and
+// |r~|^2, summed in FP64 and rounded to FP32 (relative error 2^-24).
 __global__ void shadow_residual_kernel(const float *__restrict__ Xs, int64_t n, int d,
                                        const __nv_bfloat16 *__restrict__ C,
-                                       __nv_bfloat16 *__restrict__ Rb, float *__restrict__ rnorm)
+                                       __nv_bfloat16 *__restrict__ Rb, float *__restrict__ rnorm,
+                                       float2 *__restrict__ rcr)
 {
     const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= n) return;
     const float *x = Xs + r * d;
     const __nv_bfloat16 *cg = C + (r >> 7) * d;
-    double s = 0.0;
+    double s = 0.0, cr = 0.0, rr = 0.0;
     for (int j = lane; j < d; j += 32) {
         const float v = __fsub_rn(x[j], __bfloat162float(cg[j]));
-        Rb[r * d + j] = __float2bfloat16_rn(v);
+        const __nv_bfloat16 vb = __float2bfloat16_rn(v);
+        Rb[r * d + j] = vb;
         s += (double)v * (double)v;
+        const double rb = (double)__bfloat162float(vb);
+        cr += (double)__bfloat162float(cg[j]) * rb;
+        rr += rb * rb;
     }
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) rnorm[r] = __double2float_ru(sqrt(s) * (1.0 + 1e-12));
+    for (int off = 16; off > 0; off >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, off);
+        cr += __shfl_xor_sync(0xffffffffu, cr, off);
+        rr += __shfl_xor_sync(0xffffffffu, rr, off);
+    }
+    if (lane == 0) {
+        rnorm[r] = __double2float_ru(sqrt(s) * (1.0 + 1e-12));
+        if (rcr) rcr[r] = make_float2(__double2float_rn(cr), __double2float_rn(rr));
+    }
 }
 
 }  // namespace
 
 qw_status launch_shadow_bf16(const float *Xs, int64_t n, int d, void *Rb, float *rnorm,
-                             void *C, cudaStream_t s)
+                             void *C, cudaStream_t s, float2 *rcr)
 {
     const int64_t groups = (n + 127) / 128;
     __nv_bfloat16 *Cb = reinterpret_cast<__nv_bfloat16 *>(C);
@@ -262,7 +277,7 @@ qw_status launch_shadow_bf16(const float *Xs, int64_t n, int d, void *Rb, float 
     QW_CUDA_TRY(cudaGetLastError());
     const int64_t blocks = (n + 7) / 8;
     shadow_residual_kernel<<<(unsigned)blocks, 256, 0, s>>>(
-        Xs, n, d, Cb, reinterpret_cast<__nv_bfloat16 *>(Rb), rnorm);
+        Xs, n, d, Cb, reinterpret_cast<__nv_bfloat16 *>(Rb), rnorm, rcr);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }

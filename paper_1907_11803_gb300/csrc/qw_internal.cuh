@@ -374,9 +374,17 @@ qw_status launch_rerank_bf16(const IndexView &ix, const void *Rb, const float *r
                              const QueryState &st, int64_t *ids_out, float *dists_out,
                              unsigned long long *rows_fp32, cudaStream_t s, int rows = 4);
 // Rows Xs (n x d) grouped by 128: C (ceil(n / 128) x d BF16) the group means,
-// Rb (n x d BF16) the residuals to them, rnorm (n) bounds of the residual norms.
+// Rb (n x d BF16) the residuals to them, rnorm (n) bounds of the residual norms,
+// rcr (n, optional) per row (C_g . r~, |r~|^2).
 qw_status launch_shadow_bf16(const float *Xs, int64_t n, int d, void *Rb, float *rnorm,
-                             void *C, cudaStream_t s);
+                             void *C, cudaStream_t s, float2 *rcr = nullptr);
+// The BF16 pre-filter with q . r~ on the tensor cores (tcgen05), then the
+// FP32 / FP64 stages; rcr from launch_shadow_bf16.  err bit 32: a tensor-core
+// wait gave up (the query's candidates then all go to the exact stages).
+qw_status launch_rerank_tc(const IndexView &ix, const void *Rb, const float *rnorm,
+                           const float2 *rcr, const void *C, const float *Qb, int nb, int k,
+                           int cap, const QueryState &st, int64_t *ids_out, float *dists_out,
+                           unsigned long long *rows_fp32, int *err, cudaStream_t s);
 // Xrows/row_of (optional): read data id `id` from row row_of[id] of Xrows
 // (the bitmap path's copy of the data in locality order).
 // rows: candidate rows a warp takes at a time (2, 4 or 8; other values: 4).

@@ -26,6 +26,7 @@
 // distance <= T are sorted; the other stages see exactly that prefix.
 #include "qw_internal.cuh"
 #include "qw_scan.cuh"
+#include "qw_tc.cuh"
 
 #include <cuda_bf16.h>
 #include <math_constants.h>
@@ -532,6 +533,285 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_bf16_kernel(
                   dists_out + (int64_t)q * k, vec);
 }
 
+// BF16 pre-filter on the tensor cores.  The same residual copy r~ = bf16(r),
+// r = fl32(x - C_g), but the distance is expanded so that its only per-
+// candidate dot product is with the query itself: with u' = q - C_g (exact)
+// and w' = u' - r~,
+//   |w'|^2 = |q - C_g|^2 - 2 q.r~ + 2 C_g.r~ + |r~|^2.
+// q.r~ is an MMA: a tile of 128 candidates' residual rows (A, M = 128, K =
+// the dimension padded to 16) against the query split into BF16 hi and lo
+// parts (B, N = 16, two columns used); the BF16 products are exact in FP32,
+// and the tensor cores accumulate in FP32 in tensor memory.  C_g.r~ and
+// |r~|^2 are per-row constants computed at build time in FP64 and rounded to
+// FP32; |q - C_g|^2 is computed once per distinct group of the query's
+// candidates (FP32 chains, relative error rho_s).  The computed a satisfies
+// | a - |w'|^2 | <= E2 = rho_s S + 2 cP |q| R~ + 2^-23 |C_g| R~ + 2^-24 |r~|^2
+//                       + 3.03 2^-24 (S + 2|q.r~| + 2|C_g.r~| + |r~|^2),
+// cP = 2^-16 (the split of q) + 1.02 (K - 1) 2^-22 (the tensor cores' FP32
+// additions, reading R15) + 2^-23, R~ = 1.004 R >= |r~|, |C_g| <= |q| +
+// |q - C_g|.  And | |q - x| - |w'| | <= |(x - C_g) - r| + |r - r~| <=
+// 1.001 (2^-24 + 2^-8) R.  The bounds follow as in rerank_bf16_kernel, and
+// the same selection keeps every candidate that could be among the k
+// nearest for the exact FP32 / FP64 stages.  A tensor-core wait that gives up
+// marks every candidate of the query as a survivor (the result is still the
+// exact one) and sets bit 32 of *err.
+constexpr int TR_ROWS = 128;  // candidates per MMA (M)
+constexpr int TR_N = 16;      // B rows: q_hi, q_lo, then zeros
+constexpr int TR_KC = 64;     // coordinates per staged chunk of the A tile
+constexpr int TR_STAGES = 4;  // chunks in flight
+
+__device__ __forceinline__ uint32_t group_slot(int32_t g, int P2)
+{
+    return ((uint32_t)g * 2654435761u) & (uint32_t)(P2 - 1);
+}
+
+__global__ void __launch_bounds__(RR_THREADS) rerank_tc_kernel(
+    const float *__restrict__ Xr, const int32_t *__restrict__ row_of,
+    const __nv_bfloat16 *__restrict__ Rb, const float *__restrict__ rnorm,
+    const float2 *__restrict__ rcr, const __nv_bfloat16 *__restrict__ Cg, int d,
+    const float *__restrict__ Qb, int k, int cap, int P2, const int32_t *__restrict__ cand,
+    const int32_t *__restrict__ nkeep, int64_t *__restrict__ ids_out,
+    float *__restrict__ dists_out, bool vec, bool vec16, float rho_s, float cP,
+    unsigned long long *__restrict__ rows_fp32, int *__restrict__ err)
+{
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ int scan_tmp[RR_WARPS];
+    __shared__ int any_mark;
+    __shared__ int hist[256];
+    __shared__ int bc[4];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tbase_s;
+    __shared__ int s_stuck;
+    __shared__ float s_qq;
+    const int dk = (d + 15) & ~15;
+    const int KC = dk < TR_KC ? dk : TR_KC;
+    unsigned char *a_t = smraw;                         // TR_STAGES x TR_ROWS x KC BF16
+    unsigned char *b_t = a_t + TR_STAGES * TR_ROWS * KC * 2;  // TR_N x dk BF16
+    RerankSmem sm = carve_rerank(b_t + TR_N * dk * 2, P2, scan_tmp, &any_mark, hist, bc);
+    int32_t *cid = reinterpret_cast<int32_t *>(sm.mark + P2 + 15 - ((P2 + 15) % 16));  // P2 ids
+    int32_t *gkey = reinterpret_cast<int32_t *>(sm.key);  // P2 group slots (-1: empty)
+    float *gS = reinterpret_cast<float *>(sm.key) + P2;    // |q - C_g|^2 per slot
+    int32_t *rowi = sm.sid;                               // row of every candidate
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int q = blockIdx.x;
+    const int nc = nkeep[q];
+    const float *qv = Qb + (int64_t)q * d;
+    const int32_t *cl = cand + (int64_t)q * cap;
+    if (tid == 0) {
+        s_stuck = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
+                         tc_smem(&tbase_s))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // 0. ids, rows, empty group slots, and B: the query split into BF16 hi
+    //    (row 0) and lo (row 1); rows 2..15 and columns past d are zero
+    for (int j = tid; j < nc; j += RR_THREADS) {
+        const int32_t id = cl[j];
+        cid[j] = id;
+        rowi[j] = row_of ? row_of[id] : id;
+    }
+    for (int sl = tid; sl < P2; sl += RR_THREADS) gkey[sl] = -1;
+    for (int e = tid; e < TR_N * dk; e += RR_THREADS) {
+        const int r = e / dk, c = e % dk;
+        float v = 0.0f;
+        if (r < 2 && c < d) {
+            const float x = __ldg(qv + c);
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+            v = r == 0 ? __bfloat162float(hi)
+                       : __bfloat162float(__float2bfloat16_rn(x - __bfloat162float(hi)));
+        }
+        *reinterpret_cast<__nv_bfloat16 *>(b_t + tc_off(r, c, dk)) = __float2bfloat16_rn(v);
+    }
+    if (warp == 0) {
+        float s = 0.0f;
+        for (int c = lane; c < d; c += 32) s = fmaf(__ldg(qv + c), __ldg(qv + c), s);
+        s = warp_sum(s);
+        if (lane == 0) s_qq = s;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tbase_s;
+    // 1. the candidates' distinct groups (open addressing; at most P2 probes,
+    //    and there are at most nc <= P2 distinct groups), then |q - C_g|^2 of
+    //    each, one warp per slot
+    for (int j = tid; j < nc; j += RR_THREADS) {
+        const int32_t g = rowi[j] >> 7;
+        uint32_t h = group_slot(g, P2);
+        for (int p = 0; p < P2; ++p) {
+            const int32_t old = atomicCAS(&gkey[h], -1, g);
+            if (old == -1 || old == g) break;
+            h = (h + 1) & (uint32_t)(P2 - 1);
+        }
+    }
+    __syncthreads();
+    for (int sl = warp; sl < P2; sl += RR_WARPS) {
+        const int32_t g = gkey[sl];
+        if (g < 0) continue;
+        const __nv_bfloat16 *cg = Cg + (int64_t)g * d;
+        float s = 0.0f;
+        for (int c = lane; c < d; c += 32) {
+            const float t = __fsub_rn(__ldg(qv + c), __bfloat162float(cg[c]));
+            s = fmaf(t, t, s);
+        }
+        s = warp_sum(s);
+        if (lane == 0) gS[sl] = s;
+    }
+    __syncthreads();
+    // 2. tiles of TR_ROWS candidates, each in chunks of KC coordinates; the
+    //    chunks of all tiles run through a TR_STAGES-deep cp.async pipeline
+    //    (16-byte copies, rows past the candidates and coordinates past d
+    //    zero-filled), and q . r~ accumulates in tensor memory (columns 0:
+    //    hi, 1: lo).  A buffer is refilled only after the MMA that read it.
+    const uint32_t idesc = tc_idesc_bf16(TR_ROWS, TR_N);
+    const float qn = sqrtf(s_qq) * 1.01f;  // >= |q|
+    const int cpt = (dk + KC - 1) / KC;    // chunks per tile
+    const int n_tiles = (nc + TR_ROWS - 1) / TR_ROWS;
+    const int n_chunks = n_tiles * cpt;
+    auto issue = [&](int ci) {
+        if (ci < n_chunks) {
+            const int t0 = (ci / cpt) * TR_ROWS, k0 = (ci % cpt) * KC;
+            const int kc = (dk - k0) < KC ? (dk - k0) : KC;
+            const int per_row = kc >> 3;
+            unsigned char *buf = a_t + (size_t)(ci % TR_STAGES) * TR_ROWS * KC * 2;
+            for (int p = tid; p < TR_ROWS * per_row; p += RR_THREADS) {
+                const int r = p / per_row, c8 = (p % per_row) * 8;
+                const int j = t0 + r, c = k0 + c8;
+                unsigned char *dst = buf + tc_off(r, c8, KC);
+                if (vec16) {
+                    // whole pieces inside the row are copied, the rest zero-filled
+                    const bool in = j < nc && c + 8 <= d;
+                    const __nv_bfloat16 *src = in ? Rb + (int64_t)rowi[j] * d + c : Rb;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc_smem(dst)),
+                                 "l"(src), "r"(in ? 16 : 0)
+                                 : "memory");
+                } else {
+                    __align__(16) __nv_bfloat16 e8[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        e8[u] = (j < nc && c + u < d) ? Rb[(int64_t)rowi[j] * d + c + u]
+                                                      : __float2bfloat16_rn(0.0f);
+                    *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(e8);
+                }
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    int mma_waited = -1;  // chunks whose MMA this thread has seen complete
+    auto wait_mma = [&](int ci) {
+        if (ci <= mma_waited) return;
+        if (s_stuck == 0 && !tc_wait(&bar, (uint32_t)(ci & 1))) s_stuck = 1;
+        mma_waited = ci;
+    };
+    for (int i = 0; i < TR_STAGES - 1; ++i) issue(i);
+    for (int ci = 0; ci < n_chunks; ++ci) {
+        // the next chunk's buffer held chunk ci - 1: its MMA must be done
+        if (ci > 0) wait_mma(ci - 1);
+        __syncthreads();
+        issue(ci + TR_STAGES - 1);
+        asm volatile("cp.async.wait_group %0;" ::"n"(TR_STAGES - 1) : "memory");
+        tc_fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        const int k0 = (ci % cpt) * KC;
+        const int kc = (dk - k0) < KC ? (dk - k0) : KC;
+        if (tid == 0 && s_stuck == 0) {
+            tc_fence_after();
+            const unsigned char *buf = a_t + (size_t)(ci % TR_STAGES) * TR_ROWS * KC * 2;
+            for (int s2 = 0; s2 < (kc >> 4); ++s2) {
+                const uint32_t acc = (k0 | s2) != 0 ? 1u : 0u;
+                const uint64_t da = tc_desc(buf + (uint32_t)(2 * s2) * 128, 128, KC * 16);
+                const uint64_t db =
+                    tc_desc(b_t + (uint32_t)((k0 >> 3) + 2 * s2) * 128, 128, dk * 16);
+                tc_mma(tbase, da, db, idesc, acc);
+            }
+            tc_commit(&bar);
+        }
+        if (ci % cpt != cpt - 1) continue;
+        // the tile's last chunk: bounds of its rows (warps 0-3 own lanes 0-127)
+        wait_mma(ci);
+        tc_fence_after();
+        __syncthreads();
+        const bool stuck = s_stuck != 0;
+        const int t0 = (ci / cpt) * TR_ROWS;
+        if (warp < 4) {
+            float v[16];
+            tc_ld16(tbase + ((uint32_t)(warp * 32) << 16), v);
+            const int j = t0 + warp * 32 + lane;
+            if (j < nc) {
+                float lo2 = 0.0f, hi2 = CUDART_INF_F;
+                if (!stuck) {
+                    const int64_t row = rowi[j];
+                    const int32_t g = (int32_t)(row >> 7);
+                    uint32_t h = group_slot(g, P2);
+                    float S = 0.0f;
+                    for (int p = 0; p < P2; ++p) {
+                        if (gkey[h] == g) {
+                            S = gS[h];
+                            break;
+                        }
+                        h = (h + 1) & (uint32_t)(P2 - 1);
+                    }
+                    const float Pq = __fadd_rn(v[0], v[1]);
+                    const float2 cr = __ldg(rcr + row);  // (C_g . r~, |r~|^2)
+                    const float R = __ldg(rnorm + row);
+                    const float a = __fadd_rn(__fadd_rn(__fsub_rn(S, 2.0f * Pq), 2.0f * cr.x), cr.y);
+                    const float Rt = R * 1.004f;
+                    const float Cn = qn + sqrtf(S) * 1.01f;
+                    const float absum = S + 2.0f * fabsf(Pq) + 2.0f * fabsf(cr.x) + cr.y;
+                    const float E2 = 1.01f * (rho_s * S + 2.0f * cP * qn * Rt + 0x1p-23f * Cn * Rt +
+                                              0x1p-24f * cr.y + 3.03f * 0x1p-24f * absum);
+                    const float tlo = fmaxf(a - E2, 0.0f) * (1.0f - 0x1p-20f);
+                    const float thi = (a + E2) * (1.0f + 0x1p-20f);
+                    const float wlo = tlo > 0.0f ? tlo * rsqrtf(tlo) : 0.0f;
+                    const float whi = thi > 0.0f ? thi * rsqrtf(thi) : 0.0f;
+                    const float e = 1.001f * 0x1.02p-8f * R;
+                    const float lo = fmaxf(wlo * (1.0f - 0x1p-18f) - e * (1.0f + 0x1p-18f), 0.0f);
+                    const float hi = (whi + e) * (1.0f + 0x1p-18f);
+                    lo2 = lo * lo * (1.0f - 0x1p-18f);
+                    hi2 = hi * hi * (1.0f + 0x1p-18f);
+                }
+                sm.d32[j] = lo2;
+                sm.outd[j] = hi2;
+            }
+        }
+        tc_fence_before();
+        __syncthreads();  // the accumulator is rewritten by the next tile
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && s_stuck) atomicOr(err, 32);
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tbase) : "memory");
+    }
+    // 3. the k-th smallest upper bound; the candidates that could be among the
+    //    k nearest go through the exact stages (the rows array is free now)
+    float uk = CUDART_INF_F;
+    if (nc > k)
+        uk = __uint_as_float(block_kth_smallest<RR_THREADS>(
+            reinterpret_cast<const uint32_t *>(sm.outd), nc, k, sm.hist, sm.bc));
+    const int per = (nc + RR_THREADS - 1) / RR_THREADS;
+    const int j0 = min(nc, tid * per), j1 = min(nc, j0 + per);
+    int mine = 0;
+    for (int j = j0; j < j1; ++j) mine += (sm.d32[j] <= uk) ? 1 : 0;
+    int ns;
+    int pos = block_exclusive_scan<RR_THREADS>(mine, sm.scan_tmp, &ns);
+    for (int j = j0; j < j1; ++j)
+        if (sm.d32[j] <= uk) sm.sid[pos++] = cid[j];
+    __syncthreads();
+    if (rows_fp32 && tid == 0) atomicAdd(rows_fp32, (unsigned long long)ns);
+    int P2s = 2;
+    while (P2s < ns) P2s <<= 1;
+    rerank_finish<4>(Xr, row_of, d, qv, k, P2s, ns, sm, ids_out + (int64_t)q * k,
+                     dists_out + (int64_t)q * k, vec);
+}
+
 }  // namespace
 
 // Rows a warp takes at a time: 2, 4 (default) or 8.
@@ -567,6 +847,44 @@ qw_status launch_rerank_bf16(const IndexView &ix, const void *Rb, const float *r
         Xr, row_of, reinterpret_cast<const __nv_bfloat16 *>(Rb), rnorm,
         reinterpret_cast<const __nv_bfloat16 *>(C), ix.d, Qb, k, cap, P2,
         st.cand, st.nkeep, ids_out, dists_out, vec, inv_omr, inv_opr, rows_fp32))
+    QW_CUDA_TRY(cudaGetLastError());
+    return QW_OK;
+}
+
+qw_status launch_rerank_tc(const IndexView &ix, const void *Rb, const float *rnorm,
+                           const float2 *rcr, const void *C, const float *Qb, int nb, int k,
+                           int cap, const QueryState &st, int64_t *ids_out, float *dists_out,
+                           unsigned long long *rows_fp32, int *err, cudaStream_t s)
+{
+    if (nb == 0) return QW_OK;
+    int P2 = 2;
+    while (P2 < cap) P2 <<= 1;
+    const int d = ix.d;
+    const int dk = (d + 15) & ~15;
+    const int KC = dk < TR_KC ? dk : TR_KC;
+    const size_t smem = (size_t)TR_STAGES * TR_ROWS * KC * 2 + (size_t)TR_N * dk * 2 +
+                        (size_t)P2 * (sizeof(double) + 2 * sizeof(float) + sizeof(int32_t) + 1) +
+                        16 + (size_t)P2 * sizeof(int32_t);
+    if (smem + 2048 > 227 * 1024) {
+        set_error("qw_run_workload: QW_RERANK_BF16_TC needs (k + v) and d small enough for its "
+                  "shared-memory tiles");
+        return QW_ERR_ARG;
+    }
+    QW_CUDA_TRY(cudaFuncSetAttribute(rerank_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    const float *Xr = ix.Xloc ? ix.Xloc : ix.X;
+    const int32_t *row_of = ix.Xloc ? ix.inv : nullptr;
+    const bool vec = (d % 4 == 0) && ((uintptr_t)Qb % 16 == 0) && ((uintptr_t)Xr % 16 == 0);
+    const bool vec16 = (d % 8 == 0) && ((uintptr_t)Rb % 16 == 0);
+    // rho of the FP32 |q - C_g|^2 chains (as the FP32 stage's); the tensor-core
+    // dot product's coefficient with K = d padded to 16 (reading R15)
+    const double rho = (double)((d + 31) / 32 + 12) * 5.9604644775390625e-08 * 1.02;
+    const double cP = 1.52587890625e-05 + 1.02 * (double)(dk - 1) * 2.384185791015625e-07 +
+                      1.1920928955078125e-07;
+    rerank_tc_kernel<<<nb, RR_THREADS, smem, s>>>(
+        Xr, row_of, reinterpret_cast<const __nv_bfloat16 *>(Rb), rnorm, rcr,
+        reinterpret_cast<const __nv_bfloat16 *>(C), d, Qb, k, cap, P2, st.cand, st.nkeep, ids_out,
+        dists_out, vec, vec16, (float)(rho * 1.01), (float)(cP * 1.01), rows_fp32, err);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }

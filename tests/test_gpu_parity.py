@@ -66,7 +66,7 @@ def _gpu_workload(qw, dev, X, Q, A, b, *, w, k, v, l, c=2, batch=0, host=False, 
         Qd = torch.from_numpy(np.ascontiguousarray(Q))
     else:
         Xd, Qd, Ad, bd = _t(X, dev), _t(Q, dev), _t(A, dev), _t(b, dev)
-    index = qw.Index(Xd, Ad, bd, w=w, c=c, v=v, l=l, shadow_bf16=(rerank == "bf16"),
+    index = qw.Index(Xd, Ad, bd, w=w, c=c, v=v, l=l, shadow_bf16=rerank in ("bf16", "bf16_tc"),
                      bitmaps=path.startswith("bitmap"))
     graph = path in ("graph", "bitmap_graph", "bitmap_direct_graph", "bitmap_fused_graph")
     loads = ("direct" if path.startswith("bitmap_direct") else
@@ -330,7 +330,7 @@ def test_tile_shapes_same_results(orc, qwlib, cuda, loads):
     Q = _t(wl.Q, cuda)
     for tpw in (4, 8, 16):
         for rows in (2, 4, 8):
-            for rerank in ("fp32", "bf16"):
+            for rerank in ("fp32", "bf16", "bf16_tc"):
                 for graph in (False, True):
                     ids, dists, st = index.query(Q, 12, stats=True, path="bitmap", loads=loads,
                                                  graph=graph, tiles_per_warp=tpw,
@@ -463,7 +463,7 @@ def test_bitmap_many_projections(orc, qwlib, cuda, path, m):
     _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=10, v=60, path=path)
 
 
-@pytest.mark.parametrize("rerank", ["fp32", "bf16"])
+@pytest.mark.parametrize("rerank", ["fp32", "bf16", "bf16_tc"])
 @pytest.mark.parametrize("path", ["levels", "bitmap_direct_graph"])
 @pytest.mark.parametrize("shell", [12, 60])
 def test_rerank_near_ties_at_k(orc, qwlib, cuda, path, shell, rerank):
@@ -497,19 +497,35 @@ def test_empty_workload(qwlib, cuda):
     index.free()
 
 
+@pytest.mark.parametrize("rerank", ["bf16", "bf16_tc"])
 @pytest.mark.parametrize("path", ["levels", "bitmap_direct_graph"])
-@pytest.mark.parametrize("d", [32, 30])
-def test_bf16_prefilter_rerank_is_exact(orc, qwlib, cuda, d, path):
-    """The BF16 pre-filter keeps every candidate that could be among the k
-    nearest: same ids as the oracle, distances within 1e-5 (d = 30 takes the
-    scalar, unaligned path; an index with bitmaps keeps its residual copy in
-    the locality order, one without in data order)."""
+@pytest.mark.parametrize("d", [32, 30, 100])
+def test_bf16_prefilter_rerank_is_exact(orc, qwlib, cuda, d, path, rerank):
+    """The BF16 pre-filter (on CUDA cores, or with its dot products on the
+    tensor cores) keeps every candidate that could be among the k nearest:
+    same ids as the oracle, distances within 1e-5 (d = 30 and 100 take the
+    scalar, unaligned loads and a dimension padded to the MMA's 16; an index
+    with bitmaps keeps its residual copy in the locality order, one without in
+    data order)."""
     wl = workloads.make_workload("mix10k_d32", seed=31, n=6000, nq=80, d=d)
-    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=10, v=300, rerank="bf16",
+    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=10, v=300, rerank=rerank,
                  path=path)
 
 
-def test_bf16_prefilter_ragged_groups_and_duplicates(orc, qwlib, cuda):
+def test_bf16_tc_prefilter_many_candidates(orc, qwlib, cuda):
+    """The tensor-core pre-filter at k + v = 4,096 candidates per query in
+    d = 256 (32 MMA tiles per query, the largest shared-memory layout), and
+    with a ragged last tile: the oracle's ids."""
+    wl = workloads.make_workload("mix10k_d32", seed=34, n=30000, nq=40, d=256, m=16,
+                                 n_clusters=8)
+    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=10, v=4086, l=2,
+                 rerank="bf16_tc", path="levels")
+    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=7, v=1000, l=2,
+                 rerank="bf16_tc", path="levels")
+
+
+@pytest.mark.parametrize("rerank", ["bf16", "bf16_tc"])
+def test_bf16_prefilter_ragged_groups_and_duplicates(orc, qwlib, cuda, rerank):
     """Residual groups of 128 rows with a ragged last group, exact duplicate
     rows (zero residual spread within a tie) and queries that are data rows
     (distance 0): the bound must hold at both ends."""
@@ -518,7 +534,7 @@ def test_bf16_prefilter_ragged_groups_and_duplicates(orc, qwlib, cuda):
     X[100:140] = X[99]
     Q = np.concatenate([X[[3, 99, 120, 600]], wl.Q[:26]]).astype(np.float32)
     for path in ("levels", "bitmap_direct"):
-        _full_parity(orc, qwlib, cuda, X, Q, wl.A, wl.b, w=4.0, k=12, v=200, rerank="bf16",
+        _full_parity(orc, qwlib, cuda, X, Q, wl.A, wl.b, w=4.0, k=12, v=200, rerank=rerank,
                      path=path)
 
 
@@ -530,10 +546,12 @@ def test_bf16_prefilter_reads_fewer_fp32_rows(qwlib, cuda):
     Q = torch.from_numpy(wl.Q).to(cuda)
     ref_ids, ref_d = index.query(Q, 10, rerank="fp32")
     index.profile(reset=True)
-    ids, dists = index.query(Q, 10, rerank="bf16", profile=True)
-    p = index.profile(reset=True)
-    assert torch.equal(ids, ref_ids)
-    assert p["rerank_fp32_rows"] < p["rerank_candidates"]
+    for rerank in ("bf16", "bf16_tc"):
+        ids, dists = index.query(Q, 10, rerank=rerank, profile=True)
+        p = index.profile(reset=True)
+        assert torch.equal(ids, ref_ids), rerank
+        assert torch.equal(dists, ref_d), rerank
+        assert p["rerank_fp32_rows"] < p["rerank_candidates"], rerank
     index.free()
     with pytest.raises(qwlib.QwError):
         plain = qwlib.Index(X, A, b, w=4.0, v=400)
