@@ -531,9 +531,22 @@ __global__ void __launch_bounds__(256, 3) bm_count_kernel(IndexView ix, int leve
             add8(P, x);
         }
         const uint4 cand = candidates_of(P, l);
-        st.cbits[(int64_t)(level & 1) * st.cb_par + qt * kBmUint4 + g] = cand;
         const int nc = __popc(cand.x) + __popc(cand.y) + __popc(cand.z) + __popc(cand.w);
+        // A group without candidates (most live groups) writes no word: its
+        // live bit is cleared instead, and every reader of candidate words
+        // (the next level, the list rebuild) treats a cleared bit as an empty
+        // word.  Lanes clearing bits of the same mask word combine them.
+        {
+            const int64_t mw = ((int64_t)(level & 1) * st.cln_par + qt) * kSumWords + (g >> 5);
+            const uint32_t clear = nc == 0 ? (1u << (g & 31)) : 0u;
+            const unsigned act = __activemask();
+            const unsigned peers = __match_any_sync(act, (unsigned long long)mw);
+            const uint32_t all = __reduce_or_sync(peers, clear);
+            if (all != 0u && (threadIdx.x & 31) == __ffs(peers) - 1)
+                atomicAnd(st.bm_amask + mw, ~all);
+        }
         if (nc == 0) continue;
+        st.cbits[(int64_t)(level & 1) * st.cb_par + qt * kBmUint4 + g] = cand;
         // the previous level's candidate word, needed only to flag the new
         // candidates: written there only if the tile had candidates and the
         // group was live
