@@ -1249,7 +1249,7 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
                 QW_TRY(host_level_loop(ix, tm, view, nb, cap, learned, use_bitmap, loads, tpw, err,
                                        st, s, &levels_run));
             }
-            QW_TRY(tm.run(QW_K_SELECT, use_bitmap ? (learned ? 3 : 2) : 2, [&] {
+            QW_TRY(tm.run(QW_K_SELECT, use_bitmap ? (learned ? 4 : 2) : 2, [&] {
                 if (use_bitmap)
                     QW_TRY(launch_bm_reduce(view, nb, ix->l, cap, ix->c, st, tma_loads,
                                             (int)std::min<int64_t>(B, bm_reduce_wave(ix->nT)), s));
@@ -1559,11 +1559,13 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
     qw_query_params cur = p0;
     float cur_ms = 0.0f;
     int cur_slot = 0;
+    // an alternative replaces the current setting only when it is more than
+    // 1 % faster (trials differing by less than that are noise)
     auto try_alt = [&](const qw_query_params &alt) -> qw_status {
         float ms = 0.0f;
         const int slot = tried;
         QW_TRY(time_one(alt, &ms));
-        if (ms < cur_ms) {
+        if (ms < cur_ms * 0.99f) {
             cur = alt;
             cur_ms = ms;
             cur_slot = slot;
@@ -1606,12 +1608,24 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
             bp0.path = QW_PATH_BITMAP;
             bp0.batch = 0;
             bp0.graph = 0;
+            bp0.bitmap_loads = QW_LOADS_DIRECT;
             float bms = 0.0f;
             const int bslot = tried;
             if ((status = time_one(bp0, &bms)) != QW_OK) break;
             cur = bp0;
             cur_ms = bms;
             cur_slot = bslot;
+            // the counting kernels first, then the batch size and graph mode
+            // for the kernels chosen
+            {
+                const qw_query_params keepl = cur;
+                for (int32_t ld : {QW_LOADS_TMA, QW_LOADS_FUSED}) {
+                    qw_query_params alt = keepl;
+                    alt.bitmap_loads = ld;
+                    if ((status = try_alt(alt)) != QW_OK) break;
+                }
+                if (status != QW_OK) break;
+            }
             const int64_t cb_b = (int64_t)ix->nT * kBmUint4 * (int64_t)sizeof(uint4) * 2 +
                                  (int64_t)ix->nT * (int64_t)sizeof(int32_t) * 2 +
                                  ((int64_t)kQCap * (int64_t)sizeof(uint64_t) + 4) * 2;
@@ -1629,12 +1643,6 @@ qw_status qw_autotune(qw_index *ix, const float *queries, int64_t nq, int32_t k,
             if (status != QW_OK) break;
             qw_query_params alt = cur;
             alt.graph = 1;
-            if ((status = try_alt(alt)) != QW_OK) break;
-            alt = cur;
-            alt.bitmap_loads = QW_LOADS_DIRECT;
-            if ((status = try_alt(alt)) != QW_OK) break;
-            alt = cur;
-            alt.bitmap_loads = QW_LOADS_FUSED;
             if ((status = try_alt(alt)) != QW_OK) break;
             // tile shape of the filter / fused kernels: tiles per warp
             if (cur.bitmap_loads != QW_LOADS_TMA) {

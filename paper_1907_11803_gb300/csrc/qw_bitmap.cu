@@ -1588,8 +1588,12 @@ __global__ void __launch_bounds__(RD_THREADS) rd_scan_kernel(IndexView ix, Query
 // word by SIMD compares.
 // The plain path would have stopped earlier if |C(L-1)| >= k + v or if radius
 // c^(L-1) already exceeded every useful radius of the query: such queries are
-// marked for the level path.
+// marked for the level path.  A query's candidates are split over
+// kRcSplits blocks (a long list would otherwise leave one block working
+// alone); their counts add up in nprev, and a second kernel compares the sum
+// with k + v.
 constexpr int RC_THREADS = 128;
+constexpr int kRcSplits = 8;
 constexpr int kRcChunks = (QW_MAX_M * 4 + 15) / 16;  // 16-byte pieces of the widest row
 
 // Ids of a 32-bit word within [lo, hi] (element-wise, inclusive).
@@ -1614,6 +1618,7 @@ __global__ void __launch_bounds__(RC_THREADS) bm_recount_kernel(IndexView ix, in
     __shared__ uint4 blo[kRcChunks], bhi[kRcChunks];
     __shared__ int s_nprev;
     const int q = blockIdx.x;
+    const int split = blockIdx.y, nsplit = gridDim.y;
     if (!st.recount[q]) return;
     const int m = ix.m;
     const int L = st.levels[q] - 1;
@@ -1623,7 +1628,7 @@ __global__ void __launch_bounds__(RC_THREADS) bm_recount_kernel(IndexView ix, in
     if (n > kQCap) return;  // the selection marks the query for the level path
     if (R > st.top[q]) {
         // the plain path stops at level L - 1 by radius: not this answer
-        if (threadIdx.x == 0) atomicOr(st.bm_ovf + q, 2);
+        if (threadIdx.x == 0 && split == 0) atomicOr(st.bm_ovf + q, 2);
         return;
     }
     const int chunks = ix.hloc_stride / 16;
@@ -1648,7 +1653,7 @@ __global__ void __launch_bounds__(RC_THREADS) bm_recount_kernel(IndexView ix, in
     __syncthreads();
     const char *H = static_cast<const char *>(ix.hloc);
     int mine = 0;
-    for (int j = threadIdx.x; j < n; j += RC_THREADS) {
+    for (int j = split * RC_THREADS + threadIdx.x; j < n; j += nsplit * RC_THREADS) {
         const uint64_t e = E[j];
         const uint4 *row = reinterpret_cast<const uint4 *>(H + (int64_t)(e >> 32) * ix.hloc_stride);
         int c = 0;
@@ -1667,10 +1672,21 @@ __global__ void __launch_bounds__(RC_THREADS) bm_recount_kernel(IndexView ix, in
     mine = __reduce_add_sync(0xffffffffu, mine);
     if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&s_nprev, mine);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        if (s_nprev >= cap) atomicOr(st.bm_ovf + q, 2);  // the plain path stops at L - 1
-        else st.nprev[q] = s_nprev;
-    }
+    // nprev of a query stopped at its first level starts at 0 (the decision
+    // kernel set it from the empty count before that level)
+    if (threadIdx.x == 0 && s_nprev) atomicAdd(st.nprev + q, s_nprev);
+}
+
+// After the split recount: a query whose |C(L-1)| reaches k + v would have
+// stopped at level L - 1 on the plain path; it is marked for the level path.
+__global__ void recount_decide_kernel(QueryState st, int nb, int cap, int cgrow)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nb || !st.recount[q]) return;
+    const int L = st.levels[q] - 1;
+    if (st.qbuf_n[(int64_t)(L & 1) * st.qbn_par + q] > kQCap) return;
+    if (st.finalR[q] / cgrow > st.top[q]) return;
+    if (st.nprev[q] >= cap) atomicOr(st.bm_ovf + q, 2);
 }
 
 template <typename T>
@@ -2048,12 +2064,15 @@ qw_status launch_bm_recount(const IndexView &ix, int nb, int l, int cap, int cgr
                             cudaStream_t s)
 {
     if (nb == 0) return QW_OK;
+    const dim3 grid((unsigned)nb, kRcSplits);
     if (ix.hloc_bytes == 1)
-        bm_recount_kernel<uint8_t><<<nb, RC_THREADS, 0, s>>>(ix, l, cap, cgrow, st);
+        bm_recount_kernel<uint8_t><<<grid, RC_THREADS, 0, s>>>(ix, l, cap, cgrow, st);
     else if (ix.hloc_bytes == 2)
-        bm_recount_kernel<uint16_t><<<nb, RC_THREADS, 0, s>>>(ix, l, cap, cgrow, st);
+        bm_recount_kernel<uint16_t><<<grid, RC_THREADS, 0, s>>>(ix, l, cap, cgrow, st);
     else
-        bm_recount_kernel<uint32_t><<<nb, RC_THREADS, 0, s>>>(ix, l, cap, cgrow, st);
+        bm_recount_kernel<uint32_t><<<grid, RC_THREADS, 0, s>>>(ix, l, cap, cgrow, st);
+    QW_CUDA_TRY(cudaGetLastError());
+    recount_decide_kernel<<<(nb + 255) / 256, 256, 0, s>>>(st, nb, cap, cgrow);
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }
