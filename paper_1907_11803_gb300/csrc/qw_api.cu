@@ -1273,8 +1273,8 @@ static qw_status run_impl(qw_index *ix, const float *queries, int64_t nq, int k,
         if (want_ids) QW_TRY(l2.use(L2Use::Data, s));
         if (want_ids && bf16)
             QW_TRY(tm.run(QW_K_RERANK, 1, [&] {
-                return launch_rerank_bf16(view, ix->Xb.p, ix->xnorm.as<float>(), ix->Cg.p,
-                                          Qb, nb, k, cap, st,
+                return launch_rerank_bf16(view, ix->Xb.p, ix->xnorm.as<float>(),
+                                          ix->Xcr.as<float2>(), ix->Cg.p, Qb, nb, k, cap, st,
                                           ids_b, dists_b, tm.on ? rows_ctr : nullptr, s, rr_rows);
             }));
         else if (want_ids && bf16_tc)

@@ -370,7 +370,8 @@ qw_status launch_candidates_out(const QueryState &st, int nb, int cap, int64_t *
 // BF16 copy built by launch_shadow_bf16 over the index's row order (the
 // locality order when the index has bitmaps, read through ix.inv).
 qw_status launch_rerank_bf16(const IndexView &ix, const void *Rb, const float *rnorm,
-                             const void *C, const float *Qb, int nb, int k, int cap,
+                             const float2 *rcr, const void *C, const float *Qb, int nb, int k,
+                             int cap,
                              const QueryState &st, int64_t *ids_out, float *dists_out,
                              unsigned long long *rows_fp32, cudaStream_t s, int rows = 4);
 // Rows Xs (n x d) grouped by 128: C (ceil(n / 128) x d BF16) the group means,

@@ -44,6 +44,43 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
+// Warp sums of R per-lane values a[0..R) (R a power of two <= 32) in
+// 5 + R - 1 - log2 R shuffles: at each of the first log2 R steps a lane
+// keeps half of its values and adds its partner's half of the others.  Lane
+// l returns the sum of value l >> (5 - log2 R) (every value's sum is a tree
+// of 5 additions over the lanes' partial sums, as in warp_sum).
+// One halving step: lanes with `off` set keep value hi and receive their
+// partner's hi; the others keep lo and receive the partner's lo.
+__device__ __forceinline__ float fold_pair(float lo, float hi, bool up, int off)
+{
+    const float send = up ? lo : hi;
+    return (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, send, off);
+}
+
+template <int R>
+__device__ __forceinline__ float rows_sum(const float (&a)[R], int lane)
+{
+    static_assert(R == 2 || R == 4 || R == 8, "rows per warp: 2, 4 or 8");
+    float v;
+    if constexpr (R == 2) {
+        v = fold_pair(a[0], a[1], (lane & 16) != 0, 16);
+    } else if constexpr (R == 4) {
+        const bool u = (lane & 16) != 0;
+        const float b0 = fold_pair(a[0], a[2], u, 16), b1 = fold_pair(a[1], a[3], u, 16);
+        v = fold_pair(b0, b1, (lane & 8) != 0, 8);
+    } else {
+        const bool u = (lane & 16) != 0;
+        const float b0 = fold_pair(a[0], a[4], u, 16), b1 = fold_pair(a[1], a[5], u, 16);
+        const float b2 = fold_pair(a[2], a[6], u, 16), b3 = fold_pair(a[3], a[7], u, 16);
+        const bool u2 = (lane & 8) != 0;
+        const float c0 = fold_pair(b0, b2, u2, 8), c1 = fold_pair(b1, b3, u2, 8);
+        v = fold_pair(c0, c1, (lane & 4) != 0, 4);
+    }
+#pragma unroll
+    for (int off = 16 / R; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
 // Shared-memory arrays of one query's rerank (P2 entries each), and small
 // scratch: scan_tmp (RR_WARPS ints), hist (256 ints), bc (4 ints).
 struct RerankSmem {
@@ -360,70 +397,214 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(
                   dists_out + (int64_t)q * k, vec);
 }
 
-// BF16 pre-filter.  Distances to every kept candidate are first computed from
+// BF16 pre-filter.  Distances to every kept candidate are first bounded from
 // the index's residual BF16 copy (half the bytes of the rows): row r of the
 // rerank's row order is stored as r~ = bf16(r), r = fl32(x - C_g), C_g the
-// mean of its 128-row group g = r / 128 rounded to BF16 (in the locality order the group
-// is spatially compact, so |r| is about the group's spread).  The kernel forms
-// u = fl32(q - C_g) and a = the FP32 sum of fl32(u - r~)^2 (per-lane FMA
-// chains, butterfly sum: relative error <= rho, as in the FP32 stage).
-// With w = u - r~ (exact), v = q - x, and R >= |r|:
-//   |w - v| <= |u - (q - C_g)| + |(x - C_g) - r| + |r - r~|
-//           <= 2^-24 |q - C_g| + 2^-24 |x - C_g| + 2^-8 R,
-// and |q - C_g| <= |v| + |x - C_g|, |v| <= |w| + |w - v|, |x - C_g| <=
-// R / (1 - 2^-24), so |w - v| <= E = 1.001 (2^-8 R + 2^-23 R + 2^-24 W_hi),
-// W_hi = sqrt(a / (1 - rho)) >= |w|, W_lo = sqrt(a / (1 + rho)) <= |w|.
-// Hence |v|^2 lies in [max(0, W_lo - E)^2, (W_hi + E)^2]; every bound is
-// formed in FP32 with relative margins of 2^-18 that cover the rounding of the
-// bound arithmetic itself (no FP64 work per candidate).  A
-// candidate whose lower bound exceeds the k-th smallest upper bound cannot be
-// among the k nearest (the k candidates with the smallest upper bounds all lie
-// within it); all others go through the exact FP32 + FP64 stages on the FP32
-// rows, so the result is the same as without the pre-filter.
+// mean of its 128-row group g = r / 128 rounded to BF16 (in the locality order
+// the group is spatially compact, so |r| is about the group's spread).  With
+// u' = q - C_g and w' = u' - r~ (both exact),
+//   |w'|^2 = |q - C_g|^2 - 2 q.r~ + 2 C_g.r~ + |r~|^2,
+// so the only per-candidate dot product is q.r~, over the BF16 row alone:
+// FP32 FMA chains per lane and a butterfly sum (each BF16 value is exact in
+// FP32), |P - q.r~| <= gam |q| |r~| with gam >= 1.02 (ceil(d / 32) + 8) 2^-24.
+// C_g.r~ and |r~|^2 are per-row constants computed at build time in FP64 and
+// rounded to FP32; S = |q - C_g|^2 is computed once per distinct group of the
+// query's candidates (FP32 chains, relative error rho_s).  The computed
+// a = ((S - 2P) + 2 C_g.r~) + |r~|^2 then satisfies
+// | a - |w'|^2 | <= E2 = rho_s S + 2 gam |q| R~ + 2^-23 |C_g| R~ + 2^-24 |r~|^2
+//                       + 3.03 2^-24 (S + 2|P| + 2|C_g.r~| + |r~|^2),
+// with R~ = 1.004 R >= |r~| (R >= |r| is stored per row) and |C_g| <= |q| +
+// |q - C_g|.  And | |q - x| - |w'| | <= |(x - C_g) - r| + |r - r~| <= 1.001
+// (2^-24 + 2^-8) R = e.  Hence |q - x| lies in [max(0, W_lo - e), W_hi + e],
+// W_lo / W_hi the square roots of max(0, a - E2) and a + E2; every bound is
+// formed in FP32 with relative margins of 2^-18 or more that cover the
+// rounding of the bound arithmetic itself (rsqrtf: 2 ulp).  A candidate whose
+// lower bound exceeds the k-th smallest upper bound cannot be among the k
+// nearest (the k candidates with the smallest upper bounds all lie within
+// it); all others go through the exact FP32 + FP64 stages on the FP32 rows, so
+// the result is the same as without the pre-filter.
+__device__ __forceinline__ uint32_t group_slot(int32_t g, int P2)
+{
+    return ((uint32_t)g * 2654435761u) & (uint32_t)(P2 - 1);
+}
+
+// The candidates' distinct groups into the open-addressed table gkey (P2
+// slots, -1 empty; at most nc <= P2 distinct groups, so an insertion ends
+// within P2 probes), then |q - C_g|^2 of each slot, one warp per slot.
+__device__ __forceinline__ void group_norms(const int32_t *rowi, int nc, int P2, int32_t *gkey,
+                                            float *gS, const __nv_bfloat16 *__restrict__ Cg,
+                                            const float *__restrict__ qv, int d)
+{
+    // 16-byte loads of the query and of the group means when aligned
+    const bool vec16 = (d % 8 == 0) && (((uintptr_t)qv | (uintptr_t)Cg) % 16 == 0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = threadIdx.x; j < nc; j += RR_THREADS) {
+        const int32_t g = rowi[j] >> 7;
+        uint32_t h = group_slot(g, P2);
+        for (int p = 0; p < P2; ++p) {
+            const int32_t old = atomicCAS(&gkey[h], -1, g);
+            if (old == -1 || old == g) break;
+            h = (h + 1) & (uint32_t)(P2 - 1);
+        }
+    }
+    __syncthreads();
+    // a warp takes windows of kG slots of its share (rows of the occupied
+    // ones loaded together; windows without a group are skipped)
+    constexpr int kG = 8;
+    const int per = ((P2 + RR_WARPS - 1) / RR_WARPS + kG - 1) / kG * kG;
+    const int s1 = min(P2, (warp + 1) * per);
+    for (int sl = warp * per; sl < s1; sl += kG) {
+        int32_t g[kG];
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < kG; ++u) {
+            g[u] = sl + u < s1 ? gkey[sl + u] : -1;
+            any |= g[u] >= 0;
+        }
+        if (!any) continue;
+        float acc[kG];
+        const __nv_bfloat16 *cg[kG];
+#pragma unroll
+        for (int u = 0; u < kG; ++u) {
+            acc[u] = 0.0f;
+            cg[u] = Cg + (int64_t)(g[u] >= 0 ? g[u] : 0) * d;
+        }
+        if (vec16) {
+            for (int c = lane; c < (d >> 3); c += 32) {
+                const float4 b0 = __ldg(reinterpret_cast<const float4 *>(qv) + 2 * c);
+                const float4 b1 = __ldg(reinterpret_cast<const float4 *>(qv) + 2 * c + 1);
+                const float qc[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                uint4 raw[kG];
+#pragma unroll
+                for (int u = 0; u < kG; ++u)
+                    raw[u] = g[u] >= 0 ? __ldg(reinterpret_cast<const uint4 *>(cg[u]) + c)
+                                       : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int u = 0; u < kG; ++u) {
+                    const uint32_t wv[4] = {raw[u].x, raw[u].y, raw[u].z, raw[u].w};
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const float gvv = __uint_as_float((e & 1) ? (wv[e >> 1] & 0xffff0000u)
+                                                                  : (wv[e >> 1] << 16));
+                        const float t = __fsub_rn(qc[e], gvv);
+                        acc[u] = fmaf(t, t, acc[u]);
+                    }
+                }
+            }
+        } else {
+            for (int c = lane; c < d; c += 32) {
+                const float qc = __ldg(qv + c);
+                float gv[kG];
+#pragma unroll
+                for (int u = 0; u < kG; ++u) gv[u] = g[u] >= 0 ? __bfloat162float(cg[u][c]) : 0.0f;
+#pragma unroll
+                for (int u = 0; u < kG; ++u) {
+                    const float t = __fsub_rn(qc, gv[u]);
+                    acc[u] = fmaf(t, t, acc[u]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kG; ++u) {
+            const float sum = warp_sum(acc[u]);
+            if (lane == 0 && g[u] >= 0) gS[sl + u] = sum;
+        }
+    }
+}
+
+__device__ __forceinline__ float group_norm_of(const int32_t *gkey, const float *gS, int P2,
+                                               int32_t g)
+{
+    uint32_t h = group_slot(g, P2);
+    for (int p = 0; p < P2; ++p) {
+        if (gkey[h] == g) return gS[h];
+        h = (h + 1) & (uint32_t)(P2 - 1);
+    }
+    return 0.0f;  // not reached: every candidate's group was inserted
+}
+
+// Squared-distance bounds (lo2, hi2) of a candidate from P = q.r~ (above).
+__device__ __forceinline__ void expanded_bounds(float P, float S, float2 cr, float R, float qn,
+                                                float rho_s, float gam, float &lo2, float &hi2)
+{
+    const float a = __fadd_rn(__fadd_rn(__fsub_rn(S, 2.0f * P), 2.0f * cr.x), cr.y);
+    const float Rt = R * 1.004f;
+    const float Cn = qn + sqrtf(S) * 1.01f;
+    const float absum = S + 2.0f * fabsf(P) + 2.0f * fabsf(cr.x) + cr.y;
+    const float E2 = 1.01f * (rho_s * S + 2.0f * gam * qn * Rt + 0x1p-23f * Cn * Rt +
+                              0x1p-24f * cr.y + 3.03f * 0x1p-24f * absum);
+    const float tlo = fmaxf(a - E2, 0.0f) * (1.0f - 0x1p-20f);
+    const float thi = (a + E2) * (1.0f + 0x1p-20f);
+    const float wlo = tlo > 0.0f ? tlo * rsqrtf(tlo) : 0.0f;
+    const float whi = thi > 0.0f ? thi * rsqrtf(thi) : 0.0f;
+    const float e = 1.001f * 0x1.02p-8f * R;
+    const float lo = fmaxf(wlo * (1.0f - 0x1p-18f) - e * (1.0f + 0x1p-18f), 0.0f);
+    const float hi = (whi + e) * (1.0f + 0x1p-18f);
+    lo2 = lo * lo * (1.0f - 0x1p-18f);
+    hi2 = hi * hi * (1.0f + 0x1p-18f);
+}
+
 template <int kRows>
 __global__ void __launch_bounds__(RR_THREADS) rerank_bf16_kernel(
     const float *__restrict__ Xr, const int32_t *__restrict__ row_of,
     const __nv_bfloat16 *__restrict__ Rb, const float *__restrict__ rnorm,
-    const __nv_bfloat16 *__restrict__ Cg, int d, const float *__restrict__ Qb, int k, int cap, int P2,
-    const int32_t *__restrict__ cand, const int32_t *__restrict__ nkeep,
-    int64_t *__restrict__ ids_out, float *__restrict__ dists_out, bool vec, float inv_omr,
-    float inv_opr, unsigned long long *__restrict__ rows_fp32)
+    const float2 *__restrict__ rcr, const __nv_bfloat16 *__restrict__ Cg, int d,
+    const float *__restrict__ Qb, int k, int cap, int P2, const int32_t *__restrict__ cand,
+    const int32_t *__restrict__ nkeep, int64_t *__restrict__ ids_out,
+    float *__restrict__ dists_out, bool vec, bool vec8, bool vec16, float rho_s, float gam,
+    unsigned long long *__restrict__ rows_fp32)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int scan_tmp[RR_WARPS];
     __shared__ int any_mark;
     __shared__ int hist[256];
     __shared__ int bc[4];
+    __shared__ float s_qq;
+    __shared__ int hist2[2048];
     RerankSmem sm = carve_rerank(smraw, P2, scan_tmp, &any_mark, hist, bc);
     int32_t *cid = reinterpret_cast<int32_t *>(sm.mark + P2 + 15 - ((P2 + 15) % 16));  // P2 ids
+    int32_t *gkey = reinterpret_cast<int32_t *>(sm.key);  // P2 group slots (-1: empty)
+    float *gS = reinterpret_cast<float *>(sm.key) + P2;    // |q - C_g|^2 per slot
+    int32_t *rowi = sm.sid;                               // row of every candidate
     const int q = blockIdx.x;
     const int nc = nkeep[q];
     const float *qv = Qb + (int64_t)q * d;
     const int32_t *cl = cand + (int64_t)q * cap;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    // A. BF16 distances and their bounds (d32 <- lower, outd <- upper).  A
-    //    warp takes kRows candidates at a time (kRows independent row loads
-    //    per lane in flight); lane u then forms the bounds of row u.
-    // 0. the row of every candidate (staged in `key`, free until the FP32
-    //    stage), so the loop below starts its row loads without a dependent
-    //    chain of global reads
-    int32_t *rowi = reinterpret_cast<int32_t *>(sm.key);
+    // 0. ids, rows, empty group slots, |q|^2
     for (int j = threadIdx.x; j < nc; j += RR_THREADS) {
         const int32_t id = cl[j];
-        rowi[j] = row_of ? row_of[id] : id;
         cid[j] = id;
+        rowi[j] = row_of ? row_of[id] : id;
+    }
+    for (int sl = threadIdx.x; sl < P2; sl += RR_THREADS) gkey[sl] = -1;
+    if (warp == 0) {
+        float s = 0.0f;
+        for (int c = lane; c < d; c += 32) s = fmaf(__ldg(qv + c), __ldg(qv + c), s);
+        s = warp_sum(s);
+        if (lane == 0) s_qq = s;
     }
     __syncthreads();
-    // the query's 16-byte chunks c = lane + 32 i (i < kQReg) stay in registers
-    constexpr int kQReg = 2;
+    // 1. |q - C_g|^2 per distinct group
+    group_norms(rowi, nc, P2, gkey, gS, Cg, qv, d);
+    __syncthreads();
+    const float qn = sqrtf(s_qq) * 1.01f;  // >= |q|
+
+    // A. q.r~ and the bounds (d32 <- lower, outd <- upper).  A warp takes kRows
+    //    candidates at a time (kRows independent row loads per lane in flight,
+    //    8 bytes = 4 BF16 each); lane u then forms the bounds of row u.
+    //    The query's 16-byte chunks c = lane + 32 i (i < kQReg) stay in registers.
+    //    (16-byte form: chunk c = lane + 32 i of 8 coordinates in qreg[2i],
+    //    qreg[2i + 1])
+    constexpr int kQReg = 4;
     const int nch4 = d >> 2;
     float4 qreg[kQReg];
 #pragma unroll
     for (int i = 0; i < kQReg; ++i) {
-        const int c = lane + 32 * i;
-        qreg[i] = (vec && c < nch4) ? __ldg(reinterpret_cast<const float4 *>(qv) + c)
-                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int c = vec16 ? 2 * (lane + 32 * (i >> 1)) + (i & 1) : lane + 32 * i;
+        qreg[i] = ((vec16 || vec8) && c < nch4) ? __ldg(reinterpret_cast<const float4 *>(qv) + c)
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     for (int j0 = warp * kRows; j0 < nc; j0 += RR_WARPS * kRows) {
         int64_t row[kRows];
@@ -434,40 +615,61 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_bf16_kernel(
             row[u] = j < nc ? (int64_t)rowi[j] : -1;
             acc[u] = 0.0f;
         }
-        // lane u fetches row u's residual-norm bound early
-        const int jm = j0 + lane;
-        const float R = (lane < kRows && jm < nc) ? __ldg(rnorm + rowi[jm]) : 0.0f;
-        if (vec) {
-            const uint2 *r2[kRows];
-            const uint2 *g2[kRows];
+        // the lanes that will hold row u's sum (lanes 32 / kRows * u ...): the
+        // first of them fetches the row's constants early
+        constexpr int kLanesPerRow = 32 / kRows;
+        const int jm = j0 + lane / kLanesPerRow;
+        const bool mine_row = (lane % kLanesPerRow) == 0 && jm < nc;
+        const int64_t rm = mine_row ? (int64_t)rowi[jm] : 0;
+        const float R = mine_row ? __ldg(rnorm + rm) : 0.0f;
+        const float2 cr = mine_row ? __ldg(rcr + rm) : make_float2(0.0f, 0.0f);
+        if (vec16) {
+            // d a multiple of 256: lane chunks c = lane + 32 i of 8 BF16 each
+            const uint4 *r4[kRows];
 #pragma unroll
-            for (int u = 0; u < kRows; ++u) {
-                const int64_t rr = row[u] >= 0 ? row[u] : row[0];
-                r2[u] = reinterpret_cast<const uint2 *>(Rb + rr * d);
-                g2[u] = reinterpret_cast<const uint2 *>(Cg + (rr >> 7) * d);
+            for (int u = 0; u < kRows; ++u)
+                r4[u] = reinterpret_cast<const uint4 *>(Rb + (row[u] >= 0 ? row[u] : row[0]) * d);
+            auto chunk8 = [&](int c, const float4 b0, const float4 b1) {
+                uint4 raw[kRows];
+#pragma unroll
+                for (int u = 0; u < kRows; ++u) raw[u] = __ldg(r4[u] + c);
+#pragma unroll
+                for (int u = 0; u < kRows; ++u) {
+                    acc[u] = fmaf(b0.x, __uint_as_float(raw[u].x << 16), acc[u]);
+                    acc[u] = fmaf(b0.y, __uint_as_float(raw[u].x & 0xffff0000u), acc[u]);
+                    acc[u] = fmaf(b0.z, __uint_as_float(raw[u].y << 16), acc[u]);
+                    acc[u] = fmaf(b0.w, __uint_as_float(raw[u].y & 0xffff0000u), acc[u]);
+                    acc[u] = fmaf(b1.x, __uint_as_float(raw[u].z << 16), acc[u]);
+                    acc[u] = fmaf(b1.y, __uint_as_float(raw[u].z & 0xffff0000u), acc[u]);
+                    acc[u] = fmaf(b1.z, __uint_as_float(raw[u].w << 16), acc[u]);
+                    acc[u] = fmaf(b1.w, __uint_as_float(raw[u].w & 0xffff0000u), acc[u]);
+                }
+            };
+            const int nch8 = d >> 3;
+#pragma unroll
+            for (int i = 0; i < kQReg / 2; ++i) {
+                const int c = lane + 32 * i;
+                if (c < nch8) chunk8(c, qreg[2 * i], qreg[2 * i + 1]);
             }
+            for (int c = lane + 32 * (kQReg / 2); c < nch8; c += 32)
+                chunk8(c, __ldg(reinterpret_cast<const float4 *>(qv) + 2 * c),
+                       __ldg(reinterpret_cast<const float4 *>(qv) + 2 * c + 1));
+        } else if (vec8) {
+            const uint2 *r2[kRows];
+#pragma unroll
+            for (int u = 0; u < kRows; ++u)
+                r2[u] = reinterpret_cast<const uint2 *>(Rb + (row[u] >= 0 ? row[u] : row[0]) * d);
             // one 16-byte chunk of the query against 4 BF16 of each row
             auto chunk = [&](int c, const float4 b) {
-                uint2 raw[kRows], gr[kRows];
+                uint2 raw[kRows];
+#pragma unroll
+                for (int u = 0; u < kRows; ++u) raw[u] = __ldg(r2[u] + c);
 #pragma unroll
                 for (int u = 0; u < kRows; ++u) {
-                    raw[u] = __ldg(r2[u] + c);
-                    gr[u] = __ldg(g2[u] + c);
-                }
-#pragma unroll
-                for (int u = 0; u < kRows; ++u) {
-                    const float t0 = (b.x - __uint_as_float(gr[u].x << 16)) -
-                                     __uint_as_float(raw[u].x << 16);
-                    const float t1 = (b.y - __uint_as_float(gr[u].x & 0xffff0000u)) -
-                                     __uint_as_float(raw[u].x & 0xffff0000u);
-                    const float t2 = (b.z - __uint_as_float(gr[u].y << 16)) -
-                                     __uint_as_float(raw[u].y << 16);
-                    const float t3 = (b.w - __uint_as_float(gr[u].y & 0xffff0000u)) -
-                                     __uint_as_float(raw[u].y & 0xffff0000u);
-                    acc[u] = fmaf(t0, t0, acc[u]);
-                    acc[u] = fmaf(t1, t1, acc[u]);
-                    acc[u] = fmaf(t2, t2, acc[u]);
-                    acc[u] = fmaf(t3, t3, acc[u]);
+                    acc[u] = fmaf(b.x, __uint_as_float(raw[u].x << 16), acc[u]);
+                    acc[u] = fmaf(b.y, __uint_as_float(raw[u].x & 0xffff0000u), acc[u]);
+                    acc[u] = fmaf(b.z, __uint_as_float(raw[u].y << 16), acc[u]);
+                    acc[u] = fmaf(b.w, __uint_as_float(raw[u].y & 0xffff0000u), acc[u]);
                 }
             };
 #pragma unroll
@@ -481,42 +683,29 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_bf16_kernel(
             for (int c = lane; c < d; c += 32) {
                 const float qc = __ldg(qv + c);
 #pragma unroll
-                for (int u = 0; u < kRows; ++u) {
-                    if (row[u] < 0) continue;
-                    const float t0 = (qc - __bfloat162float(Cg[(row[u] >> 7) * d + c])) -
-                                     __bfloat162float(Rb[row[u] * d + c]);
-                    acc[u] = fmaf(t0, t0, acc[u]);
-                }
+                for (int u = 0; u < kRows; ++u)
+                    if (row[u] >= 0) acc[u] = fmaf(qc, __bfloat162float(Rb[row[u] * d + c]), acc[u]);
             }
         }
-        float mine = 0.0f;
-#pragma unroll
-        for (int u = 0; u < kRows; ++u) {
-            const float sum = warp_sum(acc[u]);
-            if (lane == u) mine = sum;
-        }
-        const int j = j0 + lane;
-        if (lane < kRows && j < nc) {
-            // bounds in FP32: every quantity below is within a few units in
-            // the last place of its exact value (rsqrtf: 2 ulp), covered by
-            // the 2^-18 margins
-            const float thi = mine * inv_omr, tlo = mine * inv_opr;
-            const float whi = thi > 0.0f ? thi * rsqrtf(thi) : 0.0f;
-            const float wlo = tlo > 0.0f ? tlo * rsqrtf(tlo) : 0.0f;
-            const float e = 1.001f * (0x1.02p-8f * R + 0x1p-24f * whi);
-            const float lo = fmaxf(wlo * (1.0f - 0x1p-18f) - e * (1.0f + 0x1p-18f), 0.0f);
-            const float hi = (whi + e) * (1.0f + 0x1p-18f);
-            sm.d32[j] = lo * lo * (1.0f - 0x1p-18f);
-            sm.outd[j] = hi * hi * (1.0f + 0x1p-18f);
+        const float P = rows_sum<kRows>(acc, lane);
+        if (mine_row) {
+            const float S = group_norm_of(gkey, gS, P2, (int32_t)(rm >> 7));
+            float lo2, hi2;
+            expanded_bounds(P, S, cr, R, qn, rho_s, gam, lo2, hi2);
+            sm.d32[jm] = lo2;
+            sm.outd[jm] = hi2;
         }
     }
     __syncthreads();
-    // B. the k-th smallest upper bound (non-negative: ordered like its bits)
+    // B. a bound uk >= the k-th smallest upper bound (non-negative: ordered like
+    //    its bits; at most 2^-13 above it): every candidate among the k nearest
+    //    has its lower bound <= uk
     float uk = CUDART_INF_F;
     if (nc > k)
-        uk = __uint_as_float(block_kth_smallest<RR_THREADS>(
-            reinterpret_cast<const uint32_t *>(sm.outd), nc, k, sm.hist, sm.bc));
+        uk = __uint_as_float(block_kth_upper<RR_THREADS>(
+            reinterpret_cast<const uint32_t *>(sm.outd), nc, k, hist2, sm.bc));
     // C. keep the candidates that could be among the k nearest, in list order
+    //    (the rows array in sid is no longer read)
     const int per = (nc + RR_THREADS - 1) / RR_THREADS;
     const int j0 = min(nc, (int)threadIdx.x * per), j1 = min(nc, j0 + per);
     int mine = 0;
@@ -533,37 +722,20 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_bf16_kernel(
                   dists_out + (int64_t)q * k, vec);
 }
 
-// BF16 pre-filter on the tensor cores.  The same residual copy r~ = bf16(r),
-// r = fl32(x - C_g), but the distance is expanded so that its only per-
-// candidate dot product is with the query itself: with u' = q - C_g (exact)
-// and w' = u' - r~,
-//   |w'|^2 = |q - C_g|^2 - 2 q.r~ + 2 C_g.r~ + |r~|^2.
-// q.r~ is an MMA: a tile of 128 candidates' residual rows (A, M = 128, K =
-// the dimension padded to 16) against the query split into BF16 hi and lo
-// parts (B, N = 16, two columns used); the BF16 products are exact in FP32,
-// and the tensor cores accumulate in FP32 in tensor memory.  C_g.r~ and
-// |r~|^2 are per-row constants computed at build time in FP64 and rounded to
-// FP32; |q - C_g|^2 is computed once per distinct group of the query's
-// candidates (FP32 chains, relative error rho_s).  The computed a satisfies
-// | a - |w'|^2 | <= E2 = rho_s S + 2 cP |q| R~ + 2^-23 |C_g| R~ + 2^-24 |r~|^2
-//                       + 3.03 2^-24 (S + 2|q.r~| + 2|C_g.r~| + |r~|^2),
-// cP = 2^-16 (the split of q) + 1.02 (K - 1) 2^-22 (the tensor cores' FP32
-// additions, reading R15) + 2^-23, R~ = 1.004 R >= |r~|, |C_g| <= |q| +
-// |q - C_g|.  And | |q - x| - |w'| | <= |(x - C_g) - r| + |r - r~| <=
-// 1.001 (2^-24 + 2^-8) R.  The bounds follow as in rerank_bf16_kernel, and
-// the same selection keeps every candidate that could be among the k
-// nearest for the exact FP32 / FP64 stages.  A tensor-core wait that gives up
-// marks every candidate of the query as a survivor (the result is still the
-// exact one) and sets bit 32 of *err.
+// BF16 pre-filter on the tensor cores.  The same residual copy, expansion and
+// bounds as rerank_bf16_kernel, but q.r~ is an MMA: a tile of 128 candidates'
+// residual rows (A, M = 128, K = the dimension padded to 16) against the query
+// split into BF16 hi and lo parts (B, N = 16, two columns used); the BF16
+// products are exact in FP32, and the tensor cores accumulate in FP32 in
+// tensor memory.  The dot product's coefficient gam becomes cP = 2^-16 (the
+// split of q) + 1.02 (K - 1) 2^-22 (the tensor cores' FP32 additions, reading
+// R15) + 2^-23.  A tensor-core wait that gives up marks every candidate of the
+// query as a survivor (the result is still the exact one) and sets bit 32 of
+// *err.
 constexpr int TR_ROWS = 128;  // candidates per MMA (M)
 constexpr int TR_N = 16;      // B rows: q_hi, q_lo, then zeros
 constexpr int TR_KC = 64;     // coordinates per staged chunk of the A tile
 constexpr int TR_STAGES = 4;  // chunks in flight
-
-__device__ __forceinline__ uint32_t group_slot(int32_t g, int P2)
-{
-    return ((uint32_t)g * 2654435761u) & (uint32_t)(P2 - 1);
-}
 
 __global__ void __launch_bounds__(RR_THREADS) rerank_tc_kernel(
     const float *__restrict__ Xr, const int32_t *__restrict__ row_of,
@@ -637,31 +809,8 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_tc_kernel(
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = tbase_s;
-    // 1. the candidates' distinct groups (open addressing; at most P2 probes,
-    //    and there are at most nc <= P2 distinct groups), then |q - C_g|^2 of
-    //    each, one warp per slot
-    for (int j = tid; j < nc; j += RR_THREADS) {
-        const int32_t g = rowi[j] >> 7;
-        uint32_t h = group_slot(g, P2);
-        for (int p = 0; p < P2; ++p) {
-            const int32_t old = atomicCAS(&gkey[h], -1, g);
-            if (old == -1 || old == g) break;
-            h = (h + 1) & (uint32_t)(P2 - 1);
-        }
-    }
-    __syncthreads();
-    for (int sl = warp; sl < P2; sl += RR_WARPS) {
-        const int32_t g = gkey[sl];
-        if (g < 0) continue;
-        const __nv_bfloat16 *cg = Cg + (int64_t)g * d;
-        float s = 0.0f;
-        for (int c = lane; c < d; c += 32) {
-            const float t = __fsub_rn(__ldg(qv + c), __bfloat162float(cg[c]));
-            s = fmaf(t, t, s);
-        }
-        s = warp_sum(s);
-        if (lane == 0) gS[sl] = s;
-    }
+    // 1. |q - C_g|^2 per distinct group
+    group_norms(rowi, nc, P2, gkey, gS, Cg, qv, d);
     __syncthreads();
     // 2. tiles of TR_ROWS candidates, each in chunks of KC coordinates; the
     //    chunks of all tiles run through a TR_STAGES-deep cp.async pipeline
@@ -747,34 +896,9 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_tc_kernel(
                 float lo2 = 0.0f, hi2 = CUDART_INF_F;
                 if (!stuck) {
                     const int64_t row = rowi[j];
-                    const int32_t g = (int32_t)(row >> 7);
-                    uint32_t h = group_slot(g, P2);
-                    float S = 0.0f;
-                    for (int p = 0; p < P2; ++p) {
-                        if (gkey[h] == g) {
-                            S = gS[h];
-                            break;
-                        }
-                        h = (h + 1) & (uint32_t)(P2 - 1);
-                    }
-                    const float Pq = __fadd_rn(v[0], v[1]);
-                    const float2 cr = __ldg(rcr + row);  // (C_g . r~, |r~|^2)
-                    const float R = __ldg(rnorm + row);
-                    const float a = __fadd_rn(__fadd_rn(__fsub_rn(S, 2.0f * Pq), 2.0f * cr.x), cr.y);
-                    const float Rt = R * 1.004f;
-                    const float Cn = qn + sqrtf(S) * 1.01f;
-                    const float absum = S + 2.0f * fabsf(Pq) + 2.0f * fabsf(cr.x) + cr.y;
-                    const float E2 = 1.01f * (rho_s * S + 2.0f * cP * qn * Rt + 0x1p-23f * Cn * Rt +
-                                              0x1p-24f * cr.y + 3.03f * 0x1p-24f * absum);
-                    const float tlo = fmaxf(a - E2, 0.0f) * (1.0f - 0x1p-20f);
-                    const float thi = (a + E2) * (1.0f + 0x1p-20f);
-                    const float wlo = tlo > 0.0f ? tlo * rsqrtf(tlo) : 0.0f;
-                    const float whi = thi > 0.0f ? thi * rsqrtf(thi) : 0.0f;
-                    const float e = 1.001f * 0x1.02p-8f * R;
-                    const float lo = fmaxf(wlo * (1.0f - 0x1p-18f) - e * (1.0f + 0x1p-18f), 0.0f);
-                    const float hi = (whi + e) * (1.0f + 0x1p-18f);
-                    lo2 = lo * lo * (1.0f - 0x1p-18f);
-                    hi2 = hi * hi * (1.0f + 0x1p-18f);
+                    const float S = group_norm_of(gkey, gS, P2, (int32_t)(row >> 7));
+                    expanded_bounds(__fadd_rn(v[0], v[1]), S, __ldg(rcr + row), __ldg(rnorm + row),
+                                    qn, rho_s, cP, lo2, hi2);
                 }
                 sm.d32[j] = lo2;
                 sm.outd[j] = hi2;
@@ -823,10 +947,11 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_tc_kernel(
     }
 
 qw_status launch_rerank_bf16(const IndexView &ix, const void *Rb, const float *rnorm,
-                             const void *C, const float *Qb, int nb, int k, int cap,
-                             const QueryState &st, int64_t *ids_out, float *dists_out,
+                             const float2 *rcr, const void *C, const float *Qb, int nb, int k,
+                             int cap, const QueryState &st, int64_t *ids_out, float *dists_out,
                              unsigned long long *rows_fp32, cudaStream_t s, int rows)
 {
+    if (nb == 0) return QW_OK;
     int P2 = 2;
     while (P2 < cap) P2 <<= 1;
     const size_t smem = (size_t)P2 * (sizeof(double) + 2 * sizeof(float) + sizeof(int32_t) + 1) +
@@ -838,15 +963,18 @@ qw_status launch_rerank_bf16(const IndexView &ix, const void *Rb, const float *r
     // rows in the locality order when the index has them (the copy's order)
     const float *Xr = ix.Xloc ? ix.Xloc : ix.X;
     const int32_t *row_of = ix.Xloc ? ix.inv : nullptr;
-    const bool vec = (ix.d % 4 == 0) && ((uintptr_t)Qb % 16 == 0) && ((uintptr_t)Xr % 16 == 0) &&
-                     ((uintptr_t)Rb % 8 == 0) && ((uintptr_t)C % 8 == 0);
-    // rho of the FP32 summation (the FP32 stage's bound): 1 / (1 -/+ rho)
-    const double rho = (double)((ix.d + 31) / 32 + 12) * 5.9604644775390625e-08 * 1.02;
-    const float inv_omr = (float)(1.0 / (1.0 - rho)), inv_opr = (float)(1.0 / (1.0 + rho));
+    const int d = ix.d;
+    const bool vec = (d % 4 == 0) && ((uintptr_t)Qb % 16 == 0) && ((uintptr_t)Xr % 16 == 0);
+    const bool vec8 = (d % 4 == 0) && ((uintptr_t)Qb % 16 == 0) && ((uintptr_t)Rb % 8 == 0);
+    const bool vec16 = (d % 256 == 0) && ((uintptr_t)Qb % 16 == 0) && ((uintptr_t)Rb % 16 == 0);
+    // rho of the FP32 chains (the FP32 stage's bound, >= 1.02 (ceil(d / 32) +
+    // 8) 2^-24 of the dot product's chains as well)
+    const double rho = (double)((d + 31) / 32 + 12) * 5.9604644775390625e-08 * 1.02;
+    const float rho_s = (float)(rho * 1.01);
     QW_RERANK_ROWS_DISPATCH(rows, rerank_bf16_kernel, <<<nb, RR_THREADS, smem, s>>>(
-        Xr, row_of, reinterpret_cast<const __nv_bfloat16 *>(Rb), rnorm,
-        reinterpret_cast<const __nv_bfloat16 *>(C), ix.d, Qb, k, cap, P2,
-        st.cand, st.nkeep, ids_out, dists_out, vec, inv_omr, inv_opr, rows_fp32))
+        Xr, row_of, reinterpret_cast<const __nv_bfloat16 *>(Rb), rnorm, rcr,
+        reinterpret_cast<const __nv_bfloat16 *>(C), d, Qb, k, cap, P2, st.cand, st.nkeep,
+        ids_out, dists_out, vec, vec8, vec16, rho_s, rho_s, rows_fp32))
     QW_CUDA_TRY(cudaGetLastError());
     return QW_OK;
 }

@@ -128,4 +128,59 @@ __device__ uint32_t block_kth_smallest(const uint32_t *v, int n, int kk, int *hi
         hist, bc);
 }
 
+// An upper bound U of the kk-th smallest (1-based, 1 <= kk <= n) of n
+// unsigned 32-bit keys with at least kk keys <= U: two radix passes of 11 bits
+// (bits 31..21, then 20..10), U = the found prefix with bits 9..0 set.  For
+// non-negative floats (ordered like their bits) U exceeds the kk-th smallest
+// by less than 2^-13 of it.  Block-wide over NT threads; hist: 2048 ints and
+// bc: 2 ints of shared memory.  Returns U in every thread.
+template <int NT>
+__device__ uint32_t block_kth_upper(const uint32_t *v, int n, int kk, int *hist, int *bc)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t prefix = 0, mask = 0;
+    for (int shift = 21; shift >= 10; shift -= 11) {
+        for (int i = threadIdx.x; i < 2048; i += NT) hist[i] = 0;
+        __syncthreads();
+        for (int j0 = 0; j0 < n; j0 += NT) {
+            const int j = j0 + threadIdx.x;
+            const uint32_t u = j < n ? v[j] : 0u;
+            const bool in = j < n && (u & mask) == prefix;
+            const uint32_t bin = in ? (u >> shift) & 2047u : 2048u + lane;
+            const uint32_t peers = __match_any_sync(0xffffffffu, bin);
+            if (in && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            // lane sums 64 bins, warp scan, then the lane holding kk walks them
+            int sl = 0;
+            for (int u = 0; u < 64; ++u) sl += hist[lane * 64 + u];
+            int incl = sl;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += y;
+            }
+            const int excl = incl - sl;
+            if (excl < kk && kk <= incl) {
+                int cum = excl;
+                for (int u = 0; u < 64; ++u) {
+                    const int c = hist[lane * 64 + u];
+                    if (cum < kk && kk <= cum + c) {
+                        bc[0] = lane * 64 + u;
+                        bc[1] = kk - cum;
+                    }
+                    cum += c;
+                }
+            }
+        }
+        __syncthreads();
+        prefix |= (uint32_t)bc[0] << shift;
+        mask |= 2047u << shift;
+        kk = bc[1];
+        __syncthreads();
+    }
+    return prefix | 1023u;
+}
+
 }  // namespace qw
