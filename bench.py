@@ -710,19 +710,16 @@ def run_ours(args):
     achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
     kept = float(st[:, 3].sum())
     bf16_rr = chosen_kw.get("rerank") in ("bf16", "bf16_tc")
-    if chosen_kw.get("rerank") == "bf16_tc":
-        # tensor-core pre-filter: per kept candidate its residual row (2 d) and
-        # its two per-row constants (8 B); FP32 stage: 4 d bytes per survivor
-        rr_bytes = (kept * (s.d * 2 + 8) + prof["rerank_fp32_rows"] / steps * s.d * 4
+    if bf16_rr:
+        # BF16 pass (both forms): per kept candidate its residual row (2 d) and
+        # its three per-row constants (12 B; the group means, read once per
+        # distinct group, are not counted); FP32 stage: 4 d bytes per survivor
+        rr_bytes = (kept * (s.d * 2 + 12) + prof["rerank_fp32_rows"] / steps * s.d * 4
                     + s.nq * s.d * 4 + s.nq * s.k * 12)
         rr_name = ("rerank_tc_kernel (residual BF16 pre-filter with q.r on the tensor cores, "
-                   "then FP32 gather + L2 + top-k of the survivors)")
-    elif bf16_rr:
-        # BF16 pass: per kept candidate its residual row and its group's mean
-        # (2 d bytes each); FP32 stage: 4 d bytes per surviving row
-        rr_bytes = (kept * s.d * 4 + prof["rerank_fp32_rows"] / steps * s.d * 4
-                    + s.nq * s.d * 4 + s.nq * s.k * 12)
-        rr_name = ("rerank_bf16_kernel (residual BF16 pre-filter, then FP32 gather + L2 + "
+                   "then FP32 gather + L2 + top-k of the survivors)"
+                   if chosen_kw.get("rerank") == "bf16_tc" else
+                   "rerank_bf16_kernel (residual BF16 pre-filter, then FP32 gather + L2 + "
                    "top-k of the survivors)")
     else:
         rr_bytes = kept * s.d * 4 + s.nq * s.d * 4 + s.nq * s.k * 12

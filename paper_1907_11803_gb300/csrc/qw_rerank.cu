@@ -430,9 +430,11 @@ __device__ __forceinline__ uint32_t group_slot(int32_t g, int P2)
 
 // The candidates' distinct groups into the open-addressed table gkey (P2
 // slots, -1 empty; at most nc <= P2 distinct groups, so an insertion ends
-// within P2 probes), then |q - C_g|^2 of each slot, one warp per slot.
+// within P2 probes); the insertion that takes a slot appends it to glist
+// (*ngroups, zero on entry).  Then |q - C_g|^2 of each listed slot.
 __device__ __forceinline__ void group_norms(const int32_t *rowi, int nc, int P2, int32_t *gkey,
-                                            float *gS, const __nv_bfloat16 *__restrict__ Cg,
+                                            float *gS, int32_t *glist, int *ngroups,
+                                            const __nv_bfloat16 *__restrict__ Cg,
                                             const float *__restrict__ qv, int d)
 {
     // 16-byte loads of the query and of the group means when aligned
@@ -443,31 +445,28 @@ __device__ __forceinline__ void group_norms(const int32_t *rowi, int nc, int P2,
         uint32_t h = group_slot(g, P2);
         for (int p = 0; p < P2; ++p) {
             const int32_t old = atomicCAS(&gkey[h], -1, g);
-            if (old == -1 || old == g) break;
+            if (old == -1) {
+                glist[atomicAdd(ngroups, 1)] = (int32_t)h;
+                break;
+            }
+            if (old == g) break;
             h = (h + 1) & (uint32_t)(P2 - 1);
         }
     }
     __syncthreads();
-    // a warp takes windows of kG slots of its share (rows of the occupied
-    // ones loaded together; windows without a group are skipped)
+    // a warp takes kG listed groups at a time, their rows' loads in flight
+    // together
     constexpr int kG = 8;
-    const int per = ((P2 + RR_WARPS - 1) / RR_WARPS + kG - 1) / kG * kG;
-    const int s1 = min(P2, (warp + 1) * per);
-    for (int sl = warp * per; sl < s1; sl += kG) {
-        int32_t g[kG];
-        bool any = false;
-#pragma unroll
-        for (int u = 0; u < kG; ++u) {
-            g[u] = sl + u < s1 ? gkey[sl + u] : -1;
-            any |= g[u] >= 0;
-        }
-        if (!any) continue;
+    const int G = *ngroups;
+    for (int base = warp * kG; base < G; base += RR_WARPS * kG) {
+        int32_t sl[kG];
         float acc[kG];
         const __nv_bfloat16 *cg[kG];
 #pragma unroll
         for (int u = 0; u < kG; ++u) {
+            sl[u] = base + u < G ? glist[base + u] : -1;
             acc[u] = 0.0f;
-            cg[u] = Cg + (int64_t)(g[u] >= 0 ? g[u] : 0) * d;
+            cg[u] = Cg + (int64_t)(sl[u] >= 0 ? gkey[sl[u]] : 0) * d;
         }
         if (vec16) {
             for (int c = lane; c < (d >> 3); c += 32) {
@@ -477,8 +476,8 @@ __device__ __forceinline__ void group_norms(const int32_t *rowi, int nc, int P2,
                 uint4 raw[kG];
 #pragma unroll
                 for (int u = 0; u < kG; ++u)
-                    raw[u] = g[u] >= 0 ? __ldg(reinterpret_cast<const uint4 *>(cg[u]) + c)
-                                       : make_uint4(0u, 0u, 0u, 0u);
+                    raw[u] = sl[u] >= 0 ? __ldg(reinterpret_cast<const uint4 *>(cg[u]) + c)
+                                        : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
                 for (int u = 0; u < kG; ++u) {
                     const uint32_t wv[4] = {raw[u].x, raw[u].y, raw[u].z, raw[u].w};
@@ -496,7 +495,7 @@ __device__ __forceinline__ void group_norms(const int32_t *rowi, int nc, int P2,
                 const float qc = __ldg(qv + c);
                 float gv[kG];
 #pragma unroll
-                for (int u = 0; u < kG; ++u) gv[u] = g[u] >= 0 ? __bfloat162float(cg[u][c]) : 0.0f;
+                for (int u = 0; u < kG; ++u) gv[u] = sl[u] >= 0 ? __bfloat162float(cg[u][c]) : 0.0f;
 #pragma unroll
                 for (int u = 0; u < kG; ++u) {
                     const float t = __fsub_rn(qc, gv[u]);
@@ -507,7 +506,7 @@ __device__ __forceinline__ void group_norms(const int32_t *rowi, int nc, int P2,
 #pragma unroll
         for (int u = 0; u < kG; ++u) {
             const float sum = warp_sum(acc[u]);
-            if (lane == 0 && g[u] >= 0) gS[sl + u] = sum;
+            if (lane == 0 && sl[u] >= 0) gS[sl[u]] = sum;
         }
     }
 }
@@ -560,6 +559,7 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_bf16_kernel(
     __shared__ int hist[256];
     __shared__ int bc[4];
     __shared__ float s_qq;
+    __shared__ int s_ngroups;
     __shared__ int hist2[2048];
     RerankSmem sm = carve_rerank(smraw, P2, scan_tmp, &any_mark, hist, bc);
     int32_t *cid = reinterpret_cast<int32_t *>(sm.mark + P2 + 15 - ((P2 + 15) % 16));  // P2 ids
@@ -579,6 +579,7 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_bf16_kernel(
         rowi[j] = row_of ? row_of[id] : id;
     }
     for (int sl = threadIdx.x; sl < P2; sl += RR_THREADS) gkey[sl] = -1;
+    if (threadIdx.x == 0) s_ngroups = 0;
     if (warp == 0) {
         float s = 0.0f;
         for (int c = lane; c < d; c += 32) s = fmaf(__ldg(qv + c), __ldg(qv + c), s);
@@ -586,14 +587,14 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_bf16_kernel(
         if (lane == 0) s_qq = s;
     }
     __syncthreads();
-    // 1. |q - C_g|^2 per distinct group
-    group_norms(rowi, nc, P2, gkey, gS, Cg, qv, d);
+    // 1. |q - C_g|^2 per distinct group (the group list in d32, free until A)
+    group_norms(rowi, nc, P2, gkey, gS, reinterpret_cast<int32_t *>(sm.d32), &s_ngroups, Cg, qv,
+                d);
     __syncthreads();
     const float qn = sqrtf(s_qq) * 1.01f;  // >= |q|
 
-    // A. q.r~ and the bounds (d32 <- lower, outd <- upper).  A warp takes kRows
-    //    candidates at a time (kRows independent row loads per lane in flight,
-    //    8 bytes = 4 BF16 each); lane u then forms the bounds of row u.
+    // A. q.r~ into d32.  A warp takes kRows candidates at a time (kRows
+    //    independent row loads per lane in flight, 8 or 16 bytes each).
     //    The query's 16-byte chunks c = lane + 32 i (i < kQReg) stay in registers.
     //    (16-byte form: chunk c = lane + 32 i of 8 coordinates in qreg[2i],
     //    qreg[2i + 1])
@@ -615,14 +616,6 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_bf16_kernel(
             row[u] = j < nc ? (int64_t)rowi[j] : -1;
             acc[u] = 0.0f;
         }
-        // the lanes that will hold row u's sum (lanes 32 / kRows * u ...): the
-        // first of them fetches the row's constants early
-        constexpr int kLanesPerRow = 32 / kRows;
-        const int jm = j0 + lane / kLanesPerRow;
-        const bool mine_row = (lane % kLanesPerRow) == 0 && jm < nc;
-        const int64_t rm = mine_row ? (int64_t)rowi[jm] : 0;
-        const float R = mine_row ? __ldg(rnorm + rm) : 0.0f;
-        const float2 cr = mine_row ? __ldg(rcr + rm) : make_float2(0.0f, 0.0f);
         if (vec16) {
             // d a multiple of 256: lane chunks c = lane + 32 i of 8 BF16 each
             const uint4 *r4[kRows];
@@ -687,14 +680,21 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_bf16_kernel(
                     if (row[u] >= 0) acc[u] = fmaf(qc, __bfloat162float(Rb[row[u] * d + c]), acc[u]);
             }
         }
+        // lanes 32 / kRows * u ... hold row u's sum
         const float P = rows_sum<kRows>(acc, lane);
-        if (mine_row) {
-            const float S = group_norm_of(gkey, gS, P2, (int32_t)(rm >> 7));
-            float lo2, hi2;
-            expanded_bounds(P, S, cr, R, qn, rho_s, gam, lo2, hi2);
-            sm.d32[jm] = lo2;
-            sm.outd[jm] = hi2;
-        }
+        const int jm = j0 + lane / (32 / kRows);
+        if ((lane % (32 / kRows)) == 0 && jm < nc) sm.d32[jm] = P;
+    }
+    __syncthreads();
+    // A2. the bounds, one candidate per thread (d32 <- lower, outd <- upper)
+    for (int j = threadIdx.x; j < nc; j += RR_THREADS) {
+        const int64_t row = rowi[j];
+        const float S = group_norm_of(gkey, gS, P2, (int32_t)(row >> 7));
+        float lo2, hi2;
+        expanded_bounds(sm.d32[j], S, __ldg(rcr + row), __ldg(rnorm + row), qn, rho_s, gam,
+                        lo2, hi2);
+        sm.d32[j] = lo2;
+        sm.outd[j] = hi2;
     }
     __syncthreads();
     // B. a bound uk >= the k-th smallest upper bound (non-negative: ordered like
@@ -754,6 +754,7 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_tc_kernel(
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tbase_s;
     __shared__ int s_stuck;
+    __shared__ int s_ngroups;
     __shared__ float s_qq;
     const int dk = (d + 15) & ~15;
     const int KC = dk < TR_KC ? dk : TR_KC;
@@ -771,6 +772,7 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_tc_kernel(
     const int32_t *cl = cand + (int64_t)q * cap;
     if (tid == 0) {
         s_stuck = 0;
+        s_ngroups = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -809,8 +811,10 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_tc_kernel(
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = tbase_s;
-    // 1. |q - C_g|^2 per distinct group
-    group_norms(rowi, nc, P2, gkey, gS, Cg, qv, d);
+    // 1. |q - C_g|^2 per distinct group (the group list in d32, free until
+    //    the tiles' bounds)
+    group_norms(rowi, nc, P2, gkey, gS, reinterpret_cast<int32_t *>(sm.d32), &s_ngroups, Cg, qv,
+                d);
     __syncthreads();
     // 2. tiles of TR_ROWS candidates, each in chunks of KC coordinates; the
     //    chunks of all tiles run through a TR_STAGES-deep cp.async pipeline
