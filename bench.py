@@ -99,6 +99,9 @@ def parse_args(argv=None):
                    help="workload order: grouped by bucket signature, or as given")
     p.add_argument("--rerank", choices=["fp32", "bf16", "bf16_tc"], default="bf16",
                    help="distance arithmetic of the chosen path (identical results)")
+    p.add_argument("--rerank-rows", type=int, choices=[0, 2, 4, 8], default=0,
+                   help="candidate rows a warp of the distance kernels takes at a time "
+                        "(0 = library choice; with --no-tune)")
     p.add_argument("--start", choices=["plain", "learned"], default="learned",
                    help="first level of the chosen path (identical results)")
     p.add_argument("--train-queries", type=int, default=20_000,
@@ -521,6 +524,8 @@ def run_ours(args):
     l2_arg = None if args.l2 == "off" else ("model" if args.l2 == "model" else int(args.l2))
     chosen_kw = dict(batch=args.batch, path=args.path, order=args.order, rerank=args.rerank,
                      start=args.start, graph=args.graph, loads=args.loads, l2=l2_arg)
+    if args.rerank_rows:
+        chosen_kw["rerank_rows"] = args.rerank_rows
     mlp = None
     train_info = None
     log(f"index built: {index.info.device_bytes / 1e9:.2f} GB on the device, "
