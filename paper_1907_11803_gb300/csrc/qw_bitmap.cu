@@ -1521,17 +1521,23 @@ __global__ void __launch_bounds__(RD_THREADS, 3) rd_emit_kernel(IndexView ix, Qu
 }
 
 // One block per slot with a long tie class: data ids 0, 1, 2, ... are tested
-// 256 at a time (tie member: a candidate of the last level, not of the
+// kScanPer * 256 at a time (thread t takes ids o0 + u * 256 + t, so the loads
+// of each u are coalesced and the kScanPer chains of dependent reads are in
+// flight together; tie member: a candidate of the last level, not of the
 // previous one, with count c*) until `take` members are found; those are the
 // take smallest original ids of the tie class (reading R5), listed with count
 // c*.  The walk reads about take * n / (tie class size) ids.
+constexpr int kScanPer = 4;
+
 __global__ void __launch_bounds__(RD_THREADS) rd_scan_kernel(IndexView ix, QueryState st,
                                                               bool tma, int wave)
 {
-    __shared__ int s_wc[RD_THREADS / 32];
+    constexpr int NW = RD_THREADS / 32;
+    __shared__ int s_wc[kScanPer][NW];
     __shared__ int s_base;
     const int nslot = min(st.rd_ctl[0], wave);
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
     for (int slot = blockIdx.x; slot < nslot; slot += gridDim.x) {
         const RdPlan pl = st.rd_plan[slot];
         if (pl.mode != 2 || pl.take <= 0) continue;
@@ -1541,35 +1547,65 @@ __global__ void __launch_bounds__(RD_THREADS) rd_scan_kernel(IndexView ix, Query
         __syncthreads();
         const int base = s_base;
         int found = 0;
-        for (int64_t o0 = 0; o0 < ix.n && found < pl.take; o0 += RD_THREADS) {
-            const int64_t o = o0 + threadIdx.x;
-            bool tie = false;
-            int64_t iid = 0;
-            if (o < ix.n) {
-                iid = ix.inv[o];
-                const int t = (int)(iid / kTile), g = (int)((iid % kTile) >> 7), b = (int)(iid & 127);
-                const int64_t qt = (int64_t)q * ix.nT + t;
-                const uint4 cw = rd_word(st, L, qt, g, tma);
-                if ((word_of(cw, b >> 5) >> (b & 31)) & 1u) {
-                    Planes P;
-                    uint4 pw;
-                    rd_stored(st, slot, ix.nT, t, g, P, pw);
-                    tie = !((word_of(pw, b >> 5) >> (b & 31)) & 1u) &&
-                          count_of(P, b >> 5, b & 31) == pl.cstar;
+        for (int64_t o0 = 0; o0 < ix.n && found < pl.take; o0 += RD_THREADS * kScanPer) {
+            int64_t iid[kScanPer];
+#pragma unroll
+            for (int u = 0; u < kScanPer; ++u) {
+                const int64_t o = o0 + u * RD_THREADS + threadIdx.x;
+                iid[u] = o < ix.n ? (int64_t)ix.inv[o] : -1;
+            }
+            uint4 cw[kScanPer];
+#pragma unroll
+            for (int u = 0; u < kScanPer; ++u) {
+                const int64_t id = iid[u] >= 0 ? iid[u] : 0;
+                const int t = (int)(id / kTile), g = (int)((id % kTile) >> 7);
+                cw[u] = iid[u] >= 0 ? rd_word(st, L, (int64_t)q * ix.nT + t, g, tma)
+                                    : make_uint4(0, 0, 0, 0);
+            }
+            bool tie[kScanPer];
+#pragma unroll
+            for (int u = 0; u < kScanPer; ++u) {
+                tie[u] = false;
+                const int64_t id = iid[u] >= 0 ? iid[u] : 0;
+                const int t = (int)(id / kTile), g = (int)((id % kTile) >> 7), b = (int)(id & 127);
+                if (iid[u] >= 0 && ((word_of(cw[u], b >> 5) >> (b & 31)) & 1u)) {
+                    // the id's bit of each stored plane and of the previous
+                    // level's word (word b / 32 of each 16-byte record)
+                    const uint32_t *rec = reinterpret_cast<const uint32_t *>(
+                        st.rd_store + ((int64_t)slot * ix.nT * kBmUint4 + (int64_t)t * kBmUint4 + g) *
+                                          kRdStoreWords) + (b >> 5);
+                    int cnt = 0;
+#pragma unroll
+                    for (int k = 0; k < 7; ++k) cnt |= (int)((rec[4 * k] >> (b & 31)) & 1u) << k;
+                    tie[u] = !((rec[4 * 7] >> (b & 31)) & 1u) && cnt == pl.cstar;
                 }
             }
-            const uint32_t bal = __ballot_sync(0xffffffffu, tie);
-            if (lane == 0) s_wc[wi] = __popc(bal);
-            __syncthreads();
-            int before = 0, total = 0;
+            uint32_t bal[kScanPer];
 #pragma unroll
-            for (int w = 0; w < RD_THREADS / 32; ++w) {
-                if (w < wi) before += s_wc[w];
-                total += s_wc[w];
+            for (int u = 0; u < kScanPer; ++u) {
+                bal[u] = __ballot_sync(0xffffffffu, tie[u]);
+                if (lane == 0) s_wc[u][wi] = __popc(bal[u]);
             }
-            const int rank = found + before + __popc(bal & ((1u << lane) - 1u));
-            if (tie && rank < pl.take && base + rank < kQCap)
-                E[base + rank] = ((uint64_t)iid << 32) | (uint64_t)pl.cstar;
+            __syncthreads();
+            // ties before (u, this warp) in id order: all of the earlier u,
+            // then the earlier warps of this u
+            int total = 0;
+#pragma unroll
+            for (int u = 0; u < kScanPer; ++u) {
+                int before = 0, tot_u = 0;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    const int c = s_wc[u][w];
+                    if (w < wi) before += c;
+                    tot_u += c;
+                }
+                if (tie[u]) {
+                    const int rank = found + total + before + __popc(bal[u] & lt);
+                    if (rank < pl.take && base + rank < kQCap)
+                        E[base + rank] = ((uint64_t)iid[u] << 32) | (uint64_t)pl.cstar;
+                }
+                total += tot_u;
+            }
             found += total;
             __syncthreads();  // s_wc is rewritten next
         }
