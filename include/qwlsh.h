@@ -86,8 +86,9 @@ typedef struct {
     int32_t shadow_bf16;  /* non-zero: also keep a BF16 copy of the data for the
                              QW_RERANK_BF16 pre-filter: rows in the rerank's row order (the
                              locality order when bitmaps are built) grouped by 128, each stored
-                             as the BF16 residual to its group's FP32 mean, with residual-norm
-                             bounds (2 * n * d + 4 * n + 4 * d * ceil(n / 128) bytes) */
+                             as the BF16 residual r~ to its group's mean C_g (kept in BF16),
+                             with a residual-norm bound and the constants C_g . r~ and |r~|^2
+                             per row (2 * n * d + 12 * n + 2 * d * ceil(n / 128) bytes) */
     int32_t bitmaps;      /* non-zero: also build the level bitmaps of QW_PATH_BITMAP: per
                              projection i, id tile and level L, one bitmap of the tile's ids
                              per level-L bucket; about m * n_tiles * (c/(c-1)) * (span_i + 1)
@@ -219,10 +220,13 @@ typedef struct {
 #define QW_START_LEARNED 1
 
 /* Candidate distance stage.  QW_RERANK_FP32: FP32 distances of every kept
- * candidate, FP64 for neighbours FP32 cannot order.  QW_RERANK_BF16: distances
- * from the residual BF16 copy first (see shadow_bf16), with a proven error
- * bound; only candidates that could still be among the k nearest go through
- * the FP32/FP64 stage.  QW_RERANK_BF16_TC: the same pre-filter with the
+ * candidate, FP64 for neighbours FP32 cannot order.  QW_RERANK_BF16: distance
+ * bounds from the residual BF16 copy first (see shadow_bf16): |q - C_g - r~|^2
+ * expanded as |q - C_g|^2 - 2 q.r~ + 2 C_g.r~ + |r~|^2, so a candidate costs
+ * one FP32 dot product with its BF16 row and |q - C_g|^2 is formed once per
+ * distinct group, with a proven error bound; only candidates that could still
+ * be among the k nearest go through the FP32/FP64 stage.  QW_RERANK_BF16_TC:
+ * the same pre-filter with the
  * candidates' residual rows multiplied by the query on the tensor cores
  * (tcgen05.mma, BF16 operands, the query split into BF16 hi + lo parts, FP32
  * accumulation in tensor memory; the per-row constants C_g . r~ and |r~|^2
