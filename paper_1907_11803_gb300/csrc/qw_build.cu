@@ -233,8 +233,8 @@ __global__ void group_centroid_kernel(const float *__restrict__ Xs, int64_t n, i
 }
 
 // Per row r: the BF16 residual r~ to its group mean, a bound R >= |r| of the
-// FP32 residual's norm, and (for the tensor-core pre-filter) C_g . r~ and
-// |r~|^2, summed in FP64 and rounded to FP32 (relative error 2^-24).
+// FP32 residual's norm, and (for the pre-filter's expanded distance) C_g . r~
+// and |r~|^2, summed in FP64 and rounded to FP32 (relative error 2^-24).
 __global__ void shadow_residual_kernel(const float *__restrict__ Xs, int64_t n, int d,
                                        const __nv_bfloat16 *__restrict__ C,
                                        __nv_bfloat16 *__restrict__ Rb, float *__restrict__ rnorm,
