@@ -523,8 +523,10 @@ int32_t qw_l2_split_model(double setaside, double index_bytes, double index_read
  * QW_ERR_CUDA. */
 qw_status qw_measure_read_bandwidth(int64_t bytes, int32_t reps, double *gbs, void *stream);
 
-/* Copy the index's profile counters into *out (host); reset them afterwards
- * when `reset` is non-zero. */
+/* Copy the index's profile counters (launch counts of every call; kernel
+ * times and work counters of calls made with qw_query_params.profile) into
+ * the host struct *out; reset them afterwards when `reset` is non-zero.
+ * QW_ERR_ARG for a NULL index or out. */
 qw_status qw_index_profile(qw_index *index, qw_profile *out, int32_t reset);
 
 /* Settings qw_autotune tried, with their median times. */
@@ -565,23 +567,36 @@ qw_status qw_autotune(qw_index *index, const float *queries, int64_t nq, int32_t
  * accumulation; trained with Adam by the library's kernels.  Parameters are a
  * flat float array: W1 (hidden x n_in, row-major), b1, W2 (hidden x hidden),
  * b2, W3 (classes x hidden), b3.  The caller provides the initial values (the
- * random draws of the method are inputs). */
+ * random draws of the method are inputs).  Every call below that takes a
+ * model returns QW_ERR_ARG for a NULL model or pointer argument (and names the
+ * problem in qw_last_error), QW_ERR_OOM when device memory runs out and
+ * QW_ERR_CUDA on a CUDA error.  qw_mlp_loss_grad and qw_mlp_train wait for
+ * their stream; qw_mlp_predict only enqueues its kernels on it. */
 typedef struct qw_mlp qw_mlp;
 
+/* A model with zeroed parameters, owned by the caller until qw_mlp_free.
+ * QW_ERR_ARG unless 1 <= n_in <= 65536, 1 <= hidden <= 65536 and
+ * 2 <= classes <= 1024. */
 qw_status qw_mlp_create(int32_t n_in, int32_t hidden, int32_t classes, qw_mlp **out);
+/* Number of parameters (the flat array's length), -1 for a NULL model. */
 int64_t qw_mlp_param_count(const qw_mlp *mlp);
-/* Host arrays of qw_mlp_param_count floats; set_params also resets Adam. */
+/* Host arrays of qw_mlp_param_count floats (QW_ERR_ARG for another count),
+ * copied in or out; set_params also resets Adam's moments. */
 qw_status qw_mlp_set_params(qw_mlp *mlp, const float *params, int64_t count);
 qw_status qw_mlp_get_params(const qw_mlp *mlp, float *params, int64_t count);
-/* Mean loss (host *loss) and its gradient (host grad, optional) over n rows:
- * X DEVICE n x n_in float32, y DEVICE n int32 class labels. */
+/* Mean loss (host *loss, optional) and its gradient (host grad of
+ * qw_mlp_param_count floats, optional) over n rows, 1 <= n <= 2^20: X DEVICE
+ * n x n_in float32 row-major, y DEVICE n int32 class labels in [0, classes). */
 qw_status qw_mlp_loss_grad(qw_mlp *mlp, const float *X, const int32_t *y, int64_t n, float *loss,
                            float *grad, void *stream);
-/* Adam (beta 0.9 / 0.999) over the rows in order, `batch` rows per step;
- * *final_loss (host, optional) = mean loss of the last epoch. */
+/* Adam (beta 0.9 / 0.999, step size lr > 0) over the rows in order, `batch`
+ * rows per step, `epochs` passes (n, epochs, batch >= 1); X and y as in
+ * qw_mlp_loss_grad.  *final_loss (host, optional) = mean loss of the last
+ * epoch. */
 qw_status qw_mlp_train(qw_mlp *mlp, const float *X, const int32_t *y, int64_t n, int32_t epochs,
                        int32_t batch, float lr, float *final_loss, void *stream);
-/* Class probabilities (DEVICE n x classes) of DEVICE rows X. */
+/* Class probabilities (DEVICE n x classes float32, softmax) of DEVICE rows X
+ * (n x n_in float32), n >= 0. */
 qw_status qw_mlp_predict(qw_mlp *mlp, const float *X, int64_t n, float *prob, void *stream);
 /* The same forward pass on the tensor cores (tcgen05.mma, FP16 activations
  * and weights, FP32 accumulators in tensor memory), 128 rows per CTA: the form
@@ -596,15 +611,20 @@ void qw_mlp_free(qw_mlp *mlp);
 /* Features of queries for the start model (DEVICE pointers): per query its
  * d coordinates divided by the data's RMS coordinate, then for each of the m
  * projections its position in the data's bucket-id range, (g + 0.5) /
- * (span + 1) - 0.5 clamped to [-1.5, 1.5]; F is nq x (d + m). */
+ * (span + 1) - 0.5 clamped to [-1.5, 1.5]; F is nq x (d + m) float32
+ * row-major, written by the library.  QW_ERR_ARG for a NULL index, NULL
+ * pointers with nq > 0 or nq < 0; QW_ERR_RANGE if a query's bucket id leaves
+ * the 32-bit range.  Waits for the stream. */
 qw_status qw_query_features(qw_index *index, const float *queries, int64_t nq, float *F,
                             void *stream);
 /* Attach a start model (not owned; it must outlive its use) with classes =
  * level index 0, 1, ...; eps in (0, 1) bounds the predicted probability of
- * starting too late.  NULL detaches. */
+ * starting too late.  NULL detaches.  QW_ERR_ARG for a NULL index, eps
+ * outside (0, 1), or a model whose input size is not d + m. */
 qw_status qw_index_set_start_model(qw_index *index, qw_mlp *mlp, float eps);
 
-/* Copy index metadata into *info (host). */
+/* Copy index metadata into the host struct *info.  QW_ERR_ARG for a NULL
+ * index or info. */
 qw_status qw_index_get_info(const qw_index *index, qw_index_info *info);
 
 /* Export the index for inspection, into HOST buffers: o and span (m int32),
