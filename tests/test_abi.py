@@ -107,6 +107,32 @@ def test_argument_errors_without_device(qwlib):
     L.qw_index_free(None)  # no-op
 
 
+def test_start_model_argument_errors_without_device(qwlib):
+    """The start-model, feature and bandwidth calls reject bad arguments before
+    any device work, with QW_ERR_ARG and a message naming the call."""
+    L = qwlib.load()
+    fake = C.c_void_p(16)
+    out = C.c_void_p()
+    for n_in, hidden, classes in ((0, 8, 4), (8, 0, 4), (8, 8, 1), (70000, 8, 4), (8, 8, 2000)):
+        assert L.qw_mlp_create(n_in, hidden, classes, C.byref(out)) == qwlib.QW_ERR_ARG
+        assert b"qw_mlp" in L.qw_last_error()
+    assert L.qw_mlp_create(8, 8, 4, None) == qwlib.QW_ERR_ARG
+    assert L.qw_mlp_param_count(None) == -1
+    assert L.qw_mlp_set_params(None, fake, 1) == qwlib.QW_ERR_ARG
+    assert L.qw_mlp_get_params(None, fake, 1) == qwlib.QW_ERR_ARG
+    assert L.qw_mlp_loss_grad(None, fake, fake, 1, None, None, None) == qwlib.QW_ERR_ARG
+    assert L.qw_mlp_train(None, fake, fake, 1, 1, 1, C.c_float(0.01), None, None) == qwlib.QW_ERR_ARG
+    assert L.qw_mlp_predict(None, fake, 1, fake, None) == qwlib.QW_ERR_ARG
+    assert L.qw_query_features(None, fake, 1, fake, None) == qwlib.QW_ERR_ARG
+    assert b"qw_query_features" in L.qw_last_error()
+    assert L.qw_index_set_start_model(None, None, C.c_float(0.5)) == qwlib.QW_ERR_ARG
+    gbs = C.c_double()
+    assert L.qw_measure_read_bandwidth(8, 1, C.byref(gbs), None) == qwlib.QW_ERR_ARG
+    assert L.qw_measure_read_bandwidth(1 << 20, 0, C.byref(gbs), None) == qwlib.QW_ERR_ARG
+    assert L.qw_measure_read_bandwidth(1 << 20, 1, None, None) == qwlib.QW_ERR_ARG
+    L.qw_mlp_free(None)  # no-op
+
+
 def test_binding_rejects_bad_tensors(qwlib):
     torch = pytest.importorskip("torch")
     x = torch.zeros((4, 3), dtype=torch.float32)
