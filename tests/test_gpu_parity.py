@@ -512,16 +512,22 @@ def test_bf16_prefilter_rerank_is_exact(orc, qwlib, cuda, d, path, rerank):
                  path=path)
 
 
-def test_bf16_tc_prefilter_many_candidates(orc, qwlib, cuda):
-    """The tensor-core pre-filter at k + v = 4,096 candidates per query in
-    d = 256 (32 MMA tiles per query, the largest shared-memory layout), and
-    with a ragged last tile: the oracle's ids."""
+@pytest.mark.parametrize("rerank", ["bf16", "bf16_tc"])
+def test_bf16_prefilter_many_candidates(orc, qwlib, cuda, rerank):
+    """Both pre-filter forms at k + v = 4,096 candidates per query in d = 256
+    (the CUDA-core form's 16-byte loads and two-pass k-th bound; 32 MMA tiles
+    per query, the largest shared-memory layout, for the tensor-core form),
+    with a ragged last tile, and at d = 512: the oracle's ids."""
     wl = workloads.make_workload("mix10k_d32", seed=34, n=30000, nq=40, d=256, m=16,
                                  n_clusters=8)
     _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=10, v=4086, l=2,
-                 rerank="bf16_tc", path="levels")
+                 rerank=rerank, path="levels")
     _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=7, v=1000, l=2,
-                 rerank="bf16_tc", path="levels")
+                 rerank=rerank, path="levels")
+    wl = workloads.make_workload("mix10k_d32", seed=35, n=8000, nq=24, d=512, m=16,
+                                 n_clusters=8)
+    _full_parity(orc, qwlib, cuda, wl.X, wl.Q, wl.A, wl.b, w=4.0, k=10, v=1500, l=2,
+                 rerank=rerank, path="levels")
 
 
 @pytest.mark.parametrize("rerank", ["bf16", "bf16_tc"])
