@@ -80,7 +80,7 @@ def parse_args(argv=None):
                    help="hash family: Section 3's bucketed h(v) = floor((a.v + b) / w), or "
                         "QALSH's query-centred intervals (level path, w = 2.719)")
     p.add_argument("--seed", type=int, default=0)
-    p.add_argument("--quality-sample", type=int, default=200,
+    p.add_argument("--quality-sample", type=int, default=1000,
                    help="queries checked against exact k-NN for recall / ratio")
     p.add_argument("--cpu-sample", type=int, default=2,
                    help="queries per host thread the CPU oracle answers (cpu_baseline entry; "
