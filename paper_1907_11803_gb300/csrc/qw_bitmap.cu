@@ -1042,9 +1042,11 @@ __device__ __forceinline__ void smem_bitonic(uint64_t *keys, int n, int P2)
 // kept, and of those at c* the ones with the smallest original ids (radix
 // selection of the take-th smallest id of the tie class).  The kept list is
 // written with its counts in no particular order, or in ascending original id
-// when `sorted`, plus the per-query statistics.  A query whose list or tie
-// class exceeds the fixed buffers is marked for the level path and keeps
-// nothing here.
+// when `sorted`, plus the per-query statistics.  A tie class longer than its
+// list (kEqCap ids) is selected from the candidate list itself.  A query whose
+// candidate list overflowed keeps nothing here and is marked (bm_ovf); the
+// list rebuild below shortens its list and this selection runs again on it (a
+// query whose rebuilt list would still overflow goes to the level path).
 constexpr int SEL_THREADS = 256;
 static_assert(kHistBins <= 256, "count histogram shares the radix histogram");
 
